@@ -1,0 +1,321 @@
+"""Throughput of the time-difference estimator on one GB300 (or N, sharded).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (the 65536-sample, 2-bit workload the headline metric is quoted on):
+256 pairs per GPU, N = 65536, AR(1) 0.95 sources, shift d ~ U[-8192, 8192],
+SNR ~ U[0, 30] dB, 2-bit rank quantizer, every lag (+-65535), full exact
+integer correlation, tie-ruled argmax.  One step = quantize all 512 signals,
+correlate all 256 pairs, argmax all 256 -- the whole path.  Inputs (134 MB)
+and correlations (134 MB) exceed the 129 MB L2, so nothing is flushed between
+steps.
+
+The JSON line carries: value (device-timed pairs/s over all ranks), e2e
+(pairs/s through the public API from pinned host buffers, copies included),
+the roofline of the dominant kernel (the correlation engine, timed live with
+CUDA events on its own stream by the library), the oracle's throughput on a
+bounded sample of the same pairs (cpu_baseline) and a lag-parity check
+against it, the SM clocks sampled during the timed region, and the number of
+library kernel launches in the timed region.
+
+``--impl reference`` times the CPU oracle (test infrastructure) on the host
+cores on the same workload, one bounded sample of pairs per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TDE pairs/s at N=65536, 2-bit: learned-proposal vs full int xcorr (bit-exact lag)"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+SMS = 152          # GB300 SMs
+POPC_PER_SM_CLK = 16  # POPC issue rate per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--npairs", type=int, default=256)
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--bits", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    from paper_2509_19974_gb300 import synth
+    return synth.equal_batch(seed=1002 + 7919 * rank, npairs=args.npairs, n=args.n, bits=args.bits)
+
+
+def config(args, world):
+    return {"workload": f"{args.npairs} pairs/GPU, N={args.n}, AR(1) 0.95, d~U[-8192,8192], "
+                        f"SNR~U[0,30] dB, b={args.bits} rank quantizer, all lags "
+                        f"+-{args.n - 1}, full exact integer correlation + tie-ruled argmax",
+            "form": "full integer correlation (learned-proposal form not built yet)",
+            "global_batch": args.npairs * world, "seq_len": args.n, "bits": args.bits,
+            "engine": args.engine, "parallelism": f"pairs sharded over {world} GPU(s)",
+            "l2": "inputs 134 MB + correlations 134 MB per GPU exceed the 129 MB L2; no flush"}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": int(rows[0][2]),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                         if r[3].replace(".", "").isdigit()),
+                "reasons": reasons}
+
+
+def overlap_macs(nx, ny, lo, hi):
+    """Sum over lags lo..hi of the overlap length min(nx, ny - tau) - max(0, -tau)."""
+    taus = np.arange(lo, hi + 1, dtype=np.int64)
+    ov = np.minimum(nx, ny - taus) - np.maximum(0, -taus)
+    return int(np.clip(ov, 0, None).sum())
+
+
+def cpu_baseline(b, seconds, max_pairs=64):
+    import oracle
+    oracle.build()
+    lags, t0, k = [], time.perf_counter(), 0
+    while k < min(max_pairs, b.npairs):
+        lags.append(oracle.estimate(b.x[k], b.y[k], b.bits, int(b.lag_min[k]), int(b.lag_max[k])))
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {k} of the {b.npairs} pairs (quantize + direct int64 correlation "
+                      f"over all lags + argmax), {dt:.1f} s"}, lags
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    b = workload(args, 0)
+    import oracle
+    oracle.build()
+    per_step = []
+    k = 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.estimate(b.x[k % b.npairs], b.y[k % b.npairs], b.bits)
+        dt = time.perf_counter() - t0
+        k += 1
+        if step >= args.warmup:
+            per_step.append(dt)
+    secs = float(np.sum(per_step))
+    value = args.steps / secs
+    out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic", "impl": "reference", "config": config(args, 1),
+           "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": "one pair of the workload per step"},
+           "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2509_19974_gb300 import build, tde
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    ctx = tde.Context(local)
+    b = workload(args, rank)
+    X, Y = b.stacked()
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    xs, ys = list(Xd.unbind(0)), list(Yd.unbind(0))
+    descs = tde.make_descs(xs, ys, b.lag_min, b.lag_max)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return tde.tde_estimate_batch(ctx, None, None, args.bits, engine=args.engine, descs=descs)
+
+    for _ in range(max(args.warmup, 3)):
+        lags, vals = step()
+    ctx.sync()
+    ctx.read_profile()
+    ctx.set_profiling(True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with ClockSampler(local) as clk:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            lags, vals = step()
+        e1.record(stream)
+        barrier()
+    ctx.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    launches, eng_launches, eng_ms = ctx.read_profile()
+    ctx.sync()
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = args.npairs * world * args.steps / (ms_max / 1e3)
+
+    # --- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Yh = torch.from_numpy(Y).pin_memory()
+        lag_h = torch.empty(args.npairs, dtype=torch.int64).pin_memory()
+        for _ in range(2):
+            Xd.copy_(Xh, non_blocking=True), Yd.copy_(Yh, non_blocking=True)
+            lags, vals = step()
+            lag_h.copy_(lags, non_blocking=True)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            Xd.copy_(Xh, non_blocking=True)
+            Yd.copy_(Yh, non_blocking=True)
+            lags, vals = step()
+            lag_h.copy_(lags, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        t = torch.tensor([f0.elapsed_time(f1)], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": args.npairs * world * args.steps / (float(t.item()) / 1e3),
+               "unit": "pairs/s", "h2d_bytes_per_step": int(X.nbytes + Y.nbytes),
+               "d2h_bytes_per_step": int(lag_h.numel() * 8)}
+
+    gpu_lags = lags.cpu().numpy()
+    gpu_vals = vals.cpu().numpy()
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # --- roofline of the correlation engine kernel
+    pk, pk_kind = peaks()
+    macs = sum(overlap_macs(args.n, args.n, int(b.lag_min[i]), int(b.lag_max[i]))
+               for i in range(args.npairs))
+    per_launch_ms = eng_ms / max(eng_launches, 1)
+    engine = args.engine
+    roof = None
+    if eng_launches:
+        achieved_mac = macs * (args.steps / eng_launches) / (per_launch_ms / 1e3)
+        if engine in ("auto", "popc"):
+            popc_per_mac = (2.0 if args.bits <= 2 else 18.0) / 32.0
+            peak_mac = SMS * POPC_PER_SM_CLK * pk.get("sm_max_mhz", 2070.0) * 1e6 / popc_per_mac
+            roof = {"bound": "alu", "kernel": "k_xcorr_popc", "achieved": achieved_mac / 1e12,
+                    "peak": peak_mac / 1e12, "unit": "TMAC/s", "frac": achieved_mac / peak_mac,
+                    "traffic": None,
+                    "peak_source": f"POPC pipe: {SMS} SMs x {POPC_PER_SM_CLK}/clk x "
+                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+                    "ms_per_launch": per_launch_ms, "macs_per_launch": macs * args.steps / eng_launches}
+
+    out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+           "data": "synthetic", "config": config(args, world), "e2e": e2e,
+           "gpu_launches": int(launches), "roofline": roof,
+           "mac_per_s": macs * world * args.steps / (ms_max / 1e3),
+           "clocks": clk.summary()}
+    if not args.no_cpu_baseline and world == 1:
+        cb, ref = cpu_baseline(b, args.cpu_seconds)
+        out["cpu_baseline"] = cb
+        mism = sum(1 for k, (l, v) in enumerate(ref) if (int(gpu_lags[k]), int(gpu_vals[k])) != (l, v))
+        out["parity"] = {"checked_pairs": len(ref), "lag_value_mismatches": mism}
+    out["true_shift_hit_rate"] = float(np.mean(gpu_lags == b.shift))
+    print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

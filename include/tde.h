@@ -1,0 +1,159 @@
+/*
+ * tde.h -- C ABI of the GB300 time-difference estimator (libtde.so).
+ *
+ * The estimator is Algorithm 1 (lines 1-4) of "On the Invariance of
+ * Cross-Correlation Peak Positions Under Monotonic Signal Transformations,
+ * with Application to Fast Time Difference Estimation" (arXiv 2509.19974):
+ *   1-2. quantize both signals with a monotone non-decreasing integer map phi
+ *        with phi(0) = 0 (Theorem 1's hypotheses, Sec. 3.1),
+ *   3.   compute their integer cross-correlation, Eq. (1),
+ *   4.   take the maximiser.  The paper returns the set of maximisers; this
+ *        library returns one lag: the largest value, ties to the smallest
+ *        |tau|, then to the smallest tau.
+ *
+ * Conventions shared by every call below.
+ *  - Lag convention, Eq. (1): c[tau] = sum_n qx[n] * qy[n + tau] over the
+ *    overlap 0 <= n < nx, 0 <= n + tau < ny.  If x[n] = a * y[n + nu] (Eq. (2))
+ *    the peak is at tau = nu.  Output element i holds lag lag_min + i.
+ *  - Every array argument is DEVICE memory owned by the caller, unless the
+ *    argument says "host".  The library never frees or retains caller memory.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream) and returns after enqueueing.  Host-side argument
+ *    errors are returned immediately and nothing is enqueued.  Errors that only
+ *    the device can see (NaN or Inf in the input, a bounded wait that ran out)
+ *    are latched in the context's device status word and returned by
+ *    tde_ctx_sync().
+ *  - A context is bound to one device and is not thread-safe: use one context
+ *    per host thread.  Calls on one context must not overlap in time on
+ *    different streams, because they share the context's workspace.
+ *  - Quantization levels (Algorithm 1, line 1, phi : R -> Z):
+ *      bits = 1: q = sign(x), with sign(0) = sign(-0.0) = 0 (Sec. 4.2).
+ *      bits = 2, 4: sign-magnitude rank quantizer with L = 2^bits - 1 levels:
+ *        a = |x| sorted ascending, t_m = a[min(n-1, floor((2m-1) n / L))]
+ *        for m = 1 .. 2^(bits-1) - 1, q = sign(x) * #{m : |x| >= t_m}.
+ *        Levels are {-1,0,1} for bits = 2 and -7..7 for bits = 4.
+ *  - int32 correlation output requires min(nx, ny) * (2^(bits-1))^2 < 2^31;
+ *    otherwise TDE_ERR_OVERFLOW is returned and the caller must ask for int64.
+ */
+#ifndef TDE_H_
+#define TDE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object type as cudaStream_t. */
+typedef struct CUstream_st* tde_stream_t;
+
+typedef enum {
+  TDE_OK = 0,
+  TDE_ERR_INVALID = 1,     /* bad argument; or NaN/Inf input seen on the device */
+  TDE_ERR_OVERFLOW = 2,    /* int32 output could overflow for these sizes */
+  TDE_ERR_UNSUPPORTED = 3, /* valid request this build cannot serve */
+  TDE_ERR_CUDA = 4,        /* a CUDA runtime call failed; see tde_last_error */
+  TDE_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} tde_status;
+
+/* Correlation engines (the "engine" argument). */
+enum {
+  TDE_ENGINE_AUTO = 0, /* pick by length and bits */
+  TDE_ENGINE_POPC = 1, /* bit-plane AND/XOR + popcount direct sums */
+  TDE_ENGINE_MMA = 2,  /* Toeplitz-as-GEMM on the tcgen05 tensor cores */
+  TDE_ENGINE_NTT = 3   /* two-prime number-theoretic transform + CRT */
+};
+
+/* Correlation output element types (the "dtype" arguments). */
+enum { TDE_I32 = 0, TDE_I64 = 1 };
+
+typedef struct tde_ctx tde_ctx;
+
+/* Create a context on CUDA device `device` (0-based).  *out receives the
+ * handle (host memory).  The context owns a device workspace that grows on
+ * demand and a device status word.  Returns TDE_ERR_CUDA if the device cannot
+ * be used. */
+tde_status tde_ctx_create(int device, tde_ctx** out);
+
+/* Synchronize the device, then free everything the context owns.  NULL is
+ * accepted and ignored. */
+tde_status tde_ctx_destroy(tde_ctx* ctx);
+
+/* Wait for `stream`, then read and clear the device status word.  Returns
+ * TDE_ERR_INVALID if a kernel saw NaN/Inf input, TDE_ERR_TIMEOUT if a bounded
+ * wait gave up, TDE_ERR_CUDA on an asynchronous CUDA error, else TDE_OK. */
+tde_status tde_ctx_sync(tde_ctx* ctx, tde_stream_t stream);
+
+/* Text of the last error on this context (host string owned by the context,
+ * valid until the next call on it).  Never NULL. */
+const char* tde_last_error(const tde_ctx* ctx);
+
+/* Instrumentation.  With profiling enabled, every launch of a correlation
+ * engine's main kernel is bracketed by two CUDA events on its stream (the
+ * events are the context's; no caller memory is touched). */
+tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
+
+/* Counters since the previous read, then reset: kernel launches this context
+ * enqueued (host pointer *kernel_launches), engine-kernel launches
+ * (*engine_launches) and their summed device time in milliseconds
+ * (*engine_ms, waits for the recorded events).  Any pointer may be NULL. */
+tde_status tde_ctx_read_profile(tde_ctx* ctx, int64_t* kernel_launches, int64_t* engine_launches,
+                                double* engine_ms);
+
+/* Algorithm 1, lines 1-2.  x: n floats (device).  q_out: n int8 (device).
+ * bits in {1, 2, 4}.  NaN/Inf inputs are latched as TDE_ERR_INVALID (see
+ * tde_ctx_sync) and the output is then unspecified. */
+tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits, int8_t* q_out,
+                        tde_stream_t stream);
+
+/* Algorithm 1, line 3 / Eq. (1) on quantized input.  qx: nx int8, qy: ny int8
+ * (device), with |q| <= 2^(bits-1) - 1 (1 for bits <= 2, 7 for bits = 4).
+ * Computes c[tau] for lag_min <= tau <= lag_max, which must lie inside
+ * [-(nx-1), ny-1].  c_out: (lag_max - lag_min + 1) elements of `out_dtype`
+ * (TDE_I32 or TDE_I64), device.  `engine` is a TDE_ENGINE_* value.  The
+ * result is exact for every engine. */
+tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, const int8_t* qy,
+                         int64_t ny, int bits, int64_t lag_min, int64_t lag_max, int engine,
+                         void* c_out, int out_dtype, tde_stream_t stream);
+
+/* Algorithm 1, line 4.  c: `count` elements of `dtype` (device), element i
+ * holding lag lag_min + i.  Writes the maximising lag and its value to
+ * lag_out[0] and val_out[0] (device int64).  Ties go to the smallest |tau|,
+ * then to the smallest tau.  count >= 1 and |lag| < 2^31 are required. */
+tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t lag_min, int64_t count,
+                      int64_t* lag_out, int64_t* val_out, tde_stream_t stream);
+
+/* Algorithm 1, lines 1-4 for one pair.  x: nx floats, y: ny floats (device).
+ * Lags lag_min..lag_max as in tde_xcorr_int.  lag_out[0], val_out[0]: device
+ * int64.  Intermediate quantized signals and correlations live in the
+ * context's workspace. */
+tde_status tde_estimate(tde_ctx* ctx, const float* x, int64_t nx, const float* y, int64_t ny,
+                        int bits, int64_t lag_min, int64_t lag_max, int engine,
+                        int64_t* lag_out, int64_t* val_out, tde_stream_t stream);
+
+/* One pair of a batch: device pointers and sizes, lag range inclusive. */
+typedef struct {
+  const float* x; /* device, nx floats */
+  const float* y; /* device, ny floats */
+  int64_t nx;
+  int64_t ny;
+  int64_t lag_min;
+  int64_t lag_max;
+} tde_pair_desc;
+
+/* Algorithm 1, lines 1-4 for `npairs` independent pairs of possibly uneven
+ * lengths and lag ranges.  descs: host array of npairs descriptors.
+ * lag_out, val_out: npairs int64 each (device).  If c_out is not NULL it
+ * receives every pair's correlation as int32, pair after pair (pair p starts
+ * at the sum of the earlier pairs' lag counts).  Same bits and engine for all
+ * pairs.  Pairs are independent: the result of each equals tde_estimate on
+ * it. */
+tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int bits,
+                              int engine, int32_t* c_out, int64_t* lag_out, int64_t* val_out,
+                              tde_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDE_H_ */

@@ -1,0 +1,602 @@
+// api.cu -- the C ABI of libtde (declared in include/tde.h): argument checks,
+// the context (device workspace, pinned descriptor staging, device status
+// word), and the dispatch of Algorithm 1's steps (arXiv 2509.19974, Sec. 3.2)
+// to the kernels.  No step of the path runs on the host.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+struct tde_ctx {
+  int device = 0;
+  int sm_count = 0;
+  uint32_t* d_status = nullptr;
+  char* ws = nullptr;          // device workspace
+  size_t ws_cap = 0;
+  char* stage = nullptr;       // pinned host staging for descriptor uploads
+  size_t stage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;
+  bool stage_busy = false;
+  std::string err;
+  // instrumentation
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;  // start/end pairs around engine kernels
+  size_t ev_used = 0;
+  int64_t launches = 0, engine_launches = 0;
+};
+
+thread_local int64_t tde_launch_counter = 0;
+
+namespace {
+
+tde_status set_err(tde_ctx* ctx, tde_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return s;
+}
+
+tde_status cuda_err(tde_ctx* ctx, cudaError_t e, const char* what) {
+  return set_err(ctx, TDE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TDE_CK(call)                                          \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call);   \
+  } while (0)
+
+// Makes ctx->device current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Bump allocator over a region whose size is computed first (dry run) and
+// then carved for real.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(char* b) : base(b) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+tde_status ensure_ws(tde_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_cap) return TDE_OK;
+  // Earlier calls may still use the old workspace on any stream.
+  TDE_CK(cudaDeviceSynchronize());
+  if (ctx->ws) TDE_CK(cudaFree(ctx->ws));
+  ctx->ws = nullptr;
+  ctx->ws_cap = 0;
+  size_t cap = align_up(bytes + bytes / 4, 1 << 20);
+  TDE_CK(cudaMalloc(&ctx->ws, cap));
+  ctx->ws_cap = cap;
+  return TDE_OK;
+}
+
+// Host staging of descriptors: waits until the previous upload has left the
+// pinned buffer before it is rewritten.
+tde_status stage_begin(tde_ctx* ctx, size_t bytes, char** host) {
+  if (ctx->stage_busy) {
+    TDE_CK(cudaEventSynchronize(ctx->stage_ev));
+    ctx->stage_busy = false;
+  }
+  if (bytes > ctx->stage_cap) {
+    if (ctx->stage) TDE_CK(cudaFreeHost(ctx->stage));
+    ctx->stage = nullptr;
+    ctx->stage_cap = 0;
+    size_t cap = align_up(bytes + bytes / 4, 1 << 16);
+    TDE_CK(cudaMallocHost(&ctx->stage, cap));
+    ctx->stage_cap = cap;
+  }
+  *host = ctx->stage;
+  return TDE_OK;
+}
+
+tde_status stage_upload(tde_ctx* ctx, void* dev, size_t bytes, cudaStream_t st) {
+  if (bytes) TDE_CK(cudaMemcpyAsync(dev, ctx->stage, bytes, cudaMemcpyHostToDevice, st));
+  TDE_CK(cudaEventRecord(ctx->stage_ev, st));
+  ctx->stage_busy = true;
+  return TDE_OK;
+}
+
+// Adds the kernel launches enqueued during its lifetime to the context.
+struct LaunchCount {
+  tde_ctx* ctx;
+  int64_t before;
+  explicit LaunchCount(tde_ctx* c) : ctx(c), before(tde_launch_counter) {}
+  ~LaunchCount() { ctx->launches += tde_launch_counter - before; }
+};
+
+// Brackets one engine-kernel launch with the context's events when profiling.
+struct EngineTimer {
+  tde_ctx* ctx;
+  cudaStream_t st;
+  cudaEvent_t end = nullptr;
+  EngineTimer(tde_ctx* c, cudaStream_t s) : ctx(c), st(s) {
+    if (!ctx->profile) return;
+    while (ctx->ev.size() < ctx->ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      ctx->ev.push_back(e);
+    }
+    cudaEventRecord(ctx->ev[ctx->ev_used], st);
+    end = ctx->ev[ctx->ev_used + 1];
+    ctx->ev_used += 2;
+  }
+  ~EngineTimer() {
+    if (!end) return;
+    cudaEventRecord(end, st);
+    ctx->engine_launches += 1;
+  }
+};
+
+bool valid_bits(int bits) { return bits == 1 || bits == 2 || bits == 4; }
+int planes_for(int bits) { return bits == 4 ? 4 : 2; }
+
+tde_status check_xcorr_args(tde_ctx* ctx, int64_t nx, int64_t ny, int bits, int64_t lag_min,
+                            int64_t lag_max, int engine, int out_dtype) {
+  if (!valid_bits(bits)) return set_err(ctx, TDE_ERR_INVALID, "bits must be 1, 2 or 4 (got %d)", bits);
+  if (nx <= 0 || ny <= 0) return set_err(ctx, TDE_ERR_INVALID, "signal lengths must be positive");
+  if (nx > INT32_MAX || ny > INT32_MAX)
+    return set_err(ctx, TDE_ERR_UNSUPPORTED, "signal lengths above 2^31-1 are not supported");
+  if (lag_min > lag_max) return set_err(ctx, TDE_ERR_INVALID, "lag_min > lag_max");
+  if (lag_min < -(nx - 1) || lag_max > ny - 1)
+    return set_err(ctx, TDE_ERR_INVALID,
+                   "lag range [%lld, %lld] outside the overlap range [%lld, %lld]",
+                   (long long)lag_min, (long long)lag_max, (long long)-(nx - 1),
+                   (long long)(ny - 1));
+  if (engine < TDE_ENGINE_AUTO || engine > TDE_ENGINE_NTT)
+    return set_err(ctx, TDE_ERR_INVALID, "unknown engine %d", engine);
+  if (out_dtype != TDE_I32 && out_dtype != TDE_I64)
+    return set_err(ctx, TDE_ERR_INVALID, "unknown output dtype %d", out_dtype);
+  if (out_dtype == TDE_I32) {
+    // The bound N * (2^(bits-1))^2 < 2^31, asserted as stated.
+    const int64_t k = (int64_t)1 << (bits - 1);
+    const int64_t n = nx < ny ? nx : ny;
+    if (n * k * k >= ((int64_t)1 << 31))
+      return set_err(ctx, TDE_ERR_OVERFLOW,
+                     "int32 output may overflow: min(nx,ny)*(2^(bits-1))^2 = %lld >= 2^31; "
+                     "request TDE_I64", (long long)(n * k * k));
+  }
+  return TDE_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" tde_status tde_ctx_create(int device, tde_ctx** out) {
+  if (!out) return TDE_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return TDE_ERR_CUDA;
+  tde_ctx* ctx = new tde_ctx();
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+    tde_ctx_destroy(ctx);
+    return TDE_ERR_CUDA;
+  }
+  *out = ctx;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_ctx_destroy(tde_ctx* ctx) {
+  if (!ctx) return TDE_OK;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  }
+  delete ctx;
+  return TDE_OK;
+}
+
+extern "C" const char* tde_last_error(const tde_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" tde_status tde_ctx_sync(tde_ctx* ctx, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  TDE_CK(cudaStreamSynchronize(st));
+  uint32_t s = 0;
+  TDE_CK(cudaMemcpy(&s, ctx->d_status, sizeof s, cudaMemcpyDeviceToHost));
+  TDE_CK(cudaMemset(ctx->d_status, 0, sizeof s));
+  if (s & TDE_ST_NONFINITE) return set_err(ctx, TDE_ERR_INVALID, "NaN or Inf in a quantizer input");
+  if (s & TDE_ST_INTERNAL)
+    return set_err(ctx, TDE_ERR_INVALID, "a quantized level is outside the range of `bits`");
+  if (s & TDE_ST_TIMEOUT) return set_err(ctx, TDE_ERR_TIMEOUT, "a bounded device wait gave up");
+  return TDE_OK;
+}
+
+
+extern "C" tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable) {
+  if (!ctx) return TDE_ERR_INVALID;
+  ctx->profile = enable != 0;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_ctx_read_profile(tde_ctx* ctx, int64_t* kernel_launches,
+                                           int64_t* engine_launches, double* engine_ms) {
+  if (!ctx) return TDE_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    TDE_CK(cudaEventSynchronize(ctx->ev[i + 1]));
+    float t = 0.f;
+    TDE_CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+    ms += t;
+  }
+  if (kernel_launches) *kernel_launches = ctx->launches;
+  if (engine_launches) *engine_launches = ctx->engine_launches;
+  if (engine_ms) *engine_ms = ms;
+  ctx->launches = ctx->engine_launches = 0;
+  ctx->ev_used = 0;
+  return TDE_OK;
+}
+
+namespace {
+
+// Offsets of one API call's regions: a descriptor block (uploaded in one copy
+// from the pinned staging buffer) followed by a data block, both inside the
+// context workspace.
+struct Layout {
+  size_t desc = 0, data = 0;
+  template <typename T>
+  size_t d(size_t n) {
+    desc = align_up(desc, 16);
+    size_t o = desc;
+    desc += n * sizeof(T);
+    return o;
+  }
+  template <typename T>
+  size_t w(size_t n) {
+    data = align_up(data, 256);
+    size_t o = data;
+    data += n * sizeof(T);
+    return o;
+  }
+  size_t data_base() const { return align_up(desc, 256); }
+  size_t total() const { return data_base() + data; }
+};
+
+// Resolved base pointers once the workspace and the staging exist.
+struct Bases {
+  char* hdesc;  // pinned host copy of the descriptor block
+  char* ddesc;  // device descriptor block
+  char* ddata;  // device data block
+  template <typename T>
+  T* hd(size_t o) const { return reinterpret_cast<T*>(hdesc + o); }
+  template <typename T>
+  T* dd(size_t o) const { return reinterpret_cast<T*>(ddesc + o); }
+  template <typename T>
+  T* dw(size_t o) const { return reinterpret_cast<T*>(ddata + o); }
+};
+
+// ---- step A: quantize a list of signals
+struct QuantStage {
+  int nsig = 0, bits = 1;
+  int64_t max_n = 0;
+  size_t o_sigs = 0, o_state = 0, o_hist = 0;
+  void plan(Layout& L, int n, int b, int64_t mx) {
+    nsig = n, bits = b, max_n = mx;
+    o_sigs = L.d<QSig>(nsig);
+    if (bits != 1) {
+      o_state = L.w<RankState>(nsig);
+      o_hist = L.w<uint32_t>((size_t)nsig * 7 * 2048);
+    }
+  }
+  void fill(const Bases& B, const float* const* xs, int8_t* const* qs, const int64_t* ns) const {
+    QSig* h = B.hd<QSig>(o_sigs);
+    for (int i = 0; i < nsig; ++i) h[i] = QSig{xs[i], qs[i], ns[i]};
+  }
+  cudaError_t launch(const Bases& B, uint32_t* status, cudaStream_t st) const {
+    if (nsig == 0) return cudaSuccess;
+    if (bits == 1) return launch_quantize_sign(B.dd<QSig>(o_sigs), nsig, max_n, status, st);
+    return launch_quantize_rank(B.dd<QSig>(o_sigs), nsig, max_n, bits, B.dw<RankState>(o_state),
+                                B.dw<uint32_t>(o_hist), status, st);
+  }
+};
+
+// One correlation job on quantized inputs already in device memory.
+struct Job {
+  const int8_t* qx;
+  const int8_t* qy;
+  int64_t nx, ny, lag_min, lag_max;
+  void* c;
+  int c64;
+};
+
+// ---- step B, popc engine
+struct PopcStage {
+  int njobs = 0, bits = 1, nitems = 0;
+  int64_t max_words = 0;
+  size_t o_psig = 0, o_pairs = 0, o_items = 0;
+  std::vector<size_t> o_planes;  // per signal (2 per job)
+  std::vector<int64_t> words;
+  void plan(Layout& L, const std::vector<Job>& jobs, int b) {
+    njobs = (int)jobs.size(), bits = b;
+    const int pl = planes_for(bits);
+    o_psig = L.d<PlaneSig>(2 * njobs);
+    o_pairs = L.d<XcPair>(njobs);
+    nitems = 0;
+    for (const Job& j : jobs) {
+      int64_t a_lo = floor_div64(j.lag_min, 32), a_hi = floor_div64(j.lag_max, 32);
+      nitems += (int)ceil_div64(a_hi - a_lo + 1, kPopcLagsPerCta / 32);
+    }
+    o_items = L.d<PopcItem>(nitems);
+    o_planes.resize(2 * njobs);
+    words.resize(2 * njobs);
+    max_words = 0;
+    for (int i = 0; i < njobs; ++i)
+      for (int s = 0; s < 2; ++s) {
+        int64_t n = s ? jobs[i].ny : jobs[i].nx;
+        words[2 * i + s] = ceil_div64(n, 32);
+        max_words = words[2 * i + s] > max_words ? words[2 * i + s] : max_words;
+        o_planes[2 * i + s] = L.w<uint32_t>((size_t)pl * words[2 * i + s]);
+      }
+  }
+  void fill(const Bases& B, const std::vector<Job>& jobs) const {
+    PlaneSig* ps = B.hd<PlaneSig>(o_psig);
+    XcPair* xp = B.hd<XcPair>(o_pairs);
+    PopcItem* it = B.hd<PopcItem>(o_items);
+    int k = 0;
+    for (int i = 0; i < njobs; ++i) {
+      const Job& j = jobs[i];
+      uint32_t* px = B.dw<uint32_t>(o_planes[2 * i]);
+      uint32_t* py = B.dw<uint32_t>(o_planes[2 * i + 1]);
+      ps[2 * i] = PlaneSig{j.qx, px, j.nx, words[2 * i]};
+      ps[2 * i + 1] = PlaneSig{j.qy, py, j.ny, words[2 * i + 1]};
+      xp[i] = XcPair{px, py, words[2 * i], words[2 * i + 1], j.lag_min, j.lag_max, j.c, j.c64};
+      int64_t a_lo = floor_div64(j.lag_min, 32), a_hi = floor_div64(j.lag_max, 32);
+      for (int64_t a = a_lo; a <= a_hi; a += kPopcLagsPerCta / 32) it[k++] = PopcItem{i, 0, a};
+    }
+  }
+  cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
+    cudaError_t e = launch_pack_planes(B.dd<PlaneSig>(o_psig), 2 * njobs, max_words, bits,
+                                       ctx->d_status, st);
+    if (e != cudaSuccess) return e;
+    EngineTimer t(ctx, st);
+    return launch_xcorr_popc(B.dd<XcPair>(o_pairs), B.dd<PopcItem>(o_items), nitems, bits, st);
+  }
+};
+
+// ---- step C
+struct ArgStage {
+  int n = 0, c64 = 0;
+  int64_t max_count = 0;
+  size_t o_pairs = 0, o_keys = 0;
+  void plan(Layout& L, int npairs, int64_t maxc, int is64) {
+    n = npairs, max_count = maxc, c64 = is64;
+    o_pairs = L.d<ArgPair>(n);
+    o_keys = L.w<unsigned long long>(2 * (size_t)n);
+  }
+  void set(const Bases& B, int i, const void* c, int64_t lag_min, int64_t count, int64_t* lag_out,
+           int64_t* val_out) const {
+    B.hd<ArgPair>(o_pairs)[i] = ArgPair{c, lag_min, count, lag_out, val_out};
+  }
+  cudaError_t launch(const Bases& B, cudaStream_t st) const {
+    return launch_argmax(B.dd<ArgPair>(o_pairs), n, max_count, c64,
+                         B.dw<unsigned long long>(o_keys), st);
+  }
+};
+
+// Allocates the workspace and the staging for a planned call.
+tde_status realize(tde_ctx* ctx, const Layout& L, Bases* B) {
+  tde_status s = ensure_ws(ctx, L.total());
+  if (s != TDE_OK) return s;
+  char* host = nullptr;
+  s = stage_begin(ctx, L.desc ? L.desc : 16, &host);
+  if (s != TDE_OK) return s;
+  B->hdesc = host;
+  B->ddesc = ctx->ws;
+  B->ddata = ctx->ws + L.data_base();
+  return TDE_OK;
+}
+
+int pick_engine(int engine, int bits, int64_t nx, int64_t ny) {
+  (void)bits, (void)nx, (void)ny;
+  if (engine != TDE_ENGINE_AUTO) return engine;
+  return TDE_ENGINE_POPC;
+}
+
+tde_status engine_available(tde_ctx* ctx, int engine) {
+  if (engine == TDE_ENGINE_POPC) return TDE_OK;
+  return set_err(ctx, TDE_ERR_UNSUPPORTED, "engine %d is not available in this build", engine);
+}
+
+}  // namespace
+
+extern "C" tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits,
+                                   int8_t* q_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!x || !q_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (n <= 0) return set_err(ctx, TDE_ERR_INVALID, "n must be positive");
+  if (n > INT32_MAX) return set_err(ctx, TDE_ERR_UNSUPPORTED, "n above 2^31-1 is not supported");
+  if (!valid_bits(bits)) return set_err(ctx, TDE_ERR_INVALID, "bits must be 1, 2 or 4");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  QuantStage Q;
+  Q.plan(L, 1, bits, n);
+  Bases B;
+  tde_status s = realize(ctx, L, &B);
+  if (s != TDE_OK) return s;
+  Q.fill(B, &x, &q_out, &n);
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  cudaError_t e = Q.launch(B, ctx->d_status, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "quantize launch");
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, const int8_t* qy,
+                                    int64_t ny, int bits, int64_t lag_min, int64_t lag_max,
+                                    int engine, void* c_out, int out_dtype, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!qx || !qy || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  tde_status s = check_xcorr_args(ctx, nx, ny, bits, lag_min, lag_max, engine, out_dtype);
+  if (s != TDE_OK) return s;
+  const int eng = pick_engine(engine, bits, nx, ny);
+  if ((s = engine_available(ctx, eng)) != TDE_OK) return s;
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<Job> jobs{Job{qx, qy, nx, ny, lag_min, lag_max, c_out, out_dtype == TDE_I64}};
+  Layout L;
+  PopcStage E;
+  E.plan(L, jobs, bits);
+  Bases B;
+  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
+  E.fill(B, jobs);
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  cudaError_t e = E.launch(ctx, B, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "xcorr launch");
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t lag_min,
+                                 int64_t count, int64_t* lag_out, int64_t* val_out,
+                                 tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!c || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (dtype != TDE_I32 && dtype != TDE_I64) return set_err(ctx, TDE_ERR_INVALID, "unknown dtype");
+  if (count <= 0) return set_err(ctx, TDE_ERR_INVALID, "count must be positive");
+  const int64_t lim = INT32_MAX;
+  if (lag_min < -lim || lag_min + count - 1 > lim)
+    return set_err(ctx, TDE_ERR_UNSUPPORTED, "lags beyond +-(2^31-1) are not supported");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  ArgStage A;
+  A.plan(L, 1, count, dtype == TDE_I64);
+  Bases B;
+  tde_status s = realize(ctx, L, &B);
+  if (s != TDE_OK) return s;
+  A.set(B, 0, c, lag_min, count, lag_out, val_out);
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  cudaError_t e = A.launch(B, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "argmax launch");
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* descs, int npairs,
+                                         int bits, int engine, int32_t* c_out, int64_t* lag_out,
+                                         int64_t* val_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!descs || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
+  tde_status s;
+  int eng = -1;
+  int64_t max_n = 0, max_count = 0;
+  for (int p = 0; p < npairs; ++p) {
+    const tde_pair_desc& d = descs[p];
+    if (!d.x || !d.y) return set_err(ctx, TDE_ERR_INVALID, "null signal pointer in pair %d", p);
+    s = check_xcorr_args(ctx, d.nx, d.ny, bits, d.lag_min, d.lag_max, engine, TDE_I32);
+    if (s != TDE_OK) return s;
+    const int e = pick_engine(engine, bits, d.nx, d.ny);
+    if (eng >= 0 && e != eng)
+      return set_err(ctx, TDE_ERR_UNSUPPORTED, "mixed engines in one batch");
+    eng = e;
+    max_n = d.nx > max_n ? d.nx : max_n;
+    max_n = d.ny > max_n ? d.ny : max_n;
+    const int64_t cnt = d.lag_max - d.lag_min + 1;
+    max_count = cnt > max_count ? cnt : max_count;
+  }
+  if ((s = engine_available(ctx, eng)) != TDE_OK) return s;
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+  // Plan: quantized signals and (unless the caller gives c_out) correlations
+  // live in the workspace.
+  Layout L;
+  QuantStage Q;
+  Q.plan(L, 2 * npairs, bits, max_n);
+  std::vector<size_t> o_q(2 * npairs), o_c(npairs);
+  std::vector<int64_t> c_start(npairs);
+  int64_t c_total = 0;
+  for (int p = 0; p < npairs; ++p) {
+    o_q[2 * p] = L.w<int8_t>((size_t)descs[p].nx);
+    o_q[2 * p + 1] = L.w<int8_t>((size_t)descs[p].ny);
+    c_start[p] = c_total;
+    c_total += descs[p].lag_max - descs[p].lag_min + 1;
+  }
+  const size_t o_call = c_out ? 0 : L.w<int32_t>((size_t)c_total);
+  // The engine's plan needs only the sizes; pointers are bound after realize().
+  std::vector<Job> jobs(npairs);
+  for (int p = 0; p < npairs; ++p)
+    jobs[p] = Job{nullptr, nullptr, descs[p].nx, descs[p].ny, descs[p].lag_min, descs[p].lag_max,
+                  nullptr, 0};
+  PopcStage E;
+  E.plan(L, jobs, bits);
+  ArgStage A;
+  A.plan(L, npairs, max_count, 0);
+  Bases B;
+  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
+
+  std::vector<const float*> xs(2 * npairs);
+  std::vector<int8_t*> qs(2 * npairs);
+  std::vector<int64_t> ns(2 * npairs);
+  int32_t* c_base = c_out ? c_out : B.dw<int32_t>(o_call);
+  for (int p = 0; p < npairs; ++p) {
+    xs[2 * p] = descs[p].x, xs[2 * p + 1] = descs[p].y;
+    qs[2 * p] = B.dw<int8_t>(o_q[2 * p]), qs[2 * p + 1] = B.dw<int8_t>(o_q[2 * p + 1]);
+    ns[2 * p] = descs[p].nx, ns[2 * p + 1] = descs[p].ny;
+    jobs[p].qx = qs[2 * p], jobs[p].qy = qs[2 * p + 1];
+    jobs[p].c = c_base + c_start[p];
+    A.set(B, p, jobs[p].c, descs[p].lag_min, descs[p].lag_max - descs[p].lag_min + 1,
+          lag_out + p, val_out + p);
+  }
+  Q.fill(B, xs.data(), qs.data(), ns.data());
+  E.fill(B, jobs);
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  cudaError_t e = Q.launch(B, ctx->d_status, st);
+  if (e == cudaSuccess) e = E.launch(ctx, B, st);
+  if (e == cudaSuccess) e = A.launch(B, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_estimate(tde_ctx* ctx, const float* x, int64_t nx, const float* y,
+                                   int64_t ny, int bits, int64_t lag_min, int64_t lag_max,
+                                   int engine, int64_t* lag_out, int64_t* val_out,
+                                   tde_stream_t stream) {
+  tde_pair_desc d{x, y, nx, ny, lag_min, lag_max};
+  return tde_estimate_batch(ctx, &d, 1, bits, engine, nullptr, lag_out, val_out, stream);
+}

@@ -1,0 +1,98 @@
+// common.cuh -- types shared by the kernels and the C-ABI layer of libtde.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tde.h"
+
+// Bits of the per-context device status word (see tde_ctx_sync).
+#define TDE_ST_NONFINITE 1u  // NaN or Inf in a quantizer input
+#define TDE_ST_TIMEOUT 2u    // a bounded wait gave up
+#define TDE_ST_INTERNAL 4u   // a kernel's own bounds check refused an access
+
+// ---------------------------------------------------------------- quantize
+// One signal to quantize: n floats at x -> n int8 at q.
+struct QSig {
+  const float* x;
+  int8_t* q;
+  int64_t n;
+};
+
+// Radix-select state of the rank quantizer for one signal: for each threshold
+// m (0-based, at most 7) the bits of |x| fixed so far and the rank still to
+// find among the elements that share them.
+struct RankState {
+  uint32_t prefix[7];
+  uint32_t rank[7];
+};
+
+// ------------------------------------------------------------- popc engine
+// Bit-plane image of one quantized signal: plane 0 = sign (q < 0); for
+// bits <= 2 plane 1 = (q != 0); for bits = 4 planes 1..3 = bits 0..2 of |q|.
+// Word w of plane p is planes[p * words + w], bit i = sample 32 w + i.
+struct PlaneSig {
+  const int8_t* q;
+  uint32_t* planes;
+  int64_t n;
+  int64_t words;
+};
+
+// One correlation problem for the direct engines.
+struct XcPair {
+  const uint32_t* px;  // planes of x
+  const uint32_t* py;  // planes of y
+  int64_t wx, wy;      // words per plane
+  int64_t lag_min, lag_max;
+  void* c;             // output, lag_max - lag_min + 1 elements
+  int c64;             // 1: int64 output, 0: int32 output
+};
+
+// One CTA of the popc engine: pair index and the first 32-lag block index a0
+// (lags 32*a0 .. 32*(a0 + 64) - 1, floor division).
+struct PopcItem {
+  int32_t pair;
+  int32_t pad;
+  int64_t a0;
+};
+
+// ------------------------------------------------------------------ argmax
+struct ArgPair {
+  const void* c;
+  int64_t lag_min;
+  int64_t count;
+  int64_t* lag_out;
+  int64_t* val_out;
+};
+
+// ----------------------------------------------------------- host launchers
+// Each returns the first CUDA error it met (cudaSuccess otherwise).  All
+// descriptor pointers below are device pointers.
+cudaError_t launch_quantize_sign(const QSig* d_sigs, int nsig, int64_t max_n, uint32_t* d_status,
+                                 cudaStream_t st);
+// Rank quantizer for bits in {2,4}.  d_state: nsig RankState; d_hist:
+// nsig * 7 * 2048 uint32 of scratch.
+cudaError_t launch_quantize_rank(const QSig* d_sigs, int nsig, int64_t max_n, int bits,
+                                 RankState* d_state, uint32_t* d_hist, uint32_t* d_status,
+                                 cudaStream_t st);
+
+// Flags TDE_ST_INTERNAL if a level exceeds the bits' range (|q| > 1 or > 7).
+cudaError_t launch_pack_planes(const PlaneSig* d_sigs, int nsig, int64_t max_words, int bits,
+                               uint32_t* d_status, cudaStream_t st);
+// Number of lags one popc CTA covers.
+constexpr int kPopcLagsPerCta = 2048;
+cudaError_t launch_xcorr_popc(const XcPair* d_pairs, const PopcItem* d_items, int nitems, int bits,
+                              cudaStream_t st);
+
+// d_keys: npairs * 2 uint64 of scratch.
+cudaError_t launch_argmax(const ArgPair* d_pairs, int npairs, int64_t max_count, int c64,
+                          unsigned long long* d_keys, cudaStream_t st);
+
+// Kernel launches enqueued by this host thread (read by the context).
+extern thread_local int64_t tde_launch_counter;
+#define TDE_COUNT_LAUNCH(n) (tde_launch_counter += (n))
+
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int64_t floor_div64(int64_t a, int64_t b) {
+  return a >= 0 ? a / b : -((-a + b - 1) / b);
+}

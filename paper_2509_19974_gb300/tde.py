@@ -1,0 +1,247 @@
+"""Thin Python binding of libtde (include/tde.h) -- argument marshalling only.
+
+Every step of the estimator runs in libtde's CUDA kernels; torch supplies
+device memory (``Tensor.data_ptr()``) and the current CUDA stream.  There is
+no CPU fallback: if libtde.so is missing or no GPU is present, the calls raise.
+
+The functions keep the C names (``tde_quantize`` ...) and take a
+:class:`Context`; :class:`Context` also offers them as methods without the
+prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtde.so")
+
+TDE_OK, TDE_ERR_INVALID, TDE_ERR_OVERFLOW, TDE_ERR_UNSUPPORTED, TDE_ERR_CUDA, TDE_ERR_TIMEOUT = range(6)
+STATUS_NAMES = {0: "TDE_OK", 1: "TDE_ERR_INVALID", 2: "TDE_ERR_OVERFLOW", 3: "TDE_ERR_UNSUPPORTED",
+                4: "TDE_ERR_CUDA", 5: "TDE_ERR_TIMEOUT"}
+ENGINES = {"auto": 0, "popc": 1, "mma": 2, "ntt": 3}
+TDE_I32, TDE_I64 = 0, 1
+
+# Every symbol include/tde.h declares.
+EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
+           "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_quantize",
+           "tde_xcorr_int", "tde_argmax", "tde_estimate", "tde_estimate_batch")
+
+
+class TdeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PairDesc(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("nx", ctypes.c_int64),
+                ("ny", ctypes.c_int64), ("lag_min", ctypes.c_int64), ("lag_max", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libtde.so (built by ``paper_2509_19974_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libtde.so not found at {path}: run paper_2509_19974_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    i64, p, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "tde_ctx_create": ([i32, ctypes.POINTER(p)], st),
+        "tde_ctx_destroy": ([p], st),
+        "tde_ctx_sync": ([p, p], st),
+        "tde_last_error": ([p], ctypes.c_char_p),
+        "tde_ctx_set_profiling": ([p, i32], st),
+        "tde_ctx_read_profile": ([p, p, p, p], st),
+        "tde_quantize": ([p, p, i64, i32, p, p], st),
+        "tde_xcorr_int": ([p, p, i64, p, i64, i32, i64, i64, i32, p, i32, p], st),
+        "tde_argmax": ([p, p, i32, i64, i64, p, p, p], st),
+        "tde_estimate": ([p, p, i64, p, i64, i32, i64, i64, i32, p, p, p], st),
+        "tde_estimate_batch": ([p, ctypes.POINTER(PairDesc), i32, i32, i32, p, p, p, p], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes, fn.restype = args, res
+    _lib = lib
+    return lib
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _engine(e) -> int:
+    return ENGINES[e] if isinstance(e, str) else int(e)
+
+
+class Context:
+    """Owns a ``tde_ctx`` on one device (workspace, staging, status word)."""
+
+    def __init__(self, device: int | None = None):
+        self.lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        s = self.lib.tde_ctx_create(self.device, ctypes.byref(h))
+        if s != TDE_OK:
+            raise TdeError(s, f"tde_ctx_create(device={device}) failed")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tde_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status: int):
+        if status != TDE_OK:
+            msg = self.lib.tde_last_error(self.handle)
+            raise TdeError(status, msg.decode() if msg else "")
+
+    # --- methods mirroring the C entry points -----------------------------
+    def sync(self, stream=None):
+        self.check(self.lib.tde_ctx_sync(self.handle, _stream(stream)))
+
+    def set_profiling(self, enable: bool):
+        self.check(self.lib.tde_ctx_set_profiling(self.handle, int(bool(enable))))
+
+    def read_profile(self):
+        """(kernel launches, engine-kernel launches, engine ms) since last read."""
+        k, e, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        self.check(self.lib.tde_ctx_read_profile(self.handle, ctypes.byref(k), ctypes.byref(e),
+                                                 ctypes.byref(ms)))
+        return int(k.value), int(e.value), float(ms.value)
+
+    def quantize(self, x, bits, q_out=None, stream=None):
+        return tde_quantize(self, x, bits, q_out, stream)
+
+    def xcorr_int(self, qx, qy, bits, lag_min=None, lag_max=None, engine="auto",
+                  dtype=torch.int32, c_out=None, stream=None):
+        return tde_xcorr_int(self, qx, qy, bits, lag_min, lag_max, engine, dtype, c_out, stream)
+
+    def argmax(self, c, lag_min, stream=None):
+        return tde_argmax(self, c, lag_min, stream)
+
+    def estimate(self, x, y, bits, lag_min=None, lag_max=None, engine="auto", stream=None):
+        return tde_estimate(self, x, y, bits, lag_min, lag_max, engine, stream)
+
+    def estimate_batch(self, xs, ys, bits, lag_mins=None, lag_maxs=None, engine="auto",
+                       c_out=None, stream=None):
+        return tde_estimate_batch(self, xs, ys, bits, lag_mins, lag_maxs, engine, c_out, stream)
+
+
+def full_lags(nx: int, ny: int):
+    return -(nx - 1), ny - 1
+
+
+def tde_quantize(ctx: Context, x: torch.Tensor, bits: int, q_out=None, stream=None):
+    _need(x, torch.float32, "x")
+    if q_out is None:
+        q_out = torch.empty(x.numel(), dtype=torch.int8, device=x.device)
+    _need(q_out, torch.int8, "q_out")
+    ctx.check(ctx.lib.tde_quantize(ctx.handle, x.data_ptr(), x.numel(), int(bits),
+                                   q_out.data_ptr(), _stream(stream)))
+    return q_out
+
+
+def tde_xcorr_int(ctx: Context, qx, qy, bits, lag_min=None, lag_max=None, engine="auto",
+                  dtype=torch.int32, c_out=None, stream=None):
+    _need(qx, torch.int8, "qx")
+    _need(qy, torch.int8, "qy")
+    lo, hi = full_lags(qx.numel(), qy.numel())
+    lag_min = lo if lag_min is None else int(lag_min)
+    lag_max = hi if lag_max is None else int(lag_max)
+    count = lag_max - lag_min + 1
+    if c_out is None:
+        c_out = torch.empty(max(count, 0), dtype=dtype, device=qx.device)
+    _need(c_out, dtype, "c_out")
+    code = TDE_I64 if dtype == torch.int64 else TDE_I32
+    ctx.check(ctx.lib.tde_xcorr_int(ctx.handle, qx.data_ptr(), qx.numel(), qy.data_ptr(),
+                                    qy.numel(), int(bits), lag_min, lag_max, _engine(engine),
+                                    c_out.data_ptr(), code, _stream(stream)))
+    return c_out
+
+
+def tde_argmax(ctx: Context, c, lag_min, stream=None):
+    if c.dtype not in (torch.int32, torch.int64):
+        raise TypeError("c must be int32 or int64")
+    _need(c, c.dtype, "c")
+    lag = torch.empty(1, dtype=torch.int64, device=c.device)
+    val = torch.empty(1, dtype=torch.int64, device=c.device)
+    code = TDE_I64 if c.dtype == torch.int64 else TDE_I32
+    ctx.check(ctx.lib.tde_argmax(ctx.handle, c.data_ptr(), code, int(lag_min), c.numel(),
+                                 lag.data_ptr(), val.data_ptr(), _stream(stream)))
+    return lag, val
+
+
+def tde_estimate(ctx: Context, x, y, bits, lag_min=None, lag_max=None, engine="auto", stream=None):
+    _need(x, torch.float32, "x")
+    _need(y, torch.float32, "y")
+    lo, hi = full_lags(x.numel(), y.numel())
+    lag_min = lo if lag_min is None else int(lag_min)
+    lag_max = hi if lag_max is None else int(lag_max)
+    lag = torch.empty(1, dtype=torch.int64, device=x.device)
+    val = torch.empty(1, dtype=torch.int64, device=x.device)
+    ctx.check(ctx.lib.tde_estimate(ctx.handle, x.data_ptr(), x.numel(), y.data_ptr(), y.numel(),
+                                   int(bits), lag_min, lag_max, _engine(engine), lag.data_ptr(),
+                                   val.data_ptr(), _stream(stream)))
+    return lag, val
+
+
+def make_descs(xs, ys, lag_mins=None, lag_maxs=None):
+    """Pair descriptors from lists of 1-D float32 CUDA tensors (or the rows of
+    two 2-D tensors).  Default lag range: every lag with a nonempty overlap."""
+    n = len(xs)
+    descs = (PairDesc * n)()
+    for i in range(n):
+        x, y = xs[i], ys[i]
+        _need(x, torch.float32, f"xs[{i}]")
+        _need(y, torch.float32, f"ys[{i}]")
+        lo, hi = full_lags(x.numel(), y.numel())
+        descs[i] = PairDesc(x.data_ptr(), y.data_ptr(), x.numel(), y.numel(),
+                            lo if lag_mins is None else int(lag_mins[i]),
+                            hi if lag_maxs is None else int(lag_maxs[i]))
+    return descs
+
+
+def tde_estimate_batch(ctx: Context, xs, ys, bits, lag_mins=None, lag_maxs=None, engine="auto",
+                       c_out=None, stream=None, descs=None):
+    """Returns (lags, values) as int64 CUDA tensors of length npairs."""
+    if descs is None:
+        descs = make_descs(xs, ys, lag_mins, lag_maxs)
+    n = len(descs)
+    dev = torch.device("cuda", ctx.device)
+    lags = torch.empty(n, dtype=torch.int64, device=dev)
+    vals = torch.empty(n, dtype=torch.int64, device=dev)
+    cptr = None
+    if c_out is not None:
+        _need(c_out, torch.int32, "c_out")
+        cptr = c_out.data_ptr()
+    ctx.check(ctx.lib.tde_estimate_batch(ctx.handle, descs, n, int(bits), _engine(engine), cptr,
+                                         lags.data_ptr(), vals.data_ptr(), _stream(stream)))
+    return lags, vals
