@@ -100,6 +100,11 @@ tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
 tde_status tde_ctx_read_profile(tde_ctx* ctx, int64_t* kernel_launches, int64_t* engine_launches,
                                 double* engine_ms);
 
+/* The engine TDE_ENGINE_AUTO picks for one pair of lengths nx, ny, `bits`
+ * and lag_count lags (host-only, enqueues nothing).  Returns a
+ * TDE_ENGINE_* value, or -1 if the arguments are invalid. */
+int tde_pick_engine(int bits, int64_t nx, int64_t ny, int64_t lag_count);
+
 /* Algorithm 1, lines 1-2.  x: n floats (device).  q_out: n int8 (device).
  * bits in {1, 2, 4}.  NaN/Inf inputs are latched as TDE_ERR_INVALID (see
  * tde_ctx_sync) and the output is then unspecified. */

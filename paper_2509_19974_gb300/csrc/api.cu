@@ -6,9 +6,11 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
+#include "mma.cuh"
 
 struct tde_ctx {
   int device = 0;
@@ -387,11 +389,107 @@ struct PopcStage {
     }
   }
   cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
+    if (njobs == 0) return cudaSuccess;
     cudaError_t e = launch_pack_planes(B.dd<PlaneSig>(o_psig), 2 * njobs, max_words, bits,
                                        ctx->d_status, st);
     if (e != cudaSuccess) return e;
     EngineTimer t(ctx, st);
     return launch_xcorr_popc(B.dd<XcPair>(o_pairs), B.dd<PopcItem>(o_items), nitems, bits, st);
+  }
+};
+
+// ---- step B, tensor-core engine
+struct MmaStage {
+  int njobs = 0, nitems = 0, any_zero = 0;
+  int64_t max_count = 0;
+  size_t o_pairs = 0, o_items = 0;
+  std::vector<MmaItem> items;
+  std::vector<int> zero_first;
+  void plan(Layout& L, const std::vector<Job>& jobs) {
+    njobs = (int)jobs.size();
+    items.clear();
+    zero_first.assign(njobs, 0);
+    for (int i = 0; i < njobs; ++i) {
+      const Job& j = jobs[i];
+      max_count = std::max<int64_t>(max_count, j.lag_max - j.lag_min + 1);
+      const int64_t t0 = floor_div64(j.lag_min, 64) * 64;
+      const int64_t ntiles = ceil_div64(j.lag_max - t0 + 1, kMmaTileLags);
+      for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t T0 = t0 + t * kMmaTileLags;
+        // k = x index + (127 - m); nonzero terms need k in [0, nx + 127) and
+        // y index k + T0 + 128 n in [0, ny) for some n in [0, 256).
+        int64_t klo = std::max<int64_t>(0, -T0 - 128 * 255);
+        int64_t khi = std::min<int64_t>(j.nx + 127, j.ny - T0);
+        klo = floor_div64(klo, 64) * 64;
+        khi = ceil_div64(khi, 64) * 64;
+        if (khi <= klo) {  // no overlap anywhere in this tile: its lags are 0
+          zero_first[i] = 1;
+          continue;
+        }
+        const int64_t nseg = ceil_div64(khi - klo, kMmaKs);
+        const int64_t seg = ceil_div64(ceil_div64(khi - klo, nseg), 64) * 64;
+        if (nseg > 1) zero_first[i] = 1;
+        for (int64_t s = 0; s < nseg; ++s) {
+          const int64_t ks = klo + s * seg, ke = std::min(khi, ks + seg);
+          if (ke > ks) items.push_back(MmaItem{i, nseg == 1 ? 1 : 0, T0, ks, ke});
+        }
+      }
+      any_zero |= zero_first[i];
+    }
+    nitems = (int)items.size();
+    o_pairs = L.d<MmaPair>(njobs);
+    o_items = L.d<MmaItem>(nitems);
+  }
+  void fill(const Bases& B, const std::vector<Job>& jobs) const {
+    MmaPair* p = B.hd<MmaPair>(o_pairs);
+    for (int i = 0; i < njobs; ++i) {
+      const Job& j = jobs[i];
+      p[i] = MmaPair{j.qx, j.qy, j.nx, j.ny, j.lag_min, j.lag_max, j.c, j.c64, zero_first[i]};
+    }
+    if (nitems) memcpy(B.hd<MmaItem>(o_items), items.data(), sizeof(MmaItem) * nitems);
+  }
+  cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
+    if (njobs == 0) return cudaSuccess;
+    if (any_zero) {
+      cudaError_t e = launch_mma_zero(B.dd<MmaPair>(o_pairs), njobs, max_count, st);
+      if (e != cudaSuccess) return e;
+    }
+    EngineTimer t(ctx, st);
+    return launch_xcorr_mma(B.dd<MmaPair>(o_pairs), B.dd<MmaItem>(o_items), nitems, ctx->d_status,
+                            st);
+  }
+};
+
+// Both engines over one job list: each job goes to the engine picked for it.
+struct XcorrStage {
+  std::vector<int> eng;                 // per job
+  std::vector<Job> popc_jobs, mma_jobs;
+  std::vector<int> popc_idx, mma_idx;   // job -> position in its engine list
+  PopcStage popc;
+  MmaStage mma;
+  int bits = 1;
+  void plan(Layout& L, const std::vector<Job>& jobs, const std::vector<int>& engines, int b) {
+    bits = b;
+    eng = engines;
+    popc_jobs.clear(), mma_jobs.clear();
+    for (size_t i = 0; i < jobs.size(); ++i)
+      (eng[i] == TDE_ENGINE_MMA ? mma_jobs : popc_jobs).push_back(jobs[i]);
+    popc.plan(L, popc_jobs, bits);
+    mma.plan(L, mma_jobs);
+  }
+  // Binds pointers (known after realize) and writes the descriptors.
+  void fill(const Bases& B, const std::vector<Job>& jobs) {
+    size_t a = 0, m = 0;
+    for (size_t i = 0; i < jobs.size(); ++i)
+      (eng[i] == TDE_ENGINE_MMA ? mma_jobs[m++] : popc_jobs[a++]) = jobs[i];
+    popc.fill(B, popc_jobs);
+    mma.fill(B, mma_jobs);
+  }
+  cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
+    cudaError_t e = cudaSuccess;
+    if (!popc_jobs.empty()) e = popc.launch(ctx, B, st);
+    if (e == cudaSuccess && !mma_jobs.empty()) e = mma.launch(ctx, B, st);
+    return e;
   }
 };
 
@@ -428,18 +526,27 @@ tde_status realize(tde_ctx* ctx, const Layout& L, Bases* B) {
   return TDE_OK;
 }
 
-int pick_engine(int engine, int bits, int64_t nx, int64_t ny) {
-  (void)bits, (void)nx, (void)ny;
+// AUTO: the tensor-core engine pays for a whole 32768-lag tile; it runs about
+// 16x (bits <= 2) or 150x (bits = 4) more MACs per clock than the POPC pipe,
+// so it wins once a pair asks for more lags than ~1/16 (1/128) of a tile.
+int pick_engine(int engine, int bits, int64_t nx, int64_t ny, int64_t lag_count) {
   if (engine != TDE_ENGINE_AUTO) return engine;
-  return TDE_ENGINE_POPC;
+  const int64_t n = nx < ny ? nx : ny;
+  const int64_t need = bits == 4 ? kMmaTileLags / 128 : kMmaTileLags / 16;
+  return (n >= 1024 && lag_count >= need) ? TDE_ENGINE_MMA : TDE_ENGINE_POPC;
 }
 
 tde_status engine_available(tde_ctx* ctx, int engine) {
-  if (engine == TDE_ENGINE_POPC) return TDE_OK;
+  if (engine == TDE_ENGINE_POPC || engine == TDE_ENGINE_MMA) return TDE_OK;
   return set_err(ctx, TDE_ERR_UNSUPPORTED, "engine %d is not available in this build", engine);
 }
 
 }  // namespace
+
+extern "C" int tde_pick_engine(int bits, int64_t nx, int64_t ny, int64_t lag_count) {
+  if (!valid_bits(bits) || nx <= 0 || ny <= 0 || lag_count <= 0) return -1;
+  return pick_engine(TDE_ENGINE_AUTO, bits, nx, ny, lag_count);
+}
 
 extern "C" tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits,
                                    int8_t* q_out, tde_stream_t stream) {
@@ -471,15 +578,15 @@ extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, 
   if (!qx || !qy || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   tde_status s = check_xcorr_args(ctx, nx, ny, bits, lag_min, lag_max, engine, out_dtype);
   if (s != TDE_OK) return s;
-  const int eng = pick_engine(engine, bits, nx, ny);
+  const int eng = pick_engine(engine, bits, nx, ny, lag_max - lag_min + 1);
   if ((s = engine_available(ctx, eng)) != TDE_OK) return s;
   DeviceGuard g(ctx->device);
   LaunchCount lc(ctx);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   std::vector<Job> jobs{Job{qx, qy, nx, ny, lag_min, lag_max, c_out, out_dtype == TDE_I64}};
   Layout L;
-  PopcStage E;
-  E.plan(L, jobs, bits);
+  XcorrStage E;
+  E.plan(L, jobs, std::vector<int>{eng}, bits);
   Bases B;
   if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
   E.fill(B, jobs);
@@ -522,23 +629,20 @@ extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* desc
   if (!descs || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
   tde_status s;
-  int eng = -1;
+  std::vector<int> engs(npairs);
   int64_t max_n = 0, max_count = 0;
   for (int p = 0; p < npairs; ++p) {
     const tde_pair_desc& d = descs[p];
     if (!d.x || !d.y) return set_err(ctx, TDE_ERR_INVALID, "null signal pointer in pair %d", p);
     s = check_xcorr_args(ctx, d.nx, d.ny, bits, d.lag_min, d.lag_max, engine, TDE_I32);
     if (s != TDE_OK) return s;
-    const int e = pick_engine(engine, bits, d.nx, d.ny);
-    if (eng >= 0 && e != eng)
-      return set_err(ctx, TDE_ERR_UNSUPPORTED, "mixed engines in one batch");
-    eng = e;
+    const int64_t cnt = d.lag_max - d.lag_min + 1;
+    engs[p] = pick_engine(engine, bits, d.nx, d.ny, cnt);
+    if ((s = engine_available(ctx, engs[p])) != TDE_OK) return s;
     max_n = d.nx > max_n ? d.nx : max_n;
     max_n = d.ny > max_n ? d.ny : max_n;
-    const int64_t cnt = d.lag_max - d.lag_min + 1;
     max_count = cnt > max_count ? cnt : max_count;
   }
-  if ((s = engine_available(ctx, eng)) != TDE_OK) return s;
   DeviceGuard g(ctx->device);
   LaunchCount lc(ctx);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -563,8 +667,8 @@ extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* desc
   for (int p = 0; p < npairs; ++p)
     jobs[p] = Job{nullptr, nullptr, descs[p].nx, descs[p].ny, descs[p].lag_min, descs[p].lag_max,
                   nullptr, 0};
-  PopcStage E;
-  E.plan(L, jobs, bits);
+  XcorrStage E;
+  E.plan(L, jobs, engs, bits);
   ArgStage A;
   A.plan(L, npairs, max_count, 0);
   Bases B;

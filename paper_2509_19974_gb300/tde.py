@@ -26,7 +26,7 @@ TDE_I32, TDE_I64 = 0, 1
 
 # Every symbol include/tde.h declares.
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
-           "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_quantize",
+           "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
            "tde_xcorr_int", "tde_argmax", "tde_estimate", "tde_estimate_batch")
 
 
@@ -61,6 +61,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_last_error": ([p], ctypes.c_char_p),
         "tde_ctx_set_profiling": ([p, i32], st),
         "tde_ctx_read_profile": ([p, p, p, p], st),
+        "tde_pick_engine": ([i32, i64, i64, i64], i32),
         "tde_quantize": ([p, p, i64, i32, p, p], st),
         "tde_xcorr_int": ([p, p, i64, p, i64, i32, i64, i64, i32, p, i32, p], st),
         "tde_argmax": ([p, p, i32, i64, i64, p, p, p], st),
@@ -153,6 +154,17 @@ class Context:
     def estimate_batch(self, xs, ys, bits, lag_mins=None, lag_maxs=None, engine="auto",
                        c_out=None, stream=None):
         return tde_estimate_batch(self, xs, ys, bits, lag_mins, lag_maxs, engine, c_out, stream)
+
+
+ENGINE_NAMES = {v: k for k, v in ENGINES.items()}
+
+
+def pick_engine(bits: int, nx: int, ny: int, lag_count: int) -> str:
+    """Name of the engine TDE_ENGINE_AUTO runs for such a pair."""
+    e = load().tde_pick_engine(int(bits), int(nx), int(ny), int(lag_count))
+    if e < 0:
+        raise ValueError("invalid arguments")
+    return ENGINE_NAMES[e]
 
 
 def full_lags(nx: int, ny: int):
