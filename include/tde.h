@@ -111,6 +111,35 @@ int tde_pick_engine(int bits, int64_t nx, int64_t ny, int64_t lag_count);
 tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits, int8_t* q_out,
                         tde_stream_t stream);
 
+/* Allocation-free quantizer: the paper has no counterpart to this entry
+ * point; it exists for callers that cannot allocate device memory, such as a
+ * real-time audio callback that must not block in the allocator, a host that
+ * runs this library under its own device-memory manager, or code enqueueing
+ * work while a stream is captured.  Every other call needs a tde_ctx, which
+ * allocates its workspace and pinned staging on demand; this one needs no
+ * context and allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).
+ *
+ * It quantizes nsig signals of n samples each, exactly like tde_quantize on
+ * each of them: x holds nsig * n floats (device, signal after signal), q_out
+ * receives nsig * n int8 (device).  status_out is one uint32 of caller-owned
+ * device memory: the call zeroes it, and bit 0 is set if any input was NaN or
+ * Inf (the output is then unspecified).  The calling thread's current device
+ * is used.
+ *
+ * Scratch: the rank quantizer's histograms and radix-select state live in a
+ * fixed file-scope device array (about 0.9 MiB) that every GPU loading the
+ * library keeps until the process exits.  Limits: 1 <= nsig <= 16 and
+ * n <= 2^31 - 1; larger requests return TDE_ERR_UNSUPPORTED and enqueue
+ * nothing.  Other argument errors return TDE_ERR_INVALID.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (each call clears what it
+ * needs): calls whose work may overlap on the GPU, e.g. on two unordered
+ * streams, race and give wrong results. */
+tde_status tde_quantize_noalloc(const float* x, int64_t n, int nsig, int bits, int8_t* q_out,
+                                uint32_t* status_out, tde_stream_t stream);
+
 /* Algorithm 1, line 3 / Eq. (1) on quantized input.  qx: nx int8, qy: ny int8
  * (device), with |q| <= 2^(bits-1) - 1 (1 for bits <= 2, 7 for bits = 4).
  * Computes c[tau] for lag_min <= tau <= lag_max, which must lie inside

@@ -27,7 +27,8 @@ TDE_I32, TDE_I64 = 0, 1
 # Every symbol include/tde.h declares.
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
            "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
-           "tde_xcorr_int", "tde_argmax", "tde_estimate", "tde_estimate_batch")
+           "tde_quantize_noalloc", "tde_xcorr_int", "tde_argmax", "tde_estimate",
+           "tde_estimate_batch")
 
 
 class TdeError(RuntimeError):
@@ -63,6 +64,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_ctx_read_profile": ([p, p, p, p], st),
         "tde_pick_engine": ([i32, i64, i64, i64], i32),
         "tde_quantize": ([p, p, i64, i32, p, p], st),
+        "tde_quantize_noalloc": ([p, i64, i32, i32, p, p, p], st),
         "tde_xcorr_int": ([p, p, i64, p, i64, i32, i64, i64, i32, p, i32, p], st),
         "tde_argmax": ([p, p, i32, i64, i64, p, p, p], st),
         "tde_estimate": ([p, p, i64, p, i64, i32, i64, i64, i32, p, p, p], st),
@@ -179,6 +181,27 @@ def tde_quantize(ctx: Context, x: torch.Tensor, bits: int, q_out=None, stream=No
     ctx.check(ctx.lib.tde_quantize(ctx.handle, x.data_ptr(), x.numel(), int(bits),
                                    q_out.data_ptr(), _stream(stream)))
     return q_out
+
+
+NOALLOC_MAX_SIGNALS = 16
+
+
+def tde_quantize_noalloc(x: torch.Tensor, bits: int, q_out=None, status_out=None, stream=None):
+    """Allocation-free quantizer (no context): x is [nsig, n] float32 (nsig <=
+    16) or [n]; returns (q [nsig, n] int8, status uint32 tensor of one word,
+    bit 0 = NaN/Inf seen).  Output tensors may be passed in preallocated."""
+    _need(x, torch.float32, "x")
+    nsig, n = (1, x.numel()) if x.dim() == 1 else (x.shape[0], x.shape[1])
+    if q_out is None:
+        q_out = torch.empty(x.shape, dtype=torch.int8, device=x.device)
+    if status_out is None:
+        status_out = torch.empty(1, dtype=torch.int32, device=x.device)
+    _need(q_out, torch.int8, "q_out")
+    s = load().tde_quantize_noalloc(x.data_ptr(), int(n), int(nsig), int(bits), q_out.data_ptr(),
+                                    status_out.data_ptr(), _stream(stream))
+    if s != TDE_OK:
+        raise TdeError(s, "tde_quantize_noalloc failed")
+    return q_out, status_out
 
 
 def tde_xcorr_int(ctx: Context, qx, qy, bits, lag_min=None, lag_max=None, engine="auto",
