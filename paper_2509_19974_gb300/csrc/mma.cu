@@ -36,11 +36,18 @@
 // and adds 8 new ones; the slots live in a ring of 48 with the first 24
 // mirrored past its end so every window is contiguous.
 //
-// Roles: warp 0 writes the slots and lane 0 issues the MMAs (M=128, N=256,
-// K=16) and tcgen05.commit per chunk; all 8 warps load y first and read the
-// accumulator out at the end (warp w reads lanes 32 (w % 4) .., columns
-// 128 (w / 4) ..).  Every wait is bounded by %globaltimer; on time-out the
-// CTA flags TDE_ST_TIMEOUT, waits (bounded) for its MMAs and frees TMEM.
+// Only column groups (32 columns = 4096 lags) whose overlap meets a chunk are
+// multiplied: the MMA's N shrinks at the ends of a tile's K range, so the
+// MACs issued stay within a few percent of the overlap MACs for long pairs.
+//
+// Roles: all 8 warps stage y (BF16, swizzled) and the segment of x (int8) in
+// shared memory; warps 1-2 (64 threads) write one 16-byte slot row each per
+// chunk and arrive on the chunk's "full" barrier; warp 0 lane 0 waits on it,
+// issues the chunk's MMAs (M=128, K=16, N = 32..256) and tcgen05.commit's the
+// chunk's barrier, which the producers wait on before overwriting ring slots;
+// at the end all warps read the accumulator (warp w: lanes 32 (w % 4) ..,
+// columns 128 (w / 4) ..).  Every wait is bounded by %globaltimer; on time-out
+// the CTA flags TDE_ST_TIMEOUT, waits (bounded) for its MMAs and frees TMEM.
 #include "common.cuh"
 #include "mma.cuh"
 
@@ -53,19 +60,26 @@ constexpr int kNB = 8;                                  // chunk commit barriers
 constexpr int kRowsMax = kMmaKs / 128 + 256 + 8;        // y rows per half
 constexpr int kYBytes = kRowsMax * 128;
 constexpr int kSlotBytes = kSlots * 128;
-constexpr int kSmemUsed = 2 * kYBytes + kSlotBytes + (kNB + 1) * 8 + 16;
+constexpr int kXBytes = kMmaKs + 272;                   // x samples a segment's slots read
+constexpr int kProducers = 64;                          // slot-writing threads (warps 1, 2)
+constexpr int kGroups = 8, kGroupCols = kN / kGroups;   // column groups of 32 (4096 lags)
+constexpr int kSmemUsed = 2 * kYBytes + kSlotBytes + kXBytes + (2 * kNB + 1) * 8 + 16;
 constexpr int kSmemBytes = kSmemUsed + 1024;            // room to align the base
 constexpr uint64_t kTimeoutNs = 2000000000ull;         // 2 s per wait
 static_assert(kMmaTileLags == kM * kN, "tile");
 static_assert(kMmaKs % kKc == 0, "segment");
 static_assert(kYBytes % 1024 == 0, "y arrays stay 1024-aligned");
 static_assert(kRing % 8 == 0 && kMirror >= 23 && kRing >= kMirror, "slot ring");
+static_assert(kXBytes % 16 == 0, "x stage");
+static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
 // bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_for(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -124,11 +138,22 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Zeroes 32 lanes x 32 columns of tensor memory.
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(0u)
       : "memory");
 }
 
@@ -172,6 +197,42 @@ __device__ __forceinline__ int64_t fdiv(int64_t a, int64_t b) {  // floor divisi
   return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
+// Unpacks 8 int8 levels (little-endian in w) to 8 BF16 and stores them as one
+// 16-byte core-matrix row at `addr` (and at `addr2` if non-zero).
+__device__ __forceinline__ void store_row8(uint32_t addr, uint32_t addr2, uint64_t w) {
+  int v[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) v[t] = (int)(int8_t)(w >> (8 * t));
+  const uint32_t w0 = pack2(v[0], v[1]), w1 = pack2(v[2], v[3]);
+  const uint32_t w2 = pack2(v[4], v[5]), w3 = pack2(v[6], v[7]);
+  st_shared_v4(addr, w0, w1, w2, w3);
+  if (addr2) st_shared_v4(addr2, w0, w1, w2, w3);
+}
+
+__device__ __forceinline__ uint64_t ld_shared_u64(uint32_t addr) {
+  uint64_t v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+               : "memory");
+}
+
+// 16 int8 from global memory (zero outside [0, n)); vector load when aligned.
+__device__ __forceinline__ uint4 load16(const int8_t* q, int64_t i0, int64_t n, bool al16) {
+  if (al16 && i0 >= 0 && i0 + 16 <= n) return __ldg(reinterpret_cast<const uint4*>(q + i0));
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int64_t i = i0 + t;
+    const uint32_t b = (i >= 0 && i < n) ? (uint32_t)(uint8_t)q[i] : 0u;
+    w[t >> 2] |= b << (8 * (t & 3));
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
     k_xcorr_mma(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items,
                 uint32_t* __restrict__ status) {
@@ -179,8 +240,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   const uint32_t yE = base, yO = base + kYBytes, slots = base + 2 * kYBytes;
-  const uint32_t bars = slots + kSlotBytes;           // kNB chunk barriers + 1 "done"
-  const uint32_t done_bar = bars + kNB * 8;
+  const uint32_t xs = slots + kSlotBytes;   // int8 x segment
+  const uint32_t full_bar = xs + kXBytes;   // kNB "slots written" barriers
+  const uint32_t cmt_bar = full_bar + 8 * kNB;  // kNB "chunk MMAs done" barriers
+  const uint32_t done_bar = cmt_bar + 8 * kNB;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
 
   const MmaItem it = items[blockIdx.x];
@@ -191,8 +254,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int64_t u_s = (ks + T0) / kKc, u_l = (ke - kKc + T0) / kKc;  // exact
   const int64_t r_lo = fdiv(fdiv(u_s, 2), 8) * 8;
   const int64_t nrows = fdiv(u_l, 2) + 255 - r_lo + 1;
-  // The CTA's own bounds check: the y window must fit its arrays.
-  if (nrows > kRowsMax || nchunks <= 0) {
+  // x is staged from a 16-byte aligned index; window o (x index ks - 127 + o)
+  // sits at xs + xoff + o.
+  const int64_t xs_base = fdiv(ks - 127, 16) * 16;
+  const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
+  // The CTA's own bounds checks: the y window and the x segment must fit.
+  if (nrows > kRowsMax || nchunks <= 0 || (ke - ks) + 272 > kXBytes) {
     if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
     return;
   }
@@ -205,88 +272,138 @@ __global__ void __launch_bounds__(kThreads, 2)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 32) {
-    for (int i = 0; i <= kNB; ++i) mbar_init(bars + 8 * i, 1);
+    for (int i = 0; i < kNB; ++i) {
+      mbar_init(full_bar + 8 * i, kProducers);
+      mbar_init(cmt_bar + 8 * i, 1);
+    }
+    mbar_init(done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  // y window: rows r_lo .. r_lo + nrows - 1 of E and O, zero outside [0, ny).
-  const int8_t* qy = P.qy;
-  const bool y_al8 = (reinterpret_cast<uintptr_t>(qy) & 7) == 0;
-  for (int idx = threadIdx.x; idx < nrows * 16; idx += kThreads) {
-    const int row = idx >> 4, half = (idx >> 3) & 1, ch = idx & 7;
-    const int64_t q0 = 128 * (r_lo + row) + 64 * half + 8 * ch;
-    int v[8];
-    if (y_al8 && q0 >= 0 && q0 + 8 <= P.ny) {
-      const uint2 w = *reinterpret_cast<const uint2*>(qy + q0);
+  // y window: rows r_lo .. r_lo + nrows - 1 of E and O (zero outside [0, ny)),
+  // 16 samples per load, four loads in flight per thread.
+  {
+    const int8_t* qy = P.qy;
+    const bool al16 = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+    const int total = (int)nrows * 8;  // (row, half, quarter)
+    for (int b0 = threadIdx.x; b0 < total; b0 += 4 * kThreads) {
+      uint4 w[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        v[t] = (int)(int8_t)(w.x >> (8 * t));
-        v[4 + t] = (int)(int8_t)(w.y >> (8 * t));
+      for (int k = 0; k < 4; ++k) {
+        const int idx = b0 + k * kThreads;
+        if (idx < total) {
+          const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
+          w[k] = load16(qy, 128 * (r_lo + row) + 64 * half + 16 * j, P.ny, al16);
+        }
       }
-    } else {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int64_t q = q0 + t;
-        v[t] = (q >= 0 && q < P.ny) ? (int)qy[q] : 0;
+      for (int k = 0; k < 4; ++k) {
+        const int idx = b0 + k * kThreads;
+        if (idx < total) {
+          const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
+          const uint32_t row_addr = (half ? yO : yE) + 128u * (uint32_t)row;
+          const uint32_t sw = (row_addr >> 7) & 7u;
+          store_row8(row_addr + 16u * ((uint32_t)(2 * j) ^ sw), 0u,
+                     (uint64_t)w[k].x | ((uint64_t)w[k].y << 32));
+          store_row8(row_addr + 16u * ((uint32_t)(2 * j + 1) ^ sw), 0u,
+                     (uint64_t)w[k].z | ((uint64_t)w[k].w << 32));
+        }
       }
     }
-    const uint32_t row_addr = (half ? yO : yE) + 128u * (uint32_t)row;
-    const uint32_t phys = (uint32_t)ch ^ ((row_addr >> 7) & 7u);
-    st_shared_v4(row_addr + 16u * phys, pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]),
-                 pack2(v[6], v[7]));
+  }
+  // x segment x[xs_base .. xs_base + kXBytes), zero outside [0, nx).
+  {
+    const int8_t* qx = P.qx;
+    const bool al16 = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+    for (int i = threadIdx.x; i < kXBytes / 16; i += kThreads) {
+      const uint4 w = load16(qx, xs_base + 16 * i, P.nx, al16);
+      st_shared_v4(xs + 16u * i, w.x, w.y, w.z, w.w);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // The accumulator starts at zero: column groups join the sum at different
+  // chunks, so every MMA accumulates.
+  if (warp < 4) {
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    for (int cb = 0; cb < kN; cb += 32) tmem_zero32(tmem + lane_base + (uint32_t)cb);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
-  if (warp == 0) {
-    const int8_t* qx = P.qx;
-    const int64_t d_begin = ks / 8;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      // Slots written now overwrite those last read by chunk c - (kRing/8 - 2).
+  if (warp == 1 || warp == 2) {
+    // Slot producers: thread t writes window o = 64 c + 120 + t of chunk c
+    // (chunk 0 writes windows 0..183): slot e = o / 8, row r = o % 8, i.e.
+    // x[ks - 127 + o .. + 7] as BF16.
+    const int t = threadIdx.x - 32;
+    for (int c = 0; c < nchunks; ++c) {
+      // The slots written now were last read by chunk c - (kRing/8 - 2).
       const int prev = c - (kRing / 8 - 2);
-      if (prev >= 0) ok = mbar_wait(bars + 8 * (prev % kNB), (uint32_t)((prev / kNB) & 1));
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      const int e0 = c == 0 ? 0 : 8 * c + 15, e1 = 8 * c + 22;
-      for (int idx = lane; idx < (e1 - e0 + 1) * 8; idx += 32) {
-        const int e = e0 + (idx >> 3), r = idx & 7;
-        const int64_t x0 = 8 * (d_begin + e) + r - 127;
-        int v[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int64_t i = x0 + t;
-          v[t] = (i >= 0 && i < P.nx) ? (int)qx[i] : 0;
-        }
-        const int p = e % kRing;
-        const uint32_t a = slots + 128u * p + 16u * r;
-        st_shared_v4(a, pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]),
-                     pack2(v[6], v[7]));
-        if (p < kMirror)
-          st_shared_v4(a + 128u * kRing, pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]),
-                       pack2(v[6], v[7]));
+      if (prev >= 0 && !mbar_wait(cmt_bar + 8 * (prev % kNB), (uint32_t)((prev / kNB) & 1))) {
+        ok = false;
+        break;
+      }
+      const int o_first = c == 0 ? t : 64 * c + 120 + t;
+      const int o_end = c == 0 ? 184 : 64 * c + 184;
+      for (int o = o_first; o < o_end; o += kProducers) {
+        const uint32_t pa = xs + xoff + (uint32_t)o;
+        const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
+        const uint64_t lo = ld_shared_u64(al), hi = ld_shared_u64(al + 8u);
+        const uint64_t w = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
+        const int e = o >> 3, r = o & 7;
+        const int ps = e % kRing;
+        const uint32_t a = slots + 128u * ps + 16u * r;
+        store_row8(a, ps < kMirror ? a + 128u * kRing : 0u, w);
       }
       fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) {
-        tc_fence_after();
+      mbar_arrive(full_bar + 8 * (c % kNB));
+    }
+  } else if (warp == 0) {
+    // MMA issuer: the whole warp waits (a divergent warp whose other lanes sit
+    // in a barrier wait would stall the issuing lane); lane 0 issues.  k range of column group g (columns 32 g .. 32 g + 31, lags
+    // T0 + 4096 g ..): [lo_g, hi_g), relative to ks.
+    int64_t glo[kGroups], ghi[kGroups];
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+      const int64_t lo = -T0 - 128 * (int64_t)(kGroupCols * g + kGroupCols - 1);
+      const int64_t hi = P.ny - T0 - 128 * (int64_t)(kGroupCols * g);
+      glo[g] = (lo > 0 ? lo : 0) - ks;
+      ghi[g] = (hi < P.nx + 127 ? hi : P.nx + 127) - ks;
+    }
+    for (int c = 0; c < nchunks; ++c) {
+      ok = __all_sync(0xffffffffu, mbar_wait(full_bar + 8 * (c % kNB), (uint32_t)((c / kNB) & 1)));
+      if (!ok) break;
+      tc_fence_after();
+      const int64_t kc = (int64_t)kKc * c;
+      int ga = kGroups, gb = -1;
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g)
+        if (glo[g] < kc + kKc && ghi[g] > kc) {
+          ga = g < ga ? g : ga;
+          gb = g;
+        }
+      if (gb >= ga && lane == 0) {
+        const uint32_t idesc = idesc_for(kGroupCols * (gb - ga + 1));
         const int64_t u = u_s + c;
         const int64_t half = u & 1;  // two's complement: u mod 2
-        const int64_t row0 = fdiv(u, 2) - r_lo;
+        const int64_t row0 = fdiv(u, 2) - r_lo + kGroupCols * ga;
         const uint32_t a_start = slots + 128u * (uint32_t)((8 * c) % kRing);
         const uint32_t b_row = (half ? yO : yE) + 128u * (uint32_t)row0;
+        const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
 #pragma unroll
-        for (int s = 0; s < kKc / kKStep; ++s) {
-          const uint64_t ad = sdesc(a_start + 256u * s, 128, 128, 0, 0);
-          const uint32_t bs = b_row + 32u * s;
-          const uint64_t bd = sdesc(bs, 16, 1024, 2, 0);
-          mma_bf16(tmem, ad, bd, (c > 0 || s > 0) ? 1u : 0u);
+        for (int s2 = 0; s2 < kKc / kKStep; ++s2) {
+          const uint64_t ad = sdesc(a_start + 256u * s2, 128, 128, 0, 0);
+          const uint64_t bd = sdesc(b_row + 32u * s2, 16, 1024, 2, 0);
+          mma_bf16(d_col, ad, bd, idesc, 1u);
         }
-        mma_commit(bars + 8 * (c % kNB));
       }
+      if (lane == 0) mma_commit(cmt_bar + 8 * (c % kNB));
       __syncwarp();
     }
     if (lane == 0) mma_commit(done_bar);
