@@ -60,12 +60,29 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fft", action="store_true")
     return ap.parse_args()
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own pairs (weak scaling: no pair is shared)."""
+    return 1002 + 7919 * rank
 
 
 def workload(args, rank):
     from paper_2509_19974_gb300 import synth
-    return synth.equal_batch(seed=1002 + 7919 * rank, npairs=args.npairs, n=args.n, bits=args.bits)
+    return synth.equal_batch(seed=rank_seed(rank), npairs=args.npairs, n=args.n, bits=args.bits)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time: the only cross-rank reduction of the bench."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def config(args, world):
@@ -242,10 +259,7 @@ def main():
     ms = e0.elapsed_time(e1)
     launches, eng_launches, eng_ms = ctx.read_profile()
     ctx.sync()
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, device="cuda")
     value = args.npairs * world * args.steps / (ms_max / 1e3)
 
     # --- end to end through the public API from pinned host memory
@@ -268,15 +282,43 @@ def main():
             lag_h.copy_(lags, non_blocking=True)
         f1.record(stream)
         barrier()
-        t = torch.tensor([f0.elapsed_time(f1)], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": args.npairs * world * args.steps / (float(t.item()) / 1e3),
+        t_e2e = max_over_ranks(f0.elapsed_time(f1), world, device="cuda")
+        e2e = {"value": args.npairs * world * args.steps / (t_e2e / 1e3),
                "unit": "pairs/s", "h2d_bytes_per_step": int(X.nbytes + Y.nbytes),
                "d2h_bytes_per_step": int(lag_h.numel() * 8)}
 
     gpu_lags = lags.cpu().numpy()
     gpu_vals = vals.cpu().numpy()
+
+    # --- FP32 FFT comparator beside it: the same quantized pairs, timed alone
+    fft = None
+    if not args.no_fft:
+        qX = torch.stack([ctx.quantize(x, args.bits) for x in xs])
+        qY = torch.stack([ctx.quantize(y, args.bits) for y in ys])
+        c_exact = torch.empty(args.npairs * (2 * args.n - 1), dtype=torch.int32, device="cuda")
+        tde.tde_estimate_batch(ctx, None, None, args.bits, engine=args.engine, descs=descs,
+                               c_out=c_exact)
+        c_fft = ctx.xcorr_fft32(qX, qY)
+        for _ in range(2):
+            ctx.xcorr_fft32(qX, qY, c_out=c_fft)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        reps = max(3, args.steps // 4)
+        for _ in range(reps):
+            ctx.xcorr_fft32(qX, qY, c_out=c_fft)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms_fft = g0.elapsed_time(g1) / reps
+        ce = c_exact.view(args.npairs, -1)
+        err = ((c_fft.double() - ce.double()).abs().amax(dim=1) / ce.abs().amax(dim=1).double())
+        am = c_fft.argmax(dim=1, keepdim=True)
+        agree = (ce.gather(1, am).squeeze(1) == ce.amax(dim=1)).float().mean()
+        fft = {"pairs_per_s": args.npairs / (ms_fft / 1e3), "ms_per_batch": ms_fft,
+               "what": "cuFFT R2C/C2R FP32 correlation of the same quantized pairs (int8 in)",
+               "max_err_over_max_abs_c": float(err.max()), "bound": 1e-4,
+               "lag_is_exact_maximiser_frac": float(agree)}
+        del qX, qY, c_exact, c_fft
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -322,7 +364,7 @@ def main():
            "data": "synthetic", "config": config(args, world), "e2e": e2e,
            "gpu_launches": int(launches), "roofline": roof,
            "mac_per_s": macs * world * args.steps / (ms_max / 1e3),
-           "clocks": clk.summary()}
+           "clocks": clk.summary(), "fft32_comparator": fft}
     if not args.no_cpu_baseline and world == 1:
         cb, ref = cpu_baseline(b, args.cpu_seconds)
         out["cpu_baseline"] = cb

@@ -64,8 +64,8 @@ enum {
   TDE_ENGINE_NTT = 3   /* two-prime number-theoretic transform + CRT */
 };
 
-/* Correlation output element types (the "dtype" arguments). */
-enum { TDE_I32 = 0, TDE_I64 = 1 };
+/* Element types of the "dtype" arguments. */
+enum { TDE_I32 = 0, TDE_I64 = 1, TDE_F32 = 2, TDE_I8 = 3 };
 
 typedef struct tde_ctx tde_ctx;
 
@@ -164,6 +164,19 @@ tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t lag_min, i
 tde_status tde_estimate(tde_ctx* ctx, const float* x, int64_t nx, const float* y, int64_t ny,
                         int bits, int64_t lag_min, int64_t lag_max, int engine,
                         int64_t* lag_out, int64_t* val_out, tde_stream_t stream);
+
+/* FP32 FFT correlation comparator (the real-valued FFT baseline of Sec. 2.3;
+ * not exact, not on the estimator's path): for npairs equal-shape pairs,
+ * c_out[p * count + i] = sum_n x_p[n] * y_p[n + lag_min + i] computed as
+ * IDFT(conj(DFT x) DFT y) over a zero-padded power-of-two length
+ * >= nx + ny - 1 in FP32 (cuFFT).  x: npairs * nx and y: npairs * ny elements
+ * of in_dtype (TDE_F32 or TDE_I8, e.g. quantized levels), device, pair after
+ * pair.  count = lag_max - lag_min + 1; lags as in tde_xcorr_int.  c_out:
+ * npairs * count floats, device.  Transform buffers live in the context's
+ * workspace; the cuFFT plan is cached in the context. */
+tde_status tde_xcorr_fft32(tde_ctx* ctx, const void* x, const void* y, int in_dtype, int64_t nx,
+                           int64_t ny, int npairs, int64_t lag_min, int64_t lag_max, float* c_out,
+                           tde_stream_t stream);
 
 /* One pair of a batch: device pointers and sizes, lag range inclusive. */
 typedef struct {

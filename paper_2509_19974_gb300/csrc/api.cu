@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "mma.cuh"
+#include "fftcmp.cuh"
 
 struct tde_ctx {
   int device = 0;
@@ -28,6 +29,7 @@ struct tde_ctx {
   std::vector<cudaEvent_t> ev;  // start/end pairs around engine kernels
   size_t ev_used = 0;
   int64_t launches = 0, engine_launches = 0;
+  FftPlan fft;
 };
 
 thread_local int64_t tde_launch_counter = 0;
@@ -221,6 +223,7 @@ extern "C" tde_status tde_ctx_destroy(tde_ctx* ctx) {
     if (ctx->stage) cudaFreeHost(ctx->stage);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    fft_plan_destroy(&ctx->fft);
   }
   delete ctx;
   return TDE_OK;
@@ -703,4 +706,37 @@ extern "C" tde_status tde_estimate(tde_ctx* ctx, const float* x, int64_t nx, con
                                    tde_stream_t stream) {
   tde_pair_desc d{x, y, nx, ny, lag_min, lag_max};
   return tde_estimate_batch(ctx, &d, 1, bits, engine, nullptr, lag_out, val_out, stream);
+}
+
+extern "C" tde_status tde_xcorr_fft32(tde_ctx* ctx, const void* x, const void* y, int in_dtype,
+                                      int64_t nx, int64_t ny, int npairs, int64_t lag_min,
+                                      int64_t lag_max, float* c_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!x || !y || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (in_dtype != TDE_F32 && in_dtype != TDE_I8)
+    return set_err(ctx, TDE_ERR_INVALID, "in_dtype must be TDE_F32 or TDE_I8");
+  if (nx <= 0 || ny <= 0 || npairs <= 0)
+    return set_err(ctx, TDE_ERR_INVALID, "sizes must be positive");
+  if (lag_min > lag_max || lag_min < -(nx - 1) || lag_max > ny - 1)
+    return set_err(ctx, TDE_ERR_INVALID, "lag range outside [-(nx-1), ny-1]");
+  const int64_t L = fft_length(nx, ny);
+  if (L > ((int64_t)1 << 30)) return set_err(ctx, TDE_ERR_UNSUPPORTED, "transform too long");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (fft_plan(&ctx->fft, L, npairs) != 0)
+    return set_err(ctx, TDE_ERR_CUDA, "cuFFT plan creation failed (L=%lld, batch=%d)",
+                   (long long)L, npairs);
+  Layout Lay;
+  const size_t o_rx = Lay.w<float>((size_t)npairs * L), o_ry = Lay.w<float>((size_t)npairs * L);
+  const size_t o_sx = Lay.w<float2>((size_t)npairs * (L / 2 + 1));
+  const size_t o_sy = Lay.w<float2>((size_t)npairs * (L / 2 + 1));
+  Bases B;
+  tde_status s = realize(ctx, Lay, &B);
+  if (s != TDE_OK) return s;
+  if (fft_xcorr(ctx->fft, x, y, in_dtype == TDE_I8, nx, ny, lag_min, lag_max - lag_min + 1, c_out,
+                B.dw<float>(o_rx), B.dw<float>(o_ry), B.dw<float2>(o_sx), B.dw<float2>(o_sy),
+                st) != 0)
+    return set_err(ctx, TDE_ERR_CUDA, "FFT comparator failed");
+  return TDE_OK;
 }

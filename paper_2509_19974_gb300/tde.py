@@ -22,13 +22,13 @@ TDE_OK, TDE_ERR_INVALID, TDE_ERR_OVERFLOW, TDE_ERR_UNSUPPORTED, TDE_ERR_CUDA, TD
 STATUS_NAMES = {0: "TDE_OK", 1: "TDE_ERR_INVALID", 2: "TDE_ERR_OVERFLOW", 3: "TDE_ERR_UNSUPPORTED",
                 4: "TDE_ERR_CUDA", 5: "TDE_ERR_TIMEOUT"}
 ENGINES = {"auto": 0, "popc": 1, "mma": 2, "ntt": 3}
-TDE_I32, TDE_I64 = 0, 1
+TDE_I32, TDE_I64, TDE_F32, TDE_I8 = 0, 1, 2, 3
 
 # Every symbol include/tde.h declares.
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
            "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
-           "tde_quantize_noalloc", "tde_xcorr_int", "tde_argmax", "tde_estimate",
-           "tde_estimate_batch")
+           "tde_quantize_noalloc", "tde_xcorr_int", "tde_argmax", "tde_xcorr_fft32",
+           "tde_estimate", "tde_estimate_batch")
 
 
 class TdeError(RuntimeError):
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_quantize_noalloc": ([p, i64, i32, i32, p, p, p], st),
         "tde_xcorr_int": ([p, p, i64, p, i64, i32, i64, i64, i32, p, i32, p], st),
         "tde_argmax": ([p, p, i32, i64, i64, p, p, p], st),
+        "tde_xcorr_fft32": ([p, p, p, i32, i64, i64, i32, i64, i64, p, p], st),
         "tde_estimate": ([p, p, i64, p, i64, i32, i64, i64, i32, p, p, p], st),
         "tde_estimate_batch": ([p, ctypes.POINTER(PairDesc), i32, i32, i32, p, p, p, p], st),
     }
@@ -150,6 +151,9 @@ class Context:
     def argmax(self, c, lag_min, stream=None):
         return tde_argmax(self, c, lag_min, stream)
 
+    def xcorr_fft32(self, x, y, lag_min=None, lag_max=None, c_out=None, stream=None):
+        return tde_xcorr_fft32(self, x, y, lag_min, lag_max, c_out, stream)
+
     def estimate(self, x, y, bits, lag_min=None, lag_max=None, engine="auto", stream=None):
         return tde_estimate(self, x, y, bits, lag_min, lag_max, engine, stream)
 
@@ -232,6 +236,27 @@ def tde_argmax(ctx: Context, c, lag_min, stream=None):
     ctx.check(ctx.lib.tde_argmax(ctx.handle, c.data_ptr(), code, int(lag_min), c.numel(),
                                  lag.data_ptr(), val.data_ptr(), _stream(stream)))
     return lag, val
+
+
+def tde_xcorr_fft32(ctx: Context, x, y, lag_min=None, lag_max=None, c_out=None, stream=None):
+    """FP32 FFT comparator.  x: [npairs, nx], y: [npairs, ny] (float32 or
+    int8, or 1-D for one pair); returns [npairs, count] float32."""
+    if x.dtype not in (torch.float32, torch.int8) or y.dtype != x.dtype:
+        raise TypeError("x and y must both be float32 or both int8")
+    _need(x, x.dtype, "x")
+    _need(y, y.dtype, "y")
+    x2, y2 = (x.view(1, -1), y.view(1, -1)) if x.dim() == 1 else (x, y)
+    npairs, nx, ny = x2.shape[0], x2.shape[1], y2.shape[1]
+    lo, hi = full_lags(nx, ny)
+    lag_min = lo if lag_min is None else int(lag_min)
+    lag_max = hi if lag_max is None else int(lag_max)
+    if c_out is None:
+        c_out = torch.empty((npairs, lag_max - lag_min + 1), dtype=torch.float32, device=x.device)
+    _need(c_out, torch.float32, "c_out")
+    code = TDE_I8 if x.dtype == torch.int8 else TDE_F32
+    ctx.check(ctx.lib.tde_xcorr_fft32(ctx.handle, x2.data_ptr(), y2.data_ptr(), code, nx, ny,
+                                      npairs, lag_min, lag_max, c_out.data_ptr(), _stream(stream)))
+    return c_out
 
 
 def tde_estimate(ctx: Context, x, y, bits, lag_min=None, lag_max=None, engine="auto", stream=None):
