@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "mma.cuh"
 #include "fftcmp.cuh"
+#include "ntt.cuh"
 
 struct tde_ctx {
   int device = 0;
@@ -30,6 +31,7 @@ struct tde_ctx {
   size_t ev_used = 0;
   int64_t launches = 0, engine_launches = 0;
   FftPlan fft;
+  uint32_t* ntt_tables[kNttMaxLog + 1] = {};  // per log2 length, 8 * N uint32
 };
 
 thread_local int64_t tde_launch_counter = 0;
@@ -224,6 +226,8 @@ extern "C" tde_status tde_ctx_destroy(tde_ctx* ctx) {
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     fft_plan_destroy(&ctx->fft);
+    for (uint32_t* t : ctx->ntt_tables)
+      if (t) cudaFree(t);
   }
   delete ctx;
   return TDE_OK;
@@ -463,35 +467,217 @@ struct MmaStage {
   }
 };
 
+// ---- step B, number-theoretic-transform engine
+// Template = the shorter signal; the other is cut into overlap-save blocks.
+struct NttPlanPair {
+  int logn = 0;
+  int sign = 1;
+  const int8_t* t = nullptr;
+  const int8_t* a = nullptr;
+  int64_t nt = 0, na = 0;
+  std::vector<std::pair<int64_t, int64_t>> blocks;  // (start, valid)
+};
+
+// Valid outputs of an overlap-save block of length N starting at S: R[S + j']
+// for j' < V.  Outputs j' <= N - nt never wrap.  Beyond that the circular sum
+// drops a[S + j' + j] and adds a[S + j' + j - N] for j >= N - j'; both are
+// zero when the block reaches past the end of a (S + N >= na) and the wrapped
+// indices stay below 0 (j' < N - nt + 1 - S).
+int64_t ntt_valid(int64_t N, int64_t nt, int64_t na, int64_t S) {
+  if (S < 0 && S + N >= na) return std::min<int64_t>(N, N - nt + 1 - S);
+  return N - nt + 1;
+}
+
+// Overlap-save blocks of length N = 2^logn covering k in [k0, k1].
+std::vector<std::pair<int64_t, int64_t>> ntt_blocks(int logn, int64_t nt, int64_t na, int64_t k0,
+                                                    int64_t k1) {
+  std::vector<std::pair<int64_t, int64_t>> out;
+  const int64_t N = (int64_t)1 << logn;
+  for (int64_t S = k0; S <= k1;) {
+    const int64_t V = ntt_valid(N, nt, na, S);
+    out.emplace_back(S, V);
+    S += V;
+  }
+  return out;
+}
+
+// False if no length up to 2^kNttMaxLog holds the template.
+bool ntt_plan_pair(const Job& j, NttPlanPair* pp) {
+  const bool tx = j.nx <= j.ny;  // template = x: R[k] = c[k]; else c[-k]
+  pp->t = tx ? j.qx : j.qy;
+  pp->a = tx ? j.qy : j.qx;
+  pp->nt = tx ? j.nx : j.ny;
+  pp->na = tx ? j.ny : j.nx;
+  pp->sign = tx ? 1 : -1;
+  const int64_t k0 = tx ? j.lag_min : -j.lag_max, k1 = tx ? j.lag_max : -j.lag_min;
+  double best = -1.0;
+  for (int logn = kNttMinLog; logn <= kNttMaxLog; ++logn) {
+    const int64_t N = (int64_t)1 << logn;
+    if (N < pp->nt) continue;
+    // count blocks without building the list
+    int64_t nb = 0;
+    for (int64_t S = k0; S <= k1 && nb < (1 << 22);) {
+      S += ntt_valid(N, pp->nt, pp->na, S);
+      ++nb;
+    }
+    const double cost = (double)(nb + 1) * (double)N * logn;
+    if (best < 0 || cost < best) {
+      best = cost;
+      pp->logn = logn;
+    }
+  }
+  if (best < 0) return false;
+  pp->blocks = ntt_blocks(pp->logn, pp->nt, pp->na, k0, k1);
+  return true;
+}
+
+tde_status ntt_tables(tde_ctx* ctx, int logn, NttTables* T) {
+  if (!ctx->ntt_tables[logn]) {
+    const size_t N = (size_t)1 << logn;
+    std::vector<uint32_t> h(8 * N);
+    ntt_host_tables(logn, h.data());
+    uint32_t* d = nullptr;
+    TDE_CK(cudaMalloc(&d, 8 * N * sizeof(uint32_t)));
+    TDE_CK(cudaMemcpy(d, h.data(), 8 * N * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    ctx->ntt_tables[logn] = d;
+  }
+  const size_t N = (size_t)1 << logn;
+  const uint32_t* d = ctx->ntt_tables[logn];
+  for (int q = 0; q < 2; ++q) {
+    T->tw[q] = d + (0 + q) * N;
+    T->tws[q] = d + (2 + q) * N;
+    T->itw[q] = d + (4 + q) * N;
+    T->itws[q] = d + (6 + q) * N;
+  }
+  return TDE_OK;
+}
+
+struct NttStage {
+  int njobs = 0;
+  bool ok = true;
+  std::vector<NttPlanPair> pp;
+  size_t o_pairs = 0;
+  // per log2 length: template jobs, block jobs and their buffers
+  struct Group {
+    int logn;
+    std::vector<int> pairs;
+    size_t o_tjobs = 0, o_bjobs = 0;
+    int ntemplates = 0, nblocks = 0;
+    std::vector<size_t> o_tbuf, o_bbuf;
+  };
+  std::vector<Group> groups;
+  void plan(Layout& L, const std::vector<Job>& jobs) {
+    njobs = (int)jobs.size();
+    pp.assign(njobs, NttPlanPair{});
+    groups.clear();
+    for (int i = 0; i < njobs; ++i) {
+      if (!ntt_plan_pair(jobs[i], &pp[i])) {
+        ok = false;
+        return;
+      }
+      Group* g = nullptr;
+      for (Group& x : groups)
+        if (x.logn == pp[i].logn) g = &x;
+      if (!g) {
+        groups.push_back(Group{});
+        g = &groups.back();
+        g->logn = pp[i].logn;
+      }
+      g->pairs.push_back(i);
+    }
+    o_pairs = L.d<NttPairOut>(njobs);
+    for (Group& g : groups) {
+      const size_t N = (size_t)1 << g.logn;
+      g.ntemplates = (int)g.pairs.size();
+      g.nblocks = 0;
+      for (int i : g.pairs) g.nblocks += (int)pp[i].blocks.size();
+      g.o_tjobs = L.d<NttJob>(g.ntemplates);
+      g.o_bjobs = L.d<NttJob>(g.nblocks);
+      g.o_tbuf.clear(), g.o_bbuf.clear();
+      for (int t = 0; t < g.ntemplates; ++t) g.o_tbuf.push_back(L.w<uint32_t>(2 * N));
+      for (int b = 0; b < g.nblocks; ++b) g.o_bbuf.push_back(L.w<uint32_t>(2 * N));
+    }
+  }
+  void fill(const Bases& B, const std::vector<Job>& jobs) {
+    NttPairOut* po = B.hd<NttPairOut>(o_pairs);
+    for (Group& g : groups) {
+      NttJob* tj = B.hd<NttJob>(g.o_tjobs);
+      NttJob* bj = B.hd<NttJob>(g.o_bjobs);
+      int b = 0;
+      for (int t = 0; t < g.ntemplates; ++t) {
+        const int i = g.pairs[t];
+        NttPlanPair& P = pp[i];
+        // the pointers of a Job are bound only now
+        const bool tx = jobs[i].nx <= jobs[i].ny;
+        P.t = tx ? jobs[i].qx : jobs[i].qy;
+        P.a = tx ? jobs[i].qy : jobs[i].qx;
+        uint32_t* spec = B.dw<uint32_t>(g.o_tbuf[t]);
+        tj[t] = NttJob{P.t, P.nt, 0, 0, spec, i, 1};
+        po[i] = NttPairOut{spec, jobs[i].c, jobs[i].lag_min, jobs[i].lag_max, jobs[i].c64, P.sign};
+        for (auto& blk : P.blocks) {
+          bj[b] = NttJob{P.a, P.na, blk.first, blk.second, B.dw<uint32_t>(g.o_bbuf[b]), i, 0};
+          ++b;
+        }
+      }
+    }
+  }
+  cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
+    for (const Group& g : groups) {
+      NttTables T;
+      if (ntt_tables(ctx, g.logn, &T) != TDE_OK) return cudaErrorMemoryAllocation;
+      cudaError_t e = launch_ntt_templates(B.dd<NttJob>(g.o_tjobs), g.ntemplates, g.logn, T, st);
+      if (e != cudaSuccess) return e;
+      EngineTimer t(ctx, st);
+      e = launch_ntt_blocks(B.dd<NttJob>(g.o_bjobs), g.nblocks, B.dd<NttPairOut>(o_pairs), g.logn,
+                            T, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+};
+
 // Both engines over one job list: each job goes to the engine picked for it.
 struct XcorrStage {
   std::vector<int> eng;                 // per job
-  std::vector<Job> popc_jobs, mma_jobs;
-  std::vector<int> popc_idx, mma_idx;   // job -> position in its engine list
+  std::vector<Job> popc_jobs, mma_jobs, ntt_jobs;
   PopcStage popc;
   MmaStage mma;
+  NttStage ntt;
   int bits = 1;
-  void plan(Layout& L, const std::vector<Job>& jobs, const std::vector<int>& engines, int b) {
+  std::vector<Job>& list(int e) {
+    return e == TDE_ENGINE_MMA ? mma_jobs : (e == TDE_ENGINE_NTT ? ntt_jobs : popc_jobs);
+  }
+  // False if some job cannot be served by its engine.
+  bool plan(Layout& L, const std::vector<Job>& jobs, const std::vector<int>& engines, int b) {
     bits = b;
     eng = engines;
-    popc_jobs.clear(), mma_jobs.clear();
-    for (size_t i = 0; i < jobs.size(); ++i)
-      (eng[i] == TDE_ENGINE_MMA ? mma_jobs : popc_jobs).push_back(jobs[i]);
+    popc_jobs.clear(), mma_jobs.clear(), ntt_jobs.clear();
+    for (size_t i = 0; i < jobs.size(); ++i) list(eng[i]).push_back(jobs[i]);
     popc.plan(L, popc_jobs, bits);
     mma.plan(L, mma_jobs);
+    ntt.plan(L, ntt_jobs);
+    return ntt.ok;
   }
   // Binds pointers (known after realize) and writes the descriptors.
   void fill(const Bases& B, const std::vector<Job>& jobs) {
-    size_t a = 0, m = 0;
-    for (size_t i = 0; i < jobs.size(); ++i)
-      (eng[i] == TDE_ENGINE_MMA ? mma_jobs[m++] : popc_jobs[a++]) = jobs[i];
+    size_t a = 0, m = 0, t = 0;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      if (eng[i] == TDE_ENGINE_MMA)
+        mma_jobs[m++] = jobs[i];
+      else if (eng[i] == TDE_ENGINE_NTT)
+        ntt_jobs[t++] = jobs[i];
+      else
+        popc_jobs[a++] = jobs[i];
+    }
     popc.fill(B, popc_jobs);
     mma.fill(B, mma_jobs);
+    ntt.fill(B, ntt_jobs);
   }
   cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
     cudaError_t e = cudaSuccess;
     if (!popc_jobs.empty()) e = popc.launch(ctx, B, st);
     if (e == cudaSuccess && !mma_jobs.empty()) e = mma.launch(ctx, B, st);
+    if (e == cudaSuccess && !ntt_jobs.empty()) e = ntt.launch(ctx, B, st);
     return e;
   }
 };
@@ -540,7 +726,8 @@ int pick_engine(int engine, int bits, int64_t nx, int64_t ny, int64_t lag_count)
 }
 
 tde_status engine_available(tde_ctx* ctx, int engine) {
-  if (engine == TDE_ENGINE_POPC || engine == TDE_ENGINE_MMA) return TDE_OK;
+  if (engine == TDE_ENGINE_POPC || engine == TDE_ENGINE_MMA || engine == TDE_ENGINE_NTT)
+    return TDE_OK;
   return set_err(ctx, TDE_ERR_UNSUPPORTED, "engine %d is not available in this build", engine);
 }
 
@@ -589,7 +776,10 @@ extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, 
   std::vector<Job> jobs{Job{qx, qy, nx, ny, lag_min, lag_max, c_out, out_dtype == TDE_I64}};
   Layout L;
   XcorrStage E;
-  E.plan(L, jobs, std::vector<int>{eng}, bits);
+  if (!E.plan(L, jobs, std::vector<int>{eng}, bits))
+    return set_err(ctx, TDE_ERR_UNSUPPORTED,
+                   "NTT engine: the shorter signal exceeds the largest transform (2^%d)",
+                   kNttMaxLog);
   Bases B;
   if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
   E.fill(B, jobs);
@@ -671,7 +861,10 @@ extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* desc
     jobs[p] = Job{nullptr, nullptr, descs[p].nx, descs[p].ny, descs[p].lag_min, descs[p].lag_max,
                   nullptr, 0};
   XcorrStage E;
-  E.plan(L, jobs, engs, bits);
+  if (!E.plan(L, jobs, engs, bits))
+    return set_err(ctx, TDE_ERR_UNSUPPORTED,
+                   "NTT engine: a pair's shorter signal exceeds the largest transform (2^%d)",
+                   kNttMaxLog);
   ArgStage A;
   A.plan(L, npairs, max_count, 0);
   Bases B;

@@ -15,7 +15,7 @@ from paper_2509_19974_gb300 import synth, tde
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["popc", "mma"]
+ENGINES = ["popc", "mma", "ntt"]
 
 
 @pytest.fixture(scope="module")
