@@ -199,6 +199,25 @@ tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* descs, int npai
                               int engine, int32_t* c_out, int64_t* lag_out, int64_t* val_out,
                               tde_stream_t stream);
 
+/* A planned batch: the whole step of tde_estimate_batch (quantize every
+ * signal, correlate every pair -- each engine one persistent launch over all
+ * of its pairs' work, longest work first --, argmax every pair) captured once
+ * into a CUDA graph over memory the batch owns, then replayed.  Descriptors,
+ * bits, engine and the output pointers (c_out may be NULL, as in
+ * tde_estimate_batch) are fixed at creation; the caller refills the input
+ * buffers the descriptors point to between runs.  *out (host) receives the
+ * handle.  Creation allocates device memory and synchronizes; runs do not
+ * allocate. */
+typedef struct tde_batch tde_batch;
+tde_status tde_batch_create(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int bits,
+                            int engine, int32_t* c_out, int64_t* lag_out, int64_t* val_out,
+                            tde_batch** out);
+/* Replays the batch's graph on `stream` (asynchronous).  Device-side errors
+ * are reported by tde_ctx_sync on the batch's context. */
+tde_status tde_batch_run(tde_batch* batch, tde_stream_t stream);
+/* Synchronizes the device, frees the batch.  NULL is accepted. */
+tde_status tde_batch_destroy(tde_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -409,7 +409,7 @@ struct PopcStage {
 struct MmaStage {
   int njobs = 0, nitems = 0, any_zero = 0;
   int64_t max_count = 0;
-  size_t o_pairs = 0, o_items = 0;
+  size_t o_pairs = 0, o_items = 0, o_counter = 0;
   std::vector<MmaItem> items;
   std::vector<int> zero_first;
   void plan(Layout& L, const std::vector<Job>& jobs) {
@@ -443,9 +443,14 @@ struct MmaStage {
       }
       any_zero |= zero_first[i];
     }
+    // Longest first: the persistent CTAs then finish close together.
+    std::stable_sort(items.begin(), items.end(), [](const MmaItem& a, const MmaItem& b) {
+      return a.ke - a.ks > b.ke - b.ks;
+    });
     nitems = (int)items.size();
     o_pairs = L.d<MmaPair>(njobs);
     o_items = L.d<MmaItem>(nitems);
+    o_counter = L.w<int>(1);
   }
   void fill(const Bases& B, const std::vector<Job>& jobs) const {
     MmaPair* p = B.hd<MmaPair>(o_pairs);
@@ -462,8 +467,8 @@ struct MmaStage {
       if (e != cudaSuccess) return e;
     }
     EngineTimer t(ctx, st);
-    return launch_xcorr_mma(B.dd<MmaPair>(o_pairs), B.dd<MmaItem>(o_items), nitems, ctx->d_status,
-                            st);
+    return launch_xcorr_mma(B.dd<MmaPair>(o_pairs), B.dd<MmaItem>(o_items), nitems,
+                            B.dw<int>(o_counter), 2 * ctx->sm_count, ctx->d_status, st);
   }
 };
 
@@ -815,14 +820,31 @@ extern "C" tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t
   return TDE_OK;
 }
 
-extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* descs, int npairs,
-                                         int bits, int engine, int32_t* c_out, int64_t* lag_out,
-                                         int64_t* val_out, tde_stream_t stream) {
-  if (!ctx) return TDE_ERR_INVALID;
-  if (!descs || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+namespace {
+
+// Everything one batch (Algorithm 1, lines 1-4 over many pairs) needs, planned
+// from the descriptors alone; pointers are bound by fill() once memory exists.
+struct BatchWork {
+  int npairs = 0, bits = 1;
+  Layout L;
+  QuantStage Q;
+  XcorrStage E;
+  ArgStage A;
+  std::vector<int> engs;
+  std::vector<size_t> o_q;
+  std::vector<int64_t> c_start;
+  size_t o_call = 0;
+  bool own_c = true;
+  std::vector<Job> jobs;
+};
+
+tde_status batch_plan(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int bits, int engine,
+                      bool have_c_out, BatchWork* w) {
   if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
   tde_status s;
-  std::vector<int> engs(npairs);
+  w->npairs = npairs;
+  w->bits = bits;
+  w->engs.assign(npairs, 0);
   int64_t max_n = 0, max_count = 0;
   for (int p = 0; p < npairs; ++p) {
     const tde_pair_desc& d = descs[p];
@@ -830,66 +852,173 @@ extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* desc
     s = check_xcorr_args(ctx, d.nx, d.ny, bits, d.lag_min, d.lag_max, engine, TDE_I32);
     if (s != TDE_OK) return s;
     const int64_t cnt = d.lag_max - d.lag_min + 1;
-    engs[p] = pick_engine(engine, bits, d.nx, d.ny, cnt);
-    if ((s = engine_available(ctx, engs[p])) != TDE_OK) return s;
-    max_n = d.nx > max_n ? d.nx : max_n;
-    max_n = d.ny > max_n ? d.ny : max_n;
-    max_count = cnt > max_count ? cnt : max_count;
+    w->engs[p] = pick_engine(engine, bits, d.nx, d.ny, cnt);
+    if ((s = engine_available(ctx, w->engs[p])) != TDE_OK) return s;
+    max_n = std::max(max_n, std::max(d.nx, d.ny));
+    max_count = std::max(max_count, cnt);
   }
-  DeviceGuard g(ctx->device);
-  LaunchCount lc(ctx);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-
-  // Plan: quantized signals and (unless the caller gives c_out) correlations
-  // live in the workspace.
-  Layout L;
-  QuantStage Q;
-  Q.plan(L, 2 * npairs, bits, max_n);
-  std::vector<size_t> o_q(2 * npairs), o_c(npairs);
-  std::vector<int64_t> c_start(npairs);
+  // Quantized signals and (unless the caller gives c_out) correlations live
+  // in the work memory.
+  w->Q.plan(w->L, 2 * npairs, bits, max_n);
+  w->o_q.assign(2 * npairs, 0);
+  w->c_start.assign(npairs, 0);
   int64_t c_total = 0;
   for (int p = 0; p < npairs; ++p) {
-    o_q[2 * p] = L.w<int8_t>((size_t)descs[p].nx);
-    o_q[2 * p + 1] = L.w<int8_t>((size_t)descs[p].ny);
-    c_start[p] = c_total;
+    w->o_q[2 * p] = w->L.w<int8_t>((size_t)descs[p].nx);
+    w->o_q[2 * p + 1] = w->L.w<int8_t>((size_t)descs[p].ny);
+    w->c_start[p] = c_total;
     c_total += descs[p].lag_max - descs[p].lag_min + 1;
   }
-  const size_t o_call = c_out ? 0 : L.w<int32_t>((size_t)c_total);
-  // The engine's plan needs only the sizes; pointers are bound after realize().
-  std::vector<Job> jobs(npairs);
+  w->own_c = !have_c_out;
+  w->o_call = have_c_out ? 0 : w->L.w<int32_t>((size_t)c_total);
+  w->jobs.assign(npairs, Job{});
   for (int p = 0; p < npairs; ++p)
-    jobs[p] = Job{nullptr, nullptr, descs[p].nx, descs[p].ny, descs[p].lag_min, descs[p].lag_max,
-                  nullptr, 0};
-  XcorrStage E;
-  if (!E.plan(L, jobs, engs, bits))
+    w->jobs[p] = Job{nullptr, nullptr, descs[p].nx, descs[p].ny, descs[p].lag_min,
+                     descs[p].lag_max, nullptr, 0};
+  if (!w->E.plan(w->L, w->jobs, w->engs, bits))
     return set_err(ctx, TDE_ERR_UNSUPPORTED,
                    "NTT engine: a pair's shorter signal exceeds the largest transform (2^%d)",
                    kNttMaxLog);
-  ArgStage A;
-  A.plan(L, npairs, max_count, 0);
-  Bases B;
-  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
+  w->A.plan(w->L, npairs, max_count, 0);
+  return TDE_OK;
+}
 
-  std::vector<const float*> xs(2 * npairs);
-  std::vector<int8_t*> qs(2 * npairs);
-  std::vector<int64_t> ns(2 * npairs);
-  int32_t* c_base = c_out ? c_out : B.dw<int32_t>(o_call);
-  for (int p = 0; p < npairs; ++p) {
+void batch_fill(BatchWork* w, const Bases& B, const tde_pair_desc* descs, int32_t* c_out,
+                int64_t* lag_out, int64_t* val_out) {
+  const int np = w->npairs;
+  std::vector<const float*> xs(2 * np);
+  std::vector<int8_t*> qs(2 * np);
+  std::vector<int64_t> ns(2 * np);
+  int32_t* c_base = w->own_c ? B.dw<int32_t>(w->o_call) : c_out;
+  for (int p = 0; p < np; ++p) {
     xs[2 * p] = descs[p].x, xs[2 * p + 1] = descs[p].y;
-    qs[2 * p] = B.dw<int8_t>(o_q[2 * p]), qs[2 * p + 1] = B.dw<int8_t>(o_q[2 * p + 1]);
+    qs[2 * p] = B.dw<int8_t>(w->o_q[2 * p]), qs[2 * p + 1] = B.dw<int8_t>(w->o_q[2 * p + 1]);
     ns[2 * p] = descs[p].nx, ns[2 * p + 1] = descs[p].ny;
-    jobs[p].qx = qs[2 * p], jobs[p].qy = qs[2 * p + 1];
-    jobs[p].c = c_base + c_start[p];
-    A.set(B, p, jobs[p].c, descs[p].lag_min, descs[p].lag_max - descs[p].lag_min + 1,
-          lag_out + p, val_out + p);
+    w->jobs[p].qx = qs[2 * p], w->jobs[p].qy = qs[2 * p + 1];
+    w->jobs[p].c = c_base + w->c_start[p];
+    w->A.set(B, p, w->jobs[p].c, descs[p].lag_min, descs[p].lag_max - descs[p].lag_min + 1,
+             lag_out + p, val_out + p);
   }
-  Q.fill(B, xs.data(), qs.data(), ns.data());
-  E.fill(B, jobs);
-  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
-  cudaError_t e = Q.launch(B, ctx->d_status, st);
-  if (e == cudaSuccess) e = E.launch(ctx, B, st);
-  if (e == cudaSuccess) e = A.launch(B, st);
+  w->Q.fill(B, xs.data(), qs.data(), ns.data());
+  w->E.fill(B, w->jobs);
+}
+
+cudaError_t batch_launch(tde_ctx* ctx, const BatchWork& w, const Bases& B, cudaStream_t st) {
+  cudaError_t e = w.Q.launch(B, ctx->d_status, st);
+  if (e == cudaSuccess) e = w.E.launch(ctx, B, st);
+  if (e == cudaSuccess) e = w.A.launch(B, st);
+  return e;
+}
+
+}  // namespace
+
+extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* descs, int npairs,
+                                         int bits, int engine, int32_t* c_out, int64_t* lag_out,
+                                         int64_t* val_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!descs || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  BatchWork w;
+  tde_status s = batch_plan(ctx, descs, npairs, bits, engine, c_out != nullptr, &w);
+  if (s != TDE_OK) return s;
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Bases B;
+  if ((s = realize(ctx, w.L, &B)) != TDE_OK) return s;
+  batch_fill(&w, B, descs, c_out, lag_out, val_out);
+  if ((s = stage_upload(ctx, B.ddesc, w.L.desc, st)) != TDE_OK) return s;
+  const cudaError_t e = batch_launch(ctx, w, B, st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  return TDE_OK;
+}
+
+// A batch planned once, with its own device memory and descriptors, whose
+// whole step is captured in a CUDA graph.
+struct tde_batch {
+  tde_ctx* ctx = nullptr;
+  BatchWork w;
+  char* mem = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;  // kernels in the graph
+};
+
+extern "C" tde_status tde_batch_create(tde_ctx* ctx, const tde_pair_desc* descs, int npairs,
+                                       int bits, int engine, int32_t* c_out, int64_t* lag_out,
+                                       int64_t* val_out, tde_batch** out) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!descs || !lag_out || !val_out || !out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  *out = nullptr;
+  tde_batch* b = new tde_batch();
+  b->ctx = ctx;
+  tde_status s = batch_plan(ctx, descs, npairs, bits, engine, c_out != nullptr, &b->w);
+  if (s != TDE_OK) {
+    delete b;
+    return s;
+  }
+  DeviceGuard g(ctx->device);
+  auto fail = [&](cudaError_t e, const char* what) {
+    tde_batch_destroy(b);
+    return cuda_err(ctx, e, what);
+  };
+  cudaError_t e = cudaMalloc(&b->mem, b->w.L.total());
+  if (e != cudaSuccess) return fail(e, "cudaMalloc(batch memory)");
+  std::vector<char> host(b->w.L.desc ? b->w.L.desc : 16);
+  Bases B{host.data(), b->mem, b->mem + b->w.L.data_base()};
+  batch_fill(&b->w, B, descs, c_out, lag_out, val_out);
+  e = cudaMemcpy(b->mem, host.data(), b->w.L.desc, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(e, "descriptor upload");
+  // Tables the engines need are built before capture (capture forbids cudaMalloc).
+  for (const auto& grp : b->w.E.ntt.groups) {
+    NttTables T;
+    if (ntt_tables(ctx, grp.logn, &T) != TDE_OK) {
+      tde_batch_destroy(b);
+      return TDE_ERR_CUDA;
+    }
+  }
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(e, "cudaStreamCreate");
+  const bool prof = ctx->profile;
+  ctx->profile = false;
+  const int64_t before = tde_launch_counter;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const cudaError_t le = batch_launch(ctx, b->w, B, cs);
+    e = cudaStreamEndCapture(cs, &b->graph);
+    if (le != cudaSuccess) e = le;
+  }
+  b->launches = tde_launch_counter - before;
+  tde_launch_counter = before;
+  ctx->profile = prof;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return fail(e, "graph capture");
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
+  *out = b;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_batch_run(tde_batch* b, tde_stream_t stream) {
+  if (!b || !b->exec) return TDE_ERR_INVALID;
+  tde_ctx* ctx = b->ctx;
+  DeviceGuard g(ctx->device);
+  const cudaError_t e = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGraphLaunch");
+  ctx->launches += b->launches;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_batch_destroy(tde_batch* b) {
+  if (!b) return TDE_OK;
+  {
+    DeviceGuard g(b->ctx->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->mem) cudaFree(b->mem);
+  }
+  delete b;
   return TDE_OK;
 }
 

@@ -63,7 +63,7 @@ constexpr int kSlotBytes = kSlots * 128;
 constexpr int kXBytes = kMmaKs + 272;                   // x samples a segment's slots read
 constexpr int kProducers = 64;                          // slot-writing threads (warps 1, 2)
 constexpr int kGroups = 8, kGroupCols = kN / kGroups;   // column groups of 32 (4096 lags)
-constexpr int kSmemUsed = 2 * kYBytes + kSlotBytes + kXBytes + (2 * kNB + 1) * 8 + 16;
+constexpr int kSmemUsed = 2 * kYBytes + kSlotBytes + kXBytes + (2 * kNB + 1) * 8 + 16;  // + tmem/item words
 constexpr int kSmemBytes = kSmemUsed + 1024;            // room to align the base
 constexpr uint64_t kTimeoutNs = 2000000000ull;         // 2 s per wait
 static_assert(kMmaTileLags == kM * kN, "tile");
@@ -234,8 +234,8 @@ __device__ __forceinline__ uint4 load16(const int8_t* q, int64_t i0, int64_t n, 
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
-    k_xcorr_mma(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items,
-                uint32_t* __restrict__ status) {
+    k_xcorr_mma(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems,
+                int* __restrict__ counter, uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -245,24 +245,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t cmt_bar = full_bar + 8 * kNB;  // kNB "chunk MMAs done" barriers
   const uint32_t done_bar = cmt_bar + 8 * kNB;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
-
-  const MmaItem it = items[blockIdx.x];
-  const MmaPair P = pairs[it.pair];
+  volatile int* item_slot = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t T0 = it.T0, ks = it.ks, ke = it.ke;
-  const int nchunks = (int)((ke - ks) / kKc);
-  const int64_t u_s = (ks + T0) / kKc, u_l = (ke - kKc + T0) / kKc;  // exact
-  const int64_t r_lo = fdiv(fdiv(u_s, 2), 8) * 8;
-  const int64_t nrows = fdiv(u_l, 2) + 255 - r_lo + 1;
-  // x is staged from a 16-byte aligned index; window o (x index ks - 127 + o)
-  // sits at xs + xoff + o.
-  const int64_t xs_base = fdiv(ks - 127, 16) * 16;
-  const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
-  // The CTA's own bounds checks: the y window and the x segment must fit.
-  if (nrows > kRowsMax || nchunks <= 0 || (ke - ks) + 272 > kXBytes) {
-    if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
-    return;
-  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -279,169 +263,208 @@ __global__ void __launch_bounds__(kThreads, 2)
     mbar_init(done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-
-  // y window: rows r_lo .. r_lo + nrows - 1 of E and O (zero outside [0, ny)),
-  // 16 samples per load, four loads in flight per thread.
-  {
-    const int8_t* qy = P.qy;
-    const bool al16 = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
-    const int total = (int)nrows * 8;  // (row, half, quarter)
-    for (int b0 = threadIdx.x; b0 < total; b0 += 4 * kThreads) {
-      uint4 w[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int idx = b0 + k * kThreads;
-        if (idx < total) {
-          const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
-          w[k] = load16(qy, 128 * (r_lo + row) + 64 * half + 16 * j, P.ny, al16);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int idx = b0 + k * kThreads;
-        if (idx < total) {
-          const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
-          const uint32_t row_addr = (half ? yO : yE) + 128u * (uint32_t)row;
-          const uint32_t sw = (row_addr >> 7) & 7u;
-          store_row8(row_addr + 16u * ((uint32_t)(2 * j) ^ sw), 0u,
-                     (uint64_t)w[k].x | ((uint64_t)w[k].y << 32));
-          store_row8(row_addr + 16u * ((uint32_t)(2 * j + 1) ^ sw), 0u,
-                     (uint64_t)w[k].z | ((uint64_t)w[k].w << 32));
-        }
-      }
-    }
-  }
-  // x segment x[xs_base .. xs_base + kXBytes), zero outside [0, nx).
-  {
-    const int8_t* qx = P.qx;
-    const bool al16 = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
-    for (int i = threadIdx.x; i < kXBytes / 16; i += kThreads) {
-      const uint4 w = load16(qx, xs_base + 16 * i, P.nx, al16);
-      st_shared_v4(xs + 16u * i, w.x, w.y, w.z, w.w);
-    }
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // The accumulator starts at zero: column groups join the sum at different
-  // chunks, so every MMA accumulates.
-  if (warp < 4) {
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    for (int cb = 0; cb < kN; cb += 32) tmem_zero32(tmem + lane_base + (uint32_t)cb);
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  }
-  fence_proxy_async();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
 
+  // Persistent loop: items (pair, 32768-lag tile, K segment) are taken in
+  // the host's order (longest first) from a global counter.  Barrier phases
+  // continue across items: chunk cc0 + c of this CTA uses barrier
+  // (cc0 + c) % kNB with parity ((cc0 + c) / kNB) & 1; "done" completes once per
+  // item.
+  int64_t cc0 = 0;
+  uint32_t iter = 0;
   bool ok = true;
-  if (warp == 1 || warp == 2) {
-    // Slot producers: thread t writes window o = 64 c + 120 + t of chunk c
-    // (chunk 0 writes windows 0..183): slot e = o / 8, row r = o % 8, i.e.
-    // x[ks - 127 + o .. + 7] as BF16.
-    const int t = threadIdx.x - 32;
-    for (int c = 0; c < nchunks; ++c) {
-      // The slots written now were last read by chunk c - (kRing/8 - 2).
-      const int prev = c - (kRing / 8 - 2);
-      if (prev >= 0 && !mbar_wait(cmt_bar + 8 * (prev % kNB), (uint32_t)((prev / kNB) & 1))) {
-        ok = false;
-        break;
-      }
-      const int o_first = c == 0 ? t : 64 * c + 120 + t;
-      const int o_end = c == 0 ? 184 : 64 * c + 184;
-      for (int o = o_first; o < o_end; o += kProducers) {
-        const uint32_t pa = xs + xoff + (uint32_t)o;
-        const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-        const uint64_t lo = ld_shared_u64(al), hi = ld_shared_u64(al + 8u);
-        const uint64_t w = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
-        const int e = o >> 3, r = o & 7;
-        const int ps = e % kRing;
-        const uint32_t a = slots + 128u * ps + 16u * r;
-        store_row8(a, ps < kMirror ? a + 128u * kRing : 0u, w);
-      }
-      fence_proxy_async();
-      mbar_arrive(full_bar + 8 * (c % kNB));
+  for (;; ++iter) {
+    if (threadIdx.x == 0) *item_slot = atomicAdd(counter, 1);
+    __syncthreads();
+    tc_fence_after();
+    const int w_item = *item_slot;
+    if (w_item >= nitems) break;
+    const MmaItem it = items[w_item];
+    const MmaPair P = pairs[it.pair];
+    const int64_t T0 = it.T0, ks = it.ks, ke = it.ke;
+    const int nchunks = (int)((ke - ks) / kKc);
+    const int64_t u_s = (ks + T0) / kKc, u_l = (ke - kKc + T0) / kKc;  // exact
+    const int64_t r_lo = fdiv(fdiv(u_s, 2), 8) * 8;
+    const int64_t nrows = fdiv(u_l, 2) + 255 - r_lo + 1;
+    // x is staged from a 16-byte aligned index; window o (x index ks - 127 + o)
+    // sits at xs + xoff + o.
+    const int64_t xs_base = fdiv(ks - 127, 16) * 16;
+    const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
+    // The CTA's own bounds checks: the y window and the x segment must fit.
+    if (nrows > kRowsMax || nchunks <= 0 || (ke - ks) + 272 > kXBytes) {
+      if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
+      --iter;  // "done" was not used
+      __syncthreads();
+      continue;
     }
-  } else if (warp == 0) {
-    // MMA issuer: the whole warp waits (a divergent warp whose other lanes sit
-    // in a barrier wait would stall the issuing lane); lane 0 issues.  k range of column group g (columns 32 g .. 32 g + 31, lags
-    // T0 + 4096 g ..): [lo_g, hi_g), relative to ks.
-    int64_t glo[kGroups], ghi[kGroups];
-#pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-      const int64_t lo = -T0 - 128 * (int64_t)(kGroupCols * g + kGroupCols - 1);
-      const int64_t hi = P.ny - T0 - 128 * (int64_t)(kGroupCols * g);
-      glo[g] = (lo > 0 ? lo : 0) - ks;
-      ghi[g] = (hi < P.nx + 127 ? hi : P.nx + 127) - ks;
-    }
-    for (int c = 0; c < nchunks; ++c) {
-      ok = __all_sync(0xffffffffu, mbar_wait(full_bar + 8 * (c % kNB), (uint32_t)((c / kNB) & 1)));
-      if (!ok) break;
-      tc_fence_after();
-      const int64_t kc = (int64_t)kKc * c;
-      int ga = kGroups, gb = -1;
-#pragma unroll
-      for (int g = 0; g < kGroups; ++g)
-        if (glo[g] < kc + kKc && ghi[g] > kc) {
-          ga = g < ga ? g : ga;
-          gb = g;
+
+    // y window: rows r_lo .. r_lo + nrows - 1 of E and O (zero outside [0, ny)),
+    // 16 samples per load, four loads in flight per thread.
+    {
+      const int8_t* qy = P.qy;
+      const bool al16 = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+      const int total = (int)nrows * 8;  // (row, half, quarter)
+      for (int b0 = threadIdx.x; b0 < total; b0 += 4 * kThreads) {
+        uint4 w[4];
+  #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int idx = b0 + k * kThreads;
+          if (idx < total) {
+            const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
+            w[k] = load16(qy, 128 * (r_lo + row) + 64 * half + 16 * j, P.ny, al16);
+          }
         }
-      if (gb >= ga && lane == 0) {
-        const uint32_t idesc = idesc_for(kGroupCols * (gb - ga + 1));
-        const int64_t u = u_s + c;
-        const int64_t half = u & 1;  // two's complement: u mod 2
-        const int64_t row0 = fdiv(u, 2) - r_lo + kGroupCols * ga;
-        const uint32_t a_start = slots + 128u * (uint32_t)((8 * c) % kRing);
-        const uint32_t b_row = (half ? yO : yE) + 128u * (uint32_t)row0;
-        const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
-#pragma unroll
-        for (int s2 = 0; s2 < kKc / kKStep; ++s2) {
-          const uint64_t ad = sdesc(a_start + 256u * s2, 128, 128, 0, 0);
-          const uint64_t bd = sdesc(b_row + 32u * s2, 16, 1024, 2, 0);
-          mma_bf16(d_col, ad, bd, idesc, 1u);
+  #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int idx = b0 + k * kThreads;
+          if (idx < total) {
+            const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
+            const uint32_t row_addr = (half ? yO : yE) + 128u * (uint32_t)row;
+            const uint32_t sw = (row_addr >> 7) & 7u;
+            store_row8(row_addr + 16u * ((uint32_t)(2 * j) ^ sw), 0u,
+                       (uint64_t)w[k].x | ((uint64_t)w[k].y << 32));
+            store_row8(row_addr + 16u * ((uint32_t)(2 * j + 1) ^ sw), 0u,
+                       (uint64_t)w[k].z | ((uint64_t)w[k].w << 32));
+          }
         }
       }
-      if (lane == 0) mma_commit(cmt_bar + 8 * (c % kNB));
+    }
+    // x segment x[xs_base .. xs_base + kXBytes), zero outside [0, nx).
+    {
+      const int8_t* qx = P.qx;
+      const bool al16 = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+      for (int i = threadIdx.x; i < kXBytes / 16; i += kThreads) {
+        const uint4 w = load16(qx, xs_base + 16 * i, P.nx, al16);
+        st_shared_v4(xs + 16u * i, w.x, w.y, w.z, w.w);
+      }
+    }
+    // The accumulator starts at zero: column groups join the sum at different
+    // chunks, so every MMA accumulates.
+    if (warp < 4) {
+      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      for (int cb = 0; cb < kN; cb += 32) tmem_zero32(tmem + lane_base + (uint32_t)cb);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 1 || warp == 2) {
+      // Slot producers: thread t writes window o = 64 c + 120 + t of chunk c
+      // (chunk 0 writes windows 0..183): slot e = o / 8, row r = o % 8, i.e.
+      // x[ks - 127 + o .. + 7] as BF16.
+      const int t = threadIdx.x - 32;
+      for (int c = 0; c < nchunks; ++c) {
+        // The slots written now were last read by chunk c - (kRing/8 - 2).
+        const int64_t prev = cc0 + c - (kRing / 8 - 2);
+        if (prev >= 0 && !mbar_wait(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
+          ok = false;
+          break;
+        }
+        const int o_first = c == 0 ? t : 64 * c + 120 + t;
+        const int o_end = c == 0 ? 184 : 64 * c + 184;
+        for (int o = o_first; o < o_end; o += kProducers) {
+          const uint32_t pa = xs + xoff + (uint32_t)o;
+          const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
+          const uint64_t lo = ld_shared_u64(al), hi = ld_shared_u64(al + 8u);
+          const uint64_t w = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
+          const int e = o >> 3, r = o & 7;
+          const int ps = e % kRing;
+          const uint32_t a = slots + 128u * ps + 16u * r;
+          store_row8(a, ps < kMirror ? a + 128u * kRing : 0u, w);
+        }
+        fence_proxy_async();
+        mbar_arrive(full_bar + 8 * (uint32_t)((cc0 + c) % kNB));
+      }
+    } else if (warp == 0) {
+      // MMA issuer: the whole warp waits (a divergent warp whose other lanes sit
+      // in a barrier wait would stall the issuing lane); lane 0 issues.  k range of column group g (columns 32 g .. 32 g + 31, lags
+      // T0 + 4096 g ..): [lo_g, hi_g), relative to ks.
+      int64_t glo[kGroups], ghi[kGroups];
+  #pragma unroll
+      for (int g = 0; g < kGroups; ++g) {
+        const int64_t lo = -T0 - 128 * (int64_t)(kGroupCols * g + kGroupCols - 1);
+        const int64_t hi = P.ny - T0 - 128 * (int64_t)(kGroupCols * g);
+        glo[g] = (lo > 0 ? lo : 0) - ks;
+        ghi[g] = (hi < P.nx + 127 ? hi : P.nx + 127) - ks;
+      }
+      for (int c = 0; c < nchunks; ++c) {
+        const int64_t cc = cc0 + c;
+        ok = __all_sync(0xffffffffu, mbar_wait(full_bar + 8 * (uint32_t)(cc % kNB), (uint32_t)((cc / kNB) & 1)));
+        if (!ok) break;
+        tc_fence_after();
+        const int64_t kc = (int64_t)kKc * c;
+        int ga = kGroups, gb = -1;
+  #pragma unroll
+        for (int g = 0; g < kGroups; ++g)
+          if (glo[g] < kc + kKc && ghi[g] > kc) {
+            ga = g < ga ? g : ga;
+            gb = g;
+          }
+        if (gb >= ga && lane == 0) {
+          const uint32_t idesc = idesc_for(kGroupCols * (gb - ga + 1));
+          const int64_t u = u_s + c;
+          const int64_t half = u & 1;  // two's complement: u mod 2
+          const int64_t row0 = fdiv(u, 2) - r_lo + kGroupCols * ga;
+          const uint32_t a_start = slots + 128u * (uint32_t)((8 * c) % kRing);
+          const uint32_t b_row = (half ? yO : yE) + 128u * (uint32_t)row0;
+          const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
+  #pragma unroll
+          for (int s2 = 0; s2 < kKc / kKStep; ++s2) {
+            const uint64_t ad = sdesc(a_start + 256u * s2, 128, 128, 0, 0);
+            const uint64_t bd = sdesc(b_row + 32u * s2, 16, 1024, 2, 0);
+            mma_bf16(d_col, ad, bd, idesc, 1u);
+          }
+        }
+        if (lane == 0) mma_commit(cmt_bar + 8 * (uint32_t)(cc % kNB));
+        __syncwarp();
+      }
+      if (lane == 0) mma_commit(done_bar);
       __syncwarp();
     }
-    if (lane == 0) mma_commit(done_bar);
-    __syncwarp();
-  }
 
-  // Epilogue: every thread waits for the accumulator.
-  const bool done = mbar_wait(done_bar, 0);
-  ok = __syncthreads_and(ok && done);
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
-  } else {
-    tc_fence_after();
-    const int q = warp & 3, colh = warp >> 2;
-    const int m = 32 * q + lane;
-    for (int cb = 0; cb < 4; ++cb) {
-      const int col0 = 128 * colh + 32 * cb;
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
+    // Epilogue: every thread waits for the accumulator.
+    const bool done = mbar_wait(done_bar, iter & 1u);
+    ok = __syncthreads_and(ok && done);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
+      break;
+    }
+    {
+      tc_fence_after();
+      const int q = warp & 3, colh = warp >> 2;
+      const int m = 32 * q + lane;
+      for (int cb = 0; cb < 4; ++cb) {
+        const int col0 = 128 * colh + 32 * cb;
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t tau = T0 + 127 - m + 128 * (int64_t)(col0 + j);
-        if (tau < P.lag_min || tau > P.lag_max) continue;
-        const int val = __float2int_rn(__uint_as_float(v[j]));
-        const int64_t o = tau - P.lag_min;
-        if (P.c64) {
-          if (it.single)
-            static_cast<long long*>(P.c)[o] = val;
-          else
-            atomicAdd(reinterpret_cast<unsigned long long*>(P.c) + o, (unsigned long long)(long long)val);
-        } else {
-          if (it.single)
-            static_cast<int*>(P.c)[o] = val;
-          else
-            atomicAdd(static_cast<int*>(P.c) + o, val);
+        for (int j = 0; j < 32; ++j) {
+          const int64_t tau = T0 + 127 - m + 128 * (int64_t)(col0 + j);
+          if (tau < P.lag_min || tau > P.lag_max) continue;
+          const int val = __float2int_rn(__uint_as_float(v[j]));
+          const int64_t o = tau - P.lag_min;
+          if (P.c64) {
+            if (it.single)
+              static_cast<long long*>(P.c)[o] = val;
+            else
+              atomicAdd(reinterpret_cast<unsigned long long*>(P.c) + o, (unsigned long long)(long long)val);
+          } else {
+            if (it.single)
+              static_cast<int*>(P.c)[o] = val;
+            else
+              atomicAdd(static_cast<int*>(P.c) + o, val);
+          }
         }
       }
     }
+    tc_fence_before();
+    __syncthreads();
+    cc0 += nchunks;
   }
   tc_fence_before();
   __syncthreads();
@@ -481,12 +504,15 @@ cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_coun
 }
 
 cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
-                             uint32_t* d_status, cudaStream_t st) {
+                             int* d_counter, int grid, uint32_t* d_status, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
   if (e != cudaSuccess) return e;
-  k_xcorr_mma<<<nitems, kThreads, kSmemBytes, st>>>(d_pairs, d_items, d_status);
+  e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (grid > nitems) grid = nitems;
+  k_xcorr_mma<<<grid, kThreads, kSmemBytes, st>>>(d_pairs, d_items, nitems, d_counter, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

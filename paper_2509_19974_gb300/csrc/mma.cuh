@@ -30,5 +30,7 @@ struct MmaItem {
 int mma_smem_bytes();
 // Zeroes the outputs of pairs with zero_first set.
 cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st);
+// Persistent launch: `grid` CTAs (two per SM fit) take items from *d_counter
+// (zeroed here) in array order; sort items longest first.
 cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
-                             uint32_t* d_status, cudaStream_t st);
+                             int* d_counter, int grid, uint32_t* d_status, cudaStream_t st);

@@ -28,7 +28,8 @@ TDE_I32, TDE_I64, TDE_F32, TDE_I8 = 0, 1, 2, 3
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
            "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
            "tde_quantize_noalloc", "tde_xcorr_int", "tde_argmax", "tde_xcorr_fft32",
-           "tde_estimate", "tde_estimate_batch")
+           "tde_estimate", "tde_estimate_batch", "tde_batch_create", "tde_batch_run",
+           "tde_batch_destroy")
 
 
 class TdeError(RuntimeError):
@@ -70,6 +71,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_xcorr_fft32": ([p, p, p, i32, i64, i64, i32, i64, i64, p, p], st),
         "tde_estimate": ([p, p, i64, p, i64, i32, i64, i64, i32, p, p, p], st),
         "tde_estimate_batch": ([p, ctypes.POINTER(PairDesc), i32, i32, i32, p, p, p, p], st),
+        "tde_batch_create": ([p, ctypes.POINTER(PairDesc), i32, i32, i32, p, p, p,
+                              ctypes.POINTER(p)], st),
+        "tde_batch_run": ([p, p], st),
+        "tde_batch_destroy": ([p], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -305,3 +310,44 @@ def tde_estimate_batch(ctx: Context, xs, ys, bits, lag_mins=None, lag_maxs=None,
     ctx.check(ctx.lib.tde_estimate_batch(ctx.handle, descs, n, int(bits), _engine(engine), cptr,
                                          lags.data_ptr(), vals.data_ptr(), _stream(stream)))
     return lags, vals
+
+
+class Batch:
+    """A planned batch (tde_batch_create): the whole estimate step for fixed
+    descriptors captured in a CUDA graph; run() replays it.  Refill the input
+    tensors the descriptors point to between runs; results land in .lags,
+    .vals (and c_out if given)."""
+
+    def __init__(self, ctx: Context, xs, ys, bits, lag_mins=None, lag_maxs=None, engine="auto",
+                 c_out=None, descs=None):
+        self.ctx = ctx
+        self.descs = descs if descs is not None else make_descs(xs, ys, lag_mins, lag_maxs)
+        n = len(self.descs)
+        dev = torch.device("cuda", ctx.device)
+        self.lags = torch.empty(n, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(n, dtype=torch.int64, device=dev)
+        self.c_out = c_out
+        cptr = None
+        if c_out is not None:
+            _need(c_out, torch.int32, "c_out")
+            cptr = c_out.data_ptr()
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.tde_batch_create(ctx.handle, self.descs, n, int(bits), _engine(engine),
+                                           cptr, self.lags.data_ptr(), self.vals.data_ptr(),
+                                           ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        self.ctx.check(self.ctx.lib.tde_batch_run(self.handle, _stream(stream)))
+        return self.lags, self.vals
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.tde_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
