@@ -111,6 +111,12 @@ int tde_pick_engine(int bits, int64_t nx, int64_t ny, int64_t lag_count);
 tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits, int8_t* q_out,
                         tde_stream_t stream);
 
+/* tde_quantize for nsig signals of n samples each, stored one after another:
+ * x: nsig * n floats, q_out: nsig * n int8 (device).  Same levels and error
+ * reporting as tde_quantize on each signal; one launch per pass for all. */
+tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n, int nsig, int bits,
+                              int8_t* q_out, tde_stream_t stream);
+
 /* Allocation-free quantizer: the paper has no counterpart to this entry
  * point; it exists for callers that cannot allocate device memory, such as a
  * real-time audio callback that must not block in the allocator, a host that
@@ -217,6 +223,77 @@ tde_status tde_batch_create(tde_ctx* ctx, const tde_pair_desc* descs, int npairs
 tde_status tde_batch_run(tde_batch* batch, tde_stream_t stream);
 /* Synchronizes the device, frees the batch.  NULL is accepted. */
 tde_status tde_batch_destroy(tde_batch* batch);
+
+/* ------------------------------------------------------------------------
+ * Learned lag proposal.  Not part of the paper's method: a small 1-D CNN
+ * reads the quantized pair decimated 16x (block sums) and proposes the 8 most
+ * likely 257-lag windows; the exact integer correlation (Eq. 1) is then
+ * evaluated only inside them, and over the full range when the proposal's
+ * confidence is low.  The returned lag is always the tie-ruled maximiser of
+ * exact integer values (Algorithm 1, line 4) over the lags evaluated.
+ *
+ * Architecture (weights shared by x and y): d[i] = (sum of 16 levels) / 4;
+ * 4 x [conv1d kernel 9, padding 4, 32 channels, bias, ReLU, max-pool 2] ->
+ * features f[32][n/256]; score[l] = alpha * sum_c sum_i fx[c][i] fy[c][i + l]
+ * for bins l in [-(n/256 - 1), n/256 - 1]; bin l stands for the lags
+ * [256 l - 128, 256 l + 128].  Weights are BF16 in the forward pass, all
+ * accumulation FP32; training keeps FP32 master weights and AdamW moments and
+ * is deterministic.  Pair p's quantized signals are q[(2p) n ..] (x) and
+ * q[(2p+1) n ..] (y), int8, device. */
+typedef struct tde_model tde_model;
+
+/* Number of FP32 parameters of a model (host-only). */
+int64_t tde_model_param_count(void);
+
+/* A model for signals of n samples (n a multiple of 2048 in [16384, 2^24]),
+ * weights drawn from `seed` (He-uniform), Adam state zero.  Allocates device
+ * memory on ctx's device. */
+tde_status tde_model_create(tde_ctx* ctx, int64_t n, uint64_t seed, tde_model** out);
+tde_status tde_model_destroy(tde_model* model);
+
+/* Checkpointing: copy (after a device synchronize) the parameters, the two
+ * AdamW moments, the last gradient and the step count to host arrays of
+ * tde_model_param_count() floats each; any pointer may be NULL. */
+tde_status tde_model_get(const tde_model* model, float* params, float* adam_m, float* adam_v,
+                         float* grad, int64_t* step);
+/* Restore parameters (required), moments (NULL: zero) and step. */
+tde_status tde_model_set(tde_model* model, const float* params, const float* adam_m,
+                         const float* adam_v, int64_t step);
+
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay on conv
+ * weights) of softmax cross-entropy against the bin holding each pair's label
+ * lag.  labels: npairs int64 (device); loss_out: npairs floats (device), the
+ * per-pair loss before the update. */
+tde_status tde_train_step(tde_ctx* ctx, tde_model* model, const int8_t* q, int npairs,
+                          const int64_t* labels, float lr, float weight_decay, float* loss_out,
+                          tde_stream_t stream);
+
+/* Proposal only: centres[8 p + r] (device int32, samples, = 256 l) of pair
+ * p's r-th best bin and margin[p] (device float) = softmax mass of its top 8
+ * bins. */
+tde_status tde_propose(tde_ctx* ctx, const tde_model* model, const int8_t* q, int npairs,
+                       int32_t* centres, float* margin, tde_stream_t stream);
+
+/* Algorithm 1, lines 1-4 with the proposal, for npairs pairs of n samples
+ * (x, y: npairs * n floats each, device, pair after pair; all lags).  Pairs
+ * whose margin is below theta (theta > 1: all pairs) are re-estimated with the
+ * full correlation (tde_estimate_batch, AUTO engine) and flagged in
+ * fallback_out (device int32 per pair, may be NULL).  bits 1 or 2.  The call
+ * synchronizes `stream` once to read the margins. */
+tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* model, const float* x,
+                                const float* y, int npairs, int bits, float theta,
+                                int64_t* lag_out, int64_t* val_out, int32_t* fallback_out,
+                                tde_stream_t stream);
+
+/* Seeded synthetic pairs on the device (a workload generator, not part of
+ * the estimator): pair first + i gets shift d ~ U[-dmax, dmax], AR(1)
+ * coefficient ~ U[ar_lo, ar_hi], SNR ~ U[snr_lo, snr_hi] dB; x = s[dmax ..],
+ * y = s[dmax - d ..] plus independent Gaussian noise, so x[n] = y[n + d]
+ * before noise.  x_out, y_out: npairs * n floats, shift_out: npairs int64
+ * (device). */
+tde_status tde_synth_pairs(tde_ctx* ctx, uint64_t seed, int64_t first, int npairs, int64_t n,
+                           int64_t dmax, float ar_lo, float ar_hi, float snr_lo, float snr_hi,
+                           float* x_out, float* y_out, int64_t* shift_out, tde_stream_t stream);
 
 #ifdef __cplusplus
 }

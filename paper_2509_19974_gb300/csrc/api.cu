@@ -13,6 +13,7 @@
 #include "mma.cuh"
 #include "fftcmp.cuh"
 #include "ntt.cuh"
+#include "cnn.cuh"
 
 struct tde_ctx {
   int device = 0;
@@ -766,6 +767,32 @@ extern "C" tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int 
   return TDE_OK;
 }
 
+extern "C" tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n, int nsig,
+                                         int bits, int8_t* q_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!x || !q_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (n <= 0 || nsig <= 0) return set_err(ctx, TDE_ERR_INVALID, "n and nsig must be positive");
+  if (n > INT32_MAX) return set_err(ctx, TDE_ERR_UNSUPPORTED, "n above 2^31-1 is not supported");
+  if (!valid_bits(bits)) return set_err(ctx, TDE_ERR_INVALID, "bits must be 1, 2 or 4");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  QuantStage Q;
+  Q.plan(L, nsig, bits, n);
+  Bases B;
+  tde_status s = realize(ctx, L, &B);
+  if (s != TDE_OK) return s;
+  std::vector<const float*> xs(nsig);
+  std::vector<int8_t*> qs(nsig);
+  std::vector<int64_t> ns(nsig, n);
+  for (int i = 0; i < nsig; ++i) xs[i] = x + (int64_t)i * n, qs[i] = q_out + (int64_t)i * n;
+  Q.fill(B, xs.data(), qs.data(), ns.data());
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  const cudaError_t e = Q.launch(B, ctx->d_status, st);
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "quantize launch");
+}
+
 extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, const int8_t* qy,
                                     int64_t ny, int bits, int64_t lag_min, int64_t lag_max,
                                     int engine, void* c_out, int out_dtype, tde_stream_t stream) {
@@ -1060,5 +1087,398 @@ extern "C" tde_status tde_xcorr_fft32(tde_ctx* ctx, const void* x, const void* y
                 B.dw<float>(o_rx), B.dw<float>(o_ry), B.dw<float2>(o_sx), B.dw<float2>(o_sy),
                 st) != 0)
     return set_err(ctx, TDE_ERR_CUDA, "FFT comparator failed");
+  return TDE_OK;
+}
+
+// ====================================================== learned lag proposal
+
+cudaError_t launch_synth_pairs(uint64_t seed, int64_t first, int npairs, int64_t n, int64_t dmax,
+                               float a_lo, float a_hi, float snr_lo, float snr_hi, float* x,
+                               float* y, int64_t* shift, cudaStream_t st);
+
+extern "C" tde_status tde_synth_pairs(tde_ctx* ctx, uint64_t seed, int64_t first, int npairs,
+                                      int64_t n, int64_t dmax, float ar_lo, float ar_hi,
+                                      float snr_lo, float snr_hi, float* x_out, float* y_out,
+                                      int64_t* shift_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!x_out || !y_out || !shift_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (npairs <= 0 || n <= 0 || dmax < 0 || first < 0)
+    return set_err(ctx, TDE_ERR_INVALID, "sizes must be positive (dmax, first >= 0)");
+  if (!(ar_lo >= 0.f && ar_hi < 1.f && ar_lo <= ar_hi) || !(snr_lo <= snr_hi))
+    return set_err(ctx, TDE_ERR_INVALID, "need 0 <= ar_lo <= ar_hi < 1 and snr_lo <= snr_hi");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  const cudaError_t e =
+      launch_synth_pairs(seed, first, npairs, n, dmax, ar_lo, ar_hi, snr_lo, snr_hi, x_out, y_out,
+                         shift_out, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "synth launch");
+}
+
+struct tde_model {
+  tde_ctx* ctx = nullptr;
+  int64_t n = 0;
+  float* params = nullptr;  // FP32 master
+  uint16_t* wbf = nullptr;  // BF16 copy used by the forward pass
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  int64_t step = 0;
+};
+
+namespace {
+
+uint64_t host_splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+bool model_len_ok(int64_t n) { return n >= 16384 && n % 2048 == 0 && n <= ((int64_t)1 << 24); }
+
+// Work memory of the CNN for npairs pairs (2 npairs signals): decimated input,
+// per-layer outputs (and, for training, pre-pool activations and gradients).
+struct CnnPlan {
+  int P = 0, Ld = 0, Lf = 0;
+  size_t o_d = 0, o_out[kCnnLayers] = {}, o_pre[kCnnLayers] = {}, o_scores = 0;
+  size_t o_dscores = 0, o_dalpha = 0, o_dz = 0, o_dA = 0, o_dB = 0, o_partial = 0, o_loss = 0;
+  void plan(Layout& L, int npairs, int64_t n, bool train) {
+    P = npairs;
+    Ld = (int)(n / kCnnDec);
+    Lf = Ld / 16;
+    const size_t S = 2 * (size_t)P;
+    o_d = L.w<float>(S * Ld);
+    for (int l = 0; l < kCnnLayers; ++l) {
+      const size_t len = (size_t)Ld >> l;  // input length of layer l
+      o_out[l] = L.w<float>(S * kCnnC * (len / 2));
+      if (train) o_pre[l] = L.w<float>(S * kCnnC * len);
+    }
+    o_scores = L.w<float>((size_t)P * (2 * Lf - 1));
+    if (train) {
+      o_dscores = L.w<float>((size_t)P * (2 * Lf - 1));
+      o_dalpha = L.w<float>((size_t)P);
+      o_loss = L.w<float>((size_t)P);
+      o_dz = L.w<float>(S * kCnnC * Ld);
+      o_dA = L.w<float>(S * kCnnC * (Ld / 2));
+      o_dB = L.w<float>(S * kCnnC * (Ld / 2));
+      o_partial = L.w<float>(S * (kCnnC * kCnnC * kCnnK + kCnnC));
+    }
+  }
+  float* layer_in(const Bases& B, int l) const {
+    return l == 0 ? B.dw<float>(o_d) : B.dw<float>(o_out[l - 1]);
+  }
+  cudaError_t forward(const Bases& B, const tde_model* m, const int8_t* q, int64_t n, bool train,
+                      cudaStream_t st) const {
+    cudaError_t e = launch_cnn_decimate(q, n, 2 * P, B.dw<float>(o_d), st);
+    for (int l = 0; l < kCnnLayers && e == cudaSuccess; ++l) {
+      CnnLayerIO io{layer_in(B, l), train ? B.dw<float>(o_pre[l]) : nullptr, B.dw<float>(o_out[l]),
+                    Ld >> l};
+      e = launch_cnn_layer(io, l, 2 * P, m->wbf, m->params, st);
+    }
+    if (e == cudaSuccess)
+      e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
+                            B.dw<float>(o_scores), st);
+    return e;
+  }
+};
+
+tde_status check_model(tde_ctx* ctx, const tde_model* m) {
+  if (!m || !m->params) return set_err(ctx, TDE_ERR_INVALID, "null model");
+  if (m->ctx && m->ctx->device != ctx->device)
+    return set_err(ctx, TDE_ERR_INVALID, "model lives on another device");
+  return TDE_OK;
+}
+
+// Window jobs of the proposal: [c - 128, c + 128] clipped to the overlap.
+__global__ void k_make_windows(const int32_t* __restrict__ centres, int npairs, int64_t n,
+                               const uint32_t* __restrict__ planes, int64_t words,
+                               int32_t* __restrict__ cbuf, WinJob* __restrict__ jobs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npairs * kCnnTopK) return;
+  const int p = i / kCnnTopK;
+  const int64_t c = centres[i];
+  int64_t lo = c - kCnnBin / 2, hi = c + kCnnBin / 2;
+  if (lo < -(n - 1)) lo = -(n - 1);
+  if (hi > n - 1) hi = n - 1;
+  WinJob J;
+  J.px = planes + (int64_t)(2 * p) * 2 * words;
+  J.py = planes + (int64_t)(2 * p + 1) * 2 * words;
+  J.wx = J.wy = words;
+  J.lag_lo = lo;
+  J.lag_hi = hi;
+  J.c = cbuf + (int64_t)i * 288;
+  jobs[i] = J;
+}
+
+__global__ void k_fallback_scatter(const int32_t* __restrict__ idx, int nfb,
+                                   const int64_t* __restrict__ lag_fb,
+                                   const int64_t* __restrict__ val_fb, int64_t* __restrict__ lag,
+                                   int64_t* __restrict__ val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfb) return;
+  lag[idx[i]] = lag_fb[i];
+  val[idx[i]] = val_fb[i];
+}
+
+}  // namespace
+
+extern "C" tde_status tde_model_create(tde_ctx* ctx, int64_t n, uint64_t seed, tde_model** out) {
+  if (!ctx || !out) return TDE_ERR_INVALID;
+  *out = nullptr;
+  if (!model_len_ok(n))
+    return set_err(ctx, TDE_ERR_UNSUPPORTED,
+                   "proposal model needs n a multiple of 2048 in [16384, 2^24] (got %lld)",
+                   (long long)n);
+  DeviceGuard g(ctx->device);
+  tde_model* m = new tde_model();
+  m->ctx = ctx;
+  m->n = n;
+  // He-uniform conv weights from a seeded splitmix64 stream; zero biases;
+  // alpha scaled to the feature length.
+  std::vector<float> h(kCnnParams, 0.f);
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 12345;
+  for (int l = 0; l < kCnnLayers; ++l) {
+    const int fan_in = cnn_cin(l) * kCnnK;
+    const float bound = sqrtf(6.0f / (float)fan_in);
+    for (int i = cnn_woff(l); i < cnn_boff(l); ++i) {
+      const double u = (double)(host_splitmix(st) >> 11) / 9007199254740992.0;
+      h[i] = (float)((2.0 * u - 1.0) * bound);
+    }
+  }
+  h[kCnnAlpha] = 1.0f / (float)(kCnnC * (n / kCnnDec / 16));
+  const size_t bytes = sizeof(float) * kCnnParams;
+  if (cudaMalloc(&m->params, bytes) != cudaSuccess || cudaMalloc(&m->m, bytes) != cudaSuccess ||
+      cudaMalloc(&m->v, bytes) != cudaSuccess || cudaMalloc(&m->grad, bytes) != cudaSuccess ||
+      cudaMalloc(&m->wbf, sizeof(uint16_t) * kCnnParams) != cudaSuccess ||
+      cudaMemcpy(m->params, h.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(m->m, 0, bytes) != cudaSuccess || cudaMemset(m->v, 0, bytes) != cudaSuccess ||
+      cudaMemset(m->grad, 0, bytes) != cudaSuccess ||
+      launch_cnn_to_bf16(m->params, m->wbf, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    tde_model_destroy(m);
+    return set_err(ctx, TDE_ERR_CUDA, "model allocation failed");
+  }
+  *out = m;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_model_destroy(tde_model* m) {
+  if (!m) return TDE_OK;
+  {
+    DeviceGuard g(m->ctx ? m->ctx->device : 0);
+    cudaDeviceSynchronize();
+    cudaFree(m->params), cudaFree(m->wbf), cudaFree(m->m), cudaFree(m->v), cudaFree(m->grad);
+  }
+  delete m;
+  return TDE_OK;
+}
+
+extern "C" int64_t tde_model_param_count(void) { return kCnnParams; }
+
+extern "C" tde_status tde_model_get(const tde_model* m, float* params, float* adam_m, float* adam_v,
+                                    float* grad, int64_t* step) {
+  if (!m) return TDE_ERR_INVALID;
+  DeviceGuard g(m->ctx->device);
+  const size_t bytes = sizeof(float) * kCnnParams;
+  if (cudaDeviceSynchronize() != cudaSuccess) return TDE_ERR_CUDA;
+  if ((params && cudaMemcpy(params, m->params, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (adam_m && cudaMemcpy(adam_m, m->m, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (adam_v && cudaMemcpy(adam_v, m->v, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (grad && cudaMemcpy(grad, m->grad, bytes, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return TDE_ERR_CUDA;
+  if (step) *step = m->step;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_model_set(tde_model* m, const float* params, const float* adam_m,
+                                    const float* adam_v, int64_t step) {
+  if (!m || !params) return TDE_ERR_INVALID;
+  DeviceGuard g(m->ctx->device);
+  const size_t bytes = sizeof(float) * kCnnParams;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(m->params, params, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (adam_m && cudaMemcpy(m->m, adam_m, bytes, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (adam_v && cudaMemcpy(m->v, adam_v, bytes, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      launch_cnn_to_bf16(m->params, m->wbf, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return TDE_ERR_CUDA;
+  if (!adam_m) cudaMemset(m->m, 0, bytes);
+  if (!adam_v) cudaMemset(m->v, 0, bytes);
+  m->step = step;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_train_step(tde_ctx* ctx, tde_model* m, const int8_t* q, int npairs,
+                                     const int64_t* labels, float lr, float weight_decay,
+                                     float* loss_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  tde_status s = check_model(ctx, m);
+  if (s != TDE_OK) return s;
+  if (!q || !labels || !loss_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  CnnPlan C;
+  C.plan(L, npairs, m->n, true);
+  Bases B;
+  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
+  const int S = 2 * npairs, Ld = C.Ld, Lf = C.Lf;
+  cudaError_t e = C.forward(B, m, q, m->n, true, st);
+  if (e == cudaSuccess)
+    e = launch_cnn_softmax_ce(B.dw<float>(C.o_scores), labels, npairs, Lf, loss_out,
+                              B.dw<float>(C.o_dscores), st);
+  // d features -> dA (gradient w.r.t. the last layer's pooled output)
+  if (e == cudaSuccess)
+    e = launch_cnn_scores_bwd(B.dw<float>(C.o_out[kCnnLayers - 1]), B.dw<float>(C.o_dscores),
+                              npairs, Lf, m->params, B.dw<float>(C.o_dA), B.dw<float>(C.o_dalpha),
+                              st);
+  float* dout = B.dw<float>(C.o_dA);
+  float* dnext = B.dw<float>(C.o_dB);
+  for (int l = kCnnLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+    const int len = Ld >> l;
+    float* dz = B.dw<float>(C.o_dz);
+    e = launch_cnn_pool_relu_bwd(B.dw<float>(C.o_pre[l]), dout, S, len, dz, st);
+    if (e == cudaSuccess)
+      e = launch_cnn_wgrad(dz, C.layer_in(B, l), S, len, l, B.dw<float>(C.o_partial), st);
+    if (e == cudaSuccess)
+      e = launch_cnn_reduce(B.dw<float>(C.o_partial), S,
+                            kCnnC * cnn_cin(l) * kCnnK + kCnnC, m->grad + cnn_woff(l), st);
+    if (e == cudaSuccess && l > 0) {
+      e = launch_cnn_dgrad(dz, S, len, l, m->wbf, dnext, st);
+      std::swap(dout, dnext);
+    }
+  }
+  if (e == cudaSuccess)
+    e = launch_cnn_reduce(B.dw<float>(C.o_dalpha), npairs, 1, m->grad + kCnnAlpha, st);
+  if (e == cudaSuccess) {
+    m->step += 1;
+    e = launch_cnn_adamw(m->params, m->grad, m->m, m->v, m->wbf, m->step, lr, 0.9f, 0.999f, 1e-8f,
+                         weight_decay, st);
+  }
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "train step");
+}
+
+extern "C" tde_status tde_propose(tde_ctx* ctx, const tde_model* m, const int8_t* q, int npairs,
+                                  int32_t* centres, float* margin, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  tde_status s = check_model(ctx, m);
+  if (s != TDE_OK) return s;
+  if (!q || !centres || !margin) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  CnnPlan C;
+  C.plan(L, npairs, m->n, false);
+  Bases B;
+  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
+  cudaError_t e = C.forward(B, m, q, m->n, false, st);
+  if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(C.o_scores), npairs, C.Lf, centres, margin, st);
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "propose");
+}
+
+extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, const float* x,
+                                           const float* y, int npairs, int bits, float theta,
+                                           int64_t* lag_out, int64_t* val_out,
+                                           int32_t* fallback_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  tde_status s = check_model(ctx, m);
+  if (s != TDE_OK) return s;
+  if (!x || !y || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
+  if (bits != 1 && bits != 2)
+    return set_err(ctx, TDE_ERR_UNSUPPORTED, "the learned path supports bits 1 and 2");
+  const int64_t n = m->n;
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int S = 2 * npairs;
+  const int64_t words = ceil_div64(n, 32);
+  Layout L;
+  QuantStage Q;
+  Q.plan(L, S, bits, n);
+  const size_t o_psig = L.d<PlaneSig>(S);
+  const size_t o_q = L.w<int8_t>((size_t)S * n);
+  const size_t o_planes = L.w<uint32_t>((size_t)S * 2 * words);
+  CnnPlan C;
+  C.plan(L, npairs, n, false);
+  const size_t o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
+  const size_t o_marg = L.w<float>((size_t)npairs);
+  const size_t o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
+  const size_t o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * 288);
+  Bases B;
+  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
+  std::vector<const float*> xs(S);
+  std::vector<int8_t*> qs(S);
+  std::vector<int64_t> ns(S, n);
+  int8_t* qbuf = B.dw<int8_t>(o_q);
+  uint32_t* planes = B.dw<uint32_t>(o_planes);
+  PlaneSig* ps = B.hd<PlaneSig>(o_psig);
+  for (int p = 0; p < npairs; ++p)
+    for (int k = 0; k < 2; ++k) {
+      const int i = 2 * p + k;
+      xs[i] = (k ? y : x) + (int64_t)p * n;
+      qs[i] = qbuf + (int64_t)i * n;
+      ps[i] = PlaneSig{qs[i], planes + (int64_t)i * 2 * words, n, words};
+    }
+  Q.fill(B, xs.data(), qs.data(), ns.data());
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  int32_t* cent = B.dw<int32_t>(o_cent);
+  float* marg = B.dw<float>(o_marg);
+  WinJob* jobs = B.dw<WinJob>(o_jobs);
+  cudaError_t e = Q.launch(B, ctx->d_status, st);
+  if (e == cudaSuccess) e = launch_pack_planes(B.dd<PlaneSig>(o_psig), S, words, bits, ctx->d_status, st);
+  if (e == cudaSuccess) e = C.forward(B, m, qbuf, n, false, st);
+  if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(C.o_scores), npairs, C.Lf, cent, marg, st);
+  if (e == cudaSuccess) {
+    k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, npairs, n, planes, words,
+                                                                     B.dw<int32_t>(o_cwin), jobs);
+    TDE_COUNT_LAUNCH(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    EngineTimer t(ctx, st);
+    e = launch_xcorr_popc_windows(jobs, npairs * kCnnTopK, st);
+  }
+  if (e == cudaSuccess) e = launch_window_argmax(jobs, npairs, lag_out, val_out, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "learned estimate");
+  // Fallback: pairs whose proposal is not confident get the full correlation.
+  std::vector<float> hm(npairs);
+  TDE_CK(cudaMemcpyAsync(hm.data(), marg, sizeof(float) * npairs, cudaMemcpyDeviceToHost, st));
+  TDE_CK(cudaStreamSynchronize(st));
+  std::vector<int32_t> fb, flag(npairs, 0);
+  for (int p = 0; p < npairs; ++p)
+    if (!(hm[p] >= theta)) {
+      fb.push_back(p);
+      flag[p] = 1;
+    }
+  if (fallback_out)
+    TDE_CK(cudaMemcpyAsync(fallback_out, flag.data(), sizeof(int32_t) * npairs,
+                           cudaMemcpyHostToDevice, st));
+  if (!fb.empty()) {
+    const int nfb = (int)fb.size();
+    std::vector<tde_pair_desc> d(nfb);
+    for (int i = 0; i < nfb; ++i)
+      d[i] = tde_pair_desc{x + (int64_t)fb[i] * n, y + (int64_t)fb[i] * n, n, n, -(n - 1), n - 1};
+    // The fallback runs in its own memory (the context workspace is reused).
+    int64_t* tmp = nullptr;
+    int32_t* idx = nullptr;
+    TDE_CK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(int64_t) * 2 * nfb, st));
+    TDE_CK(cudaMallocAsync(reinterpret_cast<void**>(&idx), sizeof(int32_t) * nfb, st));
+    TDE_CK(cudaMemcpyAsync(idx, fb.data(), sizeof(int32_t) * nfb, cudaMemcpyHostToDevice, st));
+    TDE_CK(cudaStreamSynchronize(st));  // fb, flag and d leave scope only after the copies
+    s = tde_estimate_batch(ctx, d.data(), nfb, bits, TDE_ENGINE_AUTO, nullptr, tmp, tmp + nfb,
+                           stream);
+    if (s != TDE_OK) return s;
+    k_fallback_scatter<<<(nfb + 255) / 256, 256, 0, st>>>(idx, nfb, tmp, tmp + nfb, lag_out,
+                                                          val_out);
+    TDE_COUNT_LAUNCH(1);
+    TDE_CK(cudaFreeAsync(tmp, st));
+    TDE_CK(cudaFreeAsync(idx, st));
+  }
+  TDE_CK(cudaStreamSynchronize(st));  // host vectors above must outlive their copies
   return TDE_OK;
 }

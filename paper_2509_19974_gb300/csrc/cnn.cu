@@ -1,0 +1,614 @@
+// cnn.cu -- learned lag proposal kernels (inference and training) and the
+// windowed exact correlation that checks its proposals.
+//
+// The proposal only decides WHERE the exact integer correlation of
+// Algorithm 1, line 3 (arXiv 2509.19974) is evaluated: the lag returned is
+// always the tie-ruled maximiser of exact integer values, either inside the
+// proposed windows or, when the proposal's confidence (softmax mass of its top
+// 8 bins) is below a threshold, over the full lag range.
+//
+// All CNN arithmetic is FP32 with BF16-rounded weights; the backward pass is
+// deterministic (per-signal partial sums reduced in a fixed order, no float
+// atomics).  Shapes: conv layers tile 128 output positions x 32 channels per
+// CTA; a warp's 32 lanes are the 32 output channels (forward) or input
+// channels (data gradient), so shared-memory weight reads are contiguous and
+// activation reads are broadcasts.
+#include <cstring>
+
+#include "cnn.cuh"
+
+namespace {
+
+constexpr int kT = 128;  // positions per conv CTA
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float bf16_to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// FP32 -> BF16, round to nearest even (NaN-free inputs).
+__host__ __device__ __forceinline__ uint16_t f_to_bf16(float f) {
+#ifdef __CUDA_ARCH__
+  const uint32_t u = __float_as_uint(f);
+#else
+  uint32_t u;
+  memcpy(&u, &f, 4);
+#endif
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+__global__ void k_decimate(const int8_t* __restrict__ q, int64_t n, int nsig, float* __restrict__ d) {
+  const int64_t ld = n / kCnnDec;
+  const int64_t total = (int64_t)nsig * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / ld, j = i % ld;
+    const int8_t* src = q + s * n + j * kCnnDec;
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < kCnnDec; ++k) acc += src[k];
+    d[i] = 0.25f * (float)acc;
+  }
+}
+
+// conv (kernel 9, pad 4) + bias + ReLU (+ store) + max-pool 2.
+template <int CIN>
+__global__ void __launch_bounds__(kThreads) k_conv_fwd(const float* __restrict__ in,
+                                                       float* __restrict__ pre,
+                                                       float* __restrict__ out, int L,
+                                                       const uint16_t* __restrict__ wbf,
+                                                       const float* __restrict__ bias) {
+  extern __shared__ float csm[];
+  float (*in_s)[kT + 8] = reinterpret_cast<float (*)[kT + 8]>(csm);                  // [CIN][kT+8]
+  float (*w_s)[kCnnC] = reinterpret_cast<float (*)[kCnnC]>(csm + CIN * (kT + 8));  // [ci*9+k][co]
+  const int s = blockIdx.y, p0 = blockIdx.x * kT;
+  const float* src = in + (int64_t)s * CIN * L;
+  for (int idx = threadIdx.x; idx < CIN * (kT + 8); idx += kThreads) {
+    const int ci = idx / (kT + 8), j = idx % (kT + 8);
+    const int pos = p0 - 4 + j;
+    in_s[ci][j] = (pos >= 0 && pos < L) ? src[(int64_t)ci * L + pos] : 0.f;
+  }
+  for (int idx = threadIdx.x; idx < kCnnC * CIN * kCnnK; idx += kThreads) {
+    const int co = idx / (CIN * kCnnK), r = idx % (CIN * kCnnK);
+    w_s[r][co] = bf16_to_f(wbf[idx]);
+  }
+  __syncthreads();
+  const int co = threadIdx.x & 31, pg = threadIdx.x >> 5;
+  float acc[16];
+  const float b = bias[co];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = b;
+  for (int ci = 0; ci < CIN; ++ci) {
+    float xr[24];
+#pragma unroll
+    for (int j = 0; j < 24; ++j) xr[j] = in_s[ci][pg * 16 + j];
+#pragma unroll
+    for (int k = 0; k < kCnnK; ++k) {
+      const float w = w_s[ci * kCnnK + k][co];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = fmaf(w, xr[j + k], acc[j]);
+    }
+  }
+  const int pbase = p0 + pg * 16;
+  float* dst_pre = pre ? pre + ((int64_t)s * kCnnC + co) * L + pbase : nullptr;
+  float* dst = out + ((int64_t)s * kCnnC + co) * (L / 2) + pbase / 2;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = fmaxf(acc[j], 0.f);
+  if (dst_pre) {
+#pragma unroll
+    for (int j = 0; j < 16; j += 4)
+      *reinterpret_cast<float4*>(dst_pre + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 16; j += 8)
+    *reinterpret_cast<float4*>(dst + j / 2) =
+        make_float4(fmaxf(acc[j], acc[j + 1]), fmaxf(acc[j + 2], acc[j + 3]),
+                    fmaxf(acc[j + 4], acc[j + 5]), fmaxf(acc[j + 6], acc[j + 7]));
+}
+
+// scores of one pair; fy zero-padded by Lf on both sides in shared memory.
+__global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ feat, int Lf,
+                                                     const float* __restrict__ params,
+                                                     float* __restrict__ scores) {
+  extern __shared__ float sm[];
+  float* fx = sm;                   // [32][Lf]
+  float* fy = sm + kCnnC * Lf;      // [32][3 Lf]
+  const int p = blockIdx.x;
+  const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
+  const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
+  for (int i = threadIdx.x; i < kCnnC * Lf; i += kThreads) fx[i] = gx[i];
+  for (int i = threadIdx.x; i < kCnnC * 3 * Lf; i += kThreads) {
+    const int c = i / (3 * Lf), j = i % (3 * Lf) - Lf;
+    fy[i] = (j >= 0 && j < Lf) ? gy[c * Lf + j] : 0.f;
+  }
+  __syncthreads();
+  const float alpha = params[kCnnAlpha];
+  const int nb = 2 * Lf - 1;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    const int l = b - (Lf - 1);
+    float acc = 0.f;
+    for (int c = 0; c < kCnnC; ++c) {
+      const float* a = fx + c * Lf;
+      const float* y = fy + c * 3 * Lf + Lf + l;
+      for (int i = 0; i < Lf; ++i) acc = fmaf(a[i], y[i], acc);
+    }
+    scores[(int64_t)p * nb + b] = alpha * acc;
+  }
+}
+
+// lag rank of bin l: smaller |l| first, then negative first (the estimator's
+// tie order), used to break exact score ties deterministically.
+__device__ __forceinline__ bool better(float s, int l, float bs, int bl) {
+  if (s != bs) return s > bs;
+  const int a = l < 0 ? -l : l, ab = bl < 0 ? -bl : bl;
+  return a != ab ? a < ab : l < bl;
+}
+
+// One warp per pair: softmax, top-8 bins, margin.
+__global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
+                       int32_t* __restrict__ centres, float* __restrict__ margin) {
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= npairs) return;
+  const int nb = 2 * Lf - 1;
+  const float* sc = scores + (int64_t)p * nb;
+  float mx = -INFINITY;
+  for (int b = lane; b < nb; b += 32) mx = fmaxf(mx, sc[b]);
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float sum = 0.f;
+  for (int b = lane; b < nb; b += 32) sum += __expf(sc[b] - mx);
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  float top = 0.f;
+  int taken[kCnnTopK];
+  for (int r = 0; r < kCnnTopK; ++r) {
+    float bs = -INFINITY;
+    int bl = 1 << 30;
+    for (int b = lane; b < nb; b += 32) {
+      const int l = b - (Lf - 1);
+      bool used = false;
+      for (int t = 0; t < r; ++t) used |= taken[t] == l;
+      if (!used && (bl == (1 << 30) || better(sc[b], l, bs, bl))) {
+        bs = sc[b];
+        bl = l;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (ol != (1 << 30) && (bl == (1 << 30) || better(os, ol, bs, bl))) {
+        bs = os;
+        bl = ol;
+      }
+    }
+    taken[r] = bl;
+    top += __expf(bs - mx);
+    if (lane == 0) centres[(int64_t)p * kCnnTopK + r] = kCnnBin * bl;
+  }
+  if (lane == 0) margin[p] = top / sum;
+}
+
+// ---------------------------------------------------------------- training
+
+__global__ void k_softmax_ce(const float* __restrict__ scores, const int64_t* __restrict__ labels,
+                             int npairs, int Lf, float* __restrict__ loss,
+                             float* __restrict__ dscores) {
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= npairs) return;
+  const int nb = 2 * Lf - 1;
+  const float* sc = scores + (int64_t)p * nb;
+  // label bin: the window [256 l - 128, 256 l + 128] holding the lag
+  int64_t l = labels[p] + kCnnBin / 2;
+  l = l >= 0 ? l / kCnnBin : -((-l + kCnnBin - 1) / kCnnBin);
+  if (l < -(Lf - 1)) l = -(Lf - 1);
+  if (l > Lf - 1) l = Lf - 1;
+  const int t = (int)l + Lf - 1;
+  float mx = -INFINITY;
+  for (int b = lane; b < nb; b += 32) mx = fmaxf(mx, sc[b]);
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float sum = 0.f;
+  for (int b = lane; b < nb; b += 32) sum += expf(sc[b] - mx);
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const float inv = 1.f / sum, scale = 1.f / (float)npairs;
+  for (int b = lane; b < nb; b += 32)
+    dscores[(int64_t)p * nb + b] = (expf(sc[b] - mx) * inv - (b == t ? 1.f : 0.f)) * scale;
+  if (lane == 0) loss[p] = logf(sum) + mx - sc[t];
+}
+
+// d features of one pair; d alpha partial = sum_b dS[b] * score[b] / alpha.
+__global__ void __launch_bounds__(kThreads) k_scores_bwd(const float* __restrict__ feat,
+                                                         const float* __restrict__ dscores,
+                                                         int Lf, const float* __restrict__ params,
+                                                         float* __restrict__ dfeat,
+                                                         float* __restrict__ dalpha_pp) {
+  extern __shared__ float sm[];
+  const int nb = 2 * Lf - 1;
+  float* fx = sm;                  // [32][3 Lf] padded
+  float* fy = sm + kCnnC * 3 * Lf; // [32][3 Lf] padded
+  float* ds = fy + kCnnC * 3 * Lf; // [nb]
+  __shared__ float red[kThreads / 32];
+  const int p = blockIdx.x;
+  const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
+  const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
+  for (int i = threadIdx.x; i < kCnnC * 3 * Lf; i += kThreads) {
+    const int c = i / (3 * Lf), j = i % (3 * Lf) - Lf;
+    fx[i] = (j >= 0 && j < Lf) ? gx[c * Lf + j] : 0.f;
+    fy[i] = (j >= 0 && j < Lf) ? gy[c * Lf + j] : 0.f;
+  }
+  for (int b = threadIdx.x; b < nb; b += kThreads) ds[b] = dscores[(int64_t)p * nb + b];
+  __syncthreads();
+  const float alpha = params[kCnnAlpha];
+  float* dx = dfeat + (int64_t)(2 * p) * kCnnC * Lf;
+  float* dy = dfeat + (int64_t)(2 * p + 1) * kCnnC * Lf;
+  // dfx[c][i] = alpha sum_l dS[l] fy[c][i + l];  dfy[c][j] = alpha sum_l dS[l] fx[c][j - l]
+  float da = 0.f;
+  for (int e = threadIdx.x; e < kCnnC * Lf; e += kThreads) {
+    const int c = e / Lf, i = e % Lf;
+    const float* yrow = fy + c * 3 * Lf + Lf + i - (Lf - 1);   // index by b: fy[i + l]
+    const float* xrow = fx + c * 3 * Lf + Lf + i + (Lf - 1);   // fx[i - l] = xrow[-b]
+    float ax = 0.f, ay = 0.f;
+    for (int b = 0; b < nb; ++b) {
+      ax = fmaf(ds[b], yrow[b], ax);
+      ay = fmaf(ds[b], xrow[-b], ay);
+    }
+    dx[e] = alpha * ax;
+    dy[e] = alpha * ay;
+    // sum_b dS[b] raw[b] = sum_c sum_i fx[c][i] * (sum_b dS[b] fy[c][i + l_b])
+    da = fmaf(fx[c * 3 * Lf + Lf + i], ax, da);
+  }
+  for (int o = 16; o; o >>= 1) da += __shfl_xor_sync(0xffffffffu, da, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = da;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    dalpha_pp[p] = t;
+  }
+}
+
+__global__ void k_pool_relu_bwd(const float* __restrict__ pre, const float* __restrict__ dout,
+                                int64_t total_out, float* __restrict__ dz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_out;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float a0 = pre[2 * i], a1 = pre[2 * i + 1];
+    const float g = dout[i];
+    const bool second = a1 > a0;
+    const float gm = (second ? a1 : a0) > 0.f ? g : 0.f;
+    dz[2 * i] = second ? 0.f : gm;
+    dz[2 * i + 1] = second ? gm : 0.f;
+  }
+}
+
+// din[ci][p] = sum_co sum_k dz[co][p + 4 - k] W[co][ci][k]  (32 -> 32 layers)
+__global__ void __launch_bounds__(kThreads) k_conv_dgrad(const float* __restrict__ dz, int L,
+                                                         const uint16_t* __restrict__ wbf,
+                                                         float* __restrict__ din) {
+  extern __shared__ float csm[];
+  float (*dz_s)[kT + 8] = reinterpret_cast<float (*)[kT + 8]>(csm);                  // [co][kT+8]
+  float (*w_s)[kCnnC] = reinterpret_cast<float (*)[kCnnC]>(csm + kCnnC * (kT + 8));  // [co*9+k][ci]
+  const int s = blockIdx.y, p0 = blockIdx.x * kT;
+  const float* src = dz + (int64_t)s * kCnnC * L;
+  for (int idx = threadIdx.x; idx < kCnnC * (kT + 8); idx += kThreads) {
+    const int co = idx / (kT + 8), j = idx % (kT + 8);
+    const int pos = p0 - 4 + j;
+    dz_s[co][j] = (pos >= 0 && pos < L) ? src[(int64_t)co * L + pos] : 0.f;
+  }
+  for (int idx = threadIdx.x; idx < kCnnC * kCnnC * kCnnK; idx += kThreads) {
+    const int co = idx / (kCnnC * kCnnK), r = idx % (kCnnC * kCnnK);
+    const int ci = r / kCnnK, k = r % kCnnK;
+    w_s[co * kCnnK + k][ci] = bf16_to_f(wbf[idx]);
+  }
+  __syncthreads();
+  const int ci = threadIdx.x & 31, pg = threadIdx.x >> 5;
+  float acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+  for (int co = 0; co < kCnnC; ++co) {
+    float g[24];
+#pragma unroll
+    for (int j = 0; j < 24; ++j) g[j] = dz_s[co][pg * 16 + j];
+#pragma unroll
+    for (int k = 0; k < kCnnK; ++k) {
+      const float w = w_s[co * kCnnK + k][ci];
+      // dz[p + 4 - k] sits at dz_s[.][p - p0 + 8 - k]
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = fmaf(w, g[j + 8 - k], acc[j]);
+    }
+  }
+  float* dst = din + ((int64_t)s * kCnnC + ci) * L + p0 + pg * 16;
+#pragma unroll
+  for (int j = 0; j < 16; j += 4)
+    *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+}
+
+// Per-signal partials: dW[co][ci][k] = sum_p dz[co][p] in[ci][p + k - 4],
+// db[co] = sum_p dz[co][p].  One CTA per signal.
+template <int CIN>
+__global__ void __launch_bounds__(kThreads) k_conv_wgrad(const float* __restrict__ dz,
+                                                         const float* __restrict__ in, int L,
+                                                         float* __restrict__ partial) {
+  __shared__ float dz_s[kCnnC][kT];
+  __shared__ float in_s[CIN][kT + 8];
+  constexpr int kOut = kCnnC * CIN * kCnnK;
+  constexpr int kPer = (kOut + kThreads - 1) / kThreads;
+  const int s = blockIdx.x;
+  const float* gz = dz + (int64_t)s * kCnnC * L;
+  const float* gi = in + (int64_t)s * CIN * L;
+  float acc[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) acc[r] = 0.f;
+  float accb = 0.f;
+  for (int p0 = 0; p0 < L; p0 += kT) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kCnnC * kT; idx += kThreads)
+      dz_s[idx / kT][idx % kT] = gz[(int64_t)(idx / kT) * L + p0 + idx % kT];
+    for (int idx = threadIdx.x; idx < CIN * (kT + 8); idx += kThreads) {
+      const int ci = idx / (kT + 8), j = idx % (kT + 8);
+      const int pos = p0 - 4 + j;
+      in_s[ci][j] = (pos >= 0 && pos < L) ? gi[(int64_t)ci * L + pos] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int o = threadIdx.x + r * kThreads;
+      if (o < kOut) {
+        const int co = o / (CIN * kCnnK), ci = (o / kCnnK) % CIN, k = o % kCnnK;
+        float a = acc[r];
+        for (int p = 0; p < kT; ++p) a = fmaf(dz_s[co][p], in_s[ci][p + k], a);
+        acc[r] = a;
+      }
+    }
+    if (threadIdx.x < kCnnC)
+      for (int p = 0; p < kT; ++p) accb += dz_s[threadIdx.x][p];
+  }
+  float* dst = partial + (int64_t)s * (kOut + kCnnC);
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int o = threadIdx.x + r * kThreads;
+    if (o < kOut) dst[o] = acc[r];
+  }
+  if (threadIdx.x < kCnnC) dst[kOut + threadIdx.x] = accb;
+}
+
+__global__ void k_reduce(const float* __restrict__ partial, int nsig, int count,
+                         float* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float a = 0.f;
+  for (int s = 0; s < nsig; ++s) a += partial[(int64_t)s * count + i];
+  grad[i] = a;
+}
+
+__global__ void k_adamw(float* __restrict__ params, const float* __restrict__ grad,
+                        float* __restrict__ m, float* __restrict__ v, uint16_t* __restrict__ wbf,
+                        float c1, float c2, float lr, float beta1, float beta2, float eps,
+                        float wd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kCnnParams) return;
+  const float g = grad[i];
+  const float mi = beta1 * m[i] + (1.f - beta1) * g;
+  const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  // decoupled weight decay on conv weights only (not biases or alpha)
+  bool is_w = false;
+  for (int l = 0; l < kCnnLayers; ++l) is_w |= (i >= cnn_woff(l) && i < cnn_boff(l));
+  float p = params[i];
+  p -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + (is_w ? wd * p : 0.f));
+  params[i] = p;
+  wbf[i] = f_to_bf16(p);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ params, uint16_t* __restrict__ wbf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kCnnParams) wbf[i] = f_to_bf16(params[i]);
+}
+
+// ------------------------------------------------ windowed exact correlation
+
+constexpr int kWinA = 9;  // 32-lag groups per window CTA (288 lags >= 257)
+
+__global__ void __launch_bounds__(kThreads) k_xcorr_popc_win(const WinJob* __restrict__ jobs) {
+  __shared__ int red[kThreads / 32][kWinA][32];
+  const WinJob J = jobs[blockIdx.x];
+  const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
+  const int64_t a0 = J.lag_lo >= 0 ? J.lag_lo / 32 : -((-J.lag_lo + 31) / 32);
+  int acc[kWinA], acc2[kWinA];
+#pragma unroll
+  for (int i = 0; i < kWinA; ++i) acc[i] = acc2[i] = 0;
+  const int64_t per = (J.wx + 7) / 8;
+  const int64_t w_lo = warp * per, w_hi = w_lo + per < J.wx ? w_lo + per : J.wx;
+  for (int64_t w = w_lo; w < w_hi; ++w) {
+    const uint32_t sx = __ldg(J.px + w), zx = __ldg(J.px + J.wx + w);
+    uint32_t ys[kWinA + 1], yz[kWinA + 1];
+#pragma unroll
+    for (int i = 0; i <= kWinA; ++i) {
+      const int64_t yw = w + a0 + i;
+      const bool in = yw >= 0 && yw < J.wy;
+      ys[i] = in ? __ldg(J.py + yw) : 0u;
+      yz[i] = in ? __ldg(J.py + J.wy + yw) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kWinA; ++i) {
+      const uint32_t sy = __funnelshift_r(ys[i], ys[i + 1], r);
+      const uint32_t zy = __funnelshift_r(yz[i], yz[i + 1], r);
+      const uint32_t m = zx & zy;
+      acc[i] += __popc(m);
+      acc2[i] += __popc(m & (sx ^ sy));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kWinA; ++i) red[warp][i][r] = acc[i] - 2 * acc2[i];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kWinA * 32; e += kThreads) {
+    const int i = e / 32, rr = e % 32;
+    int t = 0;
+    for (int w8 = 0; w8 < kThreads / 32; ++w8) t += red[w8][i][rr];
+    const int64_t tau = 32 * (a0 + i) + rr;
+    if (tau >= J.lag_lo && tau <= J.lag_hi) J.c[tau - J.lag_lo] = t;
+  }
+}
+
+__device__ __forceinline__ unsigned long long pack_key(int32_t v, int64_t tau) {
+  const uint64_t a = (uint64_t)(tau < 0 ? -tau : tau);
+  const uint32_t rank = (uint32_t)(2 * a + (tau > 0 ? 1 : 0));
+  return ((unsigned long long)((uint32_t)v ^ 0x80000000u) << 32) | (0xFFFFFFFFu - rank);
+}
+
+__global__ void __launch_bounds__(kThreads) k_window_argmax(const WinJob* __restrict__ jobs,
+                                                            int64_t* __restrict__ lag,
+                                                            int64_t* __restrict__ val) {
+  __shared__ unsigned long long red[kThreads / 32];
+  const int p = blockIdx.x;
+  unsigned long long best = 0;
+  for (int w = 0; w < kCnnTopK; ++w) {
+    const WinJob J = jobs[(int64_t)p * kCnnTopK + w];
+    const int64_t cnt = J.lag_hi - J.lag_lo + 1;
+    for (int64_t i = threadIdx.x; i < cnt; i += kThreads) {
+      const unsigned long long k = pack_key(J.c[i], J.lag_lo + i);
+      best = k > best ? k : best;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+    best = t > best ? t : best;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) best = red[w] > best ? red[w] : best;
+    best = red[0] > best ? red[0] : best;
+    const uint64_t rank = 0xFFFFFFFFull - (best & 0xFFFFFFFFull);
+    const int64_t a = (int64_t)(rank >> 1);
+    lag[p] = (rank & 1) ? a : -a;
+    val[p] = (int64_t)(int32_t)((uint32_t)(best >> 32) ^ 0x80000000u);
+  }
+}
+
+unsigned grid1(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (unsigned)(g < 1 ? 1 : (g > 65535 ? 65535 : g));
+}
+
+}  // namespace
+
+cudaError_t launch_cnn_decimate(const int8_t* q, int64_t n, int nsig, float* d, cudaStream_t st) {
+  k_decimate<<<grid1((int64_t)nsig * n / kCnnDec), 256, 0, st>>>(q, n, nsig, d);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+constexpr int conv_smem(int cin) { return (cin * (kT + 8) + cin * kCnnK * kCnnC) * 4; }
+
+cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16_t* wbf,
+                             const float* params, cudaStream_t st) {
+  dim3 grid(io.L / kT, nsig);
+  if (l == 0) {
+    k_conv_fwd<1><<<grid, kThreads, conv_smem(1), st>>>(io.in, io.pre, io.out, io.L,
+                                                        wbf + cnn_woff(0), params + cnn_boff(0));
+  } else {
+    cudaFuncSetAttribute(k_conv_fwd<kCnnC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         conv_smem(kCnnC));
+    k_conv_fwd<kCnnC><<<grid, kThreads, conv_smem(kCnnC), st>>>(
+        io.in, io.pre, io.out, io.L, wbf + cnn_woff(l), params + cnn_boff(l));
+  }
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
+                              float* scores, cudaStream_t st) {
+  const int smem = (kCnnC * Lf + kCnnC * 3 * Lf) * 4;
+  cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_scores<<<npairs, kThreads, smem, st>>>(feat, Lf, params, scores);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_topk(const float* scores, int npairs, int Lf, int32_t* centres,
+                            float* margin, cudaStream_t st) {
+  k_topk<<<(npairs + 3) / 4, 128, 0, st>>>(scores, npairs, Lf, centres, margin);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_softmax_ce(const float* scores, const int64_t* labels, int npairs, int Lf,
+                                  float* loss, float* dscores, cudaStream_t st) {
+  k_softmax_ce<<<(npairs + 3) / 4, 128, 0, st>>>(scores, labels, npairs, Lf, loss, dscores);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_scores_bwd(const float* feat, const float* dscores, int npairs, int Lf,
+                                  const float* params, float* dfeat, float* dalpha_pp,
+                                  cudaStream_t st) {
+  const int smem = (2 * kCnnC * 3 * Lf + 2 * Lf) * 4;
+  cudaFuncSetAttribute(k_scores_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_scores_bwd<<<npairs, kThreads, smem, st>>>(feat, dscores, Lf, params, dfeat, dalpha_pp);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_pool_relu_bwd(const float* pre, const float* dout, int nsig, int L,
+                                     float* dz, cudaStream_t st) {
+  const int64_t total = (int64_t)nsig * kCnnC * (L / 2);
+  k_pool_relu_bwd<<<grid1(total), 256, 0, st>>>(pre, dout, total, dz);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_dgrad(const float* dz, int nsig, int L, int l, const uint16_t* wbf,
+                             float* din, cudaStream_t st) {
+  cudaFuncSetAttribute(k_conv_dgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       conv_smem(kCnnC));
+  k_conv_dgrad<<<dim3(L / kT, nsig), kThreads, conv_smem(kCnnC), st>>>(dz, L, wbf + cnn_woff(l),
+                                                                        din);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_wgrad(const float* dz, const float* in, int nsig, int L, int l,
+                             float* partial, cudaStream_t st) {
+  if (l == 0)
+    k_conv_wgrad<1><<<nsig, kThreads, 0, st>>>(dz, in, L, partial);
+  else
+    k_conv_wgrad<kCnnC><<<nsig, kThreads, 0, st>>>(dz, in, L, partial);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_reduce(const float* partial, int nsig, int count, float* grad,
+                              cudaStream_t st) {
+  k_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, nsig, count, grad);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_adamw(float* params, const float* grad, float* m, float* v, uint16_t* wbf,
+                             int64_t step, float lr, float beta1, float beta2, float eps,
+                             float wd, cudaStream_t st) {
+  const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+  k_adamw<<<(kCnnParams + 255) / 256, 256, 0, st>>>(params, grad, m, v, wbf, c1, c2, lr, beta1,
+                                                    beta2, eps, wd);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_to_bf16(const float* params, uint16_t* wbf, cudaStream_t st) {
+  k_to_bf16<<<(kCnnParams + 255) / 256, 256, 0, st>>>(params, wbf);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xcorr_popc_windows(const WinJob* d_jobs, int njobs, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  k_xcorr_popc_win<<<njobs, kThreads, 0, st>>>(d_jobs);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_argmax(const WinJob* d_jobs, int npairs, int64_t* lag, int64_t* val,
+                                 cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  k_window_argmax<<<npairs, kThreads, 0, st>>>(d_jobs, lag, val);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}

@@ -1,0 +1,86 @@
+// cnn.cuh -- the learned lag proposal: a small 1-D CNN over decimated
+// quantized signals whose feature correlation proposes lag windows for the
+// exact integer correlation (cnn.cu).
+#pragma once
+
+#include "common.cuh"
+
+// Architecture (shared by both signals of a pair):
+//   input  d[i] = (sum of 16 consecutive levels) / 4,  length Ld = n / 16
+//   4 x [conv1d kernel 9, padding 4, 32 output channels, + bias, ReLU,
+//        max-pool 2]   ->  features f[32][Lf],  Lf = Ld / 16 = n / 256
+//   score[l] = alpha * sum_c sum_i fx[c][i] fy[c][i + l],  l in [-(Lf-1), Lf-1]
+//   bin l covers lags tau in [256 l - 128, 256 l + 128] (width 257).
+constexpr int kCnnC = 32, kCnnK = 9, kCnnLayers = 4, kCnnDec = 16, kCnnBin = 256;
+constexpr int kCnnTopK = 8, kCnnWin = 257;
+
+// Parameter layout (FP32 master copy, BF16 copy for the forward pass):
+// per layer l: W_l[32][cin_l][9] then b_l[32] (cin_1 = 1, else 32); then alpha.
+__host__ __device__ constexpr int cnn_cin(int l) { return l == 0 ? 1 : kCnnC; }
+__host__ __device__ constexpr int cnn_woff(int l) {
+  return l == 0 ? 0 : cnn_woff(l - 1) + kCnnC * cnn_cin(l - 1) * kCnnK + kCnnC;
+}
+__host__ __device__ constexpr int cnn_boff(int l) { return cnn_woff(l) + kCnnC * cnn_cin(l) * kCnnK; }
+constexpr int kCnnAlpha = cnn_woff(kCnnLayers);
+constexpr int kCnnParams = kCnnAlpha + 1;
+
+struct CnnLayerIO {
+  const float* in;  // [S][cin][L]
+  float* pre;       // [S][32][L] post-ReLU before pooling (training), or nullptr
+  float* out;       // [S][32][L/2]
+  int L;
+};
+
+// Decimate: q [S][n] int8 -> d [S][n/16] float (block sums / 4).
+cudaError_t launch_cnn_decimate(const int8_t* q, int64_t n, int nsig, float* d, cudaStream_t st);
+// One layer for S signals with the BF16 weights of layer l.
+cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16_t* wbf,
+                             const float* params, cudaStream_t st);
+// score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1).
+cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
+                              float* scores, cudaStream_t st);
+// Top-8 bins per pair -> window centres in samples (256 l), softmax mass of
+// the top 8 (margin).
+cudaError_t launch_cnn_topk(const float* scores, int npairs, int Lf, int32_t* centres,
+                            float* margin, cudaStream_t st);
+
+// ---- training
+// Softmax cross-entropy against label bins round(tau / 256); loss[p],
+// dscore[p][.] = (softmax - onehot) / npairs.
+cudaError_t launch_cnn_softmax_ce(const float* scores, const int64_t* labels, int npairs, int Lf,
+                                  float* loss, float* dscores, cudaStream_t st);
+// d features and per-pair d alpha from d scores.
+cudaError_t launch_cnn_scores_bwd(const float* feat, const float* dscores, int npairs, int Lf,
+                                  const float* params, float* dfeat, float* dalpha_pp,
+                                  cudaStream_t st);
+// Through max-pool and ReLU: dout [S][32][L/2] -> dz [S][32][L].
+cudaError_t launch_cnn_pool_relu_bwd(const float* pre, const float* dout, int nsig, int L,
+                                     float* dz, cudaStream_t st);
+// din [S][32][L] = conv^T(dz) with layer l's weights (l >= 1).
+cudaError_t launch_cnn_dgrad(const float* dz, int nsig, int L, int l, const uint16_t* wbf,
+                             float* din, cudaStream_t st);
+// Per-signal weight/bias gradient partials [S][32*cin*9 + 32].
+cudaError_t launch_cnn_wgrad(const float* dz, const float* in, int nsig, int L, int l,
+                             float* partial, cudaStream_t st);
+// grad[off + i] = sum over signals of partial[s][i] (fixed order).
+cudaError_t launch_cnn_reduce(const float* partial, int nsig, int count, float* grad,
+                              cudaStream_t st);
+// AdamW on all parameters; refreshes the BF16 copy.
+cudaError_t launch_cnn_adamw(float* params, const float* grad, float* m, float* v, uint16_t* wbf,
+                             int64_t step, float lr, float beta1, float beta2, float eps,
+                             float wd, cudaStream_t st);
+cudaError_t launch_cnn_to_bf16(const float* params, uint16_t* wbf, cudaStream_t st);
+
+// ---- windowed exact correlation (popc planes) and its argmax
+struct WinJob {
+  const uint32_t* px;  // planes of x (sign, nonzero), words per plane wx
+  const uint32_t* py;
+  int64_t wx, wy;
+  int64_t lag_lo, lag_hi;  // window, clipped to the overlap range
+  int32_t* c;              // 288 int32, lag lag_lo + i at c[i]
+};
+// bits <= 2 planes.  One CTA per window.
+cudaError_t launch_xcorr_popc_windows(const WinJob* d_jobs, int njobs, cudaStream_t st);
+// Per pair: tie-ruled argmax over its 8 windows -> lag, value.
+cudaError_t launch_window_argmax(const WinJob* d_jobs, int npairs, int64_t* lag, int64_t* val,
+                                 cudaStream_t st);

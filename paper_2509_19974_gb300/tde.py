@@ -27,9 +27,11 @@ TDE_I32, TDE_I64, TDE_F32, TDE_I8 = 0, 1, 2, 3
 # Every symbol include/tde.h declares.
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
            "tde_ctx_set_profiling", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
-           "tde_quantize_noalloc", "tde_xcorr_int", "tde_argmax", "tde_xcorr_fft32",
+           "tde_quantize_noalloc", "tde_quantize_batch", "tde_xcorr_int", "tde_argmax", "tde_xcorr_fft32",
            "tde_estimate", "tde_estimate_batch", "tde_batch_create", "tde_batch_run",
-           "tde_batch_destroy")
+           "tde_batch_destroy", "tde_model_param_count", "tde_model_create", "tde_model_destroy",
+           "tde_model_get", "tde_model_set", "tde_train_step", "tde_propose",
+           "tde_estimate_learned", "tde_synth_pairs")
 
 
 class TdeError(RuntimeError):
@@ -54,7 +56,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libtde.so not found at {path}: run paper_2509_19974_gb300.build.build()")
     lib = ctypes.CDLL(path)
-    i64, p, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    i64, p, i32, f32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_float
     st = ctypes.c_int
     sig = {
         "tde_ctx_create": ([i32, ctypes.POINTER(p)], st),
@@ -66,6 +68,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_pick_engine": ([i32, i64, i64, i64], i32),
         "tde_quantize": ([p, p, i64, i32, p, p], st),
         "tde_quantize_noalloc": ([p, i64, i32, i32, p, p, p], st),
+        "tde_quantize_batch": ([p, p, i64, i32, i32, p, p], st),
         "tde_xcorr_int": ([p, p, i64, p, i64, i32, i64, i64, i32, p, i32, p], st),
         "tde_argmax": ([p, p, i32, i64, i64, p, p, p], st),
         "tde_xcorr_fft32": ([p, p, p, i32, i64, i64, i32, i64, i64, p, p], st),
@@ -75,6 +78,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                               ctypes.POINTER(p)], st),
         "tde_batch_run": ([p, p], st),
         "tde_batch_destroy": ([p], st),
+        "tde_model_param_count": ([], i64),
+        "tde_model_create": ([p, i64, ctypes.c_uint64, ctypes.POINTER(p)], st),
+        "tde_model_destroy": ([p], st),
+        "tde_model_get": ([p, p, p, p, p, p], st),
+        "tde_model_set": ([p, p, p, p, i64], st),
+        "tde_train_step": ([p, p, p, i32, p, f32, f32, p, p], st),
+        "tde_propose": ([p, p, p, i32, p, p, p], st),
+        "tde_estimate_learned": ([p, p, p, p, i32, i32, f32, p, p, p, p], st),
+        "tde_synth_pairs": ([p, ctypes.c_uint64, i64, i32, i64, i64, f32, f32, f32, f32, p, p, p,
+                             p], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +202,18 @@ def tde_quantize(ctx: Context, x: torch.Tensor, bits: int, q_out=None, stream=No
     _need(q_out, torch.int8, "q_out")
     ctx.check(ctx.lib.tde_quantize(ctx.handle, x.data_ptr(), x.numel(), int(bits),
                                    q_out.data_ptr(), _stream(stream)))
+    return q_out
+
+
+def tde_quantize_batch(ctx: Context, x: torch.Tensor, bits: int, q_out=None, stream=None):
+    """x: [nsig, n] float32 -> [nsig, n] int8 in one call."""
+    _need(x, torch.float32, "x")
+    nsig, n = x.shape
+    if q_out is None:
+        q_out = torch.empty((nsig, n), dtype=torch.int8, device=x.device)
+    _need(q_out, torch.int8, "q_out")
+    ctx.check(ctx.lib.tde_quantize_batch(ctx.handle, x.data_ptr(), n, nsig, int(bits),
+                                         q_out.data_ptr(), _stream(stream)))
     return q_out
 
 
@@ -351,3 +376,113 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------ learned lag proposal
+
+def synth_pairs(ctx: Context, seed: int, first: int, npairs: int, n: int, dmax: int,
+                ar=(0.0, 0.98), snr_db=(-5.0, 30.0), stream=None):
+    """Device-generated shifted pairs: (x [npairs, n], y [npairs, n], shift)."""
+    dev = torch.device("cuda", ctx.device)
+    x = torch.empty((npairs, n), dtype=torch.float32, device=dev)
+    y = torch.empty((npairs, n), dtype=torch.float32, device=dev)
+    d = torch.empty(npairs, dtype=torch.int64, device=dev)
+    ctx.check(ctx.lib.tde_synth_pairs(ctx.handle, int(seed), int(first), int(npairs), int(n),
+                                      int(dmax), float(ar[0]), float(ar[1]), float(snr_db[0]),
+                                      float(snr_db[1]), x.data_ptr(), y.data_ptr(), d.data_ptr(),
+                                      _stream(stream)))
+    return x, y, d
+
+
+def interleave_q(qx: torch.Tensor, qy: torch.Tensor) -> torch.Tensor:
+    """[P, n] int8 x and y -> [2P, n] with pair p at rows 2p (x), 2p+1 (y)."""
+    return torch.stack([qx, qy], dim=1).reshape(-1, qx.shape[1]).contiguous()
+
+
+class Model:
+    """A lag-proposal CNN on the device (tde_model_*)."""
+
+    def __init__(self, ctx: Context, n: int, seed: int = 0):
+        self.ctx, self.n = ctx, int(n)
+        self.lib = load()
+        h = ctypes.c_void_p()
+        ctx.check(self.lib.tde_model_create(ctx.handle, self.n, int(seed), ctypes.byref(h)))
+        self.handle = h
+        self.count = int(self.lib.tde_model_param_count())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tde_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state(self):
+        import numpy as np
+        arrs = [np.empty(self.count, np.float32) for _ in range(4)]
+        step = ctypes.c_int64()
+        s = self.lib.tde_model_get(self.handle, *[a.ctypes.data for a in arrs], ctypes.byref(step))
+        if s != TDE_OK:
+            raise TdeError(s, "tde_model_get failed")
+        return {"params": arrs[0], "adam_m": arrs[1], "adam_v": arrs[2], "grad": arrs[3],
+                "step": int(step.value)}
+
+    def load_state(self, st):
+        import numpy as np
+        ps = np.ascontiguousarray(st["params"], np.float32)
+        m = np.ascontiguousarray(st.get("adam_m", np.zeros_like(ps)), np.float32)
+        v = np.ascontiguousarray(st.get("adam_v", np.zeros_like(ps)), np.float32)
+        s = self.lib.tde_model_set(self.handle, ps.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                   int(st.get("step", 0)))
+        if s != TDE_OK:
+            raise TdeError(s, "tde_model_set failed")
+
+    def save(self, path: str):
+        import numpy as np
+        st = self.state()
+        np.savez(path, n=self.n, **{k: v for k, v in st.items()})
+
+    def load(self, path: str):
+        import numpy as np
+        z = np.load(path)
+        if int(z["n"]) != self.n:
+            raise ValueError("checkpoint is for another signal length")
+        self.load_state({k: z[k] for k in ("params", "adam_m", "adam_v", "step")})
+
+    def train_step(self, q2: torch.Tensor, labels: torch.Tensor, lr: float, weight_decay=1e-4,
+                   stream=None):
+        _need(q2, torch.int8, "q")
+        _need(labels, torch.int64, "labels")
+        npairs = q2.shape[0] // 2
+        loss = torch.empty(npairs, dtype=torch.float32, device=q2.device)
+        self.ctx.check(self.lib.tde_train_step(self.ctx.handle, self.handle, q2.data_ptr(), npairs,
+                                               labels.data_ptr(), float(lr), float(weight_decay),
+                                               loss.data_ptr(), _stream(stream)))
+        return loss
+
+    def propose(self, q2: torch.Tensor, stream=None):
+        _need(q2, torch.int8, "q")
+        npairs = q2.shape[0] // 2
+        cent = torch.empty((npairs, 8), dtype=torch.int32, device=q2.device)
+        marg = torch.empty(npairs, dtype=torch.float32, device=q2.device)
+        self.ctx.check(self.lib.tde_propose(self.ctx.handle, self.handle, q2.data_ptr(), npairs,
+                                            cent.data_ptr(), marg.data_ptr(), _stream(stream)))
+        return cent, marg
+
+    def estimate(self, x: torch.Tensor, y: torch.Tensor, bits: int = 2, theta: float = 0.5,
+                 stream=None):
+        _need(x, torch.float32, "x")
+        _need(y, torch.float32, "y")
+        npairs = x.shape[0]
+        lags = torch.empty(npairs, dtype=torch.int64, device=x.device)
+        vals = torch.empty(npairs, dtype=torch.int64, device=x.device)
+        fb = torch.empty(npairs, dtype=torch.int32, device=x.device)
+        self.ctx.check(self.lib.tde_estimate_learned(self.ctx.handle, self.handle, x.data_ptr(),
+                                                     y.data_ptr(), npairs, int(bits), float(theta),
+                                                     lags.data_ptr(), vals.data_ptr(),
+                                                     fb.data_ptr(), _stream(stream)))
+        return lags, vals, fb

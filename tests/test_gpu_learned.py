@@ -1,0 +1,126 @@
+"""Learned lag proposal on the GPU: the generator, the CNN's loss and
+gradient against the float64 reference, AdamW, and the learned estimator's
+lag against the exact correlation (windows only, and with full fallback)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import cnn_ref
+from paper_2509_19974_gb300 import tde
+
+pytestmark = pytest.mark.gpu
+N = 16384
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2509_19974_gb300 import build
+    build.build()
+    c = tde.Context(0)
+    yield c
+    c.close()
+
+
+def test_synth_pairs_deterministic_and_shifted(ctx):
+    x, y, d = tde.synth_pairs(ctx, 7, 100, 6, N, 2000, ar=(0.5, 0.5), snr_db=(40.0, 40.0))
+    x2, y2, d2 = tde.synth_pairs(ctx, 7, 100, 6, N, 2000, ar=(0.5, 0.5), snr_db=(40.0, 40.0))
+    torch.cuda.synchronize()
+    assert torch.equal(x, x2) and torch.equal(y, y2) and torch.equal(d, d2)
+    d = d.cpu().numpy()
+    assert np.all(np.abs(d) <= 2000)
+    xs, ys = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+    for p in range(6):      # x[n] = y[n + d] up to 40 dB noise
+        k = int(d[p])
+        a = xs[p][max(0, -k): N - max(0, k)]
+        b = ys[p][max(0, k): N - max(0, -k)]
+        assert np.corrcoef(a, b)[0, 1] > 0.99
+
+
+def _quantized_pairs(ctx, P, seed, snr=(10.0, 30.0)):
+    x, y, d = tde.synth_pairs(ctx, seed, 0, P, N, 2000, ar=(0.0, 0.9), snr_db=snr)
+    q2 = tde.tde_quantize_batch(ctx, torch.stack([x, y], dim=1).reshape(-1, N).contiguous(), 2)
+    return x, y, d, q2
+
+
+def test_loss_and_gradient_match_float64_reference(ctx):
+    m = tde.Model(ctx, N, seed=3)
+    x, y, d, q2 = _quantized_pairs(ctx, 4, 11)
+    labels = d.clone()
+    p0 = m.state()["params"]
+    loss = m.train_step(q2, labels, lr=0.0, weight_decay=0.0)
+    st = m.state()
+    torch.cuda.synchronize()
+    ref_params = p0.astype(np.float64)
+    lay, a_off = cnn_ref.layout()
+    for (wo, bo, cin) in lay:       # the device's forward pass uses BF16 weights
+        ref_params[wo:bo] = cnn_ref.bf16_round(p0[wo:bo]).astype(np.float64)
+    ref_loss, ref_grad = cnn_ref.loss_and_grad(ref_params, q2.cpu().numpy(), labels.cpu().numpy())
+    assert np.allclose(loss.cpu().numpy(), ref_loss, rtol=2e-4, atol=2e-4)
+    g = st["grad"].astype(np.float64)
+    assert np.linalg.norm(g - ref_grad) <= 2e-3 * np.linalg.norm(ref_grad)
+    m.close()
+
+
+def test_adamw_step(ctx):
+    m = tde.Model(ctx, N, seed=4)
+    x, y, d, q2 = _quantized_pairs(ctx, 2, 12)
+    p0 = m.state()["params"].astype(np.float64)
+    lr, wd = 1e-3, 1e-2
+    m.train_step(q2, d, lr=lr, weight_decay=wd)
+    st = m.state()
+    g = st["grad"].astype(np.float64)
+    mm = 0.1 * g
+    vv = 0.001 * g * g
+    is_w = np.zeros_like(p0, bool)
+    for (wo, bo, cin) in cnn_ref.layout()[0]:
+        is_w[wo:bo] = True
+    want = p0 - lr * ((mm / 0.1) / (np.sqrt(vv / 0.001) + 1e-8) + np.where(is_w, wd * p0, 0.0))
+    assert st["step"] == 1
+    assert np.allclose(st["params"], want, rtol=1e-5, atol=1e-6)
+    m.close()
+
+
+def test_training_reduces_loss(ctx):
+    m = tde.Model(ctx, N, seed=5)
+    losses = []
+    for it in range(60):
+        x, y, d, q2 = _quantized_pairs(ctx, 32, 1000 + it, snr=(20.0, 30.0))
+        losses.append(float(m.train_step(q2, d, lr=3e-3).mean()))
+    assert np.mean(losses[-10:]) < 0.7 * np.mean(losses[:5]), losses
+    m.close()
+
+
+def _window_reference(qx, qy, centres):
+    """Tie-ruled argmax of the exact correlation over the union of windows."""
+    lags = set()
+    for c in centres:
+        lags.update(range(max(int(c) - 128, -(N - 1)), min(int(c) + 128, N - 1) + 1))
+    lags = np.array(sorted(lags), np.int64)
+    vals = oracle.xcorr_at(qx, qy, lags)
+    best = None
+    for t, v in zip(lags.tolist(), vals.tolist()):
+        key = (v, -abs(t), -t)
+        if best is None or key > best[0]:
+            best = (key, t, v)
+    return best[1], best[2]
+
+
+def test_learned_estimate_windows_and_fallback(ctx):
+    m = tde.Model(ctx, N, seed=6)
+    x, y, d, q2 = _quantized_pairs(ctx, 6, 21)
+    cent, marg = m.propose(q2)
+    lags, vals, fb = m.estimate(x, y, bits=2, theta=0.0)       # windows only
+    torch.cuda.synchronize()
+    assert int(fb.sum()) == 0
+    xs, ys = x.cpu().numpy(), y.cpu().numpy()
+    cent = cent.cpu().numpy()
+    for p in range(6):
+        qx, qy = oracle.quantize(xs[p], 2), oracle.quantize(ys[p], 2)
+        assert (int(lags[p]), int(vals[p])) == _window_reference(qx, qy, cent[p])
+    lags, vals, fb = m.estimate(x, y, bits=2, theta=2.0)       # all fall back
+    torch.cuda.synchronize()
+    assert int(fb.sum()) == 6
+    for p in range(6):
+        assert (int(lags[p]), int(vals[p])) == oracle.estimate(xs[p], ys[p], 2)
+    m.close()
