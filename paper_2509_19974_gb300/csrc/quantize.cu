@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(kThreads) k_rank_select(RankState* __restrict_
   uint32_t* gh = hist + (size_t)sig * 7 * kBins;
   for (int m = 0; m < M; ++m) {
     const uint32_t* h = gh + (PASS == 0 ? 0 : m) * kBins;
+    // Every thread reads the residual rank before the scan's barriers: the
+    // one thread whose bins hold it rewrites it after them.
+    const uint32_t r = state[sig].rank[m];
     uint32_t cnt[kPer];
     uint32_t local = 0;
 #pragma unroll
@@ -137,7 +140,6 @@ __global__ void __launch_bounds__(kThreads) k_rank_select(RankState* __restrict_
       local += cnt[k];
     }
     uint32_t before = block_exclusive_scan(local, warp_tot);
-    const uint32_t r = state[sig].rank[m];
     if (r >= before && r < before + local) {
       uint32_t acc = before;
 #pragma unroll

@@ -225,3 +225,20 @@ def test_estimate_constant_signals_tie_to_zero(ctx):
     x = np.full(3000, 0.5, np.float32)
     lag, val = ctx.estimate(_gpu(x), _gpu(x), 1)
     assert (int(lag.item()), int(val.item())) == (0, 3000)
+
+
+@pytest.mark.parametrize("bits", [2, 4])
+def test_quantize_many_signals_batched(ctx, bits):
+    """512 signals in one batched call (one CTA per signal per select pass):
+    every signal's levels equal the oracle's, on two calls in a row."""
+    rng = np.random.default_rng(77 + bits)
+    X = rng.standard_normal((512, 65536)).astype(np.float32)
+    X[:, ::50] = 0.0
+    xd = torch.from_numpy(X).cuda()
+    q1 = tde.tde_quantize_batch(ctx, xd, bits)
+    q2 = tde.tde_quantize_batch(ctx, xd, bits)
+    ctx.sync()
+    assert torch.equal(q1, q2)
+    q1 = q1.cpu().numpy()
+    for i in range(512):
+        assert np.array_equal(q1[i], oracle.quantize(X[i], bits)), i
