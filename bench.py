@@ -44,6 +44,7 @@ SMS = 152          # GB300 SMs
 # from one ncu capture of this workload (see profiles/); None once the kernel
 # has changed since the capture.
 TRAFFIC = {}
+CKPT = os.path.join(ROOT, "paper_2509_19974_gb300", "models", "proposal_n65536_b2.npz")
 POPC_PER_SM_CLK = 16  # POPC issue rate per SM per clock
 
 
@@ -61,6 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -308,6 +310,38 @@ def main():
     gpu_lags = lags.cpu().numpy()
     gpu_vals = vals.cpu().numpy()
 
+    # --- the learned-proposal form on the same pairs (trained checkpoint)
+    learned = None
+    if not args.no_learned and args.n == 65536 and args.bits == 2 and os.path.exists(CKPT):
+        z = np.load(CKPT)
+        theta = float(z["theta"])
+        model = tde.Model(ctx, args.n)
+        model.load(CKPT)
+        for _ in range(3):
+            ll, lv, lf = model.estimate(Xd, Yd, args.bits, theta)
+        torch.cuda.synchronize()
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(args.steps):
+            ll, lv, lf = model.estimate(Xd, Yd, args.bits, theta)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        ms_l = k0.elapsed_time(k1) / args.steps
+        agree = float(((ll == lags) & (lv == vals)).float().mean())
+        meta = json.loads(str(z["meta"]))
+        learned = {"value": args.npairs / (ms_l / 1e3), "unit": "pairs/s", "ms_per_step": ms_l,
+                   "lag_agreement_with_full": agree, "fallback_rate": float(lf.float().mean()),
+                   "theta": theta, "full_form_value": args.npairs * args.steps / (ms_max / 1e3),
+                   "speedup_vs_full": (ms_max / args.steps) / ms_l,
+                   "what": "quantize -> 16x decimate -> CNN (BF16 weights, FP32) -> top-8 "
+                           "257-lag windows -> exact popc correlation in the windows -> "
+                           "tie-ruled argmax; full correlation when margin < theta; one host "
+                           "sync per step to read margins",
+                   "checkpoint": {"train_pairs": meta.get("train_pairs"),
+                                  "train_seconds": meta.get("train_seconds"),
+                                  "test": meta.get("test")}}
+        model.close()
+
     # --- FP32 FFT comparator beside it: the same quantized pairs, timed alone
     fft = None
     if not args.no_fft:
@@ -384,7 +418,7 @@ def main():
            "no_graph": {"value": args.npairs * world * args.steps / (ms_nograph / 1e3),
                         "ms_per_step": ms_nograph / args.steps},
            "mac_per_s": macs * world * args.steps / (ms_max / 1e3),
-           "clocks": clk.summary(), "fft32_comparator": fft}
+           "clocks": clk.summary(), "fft32_comparator": fft, "learned_proposal": learned}
     if not args.no_cpu_baseline and world == 1:
         cb, ref = cpu_baseline(b, args.cpu_seconds)
         out["cpu_baseline"] = cb
