@@ -49,7 +49,11 @@ __global__ void k_decimate(const int8_t* __restrict__ q, int64_t n, int nsig, fl
   }
 }
 
-// conv (kernel 9, pad 4) + bias + ReLU (+ store) + max-pool 2.
+// conv (kernel 9, pad 4) + bias + ReLU (+ store) + max-pool 2.  A thread owns
+// 4 output channels x 16 positions (64 accumulators); a CTA covers 512
+// positions; weights are read as float4 (4 channels) per (ci, k).
+constexpr int kTP = 512;  // positions per forward CTA
+
 template <int CIN>
 __global__ void __launch_bounds__(kThreads) k_conv_fwd(const float* __restrict__ in,
                                                        float* __restrict__ pre,
@@ -57,60 +61,189 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd(const float* __restrict__
                                                        const uint16_t* __restrict__ wbf,
                                                        const float* __restrict__ bias) {
   extern __shared__ float csm[];
-  float (*in_s)[kT + 8] = reinterpret_cast<float (*)[kT + 8]>(csm);                  // [CIN][kT+8]
-  float (*w_s)[kCnnC] = reinterpret_cast<float (*)[kCnnC]>(csm + CIN * (kT + 8));  // [ci*9+k][co]
-  const int s = blockIdx.y, p0 = blockIdx.x * kT;
+  float* in_s = csm;                          // [CIN][kTP + 8]
+  float* w_s = csm + CIN * (kTP + 8);         // [ci*9 + k][32 co]
+  const int s = blockIdx.y, p0 = blockIdx.x * kTP;
   const float* src = in + (int64_t)s * CIN * L;
-  for (int idx = threadIdx.x; idx < CIN * (kT + 8); idx += kThreads) {
-    const int ci = idx / (kT + 8), j = idx % (kT + 8);
+  for (int idx = threadIdx.x; idx < CIN * (kTP + 8); idx += kThreads) {
+    const int ci = idx / (kTP + 8), j = idx % (kTP + 8);
     const int pos = p0 - 4 + j;
-    in_s[ci][j] = (pos >= 0 && pos < L) ? src[(int64_t)ci * L + pos] : 0.f;
+    in_s[idx] = (pos >= 0 && pos < L) ? src[(int64_t)ci * L + pos] : 0.f;
   }
   for (int idx = threadIdx.x; idx < kCnnC * CIN * kCnnK; idx += kThreads) {
     const int co = idx / (CIN * kCnnK), r = idx % (CIN * kCnnK);
-    w_s[r][co] = bf16_to_f(wbf[idx]);
+    w_s[r * kCnnC + co] = bf16_to_f(wbf[idx]);
   }
   __syncthreads();
-  const int co = threadIdx.x & 31, pg = threadIdx.x >> 5;
-  float acc[16];
-  const float b = bias[co];
+  const int cg = threadIdx.x & 7, pg = threadIdx.x >> 3;  // 8 channel groups x 32 position groups
+  const int co0 = cg * 4;
+  if (p0 + pg * 16 >= L) return;  // short layers (L < 512): idle position groups
+  float acc[4][16];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j] = b;
+  for (int c = 0; c < 4; ++c) {
+    const float b = bias[co0 + c];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[c][j] = b;
+  }
   for (int ci = 0; ci < CIN; ++ci) {
     float xr[24];
+    const float* row = in_s + ci * (kTP + 8) + pg * 16;
 #pragma unroll
-    for (int j = 0; j < 24; ++j) xr[j] = in_s[ci][pg * 16 + j];
+    for (int j = 0; j < 24; ++j) xr[j] = row[j];
 #pragma unroll
     for (int k = 0; k < kCnnK; ++k) {
-      const float w = w_s[ci * kCnnK + k][co];
+      const float4 w = *reinterpret_cast<const float4*>(w_s + (ci * kCnnK + k) * kCnnC + co0);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = fmaf(w, xr[j + k], acc[j]);
+      for (int j = 0; j < 16; ++j) {
+        const float xv = xr[j + k];
+        acc[0][j] = fmaf(w.x, xv, acc[0][j]);
+        acc[1][j] = fmaf(w.y, xv, acc[1][j]);
+        acc[2][j] = fmaf(w.z, xv, acc[2][j]);
+        acc[3][j] = fmaf(w.w, xv, acc[3][j]);
+      }
     }
   }
   const int pbase = p0 + pg * 16;
-  float* dst_pre = pre ? pre + ((int64_t)s * kCnnC + co) * L + pbase : nullptr;
-  float* dst = out + ((int64_t)s * kCnnC + co) * (L / 2) + pbase / 2;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j] = fmaxf(acc[j], 0.f);
-  if (dst_pre) {
+  for (int c = 0; c < 4; ++c) {
 #pragma unroll
-    for (int j = 0; j < 16; j += 4)
-      *reinterpret_cast<float4*>(dst_pre + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    for (int j = 0; j < 16; ++j) acc[c][j] = fmaxf(acc[c][j], 0.f);
+    if (pre) {
+      float* dp = pre + ((int64_t)s * kCnnC + co0 + c) * L + pbase;
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(dp + j) =
+            make_float4(acc[c][j], acc[c][j + 1], acc[c][j + 2], acc[c][j + 3]);
+    }
+    float* dst = out + ((int64_t)s * kCnnC + co0 + c) * (L / 2) + pbase / 2;
+#pragma unroll
+    for (int j = 0; j < 16; j += 8)
+      *reinterpret_cast<float4*>(dst + j / 2) =
+          make_float4(fmaxf(acc[c][j], acc[c][j + 1]), fmaxf(acc[c][j + 2], acc[c][j + 3]),
+                      fmaxf(acc[c][j + 4], acc[c][j + 5]), fmaxf(acc[c][j + 6], acc[c][j + 7]));
   }
+}
+
+// Inference form of the 32 -> 32 conv layers on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation): for each tap k,
+// Y[p][co] += sum_ci X[p + k - 4][ci] W[co][ci][k], a 16-position x 32-channel
+// tile per warp step.  Activations are rounded to BF16 when staged; the
+// training forward keeps FP32 activations (k_conv_fwd).
+constexpr int kXR = 40;  // padded BF16 row (32 channels + 8): conflict-free fragment loads
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return (uint32_t)f_to_bf16(lo) | ((uint32_t)f_to_bf16(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restrict__ in,
+                                                          float* __restrict__ out, int L,
+                                                          const uint16_t* __restrict__ wbf,
+                                                          const float* __restrict__ bias) {
+  extern __shared__ uint32_t tsm[];
+  uint16_t* xs = reinterpret_cast<uint16_t*>(tsm);                 // [kTP + 8][kXR]
+  uint16_t* ws = xs + (kTP + 8) * kXR;                             // [9][32 co][kXR]
+  const int s = blockIdx.y, p0 = blockIdx.x * kTP;
+  const float* src = in + (int64_t)s * kCnnC * L;
+  // X rows r <-> position p0 - 4 + r; two channels per 32-bit word
+  for (int idx = threadIdx.x; idx < (kTP + 8) * (kCnnC / 2); idx += kThreads) {
+    const int r = idx % (kTP + 8), cp = idx / (kTP + 8);
+    const int pos = p0 - 4 + r;
+    float v0 = 0.f, v1 = 0.f;
+    if (pos >= 0 && pos < L) {
+      v0 = src[(int64_t)(2 * cp) * L + pos];
+      v1 = src[(int64_t)(2 * cp + 1) * L + pos];
+    }
+    *reinterpret_cast<uint32_t*>(xs + r * kXR + 2 * cp) = pack_bf16x2(v0, v1);
+  }
+  for (int idx = threadIdx.x; idx < kCnnC * kCnnC * kCnnK; idx += kThreads) {
+    const int co = idx / (kCnnC * kCnnK), r = idx % (kCnnC * kCnnK);
+    const int ci = r / kCnnK, k = r % kCnnK;
+    ws[(k * kCnnC + co) * kXR + ci] = wbf[idx];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int nmt = (L - p0) < kTP ? (L - p0) / 16 : kTP / 16;  // m-tiles of this CTA
+  float acc[4][4][4];  // [m-tile of the warp][n-tile][frag]
 #pragma unroll
-  for (int j = 0; j < 16; j += 8)
-    *reinterpret_cast<float4*>(dst + j / 2) =
-        make_float4(fmaxf(acc[j], acc[j + 1]), fmaxf(acc[j + 2], acc[j + 3]),
-                    fmaxf(acc[j + 4], acc[j + 5]), fmaxf(acc[j + 6], acc[j + 7]));
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < kCnnK; ++k) {
+#pragma unroll
+    for (int ks = 0; ks < kCnnC; ks += 16) {
+      uint32_t b[4][2];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const uint16_t* wr = ws + (k * kCnnC + ni * 8 + g) * kXR + ks + 2 * t;
+        b[ni][0] = *reinterpret_cast<const uint32_t*>(wr);
+        b[ni][1] = *reinterpret_cast<const uint32_t*>(wr + 8);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int mt = warp + 8 * mi;
+        if (mt >= nmt) continue;
+        const uint16_t* xr = xs + (mt * 16 + g + k) * kXR + ks + 2 * t;
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(xr);
+        a[1] = *reinterpret_cast<const uint32_t*>(xr + 8 * kXR);
+        a[2] = *reinterpret_cast<const uint32_t*>(xr + 8);
+        a[3] = *reinterpret_cast<const uint32_t*>(xr + 8 * kXR + 8);
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], a, b[ni][0], b[ni][1]);
+      }
+    }
+  }
+  // epilogue: bias, ReLU, max-pool rows (g, g^1) via a lane shuffle (lane ^ 4)
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi) {
+    const int mt = warp + 8 * mi;
+    if (mt >= nmt) continue;  // warp-uniform
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int co = ni * 8 + 2 * t;
+      const float b0 = bias[co], b1 = bias[co + 1];
+      float v[4] = {fmaxf(acc[mi][ni][0] + b0, 0.f), fmaxf(acc[mi][ni][1] + b1, 0.f),
+                    fmaxf(acc[mi][ni][2] + b0, 0.f), fmaxf(acc[mi][ni][3] + b1, 0.f)};
+      float o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = fmaxf(v[e], __shfl_xor_sync(0xffffffffu, v[e], 4));
+      if ((g & 1) == 0) {
+        const int prow = p0 + mt * 16 + g;  // even position; rows g and g + 8
+        float* d0 = out + ((int64_t)s * kCnnC + co) * (L / 2);
+        float* d1 = d0 + (L / 2);
+        d0[prow / 2] = o[0];
+        d1[prow / 2] = o[1];
+        d0[prow / 2 + 4] = o[2];
+        d1[prow / 2 + 4] = o[3];
+      }
+    }
+  }
 }
 
 // scores of one pair; fy zero-padded by Lf on both sides in shared memory.
+// Thread = (group of 8 consecutive bins, quarter of the channels): one fx and
+// one new fy load per 8 FMAs (the fy window slides in registers); the four
+// channel quarters are summed through shared memory.
 __global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ feat, int Lf,
                                                      const float* __restrict__ params,
                                                      float* __restrict__ scores) {
   extern __shared__ float sm[];
   float* fx = sm;                   // [32][Lf]
   float* fy = sm + kCnnC * Lf;      // [32][3 Lf]
+  float* part = fy + kCnnC * 3 * Lf;  // [4][nb rounded to 8]
   const int p = blockIdx.x;
   const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
   const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
@@ -121,17 +254,35 @@ __global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ f
   }
   __syncthreads();
   const float alpha = params[kCnnAlpha];
-  const int nb = 2 * Lf - 1;
-  for (int b = threadIdx.x; b < nb; b += kThreads) {
-    const int l = b - (Lf - 1);
-    float acc = 0.f;
-    for (int c = 0; c < kCnnC; ++c) {
+  const int nb = 2 * Lf - 1, ngroups = (nb + 7) / 8, nbr = ngroups * 8;
+  for (int w = threadIdx.x; w < ngroups * 4; w += kThreads) {
+    const int grp = w % ngroups, cq = w / ngroups;
+    const int b0 = grp * 8, l0 = b0 - (Lf - 1);
+    float acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+    for (int c = cq * 8; c < cq * 8 + 8; ++c) {
       const float* a = fx + c * Lf;
-      const float* y = fy + c * 3 * Lf + Lf + l;
-      for (int i = 0; i < Lf; ++i) acc = fmaf(a[i], y[i], acc);
+      const float* y = fy + c * 3 * Lf + Lf + l0;  // y[i + t] = fy[c][i + l0 + t]
+      float win[8];
+#pragma unroll
+      for (int t = 0; t < 7; ++t) win[t + 1] = y[t];
+      for (int i = 0; i < Lf; ++i) {
+#pragma unroll
+        for (int t = 0; t < 7; ++t) win[t] = win[t + 1];
+        win[7] = y[i + 7];
+        const float av = a[i];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = fmaf(av, win[t], acc[t]);
+      }
     }
-    scores[(int64_t)p * nb + b] = alpha * acc;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) part[cq * nbr + b0 + t] = acc[t];
   }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += kThreads)
+    scores[(int64_t)p * nb + b] =
+        alpha * ((part[b] + part[nbr + b]) + (part[2 * nbr + b] + part[3 * nbr + b]));
 }
 
 // lag rank of bin l: smaller |l| first, then negative first (the estimator's
@@ -416,16 +567,26 @@ __global__ void __launch_bounds__(kThreads) k_xcorr_popc_win(const WinJob* __res
   for (int i = 0; i < kWinA; ++i) acc[i] = acc2[i] = 0;
   const int64_t per = (J.wx + 7) / 8;
   const int64_t w_lo = warp * per, w_hi = w_lo + per < J.wx ? w_lo + per : J.wx;
-  for (int64_t w = w_lo; w < w_hi; ++w) {
-    const uint32_t sx = __ldg(J.px + w), zx = __ldg(J.px + J.wx + w);
-    uint32_t ys[kWinA + 1], yz[kWinA + 1];
+  // y words w + a0 + i, i = 0..9, slide by one word per x word.
+  uint32_t ys[kWinA + 1], yz[kWinA + 1];
 #pragma unroll
-    for (int i = 0; i <= kWinA; ++i) {
-      const int64_t yw = w + a0 + i;
-      const bool in = yw >= 0 && yw < J.wy;
-      ys[i] = in ? __ldg(J.py + yw) : 0u;
-      yz[i] = in ? __ldg(J.py + J.wy + yw) : 0u;
+  for (int i = 0; i < kWinA; ++i) {
+    const int64_t yw = w_lo + a0 + i;
+    const bool in = yw >= 0 && yw < J.wy;
+    ys[i + 1] = in ? __ldg(J.py + yw) : 0u;
+    yz[i + 1] = in ? __ldg(J.py + J.wy + yw) : 0u;
+  }
+  for (int64_t w = w_lo; w < w_hi; ++w) {
+#pragma unroll
+    for (int i = 0; i < kWinA; ++i) {
+      ys[i] = ys[i + 1];
+      yz[i] = yz[i + 1];
     }
+    const int64_t yw = w + a0 + kWinA;
+    const bool in = yw >= 0 && yw < J.wy;
+    ys[kWinA] = in ? __ldg(J.py + yw) : 0u;
+    yz[kWinA] = in ? __ldg(J.py + J.wy + yw) : 0u;
+    const uint32_t sx = __ldg(J.px + w), zx = __ldg(J.px + J.wx + w);
 #pragma unroll
     for (int i = 0; i < kWinA; ++i) {
       const uint32_t sy = __funnelshift_r(ys[i], ys[i + 1], r);
@@ -497,17 +658,24 @@ cudaError_t launch_cnn_decimate(const int8_t* q, int64_t n, int nsig, float* d, 
 }
 
 constexpr int conv_smem(int cin) { return (cin * (kT + 8) + cin * kCnnK * kCnnC) * 4; }
+constexpr int fwd_smem(int cin) { return (cin * (kTP + 8) + cin * kCnnK * kCnnC) * 4; }
 
 cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16_t* wbf,
                              const float* params, cudaStream_t st) {
-  dim3 grid(io.L / kT, nsig);
+  dim3 grid((io.L + kTP - 1) / kTP, nsig);
   if (l == 0) {
-    k_conv_fwd<1><<<grid, kThreads, conv_smem(1), st>>>(io.in, io.pre, io.out, io.L,
-                                                        wbf + cnn_woff(0), params + cnn_boff(0));
+    k_conv_fwd<1><<<grid, kThreads, fwd_smem(1), st>>>(io.in, io.pre, io.out, io.L,
+                                                       wbf + cnn_woff(0), params + cnn_boff(0));
+  } else if (io.pre == nullptr && io.L % 16 == 0) {
+    // inference: tensor cores, BF16 activations
+    const int smem = ((kTP + 8) * kXR + kCnnK * kCnnC * kXR) * 2;
+    cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_conv_fwd_tc<<<grid, kThreads, smem, st>>>(io.in, io.out, io.L, wbf + cnn_woff(l),
+                                                params + cnn_boff(l));
   } else {
     cudaFuncSetAttribute(k_conv_fwd<kCnnC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         conv_smem(kCnnC));
-    k_conv_fwd<kCnnC><<<grid, kThreads, conv_smem(kCnnC), st>>>(
+                         fwd_smem(kCnnC));
+    k_conv_fwd<kCnnC><<<grid, kThreads, fwd_smem(kCnnC), st>>>(
         io.in, io.pre, io.out, io.L, wbf + cnn_woff(l), params + cnn_boff(l));
   }
   TDE_COUNT_LAUNCH(1);
@@ -516,7 +684,7 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st) {
-  const int smem = (kCnnC * Lf + kCnnC * 3 * Lf) * 4;
+  const int smem = (kCnnC * Lf + kCnnC * 3 * Lf + 4 * (2 * Lf + 7)) * 4;
   cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_scores<<<npairs, kThreads, smem, st>>>(feat, Lf, params, scores);
   TDE_COUNT_LAUNCH(1);

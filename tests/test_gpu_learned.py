@@ -124,3 +124,31 @@ def test_learned_estimate_windows_and_fallback(ctx):
     for p in range(6):
         assert (int(lags[p]), int(vals[p])) == oracle.estimate(xs[p], ys[p], 2)
     m.close()
+
+
+def test_inference_proposal_matches_reference_top_bin(ctx):
+    """The inference forward (tensor cores, BF16 activations) proposes the same
+    best bin as the float64 reference of the trained model, and its margin is
+    within 1e-2 of the reference's."""
+    import os
+    ck = os.path.join(os.path.dirname(tde.__file__), "models", "proposal_n65536_b2.npz")
+    z = np.load(ck)
+    n = 65536
+    m = tde.Model(ctx, n)
+    m.load(ck)
+    x, y, d = tde.synth_pairs(ctx, 31, 0, 4, n, 16384, (0.5, 0.9), (10.0, 30.0))
+    q2 = tde.tde_quantize_batch(ctx, torch.stack([x, y], dim=1).reshape(-1, n).contiguous(), 2)
+    cent, marg = m.propose(q2)
+    torch.cuda.synchronize()
+    params = z["params"].astype(np.float64)
+    for (wo, bo, cin) in cnn_ref.layout()[0]:
+        params[wo:bo] = cnn_ref.bf16_round(z["params"][wo:bo]).astype(np.float64)
+    _, s = cnn_ref.forward(torch.tensor(params), q2.cpu().numpy())
+    s = s.numpy()
+    Lf = n // 256
+    for p in range(4):
+        top = np.argsort(-s[p], kind="stable")[:8]
+        assert int(cent[p, 0]) == 256 * (int(top[0]) - (Lf - 1))
+        e = np.exp(s[p] - s[p].max())
+        assert abs(float(marg[p]) - e[top].sum() / e.sum()) < 1e-2
+    m.close()
