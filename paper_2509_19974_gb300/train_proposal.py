@@ -62,11 +62,17 @@ def main():
                                                   "proposal_n65536_b2.npz"))
     ap.add_argument("--log", default=None)
     ap.add_argument("--miss-budget", type=float, default=0.0005)
+    ap.add_argument("--calibrate-only", default=None,
+                    help="load this checkpoint, skip training, recalibrate and retest")
     args = ap.parse_args()
     build.build()
     ctx = tde.Context(0)
     model = tde.Model(ctx, N, seed=SEED)
-    steps = args.pairs // args.batch
+    steps = 0 if args.calibrate_only else args.pairs // args.batch
+    prev_meta = {}
+    if args.calibrate_only:
+        model.load(args.calibrate_only)
+        prev_meta = json.loads(str(np.load(args.calibrate_only)["meta"]))
     warm = min(200, steps // 10 + 1)
     log = []
     t0 = time.time()
@@ -120,9 +126,10 @@ def main():
     st = model.state()
     np.savez(args.out, n=N, params=st["params"], adam_m=st["adam_m"], adam_v=st["adam_v"],
              step=st["step"], theta=theta,
-             meta=json.dumps({"train_pairs": steps * args.batch, "batch": args.batch,
-                              "lr": args.lr, "train_seconds": train_s, "seed": SEED,
-                              "calibration": cal, "test": test}))
+             meta=json.dumps({"train_pairs": prev_meta.get("train_pairs", steps * args.batch),
+                              "batch": args.batch, "lr": args.lr,
+                              "train_seconds": prev_meta.get("train_seconds", train_s),
+                              "seed": SEED, "calibration": cal, "test": test}))
     if args.log:
         with open(args.log, "w") as f:
             json.dump({"log": log, "calibration": cal, "test": test, "train_s": train_s}, f)
