@@ -1,7 +1,7 @@
 /*
  * tde.h -- C ABI of the GB300 time-difference estimator (libtde.so).
  *
- * The estimator is Algorithm 1 (lines 1-4) of "On the Invariance of
+ * The estimator is Algorithm 1 of "On the Invariance of
  * Cross-Correlation Peak Positions Under Monotonic Signal Transformations,
  * with Application to Fast Time Difference Estimation" (arXiv 2509.19974):
  *   1-2. quantize both signals with a monotone non-decreasing integer map phi
@@ -26,7 +26,7 @@
  *  - A context is bound to one device and is not thread-safe: use one context
  *    per host thread.  Calls on one context must not overlap in time on
  *    different streams, because they share the context's workspace.
- *  - Quantization levels (Algorithm 1, line 1, phi : R -> Z):
+ *  - Quantization levels (Algorithm 1's level map, phi : R -> Z):
  *      bits = 1: q = sign(x), with sign(0) = sign(-0.0) = 0 (Sec. 4.2).
  *      bits = 2, 4: sign-magnitude rank quantizer with L = 2^bits - 1 levels:
  *        a = |x| sorted ascending, t_m = a[min(n-1, floor((2m-1) n / L))]
@@ -100,12 +100,43 @@ tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
 tde_status tde_ctx_read_profile(tde_ctx* ctx, int64_t* kernel_launches, int64_t* engine_launches,
                                 double* engine_ms);
 
+/* One autotuner measurement: for `bits` and a pair of min(nx, ny) = 2^log2_n
+ * samples asking 2^log2_lags lags, the engine TDE_ENGINE_AUTO uses and the
+ * measured device time per pair of each engine in ns (index by TDE_ENGINE_*;
+ * entry 0 unused; < 0: not measured or not supported). */
+typedef struct {
+  int32_t bits;
+  int32_t log2_n;
+  int32_t log2_lags;
+  int32_t engine;
+  float ns_per_pair[4];
+} tde_tune_entry;
+
+/* Autotune the engine choice: for each of the npoints (n[i], lag_count[i])
+ * (host arrays; equal-length pairs of n[i] samples, lag_count[i] lags
+ * centred on 0) time every exact engine on a batch of random levels sized to
+ * fill the GPU (best of `reps` runs) and record the fastest in the context.
+ * From then on TDE_ENGINE_AUTO (in every call on this context) takes the
+ * engine of the recorded point nearest in (log2 n, log2 lags) for the same
+ * bits, falling back to the built-in rule when no point has those bits.
+ * Synchronizes the device; allocates and frees its own device buffers. */
+tde_status tde_autotune(tde_ctx* ctx, int bits, const int64_t* n, const int64_t* lag_count,
+                        int npoints, int reps);
+/* Copy the context's table (host array of capacity `cap`); *count receives
+ * the number of entries. */
+tde_status tde_autotune_table(const tde_ctx* ctx, tde_tune_entry* out, int cap, int* count);
+/* Replace the context's table by `count` entries (e.g. a cached table). */
+tde_status tde_autotune_load(tde_ctx* ctx, const tde_tune_entry* entries, int count);
+/* The engine TDE_ENGINE_AUTO runs on this context (its autotuner table, else
+ * the built-in rule of tde_pick_engine); -1 if the arguments are invalid. */
+int tde_ctx_pick_engine(const tde_ctx* ctx, int bits, int64_t nx, int64_t ny, int64_t lag_count);
+
 /* The engine TDE_ENGINE_AUTO picks for one pair of lengths nx, ny, `bits`
  * and lag_count lags (host-only, enqueues nothing).  Returns a
  * TDE_ENGINE_* value, or -1 if the arguments are invalid. */
 int tde_pick_engine(int bits, int64_t nx, int64_t ny, int64_t lag_count);
 
-/* Algorithm 1, lines 1-2.  x: n floats (device).  q_out: n int8 (device).
+/* Algorithm 1's quantization step.  x: n floats (device).  q_out: n int8 (device).
  * bits in {1, 2, 4}.  NaN/Inf inputs are latched as TDE_ERR_INVALID (see
  * tde_ctx_sync) and the output is then unspecified. */
 tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits, int8_t* q_out,
@@ -146,7 +177,7 @@ tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n, int nsig,
 tde_status tde_quantize_noalloc(const float* x, int64_t n, int nsig, int bits, int8_t* q_out,
                                 uint32_t* status_out, tde_stream_t stream);
 
-/* Algorithm 1, line 3 / Eq. (1) on quantized input.  qx: nx int8, qy: ny int8
+/* Algorithm 1's correlation step / Eq. (1) on quantized input.  qx: nx int8, qy: ny int8
  * (device), with |q| <= 2^(bits-1) - 1 (1 for bits <= 2, 7 for bits = 4).
  * Computes c[tau] for lag_min <= tau <= lag_max, which must lie inside
  * [-(nx-1), ny-1].  c_out: (lag_max - lag_min + 1) elements of `out_dtype`
@@ -156,14 +187,14 @@ tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, const int8_
                          int64_t ny, int bits, int64_t lag_min, int64_t lag_max, int engine,
                          void* c_out, int out_dtype, tde_stream_t stream);
 
-/* Algorithm 1, line 4.  c: `count` elements of `dtype` (device), element i
+/* Algorithm 1's argmax step.  c: `count` elements of `dtype` (device), element i
  * holding lag lag_min + i.  Writes the maximising lag and its value to
  * lag_out[0] and val_out[0] (device int64).  Ties go to the smallest |tau|,
  * then to the smallest tau.  count >= 1 and |lag| < 2^31 are required. */
 tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t lag_min, int64_t count,
                       int64_t* lag_out, int64_t* val_out, tde_stream_t stream);
 
-/* Algorithm 1, lines 1-4 for one pair.  x: nx floats, y: ny floats (device).
+/* Algorithm 1 for one pair.  x: nx floats, y: ny floats (device).
  * Lags lag_min..lag_max as in tde_xcorr_int.  lag_out[0], val_out[0]: device
  * int64.  Intermediate quantized signals and correlations live in the
  * context's workspace. */
@@ -194,7 +225,7 @@ typedef struct {
   int64_t lag_max;
 } tde_pair_desc;
 
-/* Algorithm 1, lines 1-4 for `npairs` independent pairs of possibly uneven
+/* Algorithm 1 for `npairs` independent pairs of possibly uneven
  * lengths and lag ranges.  descs: host array of npairs descriptors.
  * lag_out, val_out: npairs int64 each (device).  If c_out is not NULL it
  * receives every pair's correlation as int32, pair after pair (pair p starts
@@ -230,7 +261,7 @@ tde_status tde_batch_destroy(tde_batch* batch);
  * likely 257-lag windows; the exact integer correlation (Eq. 1) is then
  * evaluated only inside them, and over the full range when the proposal's
  * confidence is low.  The returned lag is always the tie-ruled maximiser of
- * exact integer values (Algorithm 1, line 4) over the lags evaluated.
+ * exact integer values (Algorithm 1's argmax step) over the lags evaluated.
  *
  * Architecture (weights shared by x and y): d[i] = (sum of 16 levels) / 4;
  * 4 x [conv1d kernel 9, padding 4, 32 channels, bias, ReLU, max-pool 2] ->
@@ -274,7 +305,7 @@ tde_status tde_train_step(tde_ctx* ctx, tde_model* model, const int8_t* q, int n
 tde_status tde_propose(tde_ctx* ctx, const tde_model* model, const int8_t* q, int npairs,
                        int32_t* centres, float* margin, tde_stream_t stream);
 
-/* Algorithm 1, lines 1-4 with the proposal, for npairs pairs of n samples
+/* Algorithm 1 with the proposal, for npairs pairs of n samples
  * (x, y: npairs * n floats each, device, pair after pair; all lags).  Pairs
  * whose margin is below theta (theta > 1: all pairs) are re-estimated with the
  * full correlation (tde_estimate_batch, AUTO engine) and flagged in

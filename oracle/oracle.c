@@ -7,17 +7,17 @@
  *
  * What it computes (paper: "On the Invariance of Cross-Correlation Peak
  * Positions Under Monotonic Signal Transformations", arXiv 2509.19974):
- *   oracle_quantize   Algorithm 1, lines 1-2: u = phi(x), a monotone
+ *   oracle_quantize   Algorithm 1's quantization step: u = phi(x), a monotone
  *                     non-decreasing integer map with phi(0) = 0.
  *                     bits = 1 is sign() with sign(0) = 0 (Sec. 4.2);
  *                     bits = 2, 4 is the sign-magnitude rank quantizer
  *                     (equal-population thresholds on |x|, 2^b - 1 levels),
  *                     a reading of the paper's "any quantization scheme,
  *                     including nonuniform" (Sec. 3.2).
- *   oracle_xcorr      Algorithm 1, line 3 / Eq. (1): the cross-correlation
+ *   oracle_xcorr      Algorithm 1's correlation step / Eq. (1): the cross-correlation
  *                     (u * v)[tau] = sum_m u[m] v[m + tau], exact in int64,
  *                     written as the direct double loop over the overlap.
- *   oracle_argmax     Algorithm 1, line 4: the maximiser; the paper returns
+ *   oracle_argmax     Algorithm 1's argmax step: the maximiser; the paper returns
  *                     the whole set of maximisers, this collapses it to one
  *                     lag: smallest |tau|, then smallest tau.
  * Parity: pinned by tests/test_oracle_pins.py (brute force, library
@@ -63,7 +63,7 @@ int oracle_rank_thresholds(const float* x, int64_t n, int bits, float* t) {
   return ORACLE_OK;
 }
 
-/* Algorithm 1, lines 1-2. */
+/* Algorithm 1's quantization step. */
 int oracle_quantize(const float* x, int64_t n, int bits, int8_t* q) {
   if (n <= 0) return ORACLE_ERR_INVALID;
   if (bits == 1) {
@@ -118,7 +118,7 @@ void oracle_xcorr_at(const int8_t* qx, int64_t nx, const int8_t* qy, int64_t ny,
   }
 }
 
-/* Algorithm 1, line 4, with the maximiser set collapsed to one lag:
+/* Algorithm 1's argmax step, with the maximiser set collapsed to one lag:
  * largest value; among equal values the smallest |tau|; then smallest tau. */
 void oracle_argmax(const int64_t* c, int64_t lag_min, int64_t count,
                    int64_t* lag_out, int64_t* val_out) {

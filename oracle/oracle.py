@@ -1,10 +1,10 @@
 """ctypes wrapper of ``oracle.c`` -- test infrastructure only (see package doc).
 
 Every function follows the paper (arXiv 2509.19974) literally:
-  quantize        Algorithm 1, lines 1-2 (sign with sign(0)=0, Sec. 4.2; or
+  quantize        Algorithm 1's quantization step (sign with sign(0)=0, Sec. 4.2; or
                   the sign-magnitude rank quantizer, Sec. 3.2 "any scheme").
   xcorr/xcorr_at  Eq. (1) on the quantized sequences, direct int64 sums.
-  argmax          Algorithm 1, line 4, ties -> smallest |tau| then tau.
+  argmax          Algorithm 1's argmax step, ties -> smallest |tau| then tau.
 Pinned by tests/test_oracle_pins.py.
 """
 from __future__ import annotations
@@ -115,7 +115,7 @@ def argmax(c: np.ndarray, lag_min: int) -> tuple[int, int]:
 
 def estimate(x: np.ndarray, y: np.ndarray, bits: int, lag_min: int | None = None,
              lag_max: int | None = None) -> tuple[int, int]:
-    """Algorithm 1, lines 1-4: quantize both signals, correlate, argmax."""
+    """Algorithm 1: quantize both signals, correlate, argmax."""
     qx, qy = quantize(x, bits), quantize(y, bits)
     lo, hi = full_lag_range(qx.shape[0], qy.shape[0])
     lag_min = lo if lag_min is None else lag_min

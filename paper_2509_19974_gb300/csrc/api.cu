@@ -33,6 +33,7 @@ struct tde_ctx {
   int64_t launches = 0, engine_launches = 0;
   FftPlan fft;
   uint32_t* ntt_tables[kNttMaxLog + 1] = {};  // per log2 length, 8 * N uint32
+  std::vector<tde_tune_entry> tune;           // autotuner table (empty: built-in rule)
 };
 
 thread_local int64_t tde_launch_counter = 0;
@@ -731,6 +732,28 @@ int pick_engine(int engine, int bits, int64_t nx, int64_t ny, int64_t lag_count)
   return (n >= 1024 && lag_count >= need) ? TDE_ENGINE_MMA : TDE_ENGINE_POPC;
 }
 
+int ilog2_round(int64_t v) {
+  int l = 0;
+  while (((int64_t)1 << (l + 1)) <= v) ++l;
+  // round to the nearer power of two
+  if (l < 62 && v - ((int64_t)1 << l) > ((int64_t)1 << (l + 1)) - v) ++l;
+  return l;
+}
+
+// AUTO with the context's autotuner table when it has entries for `bits`.
+int pick_engine_ctx(const tde_ctx* ctx, int engine, int bits, int64_t nx, int64_t ny,
+                    int64_t lag_count) {
+  if (engine != TDE_ENGINE_AUTO || ctx->tune.empty()) return pick_engine(engine, bits, nx, ny, lag_count);
+  const int ln = ilog2_round(nx < ny ? nx : ny), ll = ilog2_round(lag_count);
+  int best = -1, bd = 1 << 30;
+  for (const tde_tune_entry& t : ctx->tune) {
+    if (t.bits != bits) continue;
+    const int d = std::abs(t.log2_n - ln) + std::abs(t.log2_lags - ll);
+    if (d < bd) bd = d, best = t.engine;
+  }
+  return best >= 0 ? best : pick_engine(engine, bits, nx, ny, lag_count);
+}
+
 tde_status engine_available(tde_ctx* ctx, int engine) {
   if (engine == TDE_ENGINE_POPC || engine == TDE_ENGINE_MMA || engine == TDE_ENGINE_NTT)
     return TDE_OK;
@@ -800,7 +823,7 @@ extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, 
   if (!qx || !qy || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   tde_status s = check_xcorr_args(ctx, nx, ny, bits, lag_min, lag_max, engine, out_dtype);
   if (s != TDE_OK) return s;
-  const int eng = pick_engine(engine, bits, nx, ny, lag_max - lag_min + 1);
+  const int eng = pick_engine_ctx(ctx, engine, bits, nx, ny, lag_max - lag_min + 1);
   if ((s = engine_available(ctx, eng)) != TDE_OK) return s;
   DeviceGuard g(ctx->device);
   LaunchCount lc(ctx);
@@ -849,7 +872,7 @@ extern "C" tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t
 
 namespace {
 
-// Everything one batch (Algorithm 1, lines 1-4 over many pairs) needs, planned
+// Everything one batch (Algorithm 1 over many pairs) needs, planned
 // from the descriptors alone; pointers are bound by fill() once memory exists.
 struct BatchWork {
   int npairs = 0, bits = 1;
@@ -879,7 +902,7 @@ tde_status batch_plan(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int 
     s = check_xcorr_args(ctx, d.nx, d.ny, bits, d.lag_min, d.lag_max, engine, TDE_I32);
     if (s != TDE_OK) return s;
     const int64_t cnt = d.lag_max - d.lag_min + 1;
-    w->engs[p] = pick_engine(engine, bits, d.nx, d.ny, cnt);
+    w->engs[p] = pick_engine_ctx(ctx, engine, bits, d.nx, d.ny, cnt);
     if ((s = engine_available(ctx, w->engs[p])) != TDE_OK) return s;
     max_n = std::max(max_n, std::max(d.nx, d.ny));
     max_count = std::max(max_count, cnt);
@@ -1480,5 +1503,129 @@ extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, con
     TDE_CK(cudaFreeAsync(idx, st));
   }
   TDE_CK(cudaStreamSynchronize(st));  // host vectors above must outlive their copies
+  return TDE_OK;
+}
+
+// ================================================================ autotuner
+
+namespace {
+
+__global__ void k_random_levels(int8_t* q, int64_t n, int bits, uint64_t seed) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int k = bits == 4 ? 7 : 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint64_t z = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    q[i] = (int8_t)((int)(z % (uint64_t)(2 * k + 1)) - k);
+  }
+}
+
+}  // namespace
+
+extern "C" tde_status tde_autotune(tde_ctx* ctx, int bits, const int64_t* n,
+                                   const int64_t* lag_count, int npoints, int reps) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!valid_bits(bits) || !n || !lag_count || npoints <= 0 || reps <= 0)
+    return set_err(ctx, TDE_ERR_INVALID, "bad autotune arguments");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = nullptr;
+  TDE_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  TDE_CK(cudaEventCreate(&e0));
+  TDE_CK(cudaEventCreate(&e1));
+  std::vector<tde_tune_entry> found;
+  tde_status result = TDE_OK;
+  for (int i = 0; i < npoints && result == TDE_OK; ++i) {
+    const int64_t N = n[i];
+    const int64_t lags = std::min<int64_t>(std::max<int64_t>(lag_count[i], 1), 2 * N - 1);
+    if (N <= 0 || N > INT32_MAX) {
+      result = set_err(ctx, TDE_ERR_INVALID, "autotune point %d: bad length", i);
+      break;
+    }
+    const int64_t lo = -(lags / 2), hi = lo + lags - 1;
+    const double work = (double)N * (double)lags;
+    const int B = (int)std::max<double>(1.0, std::min<double>(512.0, 2e11 / work));
+    int8_t* q = nullptr;
+    int32_t* c = nullptr;
+    if (cudaMalloc(&q, (size_t)2 * B * N) != cudaSuccess ||
+        cudaMalloc(&c, sizeof(int32_t) * (size_t)B * lags) != cudaSuccess) {
+      cudaFree(q);
+      result = set_err(ctx, TDE_ERR_CUDA, "autotune allocation failed");
+      break;
+    }
+    k_random_levels<<<1024, 256, 0, st>>>(q, 2 * B * N, bits, 12345 + i);
+    tde_tune_entry te{bits, ilog2_round(N), ilog2_round(lags), TDE_ENGINE_POPC, {-1.f, -1.f, -1.f, -1.f}};
+    float best = -1.f;
+    for (int eng = TDE_ENGINE_POPC; eng <= TDE_ENGINE_NTT; ++eng) {
+      std::vector<Job> jobs(B);
+      for (int b = 0; b < B; ++b)
+        jobs[b] = Job{q + (int64_t)(2 * b) * N, q + (int64_t)(2 * b + 1) * N, N, N, lo, hi,
+                      c + (int64_t)b * lags, 0};
+      Layout L;
+      XcorrStage E;
+      if (!E.plan(L, jobs, std::vector<int>(B, eng), bits)) continue;  // engine cannot serve it
+      Bases Bs;
+      if (realize(ctx, L, &Bs) != TDE_OK) continue;
+      E.fill(Bs, jobs);
+      if (stage_upload(ctx, Bs.ddesc, L.desc, st) != TDE_OK) continue;
+      float ms_best = -1.f;
+      for (int r = 0; r <= reps; ++r) {  // the first run warms up
+        cudaEventRecord(e0, st);
+        const cudaError_t le = E.launch(ctx, Bs, st);
+        cudaEventRecord(e1, st);
+        if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          ms_best = -1.f;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && (ms_best < 0.f || ms < ms_best)) ms_best = ms;
+      }
+      if (ms_best < 0.f) continue;
+      te.ns_per_pair[eng] = ms_best * 1e6f / (float)B;
+      if (best < 0.f || te.ns_per_pair[eng] < best) best = te.ns_per_pair[eng], te.engine = eng;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(q);
+    cudaFree(c);
+    found.push_back(te);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (result != TDE_OK) return result;
+  // replace the entries of these bits, keep the others
+  std::vector<tde_tune_entry> keep;
+  for (const tde_tune_entry& t : ctx->tune)
+    if (t.bits != bits) keep.push_back(t);
+  keep.insert(keep.end(), found.begin(), found.end());
+  ctx->tune = keep;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_autotune_table(const tde_ctx* ctx, tde_tune_entry* out, int cap,
+                                         int* count) {
+  if (!ctx || !count) return TDE_ERR_INVALID;
+  *count = (int)ctx->tune.size();
+  if (out)
+    for (int i = 0; i < cap && i < (int)ctx->tune.size(); ++i) out[i] = ctx->tune[i];
+  return TDE_OK;
+}
+
+extern "C" int tde_ctx_pick_engine(const tde_ctx* ctx, int bits, int64_t nx, int64_t ny,
+                                   int64_t lag_count) {
+  if (!ctx || !valid_bits(bits) || nx <= 0 || ny <= 0 || lag_count <= 0) return -1;
+  return pick_engine_ctx(ctx, TDE_ENGINE_AUTO, bits, nx, ny, lag_count);
+}
+
+extern "C" tde_status tde_autotune_load(tde_ctx* ctx, const tde_tune_entry* entries, int count) {
+  if (!ctx || count < 0 || (count > 0 && !entries)) return TDE_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (!valid_bits(entries[i].bits) || entries[i].engine < TDE_ENGINE_POPC ||
+        entries[i].engine > TDE_ENGINE_NTT)
+      return set_err(ctx, TDE_ERR_INVALID, "bad autotune entry %d", i);
+  ctx->tune.assign(entries, entries + count);
   return TDE_OK;
 }

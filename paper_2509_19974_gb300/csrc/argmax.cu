@@ -1,4 +1,4 @@
-// argmax.cu -- Algorithm 1, line 4 (arXiv 2509.19974): the maximiser of the
+// argmax.cu -- Algorithm 1's argmax step (arXiv 2509.19974): the maximiser of the
 // integer correlation, collapsed to one lag by a fixed rule: largest value,
 // then smallest |tau|, then smallest tau.
 //

@@ -2,7 +2,7 @@
 // windowed exact correlation that checks its proposals.
 //
 // The proposal only decides WHERE the exact integer correlation of
-// Algorithm 1, line 3 (arXiv 2509.19974) is evaluated: the lag returned is
+// Algorithm 1's correlation step (arXiv 2509.19974) is evaluated: the lag returned is
 // always the tie-ruled maximiser of exact integer values, either inside the
 // proposed windows or, when the proposal's confidence (softmax mass of its top
 // 8 bins) is below a threshold, over the full lag range.

@@ -1,4 +1,4 @@
-// mma.cu -- exact integer cross-correlation (Algorithm 1, line 3; Eq. (1) of
+// mma.cu -- exact integer cross-correlation (Algorithm 1's correlation step; Eq. (1) of
 // arXiv 2509.19974) as a Toeplitz-structured GEMM on the 5th-generation
 // tensor cores (tcgen05.mma, accumulators in tensor memory).
 //

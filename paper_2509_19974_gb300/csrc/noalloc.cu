@@ -1,4 +1,4 @@
-// noalloc.cu -- tde_quantize_noalloc: the quantizer (Algorithm 1, lines 1-2)
+// noalloc.cu -- tde_quantize_noalloc: the quantizer (Algorithm 1's quantization step)
 // for callers that cannot allocate device memory.
 //
 // Every other entry point works through a tde_ctx, and a context allocates:

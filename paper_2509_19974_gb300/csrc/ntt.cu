@@ -1,4 +1,4 @@
-// ntt.cu -- exact integer cross-correlation (Algorithm 1, line 3; Eq. (1) of
+// ntt.cu -- exact integer cross-correlation (Algorithm 1's correlation step; Eq. (1) of
 // arXiv 2509.19974) by number-theoretic transforms, one of the paper's
 // "multimodular method based on the Chinese remainder theorem" routes
 // (Sec. 3.2), built for the GPU.

@@ -1,5 +1,5 @@
-// popc.cu -- direct integer cross-correlation on bit planes (Algorithm 1,
-// line 3; Eq. (1) of arXiv 2509.19974), exact, for short signals and for the
+// popc.cu -- direct integer cross-correlation on bit planes (Algorithm 1's
+// correlation step; Eq. (1) of arXiv 2509.19974), exact, for short signals and for the
 // windowed/edge cases where a GEMM tile would be mostly empty.
 //
 // Representation: q = s * m with s = (-1)^sign and m = |q| given by bit planes

@@ -1,4 +1,4 @@
-// quantize.cu -- Algorithm 1, lines 1-2 (arXiv 2509.19974, Sec. 3.2): the
+// quantize.cu -- Algorithm 1's quantization step (arXiv 2509.19974, Sec. 3.2): the
 // monotone integer maps phi, psi with phi(0) = psi(0) = 0.
 //
 //  bits = 1: q = sign(x), sign(0) = 0 (the quantizer of Sec. 4.2).  One pass.

@@ -31,7 +31,8 @@ EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error"
            "tde_estimate", "tde_estimate_batch", "tde_batch_create", "tde_batch_run",
            "tde_batch_destroy", "tde_model_param_count", "tde_model_create", "tde_model_destroy",
            "tde_model_get", "tde_model_set", "tde_train_step", "tde_propose",
-           "tde_estimate_learned", "tde_synth_pairs")
+           "tde_estimate_learned", "tde_synth_pairs", "tde_autotune", "tde_autotune_table",
+           "tde_autotune_load", "tde_ctx_pick_engine")
 
 
 class TdeError(RuntimeError):
@@ -43,6 +44,11 @@ class TdeError(RuntimeError):
 class PairDesc(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("nx", ctypes.c_int64),
                 ("ny", ctypes.c_int64), ("lag_min", ctypes.c_int64), ("lag_max", ctypes.c_int64)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("bits", ctypes.c_int32), ("log2_n", ctypes.c_int32), ("log2_lags", ctypes.c_int32),
+                ("engine", ctypes.c_int32), ("ns_per_pair", ctypes.c_float * 4)]
 
 
 _lib = None
@@ -88,6 +94,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_estimate_learned": ([p, p, p, p, i32, i32, f32, p, p, p, p], st),
         "tde_synth_pairs": ([p, ctypes.c_uint64, i64, i32, i64, i64, f32, f32, f32, f32, p, p, p,
                              p], st),
+        "tde_autotune": ([p, i32, p, p, i32, i32], st),
+        "tde_autotune_table": ([p, p, i32, p], st),
+        "tde_autotune_load": ([p, p, i32], st),
+        "tde_ctx_pick_engine": ([p, i32, i64, i64, i64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -178,6 +188,111 @@ class Context:
     def estimate_batch(self, xs, ys, bits, lag_mins=None, lag_maxs=None, engine="auto",
                        c_out=None, stream=None):
         return tde_estimate_batch(self, xs, ys, bits, lag_mins, lag_maxs, engine, c_out, stream)
+
+    # --- autotuner ---------------------------------------------------------
+    def autotune(self, bits: int, points, reps: int = 3):
+        """Times every exact engine at each (n, lag_count) of ``points`` and
+        makes AUTO use the fastest (nearest point in log2 n, log2 lags).
+        Returns the context's table (``autotune_table``)."""
+        n = (ctypes.c_int64 * len(points))(*[int(p[0]) for p in points])
+        lags = (ctypes.c_int64 * len(points))(*[int(p[1]) for p in points])
+        self.check(self.lib.tde_autotune(self.handle, int(bits), ctypes.addressof(n),
+                                         ctypes.addressof(lags), len(points), int(reps)))
+        return self.autotune_table()
+
+    def autotune_table(self):
+        """The table as a list of dicts (bits, log2_n, log2_lags, engine,
+        ns_per_pair {engine name: ns or None})."""
+        cnt = ctypes.c_int()
+        self.check(self.lib.tde_autotune_table(self.handle, None, 0, ctypes.byref(cnt)))
+        arr = (TuneEntry * max(cnt.value, 1))()
+        self.check(self.lib.tde_autotune_table(self.handle, ctypes.addressof(arr), cnt.value,
+                                               ctypes.byref(cnt)))
+        return [entry_to_dict(arr[i]) for i in range(cnt.value)]
+
+    def pick_engine(self, bits: int, nx: int, ny: int, lag_count: int) -> str:
+        """Name of the engine AUTO runs for such a pair on this context."""
+        e = self.lib.tde_ctx_pick_engine(self.handle, int(bits), int(nx), int(ny), int(lag_count))
+        if e < 0:
+            raise ValueError("invalid arguments")
+        return ENGINE_NAMES[e]
+
+    def autotune_load(self, table):
+        """Installs a table (as returned by ``autotune_table``)."""
+        arr = (TuneEntry * max(len(table), 1))()
+        for i, d in enumerate(table):
+            arr[i] = dict_to_entry(d)
+        self.check(self.lib.tde_autotune_load(self.handle, ctypes.addressof(arr), len(table)))
+
+
+def entry_to_dict(e: TuneEntry) -> dict:
+    return {"bits": int(e.bits), "log2_n": int(e.log2_n), "log2_lags": int(e.log2_lags),
+            "engine": ENGINE_NAMES[int(e.engine)],
+            "ns_per_pair": {ENGINE_NAMES[k]: (float(e.ns_per_pair[k]) if e.ns_per_pair[k] >= 0
+                                              else None) for k in (1, 2, 3)}}
+
+
+def dict_to_entry(d: dict) -> TuneEntry:
+    e = TuneEntry()
+    e.bits, e.log2_n, e.log2_lags = int(d["bits"]), int(d["log2_n"]), int(d["log2_lags"])
+    e.engine = _engine(d["engine"])
+    e.ns_per_pair[0] = -1.0
+    for name, v in d.get("ns_per_pair", {}).items():
+        e.ns_per_pair[ENGINES[name]] = -1.0 if v is None else float(v)
+    return e
+
+
+# Points the default autotune measures: min length 2^k and lag counts from a
+# narrow search window up to the full range.
+DEFAULT_TUNE_POINTS = tuple((1 << k, min(lags, 2 * (1 << k) - 1))
+                            for k in (10, 12, 14, 16, 18, 20)
+                            for lags in (256, 2048, 16384, 1 << 17, 1 << 21)
+                            if lags <= 2 * (1 << k) - 1 or lags == 1 << 21)
+
+
+def tune_cache_key(device: int) -> str:
+    """Key of a cached table: device name, SM count, CUDA runtime and the
+    library digest (a rebuilt library re-tunes)."""
+    prop = torch.cuda.get_device_properties(device)
+    digest = ""
+    stamp = os.path.join(_PKG, "_build", "stamp")
+    if os.path.exists(stamp):
+        with open(stamp) as f:
+            digest = f.read().strip()[:16]
+    return f"{prop.name}|sm{prop.multi_processor_count}|cuda{torch.version.cuda}|{digest}"
+
+
+def autotune_cached(ctx: Context, bits_list=(1, 2, 4), points=DEFAULT_TUNE_POINTS,
+                    path: str | None = None, reps: int = 3):
+    """Loads the table for this device from the JSON cache at ``path``
+    (default: ``$TDE_TUNE_CACHE`` or ~/.cache/tde_autotune.json), or measures
+    it with ``Context.autotune`` and stores it there."""
+    import json
+    path = path or os.environ.get("TDE_TUNE_CACHE",
+                                  os.path.join(os.path.expanduser("~"), ".cache",
+                                               "tde_autotune.json"))
+    key = tune_cache_key(ctx.device)
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    table = cache.get(key)
+    if table and {int(t["bits"]) for t in table} >= set(bits_list):
+        ctx.autotune_load(table)
+        return table
+    for b in bits_list:
+        ctx.autotune(b, points, reps)
+    table = ctx.autotune_table()
+    cache[key] = table
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+    return table
 
 
 ENGINE_NAMES = {v: k for k, v in ENGINES.items()}

@@ -44,3 +44,22 @@ def test_bad_device_is_a_cuda_error(lib):
     h = ctypes.c_void_p()
     assert lib.tde_ctx_create(-1, ctypes.byref(h)) == tde.TDE_ERR_CUDA
     assert h.value is None
+
+
+def test_autotune_entries_round_trip_and_null_context(lib):
+    d = {"bits": 2, "log2_n": 16, "log2_lags": 17, "engine": "mma",
+         "ns_per_pair": {"popc": 1000.0, "mma": 50.0, "ntt": None}}
+    assert tde.entry_to_dict(tde.dict_to_entry(d)) == d
+    arr = (tde.TuneEntry * 1)(tde.dict_to_entry(d))
+    assert lib.tde_autotune_load(None, ctypes.addressof(arr), 1) == tde.TDE_ERR_INVALID
+    assert lib.tde_autotune(None, 2, None, None, 1, 1) == tde.TDE_ERR_INVALID
+    assert lib.tde_ctx_pick_engine(None, 2, 100, 100, 10) == -1
+    cnt = ctypes.c_int()
+    assert lib.tde_autotune_table(None, None, 0, ctypes.byref(cnt)) == tde.TDE_ERR_INVALID
+
+
+def test_default_autotune_points_are_valid():
+    pts = tde.DEFAULT_TUNE_POINTS
+    assert len(set(pts)) == len(pts)
+    for n, lags in pts:
+        assert n >= 1 and 1 <= lags <= 2 * n - 1

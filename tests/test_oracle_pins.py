@@ -131,7 +131,7 @@ def test_ccf_restricted_range_and_at():
     assert np.array_equal(oracle.xcorr(x, y, 500, 502), np.zeros(3, np.int64))
 
 
-# -------------------------------------------------- Algorithm 1, lines 1-2
+# -------------------------------------------------- Algorithm 1's quantization step
 
 def test_quantize_golden_hand_computed():
     for case in read_cases("quantize_small.txt"):
@@ -193,7 +193,7 @@ def test_quantize_rejects_nonfinite():
                 oracle.quantize(x, bits)
 
 
-# -------------------------------------------------- Algorithm 1, line 4
+# -------------------------------------------------- Algorithm 1's argmax step
 
 def test_argmax_tie_rule_cases():
     # constant: every lag ties -> 0 when 0 is in range
