@@ -508,7 +508,8 @@ std::vector<std::pair<int64_t, int64_t>> ntt_blocks(int logn, int64_t nt, int64_
   return out;
 }
 
-// False if no length up to 2^kNttMaxLog holds the template.
+// False if no length up to 2^kNttMaxLog holds the template with at least
+// N/8 outputs per overlap-save block.
 bool ntt_plan_pair(const Job& j, NttPlanPair* pp) {
   const bool tx = j.nx <= j.ny;  // template = x: R[k] = c[k]; else c[-k]
   pp->t = tx ? j.qx : j.qy;
@@ -520,7 +521,8 @@ bool ntt_plan_pair(const Job& j, NttPlanPair* pp) {
   double best = -1.0;
   for (int logn = kNttMinLog; logn <= kNttMaxLog; ++logn) {
     const int64_t N = (int64_t)1 << logn;
-    if (N < pp->nt) continue;
+    // a block must keep at least N/8 outputs (else the plan is mostly waste)
+    if (N - pp->nt + 1 < N / 8) continue;
     // count blocks without building the list
     int64_t nb = 0;
     for (int64_t S = k0; S <= k1 && nb < (1 << 22);) {
@@ -833,7 +835,7 @@ extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, 
   XcorrStage E;
   if (!E.plan(L, jobs, std::vector<int>{eng}, bits))
     return set_err(ctx, TDE_ERR_UNSUPPORTED,
-                   "NTT engine: the shorter signal exceeds the largest transform (2^%d)",
+                   "NTT engine: the shorter signal needs a transform above 2^%d",
                    kNttMaxLog);
   Bases B;
   if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
@@ -1559,6 +1561,7 @@ extern "C" tde_status tde_autotune(tde_ctx* ctx, int bits, const int64_t* n,
     tde_tune_entry te{bits, ilog2_round(N), ilog2_round(lags), TDE_ENGINE_POPC, {-1.f, -1.f, -1.f, -1.f}};
     float best = -1.f;
     for (int eng = TDE_ENGINE_POPC; eng <= TDE_ENGINE_NTT; ++eng) {
+      cudaGetLastError();  // an earlier engine's failure must not be charged to this one
       std::vector<Job> jobs(B);
       for (int b = 0; b < B; ++b)
         jobs[b] = Job{q + (int64_t)(2 * b) * N, q + (int64_t)(2 * b + 1) * N, N, N, lo, hi,
@@ -1567,7 +1570,10 @@ extern "C" tde_status tde_autotune(tde_ctx* ctx, int bits, const int64_t* n,
       XcorrStage E;
       if (!E.plan(L, jobs, std::vector<int>(B, eng), bits)) continue;  // engine cannot serve it
       Bases Bs;
-      if (realize(ctx, L, &Bs) != TDE_OK) continue;
+      if (realize(ctx, L, &Bs) != TDE_OK) {
+        cudaGetLastError();
+        continue;
+      }
       E.fill(Bs, jobs);
       if (stage_upload(ctx, Bs.ddesc, L.desc, st) != TDE_OK) continue;
       float ms_best = -1.f;
