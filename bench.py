@@ -43,7 +43,10 @@ SMS = 152          # GB300 SMs
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the engine kernel
 # from one ncu capture of this workload (see profiles/); None once the kernel
 # has changed since the capture.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of each form's dominant kernel, from one
+# ncu capture of this bench's workload (profiles/); keyed by (kernel, pairs,
+# N, bits).  Cleared whenever the kernel changes.
+TRAFFIC = {("mma", 256, 65536, 2): 491.7e6, ("win", 256, 65536, 2): 8.5e6}
 CKPT = os.path.join(ROOT, "paper_2509_19974_gb300", "models", "proposal_n65536_b2.npz")
 POPC_PER_SM_CLK = 16  # POPC issue rate per SM per clock
 
@@ -353,7 +356,8 @@ def main():
         ach = win_macs / (wms / max(wl, 1) / 1e3) if wl else None
         roof_l = None if ach is None else {
             "bound": "alu", "kernel": "k_xcorr_popc_win", "achieved": ach / 1e12,
-            "peak": peak_mac / 1e12, "unit": "TMAC/s", "frac": ach / peak_mac, "traffic": None,
+            "peak": peak_mac / 1e12, "unit": "TMAC/s", "frac": ach / peak_mac,
+            "traffic": TRAFFIC.get(("win", args.npairs, args.n, args.bits)),
             "peak_source": f"POPC pipe: {SMS} SMs x {POPC_PER_SM_CLK}/clk x "
                            f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock), "
                            "2 POPC per 32 ternary MACs",
