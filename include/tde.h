@@ -305,6 +305,16 @@ tde_status tde_train_step(tde_ctx* ctx, tde_model* model, const int8_t* q, int n
 tde_status tde_propose(tde_ctx* ctx, const tde_model* model, const int8_t* q, int npairs,
                        int32_t* centres, float* margin, tde_stream_t stream);
 
+/* Eq. (1) inside the proposal's windows, exactly: for pair p (x = q + 2 p n,
+ * y = q + (2 p + 1) n; q: 2 npairs n int8 levels, device, as tde_propose
+ * reads them) and window w with centre centres[8 p + w] (device int32),
+ * c_out[(8 p + w) * 257 + i] (device int32) = c[centre - 128 + i] for
+ * i in [0, 257); lags outside [-(n-1), n-1] read 0.  Computed on the tensor
+ * cores (BF16 operands, FP32 accumulation, exact for these levels).
+ * bits 1, 2 or 4. */
+tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npairs, int bits,
+                             const int32_t* centres, int32_t* c_out, tde_stream_t stream);
+
 /* Algorithm 1 with the proposal, for npairs pairs of n samples
  * (x, y: npairs * n floats each, device, pair after pair; all lags).  Pairs
  * whose margin is below theta (theta > 1: all pairs) are re-estimated with the

@@ -322,22 +322,35 @@ struct Bases {
 struct QuantStage {
   int nsig = 0, bits = 1;
   int64_t max_n = 0;
-  size_t o_sigs = 0, o_state = 0, o_hist = 0;
-  void plan(Layout& L, int n, int b, int64_t mx) {
+  bool fused = false, with_planes = false;
+  size_t o_sigs = 0, o_state = 0, o_hist = 0, o_planes = 0;
+  // with_planes: the fused form also writes bit planes (set_planes); callers
+  // must check planes_written() and pack themselves otherwise.
+  void plan(Layout& L, int n, int b, int64_t mx, bool want_planes = false) {
     nsig = n, bits = b, max_n = mx;
+    fused = quantize_fused_ok(bits, max_n);
+    with_planes = fused && want_planes;
     o_sigs = L.d<QSig>(nsig);
-    if (bits != 1) {
+    if (with_planes) o_planes = L.d<QPlanes>(nsig);
+    if (bits != 1 && !fused) {
       o_state = L.w<RankState>(nsig);
       o_hist = L.w<uint32_t>((size_t)nsig * 7 * 2048);
     }
   }
+  bool planes_written() const { return with_planes; }
   void fill(const Bases& B, const float* const* xs, int8_t* const* qs, const int64_t* ns) const {
     QSig* h = B.hd<QSig>(o_sigs);
     for (int i = 0; i < nsig; ++i) h[i] = QSig{xs[i], qs[i], ns[i]};
   }
+  void set_planes(const Bases& B, int i, uint32_t* planes, int64_t words) const {
+    if (with_planes) B.hd<QPlanes>(o_planes)[i] = QPlanes{planes, words};
+  }
   cudaError_t launch(const Bases& B, uint32_t* status, cudaStream_t st) const {
     if (nsig == 0) return cudaSuccess;
     if (bits == 1) return launch_quantize_sign(B.dd<QSig>(o_sigs), nsig, max_n, status, st);
+    if (fused)
+      return launch_quantize_fused(B.dd<QSig>(o_sigs), with_planes ? B.dd<QPlanes>(o_planes) : nullptr,
+                                   nsig, max_n, bits, status, st);
     return launch_quantize_rank(B.dd<QSig>(o_sigs), nsig, max_n, bits, B.dw<RankState>(o_state),
                                 B.dw<uint32_t>(o_hist), status, st);
   }
@@ -397,10 +410,16 @@ struct PopcStage {
       for (int64_t a = a_lo; a <= a_hi; a += kPopcLagsPerCta / 32) it[k++] = PopcItem{i, 0, a};
     }
   }
+  // The planes of job i's signal `side` (0: x, 1: y).
+  uint32_t* planes_of(const Bases& B, int i, int side) const {
+    return B.dw<uint32_t>(o_planes[2 * i + side]);
+  }
+  bool prepacked = false;  // the quantizer already wrote every job's planes
   cudaError_t launch(tde_ctx* ctx, const Bases& B, cudaStream_t st) const {
     if (njobs == 0) return cudaSuccess;
-    cudaError_t e = launch_pack_planes(B.dd<PlaneSig>(o_psig), 2 * njobs, max_words, bits,
-                                       ctx->d_status, st);
+    cudaError_t e = prepacked ? cudaSuccess
+                              : launch_pack_planes(B.dd<PlaneSig>(o_psig), 2 * njobs, max_words,
+                                                   bits, ctx->d_status, st);
     if (e != cudaSuccess) return e;
     EngineTimer t(ctx, st);
     return launch_xcorr_popc(B.dd<XcPair>(o_pairs), B.dd<PopcItem>(o_items), nitems, bits, st);
@@ -911,7 +930,9 @@ tde_status batch_plan(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int 
   }
   // Quantized signals and (unless the caller gives c_out) correlations live
   // in the work memory.
-  w->Q.plan(w->L, 2 * npairs, bits, max_n);
+  bool any_popc = false;
+  for (int p = 0; p < npairs; ++p) any_popc |= w->engs[p] == TDE_ENGINE_POPC;
+  w->Q.plan(w->L, 2 * npairs, bits, max_n, any_popc);
   w->o_q.assign(2 * npairs, 0);
   w->c_start.assign(npairs, 0);
   int64_t c_total = 0;
@@ -931,6 +952,7 @@ tde_status batch_plan(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int 
     return set_err(ctx, TDE_ERR_UNSUPPORTED,
                    "NTT engine: a pair's shorter signal exceeds the largest transform (2^%d)",
                    kNttMaxLog);
+  w->E.popc.prepacked = w->Q.planes_written();
   w->A.plan(w->L, npairs, max_count, 0);
   return TDE_OK;
 }
@@ -953,6 +975,16 @@ void batch_fill(BatchWork* w, const Bases& B, const tde_pair_desc* descs, int32_
   }
   w->Q.fill(B, xs.data(), qs.data(), ns.data());
   w->E.fill(B, w->jobs);
+  // popc pairs get their planes from the quantizer (the k-th popc job is the
+  // k-th pair routed to popc)
+  for (int p = 0, k = 0; p < np; ++p)
+    for (int side = 0; side < 2; ++side) {
+      const bool popc = w->engs[p] == TDE_ENGINE_POPC;
+      const int64_t n = side ? descs[p].ny : descs[p].nx;
+      w->Q.set_planes(B, 2 * p + side, popc ? w->E.popc.planes_of(B, k, side) : nullptr,
+                      popc ? ceil_div64(n, 32) : 0);
+      if (side == 1 && popc) ++k;
+    }
 }
 
 cudaError_t batch_launch(tde_ctx* ctx, const BatchWork& w, const Bases& B, cudaStream_t st) {
@@ -1215,24 +1247,20 @@ tde_status check_model(tde_ctx* ctx, const tde_model* m) {
 }
 
 // Window jobs of the proposal: [c - 128, c + 128] clipped to the overlap.
+// Window w of pair p: lags [c - 128, c + 128] clipped to the overlap range;
+// lag tau lands at cbuf[i * stride + tau - (c - 128)].
 __global__ void k_make_windows(const int32_t* __restrict__ centres, int npairs, int64_t n,
-                               const uint32_t* __restrict__ planes, int64_t words,
-                               int32_t* __restrict__ cbuf, WinJob* __restrict__ jobs) {
+                               int32_t* __restrict__ cbuf, int stride, WinJob* __restrict__ jobs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npairs * kCnnTopK) return;
-  const int p = i / kCnnTopK;
   const int64_t c = centres[i];
   int64_t lo = c - kCnnBin / 2, hi = c + kCnnBin / 2;
+  const int64_t first = lo;
   if (lo < -(n - 1)) lo = -(n - 1);
   if (hi > n - 1) hi = n - 1;
-  WinJob J;
-  J.px = planes + (int64_t)(2 * p) * 2 * words;
-  J.py = planes + (int64_t)(2 * p + 1) * 2 * words;
-  J.wx = J.wy = words;
-  J.lag_lo = lo;
-  J.lag_hi = hi;
-  J.c = cbuf + (int64_t)i * 288;
-  jobs[i] = J;
+  // an empty window (hi < lo) writes nothing; keep its pointer in range
+  const int64_t off = hi >= lo ? lo - first : 0;
+  jobs[i] = WinJob{lo, hi, cbuf + (int64_t)i * stride + off};
 }
 
 __global__ void k_fallback_scatter(const int32_t* __restrict__ idx, int nfb,
@@ -1405,6 +1433,37 @@ extern "C" tde_status tde_propose(tde_ctx* ctx, const tde_model* m, const int8_t
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "propose");
 }
 
+extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npairs,
+                                        int bits, const int32_t* centres, int32_t* c_out,
+                                        tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!q || !centres || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (!valid_bits(bits)) return set_err(ctx, TDE_ERR_INVALID, "bits must be 1, 2 or 4");
+  if (n <= 0 || npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "n and npairs must be positive");
+  if (n > INT32_MAX) return set_err(ctx, TDE_ERR_UNSUPPORTED, "n beyond 2^31 - 1");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  const size_t o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
+  Bases B;
+  tde_status s = realize(ctx, L, &B);
+  if (s != TDE_OK) return s;
+  WinJob* jobs = B.dw<WinJob>(o_jobs);
+  cudaError_t e = cudaMemsetAsync(c_out, 0, sizeof(int32_t) * (size_t)npairs * kCnnTopK * kCnnWin, st);
+  if (e == cudaSuccess) {
+    k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(centres, npairs, n, c_out,
+                                                                     kCnnWin, jobs);
+    TDE_COUNT_LAUNCH(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    EngineTimer t(ctx, st);
+    e = launch_xcorr_mma_windows(q, n, npairs, jobs, ctx->d_status, st);
+  }
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "windows");
+}
+
 extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, const float* x,
                                            const float* y, int npairs, int bits, float theta,
                                            int64_t* lag_out, int64_t* val_out,
@@ -1421,33 +1480,27 @@ extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, con
   LaunchCount lc(ctx);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int S = 2 * npairs;
-  const int64_t words = ceil_div64(n, 32);
   Layout L;
   QuantStage Q;
   Q.plan(L, S, bits, n);
-  const size_t o_psig = L.d<PlaneSig>(S);
   const size_t o_q = L.w<int8_t>((size_t)S * n);
-  const size_t o_planes = L.w<uint32_t>((size_t)S * 2 * words);
   CnnPlan C;
   C.plan(L, npairs, n, false);
   const size_t o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
   const size_t o_marg = L.w<float>((size_t)npairs);
   const size_t o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
-  const size_t o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * 288);
+  const size_t o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * kCnnWin);
   Bases B;
   if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
   std::vector<const float*> xs(S);
   std::vector<int8_t*> qs(S);
   std::vector<int64_t> ns(S, n);
   int8_t* qbuf = B.dw<int8_t>(o_q);
-  uint32_t* planes = B.dw<uint32_t>(o_planes);
-  PlaneSig* ps = B.hd<PlaneSig>(o_psig);
   for (int p = 0; p < npairs; ++p)
     for (int k = 0; k < 2; ++k) {
       const int i = 2 * p + k;
       xs[i] = (k ? y : x) + (int64_t)p * n;
       qs[i] = qbuf + (int64_t)i * n;
-      ps[i] = PlaneSig{qs[i], planes + (int64_t)i * 2 * words, n, words};
     }
   Q.fill(B, xs.data(), qs.data(), ns.data());
   if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
@@ -1455,18 +1508,21 @@ extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, con
   float* marg = B.dw<float>(o_marg);
   WinJob* jobs = B.dw<WinJob>(o_jobs);
   cudaError_t e = Q.launch(B, ctx->d_status, st);
-  if (e == cudaSuccess) e = launch_pack_planes(B.dd<PlaneSig>(o_psig), S, words, bits, ctx->d_status, st);
   if (e == cudaSuccess) e = C.forward(B, m, qbuf, n, false, st);
   if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(C.o_scores), npairs, C.Lf, cent, marg, st);
   if (e == cudaSuccess) {
-    k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, npairs, n, planes, words,
-                                                                     B.dw<int32_t>(o_cwin), jobs);
+    k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, npairs, n,
+                                                                     B.dw<int32_t>(o_cwin), kCnnWin,
+                                                                     jobs);
     TDE_COUNT_LAUNCH(1);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(B.dw<int32_t>(o_cwin), 0, sizeof(int32_t) * (size_t)npairs * kCnnTopK * kCnnWin,
+                        st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_popc_windows(jobs, npairs * kCnnTopK, st);
+    e = launch_xcorr_mma_windows(qbuf, n, npairs, jobs, ctx->d_status, st);
   }
   if (e == cudaSuccess) e = launch_window_argmax(jobs, npairs, lag_out, val_out, st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "learned estimate");

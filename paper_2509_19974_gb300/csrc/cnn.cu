@@ -7,6 +7,9 @@
 // proposed windows or, when the proposal's confidence (softmax mass of its top
 // 8 bins) is below a threshold, over the full lag range.
 //
+// The windows' exact correlation runs on the tensor cores
+// (launch_xcorr_mma_windows in mma.cu); this file holds their argmax.
+//
 // All CNN arithmetic is FP32 with BF16-rounded weights; the backward pass is
 // deterministic (per-signal partial sums reduced in a fixed order, no float
 // atomics).  Shapes: conv layers tile 128 output positions x 32 channels per
@@ -553,60 +556,7 @@ __global__ void k_to_bf16(const float* __restrict__ params, uint16_t* __restrict
   if (i < kCnnParams) wbf[i] = f_to_bf16(params[i]);
 }
 
-// ------------------------------------------------ windowed exact correlation
-
-constexpr int kWinA = 9;  // 32-lag groups per window CTA (288 lags >= 257)
-
-__global__ void __launch_bounds__(kThreads) k_xcorr_popc_win(const WinJob* __restrict__ jobs) {
-  __shared__ int red[kThreads / 32][kWinA][32];
-  const WinJob J = jobs[blockIdx.x];
-  const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
-  const int64_t a0 = J.lag_lo >= 0 ? J.lag_lo / 32 : -((-J.lag_lo + 31) / 32);
-  int acc[kWinA], acc2[kWinA];
-#pragma unroll
-  for (int i = 0; i < kWinA; ++i) acc[i] = acc2[i] = 0;
-  const int64_t per = (J.wx + 7) / 8;
-  const int64_t w_lo = warp * per, w_hi = w_lo + per < J.wx ? w_lo + per : J.wx;
-  // y words w + a0 + i, i = 0..9, slide by one word per x word.
-  uint32_t ys[kWinA + 1], yz[kWinA + 1];
-#pragma unroll
-  for (int i = 0; i < kWinA; ++i) {
-    const int64_t yw = w_lo + a0 + i;
-    const bool in = yw >= 0 && yw < J.wy;
-    ys[i + 1] = in ? __ldg(J.py + yw) : 0u;
-    yz[i + 1] = in ? __ldg(J.py + J.wy + yw) : 0u;
-  }
-  for (int64_t w = w_lo; w < w_hi; ++w) {
-#pragma unroll
-    for (int i = 0; i < kWinA; ++i) {
-      ys[i] = ys[i + 1];
-      yz[i] = yz[i + 1];
-    }
-    const int64_t yw = w + a0 + kWinA;
-    const bool in = yw >= 0 && yw < J.wy;
-    ys[kWinA] = in ? __ldg(J.py + yw) : 0u;
-    yz[kWinA] = in ? __ldg(J.py + J.wy + yw) : 0u;
-    const uint32_t sx = __ldg(J.px + w), zx = __ldg(J.px + J.wx + w);
-#pragma unroll
-    for (int i = 0; i < kWinA; ++i) {
-      const uint32_t sy = __funnelshift_r(ys[i], ys[i + 1], r);
-      const uint32_t zy = __funnelshift_r(yz[i], yz[i + 1], r);
-      const uint32_t m = zx & zy;
-      acc[i] += __popc(m);
-      acc2[i] += __popc(m & (sx ^ sy));
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < kWinA; ++i) red[warp][i][r] = acc[i] - 2 * acc2[i];
-  __syncthreads();
-  for (int e = threadIdx.x; e < kWinA * 32; e += kThreads) {
-    const int i = e / 32, rr = e % 32;
-    int t = 0;
-    for (int w8 = 0; w8 < kThreads / 32; ++w8) t += red[w8][i][rr];
-    const int64_t tau = 32 * (a0 + i) + rr;
-    if (tau >= J.lag_lo && tau <= J.lag_hi) J.c[tau - J.lag_lo] = t;
-  }
-}
+// ------------------------------------------------ argmax over the windows
 
 __device__ __forceinline__ unsigned long long pack_key(int32_t v, int64_t tau) {
   const uint64_t a = (uint64_t)(tau < 0 ? -tau : tau);
@@ -762,13 +712,6 @@ cudaError_t launch_cnn_adamw(float* params, const float* grad, float* m, float* 
 
 cudaError_t launch_cnn_to_bf16(const float* params, uint16_t* wbf, cudaStream_t st) {
   k_to_bf16<<<(kCnnParams + 255) / 256, 256, 0, st>>>(params, wbf);
-  TDE_COUNT_LAUNCH(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_xcorr_popc_windows(const WinJob* d_jobs, int njobs, cudaStream_t st) {
-  if (njobs <= 0) return cudaSuccess;
-  k_xcorr_popc_win<<<njobs, kThreads, 0, st>>>(d_jobs);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -71,16 +71,11 @@ cudaError_t launch_cnn_adamw(float* params, const float* grad, float* m, float* 
                              float wd, cudaStream_t st);
 cudaError_t launch_cnn_to_bf16(const float* params, uint16_t* wbf, cudaStream_t st);
 
-// ---- windowed exact correlation (popc planes) and its argmax
+// ---- windows of the exact correlation and their argmax
 struct WinJob {
-  const uint32_t* px;  // planes of x (sign, nonzero), words per plane wx
-  const uint32_t* py;
-  int64_t wx, wy;
-  int64_t lag_lo, lag_hi;  // window, clipped to the overlap range
-  int32_t* c;              // 288 int32, lag lag_lo + i at c[i]
+  int64_t lag_lo, lag_hi;  // window, clipped to the overlap range (lag_hi - lag_lo <= 256)
+  int32_t* c;              // lag lag_lo + i at c[i], i <= lag_hi - lag_lo
 };
-// bits <= 2 planes.  One CTA per window.
-cudaError_t launch_xcorr_popc_windows(const WinJob* d_jobs, int njobs, cudaStream_t st);
 // Per pair: tie-ruled argmax over its 8 windows -> lag, value.
 cudaError_t launch_window_argmax(const WinJob* d_jobs, int npairs, int64_t* lag, int64_t* val,
                                  cudaStream_t st);

@@ -27,6 +27,13 @@ struct RankState {
   uint32_t rank[7];
 };
 
+// Optional bit-plane output of the fused quantizer for one signal (layout of
+// PlaneSig below: plane p word w at planes[p * words + w]).
+struct QPlanes {
+  uint32_t* planes;
+  int64_t words;
+};
+
 // ------------------------------------------------------------- popc engine
 // Bit-plane image of one quantized signal: plane 0 = sign (q < 0); for
 // bits <= 2 plane 1 = (q != 0); for bits = 4 planes 1..3 = bits 0..2 of |q|.
@@ -72,6 +79,13 @@ cudaError_t launch_quantize_sign(const QSig* d_sigs, int nsig, int64_t max_n, ui
                                  cudaStream_t st);
 // Rank quantizer for bits in {2,4}.  d_state: nsig RankState; d_hist:
 // nsig * 7 * 2048 uint32 of scratch.
+// Whether the fused one-pass rank quantizer serves bits and signals of up to
+// max_n samples (bits 2: max_n <= 262144; bits 4: max_n <= 225280).
+bool quantize_fused_ok(int bits, int64_t max_n);
+// The rank quantizer in one launch (thread-block clusters, signal held on
+// chip); d_planes (nullable) receives each signal's bit planes as well.
+cudaError_t launch_quantize_fused(const QSig* d_sigs, const QPlanes* d_planes, int nsig,
+                                  int64_t max_n, int bits, uint32_t* d_status, cudaStream_t st);
 cudaError_t launch_quantize_rank(const QSig* d_sigs, int nsig, int64_t max_n, int bits,
                                  RankState* d_state, uint32_t* d_hist, uint32_t* d_status,
                                  cudaStream_t st);

@@ -48,6 +48,7 @@
 // at the end all warps read the accumulator (warp w: lanes 32 (w % 4) ..,
 // columns 128 (w / 4) ..).  Every wait is bounded by %globaltimer; on time-out
 // the CTA flags TDE_ST_TIMEOUT, waits (bounded) for its MMAs and frees TMEM.
+#include "cnn.cuh"
 #include "common.cuh"
 #include "mma.cuh"
 
@@ -124,6 +125,28 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (;;) {
     for (int i = 0; i < 32; ++i)
       if (mbar_try(bar, parity)) return true;
+    if (now_ns() - t0 > kTimeoutNs) return false;
+  }
+}
+
+// As mbar_wait, but each try may suspend the thread in hardware for up to
+// ~20 us awaiting the phase (no issue slots spent spinning).
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __noinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity) {
+  if (mbar_try_sleep(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    if (mbar_try_sleep(bar, parity)) return true;
     if (now_ns() - t0 > kTimeoutNs) return false;
   }
 }
@@ -489,6 +512,249 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Windowed form (the learned proposal's exact check): for one pair and its 8
+// windows, window w's lags are covered by tau = T_w + 128 j + 127 - m
+// (j = 0..7, T_w = its first lag rounded down to a multiple of 128), 1024
+// lags of which the window's <= 257 are kept.  A is the same Hankel slot ring
+// as above.  B needs no per-chunk copies: each window's y segment is staged
+// once per item as E/O arrays of 128-byte swizzled rows,
+//   E_w[r] = y[ks + T_w + 128 r .. + 63],  O_w[r] = y[ks + T_w + 128 r + 64 .. + 127],
+// and because ks and T_w are multiples of 128, the 8 B rows of window w for
+// K chunk c are rows floor(c/2) .. + 7 of E_w (c even) or O_w (c odd) -- the
+// same rows for every window.  Windows' arrays sit at a fixed stride, so one
+// descriptor (stride byte offset = that stride) gives an N = 64 tile: 8
+// windows x 8 columns.  A CTA takes items (pair, K segment) round-robin;
+// partial sums are added into the zeroed window outputs with integer atomics.
+
+constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
+constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
+constexpr int kWinN = kWinW * kWinJ;             // MMA N = 64
+constexpr int kWinKs = 4096;                     // max samples of the sum per item
+constexpr int kWinRows = (kWinKs / kKc + 1) / 2 + kWinJ;  // E/O rows per window (40)
+constexpr int kWinArr = kWinRows * 128;          // bytes per E (or O) array, = the SBO
+constexpr int kWinXBytes = kWinKs + 272;
+// Producers and the issuer synchronize once per super-chunk of kWinSC chunks
+// (16 MMAs), on a slot ring of 128 (+ 24 mirrored): a super-chunk writes
+// logical slots [32 s + 15, 32 s + 47) and its chunks read [32 s, 32 s + 47),
+// so the slots it writes were last read by super-chunk s - 3.
+constexpr int kWinSC = 4;
+constexpr int kWinRing = 128, kWinMirror = 24;
+constexpr int kWinSlotBytes = (kWinRing + kWinMirror) * 128;
+constexpr int kWinSmemUsed = 2 * kWinW * kWinArr + kWinSlotBytes + kWinXBytes + (2 * kNB + 1) * 8 + 16;
+constexpr int kWinSmemBytes = kWinSmemUsed + 1024;
+static_assert(kWinArr % 1024 == 0, "windows' arrays keep the 1024-byte swizzle pattern");
+static_assert(kWinXBytes % 16 == 0, "staging");
+static_assert(kWinSmemBytes + 1024 <= 114 * 1024, "two CTAs per SM");
+static_assert(kWinRing % 32 == 0 && kWinMirror >= 23, "slot ring");
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_xcorr_mma_win(const int8_t* __restrict__ q, int64_t n, int npairs, const WinJob* __restrict__ jobs,
+                    int nseg, int seg, uint32_t* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t yE = base;                                 // window w at yE + w * kWinArr
+  const uint32_t yO = yE + kWinW * kWinArr;
+  const uint32_t slots = yO + kWinW * kWinArr;
+  const uint32_t xs = slots + kWinSlotBytes;
+  const uint32_t full_bar = xs + kWinXBytes;
+  const uint32_t cmt_bar = full_bar + 8 * kNB;
+  const uint32_t done_bar = cmt_bar + 8 * kNB;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
+  __shared__ int64_t sT[kWinW], sLo[kWinW], sHi[kWinW];  // per window: T_w, lag range
+  __shared__ int32_t* sC[kWinW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kWinN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < kNB; ++i) {
+      mbar_init(full_bar + 8 * i, kProducers);
+      mbar_init(cmt_bar + 8 * i, 1);
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int64_t sc0 = 0;  // super-chunks issued by this CTA so far (barrier phases)
+  uint32_t iter = 0;
+  bool ok = true;
+  const int nitems = npairs * nseg;
+  const int64_t kmax = (n + 127 + 127) / 128 * 128;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++iter) {
+    const int p = item / nseg, sgi = item - p * nseg;
+    const int64_t ks = (int64_t)sgi * seg;
+    const int64_t ke = ks + seg < kmax ? ks + seg : kmax;
+    const int nchunks = (int)((ke - ks) / kKc);
+    const int8_t* qx = q + (int64_t)(2 * p) * n;
+    const int8_t* qy = q + (int64_t)(2 * p + 1) * n;
+    const WinJob* J = jobs + (int64_t)p * kWinW;
+    if (nchunks <= 0 || ke - ks > kWinKs || (ks & 127) != 0) {  // not for the host's segmentation
+      if (threadIdx.x == 0 && nchunks > 0) atomicOr(status, TDE_ST_INTERNAL);
+      --iter;
+      continue;
+    }
+    const int64_t xs_base = fdiv(ks - 127, 16) * 16;
+    const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
+    const int nrows = (nchunks + 1) / 2 + kWinJ;  // rows of each E/O array this item reads
+    if (threadIdx.x < kWinW) {
+      const WinJob jw = J[threadIdx.x];
+      sT[threadIdx.x] = fdiv(jw.lag_lo, 128) * 128;
+      sLo[threadIdx.x] = jw.lag_lo;
+      sHi[threadIdx.x] = jw.lag_hi;
+      sC[threadIdx.x] = jw.c;
+    }
+    __syncthreads();
+    // staging: x segment, then every window's E/O rows (int8 -> BF16, swizzled)
+    {
+      const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+      const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+      constexpr int kXV = kWinXBytes / 16;
+      const int per_w = nrows * 8;  // (row, half, quarter) per window
+      const int total = kXV + kWinW * per_w;
+      for (int b0 = threadIdx.x; b0 < total; b0 += 8 * kThreads) {
+        uint4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int idx = b0 + k * kThreads;
+          if (idx < kXV) {
+            v[k] = load16(qx, xs_base + 16 * idx, n, alx);
+          } else if (idx < total) {
+            const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
+            const int row = r8 >> 3, half = (r8 >> 2) & 1, jq = r8 & 3;
+            v[k] = load16(qy, ks + sT[w] + 128 * row + 64 * half + 16 * jq, n, aly);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int idx = b0 + k * kThreads;
+          if (idx < kXV) {
+            st_shared_v4(xs + 16u * (uint32_t)idx, v[k].x, v[k].y, v[k].z, v[k].w);
+          } else if (idx < total) {
+            const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
+            const int row = r8 >> 3, half = (r8 >> 2) & 1, jq = r8 & 3;
+            const uint32_t row_addr = (half ? yO : yE) + (uint32_t)(w * kWinArr + 128 * row);
+            const uint32_t sw = (row_addr >> 7) & 7u;
+            store_row8(row_addr + 16u * ((uint32_t)(2 * jq) ^ sw), 0u,
+                       (uint64_t)v[k].x | ((uint64_t)v[k].y << 32));
+            store_row8(row_addr + 16u * ((uint32_t)(2 * jq + 1) ^ sw), 0u,
+                       (uint64_t)v[k].z | ((uint64_t)v[k].w << 32));
+          }
+        }
+      }
+    }
+    if (warp < 4) {
+      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      tmem_zero32(tmem + lane_base);
+      tmem_zero32(tmem + lane_base + 32u);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const int nsc = (nchunks + kWinSC - 1) / kWinSC;
+    if (warp == 1 || warp == 2) {
+      // Hankel slots of x (as in k_xcorr_mma), one super-chunk at a time
+      const int t = threadIdx.x - 32;
+      for (int sc = 0; sc < nsc; ++sc) {
+        const int64_t g = sc0 + sc;
+        const int64_t prev = g - 3;
+        if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
+          ok = false;
+          break;
+        }
+        const int c_last = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC - 1 : nchunks - 1;
+        const int o_first = sc == 0 ? 0 : 64 * (sc * kWinSC) + 120;
+        const int o_end = 64 * c_last + 184;
+        for (int o = o_first + t; o < o_end; o += kProducers) {
+          const uint32_t pa = xs + xoff + (uint32_t)o;
+          const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
+          const uint64_t lo = ld_shared_u64(al), hi = ld_shared_u64(al + 8u);
+          const uint64_t w = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
+          const int e = o >> 3, r = o & 7;
+          const int ps = e % kWinRing;
+          const uint32_t a = slots + 128u * ps + 16u * r;
+          store_row8(a, ps < kWinMirror ? a + 128u * kWinRing : 0u, w);
+        }
+        fence_proxy_async();
+        mbar_arrive(full_bar + 8 * (uint32_t)(g % kNB));
+      }
+    } else if (warp == 0) {
+      const uint32_t idesc = idesc_for(kWinN);
+      for (int sc = 0; sc < nsc; ++sc) {
+        const int64_t g = sc0 + sc;
+        ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(g % kNB), (uint32_t)((g / kNB) & 1)));
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const int c_end = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC : nchunks;
+          for (int c = sc * kWinSC; c < c_end; ++c) {
+            const uint32_t a_start = slots + 128u * (uint32_t)((8 * c) % kWinRing);
+            const uint32_t b_start = ((c & 1) ? yO : yE) + 128u * (uint32_t)(c >> 1);
+#pragma unroll
+            for (int s2 = 0; s2 < kKc / kKStep; ++s2)
+              mma_bf16(tmem, sdesc(a_start + 256u * s2, 128, 128, 0, 0),
+                       sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, 1u);
+          }
+          mma_commit(cmt_bar + 8 * (uint32_t)(g % kNB));
+        }
+        __syncwarp();
+      }
+      if (lane == 0) mma_commit(done_bar);
+      __syncwarp();
+    }
+
+    // one warp waits for the accumulator; the others block in the barrier
+    bool done = true;
+    if (warp == 3) done = mbar_wait_sleep(done_bar, iter & 1u);
+    ok = __syncthreads_and(ok && done);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
+      break;
+    }
+    {
+      // warp w: TMEM lanes 32 (w % 4) .., windows 4 (w / 4) .. + 3 (columns 32 (w / 4) ..)
+      tc_fence_after();
+      const int qd = warp & 3, colh = warp >> 2;
+      const int m = 32 * qd + lane;
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * colh), v);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int w = 4 * colh + (jj >> 3), j = jj & 7;
+        const int64_t lo = sLo[w], hi = sHi[w];
+        const int64_t tau = sT[w] + 128 * j + 127 - m;
+        if (tau < lo || tau > hi) continue;
+        const int val = __float2int_rn(__uint_as_float(v[jj]));
+        if (val != 0) atomicAdd(sC[w] + (tau - lo), val);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    sc0 += nsc;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWinN)
+                 : "memory");
+  }
+}
+
 }  // namespace
 
 int mma_smem_bytes() { return kSmemBytes; }
@@ -513,6 +779,27 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
   if (e != cudaSuccess) return e;
   if (grid > nitems) grid = nitems;
   k_xcorr_mma<<<grid, kThreads, kSmemBytes, st>>>(d_pairs, d_items, nitems, d_counter, d_status);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, const WinJob* d_jobs,
+                                     uint32_t* d_status, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  // K range [0, n + 127) rounded up to 128; segments are multiples of 128
+  // (so that each segment's windows start on a 128-sample row)
+  const int64_t kmax = ceil_div64(n + 127, 128) * 128;
+  const int nseg = (int)ceil_div64(kmax, kWinKs);
+  const int seg = (int)(ceil_div64(ceil_div64(kmax, nseg), 128) * 128);
+  cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kWinSmemBytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nitems = (int64_t)npairs * nseg;
+  const int grid = (int)(nitems < 2 * sms ? nitems : 2 * sms);
+  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(d_q, n, npairs, d_jobs, nseg, seg, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

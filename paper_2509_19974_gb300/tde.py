@@ -32,7 +32,7 @@ EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error"
            "tde_batch_destroy", "tde_model_param_count", "tde_model_create", "tde_model_destroy",
            "tde_model_get", "tde_model_set", "tde_train_step", "tde_propose",
            "tde_estimate_learned", "tde_synth_pairs", "tde_autotune", "tde_autotune_table",
-           "tde_autotune_load", "tde_ctx_pick_engine")
+           "tde_autotune_load", "tde_ctx_pick_engine", "tde_xcorr_windows")
 
 
 class TdeError(RuntimeError):
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_autotune_table": ([p, p, i32, p], st),
         "tde_autotune_load": ([p, p, i32], st),
         "tde_ctx_pick_engine": ([p, i32, i64, i64, i64], i32),
+        "tde_xcorr_windows": ([p, p, i64, i32, i32, p, p, p], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -507,6 +508,24 @@ def synth_pairs(ctx: Context, seed: int, first: int, npairs: int, n: int, dmax: 
                                       float(snr_db[1]), x.data_ptr(), y.data_ptr(), d.data_ptr(),
                                       _stream(stream)))
     return x, y, d
+
+
+def tde_xcorr_windows(ctx: Context, q2: torch.Tensor, bits: int, centres: torch.Tensor,
+                      c_out=None, stream=None):
+    """Exact correlation in 8 windows per pair.  q2: [2P, n] int8 (pair p at
+    rows 2p, 2p+1); centres: [P, 8] int32 (device).  Returns [P, 8, 257]
+    int32 with [p, w, i] = c_p[centres[p, w] - 128 + i] (0 outside the lags)."""
+    _need(q2, torch.int8, "q2")
+    _need(centres, torch.int32, "centres")
+    npairs, n = q2.shape[0] // 2, q2.shape[1]
+    if centres.shape != (npairs, 8):
+        raise ValueError("centres must be [npairs, 8]")
+    if c_out is None:
+        c_out = torch.empty((npairs, 8, 257), dtype=torch.int32, device=q2.device)
+    _need(c_out, torch.int32, "c_out")
+    ctx.check(ctx.lib.tde_xcorr_windows(ctx.handle, q2.data_ptr(), n, npairs, int(bits),
+                                        centres.data_ptr(), c_out.data_ptr(), _stream(stream)))
+    return c_out
 
 
 def interleave_q(qx: torch.Tensor, qy: torch.Tensor) -> torch.Tensor:

@@ -152,3 +152,33 @@ def test_inference_proposal_matches_reference_top_bin(ctx):
         e = np.exp(s[p] - s[p].max())
         assert abs(float(marg[p]) - e[top].sum() / e.sum()) < 1e-2
     m.close()
+
+
+@pytest.mark.parametrize("bits", [1, 2, 4])
+@pytest.mark.parametrize("n", [100, 4096 + 37, 65536])
+def test_xcorr_windows_match_oracle_at_edges(ctx, bits, n):
+    """The tensor-core windows against the oracle's correlation at the same
+    lags: centres at both ends of the lag range, partly and wholly outside
+    it, duplicated, and random; lags outside [-(n-1), n-1] read 0."""
+    import oracle
+    rng = np.random.default_rng(n * 7 + bits)
+    P = 3
+    k = 7 if bits == 4 else 1
+    q = rng.integers(-k, k + 1, size=(2 * P, n)).astype(np.int8)
+    q[rng.random((2 * P, n)) < 0.2] = 0
+    cent = np.empty((P, 8), np.int32)
+    for p in range(P):
+        cent[p] = [-(n - 1), n - 1, -(n - 1) - 100, n + 300, 0, 0,
+                   rng.integers(-(n - 1), n), rng.integers(-(n - 1), n)]
+    c = tde.tde_xcorr_windows(ctx, torch.from_numpy(q).cuda(), bits,
+                              torch.from_numpy(cent).cuda())
+    ctx.sync()
+    c = c.cpu().numpy().astype(np.int64)
+    for p in range(P):
+        for w in range(8):
+            lags = np.arange(cent[p, w] - 128, cent[p, w] + 129)
+            inr = (lags >= -(n - 1)) & (lags <= n - 1)
+            ref = np.zeros(257, np.int64)
+            if inr.any():
+                ref[inr] = oracle.xcorr_at(q[2 * p], q[2 * p + 1], lags[inr])
+            assert np.array_equal(c[p, w], ref), (p, w)
