@@ -322,25 +322,31 @@ struct Bases {
 struct QuantStage {
   int nsig = 0, bits = 1;
   int64_t max_n = 0;
-  bool fused = false, with_planes = false;
-  size_t o_sigs = 0, o_state = 0, o_hist = 0, o_planes = 0;
-  // with_planes: the fused form also writes bit planes (set_planes); callers
-  // must check planes_written() and pack themselves otherwise.
-  void plan(Layout& L, int n, int b, int64_t mx, bool want_planes = false) {
+  bool with_planes = false;
+  size_t o_sigs = 0, o_hist = 0, o_state = 0, o_candp = 0, o_planes = 0;
+  std::vector<size_t> o_cand;  // per signal: room for all its keys
+  // ns: the signals' lengths (host), or nullptr when all are max_n.  With
+  // want_planes the rank quantizer also writes bit planes (set_planes);
+  // callers check planes_written() and pack themselves otherwise.
+  void plan(Layout& L, int n, int b, const int64_t* ns, int64_t mx, bool want_planes = false) {
     nsig = n, bits = b, max_n = mx;
-    fused = quantize_fused_ok(bits, max_n);
-    with_planes = fused && want_planes;
+    with_planes = bits != 1 && want_planes;
     o_sigs = L.d<QSig>(nsig);
+    if (bits == 1) return;
     if (with_planes) o_planes = L.d<QPlanes>(nsig);
-    if (bits != 1 && !fused) {
-      o_state = L.w<RankState>(nsig);
-      o_hist = L.w<uint32_t>((size_t)nsig * 7 * 2048);
-    }
+    o_candp = L.d<uint32_t*>(nsig);
+    o_hist = L.w<uint32_t>((size_t)nsig * 4096);
+    o_state = L.w<QState>(nsig);
+    o_cand.resize(nsig);
+    for (int i = 0; i < nsig; ++i) o_cand[i] = L.w<uint32_t>((size_t)(ns ? ns[i] : mx));
   }
   bool planes_written() const { return with_planes; }
   void fill(const Bases& B, const float* const* xs, int8_t* const* qs, const int64_t* ns) const {
     QSig* h = B.hd<QSig>(o_sigs);
     for (int i = 0; i < nsig; ++i) h[i] = QSig{xs[i], qs[i], ns[i]};
+    if (bits == 1) return;
+    uint32_t** cp = B.hd<uint32_t*>(o_candp);
+    for (int i = 0; i < nsig; ++i) cp[i] = B.dw<uint32_t>(o_cand[i]);
   }
   void set_planes(const Bases& B, int i, uint32_t* planes, int64_t words) const {
     if (with_planes) B.hd<QPlanes>(o_planes)[i] = QPlanes{planes, words};
@@ -348,11 +354,9 @@ struct QuantStage {
   cudaError_t launch(const Bases& B, uint32_t* status, cudaStream_t st) const {
     if (nsig == 0) return cudaSuccess;
     if (bits == 1) return launch_quantize_sign(B.dd<QSig>(o_sigs), nsig, max_n, status, st);
-    if (fused)
-      return launch_quantize_fused(B.dd<QSig>(o_sigs), with_planes ? B.dd<QPlanes>(o_planes) : nullptr,
-                                   nsig, max_n, bits, status, st);
-    return launch_quantize_rank(B.dd<QSig>(o_sigs), nsig, max_n, bits, B.dw<RankState>(o_state),
-                                B.dw<uint32_t>(o_hist), status, st);
+    const QWork w{B.dw<uint32_t>(o_hist), B.dw<QState>(o_state), B.dd<uint32_t*>(o_candp)};
+    return launch_quantize_stream(B.dd<QSig>(o_sigs), with_planes ? B.dd<QPlanes>(o_planes) : nullptr,
+                                  nsig, max_n, bits, w, status, st);
   }
 };
 
@@ -800,7 +804,7 @@ extern "C" tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Layout L;
   QuantStage Q;
-  Q.plan(L, 1, bits, n);
+  Q.plan(L, 1, bits, nullptr, n);
   Bases B;
   tde_status s = realize(ctx, L, &B);
   if (s != TDE_OK) return s;
@@ -823,7 +827,7 @@ extern "C" tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Layout L;
   QuantStage Q;
-  Q.plan(L, nsig, bits, n);
+  Q.plan(L, nsig, bits, nullptr, n);
   Bases B;
   tde_status s = realize(ctx, L, &B);
   if (s != TDE_OK) return s;
@@ -932,7 +936,9 @@ tde_status batch_plan(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int 
   // in the work memory.
   bool any_popc = false;
   for (int p = 0; p < npairs; ++p) any_popc |= w->engs[p] == TDE_ENGINE_POPC;
-  w->Q.plan(w->L, 2 * npairs, bits, max_n, any_popc);
+  std::vector<int64_t> lens(2 * (size_t)npairs);
+  for (int p = 0; p < npairs; ++p) lens[2 * p] = descs[p].nx, lens[2 * p + 1] = descs[p].ny;
+  w->Q.plan(w->L, 2 * npairs, bits, lens.data(), max_n, any_popc);
   w->o_q.assign(2 * npairs, 0);
   w->c_start.assign(npairs, 0);
   int64_t c_total = 0;
@@ -1482,7 +1488,7 @@ extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, con
   const int S = 2 * npairs;
   Layout L;
   QuantStage Q;
-  Q.plan(L, S, bits, n);
+  Q.plan(L, S, bits, nullptr, n);
   const size_t o_q = L.w<int8_t>((size_t)S * n);
   CnnPlan C;
   C.plan(L, npairs, n, false);

@@ -236,23 +236,29 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
   }
 }
 
-// scores of one pair; fy zero-padded by Lf on both sides in shared memory.
-// Thread = (group of 8 consecutive bins, quarter of the channels): one fx and
-// one new fy load per 8 FMAs (the fy window slides in registers); the four
-// channel quarters are summed through shared memory.
+// scores of one pair.  Thread = (group of 8 consecutive bins, quarter of the
+// channels); per channel it walks the positions 8 at a time with 16-byte
+// loads: 8 fx values and 8 new fy values feed 64 FMAs.  fy sits in shared
+// memory with kScorePad leading zeros (so that every 8-bin group's window
+// starts on a 16-byte boundary) and zeros past its end; the four channel
+// quarters are summed through shared memory.
+__host__ __device__ constexpr int score_pad(int Lf) { return Lf + 3; }
+__host__ __device__ constexpr int score_row(int Lf) { return ((score_pad(Lf) + 2 * Lf + 16) + 3) / 4 * 4; }
+
 __global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ feat, int Lf,
                                                      const float* __restrict__ params,
                                                      float* __restrict__ scores) {
-  extern __shared__ float sm[];
-  float* fx = sm;                   // [32][Lf]
-  float* fy = sm + kCnnC * Lf;      // [32][3 Lf]
-  float* part = fy + kCnnC * 3 * Lf;  // [4][nb rounded to 8]
+  extern __shared__ __align__(16) float sm[];
+  const int P = score_pad(Lf), R = score_row(Lf);
+  float* fx = sm;                     // [32][Lf]
+  float* fy = sm + kCnnC * Lf;        // [32][R]: fy[c][j] at P + j
+  float* part = fy + kCnnC * R;       // [4][nb rounded to 8]
   const int p = blockIdx.x;
   const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
   const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
   for (int i = threadIdx.x; i < kCnnC * Lf; i += kThreads) fx[i] = gx[i];
-  for (int i = threadIdx.x; i < kCnnC * 3 * Lf; i += kThreads) {
-    const int c = i / (3 * Lf), j = i % (3 * Lf) - Lf;
+  for (int i = threadIdx.x; i < kCnnC * R; i += kThreads) {
+    const int c = i / R, j = i % R - P;
     fy[i] = (j >= 0 && j < Lf) ? gy[c * Lf + j] : 0.f;
   }
   __syncthreads();
@@ -260,23 +266,34 @@ __global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ f
   const int nb = 2 * Lf - 1, ngroups = (nb + 7) / 8, nbr = ngroups * 8;
   for (int w = threadIdx.x; w < ngroups * 4; w += kThreads) {
     const int grp = w % ngroups, cq = w / ngroups;
-    const int b0 = grp * 8, l0 = b0 - (Lf - 1);
+    const int b0 = grp * 8, l0 = b0 - (Lf - 1);  // bins b0.. <-> lags l0..
     float acc[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0.f;
     for (int c = cq * 8; c < cq * 8 + 8; ++c) {
       const float* a = fx + c * Lf;
-      const float* y = fy + c * 3 * Lf + Lf + l0;  // y[i + t] = fy[c][i + l0 + t]
-      float win[8];
+      const float* y = fy + c * R + P + l0;  // y[i + t] = fy[c][i + l0 + t]; 16-byte aligned
+      float yw[16];
+      {
+        const float4 u0 = *reinterpret_cast<const float4*>(y);
+        const float4 u1 = *reinterpret_cast<const float4*>(y + 4);
+        yw[0] = u0.x, yw[1] = u0.y, yw[2] = u0.z, yw[3] = u0.w;
+        yw[4] = u1.x, yw[5] = u1.y, yw[6] = u1.z, yw[7] = u1.w;
+      }
+      for (int i0 = 0; i0 < Lf; i0 += 8) {
+        const float4 a0 = *reinterpret_cast<const float4*>(a + i0);
+        const float4 a1 = *reinterpret_cast<const float4*>(a + i0 + 4);
+        const float4 u0 = *reinterpret_cast<const float4*>(y + i0 + 8);
+        const float4 u1 = *reinterpret_cast<const float4*>(y + i0 + 12);
+        yw[8] = u0.x, yw[9] = u0.y, yw[10] = u0.z, yw[11] = u0.w;
+        yw[12] = u1.x, yw[13] = u1.y, yw[14] = u1.z, yw[15] = u1.w;
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-      for (int t = 0; t < 7; ++t) win[t + 1] = y[t];
-      for (int i = 0; i < Lf; ++i) {
+        for (int s2 = 0; s2 < 8; ++s2)
 #pragma unroll
-        for (int t = 0; t < 7; ++t) win[t] = win[t + 1];
-        win[7] = y[i + 7];
-        const float av = a[i];
+          for (int t = 0; t < 8; ++t) acc[t] = fmaf(av[s2], yw[s2 + t], acc[t]);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = fmaf(av, win[t], acc[t]);
+        for (int t = 0; t < 8; ++t) yw[t] = yw[t + 8];
       }
     }
 #pragma unroll
@@ -634,7 +651,8 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st) {
-  const int smem = (kCnnC * Lf + kCnnC * 3 * Lf + 4 * (2 * Lf + 7)) * 4;
+  if (Lf % 8 != 0) return cudaErrorInvalidValue;  // Lf = n / 256 with n a multiple of 2048
+  const int smem = (kCnnC * Lf + kCnnC * score_row(Lf) + 4 * (2 * Lf + 7)) * 4;
   cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_scores<<<npairs, kThreads, smem, st>>>(feat, Lf, params, scores);
   TDE_COUNT_LAUNCH(1);

@@ -27,7 +27,7 @@ struct RankState {
   uint32_t rank[7];
 };
 
-// Optional bit-plane output of the fused quantizer for one signal (layout of
+// Optional bit-plane output of the rank quantizer for one signal (layout of
 // PlaneSig below: plane p word w at planes[p * words + w]).
 struct QPlanes {
   uint32_t* planes;
@@ -79,13 +79,24 @@ cudaError_t launch_quantize_sign(const QSig* d_sigs, int nsig, int64_t max_n, ui
                                  cudaStream_t st);
 // Rank quantizer for bits in {2,4}.  d_state: nsig RankState; d_hist:
 // nsig * 7 * 2048 uint32 of scratch.
-// Whether the fused one-pass rank quantizer serves bits and signals of up to
-// max_n samples (bits 2: max_n <= 262144; bits 4: max_n <= 225280).
-bool quantize_fused_ok(int bits, int64_t max_n);
-// The rank quantizer in one launch (thread-block clusters, signal held on
-// chip); d_planes (nullable) receives each signal's bit planes as well.
-cudaError_t launch_quantize_fused(const QSig* d_sigs, const QPlanes* d_planes, int nsig,
-                                  int64_t max_n, int bits, uint32_t* d_status, cudaStream_t st);
+// Work memory of the streaming rank quantizer: a 4096-bin histogram and a
+// QState per signal, and per signal a candidate list with room for n keys.
+struct QState {
+  uint32_t pre[7];   // threshold digits found so far
+  uint32_t rank[7];  // rank within them
+  uint32_t thr[7];   // final thresholds (FP32 bit patterns of |x|)
+  uint32_t ncand;    // keys in the candidate list
+};
+struct QWork {
+  uint32_t* hist;               // [nsig][4096]
+  QState* state;                // [nsig]
+  uint32_t* const* cand;        // [nsig] device pointers to lists of n keys
+};
+// The rank quantizer (bits 2, 4) as five streaming launches; d_planes
+// (nullable) receives each signal's bit planes as well.
+cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, int nsig,
+                                   int64_t max_n, int bits, QWork w, uint32_t* d_status,
+                                   cudaStream_t st);
 cudaError_t launch_quantize_rank(const QSig* d_sigs, int nsig, int64_t max_n, int bits,
                                  RankState* d_state, uint32_t* d_hist, uint32_t* d_status,
                                  cudaStream_t st);

@@ -11,19 +11,19 @@
 //    q = sign(x) * #{m : |x| >= t_m} is then one elementwise pass.
 // All passes are HBM-streaming; the batch dimension is blockIdx.y.
 //
-// Fused form (k_rank_fused, signals up to 262144 samples, bits 2 and 4): a
-// thread-block cluster of C CTAs holds one signal on chip -- each CTA keeps
-// its slice's FP32 bit patterns in shared memory -- and runs the same three
-// radix passes there.  After each pass every CTA sums the cluster's
-// histograms through distributed shared memory and makes the same selection,
-// so all CTAs agree on the thresholds without touching HBM.  One read of x,
-// one write of q (and, on request, the bit planes of the popc kernels, by
-// warp ballots) instead of four reads.
-#include <cooperative_groups.h>
-
+// Streaming form (k_q*, used by every caller with a workspace; the
+// multi-pass kernels above serve the allocation-free entry point):
+//   k_qhist   histogram of the top 12 bits of |x| per signal (one read of x);
+//   k_qsel1   per signal: the bin of each threshold's rank;
+//   k_qcand   the keys in those bins (a few percent) appended to the
+//             signal's candidate list (one read of x);
+//   k_qsel2   per signal: two radix passes (10 + 9 bits) over the candidates
+//             give the exact order statistics;
+//   k_qapply  q = sign(x) * #{m : |x| >= t_m}, and on request the bit planes
+//             of the popc kernels (one read of x, one write of q).
+// The candidate list has room for the whole signal, so no input (ties,
+// constant signals) needs another path.
 #include "common.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace {
 
@@ -189,58 +189,75 @@ __global__ void __launch_bounds__(kThreads) k_rank_apply(const QSig* __restrict_
   }
 }
 
-// ---------------------------------------------------------------- fused form
+// ------------------------------------------------------------ streaming form
 
-constexpr int kFT = 256;                 // threads per fused CTA
-constexpr int kFusedChunkTarget = 8192;  // samples per CTA when the cluster allows
-constexpr int kFusedChunkMax = 32768;
-constexpr int kFusedClusterMax = 8;
-constexpr int kCand = 1024;            // pass-1 candidate list per CTA
+constexpr int kQB = 4096;            // first digit: bits 30..19 of |x|
+constexpr int kQT = 256;             // threads per streaming CTA
+constexpr int kQPer = 8192;          // samples per streaming CTA and step
 
-// Per-CTA selection state in shared memory, one entry per threshold.
-struct FusedSel {
-  uint32_t pre[8];    // digits of t_m fixed so far
-  uint32_t rank[8];   // rank of t_m among the keys that share pre[m]
-  int owner[8];       // first threshold with the same prefix (shares its histogram)
-};
+__device__ __forceinline__ void q_bad(uint32_t u, int& bad) { bad |= u >= 0x7F800000u; }
 
-// merged[m] = sum over the cluster's CTAs of their hist[m], for every owner
-// m < M (nbins bins each).  All remote loads of a vector are issued before
-// they are summed.
-__device__ __forceinline__ void cluster_merge(cg::cluster_group& cl, const uint32_t* hist,
-                                              uint32_t* merged, const FusedSel& sel, int M,
-                                              int nbins) {
-  const int C = (int)cl.num_blocks();
-  const int nvec = nbins >> 2;
-  for (int idx = threadIdx.x; idx < M * nvec; idx += kFT) {
-    const int m = idx / nvec, v = idx - m * nvec;
-    if (sel.owner[m] != m) continue;
-    const uint4* src = reinterpret_cast<const uint4*>(hist + m * kBins) + v;
-    uint4 t[kFusedClusterMax];
+// Histogram of the first digit; each CTA adds its non-zero bins.
+__global__ void __launch_bounds__(kQT) k_qhist(const QSig* __restrict__ sigs, QWork w,
+                                               uint32_t* __restrict__ status) {
+  __shared__ uint32_t sh[kQB];
+  const int sig = blockIdx.y;
+  const QSig s = sigs[sig];
+  for (int i = threadIdx.x; i < kQB; i += kQT) sh[i] = 0;
+  __syncthreads();
+  int bad = 0;
+  const bool vec = (reinterpret_cast<uintptr_t>(s.x) & 15) == 0;
+  const int64_t n4 = vec ? s.n >> 2 : 0;
+  const float4* x4 = reinterpret_cast<const float4*>(s.x);
+  for (int64_t i0 = (int64_t)blockIdx.x * (kQPer / 4) + threadIdx.x; i0 < n4;
+       i0 += (int64_t)gridDim.x * (kQPer / 4)) {
+    float4 v[8];
 #pragma unroll
-    for (int r = 0; r < kFusedClusterMax; ++r)
-      if (r < C) t[r] = *cl.map_shared_rank(src, r);
-    uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; k < 8; ++k) {
+      const int64_t i = i0 + k * kQT;
+      if (i < n4) v[k] = x4[i];
+    }
 #pragma unroll
-    for (int r = 0; r < kFusedClusterMax; ++r)
-      if (r < C) acc.x += t[r].x, acc.y += t[r].y, acc.z += t[r].z, acc.w += t[r].w;
-    reinterpret_cast<uint4*>(merged + m * kBins)[v] = acc;
+    for (int k = 0; k < 8; ++k) {
+      const int64_t i = i0 + k * kQT;
+      if (i < n4) {
+        const uint32_t u0 = __float_as_uint(v[k].x) & 0x7FFFFFFFu, u1 = __float_as_uint(v[k].y) & 0x7FFFFFFFu;
+        const uint32_t u2 = __float_as_uint(v[k].z) & 0x7FFFFFFFu, u3 = __float_as_uint(v[k].w) & 0x7FFFFFFFu;
+        q_bad(u0, bad), q_bad(u1, bad), q_bad(u2, bad), q_bad(u3, bad);
+        atomicAdd(&sh[u0 >> 19], 1u);
+        atomicAdd(&sh[u1 >> 19], 1u);
+        atomicAdd(&sh[u2 >> 19], 1u);
+        atomicAdd(&sh[u3 >> 19], 1u);
+      }
+    }
   }
+  // the tail (or every sample, when x is not 16-byte aligned)
+  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * kQT + threadIdx.x; i < s.n;
+       i += (int64_t)gridDim.x * kQT) {
+    const uint32_t u = __float_as_uint(s.x[i]) & 0x7FFFFFFFu;
+    q_bad(u, bad);
+    atomicAdd(&sh[u >> 19], 1u);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, TDE_ST_NONFINITE);
+  uint32_t* gh = w.hist + (size_t)sig * kQB;
+  for (int i = threadIdx.x; i < kQB; i += kQT)
+    if (sh[i]) atomicAdd(&gh[i], sh[i]);
 }
 
-// Warp-wide selection for threshold m over histogram h (nbins = 2048 or
-// 512): appends the bin holding rank[m] to pre[m] and leaves the rank within
-// it.  Every lane reads rank[m] before the shuffles; one lane writes after.
-__device__ __forceinline__ void warp_select(const uint32_t* h, int nbins, int width, FusedSel& sel,
-                                            int m) {
+// Warp-wide: the bin of h (nbins = 512, 1024 or 4096) holding rank r, in two
+// levels (lanes own nbins/32 bins; then the owning lane's bins are split over
+// the warp).  Every lane returns the bin and the rank left within it.
+__device__ __noinline__ void warp_find(const uint32_t* h, int nbins, uint32_t r, uint32_t& bin,
+                                       uint32_t& rest) {
   const int lane = threadIdx.x & 31;
-  const int per = nbins >> 5;  // 64 or 16 bins per lane
-  const uint32_t* hh = h + lane * per;
-  const uint32_t r = sel.rank[m];
+  const int per = nbins >> 5;  // 16, 32 or 128
   uint32_t local = 0;
-  for (int k = 0; k < per; k += 4) {
-    const uint4 v = *reinterpret_cast<const uint4*>(hh + k);
-    local += v.x + v.y + v.z + v.w;
+  {
+    const uint4* hv = reinterpret_cast<const uint4*>(h + lane * per);
+    for (int k = 0; k < (per >> 2); ++k) {
+      const uint4 v = hv[k];
+      local += (v.x + v.y) + (v.z + v.w);
+    }
   }
   uint32_t incl = local;
 #pragma unroll
@@ -248,250 +265,276 @@ __device__ __forceinline__ void warp_select(const uint32_t* h, int nbins, int wi
     const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
-  const uint32_t before = incl - local;
-  if (r >= before && r < incl) {
-    uint32_t acc = before;
-    for (int k = 0; k < per; ++k) {
-      const uint32_t c = hh[k];
-      if (r < acc + c) {
-        sel.pre[m] = (sel.pre[m] << width) | (uint32_t)(lane * per + k);
-        sel.rank[m] = r - acc;
+  const uint32_t own = __ballot_sync(0xffffffffu, r >= incl - local && r < incl);
+  const int L1 = own ? __ffs(own) - 1 : 0;
+  const uint32_t r1 = r - __shfl_sync(0xffffffffu, incl - local, L1);
+  // second level: bins L1*per .. + per - 1, `sub` per lane
+  const int sub = per >= 32 ? per >> 5 : 1;
+  const int base = L1 * per + lane * sub;
+  uint32_t c[4] = {0u, 0u, 0u, 0u};
+  uint32_t loc2 = 0;
+  if (lane * sub < per)
+    for (int k = 0; k < sub; ++k) c[k] = h[base + k], loc2 += c[k];
+  uint32_t inc2 = loc2;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc2, o);
+    if (lane >= o) inc2 += t;
+  }
+  const bool mine = lane * sub < per && r1 >= inc2 - loc2 && r1 < inc2;
+  uint32_t fb = 0, fr = 0;
+  if (mine) {
+    uint32_t acc = inc2 - loc2;
+    for (int k = 0; k < sub; ++k) {
+      if (r1 < acc + c[k]) {
+        fb = (uint32_t)(base + k);
+        fr = r1 - acc;
         break;
       }
-      acc += c;
+      acc += c[k];
     }
   }
+  const uint32_t who = __ballot_sync(0xffffffffu, mine);
+  const int src = who ? __ffs(who) - 1 : 0;
+  bin = __shfl_sync(0xffffffffu, fb, src);
+  rest = __shfl_sync(0xffffffffu, fr, src);
 }
 
-// One cluster per signal (blockIdx.x / C); CTA rank r holds samples
-// [r * chunk, (r + 1) * chunk).  chunk is a multiple of 32, so bit-plane
-// words never straddle CTAs.  No CTA returns early: all take part in every
-// cluster barrier.  M = number of thresholds (1 for bits 2, 7 for bits 4).
-// Pass 1 also collects its matching keys (a few percent of the slice) in a
-// candidate list, so pass 2 scans that list instead of the whole slice
-// (unless it overflowed).
+// Per signal: first digit of every threshold (warp m for threshold m).
+__global__ void __launch_bounds__(kQT) k_qsel1(const QSig* __restrict__ sigs, QWork w, int M, int L) {
+  __shared__ __align__(16) uint32_t sh[kQB];
+  const int sig = blockIdx.x;
+  const int64_t n = sigs[sig].n;
+  const uint32_t* gh = w.hist + (size_t)sig * kQB;
+  for (int i = threadIdx.x; i < kQB / 4; i += kQT)
+    reinterpret_cast<uint4*>(sh)[i] = reinterpret_cast<const uint4*>(gh)[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  QState* st = w.state + sig;
+  if (warp < M) {
+    const int64_t idx = ((2 * (int64_t)warp + 1) * n) / L;
+    const uint32_t r = (uint32_t)(idx > n - 1 ? n - 1 : idx);
+    uint32_t bin, rest;
+    warp_find(sh, kQB, r, bin, rest);
+    if ((threadIdx.x & 31) == 0) st->pre[warp] = bin, st->rank[warp] = rest;
+  }
+  if (threadIdx.x == 0) st->ncand = 0;
+}
+
+// Keys whose first digit is a threshold's -> the signal's candidate list.
+// Each thread counts its hits and reserves room for them with one shared
+// atomic; the CTA gathers them in shared memory and adds them to the list with
+// one global atomic (hits that do not fit in the buffer go straight to the
+// list).
+constexpr int kCandBuf = 4096;
+
 template <int M>
-__global__ void __launch_bounds__(kFT, M == 1 ? 4 : 1)
-    k_rank_fused(const QSig* __restrict__ sigs, const QPlanes* __restrict__ planes, int chunk,
-                 uint32_t* __restrict__ status) {
-  constexpr int kBitsT = M == 1 ? 2 : 4;
-  constexpr int L = 2 * M + 1;
-  cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int crank = (int)cl.block_rank();
-  const int sig = blockIdx.x / C;
-  extern __shared__ __align__(16) uint32_t smf[];
-  uint32_t* keys = smf;                    // [chunk] raw FP32 bits
-  uint32_t* hist = smf + chunk;            // [M][kBins] this CTA's histograms
-  uint32_t* merged = hist + M * kBins;     // [M][kBins] the cluster's sums
-  uint32_t* cand = merged + M * kBins;     // [kCand] pass-1 keys for pass 2
-  __shared__ FusedSel sel;
-  __shared__ int ncand;
+__global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QWork w) {
+  __shared__ uint32_t buf[kCandBuf];
+  __shared__ uint32_t nbuf, gbase;
+  const int sig = blockIdx.y;
   const QSig s = sigs[sig];
-  const int64_t base = (int64_t)crank * chunk;
-  const int64_t rem = s.n - base;
-  const int cnt = rem <= 0 ? 0 : (rem < chunk ? (int)rem : chunk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  for (int i = threadIdx.x; i < kBins; i += kFT) hist[i] = 0;
-  if (threadIdx.x < 8) {
-    const int m = threadIdx.x;
-    const int64_t idx = ((2 * (int64_t)m + 1) * s.n) / L;
-    sel.rank[m] = (uint32_t)(idx > s.n - 1 ? s.n - 1 : idx);
-    sel.pre[m] = 0;
-    sel.owner[m] = 0;  // pass 0: one histogram for all thresholds
-  }
-  __syncthreads();
-  // load + pass 0 (digit = bits 30..20 of |x|)
-  int bad = 0;
-  const float* xs = s.x + base;
-  const bool vec = (reinterpret_cast<uintptr_t>(xs) & 15) == 0;
-  const int n4 = vec ? cnt >> 2 : 0;
-  {
-    const float4* x4 = reinterpret_cast<const float4*>(xs);
-    // four independent 16-byte loads in flight per thread before any atomic
-    for (int i0 = threadIdx.x; i0 < n4; i0 += 4 * kFT) {
-      float4 v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (i0 + k * kFT < n4) v[k] = x4[i0 + k * kFT];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int i = i0 + k * kFT;
-        if (i >= n4) break;
-        const uint4 w = make_uint4(__float_as_uint(v[k].x), __float_as_uint(v[k].y),
-                                   __float_as_uint(v[k].z), __float_as_uint(v[k].w));
-        reinterpret_cast<uint4*>(keys)[i] = w;
-        const uint32_t u0 = w.x & 0x7FFFFFFFu, u1 = w.y & 0x7FFFFFFFu, u2 = w.z & 0x7FFFFFFFu,
-                       u3 = w.w & 0x7FFFFFFFu;
-        bad |= max(max(u0, u1), max(u2, u3)) >= 0x7F800000u;
-        atomicAdd(&hist[u0 >> 20], 1u);
-        atomicAdd(&hist[u1 >> 20], 1u);
-        atomicAdd(&hist[u2 >> 20], 1u);
-        atomicAdd(&hist[u3 >> 20], 1u);
-      }
-    }
-  }
-  for (int i = (n4 << 2) + threadIdx.x; i < cnt; i += kFT) {
-    const uint32_t w = __float_as_uint(xs[i]);
-    keys[i] = w;
-    const uint32_t u = w & 0x7FFFFFFFu;
-    bad |= u >= 0x7F800000u;
-    atomicAdd(&hist[u >> 20], 1u);
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, TDE_ST_NONFINITE);
-  cl.sync();
-  cluster_merge(cl, hist, merged, sel, 1, kBins);
-  __syncthreads();
-  if (warp < M) warp_select(merged, kBins, 11, sel, warp);
-  __syncthreads();
-
-  // ---- pass 1 (bits 19..9) over the whole slice; collect candidates
+  QState* st = w.state + sig;
   uint32_t pre[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) pre[m] = sel.pre[m];
-  cl.sync();  // the peers have finished reading the pass-0 histograms
-  if (threadIdx.x < 8) {
-    const int m = threadIdx.x;
-    int o = m;
-    for (int k = m - 1; k >= 0; --k)
-      if (sel.pre[k] == sel.pre[m]) o = k;
-    sel.owner[m] = o;
-  }
-  if (threadIdx.x == 0) ncand = 0;
-  for (int i = threadIdx.x; i < M * kBins; i += kFT) hist[i] = 0;
-  __syncthreads();
-  const int cnt4 = cnt >> 2;
-  for (int j0 = warp * 32; j0 < ((cnt + 3) >> 2); j0 += kFT) {
-    const int i = j0 + lane;  // keys 4i .. 4i+3
-    uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    int nk = 0;
-    if (i < cnt4) {
-      w = reinterpret_cast<const uint4*>(keys)[i];
-      nk = 4;
-    } else if (4 * i < cnt) {
-      nk = cnt - 4 * i;
-      w.x = keys[4 * i];
-      if (nk > 1) w.y = keys[4 * i + 1];
-      if (nk > 2) w.z = keys[4 * i + 2];
-    }
-    const uint32_t wk[4] = {w.x, w.y, w.z, w.w};
+  for (int m = 0; m < M; ++m) pre[m] = st->pre[m];
+  uint32_t* cand = w.cand[sig];
+  auto match = [&](uint32_t u) {
+    const uint32_t hi = u >> 19;
+    bool h = false;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t u = wk[k] & 0x7FFFFFFFu;
-      const uint32_t hi = u >> 20;
+    for (int m = 0; m < M; ++m) h |= hi == pre[m];
+    return h;
+  };
+  auto put = [&](uint32_t slot, uint32_t u) {
+    if (slot < kCandBuf)
+      buf[slot] = u;
+    else
+      cand[atomicAdd(&st->ncand, 1u)] = u;
+  };
+  if (threadIdx.x == 0) nbuf = 0;
+  __syncthreads();
+  const bool vec = (reinterpret_cast<uintptr_t>(s.x) & 15) == 0;
+  const int64_t n4 = vec ? s.n >> 2 : 0;
+  const float4* x4 = reinterpret_cast<const float4*>(s.x);
+  for (int64_t c0 = (int64_t)blockIdx.x * (kQPer / 4); c0 < n4; c0 += (int64_t)gridDim.x * (kQPer / 4)) {
+    float4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t i = c0 + k * kQT + threadIdx.x;
+      v[k] = i < n4 ? x4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    uint32_t hits = 0;  // bit 4k + e: element e of load k
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (c0 + k * kQT + threadIdx.x >= n4) continue;
+      const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (match(__float_as_uint(f[e]) & 0x7FFFFFFFu)) hits |= 1u << (4 * k + e);
+    }
+    if (hits) {
+      uint32_t slot = atomicAdd(&nbuf, (uint32_t)__popc(hits));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (hits >> (4 * k + e) & 1u) put(slot++, __float_as_uint(f[e]) & 0x7FFFFFFFu);
+      }
+    }
+  }
+  // the tail (or every sample, when x is not 16-byte aligned)
+  for (int64_t j = (n4 << 2) + (int64_t)blockIdx.x * kQT + threadIdx.x; j < s.n;
+       j += (int64_t)gridDim.x * kQT) {
+    const uint32_t u = __float_as_uint(s.x[j]) & 0x7FFFFFFFu;
+    if (match(u)) put(atomicAdd(&nbuf, 1u), u);
+  }
+  __syncthreads();
+  const uint32_t nb = nbuf < (uint32_t)kCandBuf ? nbuf : (uint32_t)kCandBuf;
+  if (threadIdx.x == 0) gbase = nb ? atomicAdd(&st->ncand, nb) : 0u;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nb; i += kQT) cand[gbase + i] = buf[i];
+}
+
+// Per signal: the exact thresholds from the candidates -- digits 18..9 then
+// 8..0, one histogram per distinct first digit, one warp per threshold.
+__global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QWork w, int M) {
+  __shared__ __align__(16) uint32_t sh[7 * 1024];
+  __shared__ uint32_t pre_s[7], rank_s[7];
+  __shared__ int owner_s[7];
+  const int sig = blockIdx.x;
+  QState* st = w.state + sig;
+  const uint32_t* cand = w.cand[sig];
+  const uint32_t nc = st->ncand;
+  if (threadIdx.x < 7) {
+    const int m = threadIdx.x;
+    pre_s[m] = m < M ? st->pre[m] : 0xFFFFFFFFu;
+    rank_s[m] = m < M ? st->rank[m] : 0u;
+  }
+  const int warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int nbins = pass == 0 ? 1024 : 512, shift = pass == 0 ? 9 : 0, hs = pass == 0 ? 19 : 9;
+    const uint32_t mask = pass == 0 ? 1023u : 511u;
+    __syncthreads();  // pre_s as the previous pass (or the load above) left it
+    // thresholds with equal prefixes so far share the first one's histogram
+    if (threadIdx.x < 7) {
+      const int m = threadIdx.x;
+      int o = m;
+      for (int k = m - 1; k >= 0; --k)
+        if (pre_s[k] == pre_s[m]) o = k;
+      owner_s[m] = o;
+    }
+    for (int i = threadIdx.x; i < M * 1024; i += kQT) sh[i] = 0;
+    __syncthreads();
+    uint32_t pre[7];
+    int own[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) pre[m] = pre_s[m], own[m] = owner_s[m];
+    for (uint32_t i = threadIdx.x; i < nc; i += kQT) {
+      const uint32_t u = cand[i];
+      const uint32_t hi = u >> hs;
       int mm = -1;
 #pragma unroll
-      for (int m = M - 1; m >= 0; --m)
-        if (hi == pre[m]) mm = m;
-      const bool hit = k < nk && mm >= 0;
-      if (hit) atomicAdd(&hist[mm * kBins + ((u >> 9) & 2047u)], 1u);
-      const uint32_t hits = __ballot_sync(0xffffffffu, hit);
-      if (hits) {
-        int slot0 = 0;
-        if (lane == __ffs(hits) - 1) slot0 = atomicAdd(&ncand, __popc(hits));
-        slot0 = __shfl_sync(0xffffffffu, slot0, __ffs(hits) - 1);
-        const int slot = slot0 + __popc(hits & ((1u << lane) - 1u));
-        if (hit && slot < kCand) cand[slot] = u;
+      for (int m = 6; m >= 0; --m)
+        if (m < M && hi == pre[m]) mm = own[m];
+      if (mm >= 0) atomicAdd(&sh[mm * 1024 + ((u >> shift) & mask)], 1u);
+    }
+    __syncthreads();
+    if (warp < M) {
+      uint32_t bin, rest;
+      warp_find(sh + owner_s[warp] * 1024, nbins, rank_s[warp], bin, rest);
+      if ((threadIdx.x & 31) == 0) {
+        pre_s[warp] = (pre_s[warp] << (pass == 0 ? 10 : 9)) | bin;
+        rank_s[warp] = rest;
       }
     }
+    __syncthreads();
   }
-  cl.sync();
-  cluster_merge(cl, hist, merged, sel, M, kBins);
-  __syncthreads();
-  if (warp < M) warp_select(merged + sel.owner[warp] * kBins, kBins, 11, sel, warp);
-  __syncthreads();
+  if (threadIdx.x < 7) st->thr[threadIdx.x] = threadIdx.x < M ? pre_s[threadIdx.x] : 0xFFFFFFFFu;
+}
 
-  // ---- pass 2 (bits 8..0) over the candidates
-#pragma unroll
-  for (int m = 0; m < M; ++m) pre[m] = sel.pre[m];
-  cl.sync();  // the peers have finished reading the pass-1 histograms
-  if (threadIdx.x < 8) {
-    const int m = threadIdx.x;
-    int o = m;
-    for (int k = m - 1; k >= 0; --k)
-      if (sel.pre[k] == sel.pre[m]) o = k;
-    sel.owner[m] = o;
-  }
-  for (int i = threadIdx.x; i < M * kBins; i += kFT) hist[i] = 0;
-  __syncthreads();
-  const bool from_cand = ncand <= kCand;
-  const int n2 = from_cand ? ncand : cnt;
-  for (int i = threadIdx.x; i < n2; i += kFT) {
-    const uint32_t u = (from_cand ? cand[i] : keys[i]) & 0x7FFFFFFFu;
-    const uint32_t hi = u >> 9;
-    int mm = -1;
-#pragma unroll
-    for (int m = M - 1; m >= 0; --m)
-      if (hi == pre[m]) mm = m;
-    if (mm >= 0) atomicAdd(&hist[mm * kBins + (u & 511u)], 1u);
-  }
-  cl.sync();
-  cluster_merge(cl, hist, merged, sel, M, 512);
-  __syncthreads();
-  if (warp < M) warp_select(merged + sel.owner[warp] * kBins, 512, 9, sel, warp);
-  __syncthreads();
-  cl.sync();  // last remote reads of this CTA's histograms are done
-
-  // ---- apply: q = sign(x) * #{m : |x| >= t_m}; optional planes by ballots
+// q = sign(x) * #{m : |x| >= t_m}; bit planes by warp ballots when asked.
+template <int M>
+__global__ void __launch_bounds__(kQT) k_qapply(const QSig* __restrict__ sigs,
+                                                const QPlanes* __restrict__ planes, QWork w) {
+  const int sig = blockIdx.y;
+  const QSig s = sigs[sig];
   uint32_t t[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) t[m] = sel.pre[m];
+  for (int m = 0; m < M; ++m) t[m] = w.state[sig].thr[m];
   const QPlanes pl = planes ? planes[sig] : QPlanes{nullptr, 0};
-  int8_t* qo = s.q + base;
-  if (!pl.planes && (reinterpret_cast<uintptr_t>(qo) & 3) == 0) {
-    // four levels per 32-bit store
-    for (int i = threadIdx.x; i < cnt4; i += kFT) {
-      const uint4 w = reinterpret_cast<const uint4*>(keys)[i];
-      const uint32_t wk[4] = {w.x, w.y, w.z, w.w};
-      uint32_t packed = 0;
+  const int lane = threadIdx.x & 31;
+  const bool vec = !pl.planes && (reinterpret_cast<uintptr_t>(s.x) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(s.q) & 3) == 0;
+  if (vec) {
+    const int64_t n4 = s.n >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(s.x);
+    uint32_t* q4 = reinterpret_cast<uint32_t*>(s.q);
+    for (int64_t i0 = (int64_t)blockIdx.x * (kQPer / 4) + threadIdx.x; i0 < n4;
+         i0 += (int64_t)gridDim.x * (kQPer / 4)) {
+      float4 v[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t u = wk[k] & 0x7FFFFFFFu;
-        int level = 0;
+      for (int k = 0; k < 8; ++k)
+        if (i0 + k * kQT < n4) v[k] = x4[i0 + k * kQT];
 #pragma unroll
-        for (int m = 0; m < M; ++m) level += u >= t[m];
-        const int q = sign_of(__uint_as_float(wk[k])) * level;
-        packed |= ((uint32_t)q & 0xFFu) << (8 * k);
+      for (int k = 0; k < 8; ++k) {
+        if (i0 + k * kQT >= n4) break;
+        const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+        uint32_t packed = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const uint32_t u = __float_as_uint(f[e]) & 0x7FFFFFFFu;
+          int level = 0;
+#pragma unroll
+          for (int m = 0; m < M; ++m) level += u >= t[m];
+          packed |= ((uint32_t)(sign_of(f[e]) * level) & 0xFFu) << (8 * e);
+        }
+        q4[i0 + k * kQT] = packed;
       }
-      reinterpret_cast<uint32_t*>(qo)[i] = packed;
     }
-    for (int j = (cnt4 << 2) + threadIdx.x; j < cnt; j += kFT) {
-      const uint32_t w = keys[j];
-      const uint32_t u = w & 0x7FFFFFFFu;
+    for (int64_t j = (n4 << 2) + (int64_t)blockIdx.x * kQT + threadIdx.x; j < s.n;
+         j += (int64_t)gridDim.x * kQT) {
+      const float f = s.x[j];
+      const uint32_t u = __float_as_uint(f) & 0x7FFFFFFFu;
       int level = 0;
 #pragma unroll
       for (int m = 0; m < M; ++m) level += u >= t[m];
-      qo[j] = (int8_t)(sign_of(__uint_as_float(w)) * level);
+      s.q[j] = (int8_t)(sign_of(f) * level);
     }
     return;
   }
-  for (int j0 = warp * 32; j0 < cnt; j0 += kFT) {
-    const int j = j0 + lane;
-    const bool valid = j < cnt;
-    const uint32_t w = valid ? keys[j] : 0u;
-    const uint32_t u = w & 0x7FFFFFFFu;
-    int level = 0;
+  // one sample per lane, 32 consecutive samples per warp (plane words)
+  for (int64_t c0 = (int64_t)blockIdx.x * kQPer; c0 < s.n; c0 += (int64_t)gridDim.x * kQPer) {
+    const int64_t c1 = c0 + kQPer < s.n ? c0 + kQPer : s.n;
+    for (int64_t j0 = c0 + (threadIdx.x & ~31); j0 < c1; j0 += kQT) {
+      const int64_t j = j0 + lane;
+      const bool valid = j < c1;
+      const float f = valid ? s.x[j] : 0.f;
+      const uint32_t u = __float_as_uint(f) & 0x7FFFFFFFu;
+      int level = 0;
 #pragma unroll
-    for (int m = 0; m < M; ++m) level += u >= t[m];
-    const int q = sign_of(__uint_as_float(w)) * level;
-    if (valid) qo[j] = (int8_t)q;
-    if (pl.planes) {
-      const int64_t word = (base + j0) >> 5;
-      const uint32_t b0 = __ballot_sync(0xffffffffu, q < 0);
-      if (kBitsT <= 2) {
-        const uint32_t b1 = __ballot_sync(0xffffffffu, q != 0);
-        if (lane == 0) pl.planes[word] = b0, pl.planes[pl.words + word] = b1;
-      } else {
-        const int a = q < 0 ? -q : q;
-        const uint32_t b1 = __ballot_sync(0xffffffffu, a & 1);
-        const uint32_t b2 = __ballot_sync(0xffffffffu, a & 2);
-        const uint32_t b3 = __ballot_sync(0xffffffffu, a & 4);
-        if (lane == 0) {
-          pl.planes[word] = b0;
-          pl.planes[pl.words + word] = b1;
-          pl.planes[2 * pl.words + word] = b2;
-          pl.planes[3 * pl.words + word] = b3;
+      for (int m = 0; m < M; ++m) level += u >= t[m];
+      const int q = sign_of(f) * level;
+      if (valid) s.q[j] = (int8_t)q;
+      if (pl.planes) {
+        const int64_t word = j0 >> 5;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, q < 0);
+        if (M == 1) {
+          const uint32_t b1 = __ballot_sync(0xffffffffu, q != 0);
+          if (lane == 0) pl.planes[word] = b0, pl.planes[pl.words + word] = b1;
+        } else {
+          const int a = q < 0 ? -q : q;
+          const uint32_t b1 = __ballot_sync(0xffffffffu, a & 1);
+          const uint32_t b2 = __ballot_sync(0xffffffffu, a & 2);
+          const uint32_t b3 = __ballot_sync(0xffffffffu, a & 4);
+          if (lane == 0) {
+            pl.planes[word] = b0;
+            pl.planes[pl.words + word] = b1;
+            pl.planes[2 * pl.words + word] = b2;
+            pl.planes[3 * pl.words + word] = b3;
+          }
         }
       }
     }
@@ -545,50 +588,28 @@ cudaError_t launch_quantize_rank(const QSig* d_sigs, int nsig, int64_t max_n, in
   return cudaGetLastError();
 }
 
-// Largest slice one CTA can hold: keys, 2 M histograms and the candidate
-// list within the 227 KB a CTA may use (1 KB kept for static shared memory).
-int fused_chunk_max(int bits) {
-  const int M = (1 << (bits - 1)) - 1;
-  const int fit = (232448 - 1024 - 2 * M * kBins * 4 - kCand * 4) / 4;
-  const int c = fit < kFusedChunkMax ? fit : kFusedChunkMax;
-  return c & ~31;
-}
-
-bool quantize_fused_ok(int bits, int64_t max_n) {
-  return (bits == 2 || bits == 4) && max_n >= 1 &&
-         max_n <= (int64_t)kFusedClusterMax * fused_chunk_max(bits);
-}
-
-template <int M>
-cudaError_t launch_fused_m(const QSig* d_sigs, const QPlanes* d_planes, int nsig, int C, int chunk,
-                           uint32_t* d_status, cudaStream_t st) {
-  const size_t smem = (size_t)chunk * 4 + (size_t)2 * M * kBins * 4 + kCand * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_rank_fused<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, int nsig,
+                                   int64_t max_n, int bits, QWork w, uint32_t* d_status,
+                                   cudaStream_t st) {
+  if (bits != 2 && bits != 4) return cudaErrorInvalidValue;
+  const int M = (1 << (bits - 1)) - 1, L = (1 << bits) - 1;
+  int64_t gx = ceil_div64(max_n, kQPer);
+  if (gx < 1) gx = 1;
+  if (gx > 65535) gx = 65535;
+  const dim3 grid((unsigned)gx, (unsigned)nsig);
+  cudaError_t e = cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * (size_t)nsig * kQB, st);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nsig * C));
-  cfg.blockDim = dim3(kFT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_rank_fused<M>, d_sigs, d_planes, chunk, d_status);
-  TDE_COUNT_LAUNCH(1);
-  return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-cudaError_t launch_quantize_fused(const QSig* d_sigs, const QPlanes* d_planes, int nsig,
-                                  int64_t max_n, int bits, uint32_t* d_status, cudaStream_t st) {
-  if (!quantize_fused_ok(bits, max_n)) return cudaErrorInvalidValue;
-  int C = 1;
-  while (C < kFusedClusterMax && ceil_div64(max_n, C) > kFusedChunkTarget) C *= 2;
-  const int chunk = (int)(ceil_div64(ceil_div64(max_n, C), 32) * 32);
-  return bits == 2 ? launch_fused_m<1>(d_sigs, d_planes, nsig, C, chunk, d_status, st)
-                   : launch_fused_m<7>(d_sigs, d_planes, nsig, C, chunk, d_status, st);
+  k_qhist<<<grid, kQT, 0, st>>>(d_sigs, w, d_status);
+  k_qsel1<<<nsig, kQT, 0, st>>>(d_sigs, w, M, L);
+  if (M == 1)
+    k_qcand<1><<<grid, kQT, 0, st>>>(d_sigs, w);
+  else
+    k_qcand<7><<<grid, kQT, 0, st>>>(d_sigs, w);
+  k_qsel2<<<nsig, kQT, 0, st>>>(d_sigs, w, M);
+  if (M == 1)
+    k_qapply<1><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
+  else
+    k_qapply<7><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
+  TDE_COUNT_LAUNCH(5);
+  return cudaGetLastError();
 }
