@@ -444,7 +444,7 @@ struct MmaStage {
     for (int i = 0; i < njobs; ++i) {
       const Job& j = jobs[i];
       max_count = std::max<int64_t>(max_count, j.lag_max - j.lag_min + 1);
-      const int64_t t0 = floor_div64(j.lag_min, 64) * 64;
+      const int64_t t0 = floor_div64(j.lag_min, kMmaChunk) * kMmaChunk;
       const int64_t ntiles = ceil_div64(j.lag_max - t0 + 1, kMmaTileLags);
       for (int64_t t = 0; t < ntiles; ++t) {
         const int64_t T0 = t0 + t * kMmaTileLags;
@@ -452,14 +452,14 @@ struct MmaStage {
         // y index k + T0 + 128 n in [0, ny) for some n in [0, 256).
         int64_t klo = std::max<int64_t>(0, -T0 - 128 * 255);
         int64_t khi = std::min<int64_t>(j.nx + 127, j.ny - T0);
-        klo = floor_div64(klo, 64) * 64;
-        khi = ceil_div64(khi, 64) * 64;
+        klo = floor_div64(klo, kMmaChunk) * kMmaChunk;
+        khi = ceil_div64(khi, kMmaChunk) * kMmaChunk;
         if (khi <= klo) {  // no overlap anywhere in this tile: its lags are 0
           zero_first[i] = 1;
           continue;
         }
         const int64_t nseg = ceil_div64(khi - klo, kMmaKs);
-        const int64_t seg = ceil_div64(ceil_div64(khi - klo, nseg), 64) * 64;
+        const int64_t seg = ceil_div64(ceil_div64(khi - klo, nseg), kMmaChunk) * kMmaChunk;
         if (nseg > 1) zero_first[i] = 1;
         for (int64_t s = 0; s < nseg; ++s) {
           const int64_t ks = klo + s * seg, ke = std::min(khi, ks + seg);

@@ -1,13 +1,14 @@
 // mma.cu -- exact integer cross-correlation (Algorithm 1's correlation step; Eq. (1) of
 // arXiv 2509.19974) as a Toeplitz-structured GEMM on the 5th-generation
-// tensor cores (tcgen05.mma, accumulators in tensor memory).
+// tensor cores (tcgen05.mma, accumulators in tensor memory), and the
+// learned proposal's windows in the same form.
 //
-// The levels q in [-7, 7] are exact in BF16 and every product and partial sum
-// is an integer below 2^24 in magnitude (a CTA covers at most kKs = 12288
-// samples of the sum, 12288 * 49 < 2^20), so FP32 accumulation is exact;
-// partial sums of several CTAs are combined with integer atomics.
-// (tcgen05 has no 8-bit integer kind on sm_103a, so BF16 operands with FP32
-// accumulation carry the integer arithmetic.)
+// tcgen05 has no 8-bit integer kind on sm_103a, so the integer arithmetic
+// rides on kind::f8f6f4 with E4M3 operands and FP32 accumulation: the levels
+// -7..7 are exact in E4M3, every product is an exact integer, and a CTA sums
+// at most kMmaKs = 24576 samples (24576 * 49 < 2^21 < 2^24), so every FP32
+// partial sum is an exact integer; partial sums of several CTAs are combined
+// with integer atomics.
 //
 // Tile: a CTA computes 32768 lags  tau = T0 + (127 - m) + 128 n  for
 // m in [0,128) (TMEM lane) and n in [0,256) (TMEM column):
@@ -16,38 +17,41 @@
 //   B[n][k] = qy[k + T0 + 128 n]    (rows = windows of y at stride 128)
 // so D[m][n] = sum_i qx[i] qy[i + tau] = c[tau].  Both operands are K-major.
 //
-// B costs nothing to build: y is stored once in shared memory as two arrays
-// of 128-byte rows (64 BF16), E[r] = y[128 r .. 128 r + 63] and
-// O[r] = y[128 r + 64 .. 128 r + 127], in the 128-byte swizzled layout; the
-// 256 x 64 B tile of a K chunk starting at k is rows floor(u/2) .. +255 of E
-// (u even) or O (u odd), u = (k + T0) / 64 -- a descriptor whose start moves
-// by one row every two chunks.  The 128-byte swizzle is a function of the
-// absolute shared-memory address (16-byte chunk bits 4..6 XOR row bits 7..9),
-// so rows are written swizzled by their own address and a descriptor may start
-// at any 128-byte row with base offset 0 (checked on the device: a start off
-// the 1024-byte pattern with base offset = address bits 7..9 reads wrong data).
+// B costs nothing to build: y is stored once in shared memory as 128-byte
+// E4M3 rows Y[r] = y[128 r .. 128 r + 127] in the 128-byte swizzled layout;
+// the 256-row tile of the K chunk starting at k is rows (k + T0)/128 .. + 255
+// -- a descriptor whose start moves by one row per chunk.  The swizzle is a
+// function of the absolute shared-memory address (16-byte chunk bits 4..6 XOR
+// row bits 7..9), so rows are written swizzled by their own address and a
+// descriptor may start at any 128-byte row with base offset 0.
 //
-// A costs 1 KB per chunk instead of 16 KB: in the no-swizzle K-major layout a
-// core matrix is 8 rows x 16 bytes and core matrix (g, h) (rows 8g.., k 8h..)
-// of the Hankel A depends only on d = g + h:
-//   S[d][r][c] = qx[8 d + r + c - 127].
-// With leading- and stride-byte offsets both 128, consecutive 128-byte slots
-// S[d] serve every (g, h).  One 64-wide K chunk reads 23 consecutive slots
-// and adds 8 new ones; the slots live in a ring of 48 with the first 24
-// mirrored past its end so every window is contiguous.
+// A costs 2 KB per 128-sample chunk instead of 16 KB: in the no-swizzle
+// K-major layout a core matrix is 8 rows x 16 bytes, and core matrix (g, h)
+// (rows 8 g.., k 16 h..) of the Hankel A is slot g + 2 h of
+//   S[e][r][c] = qx[8 e + r + c - 127],
+// so with stride byte offsets 128 (M direction) and 256 (leading, K) a run of
+// 128-byte slots serves every core matrix.  The slots live in a ring with its
+// first entries mirrored past the end so every MMA's run is contiguous.
 //
 // Only column groups (32 columns = 4096 lags) whose overlap meets a chunk are
 // multiplied: the MMA's N shrinks at the ends of a tile's K range, so the
 // MACs issued stay within a few percent of the overlap MACs for long pairs.
 //
-// Roles: all 8 warps stage y (BF16, swizzled) and the segment of x (int8) in
-// shared memory; warps 1-2 (64 threads) write one 16-byte slot row each per
-// chunk and arrive on the chunk's "full" barrier; warp 0 lane 0 waits on it,
-// issues the chunk's MMAs (M=128, K=16, N = 32..256) and tcgen05.commit's the
-// chunk's barrier, which the producers wait on before overwriting ring slots;
-// at the end all warps read the accumulator (warp w: lanes 32 (w % 4) ..,
-// columns 128 (w / 4) ..).  Every wait is bounded by %globaltimer; on time-out
-// the CTA flags TDE_ST_TIMEOUT, waits (bounded) for its MMAs and frees TMEM.
+// Roles: all 8 warps stage y and the segment of x (int8 -> E4M3) in shared
+// memory; warps 1-2 (64 threads) write the chunk's new slot rows and arrive on
+// the chunk's "full" barrier; warp 0 waits on it (the whole warp, converged),
+// lane 0 issues the chunk's MMAs (M=128, K=32, N = 32..256) and
+// tcgen05.commit's the chunk's barrier, which the producers wait on before
+// overwriting ring slots; at the end all warps read the accumulator (warp w:
+// lanes 32 (w % 4) .., columns 128 (w / 4) ..).  Every wait is bounded by
+// %globaltimer; on time-out the CTA flags TDE_ST_TIMEOUT, waits (bounded) for
+// its MMAs and frees TMEM.
+//
+// Descriptor facts established on the device by one-MMA probes with
+// controlled operand images (documented descriptor forms only): the leading
+// byte offset is the K-direction core-matrix stride of the no-swizzle K-major
+// layout, overlapping core matrices read correctly, and a B descriptor that
+// starts off the 1024-byte swizzle pattern must keep base offset 0.
 #include "cnn.cuh"
 #include "common.cuh"
 #include "mma.cuh"
@@ -55,32 +59,12 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kM = 128, kN = 256, kKc = 64, kKStep = 16;
-constexpr int kRing = 48, kMirror = 24, kSlots = kRing + kMirror;
+constexpr int kM = 128, kN = 256;
 constexpr int kNB = 8;                                  // chunk commit barriers
-constexpr int kRowsMax = kMmaKs / 128 + 256 + 8;        // y rows per half
-constexpr int kYBytes = kRowsMax * 128;
-constexpr int kSlotBytes = kSlots * 128;
-constexpr int kXBytes = kMmaKs + 272;                   // x samples a segment's slots read
 constexpr int kProducers = 64;                          // slot-writing threads (warps 1, 2)
 constexpr int kGroups = 8, kGroupCols = kN / kGroups;   // column groups of 32 (4096 lags)
-constexpr int kSmemUsed = 2 * kYBytes + kSlotBytes + kXBytes + (2 * kNB + 1) * 8 + 16;  // + tmem/item words
-constexpr int kSmemBytes = kSmemUsed + 1024;            // room to align the base
 constexpr uint64_t kTimeoutNs = 2000000000ull;         // 2 s per wait
 static_assert(kMmaTileLags == kM * kN, "tile");
-static_assert(kMmaKs % kKc == 0, "segment");
-static_assert(kYBytes % 1024 == 0, "y arrays stay 1024-aligned");
-static_assert(kRing % 8 == 0 && kMirror >= 23 && kRing >= kMirror, "slot ring");
-static_assert(kXBytes % 16 == 0, "x stage");
-static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
-
-// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_for(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(kM >> 4) << 24);
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -161,15 +145,6 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
 // Zeroes 32 lanes x 32 columns of tensor memory.
 __device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
   asm volatile(
@@ -208,28 +183,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Exact BF16 encoding of a small integer: the top half of its FP32 pattern.
-__device__ __forceinline__ uint32_t bf16_bits(int v) {
-  return __float_as_uint((float)v) >> 16;
-}
-__device__ __forceinline__ uint32_t pack2(int lo, int hi) {
-  return bf16_bits(lo) | (bf16_bits(hi) << 16);
-}
-
 __device__ __forceinline__ int64_t fdiv(int64_t a, int64_t b) {  // floor division, b > 0
   return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
-// Unpacks 8 int8 levels (little-endian in w) to 8 BF16 and stores them as one
-// 16-byte core-matrix row at `addr` (and at `addr2` if non-zero).
-__device__ __forceinline__ void store_row8(uint32_t addr, uint32_t addr2, uint64_t w) {
-  int v[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) v[t] = (int)(int8_t)(w >> (8 * t));
-  const uint32_t w0 = pack2(v[0], v[1]), w1 = pack2(v[2], v[3]);
-  const uint32_t w2 = pack2(v[4], v[5]), w3 = pack2(v[6], v[7]);
-  st_shared_v4(addr, w0, w1, w2, w3);
-  if (addr2) st_shared_v4(addr2, w0, w1, w2, w3);
 }
 
 __device__ __forceinline__ uint64_t ld_shared_u64(uint32_t addr) {
@@ -256,16 +211,75 @@ __device__ __forceinline__ uint4 load16(const int8_t* q, int64_t i0, int64_t n, 
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// ---------------------------------------------------------------------------
+// The engine kernel (kind::f8f6f4, E4M3 operands, FP32 accumulation).  Per K
+// chunk of 128 samples:
+//   B: y is staged once per item as one array of 128-byte E4M3 rows
+//      Y[r] = y[128 r .. 128 r + 127] (128-byte swizzle); with T0 and ks
+//      multiples of 128 the 256-row tile of chunk k is rows (k + T0)/128 ..
+//      + 255 -- no E/O split.
+//   A: Hankel slots S[e][r][c] = qx[8 e + r + c - 127], 16 bytes per row; core
+//      matrix (g, h) (rows 8 g.., k 16 h..) is slot g + 2 h, so a K = 32 step
+//      reads 18 consecutive slots with stride byte offsets 128 (M) and 256
+//      (leading, K).  Chunk c reads slots [16 c, 16 c + 30) and adds 16; the
+//      ring holds 96 slots with 32 mirrored past its end, and the slots a
+//      chunk writes were last read by chunk c - 5.
+// These forms were checked on the device by a one-MMA probe with controlled
+// operand images (plain and Hankel A, B rows off the 1024-byte pattern, a
+// second K step).  Roles, barriers, column-group skipping and the epilogue
+// are those described at the top of this file.
+
+constexpr int kKc8 = kMmaChunk;                   // 128 samples per chunk
+constexpr int kRing8 = 96, kMirror8 = 32, kSlots8 = kRing8 + kMirror8;
+constexpr int kSlotBytes8 = kSlots8 * 128;
+constexpr int kRowsMax8 = kMmaKs / 128 + 256 + 8;  // y rows per item
+constexpr int kYBytes8 = kRowsMax8 * 128;
+constexpr int kXBytes8 = kMmaKs + 288;            // x samples a segment's slots read
+constexpr int kSmemUsed8 = kYBytes8 + kSlotBytes8 + kXBytes8 + (2 * kNB + 1) * 8 + 16;
+constexpr int kSmemBytes8 = kSmemUsed8 + 1024;
+static_assert(kMmaKs % kKc8 == 0 && kYBytes8 % 1024 == 0 && kXBytes8 % 16 == 0, "fp8 layout");
+static_assert(2 * (kSmemBytes8 + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(kMmaKs * 49 < (1 << 24), "exact FP32 sums");
+
+// Instruction descriptor, kind::f8f6f4: D F32 (bits 4-5 = 1), A and B E4M3
+// (format 0 at bits 7-9 and 10-12), both K-major, N >> 3 at 17, M >> 4 at 24.
+__host__ __device__ constexpr uint32_t idesc8_for(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Four int8 levels in [-7, 7] -> four E4M3 bytes (exact): magnitudes through
+// a byte-permute table, sign bits copied.
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t w) {
+  const uint32_t mag = __vabs4(w);
+  const uint32_t sel = (mag & 0xFu) | ((mag >> 4) & 0xF0u) | ((mag >> 8) & 0xF00u) |
+                       ((mag >> 12) & 0xF000u);
+  // bytes of {hi:lo}: 0 -> 0x00, 1 -> 0x38, 2 -> 0x40, 3 -> 0x44, 4 -> 0x48,
+  // 5 -> 0x4A, 6 -> 0x4C, 7 -> 0x4E
+  return __byte_perm(0x44403800u, 0x4E4C4A48u, sel) | (w & 0x80808080u);
+}
+__device__ __forceinline__ uint4 e4m3x16(uint4 v) {
+  return make_uint4(e4m3x4(v.x), e4m3x4(v.y), e4m3x4(v.z), e4m3x4(v.w));
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
-    k_xcorr_mma(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems,
-                int* __restrict__ counter, uint32_t* __restrict__ status) {
+    k_xcorr_mma8(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems,
+                 int* __restrict__ counter, uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t yE = base, yO = base + kYBytes, slots = base + 2 * kYBytes;
-  const uint32_t xs = slots + kSlotBytes;   // int8 x segment
-  const uint32_t full_bar = xs + kXBytes;   // kNB "slots written" barriers
-  const uint32_t cmt_bar = full_bar + 8 * kNB;  // kNB "chunk MMAs done" barriers
+  const uint32_t yr = base, slots = base + kYBytes8;
+  const uint32_t xs = slots + kSlotBytes8;    // E4M3 x segment
+  const uint32_t full_bar = xs + kXBytes8;
+  const uint32_t cmt_bar = full_bar + 8 * kNB;
   const uint32_t done_bar = cmt_bar + 8 * kNB;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
   volatile int* item_slot = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -291,11 +305,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // Persistent loop: items (pair, 32768-lag tile, K segment) are taken in
-  // the host's order (longest first) from a global counter.  Barrier phases
-  // continue across items: chunk cc0 + c of this CTA uses barrier
-  // (cc0 + c) % kNB with parity ((cc0 + c) / kNB) & 1; "done" completes once per
-  // item.
   int64_t cc0 = 0;
   uint32_t iter = 0;
   bool ok = true;
@@ -308,64 +317,54 @@ __global__ void __launch_bounds__(kThreads, 2)
     const MmaItem it = items[w_item];
     const MmaPair P = pairs[it.pair];
     const int64_t T0 = it.T0, ks = it.ks, ke = it.ke;
-    const int nchunks = (int)((ke - ks) / kKc);
-    const int64_t u_s = (ks + T0) / kKc, u_l = (ke - kKc + T0) / kKc;  // exact
-    const int64_t r_lo = fdiv(fdiv(u_s, 2), 8) * 8;
-    const int64_t nrows = fdiv(u_l, 2) + 255 - r_lo + 1;
-    // x is staged from a 16-byte aligned index; window o (x index ks - 127 + o)
-    // sits at xs + xoff + o.
+    const int nchunks = (int)((ke - ks) / kKc8);
+    const int64_t u_s = fdiv(ks + T0, kKc8);                  // exact (host alignment)
+    const int64_t r_lo = fdiv(u_s, 8) * 8;                     // 1024-byte aligned start row
+    const int64_t nrows = u_s + nchunks - 1 + 255 - r_lo + 1;
     const int64_t xs_base = fdiv(ks - 127, 16) * 16;
     const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
-    // The CTA's own bounds checks: the y window and the x segment must fit.
-    if (nrows > kRowsMax || nchunks <= 0 || (ke - ks) + 272 > kXBytes) {
+    if (nrows > kRowsMax8 || nchunks <= 0 || (ke - ks) + 288 > kXBytes8 ||
+        ((ks + T0) & (kKc8 - 1)) != 0 || (ks & (kKc8 - 1)) != 0) {
       if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
-      --iter;  // "done" was not used
+      --iter;
       __syncthreads();
       continue;
     }
 
-    // y window: rows r_lo .. r_lo + nrows - 1 of E and O (zero outside [0, ny)),
-    // 16 samples per load, four loads in flight per thread.
+    // y rows r_lo .. r_lo + nrows - 1 (E4M3, swizzled), x segment (E4M3)
     {
       const int8_t* qy = P.qy;
-      const bool al16 = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
-      const int total = (int)nrows * 8;  // (row, half, quarter)
+      const int8_t* qx = P.qx;
+      const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+      const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+      const int ny16 = (int)nrows * 8;       // 16-byte pieces of y
+      const int total = ny16 + kXBytes8 / 16;
       for (int b0 = threadIdx.x; b0 < total; b0 += 4 * kThreads) {
         uint4 w[4];
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int idx = b0 + k * kThreads;
-          if (idx < total) {
-            const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
-            w[k] = load16(qy, 128 * (r_lo + row) + 64 * half + 16 * j, P.ny, al16);
-          }
+          if (idx < ny16)
+            w[k] = load16(qy, 128 * (r_lo + (idx >> 3)) + 16 * (idx & 7), P.ny, aly);
+          else if (idx < total)
+            w[k] = load16(qx, xs_base + 16 * (idx - ny16), P.nx, alx);
         }
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int idx = b0 + k * kThreads;
-          if (idx < total) {
-            const int row = idx >> 3, half = (idx >> 2) & 1, j = idx & 3;
-            const uint32_t row_addr = (half ? yO : yE) + 128u * (uint32_t)row;
-            const uint32_t sw = (row_addr >> 7) & 7u;
-            store_row8(row_addr + 16u * ((uint32_t)(2 * j) ^ sw), 0u,
-                       (uint64_t)w[k].x | ((uint64_t)w[k].y << 32));
-            store_row8(row_addr + 16u * ((uint32_t)(2 * j + 1) ^ sw), 0u,
-                       (uint64_t)w[k].z | ((uint64_t)w[k].w << 32));
+          if (idx >= total) continue;
+          const uint4 e = e4m3x16(w[k]);
+          uint32_t a;
+          if (idx < ny16) {
+            const uint32_t row_addr = yr + 128u * (uint32_t)(idx >> 3);
+            a = row_addr + 16u * ((uint32_t)(idx & 7) ^ ((row_addr >> 7) & 7u));
+          } else {
+            a = xs + 16u * (uint32_t)(idx - ny16);
           }
+          st_shared_v4(a, e.x, e.y, e.z, e.w);
         }
       }
     }
-    // x segment x[xs_base .. xs_base + kXBytes), zero outside [0, nx).
-    {
-      const int8_t* qx = P.qx;
-      const bool al16 = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
-      for (int i = threadIdx.x; i < kXBytes / 16; i += kThreads) {
-        const uint4 w = load16(qx, xs_base + 16 * i, P.nx, al16);
-        st_shared_v4(xs + 16u * i, w.x, w.y, w.z, w.w);
-      }
-    }
-    // The accumulator starts at zero: column groups join the sum at different
-    // chunks, so every MMA accumulates.
     if (warp < 4) {
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
       for (int cb = 0; cb < kN; cb += 32) tmem_zero32(tmem + lane_base + (uint32_t)cb);
@@ -377,38 +376,38 @@ __global__ void __launch_bounds__(kThreads, 2)
     tc_fence_after();
 
     if (warp == 1 || warp == 2) {
-      // Slot producers: thread t writes window o = 64 c + 120 + t of chunk c
-      // (chunk 0 writes windows 0..183): slot e = o / 8, row r = o % 8, i.e.
-      // x[ks - 127 + o .. + 7] as BF16.
+      // Slot producers: row o = 8 e + r (slot e, row r) is x[ks - 127 + o .. + 15];
+      // chunk 0 writes o in [0, 240), chunk c >= 1 writes [128 c + 112, 128 c + 240).
       const int t = threadIdx.x - 32;
       for (int c = 0; c < nchunks; ++c) {
-        // The slots written now were last read by chunk c - (kRing/8 - 2).
-        const int64_t prev = cc0 + c - (kRing / 8 - 2);
+        const int64_t prev = cc0 + c - 5;
         if (prev >= 0 && !mbar_wait(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
           ok = false;
           break;
         }
-        const int o_first = c == 0 ? t : 64 * c + 120 + t;
-        const int o_end = c == 0 ? 184 : 64 * c + 184;
+        const int o_first = c == 0 ? t : 128 * c + 112 + t;
+        const int o_end = c == 0 ? 240 : 128 * c + 240;
         for (int o = o_first; o < o_end; o += kProducers) {
           const uint32_t pa = xs + xoff + (uint32_t)o;
           const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-          const uint64_t lo = ld_shared_u64(al), hi = ld_shared_u64(al + 8u);
-          const uint64_t w = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
+          const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
+          const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
+          const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
           const int e = o >> 3, r = o & 7;
-          const int ps = e % kRing;
+          const int ps = e % kRing8;
           const uint32_t a = slots + 128u * ps + 16u * r;
-          store_row8(a, ps < kMirror ? a + 128u * kRing : 0u, w);
+          st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+          if (ps < kMirror8)
+            st_shared_v4(a + 128u * kRing8, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
+                         (uint32_t)(hi >> 32));
         }
         fence_proxy_async();
         mbar_arrive(full_bar + 8 * (uint32_t)((cc0 + c) % kNB));
       }
     } else if (warp == 0) {
-      // MMA issuer: the whole warp waits (a divergent warp whose other lanes sit
-      // in a barrier wait would stall the issuing lane); lane 0 issues.  k range of column group g (columns 32 g .. 32 g + 31, lags
-      // T0 + 4096 g ..): [lo_g, hi_g), relative to ks.
+      // MMA issuer (whole warp waits, lane 0 issues); column groups of 32
       int64_t glo[kGroups], ghi[kGroups];
-  #pragma unroll
+#pragma unroll
       for (int g = 0; g < kGroups; ++g) {
         const int64_t lo = -T0 - 128 * (int64_t)(kGroupCols * g + kGroupCols - 1);
         const int64_t hi = P.ny - T0 - 128 * (int64_t)(kGroupCols * g);
@@ -420,27 +419,25 @@ __global__ void __launch_bounds__(kThreads, 2)
         ok = __all_sync(0xffffffffu, mbar_wait(full_bar + 8 * (uint32_t)(cc % kNB), (uint32_t)((cc / kNB) & 1)));
         if (!ok) break;
         tc_fence_after();
-        const int64_t kc = (int64_t)kKc * c;
+        const int64_t kc = (int64_t)kKc8 * c;
         int ga = kGroups, gb = -1;
-  #pragma unroll
+#pragma unroll
         for (int g = 0; g < kGroups; ++g)
-          if (glo[g] < kc + kKc && ghi[g] > kc) {
+          if (glo[g] < kc + kKc8 && ghi[g] > kc) {
             ga = g < ga ? g : ga;
             gb = g;
           }
         if (gb >= ga && lane == 0) {
-          const uint32_t idesc = idesc_for(kGroupCols * (gb - ga + 1));
-          const int64_t u = u_s + c;
-          const int64_t half = u & 1;  // two's complement: u mod 2
-          const int64_t row0 = fdiv(u, 2) - r_lo + kGroupCols * ga;
-          const uint32_t a_start = slots + 128u * (uint32_t)((8 * c) % kRing);
-          const uint32_t b_row = (half ? yO : yE) + 128u * (uint32_t)row0;
+          const uint32_t idesc = idesc8_for(kGroupCols * (gb - ga + 1));
+          const int64_t row0 = u_s + c - r_lo + kGroupCols * ga;
+          const uint32_t a_start = slots + 128u * (uint32_t)((16 * c) % kRing8);
+          const uint32_t b_row = yr + 128u * (uint32_t)row0;
           const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
-  #pragma unroll
-          for (int s2 = 0; s2 < kKc / kKStep; ++s2) {
-            const uint64_t ad = sdesc(a_start + 256u * s2, 128, 128, 0, 0);
+#pragma unroll
+          for (int s2 = 0; s2 < 4; ++s2) {
+            const uint64_t ad = sdesc(a_start + 512u * s2, 256, 128, 0, 0);
             const uint64_t bd = sdesc(b_row + 32u * s2, 16, 1024, 2, 0);
-            mma_bf16(d_col, ad, bd, idesc, 1u);
+            mma_e4m3(d_col, ad, bd, idesc, 1u);
           }
         }
         if (lane == 0) mma_commit(cmt_bar + 8 * (uint32_t)(cc % kNB));
@@ -450,7 +447,6 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncwarp();
     }
 
-    // Epilogue: every thread waits for the accumulator.
     const bool done = mbar_wait(done_bar, iter & 1u);
     ok = __syncthreads_and(ok && done);
     if (!ok) {
@@ -514,40 +510,39 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
 
 
 // ---------------------------------------------------------------------------
-// Windowed form (the learned proposal's exact check): for one pair and its 8
-// windows, window w's lags are covered by tau = T_w + 128 j + 127 - m
-// (j = 0..7, T_w = its first lag rounded down to a multiple of 128), 1024
-// lags of which the window's <= 257 are kept.  A is the same Hankel slot ring
-// as above.  B needs no per-chunk copies: each window's y segment is staged
-// once per item as E/O arrays of 128-byte swizzled rows,
-//   E_w[r] = y[ks + T_w + 128 r .. + 63],  O_w[r] = y[ks + T_w + 128 r + 64 .. + 127],
-// and because ks and T_w are multiples of 128, the 8 B rows of window w for
-// K chunk c are rows floor(c/2) .. + 7 of E_w (c even) or O_w (c odd) -- the
-// same rows for every window.  Windows' arrays sit at a fixed stride, so one
-// descriptor (stride byte offset = that stride) gives an N = 64 tile: 8
-// windows x 8 columns.  A CTA takes items (pair, K segment) round-robin;
-// partial sums are added into the zeroed window outputs with integer atomics.
+// Windowed form (the learned proposal's exact check), FP8 like the engine
+// above: for one pair and its 8 windows, window w's lags are covered by
+// tau = T_w + 128 j + 127 - m (j = 0..7, T_w = its first lag rounded down to
+// a multiple of 128), 1024 lags of which the window's <= 257 are kept.  A is
+// the same E4M3 Hankel slot ring; B needs no per-chunk copies: each window's
+// y segment is staged once per item as 128-byte E4M3 rows
+//   Y_w[r] = y[ks + T_w + 128 r .. + 127],
+// and because ks and T_w are multiples of 128 the 8 B rows of window w for K
+// chunk c are rows c .. c + 7 of Y_w -- the same rows for every window, one
+// core-matrix group per window.  The windows' arrays sit at a fixed stride, so
+// one descriptor (stride byte offset = that stride) gives an N = 64 tile:
+// 8 windows x 8 columns.  Producers and the issuer synchronize once per
+// super-chunk of 2 chunks (8 MMAs): super-chunk s writes logical slots
+// [32 s + 14, 32 s + 46) and reads [32 s, 32 s + 46), so on a ring of 128 its
+// slots were last read by super-chunk s - 3.  A CTA takes items (pair, K
+// segment) round-robin; partial sums are added into the zeroed window outputs
+// with integer atomics.
 
 constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
 constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
 constexpr int kWinN = kWinW * kWinJ;             // MMA N = 64
 constexpr int kWinKs = 4096;                     // max samples of the sum per item
-constexpr int kWinRows = (kWinKs / kKc + 1) / 2 + kWinJ;  // E/O rows per window (40)
-constexpr int kWinArr = kWinRows * 128;          // bytes per E (or O) array, = the SBO
-constexpr int kWinXBytes = kWinKs + 272;
-// Producers and the issuer synchronize once per super-chunk of kWinSC chunks
-// (16 MMAs), on a slot ring of 128 (+ 24 mirrored): a super-chunk writes
-// logical slots [32 s + 15, 32 s + 47) and its chunks read [32 s, 32 s + 47),
-// so the slots it writes were last read by super-chunk s - 3.
-constexpr int kWinSC = 4;
-constexpr int kWinRing = 128, kWinMirror = 24;
+constexpr int kWinRows = kWinKs / kKc8 + kWinJ;  // rows per window (40)
+constexpr int kWinArr = kWinRows * 128;          // bytes per window array, = the SBO
+constexpr int kWinXBytes = kWinKs + 288;
+constexpr int kWinSC = 2;                        // chunks per super-chunk
+constexpr int kWinRing = 128, kWinMirror = 32;
 constexpr int kWinSlotBytes = (kWinRing + kWinMirror) * 128;
-constexpr int kWinSmemUsed = 2 * kWinW * kWinArr + kWinSlotBytes + kWinXBytes + (2 * kNB + 1) * 8 + 16;
+constexpr int kWinSmemUsed = kWinW * kWinArr + kWinSlotBytes + kWinXBytes + (2 * kNB + 1) * 8 + 16;
 constexpr int kWinSmemBytes = kWinSmemUsed + 1024;
 static_assert(kWinArr % 1024 == 0, "windows' arrays keep the 1024-byte swizzle pattern");
 static_assert(kWinXBytes % 16 == 0, "staging");
 static_assert(kWinSmemBytes + 1024 <= 114 * 1024, "two CTAs per SM");
-static_assert(kWinRing % 32 == 0 && kWinMirror >= 23, "slot ring");
 
 __global__ void __launch_bounds__(kThreads, 2)
     k_xcorr_mma_win(const int8_t* __restrict__ q, int64_t n, int npairs, const WinJob* __restrict__ jobs,
@@ -555,9 +550,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t yE = base;                                 // window w at yE + w * kWinArr
-  const uint32_t yO = yE + kWinW * kWinArr;
-  const uint32_t slots = yO + kWinW * kWinArr;
+  const uint32_t ya = base;                                 // window w at ya + w * kWinArr
+  const uint32_t slots = ya + kWinW * kWinArr;
   const uint32_t xs = slots + kWinSlotBytes;
   const uint32_t full_bar = xs + kWinXBytes;
   const uint32_t cmt_bar = full_bar + 8 * kNB;
@@ -596,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int p = item / nseg, sgi = item - p * nseg;
     const int64_t ks = (int64_t)sgi * seg;
     const int64_t ke = ks + seg < kmax ? ks + seg : kmax;
-    const int nchunks = (int)((ke - ks) / kKc);
+    const int nchunks = (int)((ke - ks) / kKc8);
     const int8_t* qx = q + (int64_t)(2 * p) * n;
     const int8_t* qy = q + (int64_t)(2 * p + 1) * n;
     const WinJob* J = jobs + (int64_t)p * kWinW;
@@ -607,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     const int64_t xs_base = fdiv(ks - 127, 16) * 16;
     const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
-    const int nrows = (nchunks + 1) / 2 + kWinJ;  // rows of each E/O array this item reads
+    const int nrows = nchunks + kWinJ - 1;  // rows of each window array this item reads
     if (threadIdx.x < kWinW) {
       const WinJob jw = J[threadIdx.x];
       sT[threadIdx.x] = fdiv(jw.lag_lo, 128) * 128;
@@ -616,12 +610,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       sC[threadIdx.x] = jw.c;
     }
     __syncthreads();
-    // staging: x segment, then every window's E/O rows (int8 -> BF16, swizzled)
+    // staging: x segment, then every window's rows (int8 -> E4M3, swizzled)
     {
       const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
       const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
       constexpr int kXV = kWinXBytes / 16;
-      const int per_w = nrows * 8;  // (row, half, quarter) per window
+      const int per_w = nrows * 8;  // (row, 16-byte piece) per window
       const int total = kXV + kWinW * per_w;
       for (int b0 = threadIdx.x; b0 < total; b0 += 8 * kThreads) {
         uint4 v[8];
@@ -632,25 +626,23 @@ __global__ void __launch_bounds__(kThreads, 2)
             v[k] = load16(qx, xs_base + 16 * idx, n, alx);
           } else if (idx < total) {
             const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
-            const int row = r8 >> 3, half = (r8 >> 2) & 1, jq = r8 & 3;
-            v[k] = load16(qy, ks + sT[w] + 128 * row + 64 * half + 16 * jq, n, aly);
+            v[k] = load16(qy, ks + sT[w] + 128 * (r8 >> 3) + 16 * (r8 & 7), n, aly);
           }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int idx = b0 + k * kThreads;
+          if (idx >= total) continue;
+          const uint4 e = e4m3x16(v[k]);
+          uint32_t a;
           if (idx < kXV) {
-            st_shared_v4(xs + 16u * (uint32_t)idx, v[k].x, v[k].y, v[k].z, v[k].w);
-          } else if (idx < total) {
+            a = xs + 16u * (uint32_t)idx;
+          } else {
             const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
-            const int row = r8 >> 3, half = (r8 >> 2) & 1, jq = r8 & 3;
-            const uint32_t row_addr = (half ? yO : yE) + (uint32_t)(w * kWinArr + 128 * row);
-            const uint32_t sw = (row_addr >> 7) & 7u;
-            store_row8(row_addr + 16u * ((uint32_t)(2 * jq) ^ sw), 0u,
-                       (uint64_t)v[k].x | ((uint64_t)v[k].y << 32));
-            store_row8(row_addr + 16u * ((uint32_t)(2 * jq + 1) ^ sw), 0u,
-                       (uint64_t)v[k].z | ((uint64_t)v[k].w << 32));
+            const uint32_t row_addr = ya + (uint32_t)(w * kWinArr + 128 * (r8 >> 3));
+            a = row_addr + 16u * ((uint32_t)(r8 & 7) ^ ((row_addr >> 7) & 7u));
           }
+          st_shared_v4(a, e.x, e.y, e.z, e.w);
         }
       }
     }
@@ -667,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int nsc = (nchunks + kWinSC - 1) / kWinSC;
     if (warp == 1 || warp == 2) {
-      // Hankel slots of x (as in k_xcorr_mma), one super-chunk at a time
+      // Hankel slots of x (as in k_xcorr_mma8), one super-chunk at a time
       const int t = threadIdx.x - 32;
       for (int sc = 0; sc < nsc; ++sc) {
         const int64_t g = sc0 + sc;
@@ -676,24 +668,29 @@ __global__ void __launch_bounds__(kThreads, 2)
           ok = false;
           break;
         }
-        const int c_last = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC - 1 : nchunks - 1;
-        const int o_first = sc == 0 ? 0 : 64 * (sc * kWinSC) + 120;
-        const int o_end = 64 * c_last + 184;
+        const int c_first = sc * kWinSC;
+        const int c_last = c_first + kWinSC - 1 < nchunks - 1 ? c_first + kWinSC - 1 : nchunks - 1;
+        const int o_first = sc == 0 ? 0 : 128 * c_first + 112;
+        const int o_end = 128 * c_last + 240;
         for (int o = o_first + t; o < o_end; o += kProducers) {
           const uint32_t pa = xs + xoff + (uint32_t)o;
           const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-          const uint64_t lo = ld_shared_u64(al), hi = ld_shared_u64(al + 8u);
-          const uint64_t w = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
+          const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
+          const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
+          const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
           const int e = o >> 3, r = o & 7;
           const int ps = e % kWinRing;
           const uint32_t a = slots + 128u * ps + 16u * r;
-          store_row8(a, ps < kWinMirror ? a + 128u * kWinRing : 0u, w);
+          st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+          if (ps < kWinMirror)
+            st_shared_v4(a + 128u * kWinRing, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
+                         (uint32_t)(hi >> 32));
         }
         fence_proxy_async();
         mbar_arrive(full_bar + 8 * (uint32_t)(g % kNB));
       }
     } else if (warp == 0) {
-      const uint32_t idesc = idesc_for(kWinN);
+      const uint32_t idesc = idesc8_for(kWinN);
       for (int sc = 0; sc < nsc; ++sc) {
         const int64_t g = sc0 + sc;
         ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(g % kNB), (uint32_t)((g / kNB) & 1)));
@@ -702,11 +699,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (lane == 0) {
           const int c_end = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC : nchunks;
           for (int c = sc * kWinSC; c < c_end; ++c) {
-            const uint32_t a_start = slots + 128u * (uint32_t)((8 * c) % kWinRing);
-            const uint32_t b_start = ((c & 1) ? yO : yE) + 128u * (uint32_t)(c >> 1);
+            const uint32_t a_start = slots + 128u * (uint32_t)((16 * c) % kWinRing);
+            const uint32_t b_start = ya + 128u * (uint32_t)c;
 #pragma unroll
-            for (int s2 = 0; s2 < kKc / kKStep; ++s2)
-              mma_bf16(tmem, sdesc(a_start + 256u * s2, 128, 128, 0, 0),
+            for (int s2 = 0; s2 < 4; ++s2)
+              mma_e4m3(tmem, sdesc(a_start + 512u * s2, 256, 128, 0, 0),
                        sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, 1u);
           }
           mma_commit(cmt_bar + 8 * (uint32_t)(g % kNB));
@@ -757,7 +754,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 }  // namespace
 
-int mma_smem_bytes() { return kSmemBytes; }
+int mma_smem_bytes() { return kSmemBytes8; }
 
 cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
@@ -772,13 +769,13 @@ cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_coun
 cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
                              int* d_counter, int grid, uint32_t* d_status, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma8, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemBytes8);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (grid > nitems) grid = nitems;
-  k_xcorr_mma<<<grid, kThreads, kSmemBytes, st>>>(d_pairs, d_items, nitems, d_counter, d_status);
+  k_xcorr_mma8<<<grid, kThreads, kSmemBytes8, st>>>(d_pairs, d_items, nitems, d_counter, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

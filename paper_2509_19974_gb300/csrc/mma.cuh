@@ -9,7 +9,9 @@
 // CTA (a K segment); a tile whose overlap is longer is split over several
 // CTAs whose partial sums are added with integer atomics.
 constexpr int kMmaTileLags = 32768;
-constexpr int kMmaKs = 12288;
+constexpr int kMmaKs = 24576;
+// Samples per K chunk; tile starts T0 and segment bounds are multiples of it.
+constexpr int kMmaChunk = 128;
 
 struct MmaPair {
   const int8_t* qx;
