@@ -1204,17 +1204,26 @@ bool model_len_ok(int64_t n) { return n >= 16384 && n % 2048 == 0 && n <= ((int6
 struct CnnPlan {
   int P = 0, Ld = 0, Lf = 0;
   size_t o_d = 0, o_out[kCnnLayers] = {}, o_pre[kCnnLayers] = {}, o_scores = 0;
+  size_t o_act[kCnnLayers - 1] = {};  // inference: BF16 activation rows
+  bool train_ = false;
   size_t o_dscores = 0, o_dalpha = 0, o_dz = 0, o_dA = 0, o_dB = 0, o_partial = 0, o_loss = 0;
   void plan(Layout& L, int npairs, int64_t n, bool train) {
     P = npairs;
+    train_ = train;
     Ld = (int)(n / kCnnDec);
     Lf = Ld / 16;
     const size_t S = 2 * (size_t)P;
-    o_d = L.w<float>(S * Ld);
-    for (int l = 0; l < kCnnLayers; ++l) {
-      const size_t len = (size_t)Ld >> l;  // input length of layer l
-      o_out[l] = L.w<float>(S * kCnnC * (len / 2));
-      if (train) o_pre[l] = L.w<float>(S * kCnnC * len);
+    if (!train) {
+      for (int l = 0; l + 1 < kCnnLayers; ++l)
+        o_act[l] = L.w<uint16_t>(S * kCnnC * (size_t)(Ld >> (l + 1)));
+      o_out[kCnnLayers - 1] = L.w<float>(S * kCnnC * (size_t)Lf);
+    } else {
+      o_d = L.w<float>(S * Ld);
+      for (int l = 0; l < kCnnLayers; ++l) {
+        const size_t len = (size_t)Ld >> l;  // input length of layer l
+        o_out[l] = L.w<float>(S * kCnnC * (len / 2));
+        o_pre[l] = L.w<float>(S * kCnnC * len);
+      }
     }
     o_scores = L.w<float>((size_t)P * (2 * Lf - 1));
     if (train) {
@@ -1232,6 +1241,16 @@ struct CnnPlan {
   }
   cudaError_t forward(const Bases& B, const tde_model* m, const int8_t* q, int64_t n, bool train,
                       cudaStream_t st) const {
+    if (!train) {
+      uint16_t* act[kCnnLayers - 1];
+      for (int l = 0; l + 1 < kCnnLayers; ++l) act[l] = B.dw<uint16_t>(o_act[l]);
+      cudaError_t e = launch_cnn_infer(q, n, 2 * P, m->wbf, m->params, act,
+                                       B.dw<float>(o_out[kCnnLayers - 1]), st);
+      if (e == cudaSuccess)
+        e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
+                              B.dw<float>(o_scores), st);
+      return e;
+    }
     cudaError_t e = launch_cnn_decimate(q, n, 2 * P, B.dw<float>(o_d), st);
     for (int l = 0; l < kCnnLayers && e == cudaSuccess; ++l) {
       CnnLayerIO io{layer_in(B, l), train ? B.dw<float>(o_pre[l]) : nullptr, B.dw<float>(o_out[l]),
@@ -1252,7 +1271,6 @@ tde_status check_model(tde_ctx* ctx, const tde_model* m) {
   return TDE_OK;
 }
 
-// Window jobs of the proposal: [c - 128, c + 128] clipped to the overlap.
 // Window w of pair p: lags [c - 128, c + 128] clipped to the overlap range;
 // lag tau lands at cbuf[i * stride + tau - (c - 128)].
 __global__ void k_make_windows(const int32_t* __restrict__ centres, int npairs, int64_t n,

@@ -236,6 +236,192 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
   }
 }
 
+// ---- inference chain with BF16 activation rows
+// Inference keeps the activations between layers as BF16 rows [signal][pos][32
+// channels] (64 bytes per position): the tensor-core layers round their inputs
+// to BF16 anyway, so the values are those of the FP32 chain, at half the
+// traffic and with 16-byte loads.  The last layer writes FP32 features
+// [signal][32][Lf] for the scores.
+
+// Layer 0 fused with the decimation: d[j] = (sum of q[16 j .. 16 j + 15]) / 4,
+// conv (kernel 9, pad 4, 1 -> 32 channels) + bias, ReLU, max-pool 2 -> BF16
+// rows.  A CTA makes 256 pooled positions; thread = one pooled position, all
+// 32 channels (FP32 arithmetic in the same order as k_conv_fwd<1>).
+constexpr int kC1T = 256;  // pooled positions per CTA
+
+__global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict__ q, int64_t n,
+                                                        const uint16_t* __restrict__ wbf,
+                                                        const float* __restrict__ bias,
+                                                        uint16_t* __restrict__ out) {
+  __shared__ float d_s[2 * kC1T + 8];
+  __shared__ __align__(16) float w_s[kCnnK][kCnnC];
+  __shared__ __align__(16) float b_s[kCnnC];
+  const int s = blockIdx.y;
+  const int Ld = (int)(n / kCnnDec);
+  const int P0 = blockIdx.x * kC1T;          // first pooled position
+  const int d0 = 2 * P0 - 4;                 // d index of d_s[0]
+  const int8_t* src = q + (int64_t)s * n;
+  for (int i = threadIdx.x; i < 2 * kC1T + 8; i += kThreads) {
+    const int j = d0 + i;
+    float v = 0.f;
+    if (j >= 0 && j < Ld) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)j * kCnnDec));
+      int acc = 0;
+      acc = __dp4a((int)w.x, 0x01010101, acc);
+      acc = __dp4a((int)w.y, 0x01010101, acc);
+      acc = __dp4a((int)w.z, 0x01010101, acc);
+      acc = __dp4a((int)w.w, 0x01010101, acc);
+      v = 0.25f * (float)acc;
+    }
+    d_s[i] = v;
+  }
+  for (int i = threadIdx.x; i < kCnnK * kCnnC; i += kThreads) {
+    const int co = i / kCnnK, k = i % kCnnK;
+    w_s[k][co] = bf16_to_f(wbf[i]);
+  }
+  if (threadIdx.x < kCnnC) b_s[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  const int P = P0 + threadIdx.x;
+  if (P >= Ld / 2) return;
+  float dv[kCnnK + 1];  // d at pre-pool positions 2P - 4 .. 2P + 5
+#pragma unroll
+  for (int k = 0; k <= kCnnK; ++k) dv[k] = d_s[2 * threadIdx.x + k];
+  uint32_t packed[kCnnC / 2];
+#pragma unroll
+  for (int c4 = 0; c4 < kCnnC / 4; ++c4) {
+    float a0[4], a1[4];  // pre-pool positions 2P, 2P + 1 of channels 4 c4 ..
+    const float4 bb = *reinterpret_cast<const float4*>(&b_s[4 * c4]);
+    a0[0] = a1[0] = bb.x, a0[1] = a1[1] = bb.y, a0[2] = a1[2] = bb.z, a0[3] = a1[3] = bb.w;
+#pragma unroll
+    for (int k = 0; k < kCnnK; ++k) {
+      const float4 w = *reinterpret_cast<const float4*>(&w_s[k][4 * c4]);
+      const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        a0[h] = fmaf(wv[h], dv[k], a0[h]);
+        a1[h] = fmaf(wv[h], dv[k + 1], a1[h]);
+      }
+    }
+    float r[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) r[h] = fmaxf(fmaxf(a0[h], 0.f), fmaxf(a1[h], 0.f));
+    packed[2 * c4] = pack_bf16x2(r[0], r[1]);
+    packed[2 * c4 + 1] = pack_bf16x2(r[2], r[3]);
+  }
+  uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)s * (Ld / 2) + P) * kCnnC);
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+    dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// 32 -> 32 channel layer on BF16 rows: conv (kernel 9, pad 4) + bias, ReLU,
+// max-pool 2.  The same tiles and accumulation order as k_conv_fwd_tc, with
+// fragments loaded by ldmatrix.  kLast: FP32 channel-major output, else BF16
+// rows.
+template <bool kLast>
+__global__ void __launch_bounds__(kThreads) k_conv_rows(const uint16_t* __restrict__ in,
+                                                        void* __restrict__ out, int L,
+                                                        const uint16_t* __restrict__ wbf,
+                                                        const float* __restrict__ bias) {
+  extern __shared__ __align__(16) uint32_t tsm[];
+  uint16_t* xs = reinterpret_cast<uint16_t*>(tsm);                 // [kTP + 8][kXR]
+  uint16_t* ws = xs + (kTP + 8) * kXR;                             // [9][32 co][kXR]
+  const int s = blockIdx.y, p0 = blockIdx.x * kTP;
+  const uint16_t* src = in + (int64_t)s * L * kCnnC;
+  // X rows r <-> position p0 - 4 + r: four 16-byte pieces per row
+  for (int idx = threadIdx.x; idx < (kTP + 8) * 4; idx += kThreads) {
+    const int r = idx >> 2, piece = idx & 3;
+    const int pos = p0 - 4 + r;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (pos >= 0 && pos < L) v = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)pos * kCnnC) + piece);
+    *reinterpret_cast<uint4*>(xs + r * kXR + 8 * piece) = v;
+  }
+  for (int idx = threadIdx.x; idx < kCnnC * kCnnC * kCnnK; idx += kThreads) {
+    const int co = idx / (kCnnC * kCnnK), r = idx % (kCnnC * kCnnK);
+    const int ci = r / kCnnK, k = r % kCnnK;
+    ws[(k * kCnnC + co) * kXR + ci] = wbf[idx];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int nmt = (L - p0) < kTP ? (L - p0) / 16 : kTP / 16;  // m-tiles of this CTA
+  const uint32_t xs_a = (uint32_t)__cvta_generic_to_shared(xs);
+  const uint32_t ws_a = (uint32_t)__cvta_generic_to_shared(ws);
+  // ldmatrix row addresses: A (16 x 16): lanes 0-7 rows 0-7 k 0-7, 8-15 rows 8-15
+  // k 0-7, 16-23 rows 0-7 k 8-15, 24-31 rows 8-15 k 8-15.  B (two n-tiles of 8
+  // co x 16 ci): lanes 0-7 co 0-7 ci 0-7, 8-15 co 0-7 ci 8-15, 16-23 co 8-15
+  // ci 0-7, 24-31 co 8-15 ci 8-15.
+  const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_col = (lane >> 4) * 8;
+  const int b_row = (lane & 7) + (lane >> 4) * 8, b_col = ((lane >> 3) & 1) * 8;
+  float acc[4][4][4];
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < kCnnK; ++k) {
+#pragma unroll
+    for (int ks = 0; ks < kCnnC; ks += 16) {
+      uint32_t b[4][2];
+#pragma unroll
+      for (int nh = 0; nh < 2; ++nh) {
+        uint32_t r[4];
+        ldsm_x4(ws_a + 2u * (uint32_t)((k * kCnnC + 16 * nh + b_row) * kXR + ks + b_col), r);
+        b[2 * nh][0] = r[0], b[2 * nh][1] = r[1], b[2 * nh + 1][0] = r[2], b[2 * nh + 1][1] = r[3];
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int mt = warp + 8 * mi;
+        if (mt >= nmt) continue;
+        uint32_t a[4];
+        ldsm_x4(xs_a + 2u * (uint32_t)((mt * 16 + a_row + k) * kXR + ks + a_col), a);
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], a, b[ni][0], b[ni][1]);
+      }
+    }
+  }
+  // epilogue: bias, ReLU, max-pool rows (g, g^1) via a lane shuffle (lane ^ 4)
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi) {
+    const int mt = warp + 8 * mi;
+    if (mt >= nmt) continue;  // warp-uniform
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int co = ni * 8 + 2 * t;
+      const float b0 = bias[co], b1 = bias[co + 1];
+      float v[4] = {fmaxf(acc[mi][ni][0] + b0, 0.f), fmaxf(acc[mi][ni][1] + b1, 0.f),
+                    fmaxf(acc[mi][ni][2] + b0, 0.f), fmaxf(acc[mi][ni][3] + b1, 0.f)};
+      float o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = fmaxf(v[e], __shfl_xor_sync(0xffffffffu, v[e], 4));
+      if ((g & 1) == 0) {
+        const int prow = p0 + mt * 16 + g;  // even position; rows g and g + 8
+        if (kLast) {
+          float* d0 = static_cast<float*>(out) + ((int64_t)s * kCnnC + co) * (L / 2);
+          float* d1 = d0 + (L / 2);
+          d0[prow / 2] = o[0];
+          d1[prow / 2] = o[1];
+          d0[prow / 2 + 4] = o[2];
+          d1[prow / 2 + 4] = o[3];
+        } else {
+          uint16_t* dst = static_cast<uint16_t*>(out) + (int64_t)s * (L / 2) * kCnnC;
+          *reinterpret_cast<uint32_t*>(dst + (int64_t)(prow / 2) * kCnnC + co) = pack_bf16x2(o[0], o[1]);
+          *reinterpret_cast<uint32_t*>(dst + (int64_t)(prow / 2 + 4) * kCnnC + co) =
+              pack_bf16x2(o[2], o[3]);
+        }
+      }
+    }
+  }
+}
+
 // scores of one pair.  Thread = (group of 8 consecutive bins, quarter of the
 // channels); per channel it walks the positions 8 at a time with 16-byte
 // loads: 8 fx values and 8 new fy values feed 64 FMAs.  fy sits in shared
@@ -245,32 +431,36 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
 __host__ __device__ constexpr int score_pad(int Lf) { return Lf + 3; }
 __host__ __device__ constexpr int score_row(int Lf) { return ((score_pad(Lf) + 2 * Lf + 16) + 3) / 4 * 4; }
 
-__global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ feat, int Lf,
-                                                     const float* __restrict__ params,
-                                                     float* __restrict__ scores) {
+constexpr int kScoreT = 512;    // threads: (8-bin group, group of 4 channels)
+constexpr int kScoreCG = 8;     // channel groups
+
+__global__ void __launch_bounds__(kScoreT) k_scores(const float* __restrict__ feat, int Lf,
+                                                    const float* __restrict__ params,
+                                                    float* __restrict__ scores) {
   extern __shared__ __align__(16) float sm[];
   const int P = score_pad(Lf), R = score_row(Lf);
   float* fx = sm;                     // [32][Lf]
   float* fy = sm + kCnnC * Lf;        // [32][R]: fy[c][j] at P + j
-  float* part = fy + kCnnC * R;       // [4][nb rounded to 8]
+  float* part = fy + kCnnC * R;       // [8][nb rounded to 8]
   const int p = blockIdx.x;
   const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
   const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
-  for (int i = threadIdx.x; i < kCnnC * Lf; i += kThreads) fx[i] = gx[i];
-  for (int i = threadIdx.x; i < kCnnC * R; i += kThreads) {
+  for (int i = threadIdx.x; i < kCnnC * Lf; i += kScoreT) fx[i] = gx[i];
+  for (int i = threadIdx.x; i < kCnnC * R; i += kScoreT) {
     const int c = i / R, j = i % R - P;
     fy[i] = (j >= 0 && j < Lf) ? gy[c * Lf + j] : 0.f;
   }
   __syncthreads();
   const float alpha = params[kCnnAlpha];
   const int nb = 2 * Lf - 1, ngroups = (nb + 7) / 8, nbr = ngroups * 8;
-  for (int w = threadIdx.x; w < ngroups * 4; w += kThreads) {
+  constexpr int kPerCG = kCnnC / kScoreCG;
+  for (int w = threadIdx.x; w < ngroups * kScoreCG; w += kScoreT) {
     const int grp = w % ngroups, cq = w / ngroups;
     const int b0 = grp * 8, l0 = b0 - (Lf - 1);  // bins b0.. <-> lags l0..
     float acc[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0.f;
-    for (int c = cq * 8; c < cq * 8 + 8; ++c) {
+    for (int c = cq * kPerCG; c < cq * kPerCG + kPerCG; ++c) {
       const float* a = fx + c * Lf;
       const float* y = fy + c * R + P + l0;  // y[i + t] = fy[c][i + l0 + t]; 16-byte aligned
       float yw[16];
@@ -300,9 +490,12 @@ __global__ void __launch_bounds__(kThreads) k_scores(const float* __restrict__ f
     for (int t = 0; t < 8; ++t) part[cq * nbr + b0 + t] = acc[t];
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += kThreads)
-    scores[(int64_t)p * nb + b] =
-        alpha * ((part[b] + part[nbr + b]) + (part[2 * nbr + b] + part[3 * nbr + b]));
+  for (int b = threadIdx.x; b < nb; b += kScoreT) {
+    float t = 0.f;
+#pragma unroll
+    for (int cq = 0; cq < kScoreCG; ++cq) t += part[cq * nbr + b];
+    scores[(int64_t)p * nb + b] = alpha * t;
+  }
 }
 
 // lag rank of bin l: smaller |l| first, then negative first (the estimator's
@@ -313,9 +506,9 @@ __device__ __forceinline__ bool better(float s, int l, float bs, int bl) {
   return a != ab ? a < ab : l < bl;
 }
 
-// One warp per pair: softmax, top-8 bins, margin.
-__global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
-                       int32_t* __restrict__ centres, float* __restrict__ margin) {
+// Any length: the bins are re-read from global memory every round.
+__global__ void k_topk_any(const float* __restrict__ scores, int npairs, int Lf,
+                           int32_t* __restrict__ centres, float* __restrict__ margin) {
   const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (p >= npairs) return;
@@ -350,6 +543,65 @@ __global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
       }
     }
     taken[r] = bl;
+    top += __expf(bs - mx);
+    if (lane == 0) centres[(int64_t)p * kCnnTopK + r] = kCnnBin * bl;
+  }
+  if (lane == 0) margin[p] = top / sum;
+}
+
+// One warp per pair: softmax, top-8 bins, margin.  Each lane keeps its bins'
+// scores in registers (bins lane, lane + 32, ...); a taken bin is marked by a
+// flag bit, so every round is a register scan plus one warp reduction.
+constexpr int kTopPer = 32;  // bins per lane held in registers (nb <= 1024)
+
+__global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
+                       int32_t* __restrict__ centres, float* __restrict__ margin) {
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= npairs) return;
+  const int nb = 2 * Lf - 1;
+  const float* sc = scores + (int64_t)p * nb;
+  float v[kTopPer];
+  uint32_t taken = 0;
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < kTopPer; ++i) {
+    const int b = lane + 32 * i;
+    v[i] = b < nb ? sc[b] : -INFINITY;
+    mx = fmaxf(mx, v[i]);
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < kTopPer; ++i)
+    if (lane + 32 * i < nb) sum += __expf(v[i] - mx);
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  float top = 0.f;
+  for (int r = 0; r < kCnnTopK; ++r) {
+    float bs = -INFINITY;
+    int bl = 1 << 30, bi = -1;
+#pragma unroll
+    for (int i = 0; i < kTopPer; ++i) {
+      const int b = lane + 32 * i;
+      const int l = b - (Lf - 1);
+      if (b < nb && !(taken >> i & 1u) && (bl == (1 << 30) || better(v[i], l, bs, bl))) {
+        bs = v[i];
+        bl = l;
+        bi = i;
+      }
+    }
+    int owner = lane;
+    for (int o = 16; o; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      const int ow = __shfl_xor_sync(0xffffffffu, owner, o);
+      if (ol != (1 << 30) && (bl == (1 << 30) || better(os, ol, bs, bl))) {
+        bs = os;
+        bl = ol;
+        owner = ow;
+      }
+    }
+    if (lane == owner && bi >= 0) taken |= 1u << bi;
     top += __expf(bs - mx);
     if (lane == 0) centres[(int64_t)p * kCnnTopK + r] = kCnnBin * bl;
   }
@@ -649,19 +901,47 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
   return cudaGetLastError();
 }
 
+cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
+                             const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
+                             cudaStream_t st) {
+  const int Ld = (int)(n / kCnnDec);
+  if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
+  k_conv1_inf<<<dim3((Ld / 2 + kC1T - 1) / kC1T, nsig), kThreads, 0, st>>>(
+      q, n, wbf + cnn_woff(0), params + cnn_boff(0), act[0]);
+  TDE_COUNT_LAUNCH(1);
+  const int smem = ((kTP + 8) * kXR + kCnnK * kCnnC * kXR) * 2;
+  cudaFuncSetAttribute(k_conv_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_conv_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int l = 1; l < kCnnLayers; ++l) {
+    const int L = Ld >> l;  // input length of layer l
+    const dim3 grid((L + kTP - 1) / kTP, nsig);
+    if (l == kCnnLayers - 1)
+      k_conv_rows<true><<<grid, kThreads, smem, st>>>(act[l - 1], feat, L, wbf + cnn_woff(l),
+                                                      params + cnn_boff(l));
+    else
+      k_conv_rows<false><<<grid, kThreads, smem, st>>>(act[l - 1], act[l], L, wbf + cnn_woff(l),
+                                                       params + cnn_boff(l));
+    TDE_COUNT_LAUNCH(1);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st) {
   if (Lf % 8 != 0) return cudaErrorInvalidValue;  // Lf = n / 256 with n a multiple of 2048
-  const int smem = (kCnnC * Lf + kCnnC * score_row(Lf) + 4 * (2 * Lf + 7)) * 4;
+  const int smem = (kCnnC * Lf + kCnnC * score_row(Lf) + kScoreCG * (2 * Lf + 7)) * 4;
   cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_scores<<<npairs, kThreads, smem, st>>>(feat, Lf, params, scores);
+  k_scores<<<npairs, kScoreT, smem, st>>>(feat, Lf, params, scores);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cnn_topk(const float* scores, int npairs, int Lf, int32_t* centres,
                             float* margin, cudaStream_t st) {
-  k_topk<<<(npairs + 3) / 4, 128, 0, st>>>(scores, npairs, Lf, centres, margin);
+  if (2 * Lf - 1 > 32 * kTopPer)
+    k_topk_any<<<(npairs + 3) / 4, 128, 0, st>>>(scores, npairs, Lf, centres, margin);
+  else
+    k_topk<<<(npairs + 3) / 4, 128, 0, st>>>(scores, npairs, Lf, centres, margin);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -36,6 +36,12 @@ cudaError_t launch_cnn_decimate(const int8_t* q, int64_t n, int nsig, float* d, 
 // One layer for S signals with the BF16 weights of layer l.
 cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16_t* wbf,
                              const float* params, cudaStream_t st);
+// Inference forward (decimate + 4 layers) with BF16 activation rows between
+// layers: act[l] holds layer l's output, [nsig][(n/16) >> (l+1)][32] BF16;
+// feat receives the FP32 features [nsig][32][n/256].  n a multiple of 2048.
+cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
+                             const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
+                             cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st);
