@@ -305,6 +305,17 @@ tde_status tde_train_step(tde_ctx* ctx, tde_model* model, const int8_t* q, int n
 tde_status tde_propose(tde_ctx* ctx, const tde_model* model, const int8_t* q, int npairs,
                        int32_t* centres, float* margin, tde_stream_t stream);
 
+/* tde_estimate_learned planned once for fixed buffers, with its own device
+ * memory, and captured in a CUDA graph: tde_learned_run replays it on the
+ * current contents of x and y (refill them between runs).  The model must
+ * outlive the plan; its current parameters are read on every run. */
+typedef struct tde_learned tde_learned;
+tde_status tde_learned_create(tde_ctx* ctx, const tde_model* model, const float* x, const float* y,
+                              int npairs, int bits, float theta, int64_t* lag_out,
+                              int64_t* val_out, int32_t* fallback_out, tde_learned** out);
+tde_status tde_learned_run(tde_learned* plan, tde_stream_t stream);
+tde_status tde_learned_destroy(tde_learned* plan);
+
 /* Eq. (1) inside the proposal's windows, exactly: for pair p (x = q + 2 p n,
  * y = q + (2 p + 1) n; q: 2 npairs n int8 levels, device, as tde_propose
  * reads them) and window w with centre centres[8 p + w] (device int32),
@@ -317,10 +328,10 @@ tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npair
 
 /* Algorithm 1 with the proposal, for npairs pairs of n samples
  * (x, y: npairs * n floats each, device, pair after pair; all lags).  Pairs
- * whose margin is below theta (theta > 1: all pairs) are re-estimated with the
- * full correlation (tde_estimate_batch, AUTO engine) and flagged in
- * fallback_out (device int32 per pair, may be NULL).  bits 1 or 2.  The call
- * synchronizes `stream` once to read the margins. */
+ * whose margin is below theta (theta > 1: all pairs) get the full exact
+ * correlation instead, decided and run on the device (tensor-core engine),
+ * and are flagged in fallback_out (device int32 per pair, may be NULL).
+ * bits 1 or 2.  Asynchronous on `stream` (no host synchronization). */
 tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* model, const float* x,
                                 const float* y, int npairs, int bits, float theta,
                                 int64_t* lag_out, int64_t* val_out, int32_t* fallback_out,

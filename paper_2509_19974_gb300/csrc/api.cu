@@ -1287,15 +1287,6 @@ __global__ void k_make_windows(const int32_t* __restrict__ centres, int npairs, 
   jobs[i] = WinJob{lo, hi, cbuf + (int64_t)i * stride + off};
 }
 
-__global__ void k_fallback_scatter(const int32_t* __restrict__ idx, int nfb,
-                                   const int64_t* __restrict__ lag_fb,
-                                   const int64_t* __restrict__ val_fb, int64_t* __restrict__ lag,
-                                   int64_t* __restrict__ val) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nfb) return;
-  lag[idx[i]] = lag_fb[i];
-  val[idx[i]] = val_fb[i];
-}
 
 }  // namespace
 
@@ -1488,103 +1479,297 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "windows");
 }
 
-extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, const float* x,
-                                           const float* y, int npairs, int bits, float theta,
-                                           int64_t* lag_out, int64_t* val_out,
-                                           int32_t* fallback_out, tde_stream_t stream) {
-  if (!ctx) return TDE_ERR_INVALID;
+namespace {
+
+// Fallback on the device: the pairs whose margin is below theta (in any
+// order) -> fb_idx[0 .. *nfb).  One CTA.
+__global__ void k_fb_select(const float* __restrict__ marg, int P, float theta,
+                            int32_t* __restrict__ fb_idx, int* __restrict__ nfb,
+                            int32_t* __restrict__ fb_out) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const bool f = !(marg[p] >= theta);
+    if (fb_out) fb_out[p] = f ? 1 : 0;
+    if (f) fb_idx[atomicAdd(&cnt, 1)] = p;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *nfb = cnt;
+}
+
+// Descriptors of the fallback's full correlations: slot k < *nfb is pair
+// fb_idx[k] (all lags, output row k of cfb), its engine items are the
+// one-pair template with pair = k, and its argmax writes tlag/tval[k].
+__global__ void k_fb_build(const int32_t* __restrict__ fb_idx, const int* __restrict__ nfb, int P,
+                           const int8_t* __restrict__ qbuf, int64_t n,
+                           const MmaItem* __restrict__ tmpl, int nt, int zero_first,
+                           int32_t* __restrict__ cfb, MmaPair* __restrict__ pairs,
+                           MmaItem* __restrict__ items, ArgPair* __restrict__ args,
+                           int64_t* __restrict__ tlag, int64_t* __restrict__ tval,
+                           int* __restrict__ nitems) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cnt = *nfb;
+  const int64_t lags = 2 * n - 1;
+  if (i == 0) *nitems = cnt * nt;
+  if (i < (int64_t)cnt * nt) {
+    MmaItem it = tmpl[i % nt];
+    it.pair = (int32_t)(i / nt);
+    items[i] = it;
+  }
+  if (i < cnt) {
+    const int64_t p = fb_idx[i];
+    int32_t* c = cfb + i * lags;
+    pairs[i] = MmaPair{qbuf + 2 * p * n, qbuf + (2 * p + 1) * n, n, n, -(n - 1), n - 1, c, 0,
+                       zero_first};
+    args[i] = ArgPair{c, -(n - 1), lags, tlag + i, tval + i};
+  } else if (i < P) {
+    pairs[i] = MmaPair{qbuf, qbuf, n, n, -(n - 1), n - 1, cfb, 0, 0};  // idle slot
+  }
+}
+
+__global__ void k_fb_scatter(const int32_t* __restrict__ fb_idx, const int* __restrict__ nfb,
+                             const int64_t* __restrict__ tlag, const int64_t* __restrict__ tval,
+                             int64_t* __restrict__ lag, int64_t* __restrict__ val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *nfb) return;
+  lag[fb_idx[i]] = tlag[i];
+  val[fb_idx[i]] = tval[i];
+}
+
+// Everything one learned estimate needs: quantize, proposal, windows, window
+// argmax, and the device-side fallback (full correlations of the pairs whose
+// margin is below theta), planned from the sizes alone.
+struct LearnedWork {
+  int P = 0, bits = 2;
+  int64_t n = 0;
+  float theta = 0.f;
+  Layout L;
+  QuantStage Q;
+  CnnPlan C;
+  MmaStage T;  // one full-range pair: the fallback's item template
+  size_t o_q = 0, o_cent = 0, o_marg = 0, o_jobs = 0, o_cwin = 0;
+  size_t o_fbidx = 0, o_nfb = 0, o_fbpairs = 0, o_fbitems = 0, o_nitems = 0, o_counter = 0;
+  size_t o_fbargs = 0, o_keys = 0, o_tlag = 0, o_tval = 0, o_cfb = 0;
+};
+
+void learned_plan(LearnedWork* w, int npairs, int64_t n, int bits, float theta) {
+  w->P = npairs, w->n = n, w->bits = bits, w->theta = theta;
+  Layout& L = w->L;
+  const int S = 2 * npairs;
+  w->Q.plan(L, S, bits, nullptr, n);
+  w->o_q = L.w<int8_t>((size_t)S * n);
+  w->C.plan(L, npairs, n, false);
+  w->o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
+  w->o_marg = L.w<float>((size_t)npairs);
+  w->o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
+  w->o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * kCnnWin);
+  std::vector<Job> one{Job{nullptr, nullptr, n, n, -(n - 1), n - 1, nullptr, 0}};
+  w->T.plan(L, one);
+  const int nt = w->T.nitems;
+  w->o_fbidx = L.w<int32_t>((size_t)npairs);
+  w->o_nfb = L.w<int>(1);
+  w->o_fbpairs = L.w<MmaPair>((size_t)npairs);
+  w->o_fbitems = L.w<MmaItem>((size_t)npairs * nt);
+  w->o_nitems = L.w<int>(1);
+  w->o_counter = L.w<int>(1);
+  w->o_fbargs = L.w<ArgPair>((size_t)npairs);
+  w->o_keys = L.w<unsigned long long>(2 * (size_t)npairs);
+  w->o_tlag = L.w<int64_t>((size_t)npairs);
+  w->o_tval = L.w<int64_t>((size_t)npairs);
+  w->o_cfb = L.w<int32_t>((size_t)npairs * (size_t)(2 * n - 1));
+}
+
+void learned_fill(LearnedWork* w, const Bases& B, const float* x, const float* y) {
+  const int S = 2 * w->P;
+  const int64_t n = w->n;
+  std::vector<const float*> xs(S);
+  std::vector<int8_t*> qs(S);
+  std::vector<int64_t> ns(S, n);
+  int8_t* qbuf = B.dw<int8_t>(w->o_q);
+  for (int p = 0; p < w->P; ++p)
+    for (int k = 0; k < 2; ++k) {
+      const int i = 2 * p + k;
+      xs[i] = (k ? y : x) + (int64_t)p * n;
+      qs[i] = qbuf + (int64_t)i * n;
+    }
+  w->Q.fill(B, xs.data(), qs.data(), ns.data());
+  std::vector<Job> one{Job{qbuf, qbuf + n, n, n, -(n - 1), n - 1, B.dw<int32_t>(w->o_cfb), 0}};
+  w->T.fill(B, one);  // only its items (the template) are used
+}
+
+cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& w, const Bases& B,
+                           int64_t* lag_out, int64_t* val_out, int32_t* fb_out, cudaStream_t st) {
+  const int P = w.P;
+  const int64_t n = w.n;
+  int8_t* qbuf = B.dw<int8_t>(w.o_q);
+  int32_t* cent = B.dw<int32_t>(w.o_cent);
+  float* marg = B.dw<float>(w.o_marg);
+  WinJob* jobs = B.dw<WinJob>(w.o_jobs);
+  cudaError_t e = w.Q.launch(B, ctx->d_status, st);
+  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, st);
+  if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
+  if (e == cudaSuccess) {
+    k_make_windows<<<(P * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, P, n, B.dw<int32_t>(w.o_cwin),
+                                                               kCnnWin, jobs);
+    TDE_COUNT_LAUNCH(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(B.dw<int32_t>(w.o_cwin), 0, sizeof(int32_t) * (size_t)P * kCnnTopK * kCnnWin,
+                        st);
+  if (e == cudaSuccess) {
+    EngineTimer t(ctx, st);
+    e = launch_xcorr_mma_windows(qbuf, n, P, jobs, ctx->d_status, st);
+  }
+  if (e == cudaSuccess) e = launch_window_argmax(jobs, P, lag_out, val_out, st);
+  // fallback, decided and run on the device
+  int32_t* fb_idx = B.dw<int32_t>(w.o_fbidx);
+  int* nfb = B.dw<int>(w.o_nfb);
+  if (e == cudaSuccess) {
+    k_fb_select<<<1, 1024, 0, st>>>(marg, P, w.theta, fb_idx, nfb, fb_out);
+    TDE_COUNT_LAUNCH(1);
+    e = cudaGetLastError();
+  }
+  const int nt = w.T.nitems;
+  if (e == cudaSuccess) {
+    const int64_t total = (int64_t)P * (nt > 1 ? nt : 1);
+    k_fb_build<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+        fb_idx, nfb, P, qbuf, n, B.dd<MmaItem>(w.T.o_items), nt, w.T.zero_first[0],
+        B.dw<int32_t>(w.o_cfb), B.dw<MmaPair>(w.o_fbpairs), B.dw<MmaItem>(w.o_fbitems),
+        B.dw<ArgPair>(w.o_fbargs), B.dw<int64_t>(w.o_tlag), B.dw<int64_t>(w.o_tval),
+        B.dw<int>(w.o_nitems));
+    TDE_COUNT_LAUNCH(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && w.T.any_zero) e = launch_mma_zero(B.dw<MmaPair>(w.o_fbpairs), P, 2 * n - 1, st);
+  if (e == cudaSuccess)
+    e = launch_xcorr_mma(B.dw<MmaPair>(w.o_fbpairs), B.dw<MmaItem>(w.o_fbitems), P * nt,
+                         B.dw<int>(w.o_counter), 2 * ctx->sm_count, ctx->d_status, st,
+                         B.dw<int>(w.o_nitems));
+  if (e == cudaSuccess)
+    e = launch_argmax(B.dw<ArgPair>(w.o_fbargs), P, 2 * n - 1, 0,
+                      B.dw<unsigned long long>(w.o_keys), st, nfb);
+  if (e == cudaSuccess) {
+    k_fb_scatter<<<(P + 255) / 256, 256, 0, st>>>(fb_idx, nfb, B.dw<int64_t>(w.o_tlag),
+                                                  B.dw<int64_t>(w.o_tval), lag_out, val_out);
+    TDE_COUNT_LAUNCH(1);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+tde_status check_learned_args(tde_ctx* ctx, const tde_model* m, const float* x, const float* y,
+                              int npairs, int bits, const int64_t* lag_out, const int64_t* val_out) {
   tde_status s = check_model(ctx, m);
   if (s != TDE_OK) return s;
   if (!x || !y || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "npairs must be positive");
   if (bits != 1 && bits != 2)
     return set_err(ctx, TDE_ERR_UNSUPPORTED, "the learned path supports bits 1 and 2");
-  const int64_t n = m->n;
+  return TDE_OK;
+}
+
+}  // namespace
+
+extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, const float* x,
+                                           const float* y, int npairs, int bits, float theta,
+                                           int64_t* lag_out, int64_t* val_out,
+                                           int32_t* fallback_out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  tde_status s = check_learned_args(ctx, m, x, y, npairs, bits, lag_out, val_out);
+  if (s != TDE_OK) return s;
   DeviceGuard g(ctx->device);
   LaunchCount lc(ctx);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int S = 2 * npairs;
-  Layout L;
-  QuantStage Q;
-  Q.plan(L, S, bits, nullptr, n);
-  const size_t o_q = L.w<int8_t>((size_t)S * n);
-  CnnPlan C;
-  C.plan(L, npairs, n, false);
-  const size_t o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
-  const size_t o_marg = L.w<float>((size_t)npairs);
-  const size_t o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
-  const size_t o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * kCnnWin);
+  LearnedWork w;
+  learned_plan(&w, npairs, m->n, bits, theta);
   Bases B;
-  if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
-  std::vector<const float*> xs(S);
-  std::vector<int8_t*> qs(S);
-  std::vector<int64_t> ns(S, n);
-  int8_t* qbuf = B.dw<int8_t>(o_q);
-  for (int p = 0; p < npairs; ++p)
-    for (int k = 0; k < 2; ++k) {
-      const int i = 2 * p + k;
-      xs[i] = (k ? y : x) + (int64_t)p * n;
-      qs[i] = qbuf + (int64_t)i * n;
-    }
-  Q.fill(B, xs.data(), qs.data(), ns.data());
-  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
-  int32_t* cent = B.dw<int32_t>(o_cent);
-  float* marg = B.dw<float>(o_marg);
-  WinJob* jobs = B.dw<WinJob>(o_jobs);
-  cudaError_t e = Q.launch(B, ctx->d_status, st);
-  if (e == cudaSuccess) e = C.forward(B, m, qbuf, n, false, st);
-  if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(C.o_scores), npairs, C.Lf, cent, marg, st);
+  if ((s = realize(ctx, w.L, &B)) != TDE_OK) return s;
+  learned_fill(&w, B, x, y);
+  if ((s = stage_upload(ctx, B.ddesc, w.L.desc, st)) != TDE_OK) return s;
+  const cudaError_t e = learned_launch(ctx, m, w, B, lag_out, val_out, fallback_out, st);
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "learned estimate");
+}
+
+// A learned estimate planned once, with its own device memory, captured in a
+// CUDA graph; every run replays it on the current contents of x and y.
+struct tde_learned {
+  tde_ctx* ctx = nullptr;
+  LearnedWork w;
+  char* mem = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+
+extern "C" tde_status tde_learned_create(tde_ctx* ctx, const tde_model* m, const float* x,
+                                         const float* y, int npairs, int bits, float theta,
+                                         int64_t* lag_out, int64_t* val_out,
+                                         int32_t* fallback_out, tde_learned** out) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  *out = nullptr;
+  tde_status s = check_learned_args(ctx, m, x, y, npairs, bits, lag_out, val_out);
+  if (s != TDE_OK) return s;
+  DeviceGuard g(ctx->device);
+  tde_learned* b = new tde_learned();
+  b->ctx = ctx;
+  learned_plan(&b->w, npairs, m->n, bits, theta);
+  auto fail = [&](cudaError_t e, const char* what) {
+    tde_learned_destroy(b);
+    return cuda_err(ctx, e, what);
+  };
+  cudaError_t e = cudaMalloc(&b->mem, b->w.L.total());
+  if (e != cudaSuccess) return fail(e, "cudaMalloc(learned plan memory)");
+  std::vector<char> host(b->w.L.desc ? b->w.L.desc : 16);
+  Bases B{host.data(), b->mem, b->mem + b->w.L.data_base()};
+  learned_fill(&b->w, B, x, y);
+  e = cudaMemcpy(b->mem, host.data(), b->w.L.desc, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(e, "descriptor upload");
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(e, "cudaStreamCreate");
+  const bool prof = ctx->profile;
+  ctx->profile = false;
+  const int64_t before = tde_launch_counter;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, npairs, n,
-                                                                     B.dw<int32_t>(o_cwin), kCnnWin,
-                                                                     jobs);
-    TDE_COUNT_LAUNCH(1);
-    e = cudaGetLastError();
+    const cudaError_t le = learned_launch(ctx, m, b->w, B, lag_out, val_out, fallback_out, cs);
+    e = cudaStreamEndCapture(cs, &b->graph);
+    if (le != cudaSuccess) e = le;
   }
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(B.dw<int32_t>(o_cwin), 0, sizeof(int32_t) * (size_t)npairs * kCnnTopK * kCnnWin,
-                        st);
-  if (e == cudaSuccess) {
-    EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(qbuf, n, npairs, jobs, ctx->d_status, st);
+  b->launches = tde_launch_counter - before;
+  tde_launch_counter = before;
+  ctx->profile = prof;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return fail(e, "graph capture");
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
+  *out = b;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_learned_run(tde_learned* b, tde_stream_t stream) {
+  if (!b || !b->exec) return TDE_ERR_INVALID;
+  tde_ctx* ctx = b->ctx;
+  DeviceGuard g(ctx->device);
+  const cudaError_t e = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGraphLaunch");
+  ctx->launches += b->launches;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_learned_destroy(tde_learned* b) {
+  if (!b) return TDE_OK;
+  {
+    DeviceGuard g(b->ctx->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->mem) cudaFree(b->mem);
   }
-  if (e == cudaSuccess) e = launch_window_argmax(jobs, npairs, lag_out, val_out, st);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "learned estimate");
-  // Fallback: pairs whose proposal is not confident get the full correlation.
-  std::vector<float> hm(npairs);
-  TDE_CK(cudaMemcpyAsync(hm.data(), marg, sizeof(float) * npairs, cudaMemcpyDeviceToHost, st));
-  TDE_CK(cudaStreamSynchronize(st));
-  std::vector<int32_t> fb, flag(npairs, 0);
-  for (int p = 0; p < npairs; ++p)
-    if (!(hm[p] >= theta)) {
-      fb.push_back(p);
-      flag[p] = 1;
-    }
-  if (fallback_out)
-    TDE_CK(cudaMemcpyAsync(fallback_out, flag.data(), sizeof(int32_t) * npairs,
-                           cudaMemcpyHostToDevice, st));
-  if (!fb.empty()) {
-    const int nfb = (int)fb.size();
-    std::vector<tde_pair_desc> d(nfb);
-    for (int i = 0; i < nfb; ++i)
-      d[i] = tde_pair_desc{x + (int64_t)fb[i] * n, y + (int64_t)fb[i] * n, n, n, -(n - 1), n - 1};
-    // The fallback runs in its own memory (the context workspace is reused).
-    int64_t* tmp = nullptr;
-    int32_t* idx = nullptr;
-    TDE_CK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(int64_t) * 2 * nfb, st));
-    TDE_CK(cudaMallocAsync(reinterpret_cast<void**>(&idx), sizeof(int32_t) * nfb, st));
-    TDE_CK(cudaMemcpyAsync(idx, fb.data(), sizeof(int32_t) * nfb, cudaMemcpyHostToDevice, st));
-    TDE_CK(cudaStreamSynchronize(st));  // fb, flag and d leave scope only after the copies
-    s = tde_estimate_batch(ctx, d.data(), nfb, bits, TDE_ENGINE_AUTO, nullptr, tmp, tmp + nfb,
-                           stream);
-    if (s != TDE_OK) return s;
-    k_fallback_scatter<<<(nfb + 255) / 256, 256, 0, st>>>(idx, nfb, tmp, tmp + nfb, lag_out,
-                                                          val_out);
-    TDE_COUNT_LAUNCH(1);
-    TDE_CK(cudaFreeAsync(tmp, st));
-    TDE_CK(cudaFreeAsync(idx, st));
-  }
-  TDE_CK(cudaStreamSynchronize(st));  // host vectors above must outlive their copies
+  delete b;
   return TDE_OK;
 }
 

@@ -54,7 +54,9 @@ struct MinU64 {
 };
 
 __global__ void __launch_bounds__(kThreads) k_argmax32(const ArgPair* __restrict__ pairs,
-                                                       unsigned long long* __restrict__ keys) {
+                                                       unsigned long long* __restrict__ keys,
+                                                       const int* __restrict__ d_count) {
+  if (d_count && (int)blockIdx.y >= *d_count) return;
   const ArgPair P = pairs[blockIdx.y];
   const int32_t* c = static_cast<const int32_t*>(P.c);
   unsigned long long best = 0;
@@ -68,7 +70,9 @@ __global__ void __launch_bounds__(kThreads) k_argmax32(const ArgPair* __restrict
 }
 
 __global__ void __launch_bounds__(kThreads) k_argmax64_value(const ArgPair* __restrict__ pairs,
-                                                             unsigned long long* __restrict__ keys) {
+                                                             unsigned long long* __restrict__ keys,
+                                                             const int* __restrict__ d_count) {
+  if (d_count && (int)blockIdx.y >= *d_count) return;
   const ArgPair P = pairs[blockIdx.y];
   const long long* c = static_cast<const long long*>(P.c);
   long long best = LLONG_MIN;
@@ -80,7 +84,9 @@ __global__ void __launch_bounds__(kThreads) k_argmax64_value(const ArgPair* __re
 }
 
 __global__ void __launch_bounds__(kThreads) k_argmax64_lag(const ArgPair* __restrict__ pairs,
-                                                           unsigned long long* __restrict__ keys) {
+                                                           unsigned long long* __restrict__ keys,
+                                                           const int* __restrict__ d_count) {
+  if (d_count && (int)blockIdx.y >= *d_count) return;
   const ArgPair P = pairs[blockIdx.y];
   const long long* c = static_cast<const long long*>(P.c);
   const long long vmax = static_cast<long long>(keys[2 * blockIdx.y]);
@@ -95,8 +101,10 @@ __global__ void __launch_bounds__(kThreads) k_argmax64_lag(const ArgPair* __rest
   if (threadIdx.x == 0 && best != ~0ull) atomicMin(&keys[2 * blockIdx.y + 1], best);
 }
 
-__global__ void k_argmax_init(unsigned long long* keys, int npairs, int c64) {
+__global__ void k_argmax_init(unsigned long long* keys, int npairs, int c64,
+                              const int* __restrict__ d_count) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d_count && p >= *d_count) return;
   if (p < npairs) {
     keys[2 * p] = c64 ? (unsigned long long)LLONG_MIN : 0ull;
     keys[2 * p + 1] = ~0ull;
@@ -110,8 +118,9 @@ __device__ __forceinline__ int64_t rank_to_lag(uint64_t rank) {
 
 __global__ void k_argmax_finalize(const ArgPair* __restrict__ pairs,
                                   const unsigned long long* __restrict__ keys, int npairs,
-                                  int c64) {
+                                  int c64, const int* __restrict__ d_count) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d_count && p >= *d_count) return;
   if (p >= npairs) return;
   const ArgPair P = pairs[p];
   if (c64) {
@@ -127,25 +136,25 @@ __global__ void k_argmax_finalize(const ArgPair* __restrict__ pairs,
 }  // namespace
 
 cudaError_t launch_argmax(const ArgPair* d_pairs, int npairs, int64_t max_count, int c64,
-                          unsigned long long* d_keys, cudaStream_t st) {
+                          unsigned long long* d_keys, cudaStream_t st, const int* d_count) {
   if (npairs <= 0) return cudaSuccess;
   const int blocks_p = (npairs + 127) / 128;
-  k_argmax_init<<<blocks_p, 128, 0, st>>>(d_keys, npairs, c64);
+  k_argmax_init<<<blocks_p, 128, 0, st>>>(d_keys, npairs, c64, d_count);
   TDE_COUNT_LAUNCH(1);
   int64_t gx = ceil_div64(max_count, (int64_t)kThreads * 16);
   if (gx < 1) gx = 1;
   if (gx > 1024) gx = 1024;
   dim3 grid((unsigned)gx, npairs);
   if (c64) {
-    k_argmax64_value<<<grid, kThreads, 0, st>>>(d_pairs, d_keys);
+    k_argmax64_value<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, d_count);
     TDE_COUNT_LAUNCH(1);
-    k_argmax64_lag<<<grid, kThreads, 0, st>>>(d_pairs, d_keys);
+    k_argmax64_lag<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, d_count);
     TDE_COUNT_LAUNCH(1);
   } else {
-    k_argmax32<<<grid, kThreads, 0, st>>>(d_pairs, d_keys);
+    k_argmax32<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, d_count);
     TDE_COUNT_LAUNCH(1);
   }
-  k_argmax_finalize<<<blocks_p, 128, 0, st>>>(d_pairs, d_keys, npairs, c64);
+  k_argmax_finalize<<<blocks_p, 128, 0, st>>>(d_pairs, d_keys, npairs, c64, d_count);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

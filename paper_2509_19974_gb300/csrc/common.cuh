@@ -109,9 +109,11 @@ constexpr int kPopcLagsPerCta = 2048;
 cudaError_t launch_xcorr_popc(const XcPair* d_pairs, const PopcItem* d_items, int nitems, int bits,
                               cudaStream_t st);
 
-// d_keys: npairs * 2 uint64 of scratch.
+// d_keys: npairs * 2 uint64 of scratch.  d_count (device, nullable): only
+// pairs [0, *d_count) are reduced.
 cudaError_t launch_argmax(const ArgPair* d_pairs, int npairs, int64_t max_count, int c64,
-                          unsigned long long* d_keys, cudaStream_t st);
+                          unsigned long long* d_keys, cudaStream_t st,
+                          const int* d_count = nullptr);
 
 // Kernel launches enqueued by this host thread (read by the context).
 extern thread_local int64_t tde_launch_counter;

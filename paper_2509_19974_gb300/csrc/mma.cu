@@ -271,8 +271,10 @@ __device__ __forceinline__ uint4 e4m3x16(uint4 v) {
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
-    k_xcorr_mma8(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems,
-                 int* __restrict__ counter, uint32_t* __restrict__ status) {
+    k_xcorr_mma8(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems_arg,
+                 const int* __restrict__ d_nitems, int* __restrict__ counter,
+                 uint32_t* __restrict__ status) {
+  const int nitems = d_nitems ? *d_nitems : nitems_arg;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -767,7 +769,8 @@ cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_coun
 }
 
 cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
-                             int* d_counter, int grid, uint32_t* d_status, cudaStream_t st) {
+                             int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
+                             const int* d_nitems) {
   if (nitems <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma8, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes8);
@@ -775,7 +778,8 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
   e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (grid > nitems) grid = nitems;
-  k_xcorr_mma8<<<grid, kThreads, kSmemBytes8, st>>>(d_pairs, d_items, nitems, d_counter, d_status);
+  k_xcorr_mma8<<<grid, kThreads, kSmemBytes8, st>>>(d_pairs, d_items, nitems, d_nitems, d_counter,
+                                                     d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -34,9 +34,12 @@ int mma_smem_bytes();
 // Zeroes the outputs of pairs with zero_first set.
 cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st);
 // Persistent launch: `grid` CTAs (two per SM fit) take items from *d_counter
-// (zeroed here) in array order; sort items longest first.
+// (zeroed here) in array order; sort items longest first.  d_nitems (device,
+// nullable) overrides the item count when the items are made on the device
+// (nitems is then an upper bound).
 cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
-                             int* d_counter, int grid, uint32_t* d_status, cudaStream_t st);
+                             int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
+                             const int* d_nitems = nullptr);
 
 // The learned proposal's windows on the tensor cores: pair p is
 // x = d_q + 2 p n, y = d_q + (2 p + 1) n (n int8 each, bits <= 2 or 4); its 8

@@ -32,7 +32,8 @@ EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error"
            "tde_batch_destroy", "tde_model_param_count", "tde_model_create", "tde_model_destroy",
            "tde_model_get", "tde_model_set", "tde_train_step", "tde_propose",
            "tde_estimate_learned", "tde_synth_pairs", "tde_autotune", "tde_autotune_table",
-           "tde_autotune_load", "tde_ctx_pick_engine", "tde_xcorr_windows")
+           "tde_autotune_load", "tde_ctx_pick_engine", "tde_xcorr_windows",
+           "tde_learned_create", "tde_learned_run", "tde_learned_destroy")
 
 
 class TdeError(RuntimeError):
@@ -99,6 +100,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_autotune_load": ([p, p, i32], st),
         "tde_ctx_pick_engine": ([p, i32, i64, i64, i64], i32),
         "tde_xcorr_windows": ([p, p, i64, i32, i32, p, p, p], st),
+        "tde_learned_create": ([p, p, p, p, i32, i32, f32, p, p, p, ctypes.POINTER(p)], st),
+        "tde_learned_run": ([p, p], st),
+        "tde_learned_destroy": ([p], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -526,6 +530,43 @@ def tde_xcorr_windows(ctx: Context, q2: torch.Tensor, bits: int, centres: torch.
     ctx.check(ctx.lib.tde_xcorr_windows(ctx.handle, q2.data_ptr(), n, npairs, int(bits),
                                         centres.data_ptr(), c_out.data_ptr(), _stream(stream)))
     return c_out
+
+
+class LearnedBatch:
+    """tde_learned_create: the learned estimate of fixed x, y buffers ([P, n]
+    float32, refilled between runs) captured in a CUDA graph; run() replays
+    it.  Results land in .lags, .vals and .fallback."""
+
+    def __init__(self, model, x: torch.Tensor, y: torch.Tensor, bits: int = 2, theta: float = 0.5):
+        _need(x, torch.float32, "x")
+        _need(y, torch.float32, "y")
+        self.model, self.ctx = model, model.ctx
+        self.x, self.y = x, y
+        npairs = x.shape[0]
+        self.lags = torch.empty(npairs, dtype=torch.int64, device=x.device)
+        self.vals = torch.empty(npairs, dtype=torch.int64, device=x.device)
+        self.fallback = torch.empty(npairs, dtype=torch.int32, device=x.device)
+        h = ctypes.c_void_p()
+        self.ctx.check(self.ctx.lib.tde_learned_create(
+            self.ctx.handle, model.handle, x.data_ptr(), y.data_ptr(), npairs, int(bits),
+            float(theta), self.lags.data_ptr(), self.vals.data_ptr(), self.fallback.data_ptr(),
+            ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        self.ctx.check(self.ctx.lib.tde_learned_run(self.handle, _stream(stream)))
+        return self.lags, self.vals, self.fallback
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.tde_learned_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def interleave_q(qx: torch.Tensor, qy: torch.Tensor) -> torch.Tensor:

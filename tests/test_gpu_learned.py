@@ -182,3 +182,37 @@ def test_xcorr_windows_match_oracle_at_edges(ctx, bits, n):
             if inr.any():
                 ref[inr] = oracle.xcorr_at(q[2 * p], q[2 * p + 1], lags[inr])
             assert np.array_equal(c[p, w], ref), (p, w)
+
+
+def test_learned_batch_graph_mixed_fallback(ctx):
+    """The graph-captured learned estimate: with theta between the pairs'
+    margins some pairs fall back (decided on the device); every lag is the
+    window reference or the full estimate accordingly, and a replay on refilled
+    inputs gives the same as a direct call."""
+    m = tde.Model(ctx, N, seed=6)
+    x, y, d, q2 = _quantized_pairs(ctx, 8, 31)
+    cent, marg = m.propose(q2)
+    theta = float(torch.median(marg).item())
+    xb, yb = x.clone(), y.clone()
+    lb = tde.LearnedBatch(m, xb, yb, bits=2, theta=theta)
+    lags, vals, fb = lb.run()
+    torch.cuda.synchronize()
+    fbn = fb.cpu().numpy()
+    margn = marg.cpu().numpy()
+    assert np.array_equal(fbn, (margn < theta).astype(np.int32))
+    assert 0 < fbn.sum() < 8
+    xs, ys = x.cpu().numpy(), y.cpu().numpy()
+    cent = cent.cpu().numpy()
+    for p in range(8):
+        qx, qy = oracle.quantize(xs[p], 2), oracle.quantize(ys[p], 2)
+        want = oracle.estimate(xs[p], ys[p], 2) if fbn[p] else _window_reference(qx, qy, cent[p])
+        assert (int(lags[p]), int(vals[p])) == want, p
+    # refill with other pairs and replay; compare with the direct (uncaptured) call
+    x2, y2, _, _ = _quantized_pairs(ctx, 8, 32)
+    xb.copy_(x2), yb.copy_(y2)
+    lags2, vals2, fb2 = [t.clone() for t in lb.run()]
+    l3, v3, f3 = m.estimate(x2, y2, bits=2, theta=theta)
+    torch.cuda.synchronize()
+    assert torch.equal(lags2, l3) and torch.equal(vals2, v3) and torch.equal(fb2, f3)
+    lb.close()
+    m.close()
