@@ -526,9 +526,10 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
 // 8 windows x 8 columns.  Producers and the issuer synchronize once per
 // super-chunk of 2 chunks (8 MMAs): super-chunk s writes logical slots
 // [32 s + 14, 32 s + 46) and reads [32 s, 32 s + 46), so on a ring of 128 its
-// slots were last read by super-chunk s - 3.  A CTA takes items (pair, K
-// segment) round-robin; partial sums are added into the zeroed window outputs
-// with integer atomics.
+// slots were last read by super-chunk s - 3.  A CTA takes items (pair, part
+// of its K segments) round-robin and walks the segments (staging each, then
+// its MMAs); the part's sum accumulates in tensor memory and is stored (one
+// part) or added with integer atomics (several parts) at the end.
 
 constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
 constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
@@ -544,11 +545,11 @@ constexpr int kWinSmemUsed = kWinW * kWinArr + kWinSlotBytes + kWinXBytes + (2 *
 constexpr int kWinSmemBytes = kWinSmemUsed + 1024;
 static_assert(kWinArr % 1024 == 0, "windows' arrays keep the 1024-byte swizzle pattern");
 static_assert(kWinXBytes % 16 == 0, "staging");
-static_assert(kWinSmemBytes + 1024 <= 114 * 1024, "two CTAs per SM");
+static_assert(3 * (kWinSmemBytes + 1024) <= 228 * 1024, "three CTAs per SM");
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     k_xcorr_mma_win(const int8_t* __restrict__ q, int64_t n, int npairs, const WinJob* __restrict__ jobs,
-                    int nseg, int seg, uint32_t* __restrict__ status) {
+                    int nseg, int seg, int parts, uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -583,27 +584,21 @@ __global__ void __launch_bounds__(kThreads, 2)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int64_t sc0 = 0;  // super-chunks issued by this CTA so far (barrier phases)
-  uint32_t iter = 0;
+  int64_t sc0 = 0;     // super-chunks issued by this CTA so far (barrier phases)
+  uint32_t dphase = 0;  // completions of done_bar so far (one per segment)
   bool ok = true;
-  const int nitems = npairs * nseg;
   const int64_t kmax = (n + 127 + 127) / 128 * 128;
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++iter) {
-    const int p = item / nseg, sgi = item - p * nseg;
-    const int64_t ks = (int64_t)sgi * seg;
-    const int64_t ke = ks + seg < kmax ? ks + seg : kmax;
-    const int nchunks = (int)((ke - ks) / kKc8);
+  // Items (pair, part of its K segments), round-robin: the part's sum
+  // accumulates in tensor memory; one part per pair stores each window lag,
+  // several parts add theirs to the zeroed outputs.
+  const int seg_per_part = (nseg + parts - 1) / parts;
+  for (int item = blockIdx.x; item < npairs * parts && ok; item += gridDim.x) {
+    const int p = item / parts, part = item - p * parts;
+    const int sg_lo = part * seg_per_part;
+    const int sg_hi = sg_lo + seg_per_part < nseg ? sg_lo + seg_per_part : nseg;
     const int8_t* qx = q + (int64_t)(2 * p) * n;
     const int8_t* qy = q + (int64_t)(2 * p + 1) * n;
     const WinJob* J = jobs + (int64_t)p * kWinW;
-    if (nchunks <= 0 || ke - ks > kWinKs || (ks & 127) != 0) {  // not for the host's segmentation
-      if (threadIdx.x == 0 && nchunks > 0) atomicOr(status, TDE_ST_INTERNAL);
-      --iter;
-      continue;
-    }
-    const int64_t xs_base = fdiv(ks - 127, 16) * 16;
-    const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
-    const int nrows = nchunks + kWinJ - 1;  // rows of each window array this item reads
     if (threadIdx.x < kWinW) {
       const WinJob jw = J[threadIdx.x];
       sT[threadIdx.x] = fdiv(jw.lag_lo, 128) * 128;
@@ -611,115 +606,132 @@ __global__ void __launch_bounds__(kThreads, 2)
       sHi[threadIdx.x] = jw.lag_hi;
       sC[threadIdx.x] = jw.c;
     }
-    __syncthreads();
-    // staging: x segment, then every window's rows (int8 -> E4M3, swizzled)
-    {
-      const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
-      const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
-      constexpr int kXV = kWinXBytes / 16;
-      const int per_w = nrows * 8;  // (row, 16-byte piece) per window
-      const int total = kXV + kWinW * per_w;
-      for (int b0 = threadIdx.x; b0 < total; b0 += 8 * kThreads) {
-        uint4 v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int idx = b0 + k * kThreads;
-          if (idx < kXV) {
-            v[k] = load16(qx, xs_base + 16 * idx, n, alx);
-          } else if (idx < total) {
-            const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
-            v[k] = load16(qy, ks + sT[w] + 128 * (r8 >> 3) + 16 * (r8 & 7), n, aly);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int idx = b0 + k * kThreads;
-          if (idx >= total) continue;
-          const uint4 e = e4m3x16(v[k]);
-          uint32_t a;
-          if (idx < kXV) {
-            a = xs + 16u * (uint32_t)idx;
-          } else {
-            const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
-            const uint32_t row_addr = ya + (uint32_t)(w * kWinArr + 128 * (r8 >> 3));
-            a = row_addr + 16u * ((uint32_t)(r8 & 7) ^ ((row_addr >> 7) & 7u));
-          }
-          st_shared_v4(a, e.x, e.y, e.z, e.w);
-        }
-      }
-    }
     if (warp < 4) {
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
       tmem_zero32(tmem + lane_base);
       tmem_zero32(tmem + lane_base + 32u);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-    fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-
-    const int nsc = (nchunks + kWinSC - 1) / kWinSC;
-    if (warp == 1 || warp == 2) {
-      // Hankel slots of x (as in k_xcorr_mma8), one super-chunk at a time
-      const int t = threadIdx.x - 32;
-      for (int sc = 0; sc < nsc; ++sc) {
-        const int64_t g = sc0 + sc;
-        const int64_t prev = g - 3;
-        if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
-          ok = false;
-          break;
-        }
-        const int c_first = sc * kWinSC;
-        const int c_last = c_first + kWinSC - 1 < nchunks - 1 ? c_first + kWinSC - 1 : nchunks - 1;
-        const int o_first = sc == 0 ? 0 : 128 * c_first + 112;
-        const int o_end = 128 * c_last + 240;
-        for (int o = o_first + t; o < o_end; o += kProducers) {
-          const uint32_t pa = xs + xoff + (uint32_t)o;
-          const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-          const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
-          const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
-          const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
-          const int e = o >> 3, r = o & 7;
-          const int ps = e % kWinRing;
-          const uint32_t a = slots + 128u * ps + 16u * r;
-          st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-          if (ps < kWinMirror)
-            st_shared_v4(a + 128u * kWinRing, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
-                         (uint32_t)(hi >> 32));
-        }
-        fence_proxy_async();
-        mbar_arrive(full_bar + 8 * (uint32_t)(g % kNB));
+    for (int sgi = sg_lo; sgi < sg_hi; ++sgi) {
+      const int64_t ks = (int64_t)sgi * seg;
+      const int64_t ke = ks + seg < kmax ? ks + seg : kmax;
+      const int nchunks = (int)((ke - ks) / kKc8);
+      if (nchunks <= 0) break;                                 // uniform
+      if (ke - ks > kWinKs || (ks & 127) != 0) {               // not for the host's segmentation
+        if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
+        break;
       }
-    } else if (warp == 0) {
-      const uint32_t idesc = idesc8_for(kWinN);
-      for (int sc = 0; sc < nsc; ++sc) {
-        const int64_t g = sc0 + sc;
-        ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(g % kNB), (uint32_t)((g / kNB) & 1)));
-        if (!ok) break;
-        tc_fence_after();
-        if (lane == 0) {
-          const int c_end = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC : nchunks;
-          for (int c = sc * kWinSC; c < c_end; ++c) {
-            const uint32_t a_start = slots + 128u * (uint32_t)((16 * c) % kWinRing);
-            const uint32_t b_start = ya + 128u * (uint32_t)c;
+      const int64_t xs_base = fdiv(ks - 127, 16) * 16;
+      const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
+      const int nrows = nchunks + kWinJ - 1;  // rows of each window array this segment reads
+      // staging: x segment, then every window's rows (int8 -> E4M3, swizzled)
+      {
+        const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+        const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+        constexpr int kXV = kWinXBytes / 16;
+        const int per_w = nrows * 8;  // (row, 16-byte piece) per window
+        const int total = kXV + kWinW * per_w;
+        for (int b0 = threadIdx.x; b0 < total; b0 += 8 * kThreads) {
+          uint4 v[8];
 #pragma unroll
-            for (int s2 = 0; s2 < 4; ++s2)
-              mma_e4m3(tmem, sdesc(a_start + 512u * s2, 256, 128, 0, 0),
-                       sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, 1u);
+          for (int k = 0; k < 8; ++k) {
+            const int idx = b0 + k * kThreads;
+            if (idx < kXV) {
+              v[k] = load16(qx, xs_base + 16 * idx, n, alx);
+            } else if (idx < total) {
+              const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
+              v[k] = load16(qy, ks + sT[w] + 128 * (r8 >> 3) + 16 * (r8 & 7), n, aly);
+            }
           }
-          mma_commit(cmt_bar + 8 * (uint32_t)(g % kNB));
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int idx = b0 + k * kThreads;
+            if (idx >= total) continue;
+            const uint4 e = e4m3x16(v[k]);
+            uint32_t a;
+            if (idx < kXV) {
+              a = xs + 16u * (uint32_t)idx;
+            } else {
+              const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
+              const uint32_t row_addr = ya + (uint32_t)(w * kWinArr + 128 * (r8 >> 3));
+              a = row_addr + 16u * ((uint32_t)(r8 & 7) ^ ((row_addr >> 7) & 7u));
+            }
+            st_shared_v4(a, e.x, e.y, e.z, e.w);
+          }
         }
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+
+      const int nsc = (nchunks + kWinSC - 1) / kWinSC;
+      if (warp == 1 || warp == 2) {
+        // Hankel slots of x (as in k_xcorr_mma8), one super-chunk at a time
+        const int t = threadIdx.x - 32;
+        for (int sc = 0; sc < nsc; ++sc) {
+          const int64_t g = sc0 + sc;
+          const int64_t prev = g - 3;
+          if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
+            ok = false;
+            break;
+          }
+          const int c_first = sc * kWinSC;
+          const int c_last = c_first + kWinSC - 1 < nchunks - 1 ? c_first + kWinSC - 1 : nchunks - 1;
+          const int o_first = sc == 0 ? 0 : 128 * c_first + 112;
+          const int o_end = 128 * c_last + 240;
+          for (int o = o_first + t; o < o_end; o += kProducers) {
+            const uint32_t pa = xs + xoff + (uint32_t)o;
+            const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
+            const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
+            const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
+            const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
+            const int e = o >> 3, r = o & 7;
+            const int ps = e % kWinRing;
+            const uint32_t a = slots + 128u * ps + 16u * r;
+            st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+            if (ps < kWinMirror)
+              st_shared_v4(a + 128u * kWinRing, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
+                           (uint32_t)(hi >> 32));
+          }
+          fence_proxy_async();
+          mbar_arrive(full_bar + 8 * (uint32_t)(g % kNB));
+        }
+      } else if (warp == 0) {
+        const uint32_t idesc = idesc8_for(kWinN);
+        for (int sc = 0; sc < nsc; ++sc) {
+          const int64_t g = sc0 + sc;
+          ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(g % kNB), (uint32_t)((g / kNB) & 1)));
+          if (!ok) break;
+          tc_fence_after();
+          if (lane == 0) {
+            const int c_end = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC : nchunks;
+            for (int c = sc * kWinSC; c < c_end; ++c) {
+              const uint32_t a_start = slots + 128u * (uint32_t)((16 * c) % kWinRing);
+              const uint32_t b_start = ya + 128u * (uint32_t)c;
+#pragma unroll
+              for (int s2 = 0; s2 < 4; ++s2)
+                mma_e4m3(tmem, sdesc(a_start + 512u * s2, 256, 128, 0, 0),
+                         sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, 1u);
+            }
+            mma_commit(cmt_bar + 8 * (uint32_t)(g % kNB));
+          }
+          __syncwarp();
+        }
+        if (lane == 0) mma_commit(done_bar);  // this segment's MMAs
         __syncwarp();
       }
-      if (lane == 0) mma_commit(done_bar);
-      __syncwarp();
+      // the segment's MMAs must finish before its staging is overwritten
+      bool done = true;
+      if (warp == 3) done = mbar_wait_sleep(done_bar, dphase & 1u);
+      ++dphase;
+      ok = __syncthreads_and(ok && done);
+      sc0 += nsc;
+      if (!ok) break;
     }
-
-    // one warp waits for the accumulator; the others block in the barrier
-    bool done = true;
-    if (warp == 3) done = mbar_wait_sleep(done_bar, iter & 1u);
-    ok = __syncthreads_and(ok && done);
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
       break;
@@ -738,12 +750,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int64_t tau = sT[w] + 128 * j + 127 - m;
         if (tau < lo || tau > hi) continue;
         const int val = __float2int_rn(__uint_as_float(v[jj]));
-        if (val != 0) atomicAdd(sC[w] + (tau - lo), val);
+        if (parts == 1)
+          sC[w][tau - lo] = val;
+        else if (val != 0)
+          atomicAdd(sC[w] + (tau - lo), val);
       }
     }
     tc_fence_before();
     __syncthreads();
-    sc0 += nsc;
   }
   tc_fence_before();
   __syncthreads();
@@ -798,9 +812,13 @@ cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, c
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t nitems = (int64_t)npairs * nseg;
-  const int grid = (int)(nitems < 2 * sms ? nitems : 2 * sms);
-  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(d_q, n, npairs, d_jobs, nseg, seg, d_status);
+  // enough items for three CTAs per SM: each pair's segments in `parts` parts
+  int parts = (int)ceil_div64(3 * (int64_t)sms, npairs);
+  parts = parts < 1 ? 1 : (parts > nseg ? nseg : (parts > 4 ? 4 : parts));
+  const int64_t nitems = (int64_t)npairs * parts;
+  const int grid = (int)(nitems < 3 * sms ? nitems : 3 * sms);
+  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(d_q, n, npairs, d_jobs, nseg, seg, parts,
+                                                         d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -43,8 +43,8 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
 
 // The learned proposal's windows on the tensor cores: pair p is
 // x = d_q + 2 p n, y = d_q + (2 p + 1) n (n int8 each, bits <= 2 or 4); its 8
-// windows d_jobs[8 p + w] (lag_lo, lag_hi <= lag_lo + 383, c) receive
-// c[i] += sum_n x[n] y[n + lag_lo + i] for lag_lo + i <= lag_hi.  The c
-// buffers must be zeroed first (partial sums are added with atomics).
+// windows d_jobs[8 p + w] (lag_lo, lag_hi <= lag_lo + 256, c) receive
+// c[i] += sum_n x[n] y[n + lag_lo + i] for lag_lo + i <= lag_hi (other entries
+// are not written): the c buffers must be zeroed first.
 cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, const WinJob* d_jobs,
                                      uint32_t* d_status, cudaStream_t st);
