@@ -323,7 +323,7 @@ struct QuantStage {
   int nsig = 0, bits = 1;
   int64_t max_n = 0;
   bool with_planes = false;
-  size_t o_sigs = 0, o_hist = 0, o_state = 0, o_candp = 0, o_planes = 0;
+  size_t o_sigs = 0, o_hist = 0, o_chist = 0, o_state = 0, o_candp = 0, o_planes = 0;
   std::vector<size_t> o_cand;  // per signal: room for all its keys
   // ns: the signals' lengths (host), or nullptr when all are max_n.  With
   // want_planes the rank quantizer also writes bit planes (set_planes);
@@ -336,6 +336,7 @@ struct QuantStage {
     if (with_planes) o_planes = L.d<QPlanes>(nsig);
     o_candp = L.d<uint32_t*>(nsig);
     o_hist = L.w<uint32_t>((size_t)nsig * 4096);
+    o_chist = L.w<uint32_t>((size_t)nsig * 7 * 1024);
     o_state = L.w<QState>(nsig);
     o_cand.resize(nsig);
     for (int i = 0; i < nsig; ++i) o_cand[i] = L.w<uint32_t>((size_t)(ns ? ns[i] : mx));
@@ -354,7 +355,8 @@ struct QuantStage {
   cudaError_t launch(const Bases& B, uint32_t* status, cudaStream_t st) const {
     if (nsig == 0) return cudaSuccess;
     if (bits == 1) return launch_quantize_sign(B.dd<QSig>(o_sigs), nsig, max_n, status, st);
-    const QWork w{B.dw<uint32_t>(o_hist), B.dw<QState>(o_state), B.dd<uint32_t*>(o_candp)};
+    const QWork w{B.dw<uint32_t>(o_hist), B.dw<QState>(o_state), B.dd<uint32_t*>(o_candp),
+                  B.dw<uint32_t>(o_chist)};
     return launch_quantize_stream(B.dd<QSig>(o_sigs), with_planes ? B.dd<QPlanes>(o_planes) : nullptr,
                                   nsig, max_n, bits, w, status, st);
   }

@@ -79,18 +79,21 @@ cudaError_t launch_quantize_sign(const QSig* d_sigs, int nsig, int64_t max_n, ui
                                  cudaStream_t st);
 // Rank quantizer for bits in {2,4}.  d_state: nsig RankState; d_hist:
 // nsig * 7 * 2048 uint32 of scratch.
-// Work memory of the streaming rank quantizer: a 4096-bin histogram and a
-// QState per signal, and per signal a candidate list with room for n keys.
+// Work memory of the streaming rank quantizer: a 4096-bin histogram, a
+// 7 x 1024-bin candidate histogram and a QState per signal, and per signal a
+// candidate list with room for n keys.
 struct QState {
   uint32_t pre[7];   // threshold digits found so far
   uint32_t rank[7];  // rank within them
   uint32_t thr[7];   // final thresholds (FP32 bit patterns of |x|)
+  int32_t owner[7];  // first threshold with the same prefix (shares its histogram)
   uint32_t ncand;    // keys in the candidate list
 };
 struct QWork {
   uint32_t* hist;               // [nsig][4096]
   QState* state;                // [nsig]
   uint32_t* const* cand;        // [nsig] device pointers to lists of n keys
+  uint32_t* chist;              // [nsig][7][1024] candidate histograms
 };
 // The rank quantizer (bits 2, 4) as five streaming launches; d_planes
 // (nullable) receives each signal's bit planes as well.

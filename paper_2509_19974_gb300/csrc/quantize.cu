@@ -17,7 +17,8 @@
 //   k_qsel1   per signal: the bin of each threshold's rank;
 //   k_qcand   the keys in those bins (a few percent) appended to the
 //             signal's candidate list (one read of x);
-//   k_qsel2   per signal: two radix passes (10 + 9 bits) over the candidates
+//   k_qchist, k_qcsel   two radix passes (10 + 9 bits) over the candidates,
+//             each a grid of histogram CTAs per signal and a one-CTA select,
 //             give the exact order statistics;
 //   k_qapply  q = sign(x) * #{m : |x| >= t_m}, and on request the bit planes
 //             of the popc kernels (one read of x, one write of q).
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_rank_apply(const QSig* __restrict_
 // ------------------------------------------------------------ streaming form
 
 constexpr int kQB = 4096;            // first digit: bits 30..19 of |x|
+constexpr int kQC = 7 * 1024;        // candidate-histogram words per signal
 constexpr int kQT = 256;             // threads per streaming CTA
 constexpr int kQPer = 8192;          // samples per streaming CTA and step
 
@@ -319,6 +321,8 @@ __global__ void __launch_bounds__(kQT) k_qsel1(const QSig* __restrict__ sigs, QW
     if ((threadIdx.x & 31) == 0) st->pre[warp] = bin, st->rank[warp] = rest;
   }
   if (threadIdx.x == 0) st->ncand = 0;
+  uint32_t* ch = w.chist + (size_t)sig * kQC;
+  for (int i = threadIdx.x; i < M * 1024; i += kQT) ch[i] = 0;
 }
 
 // Keys whose first digit is a threshold's -> the signal's candidate list.
@@ -397,62 +401,74 @@ __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QW
   for (uint32_t i = threadIdx.x; i < nb; i += kQT) cand[gbase + i] = buf[i];
 }
 
-// Per signal: the exact thresholds from the candidates -- digits 18..9 then
-// 8..0, one histogram per distinct first digit, one warp per threshold.
-__global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QWork w, int M) {
-  __shared__ __align__(16) uint32_t sh[7 * 1024];
-  __shared__ uint32_t pre_s[7], rank_s[7];
-  __shared__ int owner_s[7];
+// The exact thresholds from the candidates: digits 18..9 then 8..0.  Each
+// pass is a grid of CTAs per signal that histograms a share of the candidates
+// (one histogram per distinct prefix, in shared memory, non-zero bins added to
+// the signal's global histogram) and a one-CTA select per signal (one warp per
+// threshold) that also zeroes the global histogram for the next use.
+template <int PASS>
+__global__ void __launch_bounds__(kQT) k_qchist(QWork w, int M) {
+  __shared__ uint32_t sh[kQC];
+  const int sig = blockIdx.y;
+  const QState* st = w.state + sig;
+  const uint32_t nc = st->ncand;
+  const uint32_t* cand = w.cand[sig];
+  constexpr int hs = PASS == 0 ? 19 : 9, shift = PASS == 0 ? 9 : 0;
+  constexpr uint32_t mask = PASS == 0 ? 1023u : 511u;
+  uint32_t pre[7];
+  int own[7];
+#pragma unroll
+  for (int m = 0; m < 7; ++m) pre[m] = m < M ? st->pre[m] : 0xFFFFFFFFu, own[m] = st->owner[m];
+  if ((uint32_t)blockIdx.x * kQT >= nc) return;  // no candidates for this CTA (uniform)
+  for (int i = threadIdx.x; i < M * 1024; i += kQT) sh[i] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * kQT + threadIdx.x; i < nc; i += gridDim.x * kQT) {
+    const uint32_t u = cand[i];
+    const uint32_t hi = u >> hs;
+    int mm = -1;
+#pragma unroll
+    for (int m = 6; m >= 0; --m)
+      if (m < M && hi == pre[m]) mm = own[m];
+    if (mm >= 0) atomicAdd(&sh[mm * 1024 + ((u >> shift) & mask)], 1u);
+  }
+  __syncthreads();
+  uint32_t* gh = w.chist + (size_t)sig * kQC;
+  for (int i = threadIdx.x; i < M * 1024; i += kQT)
+    if (sh[i]) atomicAdd(&gh[i], sh[i]);
+}
+
+// PASS 0 / 1: select the next digit (10 / 9 bits).  PASS -1 (after k_qsel1):
+// only prepare the owners for pass 0.
+template <int PASS>
+__global__ void __launch_bounds__(kQT) k_qcsel(QWork w, int M) {
+  __shared__ uint32_t pre_s[7];
   const int sig = blockIdx.x;
   QState* st = w.state + sig;
-  const uint32_t* cand = w.cand[sig];
-  const uint32_t nc = st->ncand;
+  uint32_t* gh = w.chist + (size_t)sig * kQC;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x < 7) pre_s[threadIdx.x] = threadIdx.x < M ? st->pre[threadIdx.x] : 0xFFFFFFFFu;
+  __syncthreads();
+  if (PASS >= 0 && warp < M) {
+    const int o = st->owner[warp];
+    uint32_t bin, rest;
+    warp_find(gh + o * 1024, PASS == 0 ? 1024 : 512, st->rank[warp], bin, rest);
+    if ((threadIdx.x & 31) == 0) {
+      pre_s[warp] = (pre_s[warp] << (PASS == 0 ? 10 : 9)) | bin;
+      st->rank[warp] = rest;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x < 7) {
     const int m = threadIdx.x;
-    pre_s[m] = m < M ? st->pre[m] : 0xFFFFFFFFu;
-    rank_s[m] = m < M ? st->rank[m] : 0u;
+    st->pre[m] = pre_s[m];
+    int o = m;
+    for (int k = m - 1; k >= 0; --k)
+      if (pre_s[k] == pre_s[m]) o = k;
+    st->owner[m] = o;  // thresholds with equal prefixes share the first one's histogram
+    if (PASS == 1) st->thr[m] = m < M ? pre_s[m] : 0xFFFFFFFFu;
   }
-  const int warp = threadIdx.x >> 5;
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int nbins = pass == 0 ? 1024 : 512, shift = pass == 0 ? 9 : 0, hs = pass == 0 ? 19 : 9;
-    const uint32_t mask = pass == 0 ? 1023u : 511u;
-    __syncthreads();  // pre_s as the previous pass (or the load above) left it
-    // thresholds with equal prefixes so far share the first one's histogram
-    if (threadIdx.x < 7) {
-      const int m = threadIdx.x;
-      int o = m;
-      for (int k = m - 1; k >= 0; --k)
-        if (pre_s[k] == pre_s[m]) o = k;
-      owner_s[m] = o;
-    }
-    for (int i = threadIdx.x; i < M * 1024; i += kQT) sh[i] = 0;
-    __syncthreads();
-    uint32_t pre[7];
-    int own[7];
-#pragma unroll
-    for (int m = 0; m < 7; ++m) pre[m] = pre_s[m], own[m] = owner_s[m];
-    for (uint32_t i = threadIdx.x; i < nc; i += kQT) {
-      const uint32_t u = cand[i];
-      const uint32_t hi = u >> hs;
-      int mm = -1;
-#pragma unroll
-      for (int m = 6; m >= 0; --m)
-        if (m < M && hi == pre[m]) mm = own[m];
-      if (mm >= 0) atomicAdd(&sh[mm * 1024 + ((u >> shift) & mask)], 1u);
-    }
-    __syncthreads();
-    if (warp < M) {
-      uint32_t bin, rest;
-      warp_find(sh + owner_s[warp] * 1024, nbins, rank_s[warp], bin, rest);
-      if ((threadIdx.x & 31) == 0) {
-        pre_s[warp] = (pre_s[warp] << (pass == 0 ? 10 : 9)) | bin;
-        rank_s[warp] = rest;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < 7) st->thr[threadIdx.x] = threadIdx.x < M ? pre_s[threadIdx.x] : 0xFFFFFFFFu;
+  if (PASS >= 0)
+    for (int i = threadIdx.x; i < M * 1024; i += kQT) gh[i] = 0;
 }
 
 // q = sign(x) * #{m : |x| >= t_m}; bit planes by warp ballots when asked.
@@ -605,11 +621,19 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
     k_qcand<1><<<grid, kQT, 0, st>>>(d_sigs, w);
   else
     k_qcand<7><<<grid, kQT, 0, st>>>(d_sigs, w);
-  k_qsel2<<<nsig, kQT, 0, st>>>(d_sigs, w, M);
+  int64_t gc = ceil_div64(max_n, 32768);  // candidate-histogram CTAs per signal
+  if (gc < 1) gc = 1;
+  if (gc > 256) gc = 256;
+  const dim3 cgrid((unsigned)gc, (unsigned)nsig);
+  k_qcsel<-1><<<nsig, kQT, 0, st>>>(w, M);
+  k_qchist<0><<<cgrid, kQT, 0, st>>>(w, M);
+  k_qcsel<0><<<nsig, kQT, 0, st>>>(w, M);
+  k_qchist<1><<<cgrid, kQT, 0, st>>>(w, M);
+  k_qcsel<1><<<nsig, kQT, 0, st>>>(w, M);
   if (M == 1)
     k_qapply<1><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
   else
     k_qapply<7><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
-  TDE_COUNT_LAUNCH(5);
+  TDE_COUNT_LAUNCH(9);
   return cudaGetLastError();
 }
