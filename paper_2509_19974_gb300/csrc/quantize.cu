@@ -17,9 +17,10 @@
 //   k_qsel1   per signal: the bin of each threshold's rank;
 //   k_qcand   the keys in those bins (a few percent) appended to the
 //             signal's candidate list (one read of x);
-//   k_qchist, k_qcsel   two radix passes (10 + 9 bits) over the candidates,
-//             each a grid of histogram CTAs per signal and a one-CTA select,
-//             give the exact order statistics;
+//   k_qsel2 (signals up to 2^18 samples) or k_qchist/k_qcsel (longer: each
+//             pass a grid of histogram CTAs per signal and a one-CTA select):
+//             two radix passes (10 + 9 bits) over the candidates give the
+//             exact order statistics;
 //   k_qapply  q = sign(x) * #{m : |x| >= t_m}, and on request the bit planes
 //             of the popc kernels (one read of x, one write of q).
 // The candidate list has room for the whole signal, so no input (ties,
@@ -401,6 +402,65 @@ __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QW
   for (uint32_t i = threadIdx.x; i < nb; i += kQT) cand[gbase + i] = buf[i];
 }
 
+// Short signals (few candidates): both candidate passes in one CTA per
+// signal -- digits 18..9 then 8..0, one histogram per distinct prefix, one
+// warp per threshold.
+__global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QWork w, int M) {
+  __shared__ __align__(16) uint32_t sh[7 * 1024];
+  __shared__ uint32_t pre_s[7], rank_s[7];
+  __shared__ int owner_s[7];
+  const int sig = blockIdx.x;
+  QState* st = w.state + sig;
+  const uint32_t* cand = w.cand[sig];
+  const uint32_t nc = st->ncand;
+  if (threadIdx.x < 7) {
+    const int m = threadIdx.x;
+    pre_s[m] = m < M ? st->pre[m] : 0xFFFFFFFFu;
+    rank_s[m] = m < M ? st->rank[m] : 0u;
+  }
+  const int warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int nbins = pass == 0 ? 1024 : 512, shift = pass == 0 ? 9 : 0, hs = pass == 0 ? 19 : 9;
+    const uint32_t mask = pass == 0 ? 1023u : 511u;
+    __syncthreads();  // pre_s as the previous pass (or the load above) left it
+    // thresholds with equal prefixes so far share the first one's histogram
+    if (threadIdx.x < 7) {
+      const int m = threadIdx.x;
+      int o = m;
+      for (int k = m - 1; k >= 0; --k)
+        if (pre_s[k] == pre_s[m]) o = k;
+      owner_s[m] = o;
+    }
+    for (int i = threadIdx.x; i < M * 1024; i += kQT) sh[i] = 0;
+    __syncthreads();
+    uint32_t pre[7];
+    int own[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) pre[m] = pre_s[m], own[m] = owner_s[m];
+    for (uint32_t i = threadIdx.x; i < nc; i += kQT) {
+      const uint32_t u = cand[i];
+      const uint32_t hi = u >> hs;
+      int mm = -1;
+#pragma unroll
+      for (int m = 6; m >= 0; --m)
+        if (m < M && hi == pre[m]) mm = own[m];
+      if (mm >= 0) atomicAdd(&sh[mm * 1024 + ((u >> shift) & mask)], 1u);
+    }
+    __syncthreads();
+    if (warp < M) {
+      uint32_t bin, rest;
+      warp_find(sh + owner_s[warp] * 1024, nbins, rank_s[warp], bin, rest);
+      if ((threadIdx.x & 31) == 0) {
+        pre_s[warp] = (pre_s[warp] << (pass == 0 ? 10 : 9)) | bin;
+        rank_s[warp] = rest;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 7) st->thr[threadIdx.x] = threadIdx.x < M ? pre_s[threadIdx.x] : 0xFFFFFFFFu;
+}
+
 // The exact thresholds from the candidates: digits 18..9 then 8..0.  Each
 // pass is a grid of CTAs per signal that histograms a share of the candidates
 // (one histogram per distinct prefix, in shared memory, non-zero bins added to
@@ -621,19 +681,24 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
     k_qcand<1><<<grid, kQT, 0, st>>>(d_sigs, w);
   else
     k_qcand<7><<<grid, kQT, 0, st>>>(d_sigs, w);
-  int64_t gc = ceil_div64(max_n, 32768);  // candidate-histogram CTAs per signal
-  if (gc < 1) gc = 1;
-  if (gc > 256) gc = 256;
-  const dim3 cgrid((unsigned)gc, (unsigned)nsig);
-  k_qcsel<-1><<<nsig, kQT, 0, st>>>(w, M);
-  k_qchist<0><<<cgrid, kQT, 0, st>>>(w, M);
-  k_qcsel<0><<<nsig, kQT, 0, st>>>(w, M);
-  k_qchist<1><<<cgrid, kQT, 0, st>>>(w, M);
-  k_qcsel<1><<<nsig, kQT, 0, st>>>(w, M);
+  if (max_n <= (1 << 18)) {
+    k_qsel2<<<nsig, kQT, 0, st>>>(d_sigs, w, M);
+    TDE_COUNT_LAUNCH(1);
+  } else {
+    int64_t gc = ceil_div64(max_n, 32768);  // candidate-histogram CTAs per signal
+    if (gc > 256) gc = 256;
+    const dim3 cgrid((unsigned)gc, (unsigned)nsig);
+    k_qcsel<-1><<<nsig, kQT, 0, st>>>(w, M);
+    k_qchist<0><<<cgrid, kQT, 0, st>>>(w, M);
+    k_qcsel<0><<<nsig, kQT, 0, st>>>(w, M);
+    k_qchist<1><<<cgrid, kQT, 0, st>>>(w, M);
+    k_qcsel<1><<<nsig, kQT, 0, st>>>(w, M);
+    TDE_COUNT_LAUNCH(5);
+  }
   if (M == 1)
     k_qapply<1><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
   else
     k_qapply<7><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
-  TDE_COUNT_LAUNCH(9);
+  TDE_COUNT_LAUNCH(4);
   return cudaGetLastError();
 }
