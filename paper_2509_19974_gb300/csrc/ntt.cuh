@@ -9,7 +9,7 @@
 // below 2^31 so values kept in [0, 2p) fit 32 bits; p0 p1 / 2 > 2^61.
 constexpr uint32_t kNttP0 = 2013265921u;
 constexpr uint32_t kNttP1 = 2113929217u;
-constexpr int kNttMinLog = 10, kNttMaxLog = 18;
+constexpr int kNttMinLog = 10, kNttMaxLog = 19;  // column pass: N2 <= 512 in shared memory
 
 // Per-prime tables for transform length N = 2^logn (device pointers):
 // tw[i] = w^i and its Shoup companion floor(tw * 2^32 / p); itw[i] =

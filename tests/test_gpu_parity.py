@@ -117,6 +117,22 @@ def test_xcorr_matches_oracle(ctx, engine, bits, case):
 
 
 @pytest.mark.parametrize("engine", ENGINES)
+def test_xcorr_long_pair_restricted_lags(ctx, engine):
+    """The longest pairs of the uneven batch: 262144 samples, lags +-32768
+    (the NTT needs a 2^19 transform here)."""
+    n, w = 262144, 32768
+    rng = np.random.default_rng(5)
+    qx, qy = _levels(rng, n, 2), _levels(rng, n, 2)
+    c = ctx.xcorr_int(_gpu(qx), _gpu(qy), 2, -w, w, engine=engine)
+    ctx.sync()
+    got = c.cpu().numpy().astype(np.int64)
+    lags = np.concatenate([np.arange(-w, -w + 300), rng.integers(-w, w + 1, 2000),
+                           np.arange(w - 300, w + 1)])
+    assert np.array_equal(got[lags + w], oracle.xcorr_at(qx, qy, lags))
+    assert got.sum() == int(oracle.xcorr(qx, qy, -w, w).sum())
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 def test_xcorr_extreme_values(ctx, engine):
     """All +7 against all +7 (the largest |c|), and alternating signs."""
     n = 30011
