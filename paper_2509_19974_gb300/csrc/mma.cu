@@ -526,10 +526,13 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
 // 8 windows x 8 columns.  Producers and the issuer synchronize once per
 // super-chunk of 2 chunks (8 MMAs): super-chunk s writes logical slots
 // [32 s + 14, 32 s + 46) and reads [32 s, 32 s + 46), so on a ring of 128 its
-// slots were last read by super-chunk s - 3.  A CTA takes items (pair, part
-// of its K segments) round-robin and walks the segments (staging each, then
-// its MMAs); the part's sum accumulates in tensor memory and is stored (one
-// part) or added with integer atomics (several parts) at the end.
+// slots were last read by super-chunk s - 3.  The (pair, K segment) units of
+// the batch, pair-major, are dealt to the CTAs as contiguous runs of equal
+// length (so no CTA runs more than one unit beyond the average); a CTA walks
+// its run (staging each segment, then its MMAs), accumulating per pair in
+// tensor memory, and at each pair's end stores the sums (the run held all of
+// the pair's segments) or adds them with integer atomics (the pair is split
+// between CTAs).
 
 constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
 constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
@@ -549,7 +552,7 @@ static_assert(3 * (kWinSmemBytes + 1024) <= 228 * 1024, "three CTAs per SM");
 
 __global__ void __launch_bounds__(kThreads, 3)
     k_xcorr_mma_win(const int8_t* __restrict__ q, int64_t n, int npairs, const WinJob* __restrict__ jobs,
-                    int nseg, int seg, int parts, uint32_t* __restrict__ status) {
+                    int nseg, int seg, uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -588,14 +591,16 @@ __global__ void __launch_bounds__(kThreads, 3)
   uint32_t dphase = 0;  // completions of done_bar so far (one per segment)
   bool ok = true;
   const int64_t kmax = (n + 127 + 127) / 128 * 128;
-  // Items (pair, part of its K segments), round-robin: the part's sum
-  // accumulates in tensor memory; one part per pair stores each window lag,
-  // several parts add theirs to the zeroed outputs.
-  const int seg_per_part = (nseg + parts - 1) / parts;
-  for (int item = blockIdx.x; item < npairs * parts && ok; item += gridDim.x) {
-    const int p = item / parts, part = item - p * parts;
-    const int sg_lo = part * seg_per_part;
-    const int sg_hi = sg_lo + seg_per_part < nseg ? sg_lo + seg_per_part : nseg;
+  // This CTA's run of (pair, segment) units [u, u1), pair-major; one pass
+  // of the loop per pair the run touches.
+  const int64_t units = (int64_t)npairs * nseg;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t u = units * blockIdx.x / gridDim.x; u < u1 && ok;) {
+    const int p = (int)(u / nseg);
+    const int sg_lo = (int)(u - (int64_t)p * nseg);
+    const int sg_hi = u1 - u < nseg - sg_lo ? sg_lo + (int)(u1 - u) : nseg;
+    const bool whole = sg_lo == 0 && sg_hi == nseg;  // no other CTA adds to this pair
+    u += sg_hi - sg_lo;
     const int8_t* qx = q + (int64_t)(2 * p) * n;
     const int8_t* qy = q + (int64_t)(2 * p + 1) * n;
     const WinJob* J = jobs + (int64_t)p * kWinW;
@@ -750,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         const int64_t tau = sT[w] + 128 * j + 127 - m;
         if (tau < lo || tau > hi) continue;
         const int val = __float2int_rn(__uint_as_float(v[jj]));
-        if (parts == 1)
+        if (whole)
           sC[w][tau - lo] = val;
         else if (val != 0)
           atomicAdd(sC[w] + (tau - lo), val);
@@ -812,13 +817,10 @@ cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, c
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // enough items for three CTAs per SM: each pair's segments in `parts` parts
-  int parts = (int)ceil_div64(3 * (int64_t)sms, npairs);
-  parts = parts < 1 ? 1 : (parts > nseg ? nseg : (parts > 4 ? 4 : parts));
-  const int64_t nitems = (int64_t)npairs * parts;
-  const int grid = (int)(nitems < 3 * sms ? nitems : 3 * sms);
-  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(d_q, n, npairs, d_jobs, nseg, seg, parts,
-                                                         d_status);
+  // three CTAs per SM, each with an equal run of the (pair, segment) units
+  const int64_t units = (int64_t)npairs * nseg;
+  const int grid = (int)(units < 3 * (int64_t)sms ? units : 3 * (int64_t)sms);
+  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(d_q, n, npairs, d_jobs, nseg, seg, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
