@@ -1242,12 +1242,12 @@ struct CnnPlan {
     return l == 0 ? B.dw<float>(o_d) : B.dw<float>(o_out[l - 1]);
   }
   cudaError_t forward(const Bases& B, const tde_model* m, const int8_t* q, int64_t n, bool train,
-                      cudaStream_t st) const {
+                      uint32_t* status, cudaStream_t st) const {
     if (!train) {
       uint16_t* act[kCnnLayers - 1];
       for (int l = 0; l + 1 < kCnnLayers; ++l) act[l] = B.dw<uint16_t>(o_act[l]);
       cudaError_t e = launch_cnn_infer(q, n, 2 * P, m->wbf, m->params, act,
-                                       B.dw<float>(o_out[kCnnLayers - 1]), st);
+                                       B.dw<float>(o_out[kCnnLayers - 1]), status, st);
       if (e == cudaSuccess)
         e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
                               B.dw<float>(o_scores), st);
@@ -1395,7 +1395,7 @@ extern "C" tde_status tde_train_step(tde_ctx* ctx, tde_model* m, const int8_t* q
   Bases B;
   if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
   const int S = 2 * npairs, Ld = C.Ld, Lf = C.Lf;
-  cudaError_t e = C.forward(B, m, q, m->n, true, st);
+  cudaError_t e = C.forward(B, m, q, m->n, true, ctx->d_status, st);
   if (e == cudaSuccess)
     e = launch_cnn_softmax_ce(B.dw<float>(C.o_scores), labels, npairs, Lf, loss_out,
                               B.dw<float>(C.o_dscores), st);
@@ -1445,7 +1445,7 @@ extern "C" tde_status tde_propose(tde_ctx* ctx, const tde_model* m, const int8_t
   C.plan(L, npairs, m->n, false);
   Bases B;
   if ((s = realize(ctx, L, &B)) != TDE_OK) return s;
-  cudaError_t e = C.forward(B, m, q, m->n, false, st);
+  cudaError_t e = C.forward(B, m, q, m->n, false, ctx->d_status, st);
   if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(C.o_scores), npairs, C.Lf, centres, margin, st);
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "propose");
 }
@@ -1609,7 +1609,7 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   float* marg = B.dw<float>(w.o_marg);
   WinJob* jobs = B.dw<WinJob>(w.o_jobs);
   cudaError_t e = w.Q.launch(B, ctx->d_status, st);
-  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, st);
+  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, ctx->d_status, st);
   if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
   if (e == cudaSuccess) {
     k_make_windows<<<(P * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, P, n, B.dw<int32_t>(w.o_cwin),

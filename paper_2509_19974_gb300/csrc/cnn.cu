@@ -238,10 +238,10 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
 
 // ---- inference chain with BF16 activation rows
 // Inference keeps the activations between layers as BF16 rows [signal][pos][32
-// channels] (64 bytes per position): the tensor-core layers round their inputs
-// to BF16 anyway, so the values are those of the FP32 chain, at half the
-// traffic and with 16-byte loads.  The last layer writes FP32 features
-// [signal][32][Lf] for the scores.
+// channels] (64 bytes per position): the tensor-core layers (tcgen05, in
+// mma.cu) take BF16 operands anyway, so the values are those of the FP32
+// chain rounded where the tensor cores would round them, at half the traffic.
+// The last layer writes FP32 features [signal][32][Lf] for the scores.
 
 // Layer 0 fused with the decimation: d[j] = (sum of q[16 j .. 16 j + 15]) / 4,
 // conv (kernel 9, pad 4, 1 -> 32 channels) + bias, ReLU, max-pool 2 -> BF16
@@ -314,188 +314,96 @@ __global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict
     dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-}
+// Scores: score[l] = alpha * sum_c sum_i fx[c][i] fy[c][i + l].  A CTA
+// takes 128 consecutive bins of one pair, a warp 16 of them, a lane one
+// channel; the positions stream through shared memory in tiles of 128 (both
+// features transposed to [position][channel], rows padded to 33 floats so
+// the transposing stores and the lane-per-channel loads are conflict-free,
+// zeros outside [0, Lf)).  Each warp walks only the positions where its bins
+// overlap, in blocks of 16 (a block that runs past the overlap multiplies
+// zeros), keeps a 31-value sliding window of fy in registers (16 FMAs per
+// shared-memory load pair) and reduces its 16 per-channel sums across the
+// lanes at the end.  Any Lf: shared memory does not grow with it.
+constexpr int kScWarps = 8;                     // warps per CTA
+constexpr int kScG = 16;                        // bins per warp
+constexpr int kScBins = kScWarps * kScG;        // bins per CTA (128)
+constexpr int kScT = 128;                       // positions per tile
+constexpr int kScRow = kCnnC + 1;               // padded row
+constexpr int kScYRows = kScT + kScBins + kScG; // fy rows per tile (272)
+constexpr int kScSmem = (kScT + kScYRows) * kScRow * 4;
 
-// 32 -> 32 channel layer on BF16 rows: conv (kernel 9, pad 4) + bias, ReLU,
-// max-pool 2.  The same tiles and accumulation order as k_conv_fwd_tc, with
-// fragments loaded by ldmatrix.  kLast: FP32 channel-major output, else BF16
-// rows.
-template <bool kLast>
-__global__ void __launch_bounds__(kThreads) k_conv_rows(const uint16_t* __restrict__ in,
-                                                        void* __restrict__ out, int L,
-                                                        const uint16_t* __restrict__ wbf,
-                                                        const float* __restrict__ bias) {
-  extern __shared__ __align__(16) uint32_t tsm[];
-  uint16_t* xs = reinterpret_cast<uint16_t*>(tsm);                 // [kTP + 8][kXR]
-  uint16_t* ws = xs + (kTP + 8) * kXR;                             // [9][32 co][kXR]
-  const int s = blockIdx.y, p0 = blockIdx.x * kTP;
-  const uint16_t* src = in + (int64_t)s * L * kCnnC;
-  // X rows r <-> position p0 - 4 + r: four 16-byte pieces per row
-  for (int idx = threadIdx.x; idx < (kTP + 8) * 4; idx += kThreads) {
-    const int r = idx >> 2, piece = idx & 3;
-    const int pos = p0 - 4 + r;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (pos >= 0 && pos < L) v = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)pos * kCnnC) + piece);
-    *reinterpret_cast<uint4*>(xs + r * kXR + 8 * piece) = v;
-  }
-  for (int idx = threadIdx.x; idx < kCnnC * kCnnC * kCnnK; idx += kThreads) {
-    const int co = idx / (kCnnC * kCnnK), r = idx % (kCnnC * kCnnK);
-    const int ci = r / kCnnK, k = r % kCnnK;
-    ws[(k * kCnnC + co) * kXR + ci] = wbf[idx];
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int nmt = (L - p0) < kTP ? (L - p0) / 16 : kTP / 16;  // m-tiles of this CTA
-  const uint32_t xs_a = (uint32_t)__cvta_generic_to_shared(xs);
-  const uint32_t ws_a = (uint32_t)__cvta_generic_to_shared(ws);
-  // ldmatrix row addresses: A (16 x 16): lanes 0-7 rows 0-7 k 0-7, 8-15 rows 8-15
-  // k 0-7, 16-23 rows 0-7 k 8-15, 24-31 rows 8-15 k 8-15.  B (two n-tiles of 8
-  // co x 16 ci): lanes 0-7 co 0-7 ci 0-7, 8-15 co 0-7 ci 8-15, 16-23 co 8-15
-  // ci 0-7, 24-31 co 8-15 ci 8-15.
-  const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_col = (lane >> 4) * 8;
-  const int b_row = (lane & 7) + (lane >> 4) * 8, b_col = ((lane >> 3) & 1) * 8;
-  float acc[4][4][4];
-#pragma unroll
-  for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
-#pragma unroll 1
-  for (int k = 0; k < kCnnK; ++k) {
-#pragma unroll
-    for (int ks = 0; ks < kCnnC; ks += 16) {
-      uint32_t b[4][2];
-#pragma unroll
-      for (int nh = 0; nh < 2; ++nh) {
-        uint32_t r[4];
-        ldsm_x4(ws_a + 2u * (uint32_t)((k * kCnnC + 16 * nh + b_row) * kXR + ks + b_col), r);
-        b[2 * nh][0] = r[0], b[2 * nh][1] = r[1], b[2 * nh + 1][0] = r[2], b[2 * nh + 1][1] = r[3];
-      }
-#pragma unroll
-      for (int mi = 0; mi < 4; ++mi) {
-        const int mt = warp + 8 * mi;
-        if (mt >= nmt) continue;
-        uint32_t a[4];
-        ldsm_x4(xs_a + 2u * (uint32_t)((mt * 16 + a_row + k) * kXR + ks + a_col), a);
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], a, b[ni][0], b[ni][1]);
-      }
-    }
-  }
-  // epilogue: bias, ReLU, max-pool rows (g, g^1) via a lane shuffle (lane ^ 4)
-#pragma unroll
-  for (int mi = 0; mi < 4; ++mi) {
-    const int mt = warp + 8 * mi;
-    if (mt >= nmt) continue;  // warp-uniform
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni) {
-      const int co = ni * 8 + 2 * t;
-      const float b0 = bias[co], b1 = bias[co + 1];
-      float v[4] = {fmaxf(acc[mi][ni][0] + b0, 0.f), fmaxf(acc[mi][ni][1] + b1, 0.f),
-                    fmaxf(acc[mi][ni][2] + b0, 0.f), fmaxf(acc[mi][ni][3] + b1, 0.f)};
-      float o[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) o[e] = fmaxf(v[e], __shfl_xor_sync(0xffffffffu, v[e], 4));
-      if ((g & 1) == 0) {
-        const int prow = p0 + mt * 16 + g;  // even position; rows g and g + 8
-        if (kLast) {
-          float* d0 = static_cast<float*>(out) + ((int64_t)s * kCnnC + co) * (L / 2);
-          float* d1 = d0 + (L / 2);
-          d0[prow / 2] = o[0];
-          d1[prow / 2] = o[1];
-          d0[prow / 2 + 4] = o[2];
-          d1[prow / 2 + 4] = o[3];
-        } else {
-          uint16_t* dst = static_cast<uint16_t*>(out) + (int64_t)s * (L / 2) * kCnnC;
-          *reinterpret_cast<uint32_t*>(dst + (int64_t)(prow / 2) * kCnnC + co) = pack_bf16x2(o[0], o[1]);
-          *reinterpret_cast<uint32_t*>(dst + (int64_t)(prow / 2 + 4) * kCnnC + co) =
-              pack_bf16x2(o[2], o[3]);
-        }
-      }
-    }
-  }
-}
-
-// scores of one pair.  Thread = (group of 8 consecutive bins, quarter of the
-// channels); per channel it walks the positions 8 at a time with 16-byte
-// loads: 8 fx values and 8 new fy values feed 64 FMAs.  fy sits in shared
-// memory with kScorePad leading zeros (so that every 8-bin group's window
-// starts on a 16-byte boundary) and zeros past its end; the four channel
-// quarters are summed through shared memory.
-__host__ __device__ constexpr int score_pad(int Lf) { return Lf + 3; }
-__host__ __device__ constexpr int score_row(int Lf) { return ((score_pad(Lf) + 2 * Lf + 16) + 3) / 4 * 4; }
-
-constexpr int kScoreT = 512;    // threads: (8-bin group, group of 4 channels)
-constexpr int kScoreCG = 8;     // channel groups
-
-__global__ void __launch_bounds__(kScoreT) k_scores(const float* __restrict__ feat, int Lf,
-                                                    const float* __restrict__ params,
-                                                    float* __restrict__ scores) {
+__global__ void __launch_bounds__(kScWarps * 32) k_scores(const float* __restrict__ feat, int Lf,
+                                                          const float* __restrict__ params,
+                                                          float* __restrict__ scores) {
   extern __shared__ __align__(16) float sm[];
-  const int P = score_pad(Lf), R = score_row(Lf);
-  float* fx = sm;                     // [32][Lf]
-  float* fy = sm + kCnnC * Lf;        // [32][R]: fy[c][j] at P + j
-  float* part = fy + kCnnC * R;       // [8][nb rounded to 8]
-  const int p = blockIdx.x;
+  float* xs = sm;                    // [kScT][kScRow]: fx at position i0 + r
+  float* ys = sm + kScT * kScRow;    // [kScYRows][kScRow]: fy at position i0 + l_lo + r
+  const int p = blockIdx.y;
+  const int nb = 2 * Lf - 1;
+  const int b_lo = blockIdx.x * kScBins;
+  const int l_lo = b_lo - (Lf - 1);  // lag of the CTA's first bin
   const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
   const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
-  for (int i = threadIdx.x; i < kCnnC * Lf; i += kScoreT) fx[i] = gx[i];
-  for (int i = threadIdx.x; i < kCnnC * R; i += kScoreT) {
-    const int c = i / R, j = i % R - P;
-    fy[i] = (j >= 0 && j < Lf) ? gy[c * Lf + j] : 0.f;
-  }
-  __syncthreads();
-  const float alpha = params[kCnnAlpha];
-  const int nb = 2 * Lf - 1, ngroups = (nb + 7) / 8, nbr = ngroups * 8;
-  constexpr int kPerCG = kCnnC / kScoreCG;
-  for (int w = threadIdx.x; w < ngroups * kScoreCG; w += kScoreT) {
-    const int grp = w % ngroups, cq = w / ngroups;
-    const int b0 = grp * 8, l0 = b0 - (Lf - 1);  // bins b0.. <-> lags l0..
-    float acc[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lg = l_lo + kScG * warp;  // lag of the warp's first bin
+  // positions where some bin of the warp (of the CTA) overlaps, rounded out to 16
+  const int wlo = max(0, -(lg + kScG - 1)) & ~(kScG - 1);
+  const int whi = (min(Lf, Lf - lg) + kScG - 1) & ~(kScG - 1);
+  const int clo = max(0, -(l_lo + kScBins - 1)) & ~(kScG - 1);
+  const int chi = min(Lf, Lf - l_lo);
+  float acc[kScG];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = 0.f;
-    for (int c = cq * kPerCG; c < cq * kPerCG + kPerCG; ++c) {
-      const float* a = fx + c * Lf;
-      const float* y = fy + c * R + P + l0;  // y[i + t] = fy[c][i + l0 + t]; 16-byte aligned
-      float yw[16];
-      {
-        const float4 u0 = *reinterpret_cast<const float4*>(y);
-        const float4 u1 = *reinterpret_cast<const float4*>(y + 4);
-        yw[0] = u0.x, yw[1] = u0.y, yw[2] = u0.z, yw[3] = u0.w;
-        yw[4] = u1.x, yw[5] = u1.y, yw[6] = u1.z, yw[7] = u1.w;
-      }
-      for (int i0 = 0; i0 < Lf; i0 += 8) {
-        const float4 a0 = *reinterpret_cast<const float4*>(a + i0);
-        const float4 a1 = *reinterpret_cast<const float4*>(a + i0 + 4);
-        const float4 u0 = *reinterpret_cast<const float4*>(y + i0 + 8);
-        const float4 u1 = *reinterpret_cast<const float4*>(y + i0 + 12);
-        yw[8] = u0.x, yw[9] = u0.y, yw[10] = u0.z, yw[11] = u0.w;
-        yw[12] = u1.x, yw[13] = u1.y, yw[14] = u1.z, yw[15] = u1.w;
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  for (int t = 0; t < kScG; ++t) acc[t] = 0.f;
+  for (int i0 = clo; i0 < chi; i0 += kScT) {
+    for (int idx = threadIdx.x; idx < kCnnC * kScT; idx += kScWarps * 32) {
+      const int c = idx / kScT, r = idx % kScT, i = i0 + r;
+      xs[r * kScRow + c] = i < Lf ? __ldg(gx + (int64_t)c * Lf + i) : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < kCnnC * kScYRows; idx += kScWarps * 32) {
+      const int c = idx / kScYRows, r = idx % kScYRows, j = i0 + l_lo + r;
+      ys[r * kScRow + c] = (j >= 0 && j < Lf) ? __ldg(gy + (int64_t)c * Lf + j) : 0.f;
+    }
+    __syncthreads();
+    const int blo = max(wlo, i0), bhi = min(whi, i0 + kScT);  // warp-uniform
+    if (blo < bhi) {
+      const float* xr = xs + (blo - i0) * kScRow + lane;
+      const float* yr = ys + (blo - i0 + kScG * warp) * kScRow + lane;
+      float yv[2 * kScG - 1];
 #pragma unroll
-        for (int s2 = 0; s2 < 8; ++s2)
+      for (int t = 0; t < kScG - 1; ++t) yv[t] = yr[t * kScRow];
+      for (int ib = blo; ib < bhi; ib += kScG) {
 #pragma unroll
-          for (int t = 0; t < 8; ++t) acc[t] = fmaf(av[s2], yw[s2 + t], acc[t]);
+        for (int t = kScG - 1; t < 2 * kScG - 1; ++t) yv[t] = yr[t * kScRow];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) yw[t] = yw[t + 8];
+        for (int s2 = 0; s2 < kScG; ++s2) {
+          const float xv = xr[s2 * kScRow];
+#pragma unroll
+          for (int t = 0; t < kScG; ++t) acc[t] = fmaf(xv, yv[s2 + t], acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < kScG - 1; ++t) yv[t] = yv[t + kScG];
+        xr += kScG * kScRow;
+        yr += kScG * kScRow;
       }
     }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) part[cq * nbr + b0 + t] = acc[t];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += kScoreT) {
-    float t = 0.f;
+  // sum over the 32 lanes (channels): each step halves the values a lane
+  // keeps (the step with mask m keeps the upper half when lane & m), so
+  // afterwards the lane holds bin (lane >> 1) & 15 summed over all lanes.
 #pragma unroll
-    for (int cq = 0; cq < kScoreCG; ++cq) t += part[cq * nbr + b];
-    scores[(int64_t)p * nb + b] = alpha * t;
+  for (int half = kScG / 2, m = 16; half >= 1; half >>= 1, m >>= 1) {
+    const bool hi = (lane & m) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float send = hi ? acc[j] : acc[j + half];
+      const float keep = hi ? acc[j + half] : acc[j];
+      acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
   }
+  acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+  const int bin = b_lo + kScG * warp + ((lane >> 1) & (kScG - 1));
+  if ((lane & 1) == 0 && bin < nb) scores[(int64_t)p * nb + bin] = params[kCnnAlpha] * acc[0];
 }
 
 // lag rank of bin l: smaller |l| first, then negative first (the estimator's
@@ -903,35 +811,28 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             cudaStream_t st) {
+                             uint32_t* d_status, cudaStream_t st) {
   const int Ld = (int)(n / kCnnDec);
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
   k_conv1_inf<<<dim3((Ld / 2 + kC1T - 1) / kC1T, nsig), kThreads, 0, st>>>(
       q, n, wbf + cnn_woff(0), params + cnn_boff(0), act[0]);
   TDE_COUNT_LAUNCH(1);
-  const int smem = ((kTP + 8) * kXR + kCnnK * kCnnC * kXR) * 2;
-  cudaFuncSetAttribute(k_conv_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_conv_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  for (int l = 1; l < kCnnLayers; ++l) {
-    const int L = Ld >> l;  // input length of layer l
-    const dim3 grid((L + kTP - 1) / kTP, nsig);
-    if (l == kCnnLayers - 1)
-      k_conv_rows<true><<<grid, kThreads, smem, st>>>(act[l - 1], feat, L, wbf + cnn_woff(l),
-                                                      params + cnn_boff(l));
-    else
-      k_conv_rows<false><<<grid, kThreads, smem, st>>>(act[l - 1], act[l], L, wbf + cnn_woff(l),
-                                                       params + cnn_boff(l));
-    TDE_COUNT_LAUNCH(1);
+  cudaError_t e = cudaGetLastError();
+  for (int l = 1; l < kCnnLayers && e == cudaSuccess; ++l) {
+    const bool last = l == kCnnLayers - 1;
+    e = launch_cnn_conv_tc(act[l - 1], last ? static_cast<void*>(feat) : static_cast<void*>(act[l]),
+                           Ld >> l, nsig, wbf + cnn_woff(l), params + cnn_boff(l), last, d_status, st);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st) {
-  if (Lf % 8 != 0) return cudaErrorInvalidValue;  // Lf = n / 256 with n a multiple of 2048
-  const int smem = (kCnnC * Lf + kCnnC * score_row(Lf) + kScoreCG * (2 * Lf + 7)) * 4;
-  cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_scores<<<npairs, kScoreT, smem, st>>>(feat, Lf, params, scores);
+  if (Lf < 1 || npairs <= 0) return npairs <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, kScSmem);
+  const int nb = 2 * Lf - 1;
+  k_scores<<<dim3((nb + kScBins - 1) / kScBins, npairs), kScWarps * 32, kScSmem, st>>>(feat, Lf, params,
+                                                                                     scores);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -41,7 +41,13 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 // feat receives the FP32 features [nsig][32][n/256].  n a multiple of 2048.
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             cudaStream_t st);
+                             uint32_t* d_status, cudaStream_t st);
+// One 32 -> 32 channel layer of the inference forward on the tensor cores
+// (mma.cu): in = BF16 rows [nsig][L][32]; out = BF16 rows [nsig][L/2][32], or
+// (last) FP32 features [nsig][32][L/2]; wbf / bias = that layer's BF16
+// weights [32][32][9] and FP32 bias.  L even.  Time-outs set TDE_ST_TIMEOUT.
+cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, const uint16_t* wbf,
+                               const float* bias, bool last, uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st);
