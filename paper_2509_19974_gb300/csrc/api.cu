@@ -1217,7 +1217,7 @@ struct CnnPlan {
     const size_t S = 2 * (size_t)P;
     if (!train) {
       for (int l = 0; l + 1 < kCnnLayers; ++l)
-        o_act[l] = L.w<uint16_t>(S * kCnnC * (size_t)(Ld >> (l + 1)));
+        o_act[l] = L.w<uint16_t>(S * (size_t)cnn_eo_elems(Ld >> (l + 1)));
       o_out[kCnnLayers - 1] = L.w<float>(S * kCnnC * (size_t)Lf);
     } else {
       o_d = L.w<float>(S * Ld);

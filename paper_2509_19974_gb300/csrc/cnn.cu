@@ -244,9 +244,10 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
 // The last layer writes FP32 features [signal][32][Lf] for the scores.
 
 // Layer 0 fused with the decimation: d[j] = (sum of q[16 j .. 16 j + 15]) / 4,
-// conv (kernel 9, pad 4, 1 -> 32 channels) + bias, ReLU, max-pool 2 -> BF16
-// rows.  A CTA makes 256 pooled positions; thread = one pooled position, all
-// 32 channels (FP32 arithmetic in the same order as k_conv_fwd<1>).
+// conv (kernel 9, pad 4, 1 -> 32 channels) + bias, ReLU, max-pool 2 -> the
+// next layer's input (parity / 8-channel-chunk arrays, zero rows included).
+// A CTA makes 256 pooled positions; thread = one pooled position, all 32
+// channels (FP32 arithmetic in the same order as k_conv_fwd<1>).
 constexpr int kC1T = 256;  // pooled positions per CTA
 
 __global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict__ q, int64_t n,
@@ -308,10 +309,24 @@ __global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict
     packed[2 * c4] = pack_bf16x2(r[0], r[1]);
     packed[2 * c4 + 1] = pack_bf16x2(r[2], r[3]);
   }
-  uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)s * (Ld / 2) + P) * kCnnC);
+  const int Rn = cnn_eo_rows(Ld / 2);
+  uint16_t* dst = out + ((((int64_t)s * 2 + (P & 1)) * 4) * Rn + (P >> 1) + 2) * 8;
 #pragma unroll
   for (int v = 0; v < 4; ++v)
-    dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+    *reinterpret_cast<uint4*>(dst + (int64_t)v * Rn * 8) =
+        make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+}
+
+// The zero rows of a layer input of length L (rows 0, 1 and [L/2 + 2, R)).
+__global__ void k_eo_pad(uint16_t* __restrict__ act, int L, int nsig) {
+  const int R = cnn_eo_rows(L), v = L / 2 + 2, npad = 2 + (R - v);
+  const int64_t total = (int64_t)nsig * 8 * npad;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pr = (int)(i % npad);
+    const int r = pr < 2 ? pr : v + (pr - 2);
+    *reinterpret_cast<uint4*>(act + ((i / npad) * R + r) * 8) = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 // Scores: score[l] = alpha * sum_c sum_i fx[c][i] fy[c][i + l].  A CTA
@@ -816,7 +831,8 @@ cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
   k_conv1_inf<<<dim3((Ld / 2 + kC1T - 1) / kC1T, nsig), kThreads, 0, st>>>(
       q, n, wbf + cnn_woff(0), params + cnn_boff(0), act[0]);
-  TDE_COUNT_LAUNCH(1);
+  k_eo_pad<<<(nsig + 63) / 64, 256, 0, st>>>(act[0], Ld / 2, nsig);
+  TDE_COUNT_LAUNCH(2);
   cudaError_t e = cudaGetLastError();
   for (int l = 1; l < kCnnLayers && e == cudaSuccess; ++l) {
     const bool last = l == kCnnLayers - 1;

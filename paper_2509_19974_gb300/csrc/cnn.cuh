@@ -36,16 +36,27 @@ cudaError_t launch_cnn_decimate(const int8_t* q, int64_t n, int nsig, float* d, 
 // One layer for S signals with the BF16 weights of layer l.
 cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16_t* wbf,
                              const float* params, cudaStream_t st);
-// Inference forward (decimate + 4 layers) with BF16 activation rows between
-// layers: act[l] holds layer l's output, [nsig][(n/16) >> (l+1)][32] BF16;
-// feat receives the FP32 features [nsig][32][n/256].  n a multiple of 2048.
+// Inference forward (decimate + 4 layers) with BF16 activations between
+// layers: act[l] holds layer l's output, nsig x cnn_eo_elems((n/16) >> (l+1))
+// BF16 in the layout above; feat receives the FP32 features [nsig][32][n/256].
+// n a multiple of 2048.
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
                              uint32_t* d_status, cudaStream_t st);
+// Inference activations between conv layers: a layer's input of length L
+// is, per signal, 8 arrays (position parity x 8-channel chunk, parity-major)
+// of cnn_eo_rows(L) rows of 8 BF16 channels; row r holds position 2r - 4
+// (even array) or 2r - 3 (odd array) and is zero outside [0, L).  The rows
+// cover whole 128-output tiles plus a 4-row halo.
+__host__ __device__ constexpr int cnn_eo_rows(int L) { return (L / 2 + 127) / 128 * 128 + 4; }
+__host__ __device__ constexpr int64_t cnn_eo_elems(int L) { return (int64_t)8 * cnn_eo_rows(L) * 8; }
+
 // One 32 -> 32 channel layer of the inference forward on the tensor cores
-// (mma.cu): in = BF16 rows [nsig][L][32]; out = BF16 rows [nsig][L/2][32], or
-// (last) FP32 features [nsig][32][L/2]; wbf / bias = that layer's BF16
-// weights [32][32][9] and FP32 bias.  L even.  Time-outs set TDE_ST_TIMEOUT.
+// (mma.cu): in = that layer's input (length L, layout above); out = the next
+// layer's input (length L/2, same layout, zero rows included) or (last) FP32
+// features [nsig][32][L/2]; wbf / bias = that layer's BF16 weights
+// [32][32][9] and FP32 bias.  L a multiple of 4.  Time-outs set
+// TDE_ST_TIMEOUT.
 cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, const uint16_t* wbf,
                                const float* bias, bool last, uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1).

@@ -776,42 +776,52 @@ __global__ void __launch_bounds__(kThreads, 3)
 // ---------------------------------------------------------------------------
 // The learned proposal's 32 -> 32 channel conv layers (inference) on the
 // tensor cores: kind::f16 with BF16 operands and FP32 accumulation in tensor
-// memory.  A tile is 128 consecutive output positions p0 + m of one signal
-// (TMEM lane m) x 32 output channels (TMEM column):
-//   D[m][co] = sum_k sum_ci X[p0 + m + k - 4][ci] W[co][ci][k],
-// as 18 MMAs of K = 16 (9 taps x 2 halves of the input channels).  The input
-// rows of the tile (positions p0 - 4 .. p0 + 131, zero outside [0, L)) are
-// staged as four column arrays, one per 8 input channels, each 136 rows x
-// 16 bytes; in the no-swizzle K-major layout the A operand of tap k is then
-// the arrays' core matrices starting k rows down (start + 16 k bytes, leading
-// byte offset = the array stride, stride byte offset 128), so the Hankel
-// structure in (m, k) costs no copies.  The weights are staged once per CTA
-// as W_s[k][ci / 8][co][ci % 8] (B operand of tap k, half h: leading byte
-// offset 512, stride byte offset 128).
+// memory.  z[p][co] = sum_k sum_ci X[p + k - 4][ci] W[co][ci][k] (kernel 9,
+// pad 4), then bias, ReLU and max-pool of (2P, 2P + 1).
 //
-// A CTA takes an equal contiguous run of the (signal, tile) units.  Input
-// tiles go through a ring of kCvNB buffers (cp.async, zero-filled outside the
-// signal, issued kCvNB - 1 tiles ahead) and the accumulators are
-// double-buffered (2 x 32 TMEM columns): while tile i's MMAs run, the CTA
-// starts loading tile i + kCvNB - 1 and runs tile i - 1's epilogue (bias,
-// ReLU, max-pool of lane pairs, BF16 rows or, for the last layer, FP32
-// channel-major features).  Waits are bounded; on time-out the CTA flags TDE_ST_TIMEOUT,
-// waits (bounded) for its MMAs and frees its tensor memory.
+// Input layout (written by the previous layer): per signal, per position
+// parity (E: even positions, O: odd) and per 8-channel chunk j, an array of
+// R = cnn_eo_rows(L) rows of 16 bytes, row r holding position 2r - 4 (E) or
+// 2r - 3 (O), zero outside [0, L).  A tile is 128 pooled outputs
+// P = P0 + m (TMEM lane m); it needs rows P0 .. P0 + 131 of the 8 arrays,
+// contiguous in global memory, so one thread moves it with 8 bulk copies.
+//
+// In that layout every shifted window of rows serves two taps at once: rows
+// m + d of E feed the even output 2P through tap 2d and the odd output 2P + 1
+// through tap 2d - 1; rows m + d of O feed the even output through tap 2d + 1
+// and the odd one through tap 2d.  With the weights staged as blocks
+// W_s[j][t][co][ci % 8] for t = tap + 1 (t = 0 and t = 10 are zero blocks),
+// the B operand of a window is two consecutive blocks (N = 64: columns 0-31
+// the odd outputs' tap, 32-63 the even outputs'), so a tile is 10 windows x 2
+// halves of the input channels = 20 MMAs of 128 x 64 x 16, and each lane ends
+// with both outputs of its pooling pair: y = relu(max(z_even, z_odd) + b).
+//
+// Outputs: the next layer's E/O arrays (with their zero rows), or for the
+// last layer FP32 features [signal][32][L/2].  A CTA takes an equal
+// contiguous run of (signal, tile) units; thread 0 keeps kCvNB tiles of bulk
+// copies in flight and issues the MMAs into two accumulators (2 x 64 TMEM
+// columns), so tile i's MMAs overlap tile i - 1's epilogue.  Waits are
+// bounded; on time-out the CTA flags TDE_ST_TIMEOUT, waits (bounded) for its
+// copies and MMAs and frees its tensor memory.
 
-constexpr int kCvM = 128;                          // positions per tile (MMA M)
-constexpr int kCvRows = kCvM + kCnnK - 1;          // staged input rows (136)
-constexpr int kCvArr = kCvRows * 16;               // bytes per 8-channel column array
-constexpr int kCvXBytes = (kCnnC / 8) * kCvArr;    // one tile's input
-constexpr int kCvWBytes = kCnnK * kCnnC * kCnnC * 2;
-constexpr int kCvNB = 4;                           // input tile buffers
-constexpr int kCvSmem = kCvNB * kCvXBytes + kCvWBytes + 2 * 8 + 16 + 128;
-constexpr int kCvCtasPerSm = 4;
+constexpr int kCvM = 128;                          // pooled outputs per tile (MMA M)
+constexpr int kCvN = 64;                           // odd | even outputs
+constexpr int kCvRows = kCvM + 4;                  // input rows per parity array per tile
+constexpr int kCvArr = kCvRows * 16;               // bytes of one (parity, chunk) piece
+constexpr int kCvXBytes = 2 * (kCnnC / 8) * kCvArr;  // one tile's input (16896)
+constexpr int kCvTaps = kCnnK + 2;                 // weight blocks per chunk (zero at both ends)
+constexpr int kCvWBytes = (kCnnC / 8) * kCvTaps * kCnnC * 16;
+constexpr int kCvNB = 3;                           // input tile buffers
+constexpr int kCvSmem = kCvNB * kCvXBytes + kCvWBytes + (kCvNB + 2) * 8 + 16 + 128;
+constexpr int kCvCtasPerSm = 3;
+static_assert(kCvXBytes % 128 == 0 && kCvWBytes % 128 == 0, "conv staging alignment");
+static_assert(kCvCtasPerSm * (kCvSmem + 1024) <= 228 * 1024, "conv CTAs per SM");
 
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
 // bits 24-28.
 constexpr uint32_t kCvIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCnnC >> 3) << 17) | ((uint32_t)(kCvM >> 4) << 24);
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCvN >> 3) << 17) | ((uint32_t)(kCvM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
@@ -822,8 +832,9 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
-// 32 lanes x 16 consecutive columns of FP32 accumulator -> registers.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+// 32 lanes x 16 consecutive columns of FP32 accumulator -> registers (the
+// caller waits with tcgen05.wait::ld).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -831,17 +842,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
         "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 16 bytes global -> shared, asynchronously; zero-filled when !valid.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-               "r"(valid ? 16 : 0)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// bytes (multiple of 16) global -> shared, completing on bar's transaction count
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2_rn(float lo, float hi) {
   uint32_t r;
@@ -857,148 +870,166 @@ __global__ void __launch_bounds__(kThreads, kCvCtasPerSm)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 127u) & ~127u;
-  const uint32_t xbuf = base;                    // kCvNB tiles' input, kCvXBytes each
-  const uint32_t wsm = xbuf + kCvNB * kCvXBytes; // weights
-  const uint32_t bar = wsm + kCvWBytes;          // two MMA-done barriers
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (bar + 16 - raw));
+  const uint32_t xbuf = base;                     // kCvNB tiles' input
+  const uint32_t wsm = xbuf + kCvNB * kCvXBytes;  // weight blocks
+  const uint32_t full_bar = wsm + kCvWBytes;      // per input buffer
+  const uint32_t done_bar = full_bar + 8 * kCvNB; // per accumulator
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 16 - raw));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tps = (L + kCvM - 1) / kCvM;  // tiles per signal
-  const int64_t units = (int64_t)nsig * tps;
-  const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
-  const int ntiles = (int)(u1 - u0);
+  const int Lo = L / 2;                            // pooled outputs
+  const int tps = (Lo + kCvM - 1) / kCvM;          // tiles per signal
+  const int R = cnn_eo_rows(L);                    // rows per input array
+  const int units = nsig * tps;
+  const int u0 = (int)((int64_t)units * blockIdx.x / gridDim.x);
+  const int ntiles = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x) - u0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(2 * kCnnC)
+                 "r"(2 * kCvN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 32) {
-    mbar_init(bar, 1);
-    mbar_init(bar + 8, 1);
+    for (int b = 0; b < kCvNB; ++b) mbar_init(full_bar + 8 * b, 1);
+    mbar_init(done_bar, 1);
+    mbar_init(done_bar + 8, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // weights: W_s[k][ci / 8][co][ci % 8]
-  for (int idx = threadIdx.x; idx < kCnnC * kCnnC * kCnnK; idx += kThreads) {
-    const int co = idx / (kCnnC * kCnnK), r = idx % (kCnnC * kCnnK);
-    const int ci = r / kCnnK, k = r % kCnnK;
-    const uint32_t a = wsm + (uint32_t)(((k * (kCnnC / 8) + (ci >> 3)) * kCnnC + co) * 16 + (ci & 7) * 2);
-    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(wbf[idx]) : "memory");
-  }
-  // stage tile u's input rows into buffer b (cp.async; the caller commits)
-  auto stage = [&](int64_t u, int b) {
-    const int s = (int)(u / tps), p0 = (int)(u - (int64_t)s * tps) * kCvM;
-    const uint16_t* src = in + (int64_t)s * L * kCnnC;
-    const uint32_t xb = xbuf + (uint32_t)b * kCvXBytes;
-    for (int idx = threadIdx.x; idx < kCvRows * (kCnnC / 8); idx += kThreads) {
-      const int r = idx >> 2, j = idx & 3;
-      const int pos = p0 - (kCnnK / 2) + r;
-      const bool ok = pos >= 0 && pos < L;
-      cp_async16(xb + (uint32_t)(j * kCvArr + r * 16), src + (int64_t)(ok ? pos : 0) * kCnnC + 8 * j, ok);
+  // weight blocks W_s[j][t][co][e], t = tap + 1 (zero blocks at t = 0, 10),
+  // two elements per store
+  for (int idx = threadIdx.x; idx < (kCvWBytes / 4); idx += kThreads) {
+    const int e2 = idx & 3, co = (idx >> 2) & (kCnnC - 1), jt = idx >> 7;
+    const int t = jt % kCvTaps, j = jt / kCvTaps, k = t - 1;
+    uint32_t v = 0;
+    if (k >= 0 && k < kCnnK) {
+      const int ci = 8 * j + 2 * e2;
+      v = (uint32_t)wbf[(co * kCnnC + ci) * kCnnK + k] | ((uint32_t)wbf[(co * kCnnC + ci + 1) * kCnnK + k] << 16);
     }
-  };
-  // one commit group per tile slot (empty past the run), so that before
-  // tile i's MMAs exactly kCvNB - 2 later groups may still be in flight
-  for (int i = 0; i < kCvNB - 1; ++i) {
-    if (i < ntiles) stage(u0 + i, i);
-    cp_async_commit();
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(wsm + 4u * (uint32_t)idx), "r"(v) : "memory");
   }
-  const int qd = warp & 3, ch = warp >> 2;  // TMEM lanes 32 qd.., columns 16 ch..
+  // the next layer's zero rows: 0, 1 and [L/4 + 2, R') of each array
+  if (!kLast) {
+    const int Rn = cnn_eo_rows(Lo), vn = Lo / 2 + 2, npad = 2 + (Rn - vn);
+    uint16_t* o = static_cast<uint16_t*>(out);
+    const int64_t total = (int64_t)nsig * 8 * npad;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (int64_t)gridDim.x * kThreads) {
+      const int pr = (int)(i % npad);
+      const int64_t arr = i / npad;  // (signal, parity, chunk)
+      const int r = pr < 2 ? pr : vn + (pr - 2);
+      *reinterpret_cast<uint4*>(o + (arr * Rn + r) * 8) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  const int qd = warp & 3, ch = warp >> 2;  // TMEM lanes 32 qd.., channels 16 ch..
   float bv[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) bv[j] = bias[16 * ch + j];
+  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  bool ok = true;
-  int issued = 0;  // tiles whose MMAs were issued
-  // epilogue of tile i: accumulator i % 2
+  // thread 0: bulk copies of tile i (unit u0 + i) into buffer i % kCvNB
+  auto load = [&](int i) {
+    const int u = u0 + i, s = u / tps, P0 = (u - s * tps) * kCvM;
+    const uint32_t fb = full_bar + 8u * (uint32_t)(i % kCvNB);
+    const uint32_t xb = xbuf + (uint32_t)(i % kCvNB) * kCvXBytes;
+    mbar_expect_tx(fb, (uint32_t)kCvXBytes);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)  // a = parity * 4 + chunk
+      bulk_g2s(xb + (uint32_t)a * kCvArr, in + (((int64_t)s * 8 + a) * R + P0) * 8, (uint32_t)kCvArr, fb);
+  };
+  int loaded = 0, issued = 0;  // tiles whose copies / MMAs were issued (thread 0)
+  if (threadIdx.x == 0)
+    for (; loaded < kCvNB && loaded < ntiles; ++loaded) load(loaded);
+
   auto epilogue = [&](int i) {
-    const int64_t u = u0 + i;
-    const int s = (int)(u / tps), p0 = (int)(u - (int64_t)s * tps) * kCvM;
-    uint32_t v[16];
-    tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((i & 1) * kCnnC + 16 * ch), v);
-    const int pos = p0 + 32 * qd + lane;  // even lanes: pooled position pos / 2
-    float o[16];
+    const int u = u0 + i, s = u / tps, P = (u - s * tps) * kCvM + 32 * qd + lane;
+    const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((i & 1) * kCvN + 16 * ch);
+    uint32_t vo[16], ve[16];
+    tmem_ld16_nowait(col, vo);
+    tmem_ld16_nowait(col + 32u, ve);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    float y[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float z = fmaxf(__uint_as_float(v[j]) + bv[j], 0.f);
-      o[j] = fmaxf(z, __shfl_xor_sync(0xffffffffu, z, 1));
-    }
-    if ((lane & 1) == 0 && pos < L) {
-      const int P = pos >> 1;
-      if (kLast) {
-        float* dst = static_cast<float*>(out) + ((int64_t)s * kCnnC + 16 * ch) * (L / 2) + P;
+    for (int j = 0; j < 16; ++j)
+      y[j] = fmaxf(fmaxf(__uint_as_float(ve[j]), __uint_as_float(vo[j])) + bv[j], 0.f);
+    if (P >= Lo) return;
+    if (kLast) {
+      float* dst = static_cast<float*>(out) + ((int64_t)s * kCnnC + 16 * ch) * Lo + P;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) dst[(int64_t)j * (L / 2)] = o[j];
-      } else {
-        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) +
-                                              ((int64_t)s * (L / 2) + P) * kCnnC + 16 * ch);
-        dst[0] = make_uint4(pack_bf16x2_rn(o[0], o[1]), pack_bf16x2_rn(o[2], o[3]),
-                            pack_bf16x2_rn(o[4], o[5]), pack_bf16x2_rn(o[6], o[7]));
-        dst[1] = make_uint4(pack_bf16x2_rn(o[8], o[9]), pack_bf16x2_rn(o[10], o[11]),
-                            pack_bf16x2_rn(o[12], o[13]), pack_bf16x2_rn(o[14], o[15]));
-      }
+      for (int j = 0; j < 16; ++j) dst[(int64_t)j * Lo] = y[j];
+    } else {
+      const int Rn = cnn_eo_rows(Lo);
+      uint16_t* o = static_cast<uint16_t*>(out) +
+                    ((((int64_t)s * 2 + (P & 1)) * 4 + 2 * ch) * Rn + (P >> 1) + 2) * 8;
+      *reinterpret_cast<uint4*>(o) = make_uint4(pack_bf16x2_rn(y[0], y[1]), pack_bf16x2_rn(y[2], y[3]),
+                                                pack_bf16x2_rn(y[4], y[5]), pack_bf16x2_rn(y[6], y[7]));
+      *reinterpret_cast<uint4*>(o + (int64_t)Rn * 8) =
+          make_uint4(pack_bf16x2_rn(y[8], y[9]), pack_bf16x2_rn(y[10], y[11]),
+                     pack_bf16x2_rn(y[12], y[13]), pack_bf16x2_rn(y[14], y[15]));
     }
   };
 
+  bool ok = true;
   for (int i = 0; i < ntiles; ++i) {
-    asm volatile("cp.async.wait_group %0;" ::"n"(kCvNB - 2) : "memory");
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
     if (threadIdx.x == 0) {
-      const uint32_t xb = xbuf + (uint32_t)(i % kCvNB) * kCvXBytes;
-      const uint32_t d = tmem + (uint32_t)((i & 1) * kCnnC);
+      ok = mbar_wait_sleep(full_bar + 8u * (uint32_t)(i % kCvNB), (uint32_t)((i / kCvNB) & 1));
+      if (ok) {
+        tc_fence_after();
+        const uint32_t xb = xbuf + (uint32_t)(i % kCvNB) * kCvXBytes;
+        const uint32_t d = tmem + (uint32_t)((i & 1) * kCvN);
 #pragma unroll
-      for (int k = 0; k < kCnnK; ++k)
+        for (int w = 0; w < 10; ++w) {  // windows: E d = 0..4, O d = 0..4
+          const int par = w / 5, dd = w % 5;
+          const int t0 = 2 * dd + par;  // first weight block of the window
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          mma_bf16(d, sdesc(xb + (uint32_t)(2 * h * kCvArr + 16 * k), kCvArr, 128, 0, 0),
-                   sdesc(wsm + (uint32_t)((k * (kCnnC / 8) + 2 * h) * kCnnC * 16), kCnnC * 16, 128, 0, 0),
-                   kCvIdesc, (k | h) != 0);
-      mma_commit(bar + 8u * (uint32_t)(i & 1));
+          for (int h = 0; h < 2; ++h)
+            mma_bf16(d, sdesc(xb + (uint32_t)((par * 4 + 2 * h) * kCvArr + 16 * dd), kCvArr, 128, 0, 0),
+                     sdesc(wsm + (uint32_t)(((2 * h) * kCvTaps + t0) * kCnnC * 16), kCvTaps * kCnnC * 16, 128, 0, 0),
+                     kCvIdesc, (w | h) != 0);
+        }
+        mma_commit(done_bar + 8u * (uint32_t)(i & 1));
+        issued = i + 1;
+      }
     }
-    issued = i + 1;
     if (i > 0) {
-      // tile i - 1's MMAs: done before its input buffer is refilled and its
-      // accumulator read
-      ok = __syncthreads_and(mbar_wait_sleep(bar + 8u * (uint32_t)((i - 1) & 1),
-                                             (uint32_t)(((i - 1) >> 1) & 1)));
+      // tile i - 1's MMAs: its buffer may be refilled and its accumulator read
+      const bool w_ok = mbar_wait_sleep(done_bar + 8u * (uint32_t)((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1));
+      ok = __syncthreads_and(ok && w_ok);
       if (!ok) break;
-    }
-    // tile i + kCvNB - 1 goes to the buffer tile i - 1 read
-    if (i + kCvNB - 1 < ntiles) stage(u0 + i + kCvNB - 1, (i + kCvNB - 1) % kCvNB);
-    cp_async_commit();
-    if (i > 0) {
+      if (threadIdx.x == 0 && loaded < ntiles) load(loaded++);
       tc_fence_after();
       epilogue(i - 1);
+    } else {
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
     }
+    tc_fence_before();
+    __syncthreads();
   }
-  if (ok && issued > 0) {
-    const int i = issued - 1;
-    ok = __syncthreads_and(mbar_wait_sleep(bar + 8u * (uint32_t)(i & 1), (uint32_t)((i >> 1) & 1)));
+  if (ok && ntiles > 0) {
+    const int i = ntiles - 1;
+    ok = __syncthreads_and(mbar_wait_sleep(done_bar + 8u * (uint32_t)(i & 1), (uint32_t)((i >> 1) & 1)));
     if (ok) {
       tc_fence_after();
       epilogue(i);
     }
   }
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
-    // bounded waits for whatever this CTA issued before freeing tensor memory
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(status, TDE_ST_TIMEOUT);
+    // bounded waits for this CTA's copies and MMAs still in flight
+    for (int i = issued; i < loaded; ++i)
+      mbar_wait_sleep(full_bar + 8u * (uint32_t)(i % kCvNB), (uint32_t)((i / kCvNB) & 1));
     for (int i = issued - 2 < 0 ? 0 : issued - 2; i < issued; ++i)
-      mbar_wait_sleep(bar + 8u * (uint32_t)(i & 1), (uint32_t)((i >> 1) & 1));
+      mbar_wait_sleep(done_bar + 8u * (uint32_t)(i & 1), (uint32_t)((i >> 1) & 1));
   }
-  cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCnnC)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCvN)
                  : "memory");
   }
 }
@@ -1058,14 +1089,15 @@ cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, c
 cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, const uint16_t* wbf,
                                const float* bias, bool last, uint32_t* d_status, cudaStream_t st) {
   if (nsig <= 0 || L <= 0) return cudaSuccess;
-  if (L % 2 != 0) return cudaErrorInvalidValue;
+  if (L % 4 != 0) return cudaErrorInvalidValue;
   auto kern = last ? k_conv_tc<true> : k_conv_tc<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kCvSmem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t units = (int64_t)nsig * ((L + kCvM - 1) / kCvM);
+  const int64_t units = (int64_t)nsig * ((L / 2 + kCvM - 1) / kCvM);
+  if (units > INT32_MAX) return cudaErrorInvalidValue;
   const int64_t cap = (int64_t)kCvCtasPerSm * sms;
   const int grid = (int)(units < cap ? units : cap);
   kern<<<grid, kThreads, kCvSmem, st>>>(in, out, L, nsig, wbf, bias, d_status);
