@@ -1242,12 +1242,12 @@ struct CnnPlan {
     return l == 0 ? B.dw<float>(o_d) : B.dw<float>(o_out[l - 1]);
   }
   cudaError_t forward(const Bases& B, const tde_model* m, const int8_t* q, int64_t n, bool train,
-                      uint32_t* status, cudaStream_t st) const {
+                      uint32_t* status, cudaStream_t st, uint8_t* qe = nullptr) const {
     if (!train) {
       uint16_t* act[kCnnLayers - 1];
       for (int l = 0; l + 1 < kCnnLayers; ++l) act[l] = B.dw<uint16_t>(o_act[l]);
       cudaError_t e = launch_cnn_infer(q, n, 2 * P, m->wbf, m->params, act,
-                                       B.dw<float>(o_out[kCnnLayers - 1]), status, st);
+                                       B.dw<float>(o_out[kCnnLayers - 1]), qe, status, st);
       if (e == cudaSuccess)
         e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
                               B.dw<float>(o_scores), st);
@@ -1463,10 +1463,13 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Layout L;
   const size_t o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
+  const int64_t n_pad = (n + 127) / 128 * 128;
+  const size_t o_qe = L.w<uint8_t>((size_t)2 * npairs * n_pad);
   Bases B;
   tde_status s = realize(ctx, L, &B);
   if (s != TDE_OK) return s;
   WinJob* jobs = B.dw<WinJob>(o_jobs);
+  uint8_t* qe = B.dw<uint8_t>(o_qe);
   cudaError_t e = cudaMemsetAsync(c_out, 0, sizeof(int32_t) * (size_t)npairs * kCnnTopK * kCnnWin, st);
   if (e == cudaSuccess) {
     k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(centres, npairs, n, c_out,
@@ -1474,9 +1477,10 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
     TDE_COUNT_LAUNCH(1);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = launch_to_e4m3(q, n, n_pad, 2 * npairs, qe, st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(q, n, npairs, jobs, ctx->d_status, st);
+    e = launch_xcorr_mma_windows(qe, n, n_pad, npairs, jobs, ctx->d_status, st);
   }
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "windows");
 }
@@ -1550,7 +1554,7 @@ struct LearnedWork {
   QuantStage Q;
   CnnPlan C;
   MmaStage T;  // one full-range pair: the fallback's item template
-  size_t o_q = 0, o_cent = 0, o_marg = 0, o_jobs = 0, o_cwin = 0;
+  size_t o_q = 0, o_qe = 0, o_cent = 0, o_marg = 0, o_jobs = 0, o_cwin = 0;
   size_t o_fbidx = 0, o_nfb = 0, o_fbpairs = 0, o_fbitems = 0, o_nitems = 0, o_counter = 0;
   size_t o_fbargs = 0, o_keys = 0, o_tlag = 0, o_tval = 0, o_cfb = 0;
 };
@@ -1561,6 +1565,7 @@ void learned_plan(LearnedWork* w, int npairs, int64_t n, int bits, float theta) 
   const int S = 2 * npairs;
   w->Q.plan(L, S, bits, nullptr, n);
   w->o_q = L.w<int8_t>((size_t)S * n);
+  w->o_qe = L.w<uint8_t>((size_t)S * n);  // the levels as E4M3 bytes (n % 2048 == 0)
   w->C.plan(L, npairs, n, false);
   w->o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
   w->o_marg = L.w<float>((size_t)npairs);
@@ -1609,7 +1614,8 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   float* marg = B.dw<float>(w.o_marg);
   WinJob* jobs = B.dw<WinJob>(w.o_jobs);
   cudaError_t e = w.Q.launch(B, ctx->d_status, st);
-  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, ctx->d_status, st);
+  uint8_t* qe = B.dw<uint8_t>(w.o_qe);
+  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, ctx->d_status, st, qe);
   if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
   if (e == cudaSuccess) {
     k_make_windows<<<(P * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, P, n, B.dw<int32_t>(w.o_cwin),
@@ -1622,7 +1628,7 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
                         st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(qbuf, n, P, jobs, ctx->d_status, st);
+    e = launch_xcorr_mma_windows(qe, n, n, P, jobs, ctx->d_status, st);
   }
   if (e == cudaSuccess) e = launch_window_argmax(jobs, P, lag_out, val_out, st);
   // fallback, decided and run on the device

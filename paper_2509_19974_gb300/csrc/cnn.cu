@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
 
 // Layer 0 fused with the decimation: d[j] = (sum of q[16 j .. 16 j + 15]) / 4,
 // conv (kernel 9, pad 4, 1 -> 32 channels) + bias, ReLU, max-pool 2 -> the
-// next layer's input (parity / 8-channel-chunk arrays, zero rows included).
+// next layer's input (parity / 8-channel-chunk arrays, zero rows included);
+// on request also the levels as E4M3 bytes (the windows' tensor-core input).
 // A CTA makes 256 pooled positions; thread = one pooled position, all 32
 // channels (FP32 arithmetic in the same order as k_conv_fwd<1>).
 constexpr int kC1T = 256;  // pooled positions per CTA
@@ -253,7 +254,8 @@ constexpr int kC1T = 256;  // pooled positions per CTA
 __global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict__ q, int64_t n,
                                                         const uint16_t* __restrict__ wbf,
                                                         const float* __restrict__ bias,
-                                                        uint16_t* __restrict__ out) {
+                                                        uint16_t* __restrict__ out,
+                                                        uint8_t* __restrict__ qe) {
   __shared__ float d_s[2 * kC1T + 8];
   __shared__ __align__(16) float w_s[kCnnK][kCnnC];
   __shared__ __align__(16) float b_s[kCnnC];
@@ -273,6 +275,9 @@ __global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict
       acc = __dp4a((int)w.z, 0x01010101, acc);
       acc = __dp4a((int)w.w, 0x01010101, acc);
       v = 0.25f * (float)acc;
+      // the E4M3 copy of the levels this CTA owns (d indices 2 P0 ..)
+      if (qe && i >= 4 && i < 2 * kC1T + 4)
+        *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
     }
     d_s[i] = v;
   }
@@ -826,11 +831,11 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             uint32_t* d_status, cudaStream_t st) {
+                             uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
   const int Ld = (int)(n / kCnnDec);
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
   k_conv1_inf<<<dim3((Ld / 2 + kC1T - 1) / kC1T, nsig), kThreads, 0, st>>>(
-      q, n, wbf + cnn_woff(0), params + cnn_boff(0), act[0]);
+      q, n, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qe);
   k_eo_pad<<<(nsig + 63) / 64, 256, 0, st>>>(act[0], Ld / 2, nsig);
   TDE_COUNT_LAUNCH(2);
   cudaError_t e = cudaGetLastError();

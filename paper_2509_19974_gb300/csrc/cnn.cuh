@@ -38,11 +38,12 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
                              const float* params, cudaStream_t st);
 // Inference forward (decimate + 4 layers) with BF16 activations between
 // layers: act[l] holds layer l's output, nsig x cnn_eo_elems((n/16) >> (l+1))
-// BF16 in the layout above; feat receives the FP32 features [nsig][32][n/256].
-// n a multiple of 2048.
+// BF16 in the layout above; feat receives the FP32 features [nsig][32][n/256];
+// qe (nullable, nsig x n bytes) the levels as E4M3 bytes.  n a multiple of
+// 2048.
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             uint32_t* d_status, cudaStream_t st);
+                             uint8_t* qe, uint32_t* d_status, cudaStream_t st);
 // Inference activations between conv layers: a layer's input of length L
 // is, per signal, 8 arrays (position parity x 8-channel chunk, parity-major)
 // of cnn_eo_rows(L) rows of 8 BF16 channels; row r holds position 2r - 4

@@ -11,6 +11,23 @@
 #define TDE_ST_TIMEOUT 2u    // a bounded wait gave up
 #define TDE_ST_INTERNAL 4u   // a kernel's own bounds check refused an access
 
+// ------------------------------------------------------------ E4M3 levels
+#ifdef __CUDACC__
+// Four int8 levels in [-7, 7] -> four E4M3 bytes (exact): magnitudes through
+// a byte-permute table, sign bits copied.
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t w) {
+  const uint32_t mag = __vabs4(w);
+  const uint32_t sel = (mag & 0xFu) | ((mag >> 4) & 0xF0u) | ((mag >> 8) & 0xF00u) |
+                       ((mag >> 12) & 0xF000u);
+  // bytes of {hi:lo}: 0 -> 0x00, 1 -> 0x38, 2 -> 0x40, 3 -> 0x44, 4 -> 0x48,
+  // 5 -> 0x4A, 6 -> 0x4C, 7 -> 0x4E
+  return __byte_perm(0x44403800u, 0x4E4C4A48u, sel) | (w & 0x80808080u);
+}
+__device__ __forceinline__ uint4 e4m3x16(uint4 v) {
+  return make_uint4(e4m3x4(v.x), e4m3x4(v.y), e4m3x4(v.z), e4m3x4(v.w));
+}
+#endif
+
 // ---------------------------------------------------------------- quantize
 // One signal to quantize: n floats at x -> n int8 at q.
 struct QSig {

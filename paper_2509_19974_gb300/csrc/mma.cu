@@ -52,6 +52,8 @@
 // byte offset is the K-direction core-matrix stride of the no-swizzle K-major
 // layout, overlapping core matrices read correctly, and a B descriptor that
 // starts off the 1024-byte swizzle pattern must keep base offset 0.
+#include <cudaTypedefs.h>
+
 #include "cnn.cuh"
 #include "common.cuh"
 #include "mma.cuh"
@@ -254,20 +256,6 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
-}
-
-// Four int8 levels in [-7, 7] -> four E4M3 bytes (exact): magnitudes through
-// a byte-permute table, sign bits copied.
-__device__ __forceinline__ uint32_t e4m3x4(uint32_t w) {
-  const uint32_t mag = __vabs4(w);
-  const uint32_t sel = (mag & 0xFu) | ((mag >> 4) & 0xF0u) | ((mag >> 8) & 0xF00u) |
-                       ((mag >> 12) & 0xF000u);
-  // bytes of {hi:lo}: 0 -> 0x00, 1 -> 0x38, 2 -> 0x40, 3 -> 0x44, 4 -> 0x48,
-  // 5 -> 0x4A, 6 -> 0x4C, 7 -> 0x4E
-  return __byte_perm(0x44403800u, 0x4E4C4A48u, sel) | (w & 0x80808080u);
-}
-__device__ __forceinline__ uint4 e4m3x16(uint4 v) {
-  return make_uint4(e4m3x4(v.x), e4m3x4(v.y), e4m3x4(v.z), e4m3x4(v.w));
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
@@ -517,69 +505,119 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
 // tau = T_w + 128 j + 127 - m (j = 0..7, T_w = its first lag rounded down to
 // a multiple of 128), 1024 lags of which the window's <= 257 are kept.  A is
 // the same E4M3 Hankel slot ring; B needs no per-chunk copies: each window's
-// y segment is staged once per item as 128-byte E4M3 rows
+// y segment is one array of 128-byte E4M3 rows
 //   Y_w[r] = y[ks + T_w + 128 r .. + 127],
 // and because ks and T_w are multiples of 128 the 8 B rows of window w for K
 // chunk c are rows c .. c + 7 of Y_w -- the same rows for every window, one
 // core-matrix group per window.  The windows' arrays sit at a fixed stride, so
 // one descriptor (stride byte offset = that stride) gives an N = 64 tile:
-// 8 windows x 8 columns.  Producers and the issuer synchronize once per
-// super-chunk of 2 chunks (8 MMAs): super-chunk s writes logical slots
-// [32 s + 14, 32 s + 46) and reads [32 s, 32 s + 46), so on a ring of 128 its
-// slots were last read by super-chunk s - 3.  The (pair, K segment) units of
-// the batch, pair-major, are dealt to the CTAs as contiguous runs of equal
-// length (so no CTA runs more than one unit beyond the average); a CTA walks
-// its run (staging each segment, then its MMAs), accumulating per pair in
-// tensor memory, and at each pair's end stores the sums (the run held all of
-// the pair's segments) or adds them with integer atomics (the pair is split
-// between CTAs).
+// 8 windows x 8 columns.
+//
+// The inputs are the levels as E4M3 bytes, so a segment's operands arrive by
+// TMA: per window one 3-D tiled load (signal, 128-byte row, byte) of 40 rows
+// with the 128-byte swizzle the B descriptor expects, zero-filled outside the
+// signal, and the x segment as two loads of 144 16-byte rows.  Roles:
+//   warp 3, lane 0: TMA, two segment buffers ahead of the MMAs;
+//   warps 1-2:      Hankel slot rows, one super-chunk (2 chunks) at a time;
+//   warp 0:         MMAs (lane 0), two accumulators of 64 TMEM columns;
+//   warps 4-7:      epilogue of each finished pair (stores, or integer
+//                   atomics when the pair is split between CTAs).
+// Slot ring positions run on across segments: super-chunk S (counted over
+// the CTA's run) reads [32 S, 32 S + 46) and writes [32 S + 14, 32 S + 46) --
+// or all of [32 S, 32 S + 46) when it starts a segment -- so on a ring of 128
+// its writes wait for the commit of super-chunk S - 3 (S - 1 at a segment
+// start).  The (pair, K segment) units of the batch, pair-major, are dealt to
+// the CTAs as contiguous runs of equal length.  Every wait is bounded; a role
+// whose wait gives up raises the CTA's abort flag and leaves its loop, the
+// others leave theirs at their next wait, and the CTA flags TDE_ST_TIMEOUT,
+// waits (bounded) for its copies and MMAs in flight and frees its tensor
+// memory.
 
 constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
 constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
 constexpr int kWinN = kWinW * kWinJ;             // MMA N = 64
-constexpr int kWinKs = 4096;                     // max samples of the sum per item
+constexpr int kWinKs = 4096;                     // max samples of the sum per segment
 constexpr int kWinRows = kWinKs / kKc8 + kWinJ;  // rows per window (40)
 constexpr int kWinArr = kWinRows * 128;          // bytes per window array, = the SBO
-constexpr int kWinXBytes = kWinKs + 288;
+constexpr int kWinYBytes = kWinW * kWinArr;      // one segment's window rows
+constexpr int kWinXBox = 144;                    // 16-byte rows per x load (two loads)
+constexpr int kWinXBytes = 2 * kWinXBox * 16;    // x bytes staged per segment
+constexpr int kWinXStride = kWinXBytes;          // x buffer stride
+constexpr int kWinTx = kWinYBytes + kWinXBytes;  // TMA bytes per segment
 constexpr int kWinSC = 2;                        // chunks per super-chunk
 constexpr int kWinRing = 128, kWinMirror = 32;
 constexpr int kWinSlotBytes = (kWinRing + kWinMirror) * 128;
-constexpr int kWinSmemUsed = kWinW * kWinArr + kWinSlotBytes + kWinXBytes + (2 * kNB + 1) * 8 + 16;
-constexpr int kWinSmemBytes = kWinSmemUsed + 1024;
-static_assert(kWinArr % 1024 == 0, "windows' arrays keep the 1024-byte swizzle pattern");
-static_assert(kWinXBytes % 16 == 0, "staging");
-static_assert(3 * (kWinSmemBytes + 1024) <= 228 * 1024, "three CTAs per SM");
+constexpr int kWinOffSlots = 2 * kWinYBytes;
+constexpr int kWinOffX = kWinOffSlots + kWinSlotBytes;
+constexpr int kWinOffBar = kWinOffX + 2 * kWinXStride;
+constexpr int kWinNBar = 2 + 2 + kNB + kNB + 2 + 2;
+constexpr int kWinSmemBytes = kWinOffBar + kWinNBar * 8 + 32 + 1024;
+static_assert(kWinArr % 1024 == 0 && kWinYBytes % 1024 == 0, "window arrays keep the swizzle pattern");
+static_assert((16 * kWinXBox) % 128 == 0 && kWinXStride % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(kWinKs + 288 <= kWinXBytes, "x segment");
+static_assert(2 * (kWinSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
-__global__ void __launch_bounds__(kThreads, 3)
-    k_xcorr_mma_win(const int8_t* __restrict__ q, int64_t n, int npairs, const WinJob* __restrict__ jobs,
-                    int nseg, int seg, uint32_t* __restrict__ status) {
+// 3-D tiled TMA load (coordinates innermost first), completing on bar.
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_win(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_xcorr_mma_win(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap xmap,
+                    int64_t n, int npairs, const WinJob* __restrict__ jobs, int nseg, int seg,
+                    uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t ya = base;                                 // window w at ya + w * kWinArr
-  const uint32_t slots = ya + kWinW * kWinArr;
-  const uint32_t xs = slots + kWinSlotBytes;
-  const uint32_t full_bar = xs + kWinXBytes;
+  const uint32_t ybuf = base;  // segment buffer b at ybuf + b * kWinYBytes, window w at + w * kWinArr
+  const uint32_t slots = base + kWinOffSlots;
+  const uint32_t xbuf = base + kWinOffX;  // segment buffer b at xbuf + b * kWinXStride
+  const uint32_t seg_full = base + kWinOffBar;
+  const uint32_t seg_empty = seg_full + 16;
+  const uint32_t full_bar = seg_empty + 16;
   const uint32_t cmt_bar = full_bar + 8 * kNB;
-  const uint32_t done_bar = cmt_bar + 8 * kNB;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
-  __shared__ int64_t sT[kWinW], sLo[kWinW], sHi[kWinW];  // per window: T_w, lag range
-  __shared__ int32_t* sC[kWinW];
+  const uint32_t acc_full = cmt_bar + 8 * kNB;
+  const uint32_t acc_empty = acc_full + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (acc_empty + 16 - raw));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* loaded_sh = reinterpret_cast<int*>(tmem_slot + 2);     // segments whose loads were issued
+  int* committed_sh = reinterpret_cast<int*>(tmem_slot + 3);  // super-chunks whose MMAs were committed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t kmax = (n + 127 + 127) / 128 * 128;
+  const int64_t units = (int64_t)npairs * nseg;
+  const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
+  const int G = (int)(u1 - u0);  // segments of this CTA's run
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(kWinN)
+                 "r"(2 * kWinN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 32) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(seg_full + 8 * i, 1);
+      mbar_init(seg_empty + 8 * i, 1);
+      mbar_init(acc_full + 8 * i, 1);
+      mbar_init(acc_empty + 8 * i, 128);
+    }
     for (int i = 0; i < kNB; ++i) {
       mbar_init(full_bar + 8 * i, kProducers);
       mbar_init(cmt_bar + 8 * i, 1);
     }
-    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    *loaded_sh = 0;
+    *committed_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -587,188 +625,206 @@ __global__ void __launch_bounds__(kThreads, 3)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int64_t sc0 = 0;     // super-chunks issued by this CTA so far (barrier phases)
-  uint32_t dphase = 0;  // completions of done_bar so far (one per segment)
-  bool ok = true;
-  const int64_t kmax = (n + 127 + 127) / 128 * 128;
-  // This CTA's run of (pair, segment) units [u, u1), pair-major; one pass
-  // of the loop per pair the run touches.
-  const int64_t units = (int64_t)npairs * nseg;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
-  for (int64_t u = units * blockIdx.x / gridDim.x; u < u1 && ok;) {
-    const int p = (int)(u / nseg);
-    const int sg_lo = (int)(u - (int64_t)p * nseg);
-    const int sg_hi = u1 - u < nseg - sg_lo ? sg_lo + (int)(u1 - u) : nseg;
-    const bool whole = sg_lo == 0 && sg_hi == nseg;  // no other CTA adds to this pair
-    u += sg_hi - sg_lo;
-    const int8_t* qx = q + (int64_t)(2 * p) * n;
-    const int8_t* qy = q + (int64_t)(2 * p + 1) * n;
-    const WinJob* J = jobs + (int64_t)p * kWinW;
-    if (threadIdx.x < kWinW) {
-      const WinJob jw = J[threadIdx.x];
-      sT[threadIdx.x] = fdiv(jw.lag_lo, 128) * 128;
-      sLo[threadIdx.x] = jw.lag_lo;
-      sHi[threadIdx.x] = jw.lag_hi;
-      sC[threadIdx.x] = jw.c;
+  // K chunks of segment g of the run
+  auto seg_of = [&](int g, int* p, int64_t* ks, int* nchunks) {
+    const int64_t u = u0 + g;
+    *p = (int)(u / nseg);
+    *ks = (u - (int64_t)*p * nseg) * seg;
+    const int64_t ke = *ks + seg < kmax ? *ks + seg : kmax;
+    *nchunks = (int)((ke - *ks) / kKc8);
+  };
+
+  if (warp == 3) {
+    // ---- TMA: segment g into buffer g & 1 once segment g - 2's MMAs are done
+    if (lane == 0) {
+      for (int g = 0; g < G && !*abort_flag; ++g) {
+        const int b = g & 1;
+        if (g >= 2 && !mbar_wait_sleep(seg_empty + 8 * b, (uint32_t)(((g - 2) >> 1) & 1))) {
+          *abort_flag = 1;
+          break;
+        }
+        int p, nch;
+        int64_t ks;
+        seg_of(g, &p, &ks, &nch);
+        if (nch <= 0 || nch * kKc8 > kWinKs || (ks & 127) != 0) {  // not the host's segmentation
+          atomicOr(status, TDE_ST_INTERNAL);
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t fb = seg_full + 8 * b;
+        mbar_expect_tx_win(fb, (uint32_t)kWinTx);
+        for (int w = 0; w < kWinW; ++w) {
+          const int64_t T = fdiv(jobs[(int64_t)p * kWinW + w].lag_lo, 128) * 128;
+          tma_load3(ybuf + (uint32_t)(b * kWinYBytes + w * kWinArr), &ymap, 0, (int)((ks + T) / 128),
+                    2 * p + 1, fb);
+        }
+        const int xr = (int)fdiv(ks - 127, 16);
+        const uint32_t xb = xbuf + (uint32_t)(b * kWinXStride);
+        tma_load3(xb, &xmap, 0, xr, 2 * p, fb);
+        tma_load3(xb + 16u * kWinXBox, &xmap, 0, xr + kWinXBox, 2 * p, fb);
+        *loaded_sh = g + 1;
+      }
     }
-    if (warp < 4) {
-      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-      tmem_zero32(tmem + lane_base);
-      tmem_zero32(tmem + lane_base + 32u);
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    for (int sgi = sg_lo; sgi < sg_hi; ++sgi) {
-      const int64_t ks = (int64_t)sgi * seg;
-      const int64_t ke = ks + seg < kmax ? ks + seg : kmax;
-      const int nchunks = (int)((ke - ks) / kKc8);
-      if (nchunks <= 0) break;                                 // uniform
-      if (ke - ks > kWinKs || (ks & 127) != 0) {               // not for the host's segmentation
-        if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
+  } else if (warp == 1 || warp == 2) {
+    // ---- Hankel slots of x, one super-chunk at a time
+    const int t = threadIdx.x - 32;
+    int64_t S = 0;
+    bool ok = true;
+    for (int g = 0; g < G && ok && !*abort_flag; ++g) {
+      const int b = g & 1;
+      if (!mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1))) {
+        ok = false;
         break;
       }
-      const int64_t xs_base = fdiv(ks - 127, 16) * 16;
-      const uint32_t xoff = (uint32_t)(ks - 127 - xs_base);
-      const int nrows = nchunks + kWinJ - 1;  // rows of each window array this segment reads
-      // staging: x segment, then every window's rows (int8 -> E4M3, swizzled)
-      {
-        const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
-        const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
-        constexpr int kXV = kWinXBytes / 16;
-        const int per_w = nrows * 8;  // (row, 16-byte piece) per window
-        const int total = kXV + kWinW * per_w;
-        for (int b0 = threadIdx.x; b0 < total; b0 += 8 * kThreads) {
-          uint4 v[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int idx = b0 + k * kThreads;
-            if (idx < kXV) {
-              v[k] = load16(qx, xs_base + 16 * idx, n, alx);
-            } else if (idx < total) {
-              const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
-              v[k] = load16(qy, ks + sT[w] + 128 * (r8 >> 3) + 16 * (r8 & 7), n, aly);
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int idx = b0 + k * kThreads;
-            if (idx >= total) continue;
-            const uint4 e = e4m3x16(v[k]);
-            uint32_t a;
-            if (idx < kXV) {
-              a = xs + 16u * (uint32_t)idx;
-            } else {
-              const int w = (idx - kXV) / per_w, r8 = (idx - kXV) - w * per_w;
-              const uint32_t row_addr = ya + (uint32_t)(w * kWinArr + 128 * (r8 >> 3));
-              a = row_addr + 16u * ((uint32_t)(r8 & 7) ^ ((row_addr >> 7) & 7u));
-            }
-            st_shared_v4(a, e.x, e.y, e.z, e.w);
-          }
+      int p, nch;
+      int64_t ks;
+      seg_of(g, &p, &ks, &nch);
+      const uint32_t xs = xbuf + (uint32_t)(b * kWinXStride);
+      const uint32_t xoff = (uint32_t)(ks - 127 - fdiv(ks - 127, 16) * 16);
+      const int nsc = (nch + kWinSC - 1) / kWinSC;
+      const int64_t S0 = S;  // the segment's first super-chunk: ring base 32 S0
+      for (int sc = 0; sc < nsc; ++sc, ++S) {
+        const int64_t prev = sc == 0 ? S - 1 : S - 3;
+        if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
+          ok = false;
+          break;
         }
+        const int c_first = sc * kWinSC;
+        const int c_last = c_first + kWinSC - 1 < nch - 1 ? c_first + kWinSC - 1 : nch - 1;
+        const int o_first = sc == 0 ? 0 : 128 * c_first + 112;
+        const int o_end = 128 * c_last + 240;
+        for (int o = o_first + t; o < o_end; o += kProducers) {
+          const uint32_t pa = xs + xoff + (uint32_t)o;
+          const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
+          const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
+          const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
+          const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
+          const int ps = (int)((32 * S0 + (o >> 3)) % kWinRing);
+          const uint32_t a = slots + 128u * ps + 16u * (uint32_t)(o & 7);
+          st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+          if (ps < kWinMirror)
+            st_shared_v4(a + 128u * kWinRing, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
+                         (uint32_t)(hi >> 32));
+        }
+        fence_proxy_async();
+        mbar_arrive(full_bar + 8 * (uint32_t)(S % kNB));
       }
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-
-      const int nsc = (nchunks + kWinSC - 1) / kWinSC;
-      if (warp == 1 || warp == 2) {
-        // Hankel slots of x (as in k_xcorr_mma8), one super-chunk at a time
-        const int t = threadIdx.x - 32;
-        for (int sc = 0; sc < nsc; ++sc) {
-          const int64_t g = sc0 + sc;
-          const int64_t prev = g - 3;
-          if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
-            ok = false;
-            break;
-          }
-          const int c_first = sc * kWinSC;
-          const int c_last = c_first + kWinSC - 1 < nchunks - 1 ? c_first + kWinSC - 1 : nchunks - 1;
-          const int o_first = sc == 0 ? 0 : 128 * c_first + 112;
-          const int o_end = 128 * c_last + 240;
-          for (int o = o_first + t; o < o_end; o += kProducers) {
-            const uint32_t pa = xs + xoff + (uint32_t)o;
-            const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-            const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
-            const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
-            const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
-            const int e = o >> 3, r = o & 7;
-            const int ps = e % kWinRing;
-            const uint32_t a = slots + 128u * ps + 16u * r;
-            st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-            if (ps < kWinMirror)
-              st_shared_v4(a + 128u * kWinRing, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
-                           (uint32_t)(hi >> 32));
-          }
-          fence_proxy_async();
-          mbar_arrive(full_bar + 8 * (uint32_t)(g % kNB));
-        }
-      } else if (warp == 0) {
-        const uint32_t idesc = idesc8_for(kWinN);
-        for (int sc = 0; sc < nsc; ++sc) {
-          const int64_t g = sc0 + sc;
-          ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(g % kNB), (uint32_t)((g / kNB) & 1)));
-          if (!ok) break;
-          tc_fence_after();
-          if (lane == 0) {
-            const int c_end = (sc + 1) * kWinSC < nchunks ? (sc + 1) * kWinSC : nchunks;
-            for (int c = sc * kWinSC; c < c_end; ++c) {
-              const uint32_t a_start = slots + 128u * (uint32_t)((16 * c) % kWinRing);
-              const uint32_t b_start = ya + 128u * (uint32_t)c;
+    }
+    if (!ok) *abort_flag = 1;
+  } else if (warp == 0) {
+    // ---- MMAs
+    const uint32_t idesc = idesc8_for(kWinN);
+    int64_t S = 0;
+    int pp = -1, cur_p = -1;
+    bool ok = true, first = false;
+    for (int g = 0; g < G && ok && !*abort_flag; ++g) {
+      int p, nch;
+      int64_t ks;
+      seg_of(g, &p, &ks, &nch);
+      if (p != cur_p) {  // a new pair: its accumulator must have been read out
+        cur_p = p;
+        ++pp;
+        first = true;
+        if (pp >= 2)
+          ok = __all_sync(0xffffffffu, mbar_wait_sleep(acc_empty + 8 * (uint32_t)(pp & 1),
+                                                       (uint32_t)(((pp - 2) >> 1) & 1)));
+        if (!ok) break;
+      }
+      const int b = g & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1)));
+      if (!ok) break;
+      const uint32_t d = tmem + (uint32_t)((pp & 1) * kWinN);
+      const uint32_t yb = ybuf + (uint32_t)(b * kWinYBytes);
+      const int nsc = (nch + kWinSC - 1) / kWinSC;
+      for (int sc = 0; sc < nsc; ++sc, ++S) {
+        ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(S % kNB), (uint32_t)((S / kNB) & 1)));
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const int c_end = (sc + 1) * kWinSC < nch ? (sc + 1) * kWinSC : nch;
+          for (int c = sc * kWinSC; c < c_end; ++c) {
+            const uint32_t a_start = slots + 128u * (uint32_t)((32 * (S - sc) + 16 * c) % kWinRing);
+            const uint32_t b_start = yb + 128u * (uint32_t)c;
 #pragma unroll
-              for (int s2 = 0; s2 < 4; ++s2)
-                mma_e4m3(tmem, sdesc(a_start + 512u * s2, 256, 128, 0, 0),
-                         sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, 1u);
+            for (int s2 = 0; s2 < 4; ++s2) {
+              mma_e4m3(d, sdesc(a_start + 512u * s2, 256, 128, 0, 0),
+                       sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, first ? 0u : 1u);
+              first = false;
             }
-            mma_commit(cmt_bar + 8 * (uint32_t)(g % kNB));
           }
-          __syncwarp();
+          mma_commit(cmt_bar + 8 * (uint32_t)(S % kNB));
+          *committed_sh = (int)(S + 1);
         }
-        if (lane == 0) mma_commit(done_bar);  // this segment's MMAs
+        first = __shfl_sync(0xffffffffu, first ? 1 : 0, 0) != 0;
         __syncwarp();
       }
-      // the segment's MMAs must finish before its staging is overwritten
-      bool done = true;
-      if (warp == 3) done = mbar_wait_sleep(done_bar, dphase & 1u);
-      ++dphase;
-      ok = __syncthreads_and(ok && done);
-      sc0 += nsc;
       if (!ok) break;
-    }
-    if (!ok) {
-      if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
-      break;
-    }
-    {
-      // warp w: TMEM lanes 32 (w % 4) .., windows 4 (w / 4) .. + 3 (columns 32 (w / 4) ..)
-      tc_fence_after();
-      const int qd = warp & 3, colh = warp >> 2;
-      const int m = 32 * qd + lane;
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * colh), v);
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const int w = 4 * colh + (jj >> 3), j = jj & 7;
-        const int64_t lo = sLo[w], hi = sHi[w];
-        const int64_t tau = sT[w] + 128 * j + 127 - m;
-        if (tau < lo || tau > hi) continue;
-        const int val = __float2int_rn(__uint_as_float(v[jj]));
-        if (whole)
-          sC[w][tau - lo] = val;
-        else if (val != 0)
-          atomicAdd(sC[w] + (tau - lo), val);
+      if (lane == 0) {
+        mma_commit(seg_empty + 8 * b);  // the segment's buffers are free once its MMAs are done
+        int pn = -1, nn;
+        int64_t kn;
+        if (g + 1 < G) seg_of(g + 1, &pn, &kn, &nn);
+        if (pn != p) mma_commit(acc_full + 8 * (uint32_t)(pp & 1));  // the pair's sum is complete
       }
+      __syncwarp();
     }
-    tc_fence_before();
-    __syncthreads();
+    if (!ok) *abort_flag = 1;
+  } else if (warp >= 4) {
+    // ---- epilogue: TMEM lanes 32 (warp & 3) .., all 64 columns
+    const int qd = warp & 3;
+    const int m = 32 * qd + lane;
+    int pp = 0;
+    for (int64_t u = u0; u < u1; ++pp) {
+      const int p = (int)(u / nseg);
+      const int sg_lo = (int)(u - (int64_t)p * nseg);
+      const int sg_hi = u1 - u < nseg - sg_lo ? sg_lo + (int)(u1 - u) : nseg;
+      const bool whole = sg_lo == 0 && sg_hi == nseg;  // no other CTA adds to this pair
+      u += sg_hi - sg_lo;
+      if (*abort_flag) break;
+      if (!mbar_wait_sleep(acc_full + 8 * (uint32_t)(pp & 1), (uint32_t)((pp >> 1) & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      uint32_t v[32];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((pp & 1) * kWinN + 32 * half), v);
+#pragma unroll
+        for (int wq = 0; wq < 4; ++wq) {
+          const WinJob jw = jobs[(int64_t)p * kWinW + 4 * half + wq];
+          const int64_t T = fdiv(jw.lag_lo, 128) * 128;
+#pragma unroll
+          for (int j = 0; j < kWinJ; ++j) {
+            const int64_t tau = T + 128 * j + 127 - m;
+            if (tau < jw.lag_lo || tau > jw.lag_hi) continue;
+            const int val = __float2int_rn(__uint_as_float(v[8 * wq + j]));
+            if (whole)
+              jw.c[tau - jw.lag_lo] = val;
+            else if (val != 0)
+              atomicAdd(jw.c + (tau - jw.lag_lo), val);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acc_empty + 8 * (uint32_t)(pp & 1));
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) {
+    atomicOr(status, TDE_ST_TIMEOUT);
+    // bounded waits for the copies and MMAs still in flight
+    const int L = *loaded_sh;
+    for (int g = L - 2 < 0 ? 0 : L - 2; g < L; ++g)
+      mbar_wait_sleep(seg_full + 8 * (uint32_t)(g & 1), (uint32_t)((g >> 1) & 1));
+    const int C = *committed_sh;
+    if (C > 0) mbar_wait_sleep(cmt_bar + 8 * (uint32_t)((C - 1) % kNB), (uint32_t)(((C - 1) / kNB) & 1));
+  }
+  __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWinN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWinN)
                  : "memory");
   }
 }
@@ -1064,24 +1120,89 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, const WinJob* d_jobs,
-                                     uint32_t* d_status, cudaStream_t st) {
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D byte tensor (signal, row of `row` bytes, byte) over S signals of
+// stride bytes each; box = box_rows rows of one signal.
+bool tmap_bytes3(CUtensorMap* m, const void* base, int64_t stride, int S, int row, int box_rows,
+                 bool swizzle128) {
+  auto enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)row, (cuuint64_t)(stride / row), (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)row, (cuuint64_t)stride};
+  const cuuint32_t box[3] = {(cuuint32_t)row, (cuuint32_t)box_rows, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs,
+                                     const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
+  if (n_pad % 128 != 0 || n_pad < n || (reinterpret_cast<uintptr_t>(d_qe) & 15) != 0)
+    return cudaErrorInvalidValue;
   // K range [0, n + 127) rounded up to 128; segments are multiples of 128
   // (so that each segment's windows start on a 128-sample row)
   const int64_t kmax = ceil_div64(n + 127, 128) * 128;
   const int nseg = (int)ceil_div64(kmax, kWinKs);
   const int seg = (int)(ceil_div64(ceil_div64(kmax, nseg), 128) * 128);
+  CUtensorMap ymap, xmap;
+  if (!tmap_bytes3(&ymap, d_qe, n_pad, 2 * npairs, 128, kWinRows, true) ||
+      !tmap_bytes3(&xmap, d_qe, n_pad, 2 * npairs, 16, kWinXBox, false))
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kWinSmemBytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // three CTAs per SM, each with an equal run of the (pair, segment) units
+  // two CTAs per SM, each with an equal run of the (pair, segment) units
   const int64_t units = (int64_t)npairs * nseg;
-  const int grid = (int)(units < 3 * (int64_t)sms ? units : 3 * (int64_t)sms);
-  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(d_q, n, npairs, d_jobs, nseg, seg, d_status);
+  const int grid = (int)(units < 2 * (int64_t)sms ? units : 2 * (int64_t)sms);
+  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(ymap, xmap, n, npairs, d_jobs, nseg, seg,
+                                                         d_status);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+// Levels -> E4M3 bytes with a padded signal stride (zeros in [n, n_pad)).
+__global__ void k_to_e4m3(const int8_t* __restrict__ q, int64_t n, int64_t n_pad, int nsig,
+                          uint8_t* __restrict__ qe) {
+  const int64_t total = (int64_t)nsig * n_pad;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < total;
+       i += (int64_t)gridDim.x * blockDim.x * 4) {
+    const int64_t s = i / n_pad, j = i - s * n_pad;  // n_pad % 4 == 0: one signal per word
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (j + k < n) w |= (uint32_t)(uint8_t)q[s * n + j + k] << (8 * k);
+    *reinterpret_cast<uint32_t*>(qe + i) = e4m3x4(w);
+  }
+}
+
+cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qe,
+                           cudaStream_t st) {
+  if (nsig <= 0) return cudaSuccess;
+  if (n_pad % 4 != 0 || n_pad < n) return cudaErrorInvalidValue;
+  const int64_t words = (int64_t)nsig * n_pad / 4;
+  const int64_t grid = words / 256 + 1 < 4096 ? words / 256 + 1 : 4096;
+  k_to_e4m3<<<(unsigned)grid, 256, 0, st>>>(d_q, n, n_pad, nsig, d_qe);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -41,10 +41,15 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
                              int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
                              const int* d_nitems = nullptr);
 
-// The learned proposal's windows on the tensor cores: pair p is
-// x = d_q + 2 p n, y = d_q + (2 p + 1) n (n int8 each, bits <= 2 or 4); its 8
-// windows d_jobs[8 p + w] (lag_lo, lag_hi <= lag_lo + 256, c) receive
-// c[i] += sum_n x[n] y[n + lag_lo + i] for lag_lo + i <= lag_hi (other entries
-// are not written): the c buffers must be zeroed first.
-cudaError_t launch_xcorr_mma_windows(const int8_t* d_q, int64_t n, int npairs, const WinJob* d_jobs,
-                                     uint32_t* d_status, cudaStream_t st);
+// The learned proposal's windows on the tensor cores: the levels as E4M3
+// bytes d_qe, signal stride n_pad (a multiple of 128, zeros in [n, n_pad),
+// 16-byte aligned); pair p is x = signal 2 p, y = signal 2 p + 1 (n levels
+// each, |level| <= 7); its 8 windows d_jobs[8 p + w] (lag_lo,
+// lag_hi <= lag_lo + 256, c) receive c[i] += sum_n x[n] y[n + lag_lo + i] for
+// lag_lo + i <= lag_hi (other entries are not written): the c buffers must be
+// zeroed first.
+cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs,
+                                     const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
+// Levels [nsig][n] -> E4M3 bytes [nsig][n_pad] (zeros past n); n_pad % 4 == 0.
+cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qe,
+                           cudaStream_t st);
