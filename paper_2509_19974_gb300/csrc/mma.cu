@@ -514,19 +514,28 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
 // 8 windows x 8 columns.
 //
 // The inputs are the levels as E4M3 bytes, so a segment's operands arrive by
-// TMA: per window one 3-D tiled load (signal, 128-byte row, byte) of 40 rows
+// TMA: per window one 3-D tiled load (signal, 128-byte row, byte) of 32 rows
 // with the 128-byte swizzle the B descriptor expects, zero-filled outside the
-// signal, and the x segment as two loads of 144 16-byte rows.  Roles:
+// signal, and the x segment as two loads of 112 16-byte rows.  Roles:
 //   warp 3, lane 0: TMA, two segment buffers ahead of the MMAs;
 //   warps 1-2:      Hankel slot rows, one super-chunk (2 chunks) at a time;
-//   warp 0:         MMAs (lane 0), two accumulators of 64 TMEM columns;
+//   warps 0 and 8:  MMAs (lane 0), each into its own accumulator set (K steps
+//                   0, 2 and 1, 3 of every chunk; at N = 64 one thread's issue
+//                   loop, not the tensor pipe, bounds the MMA rate), sets
+//                   double-buffered across pairs;
 //   warps 4-7:      epilogue of each finished pair (stores, or integer
 //                   atomics when the pair is split between CTAs).
 // Slot ring positions run on across segments: super-chunk S (counted over
-// the CTA's run) reads [32 S, 32 S + 46) and writes [32 S + 14, 32 S + 46) --
-// or all of [32 S, 32 S + 46) when it starts a segment -- so on a ring of 128
-// its writes wait for the commit of super-chunk S - 3 (S - 1 at a segment
-// start).  The (pair, K segment) units of the batch, pair-major, are dealt to
+// the CTA's run, in segment g of the run) has origin R(S) = 32 (S + g) --
+// each segment starts one 32-slot block further on -- reads ring positions
+// [R, R + 46) and writes [R + 14, R + 46), or all of [R, R + 46) when it
+// starts a segment.  On a ring of 256 a super-chunk S' can alias those writes
+// only if R(S) - R(S') > 210, so the producers wait for the newest such S'
+// (at most 7 back): up to 6 super-chunks of MMAs stay in flight, and no
+// segment start waits for the previous segment's MMAs.  Eight producer lanes
+// write the 8 rows of 4 consecutive slots (128-byte runs per store): a lane
+// loads six 8-byte words, realigns them once by its byte offset and stores
+// aligned word pairs.  The (pair, K segment) units of the batch, pair-major, are dealt to
 // the CTAs as contiguous runs of equal length.  Every wait is bounded; a role
 // whose wait gives up raises the CTA's abort flag and leaves its loop, the
 // others leave theirs at their next wait, and the CTA flags TDE_ST_TIMEOUT,
@@ -536,25 +545,33 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
 constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
 constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
 constexpr int kWinN = kWinW * kWinJ;             // MMA N = 64
-constexpr int kWinKs = 4096;                     // max samples of the sum per segment
-constexpr int kWinRows = kWinKs / kKc8 + kWinJ;  // rows per window (40)
+constexpr int kWinKs = 3072;                     // max samples of the sum per segment
+constexpr int kWinRows = kWinKs / kKc8 + kWinJ;  // rows per window (32)
 constexpr int kWinArr = kWinRows * 128;          // bytes per window array, = the SBO
 constexpr int kWinYBytes = kWinW * kWinArr;      // one segment's window rows
-constexpr int kWinXBox = 144;                    // 16-byte rows per x load (two loads)
+constexpr int kWinXBox = 112;                    // 16-byte rows per x load (two loads)
 constexpr int kWinXBytes = 2 * kWinXBox * 16;    // x bytes staged per segment
 constexpr int kWinXStride = kWinXBytes;          // x buffer stride
 constexpr int kWinTx = kWinYBytes + kWinXBytes;  // TMA bytes per segment
 constexpr int kWinSC = 2;                        // chunks per super-chunk
-constexpr int kWinRing = 128, kWinMirror = 32;
+constexpr int kWinRing = 256, kWinMirror = 32;
 constexpr int kWinSlotBytes = (kWinRing + kWinMirror) * 128;
 constexpr int kWinOffSlots = 2 * kWinYBytes;
 constexpr int kWinOffX = kWinOffSlots + kWinSlotBytes;
 constexpr int kWinOffBar = kWinOffX + 2 * kWinXStride;
 constexpr int kWinNBar = 2 + 2 + kNB + kNB + 2 + 2;
+// tensor memory: 2 pair buffers x 2 accumulator sets x 64 columns (the K
+// steps of a chunk alternate between the sets, so consecutive MMAs do not
+// wait on one another's accumulator; the epilogue adds the sets)
+constexpr int kWinCols = 4 * kWinN;
+// warps: 0 and kWinIssuerB issue MMAs, 1-2 write slots, 3 (lane 0) runs the
+// TMA, 4-7 read the accumulators out
+constexpr int kWinIssuerB = 8;
+constexpr int kWinThreads = 32 * (kWinIssuerB + 1);
 constexpr int kWinSmemBytes = kWinOffBar + kWinNBar * 8 + 32 + 1024;
 static_assert(kWinArr % 1024 == 0 && kWinYBytes % 1024 == 0, "window arrays keep the swizzle pattern");
 static_assert((16 * kWinXBox) % 128 == 0 && kWinXStride % 128 == 0, "TMA destinations 128-byte aligned");
-static_assert(kWinKs + 288 <= kWinXBytes, "x segment");
+static_assert(kWinKs + 160 <= kWinXBytes, "x segment (slot producers read 32-byte windows)");
 static_assert(2 * (kWinSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
 // 3-D tiled TMA load (coordinates innermost first), completing on bar.
@@ -571,7 +588,7 @@ __device__ __forceinline__ void mbar_expect_tx_win(uint32_t bar, uint32_t bytes)
                : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kWinThreads, 2)
     k_xcorr_mma_win(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap xmap,
                     int64_t n, int npairs, const WinJob* __restrict__ jobs, int nseg, int seg,
                     uint32_t* __restrict__ status) {
@@ -600,20 +617,20 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(2 * kWinN)
+                 "r"(kWinCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 32) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(seg_full + 8 * i, 1);
-      mbar_init(seg_empty + 8 * i, 1);
-      mbar_init(acc_full + 8 * i, 1);
+      mbar_init(seg_empty + 8 * i, 2);  // both issuers commit
+      mbar_init(acc_full + 8 * i, 2);
       mbar_init(acc_empty + 8 * i, 128);
     }
     for (int i = 0; i < kNB; ++i) {
       mbar_init(full_bar + 8 * i, kProducers);
-      mbar_init(cmt_bar + 8 * i, 1);
+      mbar_init(cmt_bar + 8 * i, 2);
     }
     *abort_flag = 0;
     *loaded_sh = 0;
@@ -669,6 +686,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- Hankel slots of x, one super-chunk at a time
     const int t = threadIdx.x - 32;
     int64_t S = 0;
+    int64_t hist[8];  // unwrapped ring origins of super-chunks S - 1 .. S - 8
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[i] = INT64_MIN / 2;
     bool ok = true;
     for (int g = 0; g < G && ok && !*abort_flag; ++g) {
       const int b = g & 1;
@@ -682,41 +702,62 @@ __global__ void __launch_bounds__(kThreads, 2)
       const uint32_t xs = xbuf + (uint32_t)(b * kWinXStride);
       const uint32_t xoff = (uint32_t)(ks - 127 - fdiv(ks - 127, 16) * 16);
       const int nsc = (nch + kWinSC - 1) / kWinSC;
-      const int64_t S0 = S;  // the segment's first super-chunk: ring base 32 S0
+      const int64_t R0 = 32 * (S + g);  // the segment's ring origin (unwrapped)
       for (int sc = 0; sc < nsc; ++sc, ++S) {
-        const int64_t prev = sc == 0 ? S - 1 : S - 3;
+        const int64_t R = R0 + 32 * sc;
+        // newest earlier super-chunk whose reads may alias this one's writes
+        int64_t prev = -1;
+#pragma unroll
+        for (int k = 8; k >= 1; --k)
+          if (R - hist[k - 1] > kWinRing - 46) prev = S - k;
         if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
           ok = false;
           break;
         }
-        const int c_first = sc * kWinSC;
-        const int c_last = c_first + kWinSC - 1 < nch - 1 ? c_first + kWinSC - 1 : nch - 1;
-        const int o_first = sc == 0 ? 0 : 128 * c_first + 112;
-        const int o_end = 128 * c_last + 240;
-        for (int o = o_first + t; o < o_end; o += kProducers) {
-          const uint32_t pa = xs + xoff + (uint32_t)o;
-          const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-          const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
-          const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
-          const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
-          const int ps = (int)((32 * S0 + (o >> 3)) % kWinRing);
-          const uint32_t a = slots + 128u * ps + 16u * (uint32_t)(o & 7);
-          st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-          if (ps < kWinMirror)
-            st_shared_v4(a + 128u * kWinRing, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
-                         (uint32_t)(hi >> 32));
+        const int c_last = 2 * sc + 1 < nch ? 2 * sc + 1 : nch - 1;
+        const int e_lo = sc == 0 ? 0 : 32 * sc + 14, e_hi = 16 * c_last + 30;  // relative slots
+        // lane (octet o8, row r) writes row r of 4 consecutive slots: x bytes
+        // [xoff + 8 e + r, + 16) for e = e0 .. e0 + 3, i.e. aligned 8-byte
+        // word pairs of the stream realigned by (xoff + r) mod 8
+        const int r = t & 7;
+        for (int e0 = e_lo + 4 * (t >> 3); e0 < e_hi; e0 += 4 * (kProducers / 8)) {
+          const uint32_t pos = xoff + 8u * (uint32_t)e0 + (uint32_t)r;
+          const uint32_t al = xs + (pos & ~7u), bs = 8u * (pos & 7u);
+          uint64_t w[6], a[5];
+#pragma unroll
+          for (int i = 0; i < 6; ++i) w[i] = ld_shared_u64(al + 8u * i);
+#pragma unroll
+          for (int i = 0; i < 5; ++i) a[i] = bs ? (w[i] >> bs) | (w[i + 1] << (64u - bs)) : w[i];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (e0 + k >= e_hi) break;
+            const int ps = (int)((R0 + e0 + k) % kWinRing);
+            const uint32_t ad = slots + 128u * (uint32_t)ps + 16u * (uint32_t)r;
+            st_shared_v4(ad, (uint32_t)a[k], (uint32_t)(a[k] >> 32), (uint32_t)a[k + 1], (uint32_t)(a[k + 1] >> 32));
+            if (ps < kWinMirror)
+              st_shared_v4(ad + 128u * kWinRing, (uint32_t)a[k], (uint32_t)(a[k] >> 32), (uint32_t)a[k + 1],
+                           (uint32_t)(a[k + 1] >> 32));
+          }
         }
         fence_proxy_async();
         mbar_arrive(full_bar + 8 * (uint32_t)(S % kNB));
+#pragma unroll
+        for (int i = 7; i > 0; --i) hist[i] = hist[i - 1];
+        hist[0] = R;
       }
     }
     if (!ok) *abort_flag = 1;
-  } else if (warp == 0) {
-    // ---- MMAs
+  } else if (warp == 0 || warp == kWinIssuerB) {
+    // ---- MMAs: issuer warp 0 takes the K steps 0, 2 of every chunk into
+    // accumulator set 0, the second issuer steps 1, 3 into set 1 (a single
+    // thread's issue loop bounds the MMA rate at this N)
+    const uint32_t set = warp == 0 ? 0u : 1u;
     const uint32_t idesc = idesc8_for(kWinN);
+    const uint64_t da0 = sdesc(slots, 256, 128, 0, 0) + 32u * set;          // + ring slot * 8
+    const uint64_t db0 = sdesc(ybuf, 16, kWinArr, 2, 0) + 2u * set;         // + (buffer + row * 128) >> 4
     int64_t S = 0;
     int pp = -1, cur_p = -1;
-    bool ok = true, first = false;
+    bool ok = true, fresh = false;  // fresh: the set is not yet written for this pair
     for (int g = 0; g < G && ok && !*abort_flag; ++g) {
       int p, nch;
       int64_t ks;
@@ -724,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (p != cur_p) {  // a new pair: its accumulator must have been read out
         cur_p = p;
         ++pp;
-        first = true;
+        fresh = true;
         if (pp >= 2)
           ok = __all_sync(0xffffffffu, mbar_wait_sleep(acc_empty + 8 * (uint32_t)(pp & 1),
                                                        (uint32_t)(((pp - 2) >> 1) & 1)));
@@ -733,29 +774,30 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int b = g & 1;
       ok = __all_sync(0xffffffffu, mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1)));
       if (!ok) break;
-      const uint32_t d = tmem + (uint32_t)((pp & 1) * kWinN);
-      const uint32_t yb = ybuf + (uint32_t)(b * kWinYBytes);
+      const uint32_t d = tmem + (uint32_t)((pp & 1) * 2 * kWinN) + set * kWinN;
       const int nsc = (nch + kWinSC - 1) / kWinSC;
+      // ring slot of chunk 0 of this segment; chunk c reads from slot + 16 c (the
+      // mirror covers runs that pass the ring's end)
+      const uint32_t pos0 = (uint32_t)((32 * (S + g)) % kWinRing);
+      const uint64_t dbs = db0 + (uint64_t)((uint32_t)(b * kWinYBytes) >> 4);
       for (int sc = 0; sc < nsc; ++sc, ++S) {
         ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(S % kNB), (uint32_t)((S / kNB) & 1)));
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
-          const int c_end = (sc + 1) * kWinSC < nch ? (sc + 1) * kWinSC : nch;
-          for (int c = sc * kWinSC; c < c_end; ++c) {
-            const uint32_t a_start = slots + 128u * (uint32_t)((32 * (S - sc) + 16 * c) % kWinRing);
-            const uint32_t b_start = yb + 128u * (uint32_t)c;
-#pragma unroll
-            for (int s2 = 0; s2 < 4; ++s2) {
-              mma_e4m3(d, sdesc(a_start + 512u * s2, 256, 128, 0, 0),
-                       sdesc(b_start + 32u * s2, 16, kWinArr, 2, 0), idesc, first ? 0u : 1u);
-              first = false;
-            }
+          const int c0 = sc * kWinSC;
+          const uint64_t da = da0 + 8u * ((pos0 + 32u * (uint32_t)sc) % kWinRing);
+          const uint64_t db = dbs + 8u * (uint32_t)c0;
+          mma_e4m3(d, da, db, idesc, fresh ? 0u : 1u);
+          mma_e4m3(d, da + 64u, db + 4u, idesc, 1u);
+          if (c0 + 1 < nch) {
+            mma_e4m3(d, da + 128u, db + 8u, idesc, 1u);
+            mma_e4m3(d, da + 192u, db + 12u, idesc, 1u);
           }
           mma_commit(cmt_bar + 8 * (uint32_t)(S % kNB));
-          *committed_sh = (int)(S + 1);
+          if (set == 0) *committed_sh = (int)(S + 1);
         }
-        first = __shfl_sync(0xffffffffu, first ? 1 : 0, 0) != 0;
+        fresh = false;
         __syncwarp();
       }
       if (!ok) break;
@@ -786,10 +828,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         break;
       }
       tc_fence_after();
-      uint32_t v[32];
+      uint32_t v[32], v1[32];
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
-        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((pp & 1) * kWinN + 32 * half), v);
+        const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((pp & 1) * 2 * kWinN + 32 * half);
+        tmem_ld32(col, v);
+        tmem_ld32(col + kWinN, v1);
 #pragma unroll
         for (int wq = 0; wq < 4; ++wq) {
           const WinJob jw = jobs[(int64_t)p * kWinW + 4 * half + wq];
@@ -798,7 +842,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           for (int j = 0; j < kWinJ; ++j) {
             const int64_t tau = T + 128 * j + 127 - m;
             if (tau < jw.lag_lo || tau > jw.lag_hi) continue;
-            const int val = __float2int_rn(__uint_as_float(v[8 * wq + j]));
+            const int val = __float2int_rn(__uint_as_float(v[8 * wq + j]) + __uint_as_float(v1[8 * wq + j]));
             if (whole)
               jw.c[tau - jw.lag_lo] = val;
             else if (val != 0)
@@ -824,7 +868,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWinN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWinCols)
                  : "memory");
   }
 }
@@ -1175,8 +1219,8 @@ cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_p
   // two CTAs per SM, each with an equal run of the (pair, segment) units
   const int64_t units = (int64_t)npairs * nseg;
   const int grid = (int)(units < 2 * (int64_t)sms ? units : 2 * (int64_t)sms);
-  k_xcorr_mma_win<<<grid, kThreads, kWinSmemBytes, st>>>(ymap, xmap, n, npairs, d_jobs, nseg, seg,
-                                                         d_status);
+  k_xcorr_mma_win<<<grid, kWinThreads, kWinSmemBytes, st>>>(ymap, xmap, n, npairs, d_jobs, nseg, seg,
+                                                            d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
