@@ -710,7 +710,8 @@ __global__ void __launch_bounds__(kWinThreads, 2)
 #pragma unroll
         for (int k = 8; k >= 1; --k)
           if (R - hist[k - 1] > kWinRing - 46) prev = S - k;
-        if (prev >= 0 && !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
+        if (prev >= 0 && !mbar_try(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1)) &&
+            !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
           ok = false;
           break;
         }
@@ -722,21 +723,28 @@ __global__ void __launch_bounds__(kWinThreads, 2)
         const int r = t & 7;
         for (int e0 = e_lo + 4 * (t >> 3); e0 < e_hi; e0 += 4 * (kProducers / 8)) {
           const uint32_t pos = xoff + 8u * (uint32_t)e0 + (uint32_t)r;
-          const uint32_t al = xs + (pos & ~7u), bs = 8u * (pos & 7u);
-          uint64_t w[6], a[5];
+          const uint32_t al = xs + (pos & ~7u);
+          uint32_t u[12], a[10];
 #pragma unroll
-          for (int i = 0; i < 6; ++i) w[i] = ld_shared_u64(al + 8u * i);
+          for (int i = 0; i < 6; ++i) {
+            const uint64_t w = ld_shared_u64(al + 8u * i);
+            u[2 * i] = (uint32_t)w, u[2 * i + 1] = (uint32_t)(w >> 32);
+          }
+          // realign by (pos & 7) bytes: word select, then a byte permute
+          const bool wo = (pos & 4u) != 0;
+          const uint32_t sel = 0x3210u + 0x1111u * (pos & 3u);
 #pragma unroll
-          for (int i = 0; i < 5; ++i) a[i] = bs ? (w[i] >> bs) | (w[i + 1] << (64u - bs)) : w[i];
+          for (int j = 0; j < 10; ++j)
+            a[j] = __byte_perm(wo ? u[j + 1] : u[j], wo ? u[j + 2] : u[j + 1], sel);
+          const uint32_t rp = (uint32_t)R0 + (uint32_t)e0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (e0 + k >= e_hi) break;
-            const int ps = (int)((R0 + e0 + k) % kWinRing);
-            const uint32_t ad = slots + 128u * (uint32_t)ps + 16u * (uint32_t)r;
-            st_shared_v4(ad, (uint32_t)a[k], (uint32_t)(a[k] >> 32), (uint32_t)a[k + 1], (uint32_t)(a[k + 1] >> 32));
-            if (ps < kWinMirror)
-              st_shared_v4(ad + 128u * kWinRing, (uint32_t)a[k], (uint32_t)(a[k] >> 32), (uint32_t)a[k + 1],
-                           (uint32_t)(a[k + 1] >> 32));
+            const uint32_t ps = (rp + (uint32_t)k) & (kWinRing - 1);
+            const uint32_t ad = slots + 128u * ps + 16u * (uint32_t)r;
+            st_shared_v4(ad, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
+            if (ps < (uint32_t)kWinMirror)
+              st_shared_v4(ad + 128u * kWinRing, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
           }
         }
         fence_proxy_async();
@@ -781,7 +789,10 @@ __global__ void __launch_bounds__(kWinThreads, 2)
       const uint32_t pos0 = (uint32_t)((32 * (S + g)) % kWinRing);
       const uint64_t dbs = db0 + (uint64_t)((uint32_t)(b * kWinYBytes) >> 4);
       for (int sc = 0; sc < nsc; ++sc, ++S) {
-        ok = __all_sync(0xffffffffu, mbar_wait_sleep(full_bar + 8 * (uint32_t)(S % kNB), (uint32_t)((S / kNB) & 1)));
+        {
+          const uint32_t fb = full_bar + 8 * (uint32_t)(S % kNB), ph = (uint32_t)((S / kNB) & 1);
+          ok = __all_sync(0xffffffffu, mbar_try(fb, ph) || mbar_wait_sleep(fb, ph));
+        }
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
