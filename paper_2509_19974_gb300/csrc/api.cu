@@ -324,7 +324,7 @@ struct QuantStage {
   int64_t max_n = 0;
   bool with_planes = false;
   size_t o_sigs = 0, o_hist = 0, o_chist = 0, o_state = 0, o_candp = 0, o_planes = 0;
-  std::vector<size_t> o_cand;  // per signal: room for all its keys
+  std::vector<size_t> o_cand;  // per signal: room for all its keys, then their indices
   // ns: the signals' lengths (host), or nullptr when all are max_n.  With
   // want_planes the rank quantizer also writes bit planes (set_planes);
   // callers check planes_written() and pack themselves otherwise.
@@ -339,7 +339,7 @@ struct QuantStage {
     o_chist = L.w<uint32_t>((size_t)nsig * 7 * 1024);
     o_state = L.w<QState>(nsig);
     o_cand.resize(nsig);
-    for (int i = 0; i < nsig; ++i) o_cand[i] = L.w<uint32_t>((size_t)(ns ? ns[i] : mx));
+    for (int i = 0; i < nsig; ++i) o_cand[i] = L.w<uint32_t>(2 * (size_t)(ns ? ns[i] : mx));
   }
   bool planes_written() const { return with_planes; }
   void fill(const Bases& B, const float* const* xs, int8_t* const* qs, const int64_t* ns) const {
@@ -1250,7 +1250,7 @@ struct CnnPlan {
                                        B.dw<float>(o_out[kCnnLayers - 1]), qe, status, st);
       if (e == cudaSuccess)
         e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
-                              B.dw<float>(o_scores), st);
+                              B.dw<float>(o_scores), st, true);
       return e;
     }
     cudaError_t e = launch_cnn_decimate(q, n, 2 * P, B.dw<float>(o_d), st);

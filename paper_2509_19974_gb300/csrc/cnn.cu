@@ -352,6 +352,7 @@ constexpr int kScRow = kCnnC + 1;               // padded row
 constexpr int kScYRows = kScT + kScBins + kScG; // fy rows per tile (272)
 constexpr int kScSmem = (kScT + kScYRows) * kScRow * 4;
 
+template <bool kPosMajor>
 __global__ void __launch_bounds__(kScWarps * 32) k_scores(const float* __restrict__ feat, int Lf,
                                                           const float* __restrict__ params,
                                                           float* __restrict__ scores) {
@@ -375,13 +376,24 @@ __global__ void __launch_bounds__(kScWarps * 32) k_scores(const float* __restric
 #pragma unroll
   for (int t = 0; t < kScG; ++t) acc[t] = 0.f;
   for (int i0 = clo; i0 < chi; i0 += kScT) {
-    for (int idx = threadIdx.x; idx < kCnnC * kScT; idx += kScWarps * 32) {
-      const int c = idx / kScT, r = idx % kScT, i = i0 + r;
-      xs[r * kScRow + c] = i < Lf ? __ldg(gx + (int64_t)c * Lf + i) : 0.f;
-    }
-    for (int idx = threadIdx.x; idx < kCnnC * kScYRows; idx += kScWarps * 32) {
-      const int c = idx / kScYRows, r = idx % kScYRows, j = i0 + l_lo + r;
-      ys[r * kScRow + c] = (j >= 0 && j < Lf) ? __ldg(gy + (int64_t)c * Lf + j) : 0.f;
+    if (kPosMajor) {  // [position][channel]: coalesced rows of 32 channels
+      for (int idx = threadIdx.x; idx < kCnnC * kScT; idx += kScWarps * 32) {
+        const int r = idx >> 5, c = idx & 31, i = i0 + r;
+        xs[r * kScRow + c] = i < Lf ? __ldg(gx + (int64_t)i * kCnnC + c) : 0.f;
+      }
+      for (int idx = threadIdx.x; idx < kCnnC * kScYRows; idx += kScWarps * 32) {
+        const int r = idx >> 5, c = idx & 31, j = i0 + l_lo + r;
+        ys[r * kScRow + c] = (j >= 0 && j < Lf) ? __ldg(gy + (int64_t)j * kCnnC + c) : 0.f;
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kCnnC * kScT; idx += kScWarps * 32) {
+        const int c = idx / kScT, r = idx % kScT, i = i0 + r;
+        xs[r * kScRow + c] = i < Lf ? __ldg(gx + (int64_t)c * Lf + i) : 0.f;
+      }
+      for (int idx = threadIdx.x; idx < kCnnC * kScYRows; idx += kScWarps * 32) {
+        const int c = idx / kScYRows, r = idx % kScYRows, j = i0 + l_lo + r;
+        ys[r * kScRow + c] = (j >= 0 && j < Lf) ? __ldg(gy + (int64_t)c * Lf + j) : 0.f;
+      }
     }
     __syncthreads();
     const int blo = max(wlo, i0), bhi = min(whi, i0 + kScT);  // warp-uniform
@@ -392,14 +404,15 @@ __global__ void __launch_bounds__(kScWarps * 32) k_scores(const float* __restric
 #pragma unroll
       for (int t = 0; t < kScG - 1; ++t) yv[t] = yr[t * kScRow];
       for (int ib = blo; ib < bhi; ib += kScG) {
+        float xv[kScG];
+#pragma unroll
+        for (int s2 = 0; s2 < kScG; ++s2) xv[s2] = xr[s2 * kScRow];
 #pragma unroll
         for (int t = kScG - 1; t < 2 * kScG - 1; ++t) yv[t] = yr[t * kScRow];
 #pragma unroll
-        for (int s2 = 0; s2 < kScG; ++s2) {
-          const float xv = xr[s2 * kScRow];
+        for (int s2 = 0; s2 < kScG; ++s2)
 #pragma unroll
-          for (int t = 0; t < kScG; ++t) acc[t] = fmaf(xv, yv[s2 + t], acc[t]);
-        }
+          for (int t = 0; t < kScG; ++t) acc[t] = fmaf(xv[s2], yv[s2 + t], acc[t]);
 #pragma unroll
         for (int t = 0; t < kScG - 1; ++t) yv[t] = yv[t + kScG];
         xr += kScG * kScRow;
@@ -848,12 +861,12 @@ cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_
 }
 
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
-                              float* scores, cudaStream_t st) {
+                              float* scores, cudaStream_t st, bool pos_major) {
   if (Lf < 1 || npairs <= 0) return npairs <= 0 ? cudaSuccess : cudaErrorInvalidValue;
-  cudaFuncSetAttribute(k_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, kScSmem);
+  auto kern = pos_major ? k_scores<true> : k_scores<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kScSmem);
   const int nb = 2 * Lf - 1;
-  k_scores<<<dim3((nb + kScBins - 1) / kScBins, npairs), kScWarps * 32, kScSmem, st>>>(feat, Lf, params,
-                                                                                     scores);
+  kern<<<dim3((nb + kScBins - 1) / kScBins, npairs), kScWarps * 32, kScSmem, st>>>(feat, Lf, params, scores);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -38,7 +38,8 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
                              const float* params, cudaStream_t st);
 // Inference forward (decimate + 4 layers) with BF16 activations between
 // layers: act[l] holds layer l's output, nsig x cnn_eo_elems((n/16) >> (l+1))
-// BF16 in the layout above; feat receives the FP32 features [nsig][32][n/256];
+// BF16 in the layout above; feat receives the FP32 features [nsig][n/256][32]
+// (position-major);
 // qe (nullable, nsig x n bytes) the levels as E4M3 bytes.  n a multiple of
 // 2048.
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
@@ -55,14 +56,15 @@ __host__ __device__ constexpr int64_t cnn_eo_elems(int L) { return (int64_t)8 * 
 // One 32 -> 32 channel layer of the inference forward on the tensor cores
 // (mma.cu): in = that layer's input (length L, layout above); out = the next
 // layer's input (length L/2, same layout, zero rows included) or (last) FP32
-// features [nsig][32][L/2]; wbf / bias = that layer's BF16 weights
+// features [nsig][L/2][32] (position-major); wbf / bias = that layer's BF16 weights
 // [32][32][9] and FP32 bias.  L a multiple of 4.  Time-outs set
 // TDE_ST_TIMEOUT.
 cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, const uint16_t* wbf,
                                const float* bias, bool last, uint32_t* d_status, cudaStream_t st);
-// score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1).
+// score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1;
+// channel-major [S][32][Lf], or position-major [S][Lf][32] with pos_major).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
-                              float* scores, cudaStream_t st);
+                              float* scores, cudaStream_t st, bool pos_major = false);
 // Top-8 bins per pair -> window centres in samples (256 l), softmax mass of
 // the top 8 (margin).
 cudaError_t launch_cnn_topk(const float* scores, int npairs, int Lf, int32_t* centres,

@@ -109,7 +109,7 @@ struct QState {
 struct QWork {
   uint32_t* hist;               // [nsig][4096]
   QState* state;                // [nsig]
-  uint32_t* const* cand;        // [nsig] device pointers to lists of n keys
+  uint32_t* const* cand;        // [nsig] device pointers to lists of 2 n words (keys, index | sign)
   uint32_t* chist;              // [nsig][7][1024] candidate histograms
 };
 // The rank quantizer (bits 2, 4) as five streaming launches; d_planes

@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(kWinThreads, 2)
 // with both outputs of its pooling pair: y = relu(max(z_even, z_odd) + b).
 //
 // Outputs: the next layer's E/O arrays (with their zero rows), or for the
-// last layer FP32 features [signal][32][L/2].  A CTA takes an equal
+// last layer FP32 features [signal][L/2][32] (position-major).  A CTA takes an equal
 // contiguous run of (signal, tile) units; thread 0 keeps kCvNB tiles of bulk
 // copies in flight and issues the MMAs into two accumulators (2 x 64 TMEM
 // columns), so tile i's MMAs overlap tile i - 1's epilogue.  Waits are
@@ -1067,10 +1067,10 @@ __global__ void __launch_bounds__(kThreads, kCvCtasPerSm)
     for (int j = 0; j < 16; ++j)
       y[j] = fmaxf(fmaxf(__uint_as_float(ve[j]), __uint_as_float(vo[j])) + bv[j], 0.f);
     if (P >= Lo) return;
-    if (kLast) {
-      float* dst = static_cast<float*>(out) + ((int64_t)s * kCnnC + 16 * ch) * Lo + P;
+    if (kLast) {  // features, position-major: [signal][P][32]
+      float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + ((int64_t)s * Lo + P) * kCnnC + 16 * ch);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) dst[(int64_t)j * Lo] = y[j];
+      for (int j = 0; j < 4; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
     } else {
       const int Rn = cnn_eo_rows(Lo);
       uint16_t* o = static_cast<uint16_t*>(out) +

@@ -21,10 +21,12 @@
 //             pass a grid of histogram CTAs per signal and a one-CTA select):
 //             two radix passes (10 + 9 bits) over the candidates give the
 //             exact order statistics;
-//   k_qapply  q = sign(x) * #{m : |x| >= t_m}, and on request the bit planes
-//             of the popc kernels (one read of x, one write of q).
-// The candidate list has room for the whole signal, so no input (ties,
-// constant signals) needs another path.
+//   k_qfix    the candidates' levels: k_qcand already wrote every other
+//             sample's level (its first digit decides it), so x is read twice;
+//   k_qapply  (only when the popc kernels' bit planes are wanted)
+//             q = sign(x) * #{m : |x| >= t_m} and the planes (a third read).
+// The candidate list has room for the whole signal (keys, then index and
+// sign), so no input (ties, constant signals) needs another path.
 #include "common.cuh"
 
 namespace {
@@ -333,9 +335,14 @@ __global__ void __launch_bounds__(kQT) k_qsel1(const QSig* __restrict__ sigs, QW
 // list).
 constexpr int kCandBuf = 4096;
 
-template <int M>
+// kApply: the keys' levels are written as well wherever the first digit
+// decides them (q = sign(x) * #{m : digit > digit of t_m}); a candidate's
+// level waits for the exact thresholds (k_qfix), so its index and sign go to
+// the second half of the list, cidx[i] = index | (x < 0) << 31.
+template <int M, bool kApply>
 __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QWork w) {
   __shared__ uint32_t buf[kCandBuf];
+  __shared__ uint32_t bufi[kApply ? kCandBuf : 1];
   __shared__ uint32_t nbuf, gbase;
   const int sig = blockIdx.y;
   const QSig s = sigs[sig];
@@ -344,6 +351,7 @@ __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QW
 #pragma unroll
   for (int m = 0; m < M; ++m) pre[m] = st->pre[m];
   uint32_t* cand = w.cand[sig];
+  uint32_t* cidx = cand + s.n;
   auto match = [&](uint32_t u) {
     const uint32_t hi = u >> 19;
     bool h = false;
@@ -351,15 +359,28 @@ __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QW
     for (int m = 0; m < M; ++m) h |= hi == pre[m];
     return h;
   };
-  auto put = [&](uint32_t slot, uint32_t u) {
-    if (slot < kCandBuf)
+  // level of a non-candidate from its first digit (signed, sign(0) = 0)
+  auto level_of = [&](float f) {
+    const uint32_t hi = (__float_as_uint(f) & 0x7FFFFFFFu) >> 19;
+    int lv = 0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) lv += hi > pre[m];
+    return sign_of(f) * lv;
+  };
+  auto put = [&](uint32_t slot, uint32_t u, uint32_t ix) {
+    if (slot < kCandBuf) {
       buf[slot] = u;
-    else
-      cand[atomicAdd(&st->ncand, 1u)] = u;
+      if (kApply) bufi[slot] = ix;
+    } else {
+      const uint32_t g = atomicAdd(&st->ncand, 1u);
+      cand[g] = u;
+      if (kApply) cidx[g] = ix;
+    }
   };
   if (threadIdx.x == 0) nbuf = 0;
   __syncthreads();
-  const bool vec = (reinterpret_cast<uintptr_t>(s.x) & 15) == 0;
+  const bool vec = (reinterpret_cast<uintptr_t>(s.x) & 15) == 0 &&
+                   (!kApply || (reinterpret_cast<uintptr_t>(s.q) & 3) == 0);
   const int64_t n4 = vec ? s.n >> 2 : 0;
   const float4* x4 = reinterpret_cast<const float4*>(s.x);
   for (int64_t c0 = (int64_t)blockIdx.x * (kQPer / 4); c0 < n4; c0 += (int64_t)gridDim.x * (kQPer / 4)) {
@@ -374,32 +395,69 @@ __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QW
     for (int k = 0; k < 8; ++k) {
       if (c0 + k * kQT + threadIdx.x >= n4) continue;
       const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+      uint32_t packed = 0;
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (match(__float_as_uint(f[e]) & 0x7FFFFFFFu)) hits |= 1u << (4 * k + e);
+      for (int e = 0; e < 4; ++e) {
+        if (match(__float_as_uint(f[e]) & 0x7FFFFFFFu))
+          hits |= 1u << (4 * k + e);
+        else if (kApply)
+          packed |= ((uint32_t)level_of(f[e]) & 0xFFu) << (8 * e);
+      }
+      if (kApply) reinterpret_cast<uint32_t*>(s.q)[c0 + k * kQT + threadIdx.x] = packed;
     }
     if (hits) {
       uint32_t slot = atomicAdd(&nbuf, (uint32_t)__popc(hits));
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+        const uint32_t i4 = (uint32_t)(4 * (c0 + k * kQT + threadIdx.x));
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (hits >> (4 * k + e) & 1u) put(slot++, __float_as_uint(f[e]) & 0x7FFFFFFFu);
+          if (hits >> (4 * k + e) & 1u)
+            put(slot++, __float_as_uint(f[e]) & 0x7FFFFFFFu, (i4 + e) | (f[e] < 0.f ? 0x80000000u : 0u));
       }
     }
   }
   // the tail (or every sample, when x is not 16-byte aligned)
   for (int64_t j = (n4 << 2) + (int64_t)blockIdx.x * kQT + threadIdx.x; j < s.n;
        j += (int64_t)gridDim.x * kQT) {
-    const uint32_t u = __float_as_uint(s.x[j]) & 0x7FFFFFFFu;
-    if (match(u)) put(atomicAdd(&nbuf, 1u), u);
+    const float f = s.x[j];
+    const uint32_t u = __float_as_uint(f) & 0x7FFFFFFFu;
+    if (match(u))
+      put(atomicAdd(&nbuf, 1u), u, (uint32_t)j | (f < 0.f ? 0x80000000u : 0u));
+    else if (kApply)
+      s.q[j] = (int8_t)level_of(f);
   }
   __syncthreads();
   const uint32_t nb = nbuf < (uint32_t)kCandBuf ? nbuf : (uint32_t)kCandBuf;
   if (threadIdx.x == 0) gbase = nb ? atomicAdd(&st->ncand, nb) : 0u;
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < nb; i += kQT) cand[gbase + i] = buf[i];
+  for (uint32_t i = threadIdx.x; i < nb; i += kQT) {
+    cand[gbase + i] = buf[i];
+    if (kApply) cidx[gbase + i] = bufi[i];
+  }
+}
+
+// The candidates' levels, from the exact thresholds: q[idx] = sign * #{m :
+// key >= t_m} (sign(0) = 0).
+template <int M>
+__global__ void __launch_bounds__(kQT) k_qfix(const QSig* __restrict__ sigs, QWork w) {
+  const int sig = blockIdx.y;
+  const QSig s = sigs[sig];
+  const QState* st = w.state + sig;
+  uint32_t t[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) t[m] = st->thr[m];
+  const uint32_t nc = st->ncand;
+  const uint32_t* cand = w.cand[sig];
+  const uint32_t* cidx = cand + s.n;
+  for (uint32_t i = blockIdx.x * kQT + threadIdx.x; i < nc; i += gridDim.x * kQT) {
+    const uint32_t u = cand[i], c = cidx[i];
+    int lv = 0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) lv += u >= t[m];
+    s.q[c & 0x7FFFFFFFu] = (int8_t)(u == 0 ? 0 : ((c >> 31) ? -lv : lv));
+  }
 }
 
 // Short signals (few candidates): both candidate passes in one CTA per
@@ -677,10 +735,11 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
   if (e != cudaSuccess) return e;
   k_qhist<<<grid, kQT, 0, st>>>(d_sigs, w, d_status);
   k_qsel1<<<nsig, kQT, 0, st>>>(d_sigs, w, M, L);
+  const bool fused = d_planes == nullptr;  // levels written by k_qcand + k_qfix
   if (M == 1)
-    k_qcand<1><<<grid, kQT, 0, st>>>(d_sigs, w);
+    fused ? k_qcand<1, true><<<grid, kQT, 0, st>>>(d_sigs, w) : k_qcand<1, false><<<grid, kQT, 0, st>>>(d_sigs, w);
   else
-    k_qcand<7><<<grid, kQT, 0, st>>>(d_sigs, w);
+    fused ? k_qcand<7, true><<<grid, kQT, 0, st>>>(d_sigs, w) : k_qcand<7, false><<<grid, kQT, 0, st>>>(d_sigs, w);
   if (max_n <= (1 << 18)) {
     k_qsel2<<<nsig, kQT, 0, st>>>(d_sigs, w, M);
     TDE_COUNT_LAUNCH(1);
@@ -695,10 +754,20 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
     k_qcsel<1><<<nsig, kQT, 0, st>>>(w, M);
     TDE_COUNT_LAUNCH(5);
   }
-  if (M == 1)
+  if (fused) {
+    int64_t gf = ceil_div64(max_n, 16 * kQT);  // candidates are a few percent of a signal
+    if (gf < 1) gf = 1;
+    if (gf > 65535) gf = 65535;
+    const dim3 fgrid((unsigned)gf, (unsigned)nsig);
+    if (M == 1)
+      k_qfix<1><<<fgrid, kQT, 0, st>>>(d_sigs, w);
+    else
+      k_qfix<7><<<fgrid, kQT, 0, st>>>(d_sigs, w);
+  } else if (M == 1) {
     k_qapply<1><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
-  else
+  } else {
     k_qapply<7><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
+  }
   TDE_COUNT_LAUNCH(4);
   return cudaGetLastError();
 }
