@@ -268,8 +268,9 @@ tde_status tde_batch_destroy(tde_batch* batch);
  * features f[32][n/256]; score[l] = alpha * sum_c sum_i fx[c][i] fy[c][i + l]
  * for bins l in [-(n/256 - 1), n/256 - 1]; bin l stands for the lags
  * [256 l - 128, 256 l + 128].  Weights are BF16 in the forward pass, all
- * accumulation FP32; training keeps FP32 master weights and AdamW moments and
- * is deterministic.  Pair p's quantized signals are q[(2p) n ..] (x) and
+ * accumulation FP32 (inference also rounds the activations of layers 2-4 to
+ * BF16, where the tensor cores read them); training keeps FP32 master
+ * weights and AdamW moments and is deterministic.  Pair p's quantized signals are q[(2p) n ..] (x) and
  * q[(2p+1) n ..] (y), int8, device. */
 typedef struct tde_model tde_model;
 
@@ -321,8 +322,9 @@ tde_status tde_learned_destroy(tde_learned* plan);
  * reads them) and window w with centre centres[8 p + w] (device int32),
  * c_out[(8 p + w) * 257 + i] (device int32) = c[centre - 128 + i] for
  * i in [0, 257); lags outside [-(n-1), n-1] read 0.  Computed on the tensor
- * cores (BF16 operands, FP32 accumulation, exact for these levels).
- * bits 1, 2 or 4. */
+ * cores (E4M3 operands, FP32 accumulation: exact for levels in [-7, 7]).
+ * Uses a context workspace of 2 npairs * round_up(n, 128) bytes for the
+ * levels in E4M3.  bits 1, 2 or 4. */
 tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npairs, int bits,
                              const int32_t* centres, int32_t* c_out, tde_stream_t stream);
 
