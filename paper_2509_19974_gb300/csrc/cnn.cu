@@ -236,91 +236,12 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
   }
 }
 
-// ---- inference chain with BF16 activation rows
-// Inference keeps the activations between layers as BF16 rows [signal][pos][32
-// channels] (64 bytes per position): the tensor-core layers (tcgen05, in
-// mma.cu) take BF16 operands anyway, so the values are those of the FP32
-// chain rounded where the tensor cores would round them, at half the traffic.
-// The last layer writes FP32 features [signal][32][Lf] for the scores.
-
-// Layer 0 fused with the decimation: d[j] = (sum of q[16 j .. 16 j + 15]) / 4,
-// conv (kernel 9, pad 4, 1 -> 32 channels) + bias, ReLU, max-pool 2 -> the
-// next layer's input (parity / 8-channel-chunk arrays, zero rows included);
-// on request also the levels as E4M3 bytes (the windows' tensor-core input).
-// A CTA makes 256 pooled positions; thread = one pooled position, all 32
-// channels (FP32 arithmetic in the same order as k_conv_fwd<1>).
-constexpr int kC1T = 256;  // pooled positions per CTA
-
-__global__ void __launch_bounds__(kThreads) k_conv1_inf(const int8_t* __restrict__ q, int64_t n,
-                                                        const uint16_t* __restrict__ wbf,
-                                                        const float* __restrict__ bias,
-                                                        uint16_t* __restrict__ out,
-                                                        uint8_t* __restrict__ qe) {
-  __shared__ float d_s[2 * kC1T + 8];
-  __shared__ __align__(16) float w_s[kCnnK][kCnnC];
-  __shared__ __align__(16) float b_s[kCnnC];
-  const int s = blockIdx.y;
-  const int Ld = (int)(n / kCnnDec);
-  const int P0 = blockIdx.x * kC1T;          // first pooled position
-  const int d0 = 2 * P0 - 4;                 // d index of d_s[0]
-  const int8_t* src = q + (int64_t)s * n;
-  for (int i = threadIdx.x; i < 2 * kC1T + 8; i += kThreads) {
-    const int j = d0 + i;
-    float v = 0.f;
-    if (j >= 0 && j < Ld) {
-      const uint4 w = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)j * kCnnDec));
-      int acc = 0;
-      acc = __dp4a((int)w.x, 0x01010101, acc);
-      acc = __dp4a((int)w.y, 0x01010101, acc);
-      acc = __dp4a((int)w.z, 0x01010101, acc);
-      acc = __dp4a((int)w.w, 0x01010101, acc);
-      v = 0.25f * (float)acc;
-      // the E4M3 copy of the levels this CTA owns (d indices 2 P0 ..)
-      if (qe && i >= 4 && i < 2 * kC1T + 4)
-        *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
-    }
-    d_s[i] = v;
-  }
-  for (int i = threadIdx.x; i < kCnnK * kCnnC; i += kThreads) {
-    const int co = i / kCnnK, k = i % kCnnK;
-    w_s[k][co] = bf16_to_f(wbf[i]);
-  }
-  if (threadIdx.x < kCnnC) b_s[threadIdx.x] = bias[threadIdx.x];
-  __syncthreads();
-  const int P = P0 + threadIdx.x;
-  if (P >= Ld / 2) return;
-  float dv[kCnnK + 1];  // d at pre-pool positions 2P - 4 .. 2P + 5
-#pragma unroll
-  for (int k = 0; k <= kCnnK; ++k) dv[k] = d_s[2 * threadIdx.x + k];
-  uint32_t packed[kCnnC / 2];
-#pragma unroll
-  for (int c4 = 0; c4 < kCnnC / 4; ++c4) {
-    float a0[4], a1[4];  // pre-pool positions 2P, 2P + 1 of channels 4 c4 ..
-    const float4 bb = *reinterpret_cast<const float4*>(&b_s[4 * c4]);
-    a0[0] = a1[0] = bb.x, a0[1] = a1[1] = bb.y, a0[2] = a1[2] = bb.z, a0[3] = a1[3] = bb.w;
-#pragma unroll
-    for (int k = 0; k < kCnnK; ++k) {
-      const float4 w = *reinterpret_cast<const float4*>(&w_s[k][4 * c4]);
-      const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        a0[h] = fmaf(wv[h], dv[k], a0[h]);
-        a1[h] = fmaf(wv[h], dv[k + 1], a1[h]);
-      }
-    }
-    float r[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) r[h] = fmaxf(fmaxf(a0[h], 0.f), fmaxf(a1[h], 0.f));
-    packed[2 * c4] = pack_bf16x2(r[0], r[1]);
-    packed[2 * c4 + 1] = pack_bf16x2(r[2], r[3]);
-  }
-  const int Rn = cnn_eo_rows(Ld / 2);
-  uint16_t* dst = out + ((((int64_t)s * 2 + (P & 1)) * 4) * Rn + (P >> 1) + 2) * 8;
-#pragma unroll
-  for (int v = 0; v < 4; ++v)
-    *reinterpret_cast<uint4*>(dst + (int64_t)v * Rn * 8) =
-        make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
-}
+// ---- inference chain with BF16 activations
+// Inference keeps the activations between layers as BF16 parity arrays (the
+// layout in cnn.cuh): every layer runs on the tensor cores (tcgen05, in
+// mma.cu), which take BF16 operands anyway, so the values are those of the
+// FP32 chain rounded where the tensor cores read them, at half the traffic.
+// The last layer writes FP32 features [signal][Lf][32] for the scores.
 
 // The zero rows of a layer input of length L (rows 0, 1 and [L/2 + 2, R)).
 __global__ void k_eo_pad(uint16_t* __restrict__ act, int L, int nsig) {
@@ -847,11 +768,12 @@ cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_
                              uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
   const int Ld = (int)(n / kCnnDec);
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
-  k_conv1_inf<<<dim3((Ld / 2 + kC1T - 1) / kC1T, nsig), kThreads, 0, st>>>(
-      q, n, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qe);
+  cudaError_t e = launch_cnn_conv1_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qe,
+                                      d_status, st);
+  if (e != cudaSuccess) return e;
   k_eo_pad<<<(nsig + 63) / 64, 256, 0, st>>>(act[0], Ld / 2, nsig);
-  TDE_COUNT_LAUNCH(2);
-  cudaError_t e = cudaGetLastError();
+  TDE_COUNT_LAUNCH(1);
+  e = cudaGetLastError();
   for (int l = 1; l < kCnnLayers && e == cudaSuccess; ++l) {
     const bool last = l == kCnnLayers - 1;
     e = launch_cnn_conv_tc(act[l - 1], last ? static_cast<void*>(feat) : static_cast<void*>(act[l]),

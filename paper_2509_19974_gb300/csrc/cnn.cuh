@@ -61,6 +61,12 @@ __host__ __device__ constexpr int64_t cnn_eo_elems(int L) { return (int64_t)8 * 
 // TDE_ST_TIMEOUT.
 cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, const uint16_t* wbf,
                                const float* bias, bool last, uint32_t* d_status, cudaStream_t st);
+// The first layer of the inference forward on the tensor cores (mma.cu):
+// decimation of q [nsig][n] int8, conv 1 -> 32 (weights wbf [32][1][9], bias)
+// -> out, the second layer's input (length n/32, parity arrays; the zero rows
+// are the caller's); qe (nullable) receives the levels as E4M3 bytes.
+cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
+                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1;
 // channel-major [S][32][Lf], or position-major [S][Lf][32] with pos_major).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,

@@ -1145,6 +1145,176 @@ __global__ void __launch_bounds__(kThreads, kCvCtasPerSm)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The learned proposal's first layer (decimation + conv 1 -> 32 channels,
+// kernel 9, pad 4, bias, ReLU, max-pool 2) on the tensor cores.  A CTA takes
+// 128 pooled outputs P0 + m of one signal: it reads the 16 (264) level bytes
+// per decimated sample d[j] = (sum of 16 levels) / 4 (exact in BF16: |4 d| <=
+// 112), writes the E4M3 copy of the levels it owns, builds the im2col operand
+//   A_par[m][k] = d[2 (P0 + m) + par + k - 4]   (k < 9; k = 9..15 zero)
+// for both parities of the pooling pair as K-major no-swizzle tiles (16-byte
+// rows of 8 taps, leading byte offset 2048 between the two 8-tap halves), and
+// issues one MMA of 128 x 32 x 16 per parity (columns 0-31 odd, 32-63 even)
+// against W[co][k].  The epilogue is that of k_conv_tc: y = relu(max(z_even,
+// z_odd) + b), stored as the next layer's parity arrays.
+constexpr int kC1M = 128;                      // pooled outputs per CTA
+constexpr int kC1D = 2 * kC1M + 8;             // decimated samples per CTA (264)
+constexpr int kC1ABytes = 2 * 2 * kC1M * 16;   // A tiles: parity x 8-tap half x rows
+constexpr int kC1WBytes = 2 * kCnnC * 16;      // B: 8-tap half x co rows
+constexpr int kC1Smem = kC1ABytes + kC1WBytes + kC1D * 2 + 16 + 16 + 128;
+constexpr uint32_t kC1Idesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCnnC >> 3) << 17) | ((uint32_t)(kC1M >> 4) << 24);
+
+__global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restrict__ q, int64_t n, int nsig,
+                                                      const uint16_t* __restrict__ wbf,
+                                                      const float* __restrict__ bias,
+                                                      uint16_t* __restrict__ out,
+                                                      uint8_t* __restrict__ qe,
+                                                      uint32_t* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 127u) & ~127u;
+  uint8_t* sbase = smem_raw + (base - raw);
+  const uint32_t a_s = base;                       // [par][half][m] 16-byte rows
+  const uint32_t w_s = base + kC1ABytes;           // [half][co] 16-byte rows
+  uint16_t* d_s = reinterpret_cast<uint16_t*>(sbase + kC1ABytes + kC1WBytes);  // BF16 d
+  const uint32_t bar = base + kC1ABytes + kC1WBytes + kC1D * 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + kC1ABytes + kC1WBytes + kC1D * 2 + 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Ld = (int)(n / kCnnDec), Lo = Ld / 2;  // decimated length, pooled outputs
+  const int tps = (Lo + kC1M - 1) / kC1M;
+  const int units = nsig * tps;
+  const int u0 = (int)((int64_t)units * blockIdx.x / gridDim.x);
+  const int u1 = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(2 * kCnnC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // weights: W_s[half][co][e] = W[co][0][8 half + e] (taps 9..15 zero)
+  for (int idx = threadIdx.x; idx < 2 * kCnnC * 8; idx += kThreads) {
+    const int e = idx & 7, co = (idx >> 3) & (kCnnC - 1), h = idx >> 8;
+    const int k = 8 * h + e;
+    const uint16_t v = k < kCnnK ? wbf[co * kCnnK + k] : (uint16_t)0;
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(w_s + 2u * (uint32_t)idx), "h"(v) : "memory");
+  }
+  const int qd = warp & 3, ch = warp >> 2;
+  float bv[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) bv[j] = bias[16 * ch + j];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t bd = sdesc(w_s, kCnnC * 16, 128, 0, 0);
+  const uint64_t ad_odd = sdesc(a_s + 2u * kC1M * 16, kC1M * 16, 128, 0, 0), ad_even = sdesc(a_s, kC1M * 16, 128, 0, 0);
+  bool ok = true;
+  uint32_t phase = 0;
+  // level bytes of a tile's decimated samples d[2 P0 - 4 + i], i = threadIdx.x
+  // and threadIdx.x + kThreads, loaded one tile ahead
+  static_assert(kC1D <= 2 * kThreads, "two samples per thread");
+  auto fetch = [&](int u, uint4 (&w)[2]) {
+    const int s = u / tps, P0 = (u - s * tps) * kC1M;
+    const int8_t* src = q + (int64_t)s * n;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int i = threadIdx.x + t * kThreads, j = 2 * P0 - 4 + i;
+      w[t] = (i < kC1D && j >= 0 && j < Ld) ? __ldg(reinterpret_cast<const uint4*>(src + (int64_t)j * kCnnDec))
+                                            : make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  uint4 wn[2];
+  if (u0 < u1) fetch(u0, wn);
+  for (int u = u0; u < u1 && ok; ++u) {
+    const int s = u / tps, P0 = (u - s * tps) * kC1M;
+    uint4 wc[2] = {wn[0], wn[1]};
+    if (u + 1 < u1) fetch(u + 1, wn);
+    // decimate: d_s[i] = d[2 P0 - 4 + i]; the E4M3 copy of the samples this tile owns
+    const int d0 = 2 * P0 - 4;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int i = threadIdx.x + t * kThreads;
+      if (i >= kC1D) continue;
+      const int j = d0 + i;
+      float v = 0.f;
+      if (j >= 0 && j < Ld) {
+        const uint4 w = wc[t];
+        int acc = 0;
+        acc = __dp4a((int)w.x, 0x01010101, acc);
+        acc = __dp4a((int)w.y, 0x01010101, acc);
+        acc = __dp4a((int)w.z, 0x01010101, acc);
+        acc = __dp4a((int)w.w, 0x01010101, acc);
+        v = 0.25f * (float)acc;
+        if (qe && i >= 4 && i < 2 * kC1M + 4)
+          *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
+      }
+      d_s[i] = (uint16_t)(__float_as_uint(v) >> 16);  // exact: |4 d| <= 112
+    }
+    __syncthreads();
+    // im2col: thread (par, half, m) writes one 16-byte row of 8 taps
+    for (int row = threadIdx.x; row < 2 * 2 * kC1M; row += kThreads) {
+      const int m = row & (kC1M - 1), h = (row >> 7) & 1, par = row >> 8;
+      uint32_t wv[4];
+#pragma unroll
+      for (int e2 = 0; e2 < 4; ++e2) {
+        const int k0 = 8 * h + 2 * e2;  // taps k0, k0 + 1
+        const int i0 = 2 * m + par + k0;
+        const uint32_t lo = k0 < kCnnK ? d_s[i0] : 0u, hi = k0 + 1 < kCnnK ? d_s[i0 + 1] : 0u;
+        wv[e2] = lo | (hi << 16);
+      }
+      st_shared_v4(a_s + 16u * (uint32_t)row, wv[0], wv[1], wv[2], wv[3]);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {  // odd parity -> columns 0-31, even -> 32-63
+      mma_bf16(tmem, ad_odd, bd, kC1Idesc, 0u);
+      mma_bf16(tmem + kCnnC, ad_even, bd, kC1Idesc, 0u);
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(mbar_wait_sleep(bar, phase));
+    phase ^= 1u;
+    if (!ok) break;
+    tc_fence_after();
+    const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * ch);
+    uint32_t vo[16], ve[16];
+    tmem_ld16_nowait(col, vo);
+    tmem_ld16_nowait(col + 32u, ve);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int P = P0 + 32 * qd + lane;
+    if (P < Lo) {
+      float y[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        y[j] = fmaxf(fmaxf(__uint_as_float(ve[j]), __uint_as_float(vo[j])) + bv[j], 0.f);
+      const int Rn = cnn_eo_rows(Lo);
+      uint16_t* o = out + ((((int64_t)s * 2 + (P & 1)) * 4 + 2 * ch) * Rn + (P >> 1) + 2) * 8;
+      *reinterpret_cast<uint4*>(o) = make_uint4(pack_bf16x2_rn(y[0], y[1]), pack_bf16x2_rn(y[2], y[3]),
+                                                pack_bf16x2_rn(y[4], y[5]), pack_bf16x2_rn(y[6], y[7]));
+      *reinterpret_cast<uint4*>(o + (int64_t)Rn * 8) =
+          make_uint4(pack_bf16x2_rn(y[8], y[9]), pack_bf16x2_rn(y[10], y[11]),
+                     pack_bf16x2_rn(y[12], y[13]), pack_bf16x2_rn(y[14], y[15]));
+    }
+    tc_fence_before();  // the next tile's MMAs overwrite the accumulator after the loop's barriers
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCnnC)
+                 : "memory");
+  }
+}
+
 }  // namespace
 
 int mma_smem_bytes() { return kSmemBytes8; }
@@ -1277,6 +1447,25 @@ cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, c
   const int64_t cap = (int64_t)kCvCtasPerSm * sms;
   const int grid = (int)(units < cap ? units : cap);
   kern<<<grid, kThreads, kCvSmem, st>>>(in, out, L, nsig, wbf, bias, d_status);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
+                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
+  if (nsig <= 0) return cudaSuccess;
+  const int64_t Ld = n / kCnnDec;
+  if (n % kCnnDec != 0 || Ld % 4 != 0 || Ld > INT32_MAX) return cudaErrorInvalidValue;
+  const int64_t ctas = (int64_t)nsig * ((Ld / 2 + kC1M - 1) / kC1M);
+  if (ctas > INT32_MAX) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_conv1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kC1Smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = 4 * (int64_t)sms;  // persistent: four CTAs per SM, contiguous tile runs
+  const int grid = (int)(ctas < cap ? ctas : cap);
+  k_conv1_tc<<<grid, kThreads, kC1Smem, st>>>(q, n, nsig, wbf, bias, out, qe, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
