@@ -360,6 +360,88 @@ __global__ void __launch_bounds__(kScWarps * 32) k_scores(const float* __restric
   if ((lane & 1) == 0 && bin < nb) scores[(int64_t)p * nb + bin] = params[kCnnAlpha] * acc[0];
 }
 
+// Short features (Lf <= 256): one CTA per pair with both features whole in
+// shared memory (32 zero rows padding y on both sides), 16 warps, warp w
+// taking the bin groups w and w + ngroups/2: their overlaps add up to about
+// Lf, so every warp does the same work and the grid is one wave.  The inner
+// loop and the lane reduction are those of k_scores.
+constexpr int kSpWarps = 16;
+constexpr int kSpMaxLf = 256;
+constexpr int kSpPad = 32;
+constexpr int kSpSmem = ((kSpMaxLf + 16) + (kSpMaxLf + 2 * kSpPad)) * kScRow * 4;
+
+template <bool kPosMajor>
+__global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* __restrict__ feat, int Lf,
+                                                                  const float* __restrict__ params,
+                                                                  float* __restrict__ scores) {
+  extern __shared__ __align__(16) float sm[];
+  float* xs = sm;                               // [Lf + 16][kScRow]: fx at row i
+  float* ys = sm + (kSpMaxLf + 16) * kScRow;    // [Lf + 64][kScRow]: fy at row i + kSpPad
+  const int p = blockIdx.x;
+  const int nb = 2 * Lf - 1;
+  const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
+  const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
+  for (int idx = threadIdx.x; idx < kCnnC * (Lf + 16); idx += kSpWarps * 32) {
+    const int r = kPosMajor ? idx >> 5 : idx % (Lf + 16), c = kPosMajor ? idx & 31 : idx / (Lf + 16);
+    xs[r * kScRow + c] = r < Lf ? __ldg(kPosMajor ? gx + (int64_t)r * kCnnC + c : gx + (int64_t)c * Lf + r) : 0.f;
+  }
+  for (int idx = threadIdx.x; idx < kCnnC * (Lf + 2 * kSpPad); idx += kSpWarps * 32) {
+    const int r = kPosMajor ? idx >> 5 : idx % (Lf + 2 * kSpPad), c = kPosMajor ? idx & 31 : idx / (Lf + 2 * kSpPad);
+    const int j = r - kSpPad;
+    ys[r * kScRow + c] =
+        (j >= 0 && j < Lf) ? __ldg(kPosMajor ? gy + (int64_t)j * kCnnC + c : gy + (int64_t)c * Lf + j) : 0.f;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ngroups = (nb + kScG - 1) / kScG, half = (ngroups + 1) / 2;
+  const float alpha = params[kCnnAlpha];
+  for (int gi = 0; gi < 2; ++gi) {
+    const int g = warp + gi * half;
+    if (warp >= half || g >= ngroups) continue;  // warp-uniform
+    const int lg = kScG * g - (Lf - 1);          // lag of the group's first bin
+    const int wlo = max(0, -(lg + kScG - 1)) & ~(kScG - 1);
+    const int whi = (min(Lf, Lf - lg) + kScG - 1) & ~(kScG - 1);
+    float acc[kScG];
+#pragma unroll
+    for (int t = 0; t < kScG; ++t) acc[t] = 0.f;
+    if (wlo < whi) {
+      const float* xr = xs + wlo * kScRow + lane;
+      const float* yr = ys + (wlo + lg + kSpPad) * kScRow + lane;
+      float yv[2 * kScG - 1];
+#pragma unroll
+      for (int t = 0; t < kScG - 1; ++t) yv[t] = yr[t * kScRow];
+      for (int ib = wlo; ib < whi; ib += kScG) {
+        float xv[kScG];
+#pragma unroll
+        for (int s2 = 0; s2 < kScG; ++s2) xv[s2] = xr[s2 * kScRow];
+#pragma unroll
+        for (int t = kScG - 1; t < 2 * kScG - 1; ++t) yv[t] = yr[t * kScRow];
+#pragma unroll
+        for (int s2 = 0; s2 < kScG; ++s2)
+#pragma unroll
+          for (int t = 0; t < kScG; ++t) acc[t] = fmaf(xv[s2], yv[s2 + t], acc[t]);
+#pragma unroll
+        for (int t = 0; t < kScG - 1; ++t) yv[t] = yv[t + kScG];
+        xr += kScG * kScRow;
+        yr += kScG * kScRow;
+      }
+    }
+#pragma unroll
+    for (int hf = kScG / 2, m = 16; hf >= 1; hf >>= 1, m >>= 1) {
+      const bool hi = (lane & m) != 0;
+#pragma unroll
+      for (int j = 0; j < hf; ++j) {
+        const float send = hi ? acc[j] : acc[j + hf];
+        const float keep = hi ? acc[j + hf] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    const int bin = kScG * g + ((lane >> 1) & (kScG - 1));
+    if ((lane & 1) == 0 && bin < nb) scores[(int64_t)p * nb + bin] = alpha * acc[0];
+  }
+}
+
 // lag rank of bin l: smaller |l| first, then negative first (the estimator's
 // tie order), used to break exact score ties deterministically.
 __device__ __forceinline__ bool better(float s, int l, float bs, int bl) {
@@ -416,6 +498,7 @@ __global__ void k_topk_any(const float* __restrict__ scores, int npairs, int Lf,
 // flag bit, so every round is a register scan plus one warp reduction.
 constexpr int kTopPer = 32;  // bins per lane held in registers (nb <= 1024)
 
+template <int PER>  // bins per lane (nb <= 32 PER)
 __global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
                        int32_t* __restrict__ centres, float* __restrict__ margin) {
   const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -423,11 +506,11 @@ __global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
   if (p >= npairs) return;
   const int nb = 2 * Lf - 1;
   const float* sc = scores + (int64_t)p * nb;
-  float v[kTopPer];
+  float v[PER];
   uint32_t taken = 0;
   float mx = -INFINITY;
 #pragma unroll
-  for (int i = 0; i < kTopPer; ++i) {
+  for (int i = 0; i < PER; ++i) {
     const int b = lane + 32 * i;
     v[i] = b < nb ? sc[b] : -INFINITY;
     mx = fmaxf(mx, v[i]);
@@ -435,7 +518,7 @@ __global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
   for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   float sum = 0.f;
 #pragma unroll
-  for (int i = 0; i < kTopPer; ++i)
+  for (int i = 0; i < PER; ++i)
     if (lane + 32 * i < nb) sum += __expf(v[i] - mx);
   for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   float top = 0.f;
@@ -443,7 +526,7 @@ __global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
     float bs = -INFINITY;
     int bl = 1 << 30, bi = -1;
 #pragma unroll
-    for (int i = 0; i < kTopPer; ++i) {
+    for (int i = 0; i < PER; ++i) {
       const int b = lane + 32 * i;
       const int l = b - (Lf - 1);
       if (b < nb && !(taken >> i & 1u) && (bl == (1 << 30) || better(v[i], l, bs, bl))) {
@@ -785,6 +868,13 @@ cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
                               float* scores, cudaStream_t st, bool pos_major) {
   if (Lf < 1 || npairs <= 0) return npairs <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  if (Lf <= kSpMaxLf) {
+    auto kp = pos_major ? k_scores_pair<true> : k_scores_pair<false>;
+    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmem);
+    kp<<<npairs, kSpWarps * 32, kSpSmem, st>>>(feat, Lf, params, scores);
+    TDE_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+  }
   auto kern = pos_major ? k_scores<true> : k_scores<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kScSmem);
   const int nb = 2 * Lf - 1;
@@ -797,8 +887,10 @@ cudaError_t launch_cnn_topk(const float* scores, int npairs, int Lf, int32_t* ce
                             float* margin, cudaStream_t st) {
   if (2 * Lf - 1 > 32 * kTopPer)
     k_topk_any<<<(npairs + 3) / 4, 128, 0, st>>>(scores, npairs, Lf, centres, margin);
+  else if (2 * Lf - 1 <= 32 * 16)
+    k_topk<16><<<(npairs + 1) / 2, 64, 0, st>>>(scores, npairs, Lf, centres, margin);
   else
-    k_topk<<<(npairs + 3) / 4, 128, 0, st>>>(scores, npairs, Lf, centres, margin);
+    k_topk<kTopPer><<<(npairs + 1) / 2, 64, 0, st>>>(scores, npairs, Lf, centres, margin);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
