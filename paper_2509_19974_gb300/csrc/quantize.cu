@@ -384,24 +384,32 @@ __global__ void __launch_bounds__(kQT) k_qcand(const QSig* __restrict__ sigs, QW
   const int64_t n4 = vec ? s.n >> 2 : 0;
   const float4* x4 = reinterpret_cast<const float4*>(s.x);
   for (int64_t c0 = (int64_t)blockIdx.x * (kQPer / 4); c0 < n4; c0 += (int64_t)gridDim.x * (kQPer / 4)) {
+    const bool full = c0 + kQPer / 4 <= n4;  // uniform: no per-load bounds in the common case
     float4 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int64_t i = c0 + k * kQT + threadIdx.x;
-      v[k] = i < n4 ? x4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[k] = (full || i < n4) ? x4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     uint32_t hits = 0;  // bit 4k + e: element e of load k
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      if (c0 + k * kQT + threadIdx.x >= n4) continue;
-      const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+      if (!full && c0 + k * kQT + threadIdx.x >= n4) continue;
+      const uint32_t b[4] = {__float_as_uint(v[k].x), __float_as_uint(v[k].y), __float_as_uint(v[k].z),
+                             __float_as_uint(v[k].w)};
       uint32_t packed = 0;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        if (match(__float_as_uint(f[e]) & 0x7FFFFFFFu))
-          hits |= 1u << (4 * k + e);
-        else if (kApply)
-          packed |= ((uint32_t)level_of(f[e]) & 0xFFu) << (8 * e);
+        // bucket test and (for non-candidates) the level, integer-only: the
+        // sign bit picks +-level; +-0 has level 0.  A candidate's byte is a
+        // placeholder that k_qfix overwrites.
+        const uint32_t hi = (b[e] & 0x7FFFFFFFu) >> 19;
+        bool c = false;
+        int lv = 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) c |= hi == pre[m], lv += hi > pre[m];
+        hits |= (uint32_t)c << (4 * k + e);
+        if (kApply) packed |= ((uint32_t)((b[e] >> 31) ? -lv : lv) & 0xFFu) << (8 * e);
       }
       if (kApply) reinterpret_cast<uint32_t*>(s.q)[c0 + k * kQT + threadIdx.x] = packed;
     }
