@@ -1650,7 +1650,7 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
     TDE_COUNT_LAUNCH(1);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && w.T.any_zero) e = launch_mma_zero(B.dw<MmaPair>(w.o_fbpairs), P, 2 * n - 1, st);
+  if (e == cudaSuccess && w.T.any_zero) e = launch_mma_zero(B.dw<MmaPair>(w.o_fbpairs), P, 2 * n - 1, st, nfb);
   if (e == cudaSuccess)
     e = launch_xcorr_mma(B.dw<MmaPair>(w.o_fbpairs), B.dw<MmaItem>(w.o_fbitems), P * nt,
                          B.dw<int>(w.o_counter), 2 * ctx->sm_count, ctx->d_status, st,

@@ -53,52 +53,66 @@ struct MinU64 {
   }
 };
 
+// Pairs y = blockIdx.y, + gridDim.y, ... below the pair count (a device count
+// when the pairs were made on the device: the grid is then small).
+__device__ __forceinline__ int pair_limit(int npairs, const int* d_count) {
+  if (!d_count) return npairs;
+  const int c = *d_count;
+  return c < npairs ? c : npairs;
+}
+
 __global__ void __launch_bounds__(kThreads) k_argmax32(const ArgPair* __restrict__ pairs,
-                                                       unsigned long long* __restrict__ keys,
+                                                       unsigned long long* __restrict__ keys, int npairs,
                                                        const int* __restrict__ d_count) {
-  if (d_count && (int)blockIdx.y >= *d_count) return;
-  const ArgPair P = pairs[blockIdx.y];
-  const int32_t* c = static_cast<const int32_t*>(P.c);
-  unsigned long long best = 0;
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride) {
-    unsigned long long k = pack32(c[i], P.lag_min + i);
-    best = k > best ? k : best;
+  const int lim = pair_limit(npairs, d_count);
+  for (int y = blockIdx.y; y < lim; y += gridDim.y) {
+    const ArgPair P = pairs[y];
+    const int32_t* c = static_cast<const int32_t*>(P.c);
+    unsigned long long best = 0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride) {
+      unsigned long long k = pack32(c[i], P.lag_min + i);
+      best = k > best ? k : best;
+    }
+    best = block_reduce(best, MaxU64());
+    if (threadIdx.x == 0) atomicMax(&keys[2 * y], best);
   }
-  best = block_reduce(best, MaxU64());
-  if (threadIdx.x == 0) atomicMax(&keys[2 * blockIdx.y], best);
 }
 
 __global__ void __launch_bounds__(kThreads) k_argmax64_value(const ArgPair* __restrict__ pairs,
-                                                             unsigned long long* __restrict__ keys,
+                                                             unsigned long long* __restrict__ keys, int npairs,
                                                              const int* __restrict__ d_count) {
-  if (d_count && (int)blockIdx.y >= *d_count) return;
-  const ArgPair P = pairs[blockIdx.y];
-  const long long* c = static_cast<const long long*>(P.c);
-  long long best = LLONG_MIN;
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride)
-    best = c[i] > best ? c[i] : best;
-  best = block_reduce(best, MaxI64());
-  if (threadIdx.x == 0) atomicMax(reinterpret_cast<long long*>(&keys[2 * blockIdx.y]), best);
+  const int lim = pair_limit(npairs, d_count);
+  for (int y = blockIdx.y; y < lim; y += gridDim.y) {
+    const ArgPair P = pairs[y];
+    const long long* c = static_cast<const long long*>(P.c);
+    long long best = LLONG_MIN;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride)
+      best = c[i] > best ? c[i] : best;
+    best = block_reduce(best, MaxI64());
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<long long*>(&keys[2 * y]), best);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_argmax64_lag(const ArgPair* __restrict__ pairs,
-                                                           unsigned long long* __restrict__ keys,
+                                                           unsigned long long* __restrict__ keys, int npairs,
                                                            const int* __restrict__ d_count) {
-  if (d_count && (int)blockIdx.y >= *d_count) return;
-  const ArgPair P = pairs[blockIdx.y];
-  const long long* c = static_cast<const long long*>(P.c);
-  const long long vmax = static_cast<long long>(keys[2 * blockIdx.y]);
-  unsigned long long best = ~0ull;
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride)
-    if (c[i] == vmax) {
-      unsigned long long r = lag_rank(P.lag_min + i);
-      best = r < best ? r : best;
-    }
-  best = block_reduce(best, MinU64());
-  if (threadIdx.x == 0 && best != ~0ull) atomicMin(&keys[2 * blockIdx.y + 1], best);
+  const int lim = pair_limit(npairs, d_count);
+  for (int y = blockIdx.y; y < lim; y += gridDim.y) {
+    const ArgPair P = pairs[y];
+    const long long* c = static_cast<const long long*>(P.c);
+    const long long vmax = static_cast<long long>(keys[2 * y]);
+    unsigned long long best = ~0ull;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride)
+      if (c[i] == vmax) {
+        unsigned long long r = lag_rank(P.lag_min + i);
+        best = r < best ? r : best;
+      }
+    best = block_reduce(best, MinU64());
+    if (threadIdx.x == 0 && best != ~0ull) atomicMin(&keys[2 * y + 1], best);
+  }
 }
 
 __global__ void k_argmax_init(unsigned long long* keys, int npairs, int c64,
@@ -144,14 +158,15 @@ cudaError_t launch_argmax(const ArgPair* d_pairs, int npairs, int64_t max_count,
   int64_t gx = ceil_div64(max_count, (int64_t)kThreads * 16);
   if (gx < 1) gx = 1;
   if (gx > 1024) gx = 1024;
-  dim3 grid((unsigned)gx, npairs);
+  // counted pairs (made on the device): a small grid loops over them
+  dim3 grid((unsigned)gx, d_count ? (npairs < 8 ? npairs : 8) : npairs);
   if (c64) {
-    k_argmax64_value<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, d_count);
+    k_argmax64_value<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, npairs, d_count);
     TDE_COUNT_LAUNCH(1);
-    k_argmax64_lag<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, d_count);
+    k_argmax64_lag<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, npairs, d_count);
     TDE_COUNT_LAUNCH(1);
   } else {
-    k_argmax32<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, d_count);
+    k_argmax32<<<grid, kThreads, 0, st>>>(d_pairs, d_keys, npairs, d_count);
     TDE_COUNT_LAUNCH(1);
   }
   k_argmax_finalize<<<blocks_p, 128, 0, st>>>(d_pairs, d_keys, npairs, c64, d_count);

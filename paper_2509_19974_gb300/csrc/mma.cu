@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                  const int* __restrict__ d_nitems, int* __restrict__ counter,
                  uint32_t* __restrict__ status) {
   const int nitems = d_nitems ? *d_nitems : nitems_arg;
+  if (nitems <= 0) return;  // (a device-made item list can be empty)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -485,16 +486,22 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // Zeroes the outputs of pairs whose tiles are split over several CTAs.
-__global__ void k_zero_outputs(const MmaPair* __restrict__ pairs) {
-  const MmaPair P = pairs[blockIdx.y];
-  if (!P.zero_first) return;
-  const int64_t count = P.lag_max - P.lag_min + 1;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    if (P.c64)
-      static_cast<long long*>(P.c)[i] = 0;
-    else
-      static_cast<int*>(P.c)[i] = 0;
+// Pairs y = blockIdx.y, + gridDim.y, ... below npairs (or the device count
+// d_count when the pairs were made on the device: the grid is then small).
+__global__ void k_zero_outputs(const MmaPair* __restrict__ pairs, int npairs, const int* __restrict__ d_count) {
+  int lim = npairs;
+  if (d_count && *d_count < lim) lim = *d_count;
+  for (int y = blockIdx.y; y < lim; y += gridDim.y) {
+    const MmaPair P = pairs[y];
+    if (!P.zero_first) continue;
+    const int64_t count = P.lag_max - P.lag_min + 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+      if (P.c64)
+        static_cast<long long*>(P.c)[i] = 0;
+      else
+        static_cast<int*>(P.c)[i] = 0;
+    }
   }
 }
 
@@ -1319,12 +1326,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restri
 
 int mma_smem_bytes() { return kSmemBytes8; }
 
-cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st) {
+cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st,
+                            const int* d_count) {
   if (npairs <= 0) return cudaSuccess;
   int64_t gx = ceil_div64(max_count, 256 * 8);
   if (gx > 1024) gx = 1024;
   if (gx < 1) gx = 1;
-  k_zero_outputs<<<dim3((unsigned)gx, npairs), 256, 0, st>>>(d_pairs);
+  const int gy = d_count ? (npairs < 8 ? npairs : 8) : npairs;
+  k_zero_outputs<<<dim3((unsigned)gx, gy), 256, 0, st>>>(d_pairs, npairs, d_count);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

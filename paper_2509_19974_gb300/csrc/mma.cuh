@@ -31,8 +31,10 @@ struct MmaItem {
 };
 
 int mma_smem_bytes();
-// Zeroes the outputs of pairs with zero_first set.
-cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st);
+// Zeroes the outputs of pairs with zero_first set (of the first *d_count
+// pairs when d_count, a device count, is given).
+cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st,
+                            const int* d_count = nullptr);
 // Persistent launch: `grid` CTAs (two per SM fit) take items from *d_counter
 // (zeroed here) in array order; sort items longest first.  d_nitems (device,
 // nullable) overrides the item count when the items are made on the device
