@@ -6,5 +6,5 @@ library under ``paper_2509_19974_gb300`` never does; it has no CPU fallback.
 """
 from .oracle import (  # noqa: F401
     build, quantize, rank_thresholds, xcorr, xcorr_at, argmax, estimate,
-    num_threads, full_lag_range,
+    num_threads, full_lag_range, real_ccf, refine,
 )

@@ -5,6 +5,10 @@ Every function follows the paper (arXiv 2509.19974) literally:
                   the sign-magnitude rank quantizer, Sec. 3.2 "any scheme").
   xcorr/xcorr_at  Eq. (1) on the quantized sequences, direct int64 sums.
   argmax          Algorithm 1's argmax step, ties -> smallest |tau| then tau.
+  real_ccf        Eq. (1) on the original (unquantized) sequences, in float64.
+  refine          Algorithm 1's last steps: the tied set of integer maxima,
+                  re-ranked by the real cross-correlation when it holds several
+                  lags, plus a parabolic sub-sample offset at its representative.
 Pinned by tests/test_oracle_pins.py.
 """
 from __future__ import annotations
@@ -121,3 +125,43 @@ def estimate(x: np.ndarray, y: np.ndarray, bits: int, lag_min: int | None = None
     lag_min = lo if lag_min is None else lag_min
     lag_max = hi if lag_max is None else lag_max
     return argmax(xcorr(qx, qy, lag_min, lag_max), lag_min)
+
+
+def real_ccf(x: np.ndarray, y: np.ndarray, tau: int) -> float:
+    """(x * y)[tau] = sum_n x[n] y[n + tau] over the overlap, float64 (Eq. (1) on the
+    original signals); 0.0 for an empty overlap."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    lo, hi = max(0, -tau), min(x.shape[0], y.shape[0] - tau)
+    if hi <= lo:
+        return 0.0
+    return float(np.dot(x[lo:hi], y[lo + tau: hi + tau]))
+
+
+def refine(x: np.ndarray, y: np.ndarray, c: np.ndarray, lag_min: int) -> dict:
+    """Algorithm 1 after the integer correlation c (lags lag_min ..): the set of
+    lags where c is maximal; when it holds several, the subset where the real
+    cross-correlation of x and y is maximal.  The representative is the set's
+    tie-ruled element (smallest |tau|, then tau).  frac is the vertex offset of
+    the parabola through the real cross-correlation at the representative and
+    its two neighbours (0 when a neighbour has no overlap or the three points
+    are not a strict maximum; clamped to [-0.5, 0.5])."""
+    c = np.asarray(c, dtype=np.int64)
+    vmax = int(c.max())
+    tied = [lag_min + int(i) for i in np.nonzero(c == vmax)[0]]
+    best = tied
+    if len(tied) > 1:
+        r = [real_ccf(x, y, t) for t in tied]
+        rmax = max(r)
+        best = [t for t, v in zip(tied, r) if v == rmax]
+    rep = min(best, key=lambda t: (abs(t), t))
+    r0 = real_ccf(x, y, rep)
+    frac = 0.0
+    nx, ny = len(x), len(y)
+    if -(nx - 1) <= rep - 1 and rep + 1 <= ny - 1:
+        rm, rp = real_ccf(x, y, rep - 1), real_ccf(x, y, rep + 1)
+        den = rm - 2.0 * r0 + rp
+        if den < 0.0 and r0 >= rm and r0 >= rp:
+            frac = min(0.5, max(-0.5, 0.5 * (rm - rp) / den))
+    return {"lag": rep, "value": vmax, "r": r0, "frac": frac, "n_int_ties": len(tied),
+            "n_ties": len(best), "lag_lo": min(best), "lag_hi": max(best)}

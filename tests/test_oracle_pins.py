@@ -281,3 +281,61 @@ def test_estimate_on_synthetic_shift():
     b = synth.single_pair()
     lag, _ = oracle.estimate(b.x[0], b.y[0], 1)
     assert lag == int(b.shift[0])
+
+
+# ---- Algorithm 1's last steps (re-ranking the tied set) and the sub-sample offset
+
+def test_refine_hand_worked_tie():
+    """x = [1, 0, 2] and y = [1, 0, 1, 0, 3] quantize (sign) to [1, 0, 1] and
+    [1, 0, 1, 0, 1]: the integer correlation is 2 at lags 0 and 2 (a tie).  The
+    real one is 1*1 + 2*1 = 3 at lag 0 and 1*1 + 2*3 = 7 at lag 2, so
+    Algorithm 1 returns {2} although the integer tie rule alone says 0."""
+    x = np.array([1.0, 0.0, 2.0], dtype=np.float32)
+    y = np.array([1.0, 0.0, 1.0, 0.0, 3.0], dtype=np.float32)
+    qx, qy = oracle.quantize(x, 1), oracle.quantize(y, 1)
+    lo, hi = oracle.full_lag_range(3, 5)
+    c = oracle.xcorr(qx, qy, lo, hi)
+    assert oracle.argmax(c, lo) == (0, 2)
+    r = oracle.refine(x, y, c, lo)
+    assert (r["lag"], r["value"], r["n_int_ties"], r["n_ties"]) == (2, 2, 2, 1)
+    assert r["r"] == 7.0 and (r["lag_lo"], r["lag_hi"]) == (2, 2)
+    # swapping the weights flips the choice: 1*1 + 2*3 = 7 at lag 0
+    y2 = np.array([1.0, 0.0, 3.0, 0.0, 1.0], dtype=np.float32)
+    assert oracle.refine(x, y2, oracle.xcorr(qx, oracle.quantize(y2, 1), lo, hi), lo)["lag"] == 0
+
+
+def test_refine_real_tie_keeps_the_set():
+    """x = [1, 0, 1], y = [1, 0, 1, 0, 1]: integer and real correlations both
+    tie at lags 0 and 2 (value 2), so the set stays {0, 2}; representative 0."""
+    x = np.array([1.0, 0.0, 1.0], dtype=np.float32)
+    y = np.array([1.0, 0.0, 1.0, 0.0, 1.0], dtype=np.float32)
+    lo, hi = oracle.full_lag_range(3, 5)
+    c = oracle.xcorr(oracle.quantize(x, 1), oracle.quantize(y, 1), lo, hi)
+    r = oracle.refine(x, y, c, lo)
+    assert (r["lag"], r["n_int_ties"], r["n_ties"], r["lag_lo"], r["lag_hi"]) == (0, 2, 2, 0, 2)
+
+
+def test_refine_parabola_vertex():
+    """x = [1, 2], y = [2, 1, 0]: the real correlation is 4, 4, 1 at lags -1,
+    0, 1 (integer: 1, 2, 1, so lag 0).  The parabola through (-1, 4), (0, 4),
+    (1, 1) is -1.5 t^2 - 1.5 t + 4 with its vertex at t = -0.5."""
+    x = np.array([1.0, 2.0], dtype=np.float32)
+    y = np.array([2.0, 1.0, 0.0], dtype=np.float32)
+    lo, hi = oracle.full_lag_range(2, 3)
+    c = oracle.xcorr(oracle.quantize(x, 1), oracle.quantize(y, 1), lo, hi)
+    r = oracle.refine(x, y, c, lo)
+    assert r["lag"] == 0 and r["r"] == 4.0 and r["frac"] == -0.5
+    # a symmetric peak has its vertex on the lag: autocorrelation of [1, 1]
+    z = np.array([1.0, 1.0], dtype=np.float32)
+    cz = oracle.xcorr(oracle.quantize(z, 1), oracle.quantize(z, 1), -1, 1)
+    assert oracle.refine(z, z, cz, -1)["frac"] == 0.0
+
+
+def test_real_ccf_matches_numpy_correlate():
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(37).astype(np.float32)
+    y = rng.standard_normal(23).astype(np.float32)
+    full = np.correlate(y.astype(np.float64), x.astype(np.float64), mode="full")
+    # numpy's full correlate of (y, x) at output k is sum_n y[n + k - (len(x) - 1)] x[n]
+    for tau in range(-(37 - 1), 23):
+        assert abs(oracle.real_ccf(x, y, tau) - full[tau + 36]) < 1e-9
