@@ -194,6 +194,35 @@ tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, const int8_
 tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t lag_min, int64_t count,
                       int64_t* lag_out, int64_t* val_out, tde_stream_t stream);
 
+/* Algorithm 1's last steps (Sec. 3.3, after the argmax): the set of lags
+ * where the integer correlation c is maximal and, when it holds several, its
+ * subset where the real cross-correlation (x * y)[tau] = sum_n x[n] y[n+tau]
+ * of the original signals (Eq. (1) without quantization) is maximal; plus the
+ * sub-sample offset of the real cross-correlation's peak at the set's
+ * representative (the vertex of the parabola through tau - 1, tau, tau + 1).
+ *   x: nx floats, y: ny floats (device, the signals c was computed from);
+ *   c: `count` elements of `dtype` (device), element i holding lag lag_min + i;
+ *   out: one tde_refined (device), written asynchronously:
+ *     lag         the set's representative (smallest |tau|, then tau);
+ *     value       the maximum of c;
+ *     lag_lo/hi   the smallest and largest lag of the set (the paper counts an
+ *                 estimate correct only if every lag of the set is);
+ *     n_int_ties  lags where c is maximal; n_ties: size of the re-ranked set;
+ *     r           (x * y)[lag] in FP64 (exact FP32 products, FP64 sums in a
+ *                 fixed order; real ties are exact FP64 equality);
+ *     frac        parabola vertex offset in [-0.5, 0.5]; 0 when a neighbour
+ *                 has no overlap or the three values are not a strict peak.
+ * The work is one FP64 dot per tied lag.  Uses a context workspace of
+ * 16 * count bytes.  Errors: TDE_ERR_INVALID for null pointers, bad dtype,
+ * sizes <= 0 or lags outside [-(nx-1), ny-1]. */
+typedef struct tde_refined {
+  int64_t lag, value, lag_lo, lag_hi, n_int_ties, n_ties;
+  double r, frac;
+} tde_refined;
+tde_status tde_refine(tde_ctx* ctx, const float* x, int64_t nx, const float* y, int64_t ny,
+                      const void* c, int dtype, int64_t lag_min, int64_t count, tde_refined* out,
+                      tde_stream_t stream);
+
 /* Algorithm 1 for one pair.  x: nx floats, y: ny floats (device).
  * Lags lag_min..lag_max as in tde_xcorr_int.  lag_out[0], val_out[0]: device
  * int64.  Intermediate quantized signals and correlations live in the

@@ -13,6 +13,7 @@
 #include "mma.cuh"
 #include "fftcmp.cuh"
 #include "ntt.cuh"
+#include "refine.cuh"
 #include "cnn.cuh"
 
 struct tde_ctx {
@@ -895,6 +896,41 @@ extern "C" tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t
   cudaError_t e = A.launch(B, st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "argmax launch");
   return TDE_OK;
+}
+
+extern "C" tde_status tde_refine(tde_ctx* ctx, const float* x, int64_t nx, const float* y, int64_t ny,
+                                 const void* c, int dtype, int64_t lag_min, int64_t count,
+                                 tde_refined* out, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!x || !y || !c || !out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (dtype != TDE_I32 && dtype != TDE_I64) return set_err(ctx, TDE_ERR_INVALID, "unknown dtype");
+  if (nx <= 0 || ny <= 0 || count <= 0) return set_err(ctx, TDE_ERR_INVALID, "sizes must be positive");
+  if (lag_min < -(nx - 1) || lag_min + count - 1 > ny - 1)
+    return set_err(ctx, TDE_ERR_INVALID, "lags outside [-(nx-1), ny-1]");
+  const int64_t lim = INT32_MAX;
+  if (lag_min < -lim || lag_min + count - 1 > lim)
+    return set_err(ctx, TDE_ERR_UNSUPPORTED, "lags beyond +-(2^31-1) are not supported");
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout L;
+  ArgStage A;
+  A.plan(L, 1, count, dtype == TDE_I64);
+  const size_t o_lv = L.w<int64_t>(2);
+  const size_t o_list = L.w<int64_t>((size_t)count);
+  const size_t o_r = L.w<double>((size_t)count);
+  const size_t o_n = L.w<unsigned long long>(1);
+  Bases B;
+  tde_status s = realize(ctx, L, &B);
+  if (s != TDE_OK) return s;
+  int64_t* lv = B.dw<int64_t>(o_lv);  // [lag, value] of the maximum
+  A.set(B, 0, c, lag_min, count, lv, lv + 1);
+  if ((s = stage_upload(ctx, B.ddesc, L.desc, st)) != TDE_OK) return s;
+  cudaError_t e = A.launch(B, st);
+  if (e == cudaSuccess)
+    e = launch_refine(x, nx, y, ny, c, dtype == TDE_I64, lag_min, count, lv + 1, B.dw<int64_t>(o_list),
+                      B.dw<double>(o_r), B.dw<unsigned long long>(o_n), out, ctx->sm_count, st);
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "refine launch");
 }
 
 namespace {

@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -33,7 +34,7 @@ EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error"
            "tde_model_get", "tde_model_set", "tde_train_step", "tde_propose",
            "tde_estimate_learned", "tde_synth_pairs", "tde_autotune", "tde_autotune_table",
            "tde_autotune_load", "tde_ctx_pick_engine", "tde_xcorr_windows",
-           "tde_learned_create", "tde_learned_run", "tde_learned_destroy")
+           "tde_learned_create", "tde_learned_run", "tde_learned_destroy", "tde_refine")
 
 
 class TdeError(RuntimeError):
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_learned_create": ([p, p, p, p, i32, i32, f32, p, p, p, ctypes.POINTER(p)], st),
         "tde_learned_run": ([p, p], st),
         "tde_learned_destroy": ([p], st),
+        "tde_refine": ([p, p, i64, p, i64, p, i32, i64, i64, p, p], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -183,6 +185,9 @@ class Context:
 
     def argmax(self, c, lag_min, stream=None):
         return tde_argmax(self, c, lag_min, stream)
+
+    def refine(self, x, y, c, lag_min, stream=None):
+        return tde_refine(self, x, y, c, lag_min, stream)
 
     def xcorr_fft32(self, x, y, lag_min=None, lag_max=None, c_out=None, stream=None):
         return tde_xcorr_fft32(self, x, y, lag_min, lag_max, c_out, stream)
@@ -386,6 +391,32 @@ def tde_argmax(ctx: Context, c, lag_min, stream=None):
     ctx.check(ctx.lib.tde_argmax(ctx.handle, c.data_ptr(), code, int(lag_min), c.numel(),
                                  lag.data_ptr(), val.data_ptr(), _stream(stream)))
     return lag, val
+
+
+REFINED_FIELDS = ("lag", "value", "lag_lo", "lag_hi", "n_int_ties", "n_ties", "r", "frac")
+
+
+def tde_refine(ctx: Context, x, y, c, lag_min, stream=None) -> dict:
+    """Algorithm 1's last steps for c (the integer correlation of the
+    quantized x, y; element i = lag lag_min + i): the tied set of maxima
+    re-ranked by the real cross-correlation of x and y, its representative,
+    bounds and sizes, the real value and the sub-sample offset (synchronises
+    the stream to read the result)."""
+    _need(x, torch.float32, "x")
+    _need(y, torch.float32, "y")
+    if c.dtype not in (torch.int32, torch.int64):
+        raise TypeError("c must be int32 or int64")
+    _need(c, c.dtype, "c")
+    out = torch.zeros(8, dtype=torch.int64, device=c.device)  # one tde_refined (64 bytes)
+    code = TDE_I64 if c.dtype == torch.int64 else TDE_I32
+    ctx.check(ctx.lib.tde_refine(ctx.handle, x.data_ptr(), x.numel(), y.data_ptr(), y.numel(),
+                                 c.data_ptr(), code, int(lag_min), c.numel(), out.data_ptr(),
+                                 _stream(stream)))
+    ctx.sync(stream)
+    h = out.cpu()
+    ints = [int(v) for v in h[:6]]
+    dbl = h[6:].numpy().view(np.float64)
+    return dict(zip(REFINED_FIELDS, ints + [float(dbl[0]), float(dbl[1])]))
 
 
 def tde_xcorr_fft32(ctx: Context, x, y, lag_min=None, lag_max=None, c_out=None, stream=None):
