@@ -440,10 +440,20 @@ struct MmaStage {
   size_t o_pairs = 0, o_items = 0, o_counter = 0;
   std::vector<MmaItem> items;
   std::vector<int> zero_first;
-  void plan(Layout& L, const std::vector<Job>& jobs) {
+  // split_small: a plan with few items (fewer than half the SMs) cuts its K
+  // ranges into shorter segments (>= kMinSeg samples) so that its items spread
+  // over the SMs; the partial sums are added with integer atomics as usual.
+  static constexpr int64_t kMinSeg = 2 * kMmaChunk;
+  void plan(Layout& L, const std::vector<Job>& jobs, bool split_small = true) {
     njobs = (int)jobs.size();
     items.clear();
     zero_first.assign(njobs, 0);
+    struct Tile {
+      int job;
+      int64_t T0, klo, khi;
+    };
+    std::vector<Tile> tiles;
+    int64_t n_default = 0;  // items at the default segment length
     for (int i = 0; i < njobs; ++i) {
       const Job& j = jobs[i];
       max_count = std::max<int64_t>(max_count, j.lag_max - j.lag_min + 1);
@@ -461,16 +471,32 @@ struct MmaStage {
           zero_first[i] = 1;
           continue;
         }
-        const int64_t nseg = ceil_div64(khi - klo, kMmaKs);
-        const int64_t seg = ceil_div64(ceil_div64(khi - klo, nseg), kMmaChunk) * kMmaChunk;
-        if (nseg > 1) zero_first[i] = 1;
-        for (int64_t s = 0; s < nseg; ++s) {
-          const int64_t ks = klo + s * seg, ke = std::min(khi, ks + seg);
-          if (ke > ks) items.push_back(MmaItem{i, nseg == 1 ? 1 : 0, T0, ks, ke});
-        }
+        tiles.push_back(Tile{i, T0, klo, khi});
+        n_default += ceil_div64(khi - klo, kMmaKs);
       }
-      any_zero |= zero_first[i];
     }
+    int64_t seg_cap = kMmaKs;
+    if (split_small && !tiles.empty()) {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+          n_default < sms / 2) {
+        int64_t total = 0;
+        for (const Tile& t : tiles) total += t.khi - t.klo;
+        const int64_t want = ceil_div64(ceil_div64(total, sms), kMmaChunk) * kMmaChunk;
+        seg_cap = std::min<int64_t>(kMmaKs, std::max<int64_t>(kMinSeg, want));
+      }
+    }
+    for (const Tile& t : tiles) {
+      const int64_t nseg = ceil_div64(t.khi - t.klo, seg_cap);
+      const int64_t seg = ceil_div64(ceil_div64(t.khi - t.klo, nseg), kMmaChunk) * kMmaChunk;
+      if (nseg > 1) zero_first[t.job] = 1;
+      for (int64_t s = 0; s < nseg; ++s) {
+        const int64_t ks = t.klo + s * seg, ke = std::min(t.khi, ks + seg);
+        if (ke > ks) items.push_back(MmaItem{t.job, nseg == 1 ? 1 : 0, t.T0, ks, ke});
+      }
+    }
+    for (int i = 0; i < njobs; ++i) any_zero |= zero_first[i];
     // Longest first: the persistent CTAs then finish close together.
     std::stable_sort(items.begin(), items.end(), [](const MmaItem& a, const MmaItem& b) {
       return a.ke - a.ks > b.ke - b.ks;
@@ -1608,7 +1634,7 @@ void learned_plan(LearnedWork* w, int npairs, int64_t n, int bits, float theta) 
   w->o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
   w->o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * kCnnWin);
   std::vector<Job> one{Job{nullptr, nullptr, n, n, -(n - 1), n - 1, nullptr, 0}};
-  w->T.plan(L, one);
+  w->T.plan(L, one, false);  // replicated per fallback pair: keep the default segments
   const int nt = w->T.nitems;
   w->o_fbidx = L.w<int32_t>((size_t)npairs);
   w->o_nfb = L.w<int>(1);
