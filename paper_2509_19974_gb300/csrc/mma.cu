@@ -369,28 +369,44 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 1 || warp == 2) {
       // Slot producers: row o = 8 e + r (slot e, row r) is x[ks - 127 + o .. + 15];
       // chunk 0 writes o in [0, 240), chunk c >= 1 writes [128 c + 112, 128 c + 240).
-      const int t = threadIdx.x - 32;
+      // Lane (octet t / 8, row r = t % 8) writes row r of 2 consecutive slots
+      // (128-byte runs per store): x bytes [xoff + 8 e + r, + 16) for e = e0,
+      // e0 + 1, as aligned word pairs of the stream realigned once by
+      // (xoff + r) mod 8 with byte permutes.
+      const int t = threadIdx.x - 32, r = t & 7;
       for (int c = 0; c < nchunks; ++c) {
         const int64_t prev = cc0 + c - 5;
-        if (prev >= 0 && !mbar_wait(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
-          ok = false;
-          break;
+        if (prev >= 0) {
+          const uint32_t cb = cmt_bar + 8 * (uint32_t)(prev % kNB), ph = (uint32_t)((prev / kNB) & 1);
+          if (!mbar_try(cb, ph) && !mbar_wait(cb, ph)) {
+            ok = false;
+            break;
+          }
         }
-        const int o_first = c == 0 ? t : 128 * c + 112 + t;
-        const int o_end = c == 0 ? 240 : 128 * c + 240;
-        for (int o = o_first; o < o_end; o += kProducers) {
-          const uint32_t pa = xs + xoff + (uint32_t)o;
-          const uint32_t al = pa & ~7u, sh = 8u * (pa & 7u);
-          const uint64_t w0 = ld_shared_u64(al), w1 = ld_shared_u64(al + 8u), w2 = ld_shared_u64(al + 16u);
-          const uint64_t lo = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
-          const uint64_t hi = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
-          const int e = o >> 3, r = o & 7;
-          const int ps = e % kRing8;
-          const uint32_t a = slots + 128u * ps + 16u * r;
-          st_shared_v4(a, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-          if (ps < kMirror8)
-            st_shared_v4(a + 128u * kRing8, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
-                         (uint32_t)(hi >> 32));
+        const int e_lo = c == 0 ? 0 : 16 * c + 14, e_hi = 16 * c + 30;
+        for (int e0 = e_lo + 2 * (t >> 3); e0 < e_hi; e0 += 2 * (kProducers / 8)) {
+          const uint32_t pos = xoff + 8u * (uint32_t)e0 + (uint32_t)r;
+          const uint32_t al = xs + (pos & ~7u);
+          uint32_t u[8], a[6];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint64_t w = ld_shared_u64(al + 8u * i);
+            u[2 * i] = (uint32_t)w, u[2 * i + 1] = (uint32_t)(w >> 32);
+          }
+          const bool wo = (pos & 4u) != 0;
+          const uint32_t sel = 0x3210u + 0x1111u * (pos & 3u);
+#pragma unroll
+          for (int j = 0; j < 6; ++j)
+            a[j] = __byte_perm(wo ? u[j + 1] : u[j], wo ? u[j + 2] : u[j + 1], sel);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            if (e0 + k >= e_hi) break;
+            const uint32_t ps = (uint32_t)(e0 + k) % (uint32_t)kRing8;
+            const uint32_t ad = slots + 128u * ps + 16u * (uint32_t)r;
+            st_shared_v4(ad, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
+            if (ps < (uint32_t)kMirror8)
+              st_shared_v4(ad + 128u * kRing8, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
+          }
         }
         fence_proxy_async();
         mbar_arrive(full_bar + 8 * (uint32_t)((cc0 + c) % kNB));
@@ -405,9 +421,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         glo[g] = (lo > 0 ? lo : 0) - ks;
         ghi[g] = (hi < P.nx + 127 ? hi : P.nx + 127) - ks;
       }
+      const uint64_t da0 = sdesc(slots, 256, 128, 0, 0);  // + ring slot * 8
+      const uint64_t db0 = sdesc(yr, 16, 1024, 2, 0);     // + row * 8
       for (int c = 0; c < nchunks; ++c) {
         const int64_t cc = cc0 + c;
-        ok = __all_sync(0xffffffffu, mbar_wait(full_bar + 8 * (uint32_t)(cc % kNB), (uint32_t)((cc / kNB) & 1)));
+        {
+          const uint32_t fb = full_bar + 8 * (uint32_t)(cc % kNB), ph = (uint32_t)((cc / kNB) & 1);
+          ok = __all_sync(0xffffffffu, mbar_try(fb, ph) || mbar_wait(fb, ph));
+        }
         if (!ok) break;
         tc_fence_after();
         const int64_t kc = (int64_t)kKc8 * c;
@@ -421,15 +442,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (gb >= ga && lane == 0) {
           const uint32_t idesc = idesc8_for(kGroupCols * (gb - ga + 1));
           const int64_t row0 = u_s + c - r_lo + kGroupCols * ga;
-          const uint32_t a_start = slots + 128u * (uint32_t)((16 * c) % kRing8);
-          const uint32_t b_row = yr + 128u * (uint32_t)row0;
+          const uint64_t ad = da0 + 8u * (uint32_t)((16 * c) % kRing8);
+          const uint64_t bd = db0 + 8u * (uint32_t)row0;
           const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
 #pragma unroll
-          for (int s2 = 0; s2 < 4; ++s2) {
-            const uint64_t ad = sdesc(a_start + 512u * s2, 256, 128, 0, 0);
-            const uint64_t bd = sdesc(b_row + 32u * s2, 16, 1024, 2, 0);
-            mma_e4m3(d_col, ad, bd, idesc, 1u);
-          }
+          for (int s2 = 0; s2 < 4; ++s2) mma_e4m3(d_col, ad + 32u * s2, bd + 2u * s2, idesc, 1u);
         }
         if (lane == 0) mma_commit(cmt_bar + 8 * (uint32_t)(cc % kNB));
         __syncwarp();
