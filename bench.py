@@ -57,7 +57,7 @@ FP8_OVER_BF16 = 2.0
 # DRAM bytes (read + write) per launch of each form's dominant kernel, from one
 # ncu capture of this bench's workload (profiles/); keyed by (kernel, pairs,
 # N, bits).  Cleared whenever the kernel changes.
-TRAFFIC = {("mma", 256, 65536, 2): 307.9e6, ("win", 256, 65536, 2): 35.8e6}
+TRAFFIC = {("mma", 256, 65536, 2): 307.7e6, ("win", 256, 65536, 2): 35.8e6}
 CKPT = os.path.join(ROOT, "paper_2509_19974_gb300", "models", "proposal_n65536_b2.npz")
 POPC_PER_SM_CLK = 16  # POPC issue rate per SM per clock
 
