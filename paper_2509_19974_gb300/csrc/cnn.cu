@@ -10,12 +10,16 @@
 // The windows' exact correlation runs on the tensor cores
 // (launch_xcorr_mma_windows in mma.cu); this file holds their argmax.
 //
-// All CNN arithmetic is FP32 with BF16-rounded weights; the backward pass is
-// deterministic (per-signal partial sums reduced in a fixed order, no float
-// atomics).  Shapes: conv layers tile 128 output positions x 32 channels per
-// CTA; a warp's 32 lanes are the 32 output channels (forward) or input
-// channels (data gradient), so shared-memory weight reads are contiguous and
-// activation reads are broadcasts.
+// Weights are BF16-rounded everywhere and every sum is FP32.  Inference runs
+// its four conv layers on tcgen05 (mma.cu: k_conv1_tc, k_conv_tc) with BF16
+// activations between layers; the training forward keeps FP32 activations
+// (the first layer in FP32 FMA, the 32-channel layers as mma.sync BF16 tiles
+// with FP32 accumulation), and the backward pass is deterministic (per-signal
+// partial sums reduced in a fixed order, no float atomics).  Training shapes:
+// conv layers tile 128 output positions x 32 channels per CTA; a warp's 32
+// lanes are the 32 output channels (forward) or input channels (data
+// gradient), so shared-memory weight reads are contiguous and activation
+// reads are broadcasts.
 #include <cstring>
 
 #include "cnn.cuh"
