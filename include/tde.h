@@ -61,7 +61,7 @@ enum {
   TDE_ENGINE_AUTO = 0, /* pick by length and bits */
   TDE_ENGINE_POPC = 1, /* bit-plane AND/XOR + popcount direct sums */
   TDE_ENGINE_MMA = 2,  /* Toeplitz-as-GEMM on the tcgen05 tensor cores */
-  TDE_ENGINE_NTT = 3   /* two-prime number-theoretic transform + CRT */
+  TDE_ENGINE_NTT = 3   /* number-theoretic transform: one prime, or two + CRT */
 };
 
 /* Element types of the "dtype" arguments. */
@@ -92,6 +92,14 @@ const char* tde_last_error(const tde_ctx* ctx);
  * engine's main kernel is bracketed by two CUDA events on its stream (the
  * events are the context's; no caller memory is touched). */
 tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
+
+/* Prime count of the NTT engine (Sec. 3.2's multimodular route), for the
+ * plans made after this call.  nprimes = 0 (the default): modulo one prime
+ * p0 = 15 * 2^27 + 1 wherever every value fits its centred residues
+ * (shorter length * largest level magnitude^2 <= (p0 - 1) / 2), else two
+ * primes recombined by the Chinese remainder theorem; nprimes = 2: always
+ * two.  Both are exact.  TDE_ERR_INVALID for any other value. */
+tde_status tde_ctx_set_ntt_primes(tde_ctx* ctx, int nprimes);
 
 /* Counters since the previous read, then reset: kernel launches this context
  * enqueued (host pointer *kernel_launches), engine-kernel launches

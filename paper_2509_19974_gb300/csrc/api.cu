@@ -34,6 +34,7 @@ struct tde_ctx {
   int64_t launches = 0, engine_launches = 0;
   FftPlan fft;
   uint32_t* ntt_tables[kNttMaxLog + 1] = {};  // per log2 length, 8 * N uint32
+  bool ntt_two_primes = false;                 // NTT engine: CRT even where one prime suffices
   std::vector<tde_tune_entry> tune;           // autotuner table (empty: built-in rule)
 };
 
@@ -259,6 +260,14 @@ extern "C" tde_status tde_ctx_sync(tde_ctx* ctx, tde_stream_t stream) {
 extern "C" tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable) {
   if (!ctx) return TDE_ERR_INVALID;
   ctx->profile = enable != 0;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_ctx_set_ntt_primes(tde_ctx* ctx, int nprimes) {
+  if (!ctx) return TDE_ERR_INVALID;
+  if (nprimes != 0 && nprimes != 2)
+    return set_err(ctx, TDE_ERR_INVALID, "nprimes must be 0 (automatic) or 2, got %d", nprimes);
+  ctx->ntt_two_primes = nprimes == 2;
   return TDE_OK;
 }
 
@@ -618,45 +627,50 @@ struct NttStage {
   bool ok = true;
   std::vector<NttPlanPair> pp;
   size_t o_pairs = 0;
-  // per log2 length: template jobs, block jobs and their buffers
+  // per (log2 length, primes): template jobs, block jobs and their buffers
   struct Group {
-    int logn;
+    int logn, nprimes;
     std::vector<int> pairs;
     size_t o_tjobs = 0, o_bjobs = 0;
     int ntemplates = 0, nblocks = 0;
     std::vector<size_t> o_tbuf, o_bbuf;
   };
   std::vector<Group> groups;
-  void plan(Layout& L, const std::vector<Job>& jobs) {
+  // bits: the levels' width (largest magnitude 1, 1, 7 for b = 1, 2, 4);
+  // two_primes: CRT even where one prime suffices.
+  void plan(Layout& L, const std::vector<Job>& jobs, int bits, bool two_primes) {
     njobs = (int)jobs.size();
     pp.assign(njobs, NttPlanPair{});
     groups.clear();
+    const int64_t kmax = bits == 4 ? 7 : 1;
     for (int i = 0; i < njobs; ++i) {
       if (!ntt_plan_pair(jobs[i], &pp[i])) {
         ok = false;
         return;
       }
+      const int nq = (!two_primes && ntt_one_prime_ok(pp[i].nt, kmax)) ? 1 : 2;
       Group* g = nullptr;
       for (Group& x : groups)
-        if (x.logn == pp[i].logn) g = &x;
+        if (x.logn == pp[i].logn && x.nprimes == nq) g = &x;
       if (!g) {
         groups.push_back(Group{});
         g = &groups.back();
         g->logn = pp[i].logn;
+        g->nprimes = nq;
       }
       g->pairs.push_back(i);
     }
     o_pairs = L.d<NttPairOut>(njobs);
     for (Group& g : groups) {
-      const size_t N = (size_t)1 << g.logn;
+      const size_t words = (size_t)g.nprimes << g.logn;
       g.ntemplates = (int)g.pairs.size();
       g.nblocks = 0;
       for (int i : g.pairs) g.nblocks += (int)pp[i].blocks.size();
       g.o_tjobs = L.d<NttJob>(g.ntemplates);
       g.o_bjobs = L.d<NttJob>(g.nblocks);
       g.o_tbuf.clear(), g.o_bbuf.clear();
-      for (int t = 0; t < g.ntemplates; ++t) g.o_tbuf.push_back(L.w<uint32_t>(2 * N));
-      for (int b = 0; b < g.nblocks; ++b) g.o_bbuf.push_back(L.w<uint32_t>(2 * N));
+      for (int t = 0; t < g.ntemplates; ++t) g.o_tbuf.push_back(L.w<uint32_t>(words));
+      for (int b = 0; b < g.nblocks; ++b) g.o_bbuf.push_back(L.w<uint32_t>(words));
     }
   }
   void fill(const Bases& B, const std::vector<Job>& jobs) {
@@ -686,11 +700,12 @@ struct NttStage {
     for (const Group& g : groups) {
       NttTables T;
       if (ntt_tables(ctx, g.logn, &T) != TDE_OK) return cudaErrorMemoryAllocation;
-      cudaError_t e = launch_ntt_templates(B.dd<NttJob>(g.o_tjobs), g.ntemplates, g.logn, T, st);
+      cudaError_t e = launch_ntt_templates(B.dd<NttJob>(g.o_tjobs), g.ntemplates, g.logn,
+                                           g.nprimes, T, st);
       if (e != cudaSuccess) return e;
       EngineTimer t(ctx, st);
       e = launch_ntt_blocks(B.dd<NttJob>(g.o_bjobs), g.nblocks, B.dd<NttPairOut>(o_pairs), g.logn,
-                            T, st);
+                            g.nprimes, T, st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -708,15 +723,17 @@ struct XcorrStage {
   std::vector<Job>& list(int e) {
     return e == TDE_ENGINE_MMA ? mma_jobs : (e == TDE_ENGINE_NTT ? ntt_jobs : popc_jobs);
   }
-  // False if some job cannot be served by its engine.
-  bool plan(Layout& L, const std::vector<Job>& jobs, const std::vector<int>& engines, int b) {
+  // False if some job cannot be served by its engine.  ntt_two_primes: the
+  // NTT engine recombines two primes even where one suffices.
+  bool plan(Layout& L, const std::vector<Job>& jobs, const std::vector<int>& engines, int b,
+            bool ntt_two_primes) {
     bits = b;
     eng = engines;
     popc_jobs.clear(), mma_jobs.clear(), ntt_jobs.clear();
     for (size_t i = 0; i < jobs.size(); ++i) list(eng[i]).push_back(jobs[i]);
     popc.plan(L, popc_jobs, bits);
     mma.plan(L, mma_jobs);
-    ntt.plan(L, ntt_jobs);
+    ntt.plan(L, ntt_jobs, bits, ntt_two_primes);
     return ntt.ok;
   }
   // Binds pointers (known after realize) and writes the descriptors.
@@ -885,7 +902,7 @@ extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, 
   std::vector<Job> jobs{Job{qx, qy, nx, ny, lag_min, lag_max, c_out, out_dtype == TDE_I64}};
   Layout L;
   XcorrStage E;
-  if (!E.plan(L, jobs, std::vector<int>{eng}, bits))
+  if (!E.plan(L, jobs, std::vector<int>{eng}, bits, ctx->ntt_two_primes))
     return set_err(ctx, TDE_ERR_UNSUPPORTED,
                    "NTT engine: the shorter signal needs a transform above 2^%d",
                    kNttMaxLog);
@@ -1018,7 +1035,7 @@ tde_status batch_plan(tde_ctx* ctx, const tde_pair_desc* descs, int npairs, int 
   for (int p = 0; p < npairs; ++p)
     w->jobs[p] = Job{nullptr, nullptr, descs[p].nx, descs[p].ny, descs[p].lag_min,
                      descs[p].lag_max, nullptr, 0};
-  if (!w->E.plan(w->L, w->jobs, w->engs, bits))
+  if (!w->E.plan(w->L, w->jobs, w->engs, bits, ctx->ntt_two_primes))
     return set_err(ctx, TDE_ERR_UNSUPPORTED,
                    "NTT engine: a pair's shorter signal exceeds the largest transform (2^%d)",
                    kNttMaxLog);
@@ -1903,7 +1920,8 @@ extern "C" tde_status tde_autotune(tde_ctx* ctx, int bits, const int64_t* n,
                       c + (int64_t)b * lags, 0};
       Layout L;
       XcorrStage E;
-      if (!E.plan(L, jobs, std::vector<int>(B, eng), bits)) continue;  // engine cannot serve it
+      if (!E.plan(L, jobs, std::vector<int>(B, eng), bits, ctx->ntt_two_primes))
+        continue;  // engine cannot serve it
       Bases Bs;
       if (realize(ctx, L, &Bs) != TDE_OK) {
         cudaGetLastError();

@@ -1,6 +1,7 @@
 // ntt.cuh -- host/device interface of the number-theoretic-transform
-// correlation engine (ntt.cu): exact integer correlation modulo two primes
-// below 2^31, recombined by the Chinese remainder theorem.
+// correlation engine (ntt.cu): exact integer correlation modulo one prime
+// below 2^31 when the result's bound allows, else modulo two, recombined by
+// the Chinese remainder theorem.
 #pragma once
 
 #include "common.cuh"
@@ -10,6 +11,13 @@
 constexpr uint32_t kNttP0 = 2013265921u;
 constexpr uint32_t kNttP1 = 2113929217u;
 constexpr int kNttMinLog = 10, kNttMaxLog = 19;  // column pass: N2 <= 512 in shared memory
+
+// One prime suffices when every correlation value fits the centred residues
+// of p0: |R[k]| <= nt * kmax^2 <= (p0 - 1) / 2, nt the template's length and
+// kmax the largest level magnitude.
+inline bool ntt_one_prime_ok(int64_t nt, int64_t kmax) {
+  return nt * kmax * kmax <= (int64_t)(kNttP0 - 1) / 2;
+}
 
 // Per-prime tables for transform length N = 2^logn (device pointers):
 // tw[i] = w^i and its Shoup companion floor(tw * 2^32 / p); itw[i] =
@@ -22,8 +30,8 @@ struct NttTables {
 };
 
 // One transform: the (reversed, zero-padded) template of a pair, or one
-// overlap-save block of the other signal.  buf holds 2 * N uint32 (prime 0
-// then prime 1).
+// overlap-save block of the other signal.  buf holds nprimes * N uint32
+// (prime 0, then prime 1 if used).
 struct NttJob {
   const int8_t* src;
   int64_t nsrc;
@@ -37,7 +45,7 @@ struct NttJob {
 // Per pair: R[k] = sum_j t[j] a[k + j] is computed for the template t (the
 // shorter signal) against a (the other); lag tau = sign * k.
 struct NttPairOut {
-  const uint32_t* spec;  // template spectrum, Montgomery form, 2 * N uint32
+  const uint32_t* spec;  // template spectrum, Montgomery form, nprimes * N uint32
   void* c;
   int64_t lag_min, lag_max;
   int32_t c64;
@@ -48,12 +56,13 @@ struct NttPairOut {
 // into host memory `out` (8 * N uint32).
 void ntt_host_tables(int logn, uint32_t* out);
 
-// Launches the three passes over `njobs` transforms of length 2^logn:
-// templates (jobs with is_template) become spectra in their buf; blocks are
-// multiplied by their pair's spectrum, transformed back and written to c.
-// tmpl/blk: device job arrays; the template jobs must finish first (same
-// stream order guarantees it).
-cudaError_t launch_ntt_templates(const NttJob* d_jobs, int njobs, int logn, const NttTables& T,
-                                 cudaStream_t st);
+// Launches the passes over `njobs` transforms of length 2^logn modulo
+// `nprimes` (1: p0, the caller has checked ntt_one_prime_ok for every pair;
+// 2: p0 and p1): templates (jobs with is_template) become spectra in their
+// buf; blocks are multiplied by their pair's spectrum, transformed back and
+// written to c.  d_jobs: device job array; the template jobs must finish
+// first (same stream order guarantees it).
+cudaError_t launch_ntt_templates(const NttJob* d_jobs, int njobs, int logn, int nprimes,
+                                 const NttTables& T, cudaStream_t st);
 cudaError_t launch_ntt_blocks(const NttJob* d_jobs, int njobs, const NttPairOut* d_pairs,
-                              int logn, const NttTables& T, cudaStream_t st);
+                              int logn, int nprimes, const NttTables& T, cudaStream_t st);
