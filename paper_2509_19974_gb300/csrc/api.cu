@@ -1320,14 +1320,17 @@ struct CnnPlan {
   float* layer_in(const Bases& B, int l) const {
     return l == 0 ? B.dw<float>(o_d) : B.dw<float>(o_out[l - 1]);
   }
+  // scores = false (inference only): stop at the features, for a caller
+  // that scores them itself.
   cudaError_t forward(const Bases& B, const tde_model* m, const int8_t* q, int64_t n, bool train,
-                      uint32_t* status, cudaStream_t st, uint8_t* qe = nullptr) const {
+                      uint32_t* status, cudaStream_t st, uint8_t* qe = nullptr,
+                      bool scores = true) const {
     if (!train) {
       uint16_t* act[kCnnLayers - 1];
       for (int l = 0; l + 1 < kCnnLayers; ++l) act[l] = B.dw<uint16_t>(o_act[l]);
       cudaError_t e = launch_cnn_infer(q, n, 2 * P, m->wbf, m->params, act,
                                        B.dw<float>(o_out[kCnnLayers - 1]), qe, status, st);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && scores)
         e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
                               B.dw<float>(o_scores), st, true);
       return e;
@@ -1358,14 +1361,7 @@ __global__ void k_make_windows(const int32_t* __restrict__ centres, int npairs, 
                                int32_t* __restrict__ cbuf, int stride, WinJob* __restrict__ jobs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npairs * kCnnTopK) return;
-  const int64_t c = centres[i];
-  int64_t lo = c - kCnnBin / 2, hi = c + kCnnBin / 2;
-  const int64_t first = lo;
-  if (lo < -(n - 1)) lo = -(n - 1);
-  if (hi > n - 1) hi = n - 1;
-  // an empty window (hi < lo) writes nothing; keep its pointer in range
-  const int64_t off = hi >= lo ? lo - first : 0;
-  jobs[i] = WinJob{lo, hi, cbuf + (int64_t)i * stride + off};
+  jobs[i] = win_job_of(centres[i], n, cbuf + (int64_t)i * stride);
 }
 
 
@@ -1694,17 +1690,26 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   WinJob* jobs = B.dw<WinJob>(w.o_jobs);
   cudaError_t e = w.Q.launch(B, ctx->d_status, st);
   uint8_t* qe = B.dw<uint8_t>(w.o_qe);
-  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, ctx->d_status, st, qe);
-  if (e == cudaSuccess) e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
-  if (e == cudaSuccess) {
-    k_make_windows<<<(P * kCnnTopK + 255) / 256, 256, 0, st>>>(cent, P, n, B.dw<int32_t>(w.o_cwin),
-                                                               kCnnWin, jobs);
-    TDE_COUNT_LAUNCH(1);
-    e = cudaGetLastError();
+  // features up to kCnnFusedMaxLf: scores, top 8, window jobs and their
+  // zeroed outputs in one launch; longer ones in separate steps
+  const bool fused = w.C.Lf <= kCnnFusedMaxLf;
+  if (e == cudaSuccess) e = w.C.forward(B, m, qbuf, n, false, ctx->d_status, st, qe, !fused);
+  if (e == cudaSuccess && fused)
+    e = launch_cnn_scores_propose(B.dw<float>(w.C.o_out[kCnnLayers - 1]), P, w.C.Lf, m->params,
+                                  B.dw<float>(w.C.o_scores), cent, marg, jobs,
+                                  B.dw<int32_t>(w.o_cwin), n, st);
+  if (e == cudaSuccess && !fused) {
+    e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
+    if (e == cudaSuccess) {
+      k_make_windows<<<(P * kCnnTopK + 255) / 256, 256, 0, st>>>(
+          cent, P, n, B.dw<int32_t>(w.o_cwin), kCnnWin, jobs);
+      TDE_COUNT_LAUNCH(1);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(B.dw<int32_t>(w.o_cwin), 0,
+                          sizeof(int32_t) * (size_t)P * kCnnTopK * kCnnWin, st);
   }
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(B.dw<int32_t>(w.o_cwin), 0, sizeof(int32_t) * (size_t)P * kCnnTopK * kCnnWin,
-                        st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
     e = launch_xcorr_mma_windows(qe, n, n, P, jobs, ctx->d_status, st);

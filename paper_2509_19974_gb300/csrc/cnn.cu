@@ -364,23 +364,96 @@ __global__ void __launch_bounds__(kScWarps * 32) k_scores(const float* __restric
   if ((lane & 1) == 0 && bin < nb) scores[(int64_t)p * nb + bin] = params[kCnnAlpha] * acc[0];
 }
 
+// lag rank of bin l: smaller |l| first, then negative first (the estimator's
+// tie order), used to break exact score ties deterministically.
+__device__ __forceinline__ bool better(float s, int l, float bs, int bl) {
+  if (s != bs) return s > bs;
+  const int a = l < 0 ? -l : l, ab = bl < 0 ? -bl : bl;
+  return a != ab ? a < ab : l < bl;
+}
+
+// Top-8 of one pair's nb = 2 Lf - 1 bin scores, warp-wide.  v[i] is the
+// score of bin lane + 32 i (-inf past nb).  Softmax over all bins; eight
+// rounds of a register scan plus one warp reduction, a taken bin marked by a
+// flag bit.  Lane r < 8 receives the r-th centre in samples (256 l, best
+// first, exact ties by the lag order of `better`); every lane the softmax
+// mass of the eight (the margin).
+template <int PER>
+__device__ __forceinline__ void topk_warp(const float (&v)[PER], int nb, int Lf, int lane,
+                                          int32_t& centre, float& margin) {
+  uint32_t taken = 0;
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) mx = fmaxf(mx, v[i]);
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < PER; ++i)
+    if (lane + 32 * i < nb) sum += __expf(v[i] - mx);
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  float top = 0.f;
+  centre = 0;
+  for (int r = 0; r < kCnnTopK; ++r) {
+    float bs = -INFINITY;
+    int bl = 1 << 30, bi = -1;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int b = lane + 32 * i;
+      const int l = b - (Lf - 1);
+      if (b < nb && !(taken >> i & 1u) && (bl == (1 << 30) || better(v[i], l, bs, bl))) {
+        bs = v[i];
+        bl = l;
+        bi = i;
+      }
+    }
+    int owner = lane;
+    for (int o = 16; o; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      const int ow = __shfl_xor_sync(0xffffffffu, owner, o);
+      if (ol != (1 << 30) && (bl == (1 << 30) || better(os, ol, bs, bl))) {
+        bs = os;
+        bl = ol;
+        owner = ow;
+      }
+    }
+    if (lane == owner && bi >= 0) taken |= 1u << bi;
+    top += __expf(bs - mx);
+    if (lane == r) centre = kCnnBin * bl;
+  }
+  margin = top / sum;
+}
+
 // Short features (Lf <= 256): one CTA per pair with both features whole in
 // shared memory (32 zero rows padding y on both sides), 16 warps, warp w
 // taking the bin groups w and w + ngroups/2: their overlaps add up to about
 // Lf, so every warp does the same work and the grid is one wave.  The inner
-// loop and the lane reduction are those of k_scores.
+// loop and the lane reduction are those of k_scores.  With kTop the CTA
+// also keeps its scores in shared memory and warp 0 then takes the pair's
+// top 8 (topk_warp, as k_topk) and writes its centres, margin and window
+// jobs (the learned step's proposal in one launch).
 constexpr int kSpWarps = 16;
-constexpr int kSpMaxLf = 256;
+constexpr int kSpMaxLf = kCnnFusedMaxLf;
 constexpr int kSpPad = 32;
 constexpr int kSpSmem = ((kSpMaxLf + 16) + (kSpMaxLf + 2 * kSpPad)) * kScRow * 4;
+constexpr int kSpTopSmem = kSpSmem + 2 * kSpMaxLf * 4;  // + the scores
 
-template <bool kPosMajor>
+struct TopOut {
+  int32_t* centres;  // [P][8]
+  float* margin;     // [P]
+  WinJob* jobs;      // [P][8]
+  int32_t* cbuf;     // window w of pair p at cbuf + (8 p + w) * 257
+  int64_t n;         // signal length (lag range of the windows)
+};
+
+template <bool kPosMajor, bool kTop>
 __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* __restrict__ feat, int Lf,
                                                                   const float* __restrict__ params,
-                                                                  float* __restrict__ scores) {
+                                                                  float* __restrict__ scores, TopOut top) {
   extern __shared__ __align__(16) float sm[];
   float* xs = sm;                               // [Lf + 16][kScRow]: fx at row i
   float* ys = sm + (kSpMaxLf + 16) * kScRow;    // [Lf + 64][kScRow]: fy at row i + kSpPad
+  float* ss = sm + kSpSmem / 4;                 // kTop: [2 Lf - 1] scores
   const int p = blockIdx.x;
   const int nb = 2 * Lf - 1;
   const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
@@ -442,17 +515,34 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* _
     }
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
     const int bin = kScG * g + ((lane >> 1) & (kScG - 1));
-    if ((lane & 1) == 0 && bin < nb) scores[(int64_t)p * nb + bin] = alpha * acc[0];
+    if ((lane & 1) == 0 && bin < nb) {
+      scores[(int64_t)p * nb + bin] = alpha * acc[0];
+      if (kTop) ss[bin] = alpha * acc[0];
+    }
+  }
+  if (kTop) {
+    int32_t* cz = top.cbuf + (int64_t)p * kCnnTopK * kCnnWin;
+    for (int i = threadIdx.x; i < kCnnTopK * kCnnWin; i += kSpWarps * 32) cz[i] = 0;
+    __syncthreads();
+    if (warp != 0) return;
+    float v[kSpMaxLf * 2 / 32];
+#pragma unroll
+    for (int i = 0; i < kSpMaxLf * 2 / 32; ++i) {
+      const int b = lane + 32 * i;
+      v[i] = b < nb ? ss[b] : -INFINITY;
+    }
+    int32_t centre;
+    float margin;
+    topk_warp(v, nb, Lf, lane, centre, margin);
+    if (lane < kCnnTopK) {
+      const int64_t i = (int64_t)p * kCnnTopK + lane;
+      top.centres[i] = centre;
+      top.jobs[i] = win_job_of(centre, top.n, top.cbuf + i * kCnnWin);
+    }
+    if (lane == 0) top.margin[p] = margin;
   }
 }
 
-// lag rank of bin l: smaller |l| first, then negative first (the estimator's
-// tie order), used to break exact score ties deterministically.
-__device__ __forceinline__ bool better(float s, int l, float bs, int bl) {
-  if (s != bs) return s > bs;
-  const int a = l < 0 ? -l : l, ab = bl < 0 ? -bl : bl;
-  return a != ab ? a < ab : l < bl;
-}
 
 // Any length: the bins are re-read from global memory every round.
 __global__ void k_topk_any(const float* __restrict__ scores, int npairs, int Lf,
@@ -511,50 +601,16 @@ __global__ void k_topk(const float* __restrict__ scores, int npairs, int Lf,
   const int nb = 2 * Lf - 1;
   const float* sc = scores + (int64_t)p * nb;
   float v[PER];
-  uint32_t taken = 0;
-  float mx = -INFINITY;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int b = lane + 32 * i;
     v[i] = b < nb ? sc[b] : -INFINITY;
-    mx = fmaxf(mx, v[i]);
   }
-  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  float sum = 0.f;
-#pragma unroll
-  for (int i = 0; i < PER; ++i)
-    if (lane + 32 * i < nb) sum += __expf(v[i] - mx);
-  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  float top = 0.f;
-  for (int r = 0; r < kCnnTopK; ++r) {
-    float bs = -INFINITY;
-    int bl = 1 << 30, bi = -1;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int b = lane + 32 * i;
-      const int l = b - (Lf - 1);
-      if (b < nb && !(taken >> i & 1u) && (bl == (1 << 30) || better(v[i], l, bs, bl))) {
-        bs = v[i];
-        bl = l;
-        bi = i;
-      }
-    }
-    int owner = lane;
-    for (int o = 16; o; o >>= 1) {
-      const float os = __shfl_xor_sync(0xffffffffu, bs, o);
-      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-      const int ow = __shfl_xor_sync(0xffffffffu, owner, o);
-      if (ol != (1 << 30) && (bl == (1 << 30) || better(os, ol, bs, bl))) {
-        bs = os;
-        bl = ol;
-        owner = ow;
-      }
-    }
-    if (lane == owner && bi >= 0) taken |= 1u << bi;
-    top += __expf(bs - mx);
-    if (lane == 0) centres[(int64_t)p * kCnnTopK + r] = kCnnBin * bl;
-  }
-  if (lane == 0) margin[p] = top / sum;
+  int32_t centre;
+  float mg;
+  topk_warp(v, nb, Lf, lane, centre, mg);
+  if (lane < kCnnTopK) centres[(int64_t)p * kCnnTopK + lane] = centre;
+  if (lane == 0) margin[p] = mg;
 }
 
 // ---------------------------------------------------------------- training
@@ -873,9 +929,9 @@ cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float
                               float* scores, cudaStream_t st, bool pos_major) {
   if (Lf < 1 || npairs <= 0) return npairs <= 0 ? cudaSuccess : cudaErrorInvalidValue;
   if (Lf <= kSpMaxLf) {
-    auto kp = pos_major ? k_scores_pair<true> : k_scores_pair<false>;
+    auto kp = pos_major ? k_scores_pair<true, false> : k_scores_pair<false, false>;
     cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmem);
-    kp<<<npairs, kSpWarps * 32, kSpSmem, st>>>(feat, Lf, params, scores);
+    kp<<<npairs, kSpWarps * 32, kSpSmem, st>>>(feat, Lf, params, scores, TopOut{});
     TDE_COUNT_LAUNCH(1);
     return cudaGetLastError();
   }
@@ -883,6 +939,19 @@ cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kScSmem);
   const int nb = 2 * Lf - 1;
   kern<<<dim3((nb + kScBins - 1) / kScBins, npairs), kScWarps * 32, kScSmem, st>>>(feat, Lf, params, scores);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_scores_propose(const float* feat, int npairs, int Lf, const float* params,
+                                      float* scores, int32_t* centres, float* margin, WinJob* jobs,
+                                      int32_t* cbuf, int64_t n, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  if (Lf < 1 || Lf > kSpMaxLf) return cudaErrorNotSupported;
+  cudaFuncSetAttribute(k_scores_pair<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kSpTopSmem);
+  k_scores_pair<true, true><<<npairs, kSpWarps * 32, kSpTopSmem, st>>>(
+      feat, Lf, params, scores, TopOut{centres, margin, jobs, cbuf, n});
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

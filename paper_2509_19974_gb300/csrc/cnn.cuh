@@ -13,6 +13,7 @@
 //   bin l covers lags tau in [256 l - 128, 256 l + 128] (width 257).
 constexpr int kCnnC = 32, kCnnK = 9, kCnnLayers = 4, kCnnDec = 16, kCnnBin = 256;
 constexpr int kCnnTopK = 8, kCnnWin = 257;
+constexpr int kCnnFusedMaxLf = 256;  // longest features of the one-launch proposal
 
 // Parameter layout (FP32 master copy, BF16 copy for the forward pass):
 // per layer l: W_l[32][cin_l][9] then b_l[32] (cin_1 = 1, else 32); then alpha.
@@ -108,6 +109,28 @@ struct WinJob {
   int64_t lag_lo, lag_hi;  // window, clipped to the overlap range (lag_hi - lag_lo <= 256)
   int32_t* c;              // lag lag_lo + i at c[i], i <= lag_hi - lag_lo
 };
+#ifdef __CUDACC__
+// The window of 257 lags around centre c (samples), clipped to the lags of two
+// signals of length n; its correlations go to cbuf_i (lag c - 128 + i at
+// cbuf_i[i]).  An empty window (hi < lo) writes nothing; its pointer stays in
+// range.
+__device__ __forceinline__ WinJob win_job_of(int64_t c, int64_t n, int32_t* cbuf_i) {
+  int64_t lo = c - kCnnBin / 2, hi = c + kCnnBin / 2;
+  const int64_t first = lo;
+  if (lo < -(n - 1)) lo = -(n - 1);
+  if (hi > n - 1) hi = n - 1;
+  return WinJob{lo, hi, cbuf_i + (hi >= lo ? lo - first : 0)};
+}
+#endif
+// The learned step's proposal in one launch, for Lf <= kCnnFusedMaxLf (else
+// cudaErrorNotSupported): the scores of launch_cnn_scores (position-major
+// features), then per pair the centres and margin of launch_cnn_topk
+// (identical arithmetic, so identical values) and its 8 window jobs for
+// signals of length n (window w of pair p writes cbuf + (8 p + w) * 257),
+// with those 8 * 257 correlations zeroed.
+cudaError_t launch_cnn_scores_propose(const float* feat, int npairs, int Lf, const float* params,
+                                      float* scores, int32_t* centres, float* margin, WinJob* jobs,
+                                      int32_t* cbuf, int64_t n, cudaStream_t st);
 // Per pair: tie-ruled argmax over its 8 windows -> lag, value.
 cudaError_t launch_window_argmax(const WinJob* d_jobs, int npairs, int64_t* lag, int64_t* val,
                                  cudaStream_t st);
