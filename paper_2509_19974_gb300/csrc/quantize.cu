@@ -22,7 +22,8 @@
 //             two radix passes (10 + 9 bits) over the candidates give the
 //             exact order statistics;
 //   k_qfix    the candidates' levels: k_qcand already wrote every other
-//             sample's level (its first digit decides it), so x is read twice;
+//             sample's level (its first digit decides it), so x is read twice
+//             (for signals up to 2^18 samples k_qsel2 does this itself);
 //   k_qapply  (only when the popc kernels' bit planes are wanted)
 //             q = sign(x) * #{m : |x| >= t_m} and the planes (a third read).
 // The candidate list has room for the whole signal (keys, then index and
@@ -202,7 +203,9 @@ constexpr int kQPer = 8192;          // samples per streaming CTA and step
 
 __device__ __forceinline__ void q_bad(uint32_t u, int& bad) { bad |= u >= 0x7F800000u; }
 
-// Histogram of the first digit; each CTA adds its non-zero bins.
+// Histogram of the first digit; each CTA adds its non-zero bins.  (Having
+// the last CTA of each signal run k_qsel1's step here measured slower: every
+// CTA then waits on a fence for its atomics before it exits.)
 __global__ void __launch_bounds__(kQT) k_qhist(const QSig* __restrict__ sigs, QWork w,
                                                uint32_t* __restrict__ status) {
   __shared__ uint32_t sh[kQB];
@@ -470,7 +473,8 @@ __global__ void __launch_bounds__(kQT) k_qfix(const QSig* __restrict__ sigs, QWo
 
 // Short signals (few candidates): both candidate passes in one CTA per
 // signal -- digits 18..9 then 8..0, one histogram per distinct prefix, one
-// warp per threshold.
+// warp per threshold.  kFix: then the candidates' levels, as k_qfix.
+template <bool kFix>
 __global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QWork w, int M) {
   __shared__ __align__(16) uint32_t sh[7 * 1024];
   __shared__ uint32_t pre_s[7], rank_s[7];
@@ -525,6 +529,34 @@ __global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QW
     __syncthreads();
   }
   if (threadIdx.x < 7) st->thr[threadIdx.x] = threadIdx.x < M ? pre_s[threadIdx.x] : 0xFFFFFFFFu;
+  if (kFix) {
+    // pre_s holds the exact thresholds (the pass loop ends in a barrier)
+    const QSig s = sigs[sig];
+    const uint32_t* cidx = cand + s.n;
+    uint32_t t[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) t[m] = m < M ? pre_s[m] : 0xFFFFFFFFu;
+    // batches of kFixB candidates per thread, loaded before any store (the
+    // byte stores could alias the list, so loads after a store would wait)
+    constexpr int kFixB = 16;
+    for (uint32_t i0 = threadIdx.x; i0 < nc; i0 += kFixB * kQT) {
+      uint32_t u[kFixB], c[kFixB];
+#pragma unroll
+      for (int k = 0; k < kFixB; ++k) {
+        const uint32_t i = i0 + k * kQT;
+        u[k] = i < nc ? cand[i] : 0u;
+        c[k] = i < nc ? cidx[i] : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < kFixB; ++k) {
+        if (i0 + k * kQT >= nc) break;
+        int lv = 0;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) lv += u[k] >= t[m];
+        s.q[c[k] & 0x7FFFFFFFu] = (int8_t)(u[k] == 0 ? 0 : ((c[k] >> 31) ? -lv : lv));
+      }
+    }
+  }
 }
 
 // The exact thresholds from the candidates: digits 18..9 then 8..0.  Each
@@ -748,8 +780,10 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
     fused ? k_qcand<1, true><<<grid, kQT, 0, st>>>(d_sigs, w) : k_qcand<1, false><<<grid, kQT, 0, st>>>(d_sigs, w);
   else
     fused ? k_qcand<7, true><<<grid, kQT, 0, st>>>(d_sigs, w) : k_qcand<7, false><<<grid, kQT, 0, st>>>(d_sigs, w);
-  if (max_n <= (1 << 18)) {
-    k_qsel2<<<nsig, kQT, 0, st>>>(d_sigs, w, M);
+  const bool short_sig = max_n <= (1 << 18);
+  if (short_sig) {
+    fused ? k_qsel2<true><<<nsig, kQT, 0, st>>>(d_sigs, w, M)  // + k_qfix's step
+          : k_qsel2<false><<<nsig, kQT, 0, st>>>(d_sigs, w, M);
     TDE_COUNT_LAUNCH(1);
   } else {
     int64_t gc = ceil_div64(max_n, 32768);  // candidate-histogram CTAs per signal
@@ -762,7 +796,7 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
     k_qcsel<1><<<nsig, kQT, 0, st>>>(w, M);
     TDE_COUNT_LAUNCH(5);
   }
-  if (fused) {
+  if (fused && !short_sig) {
     int64_t gf = ceil_div64(max_n, 16 * kQT);  // candidates are a few percent of a signal
     if (gf < 1) gf = 1;
     if (gf > 65535) gf = 65535;
@@ -771,11 +805,14 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
       k_qfix<1><<<fgrid, kQT, 0, st>>>(d_sigs, w);
     else
       k_qfix<7><<<fgrid, kQT, 0, st>>>(d_sigs, w);
-  } else if (M == 1) {
-    k_qapply<1><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
-  } else {
-    k_qapply<7><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
+    TDE_COUNT_LAUNCH(1);
+  } else if (!fused) {
+    if (M == 1)
+      k_qapply<1><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
+    else
+      k_qapply<7><<<grid, kQT, 0, st>>>(d_sigs, d_planes, w);
+    TDE_COUNT_LAUNCH(1);
   }
-  TDE_COUNT_LAUNCH(4);
+  TDE_COUNT_LAUNCH(3);  // k_qhist, k_qsel1, k_qcand
   return cudaGetLastError();
 }
