@@ -65,14 +65,42 @@ __global__ void __launch_bounds__(kThreads) k_argmax32(const ArgPair* __restrict
                                                        unsigned long long* __restrict__ keys, int npairs,
                                                        const int* __restrict__ d_count) {
   const int lim = pair_limit(npairs, d_count);
+  const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * kThreads;
   for (int y = blockIdx.y; y < lim; y += gridDim.y) {
     const ArgPair P = pairs[y];
     const int32_t* c = static_cast<const int32_t*>(P.c);
+    const int64_t n = P.count;
+    // c is 4-byte aligned: `head` scalars up to the first 16-byte boundary,
+    // then nv int4 vectors (four per thread per step, all loaded before the
+    // compares), then the scalar tail
+    int64_t head = (int64_t)(((16u - ((uint32_t)reinterpret_cast<uintptr_t>(c) & 15u)) & 15u) >> 2);
+    if (head > n) head = n;
+    const int64_t nv = (n - head) >> 2;
+    const int64_t tail0 = head + 4 * nv;
     unsigned long long best = 0;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P.count; i += stride) {
-      unsigned long long k = pack32(c[i], P.lag_min + i);
+    auto take = [&](int32_t v, int64_t i) {
+      const unsigned long long k = pack32(v, P.lag_min + i);
       best = k > best ? k : best;
+    };
+    if (tid < head) take(c[tid], tid);
+    if (tid < n - tail0) take(c[tail0 + tid], tail0 + tid);
+    const int4* cv = reinterpret_cast<const int4*>(c + head);
+    for (int64_t v0 = tid; v0 < nv; v0 += 4 * nthr) {
+      int4 a[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t v = v0 + k * nthr;
+        a[k] = v < nv ? cv[v] : make_int4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t v = v0 + k * nthr;
+        if (v < nv) {
+          const int64_t i = head + 4 * v;
+          take(a[k].x, i), take(a[k].y, i + 1), take(a[k].z, i + 2), take(a[k].w, i + 3);
+        }
+      }
     }
     best = block_reduce(best, MaxU64());
     if (threadIdx.x == 0) atomicMax(&keys[2 * y], best);
