@@ -93,6 +93,15 @@ const char* tde_last_error(const tde_ctx* ctx);
  * events are the context's; no caller memory is touched). */
 tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
 
+/* Failure-detection self-test: launches one CTA whose bounded device waits
+ * (the ones every tensor-core kernel uses: a spinning and a suspending
+ * mbarrier wait, each limited to 2 s of %globaltimer) run out on a barrier
+ * that nothing arrives on.  The CTA then flags a time-out in the context's
+ * status word and returns, as a kernel whose wait gave up does, so the next
+ * tde_ctx_sync on `stream` returns TDE_ERR_TIMEOUT (after about 4 s) and the
+ * context stays usable.  No fault, trap or unbounded wait is involved. */
+tde_status tde_selftest_wait_timeout(tde_ctx* ctx, tde_stream_t stream);
+
 /* Prime count of the NTT engine (Sec. 3.2's multimodular route), for the
  * plans made after this call.  nprimes = 0 (the default): modulo one prime
  * p0 = 15 * 2^27 + 1 wherever every value fits its centred residues

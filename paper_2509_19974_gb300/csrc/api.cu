@@ -263,6 +263,14 @@ extern "C" tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable) {
   return TDE_OK;
 }
 
+extern "C" tde_status tde_selftest_wait_timeout(tde_ctx* ctx, tde_stream_t stream) {
+  if (!ctx) return TDE_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  LaunchCount lc(ctx);
+  const cudaError_t e = launch_wait_selftest(ctx->d_status, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "wait self-test");
+}
+
 extern "C" tde_status tde_ctx_set_ntt_primes(tde_ctx* ctx, int nprimes) {
   if (!ctx) return TDE_ERR_INVALID;
   if (nprimes != 0 && nprimes != 2)

@@ -1339,9 +1339,31 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restri
   }
 }
 
+// Self-test of the bounded waits the kernels above use: thread 0 waits on a
+// shared-memory barrier that nothing arrives on, first spinning (mbar_wait),
+// then suspending (mbar_wait_sleep); each gives up after kTimeoutNs, and the
+// CTA flags TDE_ST_TIMEOUT as a kernel whose wait gave up does.  No copy,
+// MMA or tensor memory is involved, so the CTA simply returns.
+__global__ void k_wait_selftest(uint32_t* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    bool ok = mbar_wait(b, 0);
+    ok = mbar_wait_sleep(b, 0) && ok;
+    if (!ok) atomicOr(status, TDE_ST_TIMEOUT);
+  }
+}
+
 }  // namespace
 
 int mma_smem_bytes() { return kSmemBytes8; }
+
+cudaError_t launch_wait_selftest(uint32_t* d_status, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(d_status);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mma_zero(const MmaPair* d_pairs, int npairs, int64_t max_count, cudaStream_t st,
                             const int* d_count) {

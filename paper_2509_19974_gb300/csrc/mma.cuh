@@ -52,6 +52,9 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
 // zeroed first.
 cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs,
                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
+// One CTA whose bounded waits (the kernels' own) run out on a barrier
+// nothing arrives on: TDE_ST_TIMEOUT in d_status after about 4 s.
+cudaError_t launch_wait_selftest(uint32_t* d_status, cudaStream_t st);
 // Levels [nsig][n] -> E4M3 bytes [nsig][n_pad] (zeros past n); n_pad % 4 == 0.
 cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qe,
                            cudaStream_t st);

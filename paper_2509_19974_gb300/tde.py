@@ -27,7 +27,7 @@ TDE_I32, TDE_I64, TDE_F32, TDE_I8 = 0, 1, 2, 3
 
 # Every symbol include/tde.h declares.
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
-           "tde_ctx_set_profiling", "tde_ctx_set_ntt_primes", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
+           "tde_ctx_set_profiling", "tde_ctx_set_ntt_primes", "tde_selftest_wait_timeout", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
            "tde_quantize_noalloc", "tde_quantize_batch", "tde_xcorr_int", "tde_argmax", "tde_xcorr_fft32",
            "tde_estimate", "tde_estimate_batch", "tde_batch_create", "tde_batch_run",
            "tde_batch_destroy", "tde_model_param_count", "tde_model_create", "tde_model_destroy",
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_last_error": ([p], ctypes.c_char_p),
         "tde_ctx_set_profiling": ([p, i32], st),
         "tde_ctx_set_ntt_primes": ([p, i32], st),
+        "tde_selftest_wait_timeout": ([p, p], st),
         "tde_ctx_read_profile": ([p, p, p, p], st),
         "tde_pick_engine": ([i32, i64, i64, i64], i32),
         "tde_quantize": ([p, p, i64, i32, p, p], st),
@@ -169,6 +170,11 @@ class Context:
 
     def set_profiling(self, enable: bool):
         self.check(self.lib.tde_ctx_set_profiling(self.handle, int(bool(enable))))
+
+    def selftest_wait_timeout(self, stream=None):
+        """Launches a CTA whose bounded waits run out (about 4 s); the next
+        sync raises TdeError with status TDE_ERR_TIMEOUT."""
+        self.check(self.lib.tde_selftest_wait_timeout(self.handle, _stream(stream)))
 
     def set_ntt_primes(self, nprimes: int):
         """0: the NTT engine uses one prime wherever the values fit it; 2: always

@@ -38,6 +38,8 @@ def test_null_context_is_rejected(lib):
     assert lib.tde_ctx_sync(None, None) == tde.TDE_ERR_INVALID
     assert lib.tde_ctx_destroy(None) == tde.TDE_OK
     assert lib.tde_last_error(None) == b"null context"
+    assert lib.tde_selftest_wait_timeout(None, None) == tde.TDE_ERR_INVALID
+    assert lib.tde_ctx_set_ntt_primes(None, 0) == tde.TDE_ERR_INVALID
 
 
 def test_bad_device_is_a_cuda_error(lib):
