@@ -242,6 +242,7 @@ extern "C" const char* tde_last_error(const tde_ctx* ctx) {
 }
 
 extern "C" tde_status tde_ctx_sync(tde_ctx* ctx, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   DeviceGuard g(ctx->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -264,6 +265,7 @@ extern "C" tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable) {
 }
 
 extern "C" tde_status tde_selftest_wait_timeout(tde_ctx* ctx, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   DeviceGuard g(ctx->device);
   LaunchCount lc(ctx);
@@ -848,6 +850,7 @@ extern "C" int tde_pick_engine(int bits, int64_t nx, int64_t ny, int64_t lag_cou
 
 extern "C" tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int bits,
                                    int8_t* q_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!x || !q_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (n <= 0) return set_err(ctx, TDE_ERR_INVALID, "n must be positive");
@@ -871,6 +874,7 @@ extern "C" tde_status tde_quantize(tde_ctx* ctx, const float* x, int64_t n, int 
 
 extern "C" tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n, int nsig,
                                          int bits, int8_t* q_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!x || !q_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (n <= 0 || nsig <= 0) return set_err(ctx, TDE_ERR_INVALID, "n and nsig must be positive");
@@ -898,6 +902,7 @@ extern "C" tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n
 extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, const int8_t* qy,
                                     int64_t ny, int bits, int64_t lag_min, int64_t lag_max,
                                     int engine, void* c_out, int out_dtype, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!qx || !qy || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   tde_status s = check_xcorr_args(ctx, nx, ny, bits, lag_min, lag_max, engine, out_dtype);
@@ -926,6 +931,7 @@ extern "C" tde_status tde_xcorr_int(tde_ctx* ctx, const int8_t* qx, int64_t nx, 
 extern "C" tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t lag_min,
                                  int64_t count, int64_t* lag_out, int64_t* val_out,
                                  tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!c || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (dtype != TDE_I32 && dtype != TDE_I64) return set_err(ctx, TDE_ERR_INVALID, "unknown dtype");
@@ -952,6 +958,7 @@ extern "C" tde_status tde_argmax(tde_ctx* ctx, const void* c, int dtype, int64_t
 extern "C" tde_status tde_refine(tde_ctx* ctx, const float* x, int64_t nx, const float* y, int64_t ny,
                                  const void* c, int dtype, int64_t lag_min, int64_t count,
                                  tde_refined* out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!x || !y || !c || !out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (dtype != TDE_I32 && dtype != TDE_I64) return set_err(ctx, TDE_ERR_INVALID, "unknown dtype");
@@ -1094,6 +1101,7 @@ cudaError_t batch_launch(tde_ctx* ctx, const BatchWork& w, const Bases& B, cudaS
 extern "C" tde_status tde_estimate_batch(tde_ctx* ctx, const tde_pair_desc* descs, int npairs,
                                          int bits, int engine, int32_t* c_out, int64_t* lag_out,
                                          int64_t* val_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!descs || !lag_out || !val_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   BatchWork w;
@@ -1125,6 +1133,7 @@ struct tde_batch {
 extern "C" tde_status tde_batch_create(tde_ctx* ctx, const tde_pair_desc* descs, int npairs,
                                        int bits, int engine, int32_t* c_out, int64_t* lag_out,
                                        int64_t* val_out, tde_batch** out) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!descs || !lag_out || !val_out || !out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   *out = nullptr;
@@ -1179,6 +1188,7 @@ extern "C" tde_status tde_batch_create(tde_ctx* ctx, const tde_pair_desc* descs,
 }
 
 extern "C" tde_status tde_batch_run(tde_batch* b, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!b || !b->exec) return TDE_ERR_INVALID;
   tde_ctx* ctx = b->ctx;
   DeviceGuard g(ctx->device);
@@ -1205,6 +1215,7 @@ extern "C" tde_status tde_estimate(tde_ctx* ctx, const float* x, int64_t nx, con
                                    int64_t ny, int bits, int64_t lag_min, int64_t lag_max,
                                    int engine, int64_t* lag_out, int64_t* val_out,
                                    tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   tde_pair_desc d{x, y, nx, ny, lag_min, lag_max};
   return tde_estimate_batch(ctx, &d, 1, bits, engine, nullptr, lag_out, val_out, stream);
 }
@@ -1212,6 +1223,7 @@ extern "C" tde_status tde_estimate(tde_ctx* ctx, const float* x, int64_t nx, con
 extern "C" tde_status tde_xcorr_fft32(tde_ctx* ctx, const void* x, const void* y, int in_dtype,
                                       int64_t nx, int64_t ny, int npairs, int64_t lag_min,
                                       int64_t lag_max, float* c_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!x || !y || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (in_dtype != TDE_F32 && in_dtype != TDE_I8)
@@ -1252,6 +1264,7 @@ extern "C" tde_status tde_synth_pairs(tde_ctx* ctx, uint64_t seed, int64_t first
                                       int64_t n, int64_t dmax, float ar_lo, float ar_hi,
                                       float snr_lo, float snr_hi, float* x_out, float* y_out,
                                       int64_t* shift_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!x_out || !y_out || !shift_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (npairs <= 0 || n <= 0 || dmax < 0 || first < 0)
@@ -1464,6 +1477,7 @@ extern "C" tde_status tde_model_set(tde_model* m, const float* params, const flo
 extern "C" tde_status tde_train_step(tde_ctx* ctx, tde_model* m, const int8_t* q, int npairs,
                                      const int64_t* labels, float lr, float weight_decay,
                                      float* loss_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   tde_status s = check_model(ctx, m);
   if (s != TDE_OK) return s;
@@ -1515,6 +1529,7 @@ extern "C" tde_status tde_train_step(tde_ctx* ctx, tde_model* m, const int8_t* q
 
 extern "C" tde_status tde_propose(tde_ctx* ctx, const tde_model* m, const int8_t* q, int npairs,
                                   int32_t* centres, float* margin, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   tde_status s = check_model(ctx, m);
   if (s != TDE_OK) return s;
@@ -1536,6 +1551,7 @@ extern "C" tde_status tde_propose(tde_ctx* ctx, const tde_model* m, const int8_t
 extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npairs,
                                         int bits, const int32_t* centres, int32_t* c_out,
                                         tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!q || !centres || !c_out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   if (!valid_bits(bits)) return set_err(ctx, TDE_ERR_INVALID, "bits must be 1, 2 or 4");
@@ -1776,6 +1792,7 @@ extern "C" tde_status tde_estimate_learned(tde_ctx* ctx, const tde_model* m, con
                                            const float* y, int npairs, int bits, float theta,
                                            int64_t* lag_out, int64_t* val_out,
                                            int32_t* fallback_out, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   tde_status s = check_learned_args(ctx, m, x, y, npairs, bits, lag_out, val_out);
   if (s != TDE_OK) return s;
@@ -1807,6 +1824,7 @@ extern "C" tde_status tde_learned_create(tde_ctx* ctx, const tde_model* m, const
                                          const float* y, int npairs, int bits, float theta,
                                          int64_t* lag_out, int64_t* val_out,
                                          int32_t* fallback_out, tde_learned** out) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
   *out = nullptr;
@@ -1851,6 +1869,7 @@ extern "C" tde_status tde_learned_create(tde_ctx* ctx, const tde_model* m, const
 }
 
 extern "C" tde_status tde_learned_run(tde_learned* b, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!b || !b->exec) return TDE_ERR_INVALID;
   tde_ctx* ctx = b->ctx;
   DeviceGuard g(ctx->device);
@@ -1893,6 +1912,7 @@ __global__ void k_random_levels(int8_t* q, int64_t n, int bits, uint64_t seed) {
 
 extern "C" tde_status tde_autotune(tde_ctx* ctx, int bits, const int64_t* n,
                                    const int64_t* lag_count, int npoints, int reps) {
+  ApiRange nvtx_range(__func__);
   if (!ctx) return TDE_ERR_INVALID;
   if (!valid_bits(bits) || !n || !lag_count || npoints <= 0 || reps <= 0)
     return set_err(ctx, TDE_ERR_INVALID, "bad autotune arguments");

@@ -2,9 +2,19 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "tde.h"
+
+// An NVTX range named after one C-ABI call, for profiler timelines (a no-op
+// unless a tool is attached).
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+  ApiRange(const ApiRange&) = delete;
+  ApiRange& operator=(const ApiRange&) = delete;
+};
 
 // Bits of the per-context device status word (see tde_ctx_sync).
 #define TDE_ST_NONFINITE 1u  // NaN or Inf in a quantizer input

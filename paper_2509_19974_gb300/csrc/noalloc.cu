@@ -71,6 +71,7 @@ cudaError_t scratch_on_current_device(char** out) {
 extern "C" tde_status tde_quantize_noalloc(const float* x, int64_t n, int nsig, int bits,
                                            int8_t* q_out, uint32_t* status_out,
                                            tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
   if (!x || !q_out || !status_out) return TDE_ERR_INVALID;
   if (bits != 1 && bits != 2 && bits != 4) return TDE_ERR_INVALID;
   if (n <= 0 || nsig <= 0) return TDE_ERR_INVALID;
