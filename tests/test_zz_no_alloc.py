@@ -12,7 +12,6 @@ point) bit for bit -- quantized levels are integers -- on two calls in a row,
 which also checks that the shared scratch left by one call does not leak into
 the next.
 """
-import ctypes
 
 import numpy as np
 import pytest
