@@ -4,6 +4,8 @@ kernel's rule in Python and checks it exhaustively or on random cases, so a
 change to the rule can be checked here before it runs on a GPU."""
 import random
 
+import numpy as np
+
 RING = 256          # k_xcorr_mma_win: slot ring of 256 (+ a 32-slot mirror)
 SC_SLOTS = 46       # slots a super-chunk reads: [R, R + 46)
 
@@ -93,3 +95,122 @@ def test_argmax32_reads_every_element_once_with_aligned_vectors():
     # the bench's layout: pair p's 131071 lags start at element 131071 p
     for p in range(4):
         assert all(c == 1 for c in _argmax32_visits((4 * 131071 * p) % 16, 131071, 32))
+
+
+def _conv_tc_model(X, W, b):
+    """k_conv_tc's operand arithmetic for one layer (32 -> 32 channels,
+    kernel 9, padding 4, + bias, ReLU, max-pool 2), on float arrays standing
+    for the BF16 bytes.  The input is split by position parity into 8
+    arrays of 8 channels (even array j holds channels 8j..8j+7 of positions
+    2r - 4, odd array of 2r - 3, row r); the weights are staged as 11 tap
+    blocks per 8-channel group (taps -1 .. 9, the ends zero).  A tile of 128
+    pooled outputs is 10 shifted row windows x 2 channel halves of
+    128 x 64 x 16 products read through the descriptors' strides (core
+    matrices of 8 rows x 16 bytes, stride byte offset 128, leading byte
+    offset one array), columns 0..31 the odd pre-pool output, 32..63 the
+    even one."""
+    C, K = 32, 9
+    L = X.shape[0]
+    Lo = L // 2
+    R = (L // 2 + 127) // 128 * 128 + 4
+    G = np.zeros((8, R, 8))
+    for r in range(R):
+        for par in range(2):
+            pos = 2 * r - 4 + par
+            if 0 <= pos < L:
+                for j in range(4):
+                    G[par * 4 + j, r] = X[pos, 8 * j:8 * j + 8]
+    Ws = np.zeros((4, 11, 32, 8))
+    for j in range(4):
+        for t in range(11):
+            if 0 <= t - 1 < K:
+                for co in range(32):
+                    Ws[j, t, co] = W[co, 8 * j:8 * j + 8, t - 1]
+    wflat = Ws.reshape(-1)
+    out = np.zeros((Lo, C))
+    arr = 132 * 16  # bytes per parity array in a tile (128 + 4 rows of 16 bytes)
+
+    def rd(flat, start, lbo, sbo, rows, kk):
+        byte = start + (rows // 8) * sbo + (rows % 8) * 16 + (kk // 8) * lbo + (kk % 8) * 2
+        assert (byte >= 0).all() and (byte // 2 < flat.size).all()
+        return flat[byte // 2]
+    m, n, kk = np.arange(128)[:, None], np.arange(64)[:, None], np.arange(16)[None, :]
+    for tile in range((Lo + 127) // 128):
+        P0 = tile * 128
+        tflat = G[:, P0:P0 + 132].copy().reshape(-1)
+        D = np.zeros((128, 64))
+        for w in range(10):
+            par, dd = w // 5, w % 5
+            for h in range(2):
+                A = rd(tflat, (par * 4 + 2 * h) * arr + 16 * dd, arr, 128, m, kk)
+                B = rd(wflat, ((2 * h) * 11 + 2 * dd + par) * 512, 11 * 512, 128, n, kk)
+                D += A @ B.T
+        for mm in range(128):
+            if P0 + mm < Lo:
+                out[P0 + mm] = np.maximum(np.maximum(D[mm, 32:], D[mm, :32]) + b, 0)
+    return out
+
+
+def test_conv_parity_layout_computes_conv_relu_pool():
+    rng = np.random.default_rng(1)
+    C, K = 32, 9
+    for L in (256, 288, 520, 1024):
+        X = rng.standard_normal((L, C))
+        W = rng.standard_normal((C, C, K))
+        b = rng.standard_normal(C)
+        Xp = np.zeros((L + 8, C))
+        Xp[4:4 + L] = X
+        z = np.zeros((L, C))
+        for k in range(K):
+            z += Xp[k:k + L] @ W[:, :, k].T
+        z = np.maximum(z + b, 0)
+        ref = np.maximum(z[0::2], z[1::2])
+        assert np.abs(_conv_tc_model(X, W, b) - ref).max() < 1e-9, L
+
+
+def _scores_pair_model(fx, fy, Lf, alpha, G=16, pad=32, warps=16):
+    """k_scores_pair's walk: x features in rows [0, Lf + 16) and y in rows
+    [0, Lf + 2 pad) of shared memory (zero outside the signal); warp w takes
+    bin groups w and w + ceil(ngroups / 2); a group walks only the blocks of
+    16 positions where its 16 bins overlap.  Asserts every shared-memory row
+    it reads is inside its array; returns the scores."""
+    nb = 2 * Lf - 1
+    out = np.full(nb, np.nan)
+    xs = np.zeros((Lf + 16, 32))
+    xs[:Lf] = fx.T
+    ys = np.zeros((Lf + 2 * pad, 32))
+    ys[pad:pad + Lf] = fy.T
+    ng = (nb + G - 1) // G
+    half = (ng + 1) // 2
+    for w in range(warps):
+        for gi in range(2):
+            g = w + gi * half
+            if w >= half or g >= ng:
+                continue
+            lg = G * g - (Lf - 1)
+            wlo = max(0, -(lg + G - 1)) & ~(G - 1)
+            whi = (min(Lf, Lf - lg) + G - 1) & ~(G - 1)
+            acc = np.zeros((32, G))
+            for ib in range(wlo, whi, G):
+                for s2 in range(G):
+                    xr = ib + s2
+                    assert 0 <= xr < Lf + 16
+                    for t in range(G):
+                        yr = ib + lg + pad + s2 + t
+                        assert 0 <= yr < Lf + 2 * pad
+                        acc[:, t] += xs[xr] * ys[yr]
+            for t in range(G):
+                if G * g + t < nb:
+                    out[G * g + t] = alpha * acc[:, t].sum()
+    return out
+
+
+def test_scores_pair_walk_stays_in_bounds_and_scores_every_bin():
+    rng = np.random.default_rng(0)
+    for Lf in (8, 64, 136, 256):
+        fx, fy = rng.standard_normal((32, Lf)), rng.standard_normal((32, Lf))
+        ref = np.array([sum((fx[:, i] * fy[:, i + l]).sum() for i in range(Lf) if 0 <= i + l < Lf)
+                        for l in range(-(Lf - 1), Lf)]) * 0.5
+        got = _scores_pair_model(fx, fy, Lf, 0.5)
+        assert not np.isnan(got).any(), Lf
+        assert np.abs(got - ref).max() < 1e-9, Lf
