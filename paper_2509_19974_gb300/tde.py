@@ -149,6 +149,7 @@ class Context:
         self.handle = h
 
     def close(self):
+        """Releases the context (its workspace, plans' tables and status word)."""
         if getattr(self, "handle", None):
             self.lib.tde_ctx_destroy(self.handle)
             self.handle = None
@@ -160,15 +161,19 @@ class Context:
             pass
 
     def check(self, status: int):
+        """Raises TdeError (with the context's last error text) for a non-OK status."""
         if status != TDE_OK:
             msg = self.lib.tde_last_error(self.handle)
             raise TdeError(status, msg.decode() if msg else "")
 
     # --- methods mirroring the C entry points -----------------------------
     def sync(self, stream=None):
+        """Waits for `stream` and raises TdeError if a kernel flagged NaN/Inf
+        input, an out-of-range level or a timed-out wait since the last sync."""
         self.check(self.lib.tde_ctx_sync(self.handle, _stream(stream)))
 
     def set_profiling(self, enable: bool):
+        """Brackets every engine-kernel launch with CUDA events (read_profile)."""
         self.check(self.lib.tde_ctx_set_profiling(self.handle, int(bool(enable))))
 
     def selftest_wait_timeout(self, stream=None):
@@ -189,26 +194,33 @@ class Context:
         return int(k.value), int(e.value), float(ms.value)
 
     def quantize(self, x, bits, q_out=None, stream=None):
+        """See tde_quantize."""
         return tde_quantize(self, x, bits, q_out, stream)
 
     def xcorr_int(self, qx, qy, bits, lag_min=None, lag_max=None, engine="auto",
                   dtype=torch.int32, c_out=None, stream=None):
+        """See tde_xcorr_int."""
         return tde_xcorr_int(self, qx, qy, bits, lag_min, lag_max, engine, dtype, c_out, stream)
 
     def argmax(self, c, lag_min, stream=None):
+        """See tde_argmax."""
         return tde_argmax(self, c, lag_min, stream)
 
     def refine(self, x, y, c, lag_min, stream=None):
+        """See tde_refine."""
         return tde_refine(self, x, y, c, lag_min, stream)
 
     def xcorr_fft32(self, x, y, lag_min=None, lag_max=None, c_out=None, stream=None):
+        """See tde_xcorr_fft32."""
         return tde_xcorr_fft32(self, x, y, lag_min, lag_max, c_out, stream)
 
     def estimate(self, x, y, bits, lag_min=None, lag_max=None, engine="auto", stream=None):
+        """See tde_estimate."""
         return tde_estimate(self, x, y, bits, lag_min, lag_max, engine, stream)
 
     def estimate_batch(self, xs, ys, bits, lag_mins=None, lag_maxs=None, engine="auto",
                        c_out=None, stream=None):
+        """See tde_estimate_batch."""
         return tde_estimate_batch(self, xs, ys, bits, lag_mins, lag_maxs, engine, c_out, stream)
 
     # --- autotuner ---------------------------------------------------------
@@ -329,10 +341,15 @@ def pick_engine(bits: int, nx: int, ny: int, lag_count: int) -> str:
 
 
 def full_lags(nx: int, ny: int):
+    """Every lag with a non-empty overlap: (-(nx - 1), ny - 1)."""
     return -(nx - 1), ny - 1
 
 
 def tde_quantize(ctx: Context, x: torch.Tensor, bits: int, q_out=None, stream=None):
+    """Algorithm 1's quantization of one FP32 signal on its device: bits = 1 is
+    sign(x) with sign(0) = 0; bits = 2, 4 the sign-magnitude rank quantizer
+    (2^bits - 1 levels, thresholds exact order statistics of |x|).  Returns
+    int8 levels [n] (or fills q_out); asynchronous on `stream`."""
     _need(x, torch.float32, "x")
     if q_out is None:
         q_out = torch.empty(x.numel(), dtype=torch.int8, device=x.device)
@@ -377,6 +394,11 @@ def tde_quantize_noalloc(x: torch.Tensor, bits: int, q_out=None, status_out=None
 
 def tde_xcorr_int(ctx: Context, qx, qy, bits, lag_min=None, lag_max=None, engine="auto",
                   dtype=torch.int32, c_out=None, stream=None):
+    """Exact integer cross-correlation (Eq. 1) of int8 levels:
+    c[i] = sum_n qx[n] qy[n + tau], tau = lag_min + i, over [lag_min, lag_max]
+    (default every lag with overlap).  engine: "auto", "popc", "mma" or
+    "ntt"; dtype int32 (rejected where it could overflow) or int64.
+    Asynchronous on `stream`."""
     _need(qx, torch.int8, "qx")
     _need(qy, torch.int8, "qy")
     lo, hi = full_lags(qx.numel(), qy.numel())
@@ -394,6 +416,9 @@ def tde_xcorr_int(ctx: Context, qx, qy, bits, lag_min=None, lag_max=None, engine
 
 
 def tde_argmax(ctx: Context, c, lag_min, stream=None):
+    """The maximiser of c (int32 or int64, element i = lag lag_min + i) by
+    the tie rule: the largest value, then the smallest |tau|, then the
+    smallest tau.  Returns device tensors (lag [1], value [1]) int64."""
     if c.dtype not in (torch.int32, torch.int64):
         raise TypeError("c must be int32 or int64")
     _need(c, c.dtype, "c")
@@ -453,6 +478,9 @@ def tde_xcorr_fft32(ctx: Context, x, y, lag_min=None, lag_max=None, c_out=None, 
 
 
 def tde_estimate(ctx: Context, x, y, bits, lag_min=None, lag_max=None, engine="auto", stream=None):
+    """Algorithm 1 for one FP32 pair: quantize both, correlate exactly over
+    [lag_min, lag_max] (default every lag), take the tie-ruled argmax.
+    Returns device tensors (lag [1], value [1]) int64; asynchronous."""
     _need(x, torch.float32, "x")
     _need(y, torch.float32, "y")
     lo, hi = full_lags(x.numel(), y.numel())
@@ -640,6 +668,7 @@ class Model:
             pass
 
     def state(self):
+        """Host copies of the parameters, AdamW moments, gradient and step."""
         import numpy as np
         arrs = [np.empty(self.count, np.float32) for _ in range(4)]
         step = ctypes.c_int64()
@@ -650,6 +679,7 @@ class Model:
                 "step": int(step.value)}
 
     def load_state(self, st):
+        """Sets the parameters (and moments, step when given) from state()."""
         import numpy as np
         ps = np.ascontiguousarray(st["params"], np.float32)
         m = np.ascontiguousarray(st.get("adam_m", np.zeros_like(ps)), np.float32)
@@ -660,11 +690,13 @@ class Model:
             raise TdeError(s, "tde_model_set failed")
 
     def save(self, path: str):
+        """Parameters, AdamW moments and step count to an .npz (exact resume)."""
         import numpy as np
         st = self.state()
         np.savez(path, n=self.n, **{k: v for k, v in st.items()})
 
     def load(self, path: str):
+        """Restores a checkpoint written by save() for the same signal length."""
         import numpy as np
         z = np.load(path)
         if int(z["n"]) != self.n:
@@ -673,6 +705,8 @@ class Model:
 
     def train_step(self, q2: torch.Tensor, labels: torch.Tensor, lr: float, weight_decay=1e-4,
                    stream=None):
+        """One deterministic AdamW step on pairs q2 [2P, n] int8 (pair p at rows
+        2p, 2p + 1) against label lags [P] int64; returns the per-pair loss."""
         _need(q2, torch.int8, "q")
         _need(labels, torch.int64, "labels")
         npairs = q2.shape[0] // 2
@@ -683,6 +717,8 @@ class Model:
         return loss
 
     def propose(self, q2: torch.Tensor, stream=None):
+        """Window centres [P, 8] int32 (lags, best first) and margins [P] (the
+        softmax mass of the top 8 bins) for pairs q2 [2P, n] int8."""
         _need(q2, torch.int8, "q")
         npairs = q2.shape[0] // 2
         cent = torch.empty((npairs, 8), dtype=torch.int32, device=q2.device)
@@ -693,6 +729,9 @@ class Model:
 
     def estimate(self, x: torch.Tensor, y: torch.Tensor, bits: int = 2, theta: float = 0.5,
                  stream=None):
+        """The learned estimate of pairs x, y [P, n] float32: the exact
+        tie-ruled maximum over the proposal's 8 windows, or over every lag
+        when the margin is below theta.  Returns (lags, values, fallback)."""
         _need(x, torch.float32, "x")
         _need(y, torch.float32, "y")
         npairs = x.shape[0]
