@@ -93,7 +93,8 @@ def workload(args, rank):
 
 
 def max_over_ranks(value: float, world: int, device=None) -> float:
-    """The slowest rank's time: the only cross-rank reduction of the bench."""
+    """The slowest rank's time (the bench's cross-rank reductions are this
+    and min_over_ranks; no data crosses ranks)."""
     if world <= 1:
         return float(value)
     import torch
@@ -101,6 +102,11 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def min_over_ranks(value: float, world: int, device=None) -> float:
+    """The smallest value over ranks (a lag agreement, an all-ranks flag)."""
+    return -max_over_ranks(-float(value), world, device)
 
 
 def config(args, world):
@@ -129,10 +135,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, tag: str = "full"):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"tde_clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"tde_clocks_{os.getpid()}_{tag}.csv")
 
     def __enter__(self):
         try:
@@ -170,8 +176,9 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": int(rows[0][2]),
-                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
-                                                         if r[3].replace(".", "").isdigit()),
+                "samples": len(rows), "power_w_max": max((float(r[3]) for r in rows
+                                                          if r[3].replace(".", "").isdigit()),
+                                                         default=None),
                 "reasons": reasons}
 
 
@@ -371,12 +378,15 @@ def main():
             lb.run(stream)
         torch.cuda.synchronize()
         ctx.read_profile()
+        clk_l = ClockSampler(local, "learned")
+        clk_l.__enter__()
         k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
         k0.record(stream)
         for _ in range(args.steps):
             lb.run(stream)
         k1.record(stream)
-        torch.cuda.synchronize()
+        barrier()
         launches_l, _, _ = ctx.read_profile()
         ms_l1 = k0.elapsed_time(k1) / args.steps
         ll, lv, lf = lb.lags, lb.vals, lb.fallback
@@ -390,7 +400,7 @@ def main():
             for _ in range(max(3, args.warmup)):
                 for b_, s_ in zip(lbs, sts):
                     b_.run(s_)
-            torch.cuda.synchronize()
+            barrier()
             k0.record(stream)
             for s_ in sts[1:]:
                 s_.wait_event(k0)
@@ -401,11 +411,16 @@ def main():
                 ev.record(s_)
                 stream.wait_event(ev)
             k1.record(stream)
-            torch.cuda.synchronize()
+            barrier()
             ms_n = k0.elapsed_time(k1) / args.steps
-            if all(bool(((b_.lags == ll) & (b_.vals == lv)).all()) for b_ in lbs[1:]):
+            same = all(bool(((b_.lags == ll) & (b_.vals == lv)).all()) for b_ in lbs[1:])
+            # every rank uses the in-flight figure only if every rank's plans agree
+            if min_over_ranks(1.0 if same else 0.0, world, device="cuda") == 1.0:
                 ms_l, in_flight = ms_n, len(lbs)
-        agree = float(((ll == lags) & (lv == vals)).float().mean())
+        ms_l1 = max_over_ranks(ms_l1, world, device="cuda")
+        ms_l = max_over_ranks(ms_l, world, device="cuda")
+        agree = min_over_ranks(float(((ll == lags) & (lv == vals)).float().mean()), world,
+                               device="cuda")
         # the window kernel, timed by the library on its stream
         ctx.read_profile()
         ctx.set_profiling(True)
@@ -444,18 +459,20 @@ def main():
             def learned_plan(xb, yb):
                 pl = tde.LearnedBatch(model, xb, yb, args.bits, theta)
                 return lambda st: pl.run(st)[0]
-            t_l, h2d, d2h = pipelined_e2e(learned_plan, X, Y, args.steps, stream,
-                                          torch.cuda.synchronize)
-            e2e_l = {"value": args.npairs * args.steps / (t_l / 1e3), "unit": "pairs/s",
+            t_l, h2d, d2h = pipelined_e2e(learned_plan, X, Y, args.steps, stream, barrier)
+            t_l = max_over_ranks(t_l, world, device="cuda")
+            e2e_l = {"value": args.npairs * world * args.steps / (t_l / 1e3), "unit": "pairs/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                      "overlap": "step i's host->device copy overlaps step i-1's compute"}
+        clk_l.__exit__(None, None, None)  # sampled over the learned form's timed regions
         meta = json.loads(str(z["meta"]))
-        learned = {"value": args.npairs / (ms_l / 1e3), "unit": "pairs/s", "ms_per_step": ms_l,
-                   "in_flight": in_flight,
-                   "single_stream": {"value": args.npairs / (ms_l1 / 1e3), "ms_per_step": ms_l1},
+        learned = {"value": args.npairs * world / (ms_l / 1e3), "unit": "pairs/s",
+                   "ms_per_step": ms_l, "in_flight": in_flight, "clocks": clk_l.summary(),
+                   "single_stream": {"value": args.npairs * world / (ms_l1 / 1e3),
+                                     "ms_per_step": ms_l1},
                    "e2e": e2e_l, "roofline": roof_l, "gpu_launches": int(launches_l),
                    "lag_agreement_with_full": agree, "fallback_rate": float(lf.float().mean()),
-                   "theta": theta, "full_form_value": args.npairs * args.steps / (ms_max / 1e3),
+                   "theta": theta, "full_form_value": args.npairs * world * args.steps / (ms_max / 1e3),
                    "speedup_vs_full": (ms_max / args.steps) / ms_l,
                    "what": "quantize -> 16x decimate -> CNN (BF16 weights; tensor-core conv, "
                            "FP32 accumulation) -> top-8 257-lag windows -> exact tensor-core "
@@ -552,13 +569,15 @@ def main():
     if learned is not None and learned["lag_agreement_with_full"] >= 0.999:
         out["full_form"] = {"value": out["value"], "ms_per_step": out["ms_per_step"],
                             "e2e": out["e2e"], "roofline": out["roofline"],
-                            "gpu_launches": out["gpu_launches"]}
+                            "gpu_launches": out["gpu_launches"], "clocks": out["clocks"]}
         out["form"] = "learned proposal (windows + exact tensor-core correlation, full fallback)"
         out["value"] = learned["value"]
         out["ms_per_step"] = learned["ms_per_step"]
         out["e2e"] = learned["e2e"]
         out["roofline"] = learned["roofline"]
         out["gpu_launches"] = learned["gpu_launches"]
+        if learned["clocks"].get("sm_mhz") is not None:
+            out["clocks"] = learned["clocks"]
     else:
         out["form"] = "full integer correlation"
     if not args.no_cpu_baseline and world == 1:

@@ -40,7 +40,10 @@ def _rank(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     # each rank times its own shard; the bench reports the slowest
     got = bench.max_over_ranks(10.0 + rank, world)
-    q.put((rank, got, bench.rank_seed(rank)))
+    # the learned form's agreement and in-flight flag: the smallest over ranks
+    agree = bench.min_over_ranks(0.999 + 0.001 * rank, world)
+    flag = bench.min_over_ranks(1.0 if rank == 0 else 0.0, world)
+    q.put((rank, got, bench.rank_seed(rank), agree, flag))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -58,3 +61,30 @@ def test_multirank_host_logic_gloo():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [11.0, 11.0]          # max over ranks
     assert res[0][2] != res[1][2]                       # disjoint pairs per rank
+    assert [r[3] for r in res] == [0.999, 0.999]        # min over ranks
+    assert [r[4] for r in res] == [0.0, 0.0]            # one rank's flag clears it for all
+
+
+def test_min_over_ranks_single_rank_is_identity():
+    assert bench.min_over_ranks(0.5, 1) == 0.5
+    assert bench.max_over_ranks(0.5, 1) == 0.5
+
+
+def test_clock_samplers_write_separate_files():
+    a, b = bench.ClockSampler(0), bench.ClockSampler(0, "learned")
+    assert a.path != b.path
+
+
+def test_clock_summary_parses_samples(tmp_path):
+    c = bench.ClockSampler(0, "unit")
+    c.path = str(tmp_path / "clocks.csv")
+    c.proc = object()  # as if nvidia-smi had run
+    with open(c.path, "w") as f:
+        f.write("0, 2070, 2070, 175.42, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 2055, 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Active\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2062.5 and s["sm_max_mhz"] == 2070 and s["samples"] == 2
+    assert s["power_w_max"] == 175.42 and s["reasons"] == ["sw_power_cap"]
+    with open(c.path, "w") as f:
+        f.write("0, 2070, 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    assert c.summary()["power_w_max"] is None
