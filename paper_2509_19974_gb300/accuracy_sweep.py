@@ -20,7 +20,7 @@ through the library over every lag:
   proposed        Algorithm 1 with the sign quantizer (b = 1): the integer
                   correlation, its tied maxima re-ranked by the real
                   cross-correlation (tde_refine);
-  until line 4    the set of integer maxima alone;
+  integer maxima  the set of integer maxima alone (no re-ranking);
   real CCF        the argmax of the unquantized cross-correlation (the FP32
                   FFT comparator).
 
@@ -72,7 +72,7 @@ def run(trials: int, snrs, seed: int = 2026):
     rows = []
     for snr in snrs:
         rng = np.random.default_rng([seed, int(round(10 * snr)) + 1000])
-        ok = {"proposed": 0, "until line 4": 0, "real CCF": 0}
+        ok = {"proposed": 0, "integer maxima": 0, "real CCF": 0}
         for _ in range(trials):
             x, y, nu = make_pair(rng, snr)
             xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
@@ -81,7 +81,7 @@ def run(trials: int, snrs, seed: int = 2026):
             r = ctx.refine(xt, yt, c, lo)
             ok["proposed"] += abs(-r["lag_lo"] - nu) < 1 and abs(-r["lag_hi"] - nu) < 1
             tied = -(torch.nonzero(c == c.max()).flatten() + lo)
-            ok["until line 4"] += bool(((tied.double() - nu).abs() < 1).all())
+            ok["integer maxima"] += bool(((tied.double() - nu).abs() < 1).all())
             f = ctx.xcorr_fft32(xt, yt)
             ok["real CCF"] += abs(-(int(torch.argmax(f.flatten())) + lo) - nu) < 1
         rows.append((snr, {k: v / trials for k, v in ok.items()}))
@@ -95,10 +95,10 @@ def main():
     ap.add_argument("--snrs", type=float, nargs="+", default=[-20, -15, -10, -5, 0, 5, 10])
     a = ap.parse_args()
     rows = run(a.trials, a.snrs)
-    print(f"| SNR (dB) | proposed | until line 4 | real CCF |  ({a.trials} trials per SNR)")
+    print(f"| SNR (dB) | proposed | integer maxima | real CCF |  ({a.trials} trials per SNR)")
     print("|---:|---:|---:|---:|")
     for snr, acc in rows:
-        print(f"| {snr:g} | {acc['proposed']:.3f} | {acc['until line 4']:.3f} | {acc['real CCF']:.3f} |")
+        print(f"| {snr:g} | {acc['proposed']:.3f} | {acc['integer maxima']:.3f} | {acc['real CCF']:.3f} |")
 
 
 if __name__ == "__main__":
