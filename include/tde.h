@@ -51,7 +51,7 @@ typedef enum {
   TDE_OK = 0,
   TDE_ERR_INVALID = 1,     /* bad argument; or NaN/Inf input seen on the device */
   TDE_ERR_OVERFLOW = 2,    /* int32 output could overflow for these sizes */
-  TDE_ERR_UNSUPPORTED = 3, /* valid request this build cannot serve */
+  TDE_ERR_UNSUPPORTED = 3, /* valid request the library cannot serve */
   TDE_ERR_CUDA = 4,        /* a CUDA runtime call failed; see tde_last_error */
   TDE_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
 } tde_status;

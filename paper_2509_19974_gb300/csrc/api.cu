@@ -838,7 +838,7 @@ int pick_engine_ctx(const tde_ctx* ctx, int engine, int bits, int64_t nx, int64_
 tde_status engine_available(tde_ctx* ctx, int engine) {
   if (engine == TDE_ENGINE_POPC || engine == TDE_ENGINE_MMA || engine == TDE_ENGINE_NTT)
     return TDE_OK;
-  return set_err(ctx, TDE_ERR_UNSUPPORTED, "engine %d is not available in this build", engine);
+  return set_err(ctx, TDE_ERR_UNSUPPORTED, "engine %d is not available in this library", engine);
 }
 
 }  // namespace
