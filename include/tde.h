@@ -187,10 +187,12 @@ tde_status tde_quantize_batch(tde_ctx* ctx, const float* x, int64_t n, int nsig,
  * n <= 2^31 - 1; larger requests return TDE_ERR_UNSUPPORTED and enqueue
  * nothing.  Other argument errors return TDE_ERR_INVALID.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress, once per
- * device); make that first call before any stream capture.  All calls share
- * the array and it keeps the last call's contents (each call clears what it
- * needs): calls whose work may overlap on the GPU, e.g. on two unordered
- * streams, race and give wrong results. */
+ * device); make that first call before any stream capture.  The address is
+ * kept for the life of the process, so do not use this entry point across a
+ * cudaDeviceReset of that device.  All calls share the array and it keeps the
+ * last call's contents (each call clears what it needs): calls whose work may
+ * overlap on the GPU, e.g. on two unordered streams, race and give wrong
+ * results. */
 tde_status tde_quantize_noalloc(const float* x, int64_t n, int nsig, int bits, int8_t* q_out,
                                 uint32_t* status_out, tde_stream_t stream);
 
@@ -368,9 +370,14 @@ tde_status tde_learned_destroy(tde_learned* plan);
  * reads them) and window w with centre centres[8 p + w] (device int32),
  * c_out[(8 p + w) * 257 + i] (device int32) = c[centre - 128 + i] for
  * i in [0, 257); lags outside [-(n-1), n-1] read 0.  Computed on the tensor
- * cores (E4M3 operands, FP32 accumulation: exact for levels in [-7, 7]).
- * Uses a context workspace of 2 npairs * round_up(n, 128) bytes for the
- * levels in E4M3.  bits 1, 2 or 4. */
+ * cores with E4M3 operands and FP32 accumulation, exact for every n: one
+ * accumulator sums at most 2^24 / (2^(bits-1))^2 samples, and the partial
+ * sums of longer pairs are added as integers.  bits 1, 2 or 4; levels must
+ * lie in the bits' range (|q| <= 1, or <= 7 for bits 4): one outside it sets
+ * the status word, and tde_ctx_sync then returns TDE_ERR_INVALID.
+ * TDE_ERR_OVERFLOW if n * (2^(bits-1))^2 >= 2^31 (the int32 bound).  Uses a
+ * context workspace of 2 npairs * round_up(n, 128) bytes for the levels in
+ * E4M3. */
 tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npairs, int bits,
                              const int32_t* centres, int32_t* c_out, tde_stream_t stream);
 

@@ -1557,6 +1557,13 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
   if (!valid_bits(bits)) return set_err(ctx, TDE_ERR_INVALID, "bits must be 1, 2 or 4");
   if (n <= 0 || npairs <= 0) return set_err(ctx, TDE_ERR_INVALID, "n and npairs must be positive");
   if (n > INT32_MAX) return set_err(ctx, TDE_ERR_UNSUPPORTED, "n beyond 2^31 - 1");
+  {
+    // the int32 windows hold values up to n * (2^(bits-1))^2 in magnitude
+    const int64_t k = (int64_t)1 << (bits - 1);
+    if (n * k * k >= ((int64_t)1 << 31))
+      return set_err(ctx, TDE_ERR_OVERFLOW,
+                     "int32 windows may overflow: n*(2^(bits-1))^2 = %lld >= 2^31", (long long)(n * k * k));
+  }
   DeviceGuard g(ctx->device);
   LaunchCount lc(ctx);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1576,10 +1583,10 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
     TDE_COUNT_LAUNCH(1);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = launch_to_e4m3(q, n, n_pad, 2 * npairs, qe, st);
+  if (e == cudaSuccess) e = launch_to_e4m3(q, n, n_pad, 2 * npairs, bits, qe, ctx->d_status, st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(qe, n, n_pad, npairs, jobs, ctx->d_status, st);
+    e = launch_xcorr_mma_windows(qe, n, n_pad, npairs, bits, jobs, ctx->d_status, st);
   }
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "windows");
 }
@@ -1736,7 +1743,7 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   }
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(qe, n, n, P, jobs, ctx->d_status, st);
+    e = launch_xcorr_mma_windows(qe, n, n, P, w.bits, jobs, ctx->d_status, st);
   }
   if (e == cudaSuccess) e = launch_window_argmax(jobs, P, lag_out, val_out, st);
   // fallback, decided and run on the device

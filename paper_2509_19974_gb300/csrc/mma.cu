@@ -560,7 +560,11 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs, int npairs, co
 // write the 8 rows of 4 consecutive slots (128-byte runs per store): a lane
 // loads six 8-byte words, realigns them once by its byte offset and stores
 // aligned word pairs.  The (pair, K segment) units of the batch, pair-major, are dealt to
-// the CTAs as contiguous runs of equal length.  Every wait is bounded; a role
+// the CTAs as contiguous runs of equal length.  A CTA accumulates a pair's
+// segments in groups of at most grp (grp * seg * K_b^2 < 2^24, set by the
+// host from the bits), reads each group out and adds groups that do not
+// cover the whole pair with integer atomics, so every FP32 value it rounds
+// is an exact integer whatever n is.  Every wait is bounded; a role
 // whose wait gives up raises the CTA's abort flag and leaves its loop, the
 // others leave theirs at their next wait, and the CTA flags TDE_ST_TIMEOUT,
 // waits (bounded) for its copies and MMAs in flight and frees its tensor
@@ -615,7 +619,7 @@ __device__ __forceinline__ void mbar_expect_tx_win(uint32_t bar, uint32_t bytes)
 __global__ void __launch_bounds__(kWinThreads, 2)
     k_xcorr_mma_win(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap xmap,
                     int64_t n, int npairs, const WinJob* __restrict__ jobs, int nseg, int seg,
-                    uint32_t* __restrict__ status) {
+                    int grp, uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -666,6 +670,12 @@ __global__ void __launch_bounds__(kWinThreads, 2)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // accumulation group of unit u: a pair's segments in runs of grp, so that
+  // no FP32 accumulator sums more than grp * seg samples
+  auto group_of = [&](int64_t u) -> int64_t {
+    const int64_t p = u / nseg;
+    return p * nseg + (u - p * nseg) / grp;
+  };
   // K chunks of segment g of the run
   auto seg_of = [&](int g, int* p, int64_t* ks, int* nchunks) {
     const int64_t u = u0 + g;
@@ -787,15 +797,15 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     const uint32_t idesc = idesc8_for(kWinN);
     const uint64_t da0 = sdesc(slots, 256, 128, 0, 0) + 32u * set;          // + ring slot * 8
     const uint64_t db0 = sdesc(ybuf, 16, kWinArr, 2, 0) + 2u * set;         // + (buffer + row * 128) >> 4
-    int64_t S = 0;
-    int pp = -1, cur_p = -1;
-    bool ok = true, fresh = false;  // fresh: the set is not yet written for this pair
+    int64_t S = 0, cur_grp = -1;
+    int pp = -1;
+    bool ok = true, fresh = false;  // fresh: the set is not yet written for this group
     for (int g = 0; g < G && ok && !*abort_flag; ++g) {
       int p, nch;
       int64_t ks;
       seg_of(g, &p, &ks, &nch);
-      if (p != cur_p) {  // a new pair: its accumulator must have been read out
-        cur_p = p;
+      if (group_of(u0 + g) != cur_grp) {  // a new group: its accumulator must have been read out
+        cur_grp = group_of(u0 + g);
         ++pp;
         fresh = true;
         if (pp >= 2)
@@ -838,10 +848,8 @@ __global__ void __launch_bounds__(kWinThreads, 2)
       if (!ok) break;
       if (lane == 0) {
         mma_commit(seg_empty + 8 * b);  // the segment's buffers are free once its MMAs are done
-        int pn = -1, nn;
-        int64_t kn;
-        if (g + 1 < G) seg_of(g + 1, &pn, &kn, &nn);
-        if (pn != p) mma_commit(acc_full + 8 * (uint32_t)(pp & 1));  // the pair's sum is complete
+        if (g + 1 >= G || group_of(u0 + g + 1) != cur_grp)
+          mma_commit(acc_full + 8 * (uint32_t)(pp & 1));  // the group's sum is complete
       }
       __syncwarp();
     }
@@ -852,10 +860,13 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     const int m = 32 * qd + lane;
     int pp = 0;
     for (int64_t u = u0; u < u1; ++pp) {
+      // the group's segments [sg_lo, sg_hi) of pair p within this CTA's run
       const int p = (int)(u / nseg);
       const int sg_lo = (int)(u - (int64_t)p * nseg);
-      const int sg_hi = u1 - u < nseg - sg_lo ? sg_lo + (int)(u1 - u) : nseg;
-      const bool whole = sg_lo == 0 && sg_hi == nseg;  // no other CTA adds to this pair
+      int sg_hi = (sg_lo / grp + 1) * grp;
+      if (sg_hi > nseg) sg_hi = nseg;
+      if (u1 - u < sg_hi - sg_lo) sg_hi = sg_lo + (int)(u1 - u);
+      const bool whole = sg_lo == 0 && sg_hi == nseg;  // no other group adds to this pair
       u += sg_hi - sg_lo;
       if (*abort_flag) break;
       if (!mbar_wait_sleep(acc_full + 8 * (uint32_t)(pp & 1), (uint32_t)((pp >> 1) & 1))) {
@@ -1425,16 +1436,22 @@ bool tmap_bytes3(CUtensorMap* m, const void* base, int64_t stride, int S, int ro
 }
 }  // namespace
 
-cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs,
+cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, int bits,
                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (n_pad % 128 != 0 || n_pad < n || (reinterpret_cast<uintptr_t>(d_qe) & 15) != 0)
     return cudaErrorInvalidValue;
+  if (bits != 1 && bits != 2 && bits != 4) return cudaErrorInvalidValue;
   // K range [0, n + 127) rounded up to 128; segments are multiples of 128
   // (so that each segment's windows start on a 128-sample row)
   const int64_t kmax = ceil_div64(n + 127, 128) * 128;
   const int nseg = (int)ceil_div64(kmax, kWinKs);
   const int seg = (int)(ceil_div64(ceil_div64(kmax, nseg), 128) * 128);
+  // segments per accumulator: grp * seg * K_b^2 < 2^24 keeps every FP32 partial
+  // (and the sum of the two sets) an exact integer; K_b = 2^(bits-1) bounds |level|
+  const int64_t kb2 = (int64_t)1 << (2 * (bits - 1));
+  const int grp = (int)(((int64_t)1 << 24) / ((int64_t)seg * kb2 + 1));
+  if (grp < 1) return cudaErrorInvalidValue;
   CUtensorMap ymap, xmap;
   if (!tmap_bytes3(&ymap, d_qe, n_pad, 2 * npairs, 128, kWinRows, true) ||
       !tmap_bytes3(&xmap, d_qe, n_pad, 2 * npairs, 16, kWinXBox, false))
@@ -1449,15 +1466,19 @@ cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_p
   const int64_t units = (int64_t)npairs * nseg;
   const int grid = (int)(units < 2 * (int64_t)sms ? units : 2 * (int64_t)sms);
   k_xcorr_mma_win<<<grid, kWinThreads, kWinSmemBytes, st>>>(ymap, xmap, n, npairs, d_jobs, nseg, seg,
-                                                            d_status);
+                                                            grp, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
 
 // Levels -> E4M3 bytes with a padded signal stride (zeros in [n, n_pad)).
-__global__ void k_to_e4m3(const int8_t* __restrict__ q, int64_t n, int64_t n_pad, int nsig,
-                          uint8_t* __restrict__ qe) {
+// Flags TDE_ST_INTERNAL if a level's magnitude exceeds maxlev (the bits'
+// range; the conversion itself is exact up to 7).
+__global__ void k_to_e4m3(const int8_t* __restrict__ q, int64_t n, int64_t n_pad, int nsig, int maxlev,
+                          uint8_t* __restrict__ qe, uint32_t* __restrict__ status) {
   const int64_t total = (int64_t)nsig * n_pad;
+  const uint32_t lim = 0x01010101u * (uint32_t)maxlev;
+  bool bad = false;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < total;
        i += (int64_t)gridDim.x * blockDim.x * 4) {
     const int64_t s = i / n_pad, j = i - s * n_pad;  // n_pad % 4 == 0: one signal per word
@@ -1465,17 +1486,20 @@ __global__ void k_to_e4m3(const int8_t* __restrict__ q, int64_t n, int64_t n_pad
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (j + k < n) w |= (uint32_t)(uint8_t)q[s * n + j + k] << (8 * k);
+    bad |= __vcmpgtu4(__vabs4(w), lim) != 0u;  // -128 stays 0x80 and is flagged
     *reinterpret_cast<uint32_t*>(qe + i) = e4m3x4(w);
   }
+  if (bad) atomicOr(status, TDE_ST_INTERNAL);
 }
 
-cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qe,
-                           cudaStream_t st) {
+cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, int bits, uint8_t* d_qe,
+                           uint32_t* d_status, cudaStream_t st) {
   if (nsig <= 0) return cudaSuccess;
   if (n_pad % 4 != 0 || n_pad < n) return cudaErrorInvalidValue;
+  if (bits != 1 && bits != 2 && bits != 4) return cudaErrorInvalidValue;
   const int64_t words = (int64_t)nsig * n_pad / 4;
   const int64_t grid = words / 256 + 1 < 4096 ? words / 256 + 1 : 4096;
-  k_to_e4m3<<<(unsigned)grid, 256, 0, st>>>(d_q, n, n_pad, nsig, d_qe);
+  k_to_e4m3<<<(unsigned)grid, 256, 0, st>>>(d_q, n, n_pad, nsig, bits == 4 ? 7 : 1, d_qe, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

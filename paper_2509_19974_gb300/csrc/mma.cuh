@@ -46,15 +46,18 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
 // The learned proposal's windows on the tensor cores: the levels as E4M3
 // bytes d_qe, signal stride n_pad (a multiple of 128, zeros in [n, n_pad),
 // 16-byte aligned); pair p is x = signal 2 p, y = signal 2 p + 1 (n levels
-// each, |level| <= 7); its 8 windows d_jobs[8 p + w] (lag_lo,
+// each, |level| <= 2^(bits-1)); its 8 windows d_jobs[8 p + w] (lag_lo,
 // lag_hi <= lag_lo + 256, c) receive c[i] += sum_n x[n] y[n + lag_lo + i] for
 // lag_lo + i <= lag_hi (other entries are not written): the c buffers must be
-// zeroed first.
-cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs,
+// zeroed first.  bits sets how many samples one FP32 accumulator may sum while
+// staying exact; the caller checks that n * 4^(bits-1) < 2^31 for the int32 c.
+cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, int bits,
                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
 // One CTA whose bounded waits (the kernels' own) run out on a barrier
 // nothing arrives on: TDE_ST_TIMEOUT in d_status after about 4 s.
 cudaError_t launch_wait_selftest(uint32_t* d_status, cudaStream_t st);
 // Levels [nsig][n] -> E4M3 bytes [nsig][n_pad] (zeros past n); n_pad % 4 == 0.
-cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qe,
-                           cudaStream_t st);
+// A level outside the bits' range (|q| > 1, or > 7 for bits 4) flags
+// TDE_ST_INTERNAL in d_status.
+cudaError_t launch_to_e4m3(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, int bits, uint8_t* d_qe,
+                           uint32_t* d_status, cudaStream_t st);

@@ -17,7 +17,9 @@
 // Host code must not hand the array's name to a kernel (on the host it is a
 // stand-in symbol, not a device address): the first call on each device asks
 // the runtime for the device address with cudaGetSymbolAddress (with that
-// device current) and caches it.  All calls share the array, and it keeps the
+// device current) and caches it for the life of the process (a
+// cudaDeviceReset of that device would make the cached address stale, so the
+// entry point must not be used across one).  All calls share the array, and it keeps the
 // previous call's contents, so each call clears the histograms it uses and
 // rewrites the descriptors and state; calls whose kernels overlap on the GPU
 // (different streams, no ordering between them) race on it.

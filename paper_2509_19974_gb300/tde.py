@@ -379,14 +379,22 @@ def tde_quantize_noalloc(x: torch.Tensor, bits: int, q_out=None, status_out=None
     16) or [n]; returns (q [nsig, n] int8, status uint32 tensor of one word,
     bit 0 = NaN/Inf seen).  Output tensors may be passed in preallocated."""
     _need(x, torch.float32, "x")
+    if x.dim() not in (1, 2):
+        raise ValueError("x must be [n] or [nsig, n]")
     nsig, n = (1, x.numel()) if x.dim() == 1 else (x.shape[0], x.shape[1])
     if q_out is None:
         q_out = torch.empty(x.shape, dtype=torch.int8, device=x.device)
     if status_out is None:
         status_out = torch.empty(1, dtype=torch.int32, device=x.device)
     _need(q_out, torch.int8, "q_out")
-    s = load().tde_quantize_noalloc(x.data_ptr(), int(n), int(nsig), int(bits), q_out.data_ptr(),
-                                    status_out.data_ptr(), _stream(stream))
+    if q_out.shape != x.shape or q_out.device != x.device:
+        raise ValueError("q_out must have x's shape and device")
+    if status_out.dtype not in (torch.int32, torch.uint32) or status_out.numel() < 1 \
+            or status_out.device != x.device:
+        raise ValueError("status_out must be a 32-bit integer tensor on x's device")
+    with torch.cuda.device(x.device):  # the library runs on the current device
+        s = load().tde_quantize_noalloc(x.data_ptr(), int(n), int(nsig), int(bits), q_out.data_ptr(),
+                                        status_out.data_ptr(), _stream(stream))
     if s != TDE_OK:
         raise TdeError(s, "tde_quantize_noalloc failed")
     return q_out, status_out

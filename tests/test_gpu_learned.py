@@ -184,6 +184,97 @@ def test_xcorr_windows_match_oracle_at_edges(ctx, bits, n):
             assert np.array_equal(c[p, w], ref), (p, w)
 
 
+def _window_lags(cent):
+    return cent[..., None].astype(np.int64) + np.arange(-128, 129)
+
+
+@pytest.mark.parametrize("bits,n,P,lev", [(4, 1 << 20, 320, 7), (2, (1 << 22) + 4133, 320, 1)])
+def test_xcorr_windows_exact_on_long_pairs(ctx, bits, n, P, lev):
+    """Eq. (1) in the windows stays exact where one CTA's share of a pair sums
+    more samples than FP32 holds exactly: every level at +lev (the largest
+    magnitude of the bits), so c[tau] = lev^2 (n - |tau|) reaches
+    49 * 2^20 > 2^24 at b = 4, with enough pairs that a CTA's run covers
+    whole pairs.  The closed form is checked against the oracle at sampled
+    lags, then every window value against the closed form."""
+    import oracle
+    rng = np.random.default_rng(n + bits)
+    q = torch.full((2 * P, n), lev, dtype=torch.int8, device="cuda")
+    cent = np.empty((P, 8), np.int32)
+    cent[:, 0] = 0
+    cent[:, 1] = -(n - 1)
+    cent[:, 2] = n - 1
+    cent[:, 3:] = rng.integers(-(n - 1), n, size=(P, 5))
+    c = tde.tde_xcorr_windows(ctx, q, bits, torch.from_numpy(cent).cuda())
+    ctx.sync()
+    c = c.cpu().numpy().astype(np.int64)
+    lags = _window_lags(cent)
+    inr = np.abs(lags) <= n - 1
+    closed = np.where(inr, lev * lev * (n - np.abs(lags)), 0)
+    assert int(closed.max()) == lev * lev * n
+    ones = np.full(n, lev, np.int8)
+    sample = np.array([0, 1, -1, n - 1, -(n - 1), 12345, -777777 % n, n // 2])
+    assert np.array_equal(oracle.xcorr_at(ones, ones, sample), lev * lev * (n - np.abs(sample)))
+    bad = np.argwhere(c != closed)
+    assert bad.size == 0, (bad[:5], c[tuple(bad[0])], closed[tuple(bad[0])])
+
+
+def test_xcorr_windows_exact_random_b4_long(ctx):
+    """Random b = 4 levels, y a shifted copy of x, n = 2^20, 320 pairs: the
+    matched lag sums about 19.6e6 > 2^24; two pairs' windows (around the shift
+    and elsewhere) are compared with the oracle lag by lag."""
+    import oracle
+    n, P = 1 << 20, 320
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randint(-7, 8, (P, n + 8192), dtype=torch.int8, device="cuda", generator=g)
+    d = np.random.default_rng(9).integers(-4000, 4001, size=P)
+    q = torch.empty((2 * P, n), dtype=torch.int8, device="cuda")
+    q[0::2] = x[:, 4096:4096 + n]
+    for p in range(P):  # x[n] = y[n + d]
+        q[2 * p + 1] = x[p, 4096 - int(d[p]):4096 - int(d[p]) + n]
+    cent = np.empty((P, 8), np.int32)
+    cent[:, 0] = d
+    cent[:, 1:] = np.random.default_rng(10).integers(-(n - 1), n, size=(P, 7))
+    c = tde.tde_xcorr_windows(ctx, q, 4, torch.from_numpy(cent).cuda())
+    ctx.sync()
+    c = c.cpu().numpy().astype(np.int64)
+    qh = q.cpu().numpy()
+    for p in (0, P - 1):
+        lags = _window_lags(cent[p])
+        want = oracle.xcorr_at(qh[2 * p], qh[2 * p + 1], lags.reshape(-1)).reshape(8, 257)
+        assert want[0, 128] > (1 << 24)
+        assert np.array_equal(c[p], want), p
+
+
+def test_xcorr_windows_int32_overflow_refused(ctx):
+    """n * (2^(bits-1))^2 >= 2^31 cannot be held in the int32 windows: the call
+    is refused on the host with TDE_ERR_OVERFLOW (b = 4, n = 2^25)."""
+    n = 1 << 25
+    q = torch.zeros((2, n), dtype=torch.int8, device="cuda")
+    cent = torch.zeros((1, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(tde.TdeError) as e:
+        tde.tde_xcorr_windows(ctx, q, 4, cent)
+    assert e.value.status == tde.TDE_ERR_OVERFLOW
+    tde.tde_xcorr_windows(ctx, q[:, : n // 2].contiguous(), 4, cent)  # 2^24 * 64 = 2^30 fits
+    ctx.sync()
+
+
+def test_xcorr_windows_level_outside_bits_flagged(ctx):
+    """A level outside the bits' range (3 with bits = 2) is flagged on the
+    device: the next sync returns TDE_ERR_INVALID, and the context is then
+    usable again."""
+    q = torch.ones((2, 4096), dtype=torch.int8, device="cuda")
+    q[0, 17] = 3
+    cent = torch.zeros((1, 8), dtype=torch.int32, device="cuda")
+    tde.tde_xcorr_windows(ctx, q, 2, cent)
+    with pytest.raises(tde.TdeError) as e:
+        ctx.sync()
+    assert e.value.status == tde.TDE_ERR_INVALID
+    q[0, 17] = 1
+    c = tde.tde_xcorr_windows(ctx, q, 2, cent)
+    ctx.sync()
+    assert int(c[0, 0, 128]) == 4096
+
+
 def test_learned_batch_graph_mixed_fallback(ctx):
     """The graph-captured learned estimate: with theta between the pairs'
     margins some pairs fall back (decided on the device); every lag is the
