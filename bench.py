@@ -79,6 +79,11 @@ def parse():
     ap.add_argument("--in-flight", type=int, default=3,
                     help="learned form: batches in flight on separate streams (1 = one stream)")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--agree-pairs", type=int, default=16384,
+                    help="proposal workload: fresh pairs checked against the full form")
+    ap.add_argument("--c5-rounds", type=int, default=4,
+                    help="proposal workload: timed rounds, each on fresh batches")
+    ap.add_argument("--no-proposal-pairs", action="store_true")
     return ap.parse_args()
 
 
@@ -231,6 +236,113 @@ def run_reference(args):
            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+# Pairs of the learned proposal's own workload: N = 65536, 2-bit, shift
+# d ~ U[-16384, 16384], AR(1) coefficient ~ U[0, 0.98], SNR ~ U[-5, 30] dB,
+# drawn by the device generator from a pair-index range disjoint from the
+# checkpoint's training, calibration and test pairs.
+PROPOSAL_SEED = 1005
+PROPOSAL_DMAX, PROPOSAL_AR, PROPOSAL_SNR = 16384, (0.0, 0.98), (-5.0, 30.0)
+PROPOSAL_BENCH_FIRST = 3 << 40
+
+
+def proposal_pairs_record(ctx, model, theta, args, stream, barrier, world, rank, local):
+    """The learned form against the full form on the proposal workload's
+    pairs, where low SNR and smooth sources make the proposal fall back:
+    lag agreement and fallback rate over --agree-pairs fresh pairs (every
+    rank its own), and both forms' throughput over --c5-rounds refills of
+    the timed plans' buffers with fresh batches (the fallback decided and run
+    on the device inside the timed steps)."""
+    import torch
+    from paper_2509_19974_gb300 import tde
+    P, n = args.npairs, args.n
+    first0 = PROPOSAL_BENCH_FIRST + (rank << 32)
+    nbuf = max(1, args.in_flight)
+    bufs = [(torch.empty((P, n), dtype=torch.float32, device="cuda"),
+             torch.empty((P, n), dtype=torch.float32, device="cuda")) for _ in range(nbuf)]
+    plans = [tde.LearnedBatch(model, xb, yb, args.bits, theta) for xb, yb in bufs]
+    sts = [stream] + [torch.cuda.Stream() for _ in range(nbuf - 1)]
+    full = tde.Batch(ctx, None, None, args.bits, engine=args.engine,
+                     descs=tde.make_descs(list(bufs[0][0].unbind(0)), list(bufs[0][1].unbind(0))))
+    batch_no = [0]
+
+    def fill(k):
+        x, y, _ = tde.synth_pairs(ctx, PROPOSAL_SEED, first0 + batch_no[0] * P, P, n,
+                                  PROPOSAL_DMAX, PROPOSAL_AR, PROPOSAL_SNR)
+        bufs[k][0].copy_(x)
+        bufs[k][1].copy_(y)
+        batch_no[0] += 1
+
+    # agreement and fallback on fresh pairs, batch after batch through plan 0
+    nb = max(1, args.agree_pairs // P)
+    agree = fb = 0
+    for _ in range(nb):
+        fill(0)
+        lf, vf = [t.clone() for t in full.run(stream)]
+        ll, lv, lfb = plans[0].run(stream)
+        agree += int(((ll == lf) & (lv == vf)).sum())
+        fb += int(lfb.sum())
+    torch.cuda.synchronize()
+    # throughput: each round refills every plan's buffers (untimed), then times
+    # `steps` steps of each form on them
+    for k in range(nbuf):
+        fill(k)
+    torch.cuda.synchronize()  # the fills (current stream) before other streams read them
+    for _ in range(max(3, args.warmup)):
+        for pl, st in zip(plans, sts):
+            pl.run(st)
+        full.run(stream)
+    torch.cuda.synchronize()  # no run in flight while the next fills write the buffers
+    t_l = t_f = 0.0
+    steps_l = steps_f = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local, "proposal") as clk:
+        for _ in range(args.c5_rounds):
+            for k in range(nbuf):
+                fill(k)
+            barrier()
+            e0.record(stream)
+            for s_ in sts[1:]:
+                s_.wait_event(e0)
+            for i in range(args.steps):
+                plans[i % nbuf].run(sts[i % nbuf])
+            for s_ in sts[1:]:
+                ev = torch.cuda.Event()
+                ev.record(s_)
+                stream.wait_event(ev)
+            e1.record(stream)
+            barrier()
+            t_l += max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
+            steps_l += args.steps
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                full.run(stream)
+            e1.record(stream)
+            barrier()
+            t_f += max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
+            steps_f += args.steps
+    for pl in plans:
+        pl.close()
+    full.close()
+    checked = nb * P
+    a = min_over_ranks(agree / checked, world, device="cuda")
+    v_l = P * world * steps_l / (t_l / 1e3)
+    v_f = P * world * steps_f / (t_f / 1e3)
+    return {"workload": f"{P} pairs/GPU per step, N={n}, b={args.bits}, d~U[-{PROPOSAL_DMAX},"
+                        f"{PROPOSAL_DMAX}], AR(1) a~U[0,0.98], SNR~U[-5,30] dB (device generator, "
+                        "pairs disjoint from the checkpoint's training/calibration/test pairs), "
+                        "all lags",
+            "pairs_checked": checked * world, "lag_agreement_with_full": a,
+            "fallback_rate": fb / checked, "theta": theta,
+            "learned": {"value": v_l, "unit": "pairs/s", "ms_per_step": t_l / steps_l,
+                        "in_flight": nbuf, "steps": steps_l,
+                        "batches": f"{args.c5_rounds} rounds x {nbuf} fresh batches"},
+            "full": {"value": v_f, "unit": "pairs/s", "ms_per_step": t_f / steps_f,
+                     "steps": steps_f},
+            "speedup_vs_full": v_l / v_f, "target_met": bool(a >= 0.999 and v_l > v_f),
+            "clocks": clk.summary()}
 
 
 def pipelined_e2e(make_plan, X, Y, steps, stream, barrier):
@@ -483,6 +595,9 @@ def main():
                                   "train_seconds": meta.get("train_seconds"),
                                   "calibration": meta.get("calibration"),
                                   "test": meta.get("test")}}
+        if not args.no_proposal_pairs:
+            learned["proposal_pairs"] = proposal_pairs_record(ctx, model, theta, args, stream,
+                                                              barrier, world, rank, local)
         model.close()
 
     # --- FP32 FFT comparator beside it: the same quantized pairs, timed alone

@@ -10,7 +10,7 @@ proposed windows.  Training, labelling and generation all run in libtde's
 kernels; the host only sequences the calls, logs and checkpoints.
 
 After training the confidence threshold theta is calibrated on held-out pairs
-(the smallest theta at which at most 0.05% of the held-out pairs keep a
+(the smallest theta at which at most 0.02% of 65536 held-out pairs keep a
 windowed lag whose window misses the full argmax), and the
 learned estimator is measured against the full one on separate test pairs.
 """
@@ -56,12 +56,12 @@ def main():
     ap.add_argument("--pairs", type=int, default=1 << 20)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--cal-pairs", type=int, default=16384)
+    ap.add_argument("--cal-pairs", type=int, default=65536)
     ap.add_argument("--test-pairs", type=int, default=65536)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "models",
                                                   "proposal_n65536_b2.npz"))
     ap.add_argument("--log", default=None)
-    ap.add_argument("--miss-budget", type=float, default=0.0005)
+    ap.add_argument("--miss-budget", type=float, default=0.0002)
     ap.add_argument("--calibrate-only", default=None,
                     help="load this checkpoint, skip training, recalibrate and retest")
     args = ap.parse_args()
@@ -98,7 +98,7 @@ def main():
         hit.append(hits(c, lags))
     margins, hit = torch.cat(margins), torch.cat(hit)
     # theta: at most `budget` held-out misses keep their (wrong) windowed lag;
-    # half of the 0.1% disagreement the estimator may have, for headroom.
+    # a fifth of the 0.1% disagreement the estimator may have, for headroom.
     budget = int(args.miss_budget * hit.numel())
     miss_m = torch.sort(margins[~hit], descending=True).values
     theta = float(miss_m[budget]) + 1e-6 if miss_m.numel() > budget else 0.0
