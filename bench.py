@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--c5-rounds", type=int, default=4,
                     help="proposal workload: timed rounds, each on fresh batches")
     ap.add_argument("--no-proposal-pairs", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the single-pair, uneven-batch and template-search records")
     return ap.parse_args()
 
 
@@ -343,6 +345,122 @@ def proposal_pairs_record(ctx, model, theta, args, stream, barrier, world, rank,
                      "steps": steps_f},
             "speedup_vs_full": v_l / v_f, "target_met": bool(a >= 0.999 and v_l > v_f),
             "clocks": clk.summary()}
+
+
+def other_workloads(ctx, args, local):
+    """The other seeded workloads on this GPU, each through the public API
+    with CUDA events on the current stream after warm-up, with the SM clocks
+    sampled over its timed region and its results checked against the oracle
+    on a stated subset:
+      single    one pair, N = 4096, b = 1, lags +-4095 (one-pair planned batch
+                replayed from its graph, AUTO);
+      uneven    4096 pairs, N log-uniform on [1024, 262144], b = 2, lags
+                +-N/8 (one planned batch replayed from its graph, AUTO);
+      template  a 2^14-sample template in a 2^24-sample signal, b = 4, every
+                valid lag, int64 (AUTO)."""
+    import torch
+    import oracle
+    from paper_2509_19974_gb300 import synth, tde
+    oracle.build()
+    pk, pk_kind = peaks()
+    peak_fl = pk["bf16_tflops"] * FP8_OVER_BF16 * 1e12
+    out = {}
+
+    def timed(fn, reps, tag):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local, tag) as clk:
+            st = torch.cuda.current_stream()
+            e0.record(st)
+            for _ in range(reps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, clk.summary()
+
+    # single pair
+    b = synth.single_pair(bits=1)
+    x, y = torch.from_numpy(b.x[0]).cuda(), torch.from_numpy(b.y[0]).cuda()
+    bt = tde.Batch(ctx, [x], [y], 1, engine="auto")
+    ms, clk = timed(bt.run, 200, "single")
+    lags, vals = bt.run()
+    want = oracle.estimate(b.x[0], b.y[0], 1)
+    macs = overlap_macs(4096, 4096, -4095, 4095)
+    out["single_pair"] = {
+        "workload": "1 pair, N=4096, b=1 sign, lags +-4095, one-pair planned batch replayed "
+                    "from its CUDA graph, AUTO engine",
+        "us_per_estimate": ms * 1e3, "estimates_per_s": 1e3 / ms, "mac_per_s": macs / (ms / 1e3),
+        "bound": "launch latency (six small launches per replay)",
+        "parity": {"checked_pairs": 1, "lag_value_mismatches":
+                   int((int(lags[0]), int(vals[0])) != want)}, "clocks": clk}
+    bt.close()
+
+    # uneven batch
+    b = synth.uneven_batch()
+    xs = [torch.from_numpy(v).cuda() for v in b.x]
+    ys = [torch.from_numpy(v).cuda() for v in b.y]
+    macs = float(sum(overlap_macs(len(xv), len(yv), int(lo), int(hi))
+                     for xv, yv, lo, hi in zip(b.x, b.y, b.lag_min, b.lag_max)))
+    bt = tde.Batch(ctx, xs, ys, 2, b.lag_min, b.lag_max, engine="auto")
+    ms, clk = timed(bt.run, max(3, args.steps // 2), "uneven")
+    lags, vals = [t.cpu().numpy() for t in bt.run()]
+    order = np.argsort([len(v) for v in b.x], kind="stable")
+    subset = list(order[:12]) + list(np.random.default_rng(7).choice(order[:2048], 4, replace=False))
+    mism = sum(int((int(lags[i]), int(vals[i])) !=
+                   oracle.estimate(b.x[i], b.y[i], 2, int(b.lag_min[i]), int(b.lag_max[i])))
+               for i in subset)
+    out["uneven_batch"] = {
+        "workload": f"{b.npairs} pairs, N log-uniform on [1024, 262144] (x64), b=2, lags +-N/8, "
+                    "one planned batch replayed from its CUDA graph, AUTO engine per pair",
+        "ms_per_batch": ms, "pairs_per_s": b.npairs / (ms / 1e3), "mac_per_s": macs / (ms / 1e3),
+        "roofline": {"bound": "tensor", "achieved": 2 * macs / (ms / 1e3) / 1e12,
+                     "peak": peak_fl / 1e12, "unit": "TFLOP/s",
+                     "frac": 2 * macs / (ms / 1e3) / peak_fl,
+                     "what": "whole replayed step (quantize, every engine, argmax) against the "
+                             f"{pk_kind} BF16 burst x 2 (FP8); 2 FLOP per overlap MAC"},
+        "parity": {"checked_pairs": len(subset), "lag_value_mismatches": mism,
+                   "subset": "the 12 shortest pairs and 4 drawn from the shorter half (seed 7)"},
+        "clocks": clk}
+    bt.close()
+    del xs, ys
+
+    # template search
+    b = synth.template_search()
+    lo, hi = int(b.lag_min[0]), int(b.lag_max[0])
+    x, y = torch.from_numpy(b.x[0]).cuda(), torch.from_numpy(b.y[0]).cuda()
+    qx, qy = ctx.quantize(x, 4), ctx.quantize(y, 4)
+    c = torch.empty(hi - lo + 1, dtype=torch.int64, device="cuda")
+    macs = float((hi - lo + 1) * len(b.y[0]))
+    eng = tde.pick_engine(4, len(b.x[0]), len(b.y[0]), hi - lo + 1)
+
+    def run():
+        ctx.xcorr_int(qx, qy, 4, lo, hi, engine="auto", dtype=torch.int64, c_out=c)
+    ms, clk = timed(run, max(3, args.steps), "template")
+    lag, val = ctx.argmax(c, lo)
+    lag, val = int(lag.item()), int(val.item())
+    qxh, qyh = oracle.quantize(b.x[0], 4), oracle.quantize(b.y[0], 4)
+    rng = np.random.default_rng(11)
+    sample = np.concatenate([[lo, hi, lag], rng.integers(lo, hi + 1, 61)]).astype(np.int64)
+    ch = c.cpu().numpy()
+    ref = oracle.xcorr_at(qxh, qyh, sample)
+    mism = int(np.sum(ch[sample - lo] != ref)) + int(val != int(ref[2]))
+    out["template_search"] = {
+        "workload": "x 2^24 white + y 2^14 AR(1) 0.9 embedded at a uniform offset, -5 dB, b=4, "
+                    f"every valid lag ({hi - lo + 1}), int64, AUTO engine ({eng})",
+        "ms": ms, "mac_per_s": macs / (ms / 1e3),
+        "roofline": {"bound": "tensor", "achieved": 2 * macs / (ms / 1e3) / 1e12,
+                     "peak": peak_fl / 1e12, "unit": "TFLOP/s",
+                     "frac": 2 * macs / (ms / 1e3) / peak_fl,
+                     "what": f"the correlation call against the {pk_kind} BF16 burst x 2 (FP8); "
+                             "2 FLOP per valid-lag MAC"},
+        "lag": lag, "true_lag": int(b.shift[0]),
+        "parity": {"checked_lags": len(sample), "value_mismatches": mism,
+                   "subset": "both ends, the GPU's argmax and 61 seeded lags vs the oracle's "
+                             "correlation at those lags"},
+        "clocks": clk}
+    return out
 
 
 def pipelined_e2e(make_plan, X, Y, steps, stream, barrier):
@@ -701,6 +819,8 @@ def main():
         mism = sum(1 for k, (l, v) in enumerate(ref) if (int(gpu_lags[k]), int(gpu_vals[k])) != (l, v))
         out["parity"] = {"checked_pairs": len(ref), "lag_value_mismatches": mism}
     out["true_shift_hit_rate"] = float(np.mean(gpu_lags == b.shift))
+    if not args.no_workloads and world == 1:
+        out["workloads"] = other_workloads(ctx, args, local)
     print(json.dumps(out))
     if world > 1:
         dist.barrier()
