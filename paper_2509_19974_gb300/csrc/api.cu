@@ -1583,10 +1583,15 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
     TDE_COUNT_LAUNCH(1);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = launch_to_e4m3(q, n, n_pad, 2 * npairs, bits, qe, ctx->d_status, st);
+  // levels in {-1, 0, 1} (bits 1, 2): packed E2M1 operands; bits 4: E4M3
+  const bool fp4 = bits <= 2;
+  if (e == cudaSuccess)
+    e = fp4 ? launch_to_e2m1(q, n, n_pad, 2 * npairs, qe, ctx->d_status, st)
+            : launch_to_e4m3(q, n, n_pad, 2 * npairs, bits, qe, ctx->d_status, st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(qe, n, n_pad, npairs, bits, jobs, ctx->d_status, st);
+    e = fp4 ? launch_xcorr_mma_windows4(qe, n, n_pad, npairs, bits, jobs, ctx->d_status, st)
+            : launch_xcorr_mma_windows(qe, n, n_pad, npairs, bits, jobs, ctx->d_status, st);
   }
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "windows");
 }

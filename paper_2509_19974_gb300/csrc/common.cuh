@@ -36,6 +36,20 @@ __device__ __forceinline__ uint32_t e4m3x4(uint32_t w) {
 __device__ __forceinline__ uint4 e4m3x16(uint4 v) {
   return make_uint4(e4m3x4(v.x), e4m3x4(v.y), e4m3x4(v.z), e4m3x4(v.w));
 }
+
+// Four int8 levels in {-1, 0, 1} -> four packed E2M1 nibbles (exact: 0 ->
+// 0x0, 1 -> 0x2 = 1.0, -1 -> 0xA = -1.0), level i in bits 4i .. 4i + 3, so
+// sample 2j of a packed signal sits in the low nibble of byte j.  Nibble of
+// byte b: bit 1 if b != 0, bit 3 = b's sign.
+__device__ __forceinline__ uint32_t e2m1x4(uint32_t w) {
+  const uint32_t t = (__vcmpne4(w, 0u) & 0x02020202u) | ((w >> 4) & 0x08080808u);
+  const uint32_t u = t | (t >> 4);
+  return (u & 0xFFu) | ((u >> 8) & 0xFF00u);
+}
+// 16 levels -> 8 bytes of packed E2M1
+__device__ __forceinline__ uint2 e2m1x16(uint4 v) {
+  return make_uint2(e2m1x4(v.x) | (e2m1x4(v.y) << 16), e2m1x4(v.z) | (e2m1x4(v.w) << 16));
+}
 #endif
 
 // ---------------------------------------------------------------- quantize

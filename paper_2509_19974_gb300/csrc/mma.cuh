@@ -53,6 +53,17 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
 // staying exact; the caller checks that n * 4^(bits-1) < 2^31 for the int32 c.
 cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, int bits,
                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
+// The same windows from packed E2M1 levels (levels in {-1, 0, 1}, bits 1 or
+// 2): d_qf holds signal s at d_qf + s * n_pad / 2, sample i in nibble i & 1 of
+// byte i / 2 (low nibble first), zeros in [n, n_pad); n_pad a multiple of
+// 128, d_qf 16-byte aligned.  Computed with block-scaled FP4 MMAs (unit
+// scales), K = 64 samples per MMA.
+cudaError_t launch_xcorr_mma_windows4(const uint8_t* d_qf, int64_t n, int64_t n_pad, int npairs, int bits,
+                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
+// Levels [nsig][n] -> packed E2M1 [nsig][n_pad / 2 bytes] (zeros past n);
+// n_pad % 8 == 0.  A level outside {-1, 0, 1} flags TDE_ST_INTERNAL.
+cudaError_t launch_to_e2m1(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qf,
+                           uint32_t* d_status, cudaStream_t st);
 // One CTA whose bounded waits (the kernels' own) run out on a barrier
 // nothing arrives on: TDE_ST_TIMEOUT in d_status after about 4 s.
 cudaError_t launch_wait_selftest(uint32_t* d_status, cudaStream_t st);
