@@ -1676,7 +1676,7 @@ void learned_plan(LearnedWork* w, int npairs, int64_t n, int bits, float theta) 
   const int S = 2 * npairs;
   w->Q.plan(L, S, bits, nullptr, n);
   w->o_q = L.w<int8_t>((size_t)S * n);
-  w->o_qe = L.w<uint8_t>((size_t)S * n);  // the levels as E4M3 bytes (n % 2048 == 0)
+  w->o_qe = L.w<uint8_t>((size_t)S * n / 2);  // the levels as packed E2M1 (n % 2048 == 0)
   w->C.plan(L, npairs, n, false);
   w->o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
   w->o_marg = L.w<float>((size_t)npairs);
@@ -1748,7 +1748,7 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   }
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows(qe, n, n, P, w.bits, jobs, ctx->d_status, st);
+    e = launch_xcorr_mma_windows4(qe, n, n, P, w.bits, jobs, ctx->d_status, st);
   }
   if (e == cudaSuccess) e = launch_window_argmax(jobs, P, lag_out, val_out, st);
   // fallback, decided and run on the device

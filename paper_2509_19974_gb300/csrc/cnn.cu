@@ -908,10 +908,10 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
+                             uint8_t* qf, uint32_t* d_status, cudaStream_t st) {
   const int Ld = (int)(n / kCnnDec);
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
-  cudaError_t e = launch_cnn_conv1_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qe,
+  cudaError_t e = launch_cnn_conv1_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qf,
                                       d_status, st);
   if (e != cudaSuccess) return e;
   k_eo_pad<<<(nsig + 63) / 64, 256, 0, st>>>(act[0], Ld / 2, nsig);

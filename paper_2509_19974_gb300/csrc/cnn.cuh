@@ -41,11 +41,12 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 // layers: act[l] holds layer l's output, nsig x cnn_eo_elems((n/16) >> (l+1))
 // BF16 in the layout above; feat receives the FP32 features [nsig][n/256][32]
 // (position-major);
-// qe (nullable, nsig x n bytes) the levels as E4M3 bytes.  n a multiple of
+// qf (nullable, nsig x n / 2 bytes) the levels as packed E2M1 nibbles (sample
+// i in nibble i & 1 of byte i / 2; levels in {-1, 0, 1}).  n a multiple of
 // 2048.
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             uint8_t* qe, uint32_t* d_status, cudaStream_t st);
+                             uint8_t* qf, uint32_t* d_status, cudaStream_t st);
 // Inference activations between conv layers: a layer's input of length L
 // is, per signal, 8 arrays (position parity x 8-channel chunk, parity-major)
 // of cnn_eo_rows(L) rows of 8 BF16 channels; row r holds position 2r - 4
@@ -65,9 +66,10 @@ cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, c
 // The first layer of the inference forward on the tensor cores (mma.cu):
 // decimation of q [nsig][n] int8, conv 1 -> 32 (weights wbf [32][1][9], bias)
 // -> out, the second layer's input (length n/32, parity arrays; the zero rows
-// are the caller's); qe (nullable) receives the levels as E4M3 bytes.
+// are the caller's); qf (nullable) receives the levels as packed E2M1 nibbles
+// (levels in {-1, 0, 1}).
 cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
-                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st);
+                                uint16_t* out, uint8_t* qf, uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1;
 // channel-major [S][32][Lf], or position-major [S][Lf][32] with pos_major).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,

@@ -1588,7 +1588,8 @@ __global__ void __launch_bounds__(kThreads, kCvCtasPerSm)
 // kernel 9, pad 4, bias, ReLU, max-pool 2) on the tensor cores.  A CTA takes
 // 128 pooled outputs P0 + m of one signal: it reads the 16 (264) level bytes
 // per decimated sample d[j] = (sum of 16 levels) / 4 (exact in BF16: |4 d| <=
-// 112), writes the E4M3 copy of the levels it owns, builds the im2col operand
+// 112), writes the packed E2M1 copy of the levels it owns (for the windows;
+// levels in {-1, 0, 1}), builds the im2col operand
 //   A_par[m][k] = d[2 (P0 + m) + par + k - 4]   (k < 9; k = 9..15 zero)
 // for both parities of the pooling pair as K-major no-swizzle tiles (16-byte
 // rows of 8 taps, leading byte offset 2048 between the two 8-tap halves), and
@@ -1607,7 +1608,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restri
                                                       const uint16_t* __restrict__ wbf,
                                                       const float* __restrict__ bias,
                                                       uint16_t* __restrict__ out,
-                                                      uint8_t* __restrict__ qe,
+                                                      uint8_t* __restrict__ qf,
                                                       uint32_t* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -1674,7 +1675,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restri
     const int s = u / tps, P0 = (u - s * tps) * kC1M;
     uint4 wc[2] = {wn[0], wn[1]};
     if (u + 1 < u1) fetch(u + 1, wn);
-    // decimate: d_s[i] = d[2 P0 - 4 + i]; the E4M3 copy of the samples this tile owns
+    // decimate: d_s[i] = d[2 P0 - 4 + i]; the packed E2M1 copy of the samples this tile owns
     const int d0 = 2 * P0 - 4;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -1690,8 +1691,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restri
         acc = __dp4a((int)w.z, 0x01010101, acc);
         acc = __dp4a((int)w.w, 0x01010101, acc);
         v = 0.25f * (float)acc;
-        if (qe && i >= 4 && i < 2 * kC1M + 4)
-          *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
+        if (qf && i >= 4 && i < 2 * kC1M + 4)
+          *reinterpret_cast<uint2*>(qf + ((int64_t)s * n + (int64_t)j * kCnnDec) / 2) = e2m1x16(w);
       }
       d_s[i] = (uint16_t)(__float_as_uint(v) >> 16);  // exact: |4 d| <= 112
     }
@@ -1987,7 +1988,7 @@ cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, c
 }
 
 cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
-                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
+                                uint16_t* out, uint8_t* qf, uint32_t* d_status, cudaStream_t st) {
   if (nsig <= 0) return cudaSuccess;
   const int64_t Ld = n / kCnnDec;
   if (n % kCnnDec != 0 || Ld % 4 != 0 || Ld > INT32_MAX) return cudaErrorInvalidValue;
@@ -2000,7 +2001,7 @@ cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t cap = 4 * (int64_t)sms;  // persistent: four CTAs per SM, contiguous tile runs
   const int grid = (int)(ctas < cap ? ctas : cap);
-  k_conv1_tc<<<grid, kThreads, kC1Smem, st>>>(q, n, nsig, wbf, bias, out, qe, d_status);
+  k_conv1_tc<<<grid, kThreads, kC1Smem, st>>>(q, n, nsig, wbf, bias, out, qf, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
