@@ -48,16 +48,25 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
 SMS = 152          # GB300 SMs
-# The tensor-core kernels compute in E4M3 (kind::f8f6f4): their peak is the
-# measured BF16 peak times the nominal dense FP8 / BF16 ratio (4.5 / 2.25).
+# The tensor-core kernels compute in E4M3 (kind::f8f6f4, bits 4) or in packed
+# E2M1 (kind::mxf4, bits 1 and 2): their peak is the measured BF16 peak times
+# the nominal dense FP8 / BF16 (4.5 / 2.25) or FP4 / BF16 (13.5 / 2.25) ratio.
 FP8_OVER_BF16 = 2.0
+FP4_OVER_BF16 = 6.0
+
+
+def tensor_peak(pk, bits):
+    """(burst TFLOP/s, sustained TFLOP/s, operand type, kernel suffix) of the
+    tensor-core kernels at `bits`."""
+    r, dt, suf = (FP4_OVER_BF16, "e2m1", "4") if bits <= 2 else (FP8_OVER_BF16, "e4m3", "8")
+    return (pk["bf16_tflops"] * r, pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * r, dt, suf)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the engine kernel
 # from one ncu capture of this workload (see profiles/); None once the kernel
 # has changed since the capture.
 # DRAM bytes (read + write) per launch of each form's dominant kernel, from one
 # ncu capture of this bench's workload (profiles/); keyed by (kernel, pairs,
 # N, bits).  Cleared whenever the kernel changes.
-TRAFFIC = {("mma", 256, 65536, 2): 307.7e6, ("win", 256, 65536, 2): 35.8e6}
+TRAFFIC = {("k_xcorr_mma8", 256, 65536, 4): None}
 CKPT = os.path.join(ROOT, "paper_2509_19974_gb300", "models", "proposal_n65536_b2.npz")
 POPC_PER_SM_CLK = 16  # POPC issue rate per SM per clock
 
@@ -363,7 +372,6 @@ def other_workloads(ctx, args, local):
     from paper_2509_19974_gb300 import synth, tde
     oracle.build()
     pk, pk_kind = peaks()
-    peak_fl = pk["bf16_tflops"] * FP8_OVER_BF16 * 1e12
     out = {}
 
     def timed(fn, reps, tag):
@@ -416,10 +424,11 @@ def other_workloads(ctx, args, local):
                     "one planned batch replayed from its CUDA graph, AUTO engine per pair",
         "ms_per_batch": ms, "pairs_per_s": b.npairs / (ms / 1e3), "mac_per_s": macs / (ms / 1e3),
         "roofline": {"bound": "tensor", "achieved": 2 * macs / (ms / 1e3) / 1e12,
-                     "peak": peak_fl / 1e12, "unit": "TFLOP/s",
-                     "frac": 2 * macs / (ms / 1e3) / peak_fl,
+                     "peak": tensor_peak(pk, 2)[0], "unit": "TFLOP/s",
+                     "frac": 2 * macs / (ms / 1e3) / 1e12 / tensor_peak(pk, 2)[0],
                      "what": "whole replayed step (quantize, every engine, argmax) against the "
-                             f"{pk_kind} BF16 burst x 2 (FP8); 2 FLOP per overlap MAC"},
+                             f"{pk_kind} BF16 burst x 6 (nominal FP4: the tensor-core pairs run on "
+                             "E2M1 operands); 2 FLOP per overlap MAC"},
         "parity": {"checked_pairs": len(subset), "lag_value_mismatches": mism,
                    "subset": "the 12 shortest pairs and 4 drawn from the shorter half (seed 7)"},
         "clocks": clk}
@@ -451,10 +460,10 @@ def other_workloads(ctx, args, local):
                     f"every valid lag ({hi - lo + 1}), int64, AUTO engine ({eng})",
         "ms": ms, "mac_per_s": macs / (ms / 1e3),
         "roofline": {"bound": "tensor", "achieved": 2 * macs / (ms / 1e3) / 1e12,
-                     "peak": peak_fl / 1e12, "unit": "TFLOP/s",
-                     "frac": 2 * macs / (ms / 1e3) / peak_fl,
-                     "what": f"the correlation call against the {pk_kind} BF16 burst x 2 (FP8); "
-                             "2 FLOP per valid-lag MAC"},
+                     "peak": tensor_peak(pk, 4)[0], "unit": "TFLOP/s",
+                     "frac": 2 * macs / (ms / 1e3) / 1e12 / tensor_peak(pk, 4)[0],
+                     "what": f"the correlation call against the {pk_kind} BF16 burst x 2 (FP8: b = 4 "
+                             "runs on E4M3 operands); 2 FLOP per valid-lag MAC"},
         "lag": lag, "true_lag": int(b.shift[0]),
         "parity": {"checked_lags": len(sample), "value_mismatches": mism,
                    "subset": "both ends, the GPU's argmax and 61 seeded lags vs the oracle's "
@@ -670,18 +679,18 @@ def main():
                 lo, hi = max(int(c) - 128, -(args.n - 1)), min(int(c) + 128, args.n - 1)
                 win_macs += overlap_macs(args.n, args.n, lo, hi) if hi >= lo else 0
         pk, pk_kind = peaks()
-        peak_fl = pk["bf16_tflops"] * FP8_OVER_BF16 * 1e12
+        pb, ps_, dt, suf = tensor_peak(pk, args.bits)
         ach = 2.0 * win_macs / (wms / max(wl, 1) / 1e3) if wl else None
+        wname = "k_xcorr_mma_win4" if args.bits <= 2 else "k_xcorr_mma_win"
         roof_l = None if ach is None else {
-            "bound": "tensor", "kernel": "k_xcorr_mma_win", "achieved": ach / 1e12,
-            "peak": peak_fl / 1e12, "unit": "TFLOP/s", "frac": ach / peak_fl,
-            "frac_of_sustained": ach / (pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-                                        * FP8_OVER_BF16 * 1e12),
-            "traffic": TRAFFIC.get(("win", args.npairs, args.n, args.bits)),
-            "peak_source": f"{pk_kind} dense BF16 burst (bf16_tflops) x 2 (nominal dense FP8 / "
-                           "BF16): the kernel computes in E4M3; achieved counts 2 FLOP per "
-                           "overlap MAC of the 257-lag windows (algorithmic; the kernel computes "
-                           "1024 lags per window)",
+            "bound": "tensor", "kernel": wname, "achieved": ach / 1e12,
+            "peak": pb, "unit": "TFLOP/s", "frac": ach / 1e12 / pb,
+            "frac_of_sustained": ach / 1e12 / ps_,
+            "traffic": TRAFFIC.get((wname, args.npairs, args.n, args.bits)),
+            "peak_source": f"{pk_kind} dense BF16 burst (bf16_tflops) x {pb / pk['bf16_tflops']:.0f} "
+                           f"(nominal dense {'FP4' if args.bits <= 2 else 'FP8'} / BF16): the kernel's "
+                           f"operands are {dt}; achieved counts 2 FLOP per overlap MAC of the 257-lag "
+                           "windows (algorithmic; the kernel computes 1024 lags per window)",
             "ms_per_launch": wms / wl, "macs_per_launch": win_macs, "launches": wl}
         # end to end: inputs from pinned host memory, lags back, every step
         e2e_l = None
@@ -775,21 +784,24 @@ def main():
                                    f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)"}
         elif engine == "mma":
             tflops = 2.0 * achieved_mac / 1e12
-            peak = pk["bf16_tflops"] * FP8_OVER_BF16
-            roof = {"bound": "tensor", "kernel": "k_xcorr_mma8", "achieved": tflops, "peak": peak,
+            peak, peak_s, dt, suf = tensor_peak(pk, args.bits)
+            kname = "k_xcorr_mma" + suf
+            roof = {"bound": "tensor", "kernel": kname, "achieved": tflops, "peak": peak,
                     "unit": "TFLOP/s", "frac": tflops / peak,
-                    "frac_of_sustained": tflops / (pk["bf16_tflops_sustained"] * FP8_OVER_BF16),
-                    "traffic": TRAFFIC.get(("mma", args.npairs, args.n, args.bits)),
-                    "peak_source": f"{pk_kind} dense BF16 burst (bf16_tflops) x 2 (nominal dense "
-                                   "FP8 / BF16): the kernel computes in E4M3; achieved counts "
-                                   "2 FLOP per overlap MAC (algorithmic)"}
+                    "frac_of_sustained": tflops / peak_s,
+                    "traffic": TRAFFIC.get((kname, args.npairs, args.n, args.bits)),
+                    "peak_source": f"{pk_kind} dense BF16 burst (bf16_tflops) x {peak / pk['bf16_tflops']:.0f} "
+                                   f"(nominal dense {'FP4' if args.bits <= 2 else 'FP8'} / BF16): the "
+                                   f"kernel's operands are {dt}; achieved counts 2 FLOP per overlap MAC "
+                                   "(algorithmic)"}
         if roof is not None:
             roof.update({"ms_per_launch": per_launch_ms, "macs_per_launch": macs_launch,
                          "launches": eng_launches})
 
     out = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": tensor_peak(peaks()[0], args.bits)[2],
            "data": "synthetic", "config": config(args, world), "e2e": e2e,
            "gpu_launches": int(launches), "roofline": roof,
            "no_graph": {"value": args.npairs * world * args.steps / (ms_nograph / 1e3),

@@ -463,8 +463,13 @@ struct MmaStage {
   // ranges into shorter segments (>= kMinSeg samples) so that its items spread
   // over the SMs; the partial sums are added with integer atomics as usual.
   static constexpr int64_t kMinSeg = 2 * kMmaChunk;
-  void plan(Layout& L, const std::vector<Job>& jobs, bool split_small = true) {
+  // fp4: levels in {-1, 0, 1} run on the packed E2M1 kernel, whose tiles are
+  // 128 columns (16384 lags) wide; otherwise E4M3 tiles of 256 columns.
+  bool fp4 = false;
+  void plan(Layout& L, const std::vector<Job>& jobs, bool split_small = true, bool use_fp4 = false) {
     njobs = (int)jobs.size();
+    fp4 = use_fp4;
+    const int64_t tile = fp4 ? kMmaTileLags4 : kMmaTileLags, cols = tile / 128;
     items.clear();
     zero_first.assign(njobs, 0);
     struct Tile {
@@ -477,12 +482,12 @@ struct MmaStage {
       const Job& j = jobs[i];
       max_count = std::max<int64_t>(max_count, j.lag_max - j.lag_min + 1);
       const int64_t t0 = floor_div64(j.lag_min, kMmaChunk) * kMmaChunk;
-      const int64_t ntiles = ceil_div64(j.lag_max - t0 + 1, kMmaTileLags);
+      const int64_t ntiles = ceil_div64(j.lag_max - t0 + 1, tile);
       for (int64_t t = 0; t < ntiles; ++t) {
-        const int64_t T0 = t0 + t * kMmaTileLags;
+        const int64_t T0 = t0 + t * tile;
         // k = x index + (127 - m); nonzero terms need k in [0, nx + 127) and
-        // y index k + T0 + 128 n in [0, ny) for some n in [0, 256).
-        int64_t klo = std::max<int64_t>(0, -T0 - 128 * 255);
+        // y index k + T0 + 128 n in [0, ny) for some n in [0, cols).
+        int64_t klo = std::max<int64_t>(0, -T0 - 128 * (cols - 1));
         int64_t khi = std::min<int64_t>(j.nx + 127, j.ny - T0);
         klo = floor_div64(klo, kMmaChunk) * kMmaChunk;
         khi = ceil_div64(khi, kMmaChunk) * kMmaChunk;
@@ -540,8 +545,9 @@ struct MmaStage {
       if (e != cudaSuccess) return e;
     }
     EngineTimer t(ctx, st);
-    return launch_xcorr_mma(B.dd<MmaPair>(o_pairs), B.dd<MmaItem>(o_items), nitems,
-                            B.dw<int>(o_counter), 2 * ctx->sm_count, ctx->d_status, st);
+    return (fp4 ? launch_xcorr_mma4 : launch_xcorr_mma)(B.dd<MmaPair>(o_pairs), B.dd<MmaItem>(o_items), nitems,
+                                                        B.dw<int>(o_counter), 2 * ctx->sm_count, ctx->d_status, st,
+                                                        nullptr);
   }
 };
 
@@ -742,7 +748,7 @@ struct XcorrStage {
     popc_jobs.clear(), mma_jobs.clear(), ntt_jobs.clear();
     for (size_t i = 0; i < jobs.size(); ++i) list(eng[i]).push_back(jobs[i]);
     popc.plan(L, popc_jobs, bits);
-    mma.plan(L, mma_jobs);
+    mma.plan(L, mma_jobs, true, bits <= 2);
     ntt.plan(L, ntt_jobs, bits, ntt_two_primes);
     return ntt.ok;
   }
@@ -1683,7 +1689,7 @@ void learned_plan(LearnedWork* w, int npairs, int64_t n, int bits, float theta) 
   w->o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
   w->o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * kCnnWin);
   std::vector<Job> one{Job{nullptr, nullptr, n, n, -(n - 1), n - 1, nullptr, 0}};
-  w->T.plan(L, one, false);  // replicated per fallback pair: keep the default segments
+  w->T.plan(L, one, false, bits <= 2);  // replicated per fallback pair: keep the default segments
   const int nt = w->T.nitems;
   w->o_fbidx = L.w<int32_t>((size_t)npairs);
   w->o_nfb = L.w<int>(1);
@@ -1772,9 +1778,9 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   }
   if (e == cudaSuccess && w.T.any_zero) e = launch_mma_zero(B.dw<MmaPair>(w.o_fbpairs), P, 2 * n - 1, st, nfb);
   if (e == cudaSuccess)
-    e = launch_xcorr_mma(B.dw<MmaPair>(w.o_fbpairs), B.dw<MmaItem>(w.o_fbitems), P * nt,
-                         B.dw<int>(w.o_counter), 2 * ctx->sm_count, ctx->d_status, st,
-                         B.dw<int>(w.o_nitems));
+    e = (w.T.fp4 ? launch_xcorr_mma4 : launch_xcorr_mma)(B.dw<MmaPair>(w.o_fbpairs), B.dw<MmaItem>(w.o_fbitems),
+                                                          P * nt, B.dw<int>(w.o_counter), 2 * ctx->sm_count,
+                                                          ctx->d_status, st, B.dw<int>(w.o_nitems));
   if (e == cudaSuccess)
     e = launch_argmax(B.dw<ArgPair>(w.o_fbargs), P, 2 * n - 1, 0,
                       B.dw<unsigned long long>(w.o_keys), st, nfb);

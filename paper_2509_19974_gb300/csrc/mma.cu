@@ -1334,6 +1334,323 @@ __global__ void __launch_bounds__(kW4Threads, 2)
 }
 
 // ---------------------------------------------------------------------------
+// The engine on packed E2M1 operands (levels in {-1, 0, 1}, bits 1 and 2):
+// tcgen05 kind::mxf4 with unit UE8M0 block scales, K = 64 samples per MMA, so
+// an MMA does twice the work of the E4M3 form in the same time.  The block
+// scales take 64 columns of tensor memory, so a tile is 128 lags x 128
+// columns (16384 lags; two CTAs per SM still fit), an MMA of N = 128 at the
+// same cost per column as N = 256.  Per K chunk of 128 samples:
+//   B: y staged once per item as 64-byte rows of 128 packed samples,
+//      Y[r] = y[128 r ..], in the 64-byte swizzle; the tile of chunk c is rows
+//      (c + u_s - r_lo) .. + 127 (stride byte offset 512), the second K step
+//      the rows' second 32 bytes.
+//   A: the Hankel slots of the windows kernel (32 samples per slot row,
+//      core matrix (g, h) = slot e0 + g + 4 h, e0 = 16 c + 8 s).
+// Super-chunks of 4 chunks (8 MMAs per wait and commit, so the issuer's
+// per-batch costs stay under the MMAs' time) on a ring of 256 slots (+ 32
+// mirrored): super-chunk j reads [64 j, 64 j + 76) and writes [64 j + 12,
+// 64 j + 76) (from 0 at an item's start); those slots were last read by
+// super-chunk j - 3, which the producers wait for.  Staging flags
+// TDE_ST_INTERNAL for a level outside {-1, 0, 1}.  Column-group skipping,
+// items, the epilogue and the bounded waits are the E4M3 engine's.
+
+constexpr int kN4 = 128;                            // tile columns
+constexpr int kGroups4 = kN4 / kGroupCols;          // column groups of 32
+constexpr int kSC4 = 4;                             // chunks per super-chunk
+constexpr int kStep4 = 16 * kSC4;                   // new slots per super-chunk
+constexpr int kRead4 = kStep4 + 12;                 // slots a super-chunk reads
+constexpr int kRing4 = 256, kMirror4 = 32;
+constexpr int kSlotBytes4 = (kRing4 + kMirror4) * 128;
+constexpr int kRowsMax4 = kMmaKs / 128 + kN4 + 8;   // y rows per item
+constexpr int kYBytes4 = (kRowsMax4 * 64 + 1023) / 1024 * 1024;
+constexpr int kXBytes4 = kMmaKs / 2 + 256;          // packed x bytes a segment's slots read
+constexpr int kCols4 = 256;                         // tensor memory: D 128 + block scales
+constexpr int kScaleCol4 = 128;
+constexpr int kSmemUsed4 = kYBytes4 + kSlotBytes4 + kXBytes4 + (2 * kNB + 1) * 8 + 16;
+constexpr int kSmemBytes4 = kSmemUsed4 + 1024;
+static_assert((32 + 8 * (16 * (kMmaKs / kKc8 - 1) + 28) + 7 + 40) / 2 + 8 <= kXBytes4, "x segment");
+static_assert(kRing4 % kStep4 == 0 && kRing4 - kStep4 + kRead4 <= kRing4 + kMirror4, "ring and mirror");
+static_assert(kYBytes4 % 1024 == 0 && kXBytes4 % 16 == 0 && kSlotBytes4 % 1024 == 0, "fp4 layout");
+static_assert(2 * (kSmemBytes4 + 1024) <= 228 * 1024 && 2 * kCols4 <= 512, "two CTAs per SM");
+static_assert(kMmaKs < (1 << 24), "exact FP32 sums of ternary products");
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_xcorr_mma4(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems_arg,
+                 const int* __restrict__ d_nitems, int* __restrict__ counter,
+                 uint32_t* __restrict__ status) {
+  const int nitems = d_nitems ? *d_nitems : nitems_arg;
+  if (nitems <= 0) return;  // (a device-made item list can be empty)
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t yr = base, slots = base + kYBytes4;
+  const uint32_t xs = slots + kSlotBytes4;  // packed x segment
+  const uint32_t full_bar = xs + kXBytes4;
+  const uint32_t cmt_bar = full_bar + 8 * kNB;
+  const uint32_t done_bar = cmt_bar + 8 * kNB;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
+  volatile int* item_slot = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kCols4)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < kNB; ++i) {
+      mbar_init(full_bar + 8 * i, kProducers);
+      mbar_init(cmt_bar + 8 * i, 1);
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp >= 4) {  // block scales: UE8M0 1.0 in every byte of columns 128 .. 191
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32)
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+          "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+          "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(tmem + lanes +
+                                                                                   kScaleCol4 + c0),
+          "r"(0x7F7F7F7Fu)
+          : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  const uint32_t sfa = tmem + kScaleCol4, sfb = tmem + kScaleCol4 + 32;
+
+  int64_t sc0 = 0;  // super-chunks of earlier items
+  uint32_t iter = 0;
+  bool ok = true;
+  for (;; ++iter) {
+    if (threadIdx.x == 0) *item_slot = atomicAdd(counter, 1);
+    __syncthreads();
+    tc_fence_after();
+    const int w_item = *item_slot;
+    if (w_item >= nitems) break;
+    const MmaItem it = items[w_item];
+    const MmaPair P = pairs[it.pair];
+    const int64_t T0 = it.T0, ks = it.ks, ke = it.ke;
+    const int nchunks = (int)((ke - ks) / kKc8);
+    const int nsc = (nchunks + kSC4 - 1) / kSC4;
+    const int64_t u_s = fdiv(ks + T0, kKc8);                  // exact (host alignment)
+    const int64_t r_lo = fdiv(u_s, 8) * 8;                     // 512-byte (swizzle atom) aligned start row
+    const int64_t nrows = u_s + nchunks - 1 + kN4 - 1 - r_lo + 1;
+    const int64_t x0 = fdiv(ks - 127, 32) * 32;               // first packed x sample
+    const uint32_t bp = (uint32_t)(ks - 127 - x0);             // nibble of sample ks - 127
+    if (nrows > kRowsMax4 || nchunks <= 0 || (ke - ks) > kMmaKs || ((ks + T0) & (kKc8 - 1)) != 0 ||
+        (ks & (kKc8 - 1)) != 0) {
+      if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
+      --iter;
+      __syncthreads();
+      continue;
+    }
+
+    // y rows r_lo .. r_lo + nrows - 1 and the x segment, packed E2M1: one
+    // 32-sample unit (16 bytes) per thread and step
+    {
+      const int8_t* qy = P.qy;
+      const int8_t* qx = P.qx;
+      const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+      const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+      const int nyu = (int)nrows * 4;
+      const int total = nyu + kXBytes4 / 16;
+      bool bad = false;
+      for (int b0 = threadIdx.x; b0 < total; b0 += 2 * kThreads) {
+        uint4 w[2][2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int idx = b0 + k * kThreads;
+          if (idx < nyu) {
+            const int64_t s0 = 128 * (r_lo + (idx >> 2)) + 32 * (idx & 3);
+            w[k][0] = load16(qy, s0, P.ny, aly);
+            w[k][1] = load16(qy, s0 + 16, P.ny, aly);
+          } else if (idx < total) {
+            const int64_t s0 = x0 + 32 * (int64_t)(idx - nyu);
+            w[k][0] = load16(qx, s0, P.nx, alx);
+            w[k][1] = load16(qx, s0 + 16, P.nx, alx);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int idx = b0 + k * kThreads;
+          if (idx >= total) continue;
+          const uint32_t lim = 0x01010101u;
+          bad |= (__vcmpgtu4(__vabs4(w[k][0].x), lim) | __vcmpgtu4(__vabs4(w[k][0].y), lim) |
+                  __vcmpgtu4(__vabs4(w[k][0].z), lim) | __vcmpgtu4(__vabs4(w[k][0].w), lim) |
+                  __vcmpgtu4(__vabs4(w[k][1].x), lim) | __vcmpgtu4(__vabs4(w[k][1].y), lim) |
+                  __vcmpgtu4(__vabs4(w[k][1].z), lim) | __vcmpgtu4(__vabs4(w[k][1].w), lim)) != 0u;
+          const uint2 lo = e2m1x16(w[k][0]), hi = e2m1x16(w[k][1]);
+          uint32_t a;
+          if (idx < nyu) {
+            const uint32_t row_addr = yr + 64u * (uint32_t)(idx >> 2);
+            a = row_addr + 16u * ((uint32_t)(idx & 3) ^ ((row_addr >> 7) & 3u));
+          } else {
+            a = xs + 16u * (uint32_t)(idx - nyu);
+          }
+          st_shared_v4(a, lo.x, lo.y, hi.x, hi.y);
+        }
+      }
+      if (bad) atomicOr(status, TDE_ST_INTERNAL);
+    }
+    if (warp < 4) {
+      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      for (int cb = 0; cb < kN4; cb += 32) tmem_zero32(tmem + lane_base + (uint32_t)cb);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 1 || warp == 2) {
+      // Slot producers: lane (octet o, row r) writes row r of the slots e0,
+      // e0 + 1 from five funnel-shifted words of the packed x segment
+      const int t = threadIdx.x - 32, r = t & 7, o = t >> 3;
+      for (int j = 0; j < nsc; ++j) {
+        const int64_t prev = sc0 + j - 3;
+        if (prev >= 0) {
+          const uint32_t cb = cmt_bar + 8 * (uint32_t)(prev % kNB), ph = (uint32_t)((prev / kNB) & 1);
+          if (!mbar_try(cb, ph) && !mbar_wait(cb, ph)) {
+            ok = false;
+            break;
+          }
+        }
+        const int c_last = kSC4 * j + kSC4 - 1 < nchunks ? kSC4 * j + kSC4 - 1 : nchunks - 1;
+        const int e_lo = j == 0 ? 0 : kStep4 * j + (kRead4 - kStep4), e_hi = 16 * c_last + 28;
+        for (int e0 = e_lo + 2 * o; e0 < e_hi; e0 += 2 * (kProducers / 8)) {
+          const uint32_t pn = bp + 8u * (uint32_t)e0 + (uint32_t)r;
+          const uint32_t a8 = (pn >> 1) & ~7u;
+          const uint32_t sbit = 4u * pn - 8u * a8;
+          uint32_t u[8], w[5];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint64_t v = ld_shared_u64(xs + a8 + 8u * i);
+            u[2 * i] = (uint32_t)v, u[2 * i + 1] = (uint32_t)(v >> 32);
+          }
+          const bool wo = sbit >= 32u;
+          const uint32_t sh = sbit & 31u;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) w[q] = __funnelshift_r(wo ? u[q + 1] : u[q], wo ? u[q + 2] : u[q + 1], sh);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            if (e0 + k >= e_hi) break;
+            const uint32_t ps = (uint32_t)(e0 + k) % (uint32_t)kRing4;
+            const uint32_t ad = slots + 128u * ps + 16u * (uint32_t)r;
+            st_shared_v4(ad, w[k], w[k + 1], w[k + 2], w[k + 3]);
+            if (ps < (uint32_t)kMirror4) st_shared_v4(ad + 128u * kRing4, w[k], w[k + 1], w[k + 2], w[k + 3]);
+          }
+        }
+        fence_proxy_async();
+        mbar_arrive(full_bar + 8 * (uint32_t)((sc0 + j) % kNB));
+      }
+    } else if (warp == 0) {
+      // MMA issuer (whole warp waits, lane 0 issues): per chunk, the live
+      // column groups, two K steps
+      int64_t glo[kGroups4], ghi[kGroups4];
+#pragma unroll
+      for (int g = 0; g < kGroups4; ++g) {
+        const int64_t lo = -T0 - 128 * (int64_t)(kGroupCols * g + kGroupCols - 1);
+        const int64_t hi = P.ny - T0 - 128 * (int64_t)(kGroupCols * g);
+        glo[g] = (lo > 0 ? lo : 0) - ks;
+        ghi[g] = (hi < P.nx + 127 ? hi : P.nx + 127) - ks;
+      }
+      const uint64_t da0 = sdesc(slots, 512, 128, 0, 0);  // + ring slot * 8
+      const uint64_t db0 = sdesc(yr, 16, 512, 4, 0);      // + row * 4
+      for (int j = 0; j < nsc; ++j) {
+        const int64_t S = sc0 + j;
+        {
+          const uint32_t fb = full_bar + 8 * (uint32_t)(S % kNB), ph = (uint32_t)((S / kNB) & 1);
+          ok = __all_sync(0xffffffffu, mbar_try(fb, ph) || mbar_wait(fb, ph));
+        }
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+#pragma unroll
+          for (int cc = 0; cc < kSC4; ++cc) {
+            const int c = kSC4 * j + cc;
+            if (c >= nchunks) break;
+            const int64_t kc = (int64_t)kKc8 * c;
+            int ga = kGroups4, gb = -1;
+#pragma unroll
+            for (int g = 0; g < kGroups4; ++g)
+              if (glo[g] < kc + kKc8 && ghi[g] > kc) {
+                ga = g < ga ? g : ga;
+                gb = g;
+              }
+            if (gb >= ga) {
+              const uint32_t idesc = idesc4_for(kGroupCols * (gb - ga + 1));
+              const int64_t row0 = u_s + c - r_lo + kGroupCols * ga;
+              const uint64_t ad = da0 + 8u * (uint32_t)((16 * c) % kRing4);
+              const uint64_t bd = db0 + 4u * (uint32_t)row0;
+              const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
+              mma_mxf4(d_col, ad, bd, idesc, sfa, sfb, 1u);
+              mma_mxf4(d_col, ad + 64u, bd + 2u, idesc, sfa, sfb, 1u);
+            }
+          }
+          mma_commit(cmt_bar + 8 * (uint32_t)(S % kNB));
+        }
+        __syncwarp();
+      }
+      if (lane == 0) mma_commit(done_bar);
+      __syncwarp();
+    }
+
+    const bool done = mbar_wait(done_bar, iter & 1u);
+    ok = __syncthreads_and(ok && done);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
+      break;
+    }
+    {
+      tc_fence_after();
+      const int q = warp & 3, colh = warp >> 2;
+      const int m = 32 * q + lane;
+      for (int cb = 0; cb < 2; ++cb) {
+        const int col0 = 64 * colh + 32 * cb;
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t tau = T0 + 127 - m + 128 * (int64_t)(col0 + j);
+          if (tau < P.lag_min || tau > P.lag_max) continue;
+          const int val = __float2int_rn(__uint_as_float(v[j]));
+          const int64_t o = tau - P.lag_min;
+          if (P.c64) {
+            if (it.single)
+              static_cast<long long*>(P.c)[o] = val;
+            else
+              atomicAdd(reinterpret_cast<unsigned long long*>(P.c) + o, (unsigned long long)(long long)val);
+          } else {
+            if (it.single)
+              static_cast<int*>(P.c)[o] = val;
+            else
+              atomicAdd(static_cast<int*>(P.c) + o, val);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    sc0 += nsc;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols4)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The learned proposal's 32 -> 32 channel conv layers (inference) on the
 // tensor cores: kind::f16 with BF16 operands and FP32 accumulation in tensor
 // memory.  z[p][co] = sum_k sum_ci X[p + k - 4][ci] W[co][ci][k] (kernel 9,
@@ -1803,6 +2120,22 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
   if (e != cudaSuccess) return e;
   if (grid > nitems) grid = nitems;
   k_xcorr_mma8<<<grid, kThreads, kSmemBytes8, st>>>(d_pairs, d_items, nitems, d_nitems, d_counter,
+                                                     d_status);
+  TDE_COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xcorr_mma4(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
+                              int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
+                              const int* d_nitems) {
+  if (nitems <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemBytes4);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (grid > nitems) grid = nitems;
+  k_xcorr_mma4<<<grid, kThreads, kSmemBytes4, st>>>(d_pairs, d_items, nitems, d_nitems, d_counter,
                                                      d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();

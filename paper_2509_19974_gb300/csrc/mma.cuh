@@ -43,6 +43,14 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
                              int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
                              const int* d_nitems = nullptr);
 
+// The same over items planned for 128-column tiles (16384 lags: tau = T0 +
+// (127 - m) + 128 n, n < 128) on packed E2M1 operands; levels must lie in
+// {-1, 0, 1} (bits 1, 2), one outside flags TDE_ST_INTERNAL.
+constexpr int kMmaTileLags4 = 16384;
+cudaError_t launch_xcorr_mma4(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
+                              int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
+                              const int* d_nitems = nullptr);
+
 // The learned proposal's windows on the tensor cores: the levels as E4M3
 // bytes d_qe, signal stride n_pad (a multiple of 128, zeros in [n, n_pad),
 // 16-byte aligned); pair p is x = signal 2 p, y = signal 2 p + 1 (n levels

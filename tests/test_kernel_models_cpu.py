@@ -103,6 +103,30 @@ def test_windows_fp4_slot_ring_never_overwrites_unread_slots():
             _ring_rule_fp4([rng.randint(1, 24) for _ in range(rng.randint(1, 30))], scc)
 
 
+def test_engine_fp4_slot_ring_waits_cover_every_alias():
+    """k_xcorr_mma4's slot ring per item: super-chunk j (4 chunks) reads
+    [64 j, 64 j + 76) and writes [64 j + 12, 64 j + 76) (from 0 when j = 0)
+    on a ring of 256 slots, after waiting for super-chunk j - 3.  Every
+    earlier super-chunk of the item whose reads alias those writes is j - 3
+    or older, and reads stay inside the ring and its 32-slot mirror."""
+    ring = 256
+    for nchunks in range(1, 193):
+        nsc = -(-nchunks // 4)
+        reads = {}
+        for j in range(nsc):
+            c_last = min(4 * j + 3, nchunks - 1)
+            lo = 0 if j == 0 else 64 * j + 12
+            writes = {e % ring for e in range(lo, 16 * c_last + 28)}
+            for jp, rd in reads.items():
+                if rd & writes:
+                    assert jp <= j - 3, (nchunks, j, jp)
+            rd = set()
+            for c in range(4 * j, c_last + 1):
+                assert (16 * c) % ring + 28 <= ring + 32
+                rd |= {(16 * c + i) % ring for i in range(28)}
+            reads[j] = rd
+
+
 def _funnel_r(lo, hi, sh):
     return (((hi << 32) | lo) >> (sh & 31)) & 0xFFFFFFFF
 
