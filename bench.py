@@ -47,12 +47,21 @@ METRIC = "TDE pairs/s at N=65536, 2-bit: learned-proposal vs full int xcorr (bit
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
-SMS = 152          # GB300 SMs
 # The tensor-core kernels compute in E4M3 (kind::f8f6f4, bits 4) or in packed
 # E2M1 (kind::mxf4, bits 1 and 2): their peak is the measured BF16 peak times
 # the nominal dense FP8 / BF16 (4.5 / 2.25) or FP4 / BF16 (13.5 / 2.25) ratio.
 FP8_OVER_BF16 = 2.0
 FP4_OVER_BF16 = 6.0
+
+
+def probe_peak(probe, key, clk, ops_per_unit=1.0):
+    """Per-second peak from the library's issue-rate probe (tde_measure_peaks):
+    rate per SM per clock x SMs x the SM clock sampled during the timed region
+    (MHz; the maximum clock if none was sampled) x ops per unit."""
+    if not probe:
+        return None
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or peaks()[0].get("sm_max_mhz", 2070.0)
+    return probe[key] * probe["sm_count"] * mhz * 1e6 * ops_per_unit
 
 
 def tensor_peak(pk, bits):
@@ -68,7 +77,6 @@ def tensor_peak(pk, bits):
 # N, bits).  Cleared whenever the kernel changes.
 TRAFFIC = {("k_xcorr_mma8", 256, 65536, 4): None}
 CKPT = os.path.join(ROOT, "paper_2509_19974_gb300", "models", "proposal_n65536_b2.npz")
-POPC_PER_SM_CLK = 16  # POPC issue rate per SM per clock
 
 
 def parse():
@@ -534,6 +542,7 @@ def main():
     if world > 1:
         dist.barrier()
     ctx = tde.Context(local)
+    probe = tde.measure_peaks(local)
     b = workload(args, rank)
     X, Y = b.stacked()
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
@@ -692,6 +701,11 @@ def main():
                            f"operands are {dt}; achieved counts 2 FLOP per overlap MAC of the 257-lag "
                            "windows (algorithmic; the kernel computes 1024 lags per window)",
             "ms_per_launch": wms / wl, "macs_per_launch": win_macs, "launches": wl}
+        if roof_l is not None:
+            pp = probe_peak(probe, "e2m1_mac_per_sm_clk" if args.bits <= 2 else "e4m3_mac_per_sm_clk",
+                            clk_l.summary(), 2.0)
+            roof_l["frac_of_probe"] = ach / pp if pp else None
+            roof_l["probe_peak"] = pp / 1e12 if pp else None
         # end to end: inputs from pinned host memory, lags back, every step
         e2e_l = None
         if not args.no_e2e:
@@ -776,19 +790,24 @@ def main():
         achieved_mac = macs_launch / (per_launch_ms / 1e3)
         if engine == "popc":
             popc_per_mac = (2.0 if args.bits <= 2 else 18.0) / 32.0
-            peak_mac = SMS * POPC_PER_SM_CLK * pk.get("sm_max_mhz", 2070.0) * 1e6 / popc_per_mac
+            peak_mac = probe_peak(probe, "popc_per_sm_clk", clk.summary(), 1.0 / popc_per_mac)
             roof = {"bound": "alu", "kernel": "k_xcorr_popc", "achieved": achieved_mac / 1e12,
                     "peak": peak_mac / 1e12, "unit": "TMAC/s", "frac": achieved_mac / peak_mac,
                     "traffic": None,
-                    "peak_source": f"POPC pipe: {SMS} SMs x {POPC_PER_SM_CLK}/clk x "
-                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)"}
+                    "peak_source": f"POPC pipe: {probe['sm_count']} SMs x "
+                                   f"{probe['popc_per_sm_clk']:.1f} POPC/clk (tde_measure_peaks) x the "
+                                   f"sampled SM clock; {popc_per_mac * 32:.0f} POPC per 32 MACs"}
         elif engine == "mma":
             tflops = 2.0 * achieved_mac / 1e12
             peak, peak_s, dt, suf = tensor_peak(pk, args.bits)
             kname = "k_xcorr_mma" + suf
+            pp = probe_peak(probe, "e2m1_mac_per_sm_clk" if args.bits <= 2 else "e4m3_mac_per_sm_clk",
+                            clk.summary(), 2.0)
             roof = {"bound": "tensor", "kernel": kname, "achieved": tflops, "peak": peak,
                     "unit": "TFLOP/s", "frac": tflops / peak,
                     "frac_of_sustained": tflops / peak_s,
+                    "probe_peak": pp / 1e12 if pp else None,
+                    "frac_of_probe": tflops * 1e12 / pp if pp else None,
                     "traffic": TRAFFIC.get((kname, args.npairs, args.n, args.bits)),
                     "peak_source": f"{pk_kind} dense BF16 burst (bf16_tflops) x {peak / pk['bf16_tflops']:.0f} "
                                    f"(nominal dense {'FP4' if args.bits <= 2 else 'FP8'} / BF16): the "
@@ -807,7 +826,9 @@ def main():
            "no_graph": {"value": args.npairs * world * args.steps / (ms_nograph / 1e3),
                         "ms_per_step": ms_nograph / args.steps},
            "mac_per_s": macs * world * args.steps / (ms_max / 1e3),
-           "clocks": clk.summary(), "fft32_comparator": fft, "learned_proposal": learned}
+           "clocks": clk.summary(), "fft32_comparator": fft, "learned_proposal": learned,
+           "peaks_probe": dict(probe, what="tde_measure_peaks: issue rates per SM per SM clock "
+                                           "(POPC, IMAD, tcgen05 E4M3 and E2M1 MACs, M=128 N=256)")}
     # Headline: the metric compares the learned-proposal form with the full
     # integer correlation; the learned form leads when its lags agree with the
     # full form's on >= 99.9% of this run's pairs, the full form is kept beside.

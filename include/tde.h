@@ -93,6 +93,29 @@ const char* tde_last_error(const tde_ctx* ctx);
  * events are the context's; no caller memory is touched). */
 tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
 
+/* Issue rates the engines' rooflines are measured against, per SM per SM
+ * clock, on `device` (the paper has no counterpart: this is a measurement
+ * utility).  Each is timed with the SM's own cycle counter inside one CTA per
+ * SM, so the rate does not depend on the clock; multiply by sm_count and a
+ * sampled SM clock for a per-second peak.
+ *   popc_per_sm_clk:      32-bit __popc results (the popc engine's operation);
+ *   imad_per_sm_clk:      32-bit integer multiply-adds (the NTT engine's);
+ *   e4m3_mac_per_sm_clk:  MACs of back-to-back tcgen05.mma kind::f8f6f4,
+ *                         M = 128, N = 256, K = 32, issued by one thread;
+ *   e2m1_mac_per_sm_clk:  the same for kind::mxf4 (E2M1, unit block scales),
+ *                         K = 64.
+ * Synchronous; allocates and frees a few bytes of device memory and runs for
+ * tens of milliseconds.  TDE_ERR_CUDA if a CUDA call fails, TDE_ERR_TIMEOUT if
+ * the MMA probe's bounded wait gives up. */
+typedef struct {
+  int sm_count;
+  double popc_per_sm_clk;
+  double imad_per_sm_clk;
+  double e4m3_mac_per_sm_clk;
+  double e2m1_mac_per_sm_clk;
+} tde_peaks;
+tde_status tde_measure_peaks(int device, tde_peaks* out);
+
 /* Failure-detection self-test: launches one CTA whose bounded device waits
  * (the ones every tensor-core kernel uses: a spinning and a suspending
  * mbarrier wait, each limited to 2 s of %globaltimer) run out on a barrier

@@ -470,6 +470,7 @@ struct MmaStage {
     njobs = (int)jobs.size();
     fp4 = use_fp4;
     const int64_t tile = fp4 ? kMmaTileLags4 : kMmaTileLags, cols = tile / 128;
+    const int64_t ks_cap = fp4 ? kMmaKs4 : kMmaKs;
     items.clear();
     zero_first.assign(njobs, 0);
     struct Tile {
@@ -496,10 +497,10 @@ struct MmaStage {
           continue;
         }
         tiles.push_back(Tile{i, T0, klo, khi});
-        n_default += ceil_div64(khi - klo, kMmaKs);
+        n_default += ceil_div64(khi - klo, ks_cap);
       }
     }
-    int64_t seg_cap = kMmaKs;
+    int64_t seg_cap = ks_cap;
     if (split_small && !tiles.empty()) {
       int dev = 0, sms = 0;
       cudaGetDevice(&dev);
@@ -508,7 +509,7 @@ struct MmaStage {
         int64_t total = 0;
         for (const Tile& t : tiles) total += t.khi - t.klo;
         const int64_t want = ceil_div64(ceil_div64(total, sms), kMmaChunk) * kMmaChunk;
-        seg_cap = std::min<int64_t>(kMmaKs, std::max<int64_t>(kMinSeg, want));
+        seg_cap = std::min<int64_t>(ks_cap, std::max<int64_t>(kMinSeg, want));
       }
     }
     for (const Tile& t : tiles) {

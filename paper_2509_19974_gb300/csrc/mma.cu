@@ -1356,23 +1356,32 @@ __global__ void __launch_bounds__(kW4Threads, 2)
 
 constexpr int kN4 = 128;                            // tile columns
 constexpr int kGroups4 = kN4 / kGroupCols;          // column groups of 32
-constexpr int kSC4 = 4;                             // chunks per super-chunk
+#ifndef TDE_M4_SC
+#define TDE_M4_SC 4
+#endif
+#ifndef TDE_M4_RING
+#define TDE_M4_RING 256
+#endif
+constexpr int kSC4 = TDE_M4_SC;                     // chunks per super-chunk
 constexpr int kStep4 = 16 * kSC4;                   // new slots per super-chunk
 constexpr int kRead4 = kStep4 + 12;                 // slots a super-chunk reads
-constexpr int kRing4 = 256, kMirror4 = 32;
+constexpr int kRing4 = TDE_M4_RING, kMirror4 = 32;
 constexpr int kSlotBytes4 = (kRing4 + kMirror4) * 128;
-constexpr int kRowsMax4 = kMmaKs / 128 + kN4 + 8;   // y rows per item
+// the newest earlier super-chunk whose reads a super-chunk's writes may alias
+constexpr int kBack4 = (kRing4 - kRead4) / kStep4 + 1;
+static_assert(kBack4 >= 2 && kBack4 <= kNB, "super-chunks in flight fit the commit barriers");
+constexpr int kRowsMax4 = kMmaKs4 / 128 + kN4 + 8;  // y rows per item
 constexpr int kYBytes4 = (kRowsMax4 * 64 + 1023) / 1024 * 1024;
-constexpr int kXBytes4 = kMmaKs / 2 + 256;          // packed x bytes a segment's slots read
+constexpr int kXBytes4 = kMmaKs4 / 2 + 256;         // packed x bytes a segment's slots read
 constexpr int kCols4 = 256;                         // tensor memory: D 128 + block scales
 constexpr int kScaleCol4 = 128;
 constexpr int kSmemUsed4 = kYBytes4 + kSlotBytes4 + kXBytes4 + (2 * kNB + 1) * 8 + 16;
 constexpr int kSmemBytes4 = kSmemUsed4 + 1024;
-static_assert((32 + 8 * (16 * (kMmaKs / kKc8 - 1) + 28) + 7 + 40) / 2 + 8 <= kXBytes4, "x segment");
+static_assert((32 + 8 * (16 * (kMmaKs4 / kKc8 - 1) + 28) + 7 + 40) / 2 + 8 <= kXBytes4, "x segment");
 static_assert(kRing4 % kStep4 == 0 && kRing4 - kStep4 + kRead4 <= kRing4 + kMirror4, "ring and mirror");
 static_assert(kYBytes4 % 1024 == 0 && kXBytes4 % 16 == 0 && kSlotBytes4 % 1024 == 0, "fp4 layout");
 static_assert(2 * (kSmemBytes4 + 1024) <= 228 * 1024 && 2 * kCols4 <= 512, "two CTAs per SM");
-static_assert(kMmaKs < (1 << 24), "exact FP32 sums of ternary products");
+static_assert(kMmaKs4 < (1 << 24) && kMmaKs4 % kKc8 == 0, "exact FP32 sums of ternary products");
 
 __global__ void __launch_bounds__(kThreads, 2)
     k_xcorr_mma4(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems_arg,
@@ -1445,7 +1454,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t nrows = u_s + nchunks - 1 + kN4 - 1 - r_lo + 1;
     const int64_t x0 = fdiv(ks - 127, 32) * 32;               // first packed x sample
     const uint32_t bp = (uint32_t)(ks - 127 - x0);             // nibble of sample ks - 127
-    if (nrows > kRowsMax4 || nchunks <= 0 || (ke - ks) > kMmaKs || ((ks + T0) & (kKc8 - 1)) != 0 ||
+    if (nrows > kRowsMax4 || nchunks <= 0 || (ke - ks) > kMmaKs4 || ((ks + T0) & (kKc8 - 1)) != 0 ||
         (ks & (kKc8 - 1)) != 0) {
       if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
       --iter;
@@ -1515,7 +1524,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // e0 + 1 from five funnel-shifted words of the packed x segment
       const int t = threadIdx.x - 32, r = t & 7, o = t >> 3;
       for (int j = 0; j < nsc; ++j) {
-        const int64_t prev = sc0 + j - 3;
+        const int64_t prev = sc0 + j - kBack4;
         if (prev >= 0) {
           const uint32_t cb = cmt_bar + 8 * (uint32_t)(prev % kNB), ph = (uint32_t)((prev / kNB) & 1);
           if (!mbar_try(cb, ph) && !mbar_wait(cb, ph)) {

@@ -47,6 +47,12 @@ cudaError_t launch_xcorr_mma(const MmaPair* d_pairs, const MmaItem* d_items, int
 // (127 - m) + 128 n, n < 128) on packed E2M1 operands; levels must lie in
 // {-1, 0, 1} (bits 1, 2), one outside flags TDE_ST_INTERNAL.
 constexpr int kMmaTileLags4 = 16384;
+// Samples of the sum per CTA on E2M1 operands: exact for any K < 2^24 (|level|
+// <= 1); bounded by the shared memory that stages a segment.
+#ifndef TDE_M4_KS
+#define TDE_M4_KS 24576
+#endif
+constexpr int kMmaKs4 = TDE_M4_KS;
 cudaError_t launch_xcorr_mma4(const MmaPair* d_pairs, const MmaItem* d_items, int nitems,
                               int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
                               const int* d_nitems = nullptr);

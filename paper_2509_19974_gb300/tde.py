@@ -27,7 +27,7 @@ TDE_I32, TDE_I64, TDE_F32, TDE_I8 = 0, 1, 2, 3
 
 # Every symbol include/tde.h declares.
 EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error",
-           "tde_ctx_set_profiling", "tde_ctx_set_ntt_primes", "tde_selftest_wait_timeout", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
+           "tde_ctx_set_profiling", "tde_ctx_set_ntt_primes", "tde_selftest_wait_timeout", "tde_measure_peaks", "tde_ctx_read_profile", "tde_pick_engine", "tde_quantize",
            "tde_quantize_noalloc", "tde_quantize_batch", "tde_xcorr_int", "tde_argmax", "tde_xcorr_fft32",
            "tde_estimate", "tde_estimate_batch", "tde_batch_create", "tde_batch_run",
            "tde_batch_destroy", "tde_model_param_count", "tde_model_create", "tde_model_destroy",
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_ctx_set_profiling": ([p, i32], st),
         "tde_ctx_set_ntt_primes": ([p, i32], st),
         "tde_selftest_wait_timeout": ([p, p], st),
+        "tde_measure_peaks": ([i32, p], st),
         "tde_ctx_read_profile": ([p, p, p, p], st),
         "tde_pick_engine": ([i32, i64, i64, i64], i32),
         "tde_quantize": ([p, p, i64, i32, p, p], st),
@@ -132,6 +133,23 @@ def _need(t: torch.Tensor, dtype, name: str):
 
 def _engine(e) -> int:
     return ENGINES[e] if isinstance(e, str) else int(e)
+
+
+class Peaks(ctypes.Structure):
+    """tde_peaks: issue rates per SM per SM clock (see tde_measure_peaks)."""
+    _fields_ = [("sm_count", ctypes.c_int), ("popc_per_sm_clk", ctypes.c_double),
+                ("imad_per_sm_clk", ctypes.c_double), ("e4m3_mac_per_sm_clk", ctypes.c_double),
+                ("e2m1_mac_per_sm_clk", ctypes.c_double)]
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """tde_measure_peaks on `device`: POPC, IMAD, E4M3 and E2M1 tensor-core MAC
+    rates per SM per clock, and the SM count."""
+    pk = Peaks()
+    s = load().tde_measure_peaks(int(device), ctypes.addressof(pk))
+    if s != TDE_OK:
+        raise TdeError(s, "tde_measure_peaks failed")
+    return {f: getattr(pk, f) for f, _ in Peaks._fields_}
 
 
 class Context:
