@@ -26,6 +26,9 @@
 //             (for signals up to 2^18 samples k_qsel2 does this itself);
 //   k_qapply  (only when the popc kernels' bit planes are wanted)
 //             q = sign(x) * #{m : |x| >= t_m} and the planes (a third read).
+//   k_qone    signals up to 2^18 samples, no planes: all of the above in one
+//             launch, one CTA per signal, x read from HBM once (its second
+//             read comes from L2).
 // The candidate list has room for the whole signal (keys, then index and
 // sign), so no input (ties, constant signals) needs another path.
 #include "common.cuh"
@@ -559,6 +562,208 @@ __global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QW
   }
 }
 
+// One CTA per signal (persistent over the signals), for signals up to
+// kQOneMax samples when no bit planes are wanted: the streaming form's steps
+// in one launch, with x read from HBM once --
+//   1. the first-digit histogram in shared memory (x from HBM);
+//   2. each threshold's bin and rank within it (one warp per threshold);
+//   3. x again (still in L2: the CTA read it just before): every level its
+//      first digit decides is written, the rest go to the signal's candidate
+//      list (key, index | sign);
+//   4. two radix passes over the candidates (digits 18..9, 8..0, one
+//      histogram per distinct prefix) give the exact thresholds;
+//   5. the candidates' levels.
+// No grid-wide step: a signal's chain is the CTA's own.
+constexpr int kQOneMax = 1 << 18;
+constexpr int kQOT = 512;  // threads per CTA of k_qone
+
+template <int M>
+__global__ void __launch_bounds__(kQOT, 2) k_qone(const QSig* __restrict__ sigs, int nsig, QWork w, int L,
+                                              uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) uint32_t qs[];  // max(kQB, M * 1024) words
+  __shared__ uint32_t pre_s[7], rank_s[7], ncand_s;
+  __shared__ int owner_s[7];
+  const int warp = threadIdx.x >> 5;
+  for (int sig = blockIdx.x; sig < nsig; sig += gridDim.x) {
+    const QSig s = sigs[sig];
+    uint32_t* cand = w.cand[sig];
+    uint32_t* cidx = cand + s.n;
+    // ---- 1. first-digit histogram
+    for (int i = threadIdx.x; i < kQB; i += kQOT) qs[i] = 0;
+    __syncthreads();
+    int bad = 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(s.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(s.q) & 3) == 0;
+    const int64_t n4 = vec ? s.n >> 2 : 0;
+    const float4* x4 = reinterpret_cast<const float4*>(s.x);
+    for (int64_t c0 = 0; c0 < n4; c0 += 8 * kQOT) {
+      float4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t i = c0 + k * kQOT + threadIdx.x;
+        if (i < n4) v[k] = x4[i];
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (c0 + k * kQOT + threadIdx.x >= n4) continue;
+        const uint32_t u0 = __float_as_uint(v[k].x) & 0x7FFFFFFFu, u1 = __float_as_uint(v[k].y) & 0x7FFFFFFFu;
+        const uint32_t u2 = __float_as_uint(v[k].z) & 0x7FFFFFFFu, u3 = __float_as_uint(v[k].w) & 0x7FFFFFFFu;
+        q_bad(u0, bad), q_bad(u1, bad), q_bad(u2, bad), q_bad(u3, bad);
+        atomicAdd(&qs[u0 >> 19], 1u);
+        atomicAdd(&qs[u1 >> 19], 1u);
+        atomicAdd(&qs[u2 >> 19], 1u);
+        atomicAdd(&qs[u3 >> 19], 1u);
+      }
+    }
+    for (int64_t j = (n4 << 2) + threadIdx.x; j < s.n; j += kQOT) {
+      const uint32_t u = __float_as_uint(s.x[j]) & 0x7FFFFFFFu;
+      q_bad(u, bad);
+      atomicAdd(&qs[u >> 19], 1u);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, TDE_ST_NONFINITE);
+    // ---- 2. the bin of each threshold's rank
+    if (warp < M) {
+      const int64_t idx = ((2 * (int64_t)warp + 1) * s.n) / L;
+      const uint32_t r = (uint32_t)(idx > s.n - 1 ? s.n - 1 : idx);
+      uint32_t bin, rest;
+      warp_find(qs, kQB, r, bin, rest);
+      if ((threadIdx.x & 31) == 0) pre_s[warp] = bin, rank_s[warp] = rest;
+    }
+    if (threadIdx.x == 0) ncand_s = 0;
+    __syncthreads();
+    // ---- 3. decided levels; candidates to the list
+    {
+      uint32_t pre[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) pre[m] = pre_s[m];
+      for (int64_t c0 = 0; c0 < n4; c0 += 8 * kQOT) {
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int64_t i = c0 + k * kQOT + threadIdx.x;
+          v[k] = i < n4 ? x4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        uint32_t hits = 0;  // bit 4k + e: element e of load k
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int64_t i = c0 + k * kQOT + threadIdx.x;
+          if (i >= n4) continue;
+          const uint32_t b[4] = {__float_as_uint(v[k].x), __float_as_uint(v[k].y), __float_as_uint(v[k].z),
+                                 __float_as_uint(v[k].w)};
+          uint32_t packed = 0;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const uint32_t hi = (b[e] & 0x7FFFFFFFu) >> 19;
+            bool c = false;
+            int lv = 0;
+#pragma unroll
+            for (int m = 0; m < M; ++m) c |= hi == pre[m], lv += hi > pre[m];
+            hits |= (uint32_t)c << (4 * k + e);
+            packed |= ((uint32_t)((b[e] >> 31) ? -lv : lv) & 0xFFu) << (8 * e);
+          }
+          reinterpret_cast<uint32_t*>(s.q)[i] = packed;  // a candidate's byte is rewritten in step 5
+        }
+        if (hits) {
+          uint32_t slot = atomicAdd(&ncand_s, (uint32_t)__popc(hits));
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+            const uint32_t i4 = (uint32_t)(4 * (c0 + k * kQOT + threadIdx.x));
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (hits >> (4 * k + e) & 1u) {
+                cand[slot] = __float_as_uint(f[e]) & 0x7FFFFFFFu;
+                cidx[slot] = (i4 + e) | (f[e] < 0.f ? 0x80000000u : 0u);
+                ++slot;
+              }
+          }
+        }
+      }
+      for (int64_t j = (n4 << 2) + threadIdx.x; j < s.n; j += kQOT) {
+        const float f = s.x[j];
+        const uint32_t u = __float_as_uint(f) & 0x7FFFFFFFu, hi = u >> 19;
+        bool c = false;
+        int lv = 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) c |= hi == pre[m], lv += hi > pre[m];
+        if (c) {
+          const uint32_t slot = atomicAdd(&ncand_s, 1u);
+          cand[slot] = u;
+          cidx[slot] = (uint32_t)j | (f < 0.f ? 0x80000000u : 0u);
+        } else {
+          s.q[j] = (int8_t)(sign_of(f) * lv);
+        }
+      }
+    }
+    __syncthreads();  // the candidate list (global, this CTA's writes) and its count
+    const uint32_t nc = ncand_s;
+    // ---- 4. exact thresholds from the candidates
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int nbins = pass == 0 ? 1024 : 512, shift = pass == 0 ? 9 : 0, hs = pass == 0 ? 19 : 9;
+      const uint32_t mask = pass == 0 ? 1023u : 511u;
+      if (threadIdx.x < 7) {  // thresholds with equal prefixes share the first one's histogram
+        const int m = threadIdx.x;
+        int o = m;
+        if (m < M)
+          for (int k = m - 1; k >= 0; --k)
+            if (pre_s[k] == pre_s[m]) o = k;
+        owner_s[m] = o;
+      }
+      for (int i = threadIdx.x; i < M * 1024; i += kQOT) qs[i] = 0;
+      __syncthreads();
+      uint32_t pre[M];
+      int own[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) pre[m] = pre_s[m], own[m] = owner_s[m];
+      for (uint32_t i = threadIdx.x; i < nc; i += kQOT) {
+        const uint32_t u = cand[i];
+        const uint32_t hi = u >> hs;
+        int mm = -1;
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m)
+          if (hi == pre[m]) mm = own[m];
+        if (mm >= 0) atomicAdd(&qs[mm * 1024 + ((u >> shift) & mask)], 1u);
+      }
+      __syncthreads();
+      if (warp < M) {
+        uint32_t bin, rest;
+        warp_find(qs + owner_s[warp] * 1024, nbins, rank_s[warp], bin, rest);
+        if ((threadIdx.x & 31) == 0) {
+          pre_s[warp] = (pre_s[warp] << (pass == 0 ? 10 : 9)) | bin;
+          rank_s[warp] = rest;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 5. the candidates' levels (loads batched ahead of the byte stores,
+    // which could alias the list)
+    {
+      uint32_t t[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) t[m] = pre_s[m];
+      constexpr int kFixB = 16;
+      for (uint32_t i0 = threadIdx.x; i0 < nc; i0 += kFixB * kQOT) {
+        uint32_t u[kFixB], c[kFixB];
+#pragma unroll
+        for (int k = 0; k < kFixB; ++k) {
+          const uint32_t i = i0 + k * kQOT;
+          u[k] = i < nc ? cand[i] : 0u;
+          c[k] = i < nc ? cidx[i] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kFixB; ++k) {
+          if (i0 + k * kQOT >= nc) break;
+          int lv = 0;
+#pragma unroll
+          for (int m = 0; m < M; ++m) lv += u[k] >= t[m];
+          s.q[c[k] & 0x7FFFFFFFu] = (int8_t)(u[k] == 0 ? 0 : ((c[k] >> 31) ? -lv : lv));
+        }
+      }
+    }
+    __syncthreads();  // shared state is reused by the next signal
+  }
+}
+
 // The exact thresholds from the candidates: digits 18..9 then 8..0.  Each
 // pass is a grid of CTAs per signal that histograms a share of the candidates
 // (one histogram per distinct prefix, in shared memory, non-zero bins added to
@@ -767,6 +972,22 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
                                    cudaStream_t st) {
   if (bits != 2 && bits != 4) return cudaErrorInvalidValue;
   const int M = (1 << (bits - 1)) - 1, L = (1 << bits) - 1;
+  if (d_planes == nullptr && max_n <= kQOneMax) {
+    // one CTA per signal, x read from HBM once: two CTAs per SM, the signals
+    // dealt in equal rounds, so that the signals in flight (one per CTA)
+    // stay within L2 until their second read
+    const size_t smem = sizeof(uint32_t) * (M == 1 ? kQB : 7 * 1024);
+    auto kern = M == 1 ? k_qone<1> : k_qone<7>;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t cap = 2 * (int64_t)sms;
+    const int64_t rounds = ceil_div64(nsig, cap);
+    const int grid = (int)ceil_div64(nsig, rounds);
+    kern<<<grid, kQOT, smem, st>>>(d_sigs, nsig, w, L, d_status);
+    TDE_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+  }
   int64_t gx = ceil_div64(max_n, kQPer);
   if (gx < 1) gx = 1;
   if (gx > 65535) gx = 65535;
