@@ -1350,7 +1350,9 @@ __global__ void __launch_bounds__(kW4Threads, 2)
 // per-batch costs stay under the MMAs' time) on a ring of 256 slots (+ 32
 // mirrored): super-chunk j reads [64 j, 64 j + 76) and writes [64 j + 12,
 // 64 j + 76) (from 0 at an item's start); those slots were last read by
-// super-chunk j - 3, which the producers wait for.  Staging flags
+// super-chunk j - 3, which the producers wait for.  Items are staged into two
+// buffers: while warp 0 issues and warps 1-2 write slots, warps 3-7 stage the
+// next item's y and x, so staging leaves the MMAs' path.  Staging flags
 // TDE_ST_INTERNAL for a level outside {-1, 0, 1}.  Column-group skipping,
 // items, the epilogue and the bounded waits are the E4M3 engine's.
 
@@ -1372,16 +1374,89 @@ constexpr int kBack4 = (kRing4 - kRead4) / kStep4 + 1;
 static_assert(kBack4 >= 2 && kBack4 <= kNB, "super-chunks in flight fit the commit barriers");
 constexpr int kRowsMax4 = kMmaKs4 / 128 + kN4 + 8;  // y rows per item
 constexpr int kYBytes4 = (kRowsMax4 * 64 + 1023) / 1024 * 1024;
-constexpr int kXBytes4 = kMmaKs4 / 2 + 256;         // packed x bytes a segment's slots read
+constexpr int kXBytes4 = (kMmaKs4 / 2 + 256 + 1023) / 1024 * 1024;  // packed x bytes a segment's slots read
 constexpr int kCols4 = 256;                         // tensor memory: D 128 + block scales
 constexpr int kScaleCol4 = 128;
-constexpr int kSmemUsed4 = kYBytes4 + kSlotBytes4 + kXBytes4 + (2 * kNB + 1) * 8 + 16;
+constexpr int kStage4 = kYBytes4 + kXBytes4;        // one item's staged y and x
+constexpr int kSmemUsed4 = 2 * kStage4 + kSlotBytes4 + (2 * kNB + 1) * 8 + 16;
 constexpr int kSmemBytes4 = kSmemUsed4 + 1024;
+static_assert(kStage4 % 1024 == 0, "staging buffers keep the 1024-byte alignment");
 static_assert((32 + 8 * (16 * (kMmaKs4 / kKc8 - 1) + 28) + 7 + 40) / 2 + 8 <= kXBytes4, "x segment");
 static_assert(kRing4 % kStep4 == 0 && kRing4 - kStep4 + kRead4 <= kRing4 + kMirror4, "ring and mirror");
-static_assert(kYBytes4 % 1024 == 0 && kXBytes4 % 16 == 0 && kSlotBytes4 % 1024 == 0, "fp4 layout");
 static_assert(2 * (kSmemBytes4 + 1024) <= 228 * 1024 && 2 * kCols4 <= 512, "two CTAs per SM");
 static_assert(kMmaKs4 < (1 << 24) && kMmaKs4 % kKc8 == 0, "exact FP32 sums of ternary products");
+
+// One item's staging geometry.
+struct Item4 {
+  int64_t T0, ks, ke, u_s, r_lo, nrows, x0;
+  int nchunks, nsc;
+  uint32_t bp;
+  bool valid;
+};
+__device__ __forceinline__ Item4 item4_of(const MmaItem& it) {
+  Item4 g;
+  g.T0 = it.T0, g.ks = it.ks, g.ke = it.ke;
+  g.nchunks = (int)((g.ke - g.ks) / kKc8);
+  g.nsc = (g.nchunks + kSC4 - 1) / kSC4;
+  g.u_s = fdiv(g.ks + g.T0, kKc8);                  // exact (host alignment)
+  g.r_lo = fdiv(g.u_s, 8) * 8;                       // 512-byte (swizzle atom) aligned start row
+  g.nrows = g.u_s + g.nchunks - 1 + kN4 - 1 - g.r_lo + 1;
+  g.x0 = fdiv(g.ks - 127, 32) * 32;                  // first packed x sample
+  g.bp = (uint32_t)(g.ks - 127 - g.x0);              // nibble of sample ks - 127
+  g.valid = g.nrows <= kRowsMax4 && g.nchunks > 0 && (g.ke - g.ks) <= kMmaKs4 &&
+            ((g.ks + g.T0) & (kKc8 - 1)) == 0 && (g.ks & (kKc8 - 1)) == 0;
+  return g;
+}
+
+// y rows r_lo .. r_lo + nrows - 1 and the x segment of an item, packed E2M1,
+// by threads t0 .. t0 + nthr - 1: one 32-sample unit (16 bytes) per thread
+// and step.  Returns whether a level outside {-1, 0, 1} was seen.
+__device__ __forceinline__ bool stage4(const MmaPair& P, const Item4& g, uint32_t yr, uint32_t xs, int t,
+                                       int nthr) {
+  const int8_t* qy = P.qy;
+  const int8_t* qx = P.qx;
+  const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
+  const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
+  const int nyu = (int)g.nrows * 4;
+  const int total = nyu + kXBytes4 / 16;
+  bool bad = false;
+  for (int b0 = t; b0 < total; b0 += 2 * nthr) {
+    uint4 w[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int idx = b0 + k * nthr;
+      if (idx < nyu) {
+        const int64_t s0 = 128 * (g.r_lo + (idx >> 2)) + 32 * (idx & 3);
+        w[k][0] = load16(qy, s0, P.ny, aly);
+        w[k][1] = load16(qy, s0 + 16, P.ny, aly);
+      } else if (idx < total) {
+        const int64_t s0 = g.x0 + 32 * (int64_t)(idx - nyu);
+        w[k][0] = load16(qx, s0, P.nx, alx);
+        w[k][1] = load16(qx, s0 + 16, P.nx, alx);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int idx = b0 + k * nthr;
+      if (idx >= total) continue;
+      const uint32_t lim = 0x01010101u;
+      bad |= (__vcmpgtu4(__vabs4(w[k][0].x), lim) | __vcmpgtu4(__vabs4(w[k][0].y), lim) |
+              __vcmpgtu4(__vabs4(w[k][0].z), lim) | __vcmpgtu4(__vabs4(w[k][0].w), lim) |
+              __vcmpgtu4(__vabs4(w[k][1].x), lim) | __vcmpgtu4(__vabs4(w[k][1].y), lim) |
+              __vcmpgtu4(__vabs4(w[k][1].z), lim) | __vcmpgtu4(__vabs4(w[k][1].w), lim)) != 0u;
+      const uint2 lo = e2m1x16(w[k][0]), hi = e2m1x16(w[k][1]);
+      uint32_t a;
+      if (idx < nyu) {
+        const uint32_t row_addr = yr + 64u * (uint32_t)(idx >> 2);
+        a = row_addr + 16u * ((uint32_t)(idx & 3) ^ ((row_addr >> 7) & 3u));
+      } else {
+        a = xs + 16u * (uint32_t)(idx - nyu);
+      }
+      st_shared_v4(a, lo.x, lo.y, hi.x, hi.y);
+    }
+  }
+  return bad;
+}
 
 __global__ void __launch_bounds__(kThreads, 2)
     k_xcorr_mma4(const MmaPair* __restrict__ pairs, const MmaItem* __restrict__ items, int nitems_arg,
@@ -1392,13 +1467,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t yr = base, slots = base + kYBytes4;
-  const uint32_t xs = slots + kSlotBytes4;  // packed x segment
-  const uint32_t full_bar = xs + kXBytes4;
+  const uint32_t stage0 = base;                 // staging buffer b at stage0 + b * kStage4: y, then x
+  const uint32_t slots = base + 2 * kStage4;
+  const uint32_t full_bar = slots + kSlotBytes4;
   const uint32_t cmt_bar = full_bar + 8 * kNB;
   const uint32_t done_bar = cmt_bar + 8 * kNB;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (done_bar + 8 - raw));
-  volatile int* item_slot = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* item_slot = reinterpret_cast<volatile int*>(tmem_slot + 1);  // [0]: this item, [1]: next
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) {
@@ -1416,6 +1491,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     mbar_init(done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (threadIdx.x == 0) item_slot[1] = atomicAdd(counter, 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1434,80 +1510,47 @@ __global__ void __launch_bounds__(kThreads, 2)
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   const uint32_t sfa = tmem + kScaleCol4, sfb = tmem + kScaleCol4 + 32;
+  // the first item, staged by every thread
+  {
+    const int w0 = item_slot[1];
+    if (w0 < nitems) {
+      const MmaItem it = items[w0];
+      const Item4 g = item4_of(it);
+      if (g.valid && stage4(pairs[it.pair], g, stage0, stage0 + kYBytes4, threadIdx.x, kThreads))
+        atomicOr(status, TDE_ST_INTERNAL);
+    }
+  }
 
-  int64_t sc0 = 0;  // super-chunks of earlier items
-  uint32_t iter = 0;
+  int64_t sc0 = 0;      // super-chunks of earlier items
+  uint32_t ndone = 0;   // items whose MMAs were committed to done_bar
+  uint32_t iter = 0;    // items taken (the staging buffer alternates with it)
   bool ok = true;
   for (;; ++iter) {
-    if (threadIdx.x == 0) *item_slot = atomicAdd(counter, 1);
+    __syncthreads();  // the previous item's epilogue and this item's staging are done
+    if (threadIdx.x == 0) {
+      item_slot[0] = item_slot[1];
+      if (item_slot[0] < nitems) item_slot[1] = atomicAdd(counter, 1);
+    }
     __syncthreads();
     tc_fence_after();
-    const int w_item = *item_slot;
+    const int w_item = item_slot[0];
     if (w_item >= nitems) break;
+    const int w_next = item_slot[1];
     const MmaItem it = items[w_item];
     const MmaPair P = pairs[it.pair];
-    const int64_t T0 = it.T0, ks = it.ks, ke = it.ke;
-    const int nchunks = (int)((ke - ks) / kKc8);
-    const int nsc = (nchunks + kSC4 - 1) / kSC4;
-    const int64_t u_s = fdiv(ks + T0, kKc8);                  // exact (host alignment)
-    const int64_t r_lo = fdiv(u_s, 8) * 8;                     // 512-byte (swizzle atom) aligned start row
-    const int64_t nrows = u_s + nchunks - 1 + kN4 - 1 - r_lo + 1;
-    const int64_t x0 = fdiv(ks - 127, 32) * 32;               // first packed x sample
-    const uint32_t bp = (uint32_t)(ks - 127 - x0);             // nibble of sample ks - 127
-    if (nrows > kRowsMax4 || nchunks <= 0 || (ke - ks) > kMmaKs4 || ((ks + T0) & (kKc8 - 1)) != 0 ||
-        (ks & (kKc8 - 1)) != 0) {
+    const Item4 g = item4_of(it);
+    const uint32_t yr = stage0 + (iter & 1u) * kStage4, xs = yr + kYBytes4;
+    if (!g.valid) {
       if (threadIdx.x == 0) atomicOr(status, TDE_ST_INTERNAL);
-      --iter;
-      __syncthreads();
-      continue;
-    }
-
-    // y rows r_lo .. r_lo + nrows - 1 and the x segment, packed E2M1: one
-    // 32-sample unit (16 bytes) per thread and step
-    {
-      const int8_t* qy = P.qy;
-      const int8_t* qx = P.qx;
-      const bool aly = (reinterpret_cast<uintptr_t>(qy) & 15) == 0;
-      const bool alx = (reinterpret_cast<uintptr_t>(qx) & 15) == 0;
-      const int nyu = (int)nrows * 4;
-      const int total = nyu + kXBytes4 / 16;
-      bool bad = false;
-      for (int b0 = threadIdx.x; b0 < total; b0 += 2 * kThreads) {
-        uint4 w[2][2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int idx = b0 + k * kThreads;
-          if (idx < nyu) {
-            const int64_t s0 = 128 * (r_lo + (idx >> 2)) + 32 * (idx & 3);
-            w[k][0] = load16(qy, s0, P.ny, aly);
-            w[k][1] = load16(qy, s0 + 16, P.ny, aly);
-          } else if (idx < total) {
-            const int64_t s0 = x0 + 32 * (int64_t)(idx - nyu);
-            w[k][0] = load16(qx, s0, P.nx, alx);
-            w[k][1] = load16(qx, s0 + 16, P.nx, alx);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int idx = b0 + k * kThreads;
-          if (idx >= total) continue;
-          const uint32_t lim = 0x01010101u;
-          bad |= (__vcmpgtu4(__vabs4(w[k][0].x), lim) | __vcmpgtu4(__vabs4(w[k][0].y), lim) |
-                  __vcmpgtu4(__vabs4(w[k][0].z), lim) | __vcmpgtu4(__vabs4(w[k][0].w), lim) |
-                  __vcmpgtu4(__vabs4(w[k][1].x), lim) | __vcmpgtu4(__vabs4(w[k][1].y), lim) |
-                  __vcmpgtu4(__vabs4(w[k][1].z), lim) | __vcmpgtu4(__vabs4(w[k][1].w), lim)) != 0u;
-          const uint2 lo = e2m1x16(w[k][0]), hi = e2m1x16(w[k][1]);
-          uint32_t a;
-          if (idx < nyu) {
-            const uint32_t row_addr = yr + 64u * (uint32_t)(idx >> 2);
-            a = row_addr + 16u * ((uint32_t)(idx & 3) ^ ((row_addr >> 7) & 3u));
-          } else {
-            a = xs + 16u * (uint32_t)(idx - nyu);
-          }
-          st_shared_v4(a, lo.x, lo.y, hi.x, hi.y);
-        }
+      // (nothing was staged for it; the next item is staged below by everyone)
+      if (w_next < nitems) {
+        const MmaItem itn = items[w_next];
+        const Item4 gn = item4_of(itn);
+        const uint32_t yn = stage0 + ((iter + 1) & 1u) * kStage4;
+        if (gn.valid && stage4(pairs[itn.pair], gn, yn, yn + kYBytes4, threadIdx.x, kThreads))
+          atomicOr(status, TDE_ST_INTERNAL);
       }
-      if (bad) atomicOr(status, TDE_ST_INTERNAL);
+      continue;
     }
     if (warp < 4) {
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
@@ -1523,7 +1566,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // Slot producers: lane (octet o, row r) writes row r of the slots e0,
       // e0 + 1 from five funnel-shifted words of the packed x segment
       const int t = threadIdx.x - 32, r = t & 7, o = t >> 3;
-      for (int j = 0; j < nsc; ++j) {
+      for (int j = 0; j < g.nsc; ++j) {
         const int64_t prev = sc0 + j - kBack4;
         if (prev >= 0) {
           const uint32_t cb = cmt_bar + 8 * (uint32_t)(prev % kNB), ph = (uint32_t)((prev / kNB) & 1);
@@ -1532,10 +1575,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             break;
           }
         }
-        const int c_last = kSC4 * j + kSC4 - 1 < nchunks ? kSC4 * j + kSC4 - 1 : nchunks - 1;
+        const int c_last = kSC4 * j + kSC4 - 1 < g.nchunks ? kSC4 * j + kSC4 - 1 : g.nchunks - 1;
         const int e_lo = j == 0 ? 0 : kStep4 * j + (kRead4 - kStep4), e_hi = 16 * c_last + 28;
         for (int e0 = e_lo + 2 * o; e0 < e_hi; e0 += 2 * (kProducers / 8)) {
-          const uint32_t pn = bp + 8u * (uint32_t)e0 + (uint32_t)r;
+          const uint32_t pn = g.bp + 8u * (uint32_t)e0 + (uint32_t)r;
           const uint32_t a8 = (pn >> 1) & ~7u;
           const uint32_t sbit = 4u * pn - 8u * a8;
           uint32_t u[8], w[5];
@@ -1565,15 +1608,15 @@ __global__ void __launch_bounds__(kThreads, 2)
       // column groups, two K steps
       int64_t glo[kGroups4], ghi[kGroups4];
 #pragma unroll
-      for (int g = 0; g < kGroups4; ++g) {
-        const int64_t lo = -T0 - 128 * (int64_t)(kGroupCols * g + kGroupCols - 1);
-        const int64_t hi = P.ny - T0 - 128 * (int64_t)(kGroupCols * g);
-        glo[g] = (lo > 0 ? lo : 0) - ks;
-        ghi[g] = (hi < P.nx + 127 ? hi : P.nx + 127) - ks;
+      for (int gg = 0; gg < kGroups4; ++gg) {
+        const int64_t lo = -g.T0 - 128 * (int64_t)(kGroupCols * gg + kGroupCols - 1);
+        const int64_t hi = P.ny - g.T0 - 128 * (int64_t)(kGroupCols * gg);
+        glo[gg] = (lo > 0 ? lo : 0) - g.ks;
+        ghi[gg] = (hi < P.nx + 127 ? hi : P.nx + 127) - g.ks;
       }
       const uint64_t da0 = sdesc(slots, 512, 128, 0, 0);  // + ring slot * 8
       const uint64_t db0 = sdesc(yr, 16, 512, 4, 0);      // + row * 4
-      for (int j = 0; j < nsc; ++j) {
+      for (int j = 0; j < g.nsc; ++j) {
         const int64_t S = sc0 + j;
         {
           const uint32_t fb = full_bar + 8 * (uint32_t)(S % kNB), ph = (uint32_t)((S / kNB) & 1);
@@ -1585,18 +1628,18 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
           for (int cc = 0; cc < kSC4; ++cc) {
             const int c = kSC4 * j + cc;
-            if (c >= nchunks) break;
+            if (c >= g.nchunks) break;
             const int64_t kc = (int64_t)kKc8 * c;
             int ga = kGroups4, gb = -1;
 #pragma unroll
-            for (int g = 0; g < kGroups4; ++g)
-              if (glo[g] < kc + kKc8 && ghi[g] > kc) {
-                ga = g < ga ? g : ga;
-                gb = g;
+            for (int gg = 0; gg < kGroups4; ++gg)
+              if (glo[gg] < kc + kKc8 && ghi[gg] > kc) {
+                ga = gg < ga ? gg : ga;
+                gb = gg;
               }
             if (gb >= ga) {
               const uint32_t idesc = idesc4_for(kGroupCols * (gb - ga + 1));
-              const int64_t row0 = u_s + c - r_lo + kGroupCols * ga;
+              const int64_t row0 = g.u_s + c - g.r_lo + kGroupCols * ga;
               const uint64_t ad = da0 + 8u * (uint32_t)((16 * c) % kRing4);
               const uint64_t bd = db0 + 4u * (uint32_t)row0;
               const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
@@ -1610,9 +1653,17 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       if (lane == 0) mma_commit(done_bar);
       __syncwarp();
+    } else if (warp >= 3 && w_next < nitems) {
+      // the next item's y and x into the other buffer while the MMAs run
+      const MmaItem itn = items[w_next];
+      const Item4 gn = item4_of(itn);
+      const uint32_t yn = stage0 + ((iter + 1) & 1u) * kStage4;
+      if (gn.valid && stage4(pairs[itn.pair], gn, yn, yn + kYBytes4, threadIdx.x - 96, kThreads - 96))
+        atomicOr(status, TDE_ST_INTERNAL);
     }
 
-    const bool done = mbar_wait(done_bar, iter & 1u);
+    const bool done = mbar_wait(done_bar, ndone & 1u);
+    ++ndone;
     ok = __syncthreads_and(ok && done);
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
@@ -1628,7 +1679,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int64_t tau = T0 + 127 - m + 128 * (int64_t)(col0 + j);
+          const int64_t tau = g.T0 + 127 - m + 128 * (int64_t)(col0 + j);
           if (tau < P.lag_min || tau > P.lag_max) continue;
           const int val = __float2int_rn(__uint_as_float(v[j]));
           const int64_t o = tau - P.lag_min;
@@ -1647,8 +1698,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     tc_fence_before();
-    __syncthreads();
-    sc0 += nsc;
+    sc0 += g.nsc;
   }
   tc_fence_before();
   __syncthreads();
