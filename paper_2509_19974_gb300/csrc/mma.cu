@@ -1606,14 +1606,26 @@ __global__ void __launch_bounds__(kThreads, 2)
     } else if (warp == 0) {
       // MMA issuer (whole warp waits, lane 0 issues): per chunk, the live
       // column groups, two K steps
-      int64_t glo[kGroups4], ghi[kGroups4];
+      // column group gg is live for chunks [clo[gg], chi[gg]) (live for chunk
+      // c iff its y rows meet the signal); chunks where every group is live
+      // take a fast path: one full-width pair of MMAs, no per-chunk tests
+      int clo[kGroups4], chi[kGroups4];
+      int full_lo = 0, full_hi = g.nchunks;
 #pragma unroll
       for (int gg = 0; gg < kGroups4; ++gg) {
         const int64_t lo = -g.T0 - 128 * (int64_t)(kGroupCols * gg + kGroupCols - 1);
         const int64_t hi = P.ny - g.T0 - 128 * (int64_t)(kGroupCols * gg);
-        glo[gg] = (lo > 0 ? lo : 0) - g.ks;
-        ghi[gg] = (hi < P.nx + 127 ? hi : P.nx + 127) - g.ks;
+        const int64_t glo = (lo > 0 ? lo : 0) - g.ks;
+        const int64_t ghi = (hi < P.nx + 127 ? hi : P.nx + 127) - g.ks;
+        // live for chunk c iff glo < 128 (c + 1) and ghi > 128 c
+        int64_t a = fdiv(glo, kKc8), z = fdiv(ghi + kKc8 - 1, kKc8);
+        a = a < 0 ? 0 : (a > g.nchunks ? g.nchunks : a);
+        z = z < 0 ? 0 : (z > g.nchunks ? g.nchunks : z);
+        clo[gg] = (int)a, chi[gg] = (int)z;
+        full_lo = full_lo > clo[gg] ? full_lo : clo[gg];
+        full_hi = full_hi < chi[gg] ? full_hi : chi[gg];
       }
+      const uint32_t idesc_full = idesc4_for(kN4);
       const uint64_t da0 = sdesc(slots, 512, 128, 0, 0);  // + ring slot * 8
       const uint64_t db0 = sdesc(yr, 16, 512, 4, 0);      // + row * 4
       for (int j = 0; j < g.nsc; ++j) {
@@ -1625,26 +1637,37 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
+          const int c0 = kSC4 * j;
+          const int c1 = c0 + kSC4 < g.nchunks ? c0 + kSC4 : g.nchunks;
+          const uint32_t row_c0 = (uint32_t)(g.u_s - g.r_lo) + (uint32_t)c0;
+          if (c0 >= full_lo && c1 <= full_hi) {
+            // every group live: ring slot and tile row advance by 16 slots and 1 row
+            const uint64_t bd0 = db0 + 4u * row_c0;
 #pragma unroll
-          for (int cc = 0; cc < kSC4; ++cc) {
-            const int c = kSC4 * j + cc;
-            if (c >= g.nchunks) break;
-            const int64_t kc = (int64_t)kKc8 * c;
-            int ga = kGroups4, gb = -1;
-#pragma unroll
-            for (int gg = 0; gg < kGroups4; ++gg)
-              if (glo[gg] < kc + kKc8 && ghi[gg] > kc) {
-                ga = gg < ga ? gg : ga;
-                gb = gg;
+            for (int cc = 0; cc < kSC4; ++cc)
+              if (c0 + cc < c1) {
+                const uint64_t ad = da0 + 8u * ((16u * (uint32_t)(c0 + cc)) & (uint32_t)(kRing4 - 1));
+                mma_mxf4(tmem, ad, bd0 + 4u * (uint32_t)cc, idesc_full, sfa, sfb, 1u);
+                mma_mxf4(tmem, ad + 64u, bd0 + 4u * (uint32_t)cc + 2u, idesc_full, sfa, sfb, 1u);
               }
-            if (gb >= ga) {
-              const uint32_t idesc = idesc4_for(kGroupCols * (gb - ga + 1));
-              const int64_t row0 = g.u_s + c - g.r_lo + kGroupCols * ga;
-              const uint64_t ad = da0 + 8u * (uint32_t)((16 * c) % kRing4);
-              const uint64_t bd = db0 + 4u * (uint32_t)row0;
-              const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
-              mma_mxf4(d_col, ad, bd, idesc, sfa, sfb, 1u);
-              mma_mxf4(d_col, ad + 64u, bd + 2u, idesc, sfa, sfb, 1u);
+          } else {
+            for (int c = c0; c < c1; ++c) {
+              int ga = kGroups4, gb = -1;
+#pragma unroll
+              for (int gg = 0; gg < kGroups4; ++gg)
+                if (c >= clo[gg] && c < chi[gg]) {
+                  ga = gg < ga ? gg : ga;
+                  gb = gg;
+                }
+              if (gb >= ga) {
+                const uint32_t idesc = idesc4_for(kGroupCols * (gb - ga + 1));
+                const uint32_t row0 = row_c0 + (uint32_t)(c - c0) + (uint32_t)(kGroupCols * ga);
+                const uint64_t ad = da0 + 8u * ((16u * (uint32_t)c) & (uint32_t)(kRing4 - 1));
+                const uint64_t bd = db0 + 4u * row0;
+                const uint32_t d_col = tmem + (uint32_t)(kGroupCols * ga);
+                mma_mxf4(d_col, ad, bd, idesc, sfa, sfb, 1u);
+                mma_mxf4(d_col, ad + 64u, bd + 2u, idesc, sfa, sfb, 1u);
+              }
             }
           }
           mma_commit(cmt_bar + 8 * (uint32_t)(S % kNB));
