@@ -93,6 +93,39 @@ const char* tde_last_error(const tde_ctx* ctx);
  * events are the context's; no caller memory is touched). */
 tde_status tde_ctx_set_profiling(tde_ctx* ctx, int enable);
 
+/* Template search over an unbounded stream (the paper's closing remark on
+ * long signals; Eq. (1) and Algorithm 1's argmax over the positions seen so
+ * far).  A short template y is searched for in a signal x that arrives in
+ * chunks; after every chunk the running answer equals Algorithm 1 on the
+ * prefix of x seen so far, over the lags where y lies wholly inside it.
+ * Positions are global: the template at position k of x is lag tau = -k of
+ * c[tau] = sum_n x[n] y[n + tau]; ties go to the larger value, then the
+ * smaller |tau| (the earlier position), as in tde_argmax.
+ *
+ * tde_stream_create: y is ny floats (device), quantized at creation; bits must
+ * be 1 (the sign quantizer is pointwise, so a chunk quantizes the same alone
+ * as inside the whole signal; the rank quantizer's thresholds are order
+ * statistics of the whole signal: TDE_ERR_UNSUPPORTED).  Every chunk holds at
+ * most max_chunk samples.  The stream owns device memory of about
+ * 2 (ny + max_chunk) bytes + 8 max_chunk bytes.
+ * tde_stream_push: the next chunk, n floats (device); asynchronous on
+ * `stream`, no host synchronisation: the chunk is quantized behind the last
+ * ny - 1 levels carried from before, correlated with the template (engine as
+ * given, int64), and its tie-ruled maximum folded on the device into the
+ * running best.  Pushes of one stream object must be ordered (one CUDA
+ * stream); pushes of n = 0 do nothing.
+ * tde_stream_best: *found (host, nullable) = 1 once ny samples have arrived;
+ * then the running best lag and value go to lag_out, val_out (device int64,
+ * each nullable), asynchronously on `stream`.
+ * tde_stream_destroy waits for the device and frees the stream's memory. */
+typedef struct tde_stream tde_stream;
+tde_status tde_stream_create(tde_ctx* ctx, const float* y, int64_t ny, int bits, int engine,
+                             int64_t max_chunk, tde_stream_t stream, tde_stream** out);
+tde_status tde_stream_push(tde_stream* s, const float* x, int64_t n, tde_stream_t stream);
+tde_status tde_stream_best(tde_stream* s, int64_t* lag_out, int64_t* val_out, int* found,
+                           tde_stream_t stream);
+tde_status tde_stream_destroy(tde_stream* s);
+
 /* Issue rates the engines' rooflines are measured against, per SM per SM
  * clock, on `device` (the paper has no counterpart: this is a measurement
  * utility).  Each is timed with the SM's own cycle counter inside one CTA per

@@ -2040,3 +2040,153 @@ extern "C" tde_status tde_autotune_load(tde_ctx* ctx, const tde_tune_entry* entr
   ctx->tune.assign(entries, entries + count);
   return TDE_OK;
 }
+
+// ===================================================================== streaming
+// Template search over a stream of chunks (overlap-save): each chunk is
+// quantized into the stream's own buffer behind the last ny - 1 levels carried
+// from before, the template is correlated there over the lags where it lies
+// wholly inside, and the chunk's tie-ruled maximum is folded on the device
+// into the running best in global positions.
+struct tde_stream {
+  tde_ctx* ctx = nullptr;
+  int bits = 1, engine = TDE_ENGINE_AUTO;
+  int64_t ny = 0, max_chunk = 0;
+  int8_t* qy = nullptr;                  // the quantized template
+  int8_t* buf[2] = {nullptr, nullptr};   // carry (<= ny - 1 levels) then a chunk, alternating
+  int cur = 0;                           // the buffer holding the carry
+  int64_t carry = 0, consumed = 0;       // levels carried; samples pushed so far
+  int64_t* c = nullptr;                  // one push's correlations (<= max_chunk lags)
+  int64_t* d = nullptr;                  // chunk lag, chunk value, found, best lag, best value
+};
+
+namespace {
+
+// The chunk's maximum (relative lag d[0], value d[1]) at global lag
+// -(base - d[0]) folded into the running best (d[2] = found, d[3], d[4]) in
+// the argmax's order: the larger value, then the smaller |lag|, then the
+// smaller lag.
+__global__ void k_stream_fold(int64_t* __restrict__ d, int64_t base) {
+  const int64_t lag = -(base - d[0]), val = d[1];
+  if (d[2] == 0) {
+    d[2] = 1, d[3] = lag, d[4] = val;
+    return;
+  }
+  const int64_t bl = d[3], bv = d[4];
+  const int64_t al = lag < 0 ? -lag : lag, abl = bl < 0 ? -bl : bl;
+  if (val > bv || (val == bv && (al < abl || (al == abl && lag < bl)))) d[3] = lag, d[4] = val;
+}
+
+void stream_free(tde_stream* s) {
+  if (!s) return;
+  DeviceGuard g(s->ctx->device);
+  cudaFree(s->qy);
+  cudaFree(s->buf[0]);
+  cudaFree(s->buf[1]);
+  cudaFree(s->c);
+  cudaFree(s->d);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" tde_status tde_stream_create(tde_ctx* ctx, const float* y, int64_t ny, int bits, int engine,
+                                        int64_t max_chunk, tde_stream_t stream, tde_stream** out) {
+  ApiRange nvtx_range(__func__);
+  if (!ctx) return TDE_ERR_INVALID;
+  if (!y || !out) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  *out = nullptr;
+  if (bits != 1)
+    return set_err(ctx, TDE_ERR_UNSUPPORTED,
+                   "streaming needs the pointwise sign quantizer (bits 1): the rank quantizer's "
+                   "thresholds are order statistics of the whole signal");
+  if (ny <= 0 || max_chunk <= 0) return set_err(ctx, TDE_ERR_INVALID, "ny and max_chunk must be positive");
+  if (ny > INT32_MAX || max_chunk > INT32_MAX)
+    return set_err(ctx, TDE_ERR_UNSUPPORTED, "ny and max_chunk must stay below 2^31");
+  if (engine < TDE_ENGINE_AUTO || engine > TDE_ENGINE_NTT)
+    return set_err(ctx, TDE_ERR_INVALID, "unknown engine %d", engine);
+  DeviceGuard g(ctx->device);
+  tde_stream* s = new tde_stream();
+  s->ctx = ctx, s->bits = bits, s->engine = engine, s->ny = ny, s->max_chunk = max_chunk;
+  const size_t nbuf = (size_t)(ny - 1 + max_chunk);
+  cudaError_t e = cudaMalloc(&s->qy, (size_t)ny);
+  if (e == cudaSuccess) e = cudaMalloc(&s->buf[0], nbuf);
+  if (e == cudaSuccess) e = cudaMalloc(&s->buf[1], nbuf);
+  if (e == cudaSuccess) e = cudaMalloc(&s->c, sizeof(int64_t) * (size_t)max_chunk);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d, 5 * sizeof(int64_t));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d, 0, 5 * sizeof(int64_t), st);
+  if (e != cudaSuccess) {
+    stream_free(s);
+    return cuda_err(ctx, e, "stream create");
+  }
+  const tde_status q = tde_quantize(ctx, y, ny, bits, s->qy, stream);
+  if (q != TDE_OK) {
+    stream_free(s);
+    return q;
+  }
+  *out = s;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_stream_push(tde_stream* s, const float* x, int64_t n, tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
+  if (!s) return TDE_ERR_INVALID;
+  tde_ctx* ctx = s->ctx;
+  if (n == 0) return TDE_OK;
+  if (!x) return set_err(ctx, TDE_ERR_INVALID, "null pointer");
+  if (n < 0 || n > s->max_chunk)
+    return set_err(ctx, TDE_ERR_INVALID, "chunk of %lld samples: at most max_chunk = %lld", (long long)n,
+                   (long long)s->max_chunk);
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int8_t* b = s->buf[s->cur];
+  tde_status r = tde_quantize(ctx, x, n, s->bits, b + s->carry, stream);
+  if (r != TDE_OK) return r;
+  const int64_t nb = s->carry + n, base = s->consumed - s->carry;  // base: position of b[0] in x
+  if (nb >= s->ny) {
+    // the template wholly inside b: tau in [-(nb - ny), 0], position base - tau
+    const int64_t lo = -(nb - s->ny);
+    r = tde_xcorr_int(ctx, b, nb, s->qy, s->ny, s->bits, lo, 0, s->engine, s->c, TDE_I64, stream);
+    if (r == TDE_OK) r = tde_argmax(ctx, s->c, TDE_I64, lo, nb - s->ny + 1, s->d, s->d + 1, stream);
+    if (r != TDE_OK) return r;
+    k_stream_fold<<<1, 1, 0, st>>>(s->d, base);
+    TDE_COUNT_LAUNCH(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "stream fold");
+  }
+  // the last ny - 1 levels become the other buffer's carry
+  const int64_t keep = nb < s->ny - 1 ? nb : s->ny - 1;
+  if (keep > 0) {
+    const cudaError_t e = cudaMemcpyAsync(s->buf[s->cur ^ 1], b + nb - keep, (size_t)keep,
+                                          cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "stream carry");
+  }
+  s->cur ^= 1;
+  s->carry = keep;
+  s->consumed += n;
+  return TDE_OK;
+}
+
+extern "C" tde_status tde_stream_best(tde_stream* s, int64_t* lag_out, int64_t* val_out, int* found,
+                                      tde_stream_t stream) {
+  ApiRange nvtx_range(__func__);
+  if (!s) return TDE_ERR_INVALID;
+  if (found) *found = s->consumed >= s->ny ? 1 : 0;
+  if (s->consumed < s->ny || (!lag_out && !val_out)) return TDE_OK;
+  DeviceGuard g(s->ctx->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (lag_out) e = cudaMemcpyAsync(lag_out, s->d + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && val_out) e = cudaMemcpyAsync(val_out, s->d + 4, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? TDE_OK : cuda_err(s->ctx, e, "stream best");
+}
+
+extern "C" tde_status tde_stream_destroy(tde_stream* s) {
+  if (!s) return TDE_OK;
+  {
+    DeviceGuard g(s->ctx->device);
+    cudaDeviceSynchronize();  // no push of this stream may still be running
+  }
+  stream_free(s);
+  return TDE_OK;
+}

@@ -34,7 +34,8 @@ EXPORTS = ("tde_ctx_create", "tde_ctx_destroy", "tde_ctx_sync", "tde_last_error"
            "tde_model_get", "tde_model_set", "tde_train_step", "tde_propose",
            "tde_estimate_learned", "tde_synth_pairs", "tde_autotune", "tde_autotune_table",
            "tde_autotune_load", "tde_ctx_pick_engine", "tde_xcorr_windows",
-           "tde_learned_create", "tde_learned_run", "tde_learned_destroy", "tde_refine")
+           "tde_learned_create", "tde_learned_run", "tde_learned_destroy", "tde_refine",
+           "tde_stream_create", "tde_stream_push", "tde_stream_best", "tde_stream_destroy")
 
 
 class TdeError(RuntimeError):
@@ -108,6 +109,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tde_learned_run": ([p, p], st),
         "tde_learned_destroy": ([p], st),
         "tde_refine": ([p, p, i64, p, i64, p, i32, i64, i64, p, p], st),
+        "tde_stream_create": ([p, p, i64, i32, i32, i64, p, ctypes.POINTER(p)], st),
+        "tde_stream_push": ([p, p, i64, p], st),
+        "tde_stream_best": ([p, p, p, ctypes.POINTER(i32), p], st),
+        "tde_stream_destroy": ([p], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

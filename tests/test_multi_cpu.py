@@ -102,10 +102,3 @@ def test_combine_argmax_matches_oracle_on_shards():
             locs = [oracle.argmax(c[a - lo: b - lo + 1], a) if b >= a else (None, None)
                     for a, b in multi.lag_shards(lo, hi, world)]
             assert multi.combine_argmax(locs) == oracle.argmax(c, lo)
-
-
-def test_stream_tie_order():
-    from paper_2509_19974_gb300 import stream
-    assert stream._better((-5, 10), (-3, 9)) == (-5, 10)     # larger value
-    assert stream._better((-5, 10), (-3, 10)) == (-3, 10)    # then smaller |lag|
-    assert stream._better((3, 10), (-3, 10)) == (-3, 10)     # then the smaller lag
