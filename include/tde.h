@@ -426,14 +426,18 @@ tde_status tde_learned_destroy(tde_learned* plan);
  * reads them) and window w with centre centres[8 p + w] (device int32),
  * c_out[(8 p + w) * 257 + i] (device int32) = c[centre - 128 + i] for
  * i in [0, 257); lags outside [-(n-1), n-1] read 0.  Computed on the tensor
- * cores with E4M3 operands and FP32 accumulation, exact for every n: one
- * accumulator sums at most 2^24 / (2^(bits-1))^2 samples, and the partial
- * sums of longer pairs are added as integers.  bits 1, 2 or 4; levels must
- * lie in the bits' range (|q| <= 1, or <= 7 for bits 4): one outside it sets
- * the status word, and tde_ctx_sync then returns TDE_ERR_INVALID.
- * TDE_ERR_OVERFLOW if n * (2^(bits-1))^2 >= 2^31 (the int32 bound).  Uses a
- * context workspace of 2 npairs * round_up(n, 128) bytes for the levels in
- * E4M3. */
+ * cores in polyphase form: with samples split as k = 128 a + b, the blocks
+ * D_u[b][j] = sum_a x[128 a + b] y[128 (a + u) + j] that the windows need are
+ * GEMMs over the rows a (E4M3 operands, FP32 accumulation over at most 512
+ * rows, so every value is an exact integer), and each lag tau is the sum of
+ * the diagonals j - b = tau - 128 u of its blocks, added in int32; longer
+ * signals' segments of 512 rows are added as integers, so the result is
+ * exact for every n.  bits 1, 2 or 4; levels must lie in the bits' range
+ * (|q| <= 1, or <= 7 for bits 4): one outside it sets the status word, and
+ * tde_ctx_sync then returns TDE_ERR_INVALID.  TDE_ERR_OVERFLOW if
+ * n * (2^(bits-1))^2 >= 2^31 (the int32 bound).  Uses a context workspace of
+ * 2 npairs * round_up(n, 128) bytes for the levels in E4M3, 24 bytes per
+ * window and 4 per pair for the window descriptors. */
 tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n, int npairs, int bits,
                              const int32_t* centres, int32_t* c_out, tde_stream_t stream);
 

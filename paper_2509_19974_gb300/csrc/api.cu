@@ -1386,10 +1386,22 @@ tde_status check_model(tde_ctx* ctx, const tde_model* m) {
 // Window w of pair p: lags [c - 128, c + 128] clipped to the overlap range;
 // lag tau lands at cbuf[i * stride + tau - (c - 128)].
 __global__ void k_make_windows(const int32_t* __restrict__ centres, int npairs, int64_t n,
-                               int32_t* __restrict__ cbuf, int stride, WinJob* __restrict__ jobs) {
+                               int32_t* __restrict__ cbuf, int stride, WinJob* __restrict__ jobs,
+                               int32_t* __restrict__ njobs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npairs * kCnnTopK) return;
   jobs[i] = win_job_of(centres[i], n, cbuf + (int64_t)i * stride);
+  if (i % kCnnTopK == 0) {  // the pair's job count in the polyphase windows kernel
+    int64_t lo[kCnnTopK], hi[kCnnTopK];
+#pragma unroll
+    for (int w = 0; w < kCnnTopK; ++w) {
+      const WinJob J = win_job_of(centres[i + w], n, cbuf);
+      lo[w] = J.lag_lo, hi[w] = J.lag_hi;
+    }
+    int a[kCnnTopK], b[kCnnTopK];
+    win_blocks(lo, hi, a, b);
+    njobs[i / kCnnTopK] = win_jobs(a, b);
+  }
 }
 
 
@@ -1576,6 +1588,7 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Layout L;
   const size_t o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
+  const size_t o_njobs = L.w<int32_t>((size_t)npairs);
   const int64_t n_pad = (n + 127) / 128 * 128;
   const size_t o_qe = L.w<uint8_t>((size_t)2 * npairs * n_pad);
   Bases B;
@@ -1586,19 +1599,16 @@ extern "C" tde_status tde_xcorr_windows(tde_ctx* ctx, const int8_t* q, int64_t n
   cudaError_t e = cudaMemsetAsync(c_out, 0, sizeof(int32_t) * (size_t)npairs * kCnnTopK * kCnnWin, st);
   if (e == cudaSuccess) {
     k_make_windows<<<(npairs * kCnnTopK + 255) / 256, 256, 0, st>>>(centres, npairs, n, c_out,
-                                                                     kCnnWin, jobs);
+                                                                     kCnnWin, jobs, B.dw<int32_t>(o_njobs));
     TDE_COUNT_LAUNCH(1);
     e = cudaGetLastError();
   }
-  // levels in {-1, 0, 1} (bits 1, 2): packed E2M1 operands; bits 4: E4M3
-  const bool fp4 = bits <= 2;
-  if (e == cudaSuccess)
-    e = fp4 ? launch_to_e2m1(q, n, n_pad, 2 * npairs, qe, ctx->d_status, st)
-            : launch_to_e4m3(q, n, n_pad, 2 * npairs, bits, qe, ctx->d_status, st);
+  // the levels as E4M3 bytes (a level outside the bits' range sets the status
+  // word), then the windows in polyphase form
+  if (e == cudaSuccess) e = launch_to_e4m3(q, n, n_pad, 2 * npairs, bits, qe, ctx->d_status, st);
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = fp4 ? launch_xcorr_mma_windows4(qe, n, n_pad, npairs, bits, jobs, ctx->d_status, st)
-            : launch_xcorr_mma_windows(qe, n, n_pad, npairs, bits, jobs, ctx->d_status, st);
+    e = launch_xcorr_win_pp(qe, n, n_pad, npairs, jobs, B.dw<int32_t>(o_njobs), ctx->d_status, st);
   }
   return e == cudaSuccess ? TDE_OK : cuda_err(ctx, e, "windows");
 }
@@ -1672,7 +1682,7 @@ struct LearnedWork {
   QuantStage Q;
   CnnPlan C;
   MmaStage T;  // one full-range pair: the fallback's item template
-  size_t o_q = 0, o_qe = 0, o_cent = 0, o_marg = 0, o_jobs = 0, o_cwin = 0;
+  size_t o_q = 0, o_qe = 0, o_cent = 0, o_marg = 0, o_jobs = 0, o_njobs = 0, o_cwin = 0;
   size_t o_fbidx = 0, o_nfb = 0, o_fbpairs = 0, o_fbitems = 0, o_nitems = 0, o_counter = 0;
   size_t o_fbargs = 0, o_keys = 0, o_tlag = 0, o_tval = 0, o_cfb = 0;
 };
@@ -1683,11 +1693,12 @@ void learned_plan(LearnedWork* w, int npairs, int64_t n, int bits, float theta) 
   const int S = 2 * npairs;
   w->Q.plan(L, S, bits, nullptr, n);
   w->o_q = L.w<int8_t>((size_t)S * n);
-  w->o_qe = L.w<uint8_t>((size_t)S * n / 2);  // the levels as packed E2M1 (n % 2048 == 0)
+  w->o_qe = L.w<uint8_t>((size_t)S * n);  // the levels as E4M3 bytes (n % 2048 == 0)
   w->C.plan(L, npairs, n, false);
   w->o_cent = L.w<int32_t>((size_t)npairs * kCnnTopK);
   w->o_marg = L.w<float>((size_t)npairs);
   w->o_jobs = L.w<WinJob>((size_t)npairs * kCnnTopK);
+  w->o_njobs = L.w<int32_t>((size_t)npairs);
   w->o_cwin = L.w<int32_t>((size_t)npairs * kCnnTopK * kCnnWin);
   std::vector<Job> one{Job{nullptr, nullptr, n, n, -(n - 1), n - 1, nullptr, 0}};
   w->T.plan(L, one, false, bits <= 2);  // replicated per fallback pair: keep the default segments
@@ -1740,12 +1751,12 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   if (e == cudaSuccess && fused)
     e = launch_cnn_scores_propose(B.dw<float>(w.C.o_out[kCnnLayers - 1]), P, w.C.Lf, m->params,
                                   B.dw<float>(w.C.o_scores), cent, marg, jobs,
-                                  B.dw<int32_t>(w.o_cwin), n, st);
+                                  B.dw<int32_t>(w.o_cwin), n, B.dw<int32_t>(w.o_njobs), st);
   if (e == cudaSuccess && !fused) {
     e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
     if (e == cudaSuccess) {
       k_make_windows<<<(P * kCnnTopK + 255) / 256, 256, 0, st>>>(
-          cent, P, n, B.dw<int32_t>(w.o_cwin), kCnnWin, jobs);
+          cent, P, n, B.dw<int32_t>(w.o_cwin), kCnnWin, jobs, B.dw<int32_t>(w.o_njobs));
       TDE_COUNT_LAUNCH(1);
       e = cudaGetLastError();
     }
@@ -1755,7 +1766,7 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   }
   if (e == cudaSuccess) {
     EngineTimer t(ctx, st);
-    e = launch_xcorr_mma_windows4(qe, n, n, P, w.bits, jobs, ctx->d_status, st);
+    e = launch_xcorr_win_pp(qe, n, n, P, jobs, B.dw<int32_t>(w.o_njobs), ctx->d_status, st);
   }
   if (e == cudaSuccess) e = launch_window_argmax(jobs, P, lag_out, val_out, st);
   // fallback, decided and run on the device

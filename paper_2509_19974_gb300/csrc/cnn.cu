@@ -444,6 +444,7 @@ struct TopOut {
   WinJob* jobs;      // [P][8]
   int32_t* cbuf;     // window w of pair p at cbuf + (8 p + w) * 257
   int64_t n;         // signal length (lag range of the windows)
+  int32_t* njobs;    // [P]: jobs of the polyphase windows kernel
 };
 
 template <bool kPosMajor, bool kTop>
@@ -534,12 +535,24 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* _
     int32_t centre;
     float margin;
     topk_warp(v, nb, Lf, lane, centre, margin);
+    const int64_t i = (int64_t)p * kCnnTopK + lane;
+    const WinJob J = win_job_of(centre, top.n, top.cbuf + i * kCnnWin);
     if (lane < kCnnTopK) {
-      const int64_t i = (int64_t)p * kCnnTopK + lane;
       top.centres[i] = centre;
-      top.jobs[i] = win_job_of(centre, top.n, top.cbuf + i * kCnnWin);
+      top.jobs[i] = J;
     }
-    if (lane == 0) top.margin[p] = margin;
+    int64_t lo[kCnnTopK], hi[kCnnTopK];
+#pragma unroll
+    for (int w = 0; w < kCnnTopK; ++w) {
+      lo[w] = __shfl_sync(0xffffffffu, J.lag_lo, w);
+      hi[w] = __shfl_sync(0xffffffffu, J.lag_hi, w);
+    }
+    if (lane == 0) {
+      int a[kCnnTopK], b[kCnnTopK];
+      win_blocks(lo, hi, a, b);
+      top.njobs[p] = win_jobs(a, b);
+      top.margin[p] = margin;
+    }
   }
 }
 
@@ -908,10 +921,10 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             uint8_t* qf, uint32_t* d_status, cudaStream_t st) {
+                             uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
   const int Ld = (int)(n / kCnnDec);
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
-  cudaError_t e = launch_cnn_conv1_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qf,
+  cudaError_t e = launch_cnn_conv1_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qe,
                                       d_status, st);
   if (e != cudaSuccess) return e;
   k_eo_pad<<<(nsig + 63) / 64, 256, 0, st>>>(act[0], Ld / 2, nsig);
@@ -945,13 +958,13 @@ cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float
 
 cudaError_t launch_cnn_scores_propose(const float* feat, int npairs, int Lf, const float* params,
                                       float* scores, int32_t* centres, float* margin, WinJob* jobs,
-                                      int32_t* cbuf, int64_t n, cudaStream_t st) {
+                                      int32_t* cbuf, int64_t n, int32_t* njobs, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (Lf < 1 || Lf > kSpMaxLf) return cudaErrorNotSupported;
   cudaFuncSetAttribute(k_scores_pair<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kSpTopSmem);
   k_scores_pair<true, true><<<npairs, kSpWarps * 32, kSpTopSmem, st>>>(
-      feat, Lf, params, scores, TopOut{centres, margin, jobs, cbuf, n});
+      feat, Lf, params, scores, TopOut{centres, margin, jobs, cbuf, n, njobs});
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

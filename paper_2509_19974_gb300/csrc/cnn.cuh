@@ -3,6 +3,8 @@
 // exact integer correlation (cnn.cu).
 #pragma once
 
+#include <climits>
+
 #include "common.cuh"
 
 // Architecture (shared by both signals of a pair):
@@ -41,12 +43,11 @@ cudaError_t launch_cnn_layer(const CnnLayerIO& io, int l, int nsig, const uint16
 // layers: act[l] holds layer l's output, nsig x cnn_eo_elems((n/16) >> (l+1))
 // BF16 in the layout above; feat receives the FP32 features [nsig][n/256][32]
 // (position-major);
-// qf (nullable, nsig x n / 2 bytes) the levels as packed E2M1 nibbles (sample
-// i in nibble i & 1 of byte i / 2; levels in {-1, 0, 1}).  n a multiple of
+// qe (nullable, nsig x n bytes) the levels as E4M3 bytes.  n a multiple of
 // 2048.
 cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf,
                              const float* params, uint16_t* const act[kCnnLayers - 1], float* feat,
-                             uint8_t* qf, uint32_t* d_status, cudaStream_t st);
+                             uint8_t* qe, uint32_t* d_status, cudaStream_t st);
 // Inference activations between conv layers: a layer's input of length L
 // is, per signal, 8 arrays (position parity x 8-channel chunk, parity-major)
 // of cnn_eo_rows(L) rows of 8 BF16 channels; row r holds position 2r - 4
@@ -66,10 +67,9 @@ cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, c
 // The first layer of the inference forward on the tensor cores (mma.cu):
 // decimation of q [nsig][n] int8, conv 1 -> 32 (weights wbf [32][1][9], bias)
 // -> out, the second layer's input (length n/32, parity arrays; the zero rows
-// are the caller's); qf (nullable) receives the levels as packed E2M1 nibbles
-// (levels in {-1, 0, 1}).
+// are the caller's); qe (nullable) receives the levels as E4M3 bytes.
 cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
-                                uint16_t* out, uint8_t* qf, uint32_t* d_status, cudaStream_t st);
+                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1;
 // channel-major [S][32][Lf], or position-major [S][Lf][32] with pos_major).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
@@ -123,16 +123,57 @@ __device__ __forceinline__ WinJob win_job_of(int64_t c, int64_t n, int32_t* cbuf
   if (hi > n - 1) hi = n - 1;
   return WinJob{lo, hi, cbuf_i + (hi >= lo ? lo - first : 0)};
 }
+
+// The windows' 128-lag blocks in the polyphase windows kernel (winpp.cu):
+// window [lo, hi] needs blocks floor(lo / 128) .. floor((hi + 127) / 128),
+// a[w] .. b[w] here (INT_MAX for an empty window, hi < lo), sorted by a.
+__device__ __forceinline__ int64_t win_fdiv128(int64_t v) { return v >= 0 ? v / 128 : -((-v + 127) / 128); }
+__device__ __forceinline__ void win_blocks(const int64_t (&lo)[kCnnTopK], const int64_t (&hi)[kCnnTopK],
+                                           int (&a)[kCnnTopK], int (&b)[kCnnTopK]) {
+#pragma unroll
+  for (int w = 0; w < kCnnTopK; ++w) {
+    const bool empty = hi[w] < lo[w];
+    a[w] = empty ? INT_MAX : (int)win_fdiv128(lo[w]);
+    b[w] = empty ? INT_MAX : (int)win_fdiv128(hi[w] + 127);
+  }
+#pragma unroll
+  for (int pass = 0; pass < kCnnTopK; ++pass)  // odd-even transposition sort
+#pragma unroll
+    for (int i = pass & 1; i + 1 < kCnnTopK; i += 2)
+      if (a[i] > a[i + 1]) {
+        const int ta = a[i], tb = b[i];
+        a[i] = a[i + 1], b[i] = b[i + 1];
+        a[i + 1] = ta, b[i + 1] = tb;
+      }
+}
+// Its jobs for those sorted ranges: overlapping or adjacent ranges join into
+// runs, and a run of L blocks is ceil(L / 2) jobs of one or two blocks.
+__device__ __forceinline__ int win_jobs(const int (&a)[kCnnTopK], const int (&b)[kCnnTopK]) {
+  if (a[0] == INT_MAX) return 0;
+  int n = 0, r0 = a[0], r1 = b[0];
+#pragma unroll
+  for (int i = 1; i < kCnnTopK; ++i) {
+    if (a[i] == INT_MAX) break;
+    if (a[i] <= r1 + 1) {
+      r1 = b[i] > r1 ? b[i] : r1;
+    } else {
+      n += (r1 - r0 + 2) / 2;
+      r0 = a[i], r1 = b[i];
+    }
+  }
+  return n + (r1 - r0 + 2) / 2;
+}
 #endif
 // The learned step's proposal in one launch, for Lf <= kCnnFusedMaxLf (else
 // cudaErrorNotSupported): the scores of launch_cnn_scores (position-major
 // features), then per pair the centres and margin of launch_cnn_topk
 // (identical arithmetic, so identical values) and its 8 window jobs for
 // signals of length n (window w of pair p writes cbuf + (8 p + w) * 257),
-// with those 8 * 257 correlations zeroed.
+// with those 8 * 257 correlations zeroed, and njobs[p] = the pair's job
+// count in the polyphase windows kernel (win_jobs).
 cudaError_t launch_cnn_scores_propose(const float* feat, int npairs, int Lf, const float* params,
                                       float* scores, int32_t* centres, float* margin, WinJob* jobs,
-                                      int32_t* cbuf, int64_t n, cudaStream_t st);
+                                      int32_t* cbuf, int64_t n, int32_t* njobs, cudaStream_t st);
 // Per pair: tie-ruled argmax over its 8 windows -> lag, value.
 cudaError_t launch_window_argmax(const WinJob* d_jobs, int npairs, int64_t* lag, int64_t* val,
                                  cudaStream_t st);

@@ -74,6 +74,14 @@ cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_p
 // scales), K = 64 samples per MMA.
 cudaError_t launch_xcorr_mma_windows4(const uint8_t* d_qf, int64_t n, int64_t n_pad, int npairs, int bits,
                                       const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
+// The same windows in polyphase form (winpp.cu): per pair the 128 x 128
+// blocks D_u[b][j] = sum_a x[128 a + b] y[128 (a + u) + j] that the windows
+// need, as MN-major E4M3 GEMMs over the rows a, and each window lag as a sum
+// of block diagonals.  d_qe as for launch_xcorr_mma_windows (any bits: a
+// block sums at most 512 rows, exact in FP32); the c buffers must be zeroed
+// first; d_njobs[p] = win_jobs of pair p's windows (device).  One CTA per SM.
+cudaError_t launch_xcorr_win_pp(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, const WinJob* d_jobs,
+                                const int32_t* d_njobs, uint32_t* d_status, cudaStream_t st);
 // Levels [nsig][n] -> packed E2M1 [nsig][n_pad / 2 bytes] (zeros past n);
 // n_pad % 8 == 0.  A level outside {-1, 0, 1} flags TDE_ST_INTERNAL.
 cudaError_t launch_to_e2m1(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qf,

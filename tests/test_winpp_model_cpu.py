@@ -1,0 +1,310 @@
+"""CPU model of the polyphase windows kernel (k_xcorr_win_pp in
+csrc/winpp.cu): its job plan, the order in which its TMA role fills and its
+MMA role releases the x-tile and y-chunk rings, and its arithmetic (blocks
+D_u over 128-sample rows, diagonals, windows, segments).  The model follows
+the kernel's rules step by step so that a change to them is checked here,
+against a direct correlation, before it runs on a GPU."""
+import random
+
+import numpy as np
+
+SEG_ROWS = 512       # rows summed per accumulator
+TILE_ROWS = 32       # K rows per MMA
+HALF_ROWS = 256      # x rows per load and release
+X_HALVES = 3         # x ring
+UNIT_ROWS = 64       # y rows per load and release
+Y_UNITS = 11         # y ring
+MIRROR_ROWS = 32     # rows of unit slot 0 mirrored past the ring's end
+GROUP_UNITS = Y_UNITS - 2
+WIN_LEN = 257
+
+
+def fdiv128(a):
+    return a // 128  # Python's floor division
+
+
+def pp_plan(wins):
+    """Blocks the windows [lo, hi] need (floor(lo/128) .. floor((hi+127)/128)),
+    merged into sorted runs (adjacent runs join), cut into jobs of 2 blocks."""
+    iv = sorted((fdiv128(lo), fdiv128(hi + 127)) for lo, hi in wins if hi >= lo)
+    jobs, i = [], 0
+    while i < len(iv):
+        r0, r1 = iv[i]
+        i += 1
+        while i < len(iv) and iv[i][0] <= r1 + 1:
+            r1 = max(r1, iv[i][1])
+            i += 1
+        for u in range(r0, r1 + 1, 2):
+            jobs.append((u, 2 if r1 - u >= 1 else 1))
+    return jobs
+
+
+def visits(plans, nseg, rows_total, J0, J1):
+    """The kernel's walk over jobs [J0, J1) in (pair, segment, job) order:
+    yields (p, s, tiles, groups) with groups a list of (first logical y
+    unit, units, [(u, nb), ...])."""
+    flat = [(p, s, k) for p, pl in enumerate(plans) for s in range(nseg) for k in range(len(pl))]
+    run = flat[J0:J1]
+    yu = 0
+    i = 0
+    while i < len(run):
+        p, s, _ = run[i]
+        ks = []
+        while i < len(run) and run[i][0] == p and run[i][1] == s:
+            ks.append(run[i][2])
+            i += 1
+        rows = min(SEG_ROWS, rows_total - SEG_ROWS * s)
+        tiles = -(-rows // TILE_ROWS)
+        jl = [plans[p][k] for k in ks]
+
+        def units(g0, k):
+            r = jl[k][0] + jl[k][1] - 1 - jl[g0][0] + TILE_ROWS * tiles
+            return -(-r // UNIT_ROWS)
+
+        groups, ge = [], 0
+        while ge < len(jl):
+            gb = ge
+            ge = gb + 1
+            while ge < len(jl) and units(gb, ge) <= GROUP_UNITS:
+                ge += 1
+            gun = units(gb, ge - 1)
+            groups.append((yu, gun, jl[gb:ge]))
+            yu += gun
+        yield p, s, tiles, groups
+
+
+def simulate(plans, nseg, rows_total, J0, J1, lanes=4):
+    """Runs the TMA role (load i of a visit by lane i % lanes, each lane in
+    order) and the MMA role as the kernel orders them: a load into a slot's
+    lap L waits for the release of lap L - 1; an MMA waits for the loads it
+    reads; releases follow the kernel's rules.  Checks that the run
+    finishes (no circular wait) and that every MMA finds in its x half and
+    y rows (through the mirror past the ring's end) the data it expects."""
+    V = list(visits(plans, nseg, rows_total, J0, J1))
+    loads = []  # ('x', logical half, (p, first row)) / ('y', logical unit, (p, first row))
+    xh = 0
+    for p, s, tiles, groups in V:
+        nh = -(-tiles * TILE_ROWS // HALF_ROWS)
+        rowbase = s * SEG_ROWS
+        for gi, (yu, gun, jl) in enumerate(groups):
+            ubase = rowbase + jl[0][0]
+            c = 0
+            if gi == 0:
+                for h in range(nh):
+                    loads.append(('x', xh + h, (p, rowbase + HALF_ROWS * h)))
+                    need = (HALF_ROWS * (h + 1) + TILE_ROWS) // UNIT_ROWS
+                    while c < gun and c <= need:
+                        loads.append(('y', yu + c, (p, ubase + UNIT_ROWS * c)))
+                        c += 1
+            while c < gun:
+                loads.append(('y', yu + c, (p, ubase + UNIT_ROWS * c)))
+                c += 1
+        xh += nh
+    mmas = []
+    xh = 0
+    for p, s, tiles, groups in V:
+        nh = -(-tiles * TILE_ROWS // HALF_ROWS)
+        tph = HALF_ROWS // TILE_ROWS
+        for gi, (yu, gun, jl) in enumerate(groups):
+            freed = yu
+            for k, (u, nb) in enumerate(jl):
+                urel = u - jl[0][0]
+                last_visit = gi == len(groups) - 1 and k == len(jl) - 1
+                last_group = k == len(jl) - 1
+                for t in range(tiles):
+                    # K tiles in batches of one x half: the batch's waits before
+                    # its first tile, its releases after its last
+                    hh = xh + t // tph
+                    t1 = min(tiles, (t // tph + 1) * tph)
+                    need_y = yu + (urel + TILE_ROWS * t1 + nb - 2) // UNIT_ROWS
+                    rel = []
+                    if t + 1 == t1:
+                        if last_visit:
+                            rel.append(('x', hh))
+                        if last_group:
+                            upto = yu + gun if t1 == tiles else yu + (urel + TILE_ROWS * t1) // UNIT_ROWS
+                            while freed < upto:
+                                rel.append(('y', freed))
+                                freed += 1
+                    want_x = [(p, s * SEG_ROWS + TILE_ROWS * t + r) for r in range(TILE_ROWS)]
+                    want_y = [(p, s * SEG_ROWS + u + TILE_ROWS * t + r) for r in range(TILE_ROWS + nb - 1)]
+                    pos = UNIT_ROWS * yu + urel + TILE_ROWS * t  # logical y row of the tile's first row
+                    mmas.append((hh, t % tph, need_y, rel, want_x, pos, want_y))
+        xh += nh
+    filled = {'x': set(), 'y': set()}
+    released = {'x': set(), 'y': set()}
+    xrows = [[None] * HALF_ROWS for _ in range(X_HALVES)]
+    yrows = [None] * (Y_UNITS * UNIT_ROWS + MIRROR_ROWS)
+    lane_loads = [[ld for i, ld in enumerate(loads) if i % lanes == l] for l in range(lanes)]
+    lp = [0] * lanes
+    mi = 0
+    while any(lp[l] < len(lane_loads[l]) for l in range(lanes)) or mi < len(mmas):
+        progressed = False
+        for l in range(lanes):
+            if lp[l] < len(lane_loads[l]):
+                kind, idx, (p, row) = lane_loads[l][lp[l]]
+                ring = X_HALVES if kind == 'x' else Y_UNITS
+                if idx < ring or (idx - ring) in released[kind]:
+                    slot = idx % ring
+                    if kind == 'x':
+                        xrows[slot] = [(p, row + r) for r in range(HALF_ROWS)]
+                    else:
+                        for r in range(UNIT_ROWS):
+                            yrows[slot * UNIT_ROWS + r] = (p, row + r)
+                        if slot == 0:
+                            for r in range(MIRROR_ROWS):
+                                yrows[Y_UNITS * UNIT_ROWS + r] = (p, row + r)
+                    filled[kind].add(idx)
+                    lp[l] += 1
+                    progressed = True
+        if mi < len(mmas):
+            hh, tin, need_y, rel, want_x, pos, want_y = mmas[mi]
+            if hh in filled['x'] and all(c in filled['y'] for c in range(need_y + 1) if c >= 0) \
+                    and all(c in filled['y'] for c in range(pos // UNIT_ROWS, need_y + 1)):
+                got_x = xrows[hh % X_HALVES][TILE_ROWS * tin:TILE_ROWS * (tin + 1)]
+                assert got_x == want_x, (mi, got_x[:2], want_x[:2])
+                phys = pos % (Y_UNITS * UNIT_ROWS)
+                got = yrows[phys:phys + len(want_y)]
+                assert got == want_y, (mi, pos, got[:3], want_y[:3])
+                for kind, idx in rel:
+                    released[kind].add(idx)
+                mi += 1
+                progressed = True
+        assert progressed, f"circular wait at loads {lp}, mma {mi}/{len(mmas)}"
+    return len(mmas)
+
+
+def _windows_adjacent(n, centre_bin, rng):
+    """8 windows of 257 lags around bins 256 l (adjacent bins)."""
+    out = []
+    for w in range(8):
+        c = 256 * (centre_bin + w - 4)
+        lo, hi = max(c - 128, -(n - 1)), min(c + 128, n - 1)
+        out.append((lo, hi))
+    return out
+
+
+def _windows_random(n, rng):
+    lf = n // 256
+    bins = rng.sample(range(-(lf - 1), lf), 8)
+    return [(max(256 * l - 128, -(n - 1)), min(256 * l + 128, n - 1)) for l in bins]
+
+
+def _runs(J, G):
+    return [(J * c // G, J * (c + 1) // G) for c in range(G)]
+
+
+def test_plan_blocks_cover_every_window_lag():
+    rng = random.Random(1)
+    for _ in range(300):
+        n = rng.choice([4096, 65536, 100000])
+        wins = _windows_random(n, rng) if rng.random() < 0.5 else _windows_adjacent(n, rng.randint(-200, 200), rng)
+        blocks = {u + i for u, nb in pp_plan(wins) for i in range(nb)}
+        for lo, hi in wins:
+            for tau in range(lo, hi + 1, 7):
+                # the blocks holding terms of c[tau]: floor((b + tau) / 128), b < 128
+                need = {(b + tau) // 128 for b in range(128)}
+                assert need <= blocks
+    # adjacent bins: 17 blocks (9 jobs) for 8 windows of 257 lags
+    wins = _windows_adjacent(65536, 0, rng)
+    pl = pp_plan(wins)
+    assert sum(nb for _, nb in pl) == 17 and len(pl) == 9
+
+
+def test_rings_fill_before_read_and_release_after_last_read():
+    rng = random.Random(2)
+    cases = 0
+    for trial in range(40):
+        n = rng.choice([65536, 65536, 4096, 3000, 100000, 140000])
+        rows_total = -(-n // 128)
+        nseg = -(-rows_total // SEG_ROWS)
+        npairs = rng.randint(1, 12)
+        plans = []
+        for _ in range(npairs):
+            r = rng.random()
+            if r < 0.4:
+                wins = _windows_adjacent(n, rng.randint(-(n // 256) + 5, n // 256 - 5), rng)
+            elif r < 0.65:
+                wins = _windows_random(n, rng)
+            elif r < 0.8:  # windows on no 128-lag boundary (four blocks each)
+                wins = [(lo, lo + 256) for lo in rng.sample(range(-(n - 1), n - 257), 8)]
+            else:
+                wins = []  # a pair without jobs (all windows empty)
+            plans.append(pp_plan(wins))
+        J = sum(len(pl) for pl in plans) * nseg
+        G = rng.choice([1, 2, 3, 7])
+        for J0, J1 in _runs(J, G):
+            if J1 > J0:
+                cases += simulate(plans, nseg, rows_total, J0, J1)
+    assert cases > 1000
+
+
+def _pp_windows(x, y, wins, n):
+    """The kernel's arithmetic, visit by visit (one per segment here): each
+    job's blocks D_u over the segment's rows, value D[b][j] added to diagonal
+    j - b + 127 of its block's slot; then per window lag tau = lo + t, with
+    q = floor(tau / 128) and r = tau - 128 q, diagonal r + 127 of block q plus
+    (r >= 1) diagonal r - 1 of block q + 1, the blocks found by their slots."""
+    rows_total = -(-n // 128)
+    xp = np.zeros(rows_total * 128, np.int64)
+    yp = np.zeros(rows_total * 128, np.int64)
+    xp[:n], yp[:n] = x, y
+    X = xp.reshape(rows_total, 128)
+    Y = yp.reshape(rows_total, 128)
+    nseg = -(-rows_total // SEG_ROWS)
+    out = [np.zeros(WIN_LEN, np.int64) for _ in wins]
+    diag_idx = (np.arange(128)[None, :] - np.arange(128)[:, None] + 127).ravel()
+    plan = pp_plan(wins)
+    assert len(plan) <= 16 and sum(nb for _, nb in plan) <= 32
+    for s in range(nseg):
+        a0, a1 = s * SEG_ROWS, min((s + 1) * SEG_ROWS, rows_total)
+        diag = np.zeros((32, 256), np.int64)
+        slot = 0
+        for u, nb in plan:
+            for blk in range(nb):
+                rows = np.arange(a0, a1) + u + blk
+                ok = (rows >= 0) & (rows < rows_total)
+                Yb = np.zeros((a1 - a0, 128), np.int64)
+                Yb[ok] = Y[rows[ok]]
+                D = X[a0:a1].T @ Yb                      # D[b][j]
+                assert np.abs(D).max(initial=0) < 2 ** 24  # exact in FP32
+                diag[slot + blk, :255] += np.bincount(diag_idx, weights=D.ravel().astype(np.float64),
+                                                      minlength=255).astype(np.int64)
+            slot += nb
+        for w, (lo, hi) in enumerate(wins):
+            if hi < lo:
+                continue
+            wslot = []
+            for i in range(4):  # slot of block floor(lo / 128) + i, or -1
+                ub, sl, acc = fdiv128(lo) + i, -1, 0
+                for u, nb in plan:
+                    if u <= ub < u + nb:
+                        sl = acc + ub - u
+                    acc += nb
+                wslot.append(sl)
+            for t in range(hi - lo + 1):
+                tau = lo + t
+                q = fdiv128(tau)
+                r, i0 = tau - 128 * q, q - fdiv128(lo)
+                v = diag[wslot[i0], r + 127] if wslot[i0] >= 0 else 0
+                if r >= 1 and wslot[i0 + 1] >= 0:
+                    v += diag[wslot[i0 + 1], r - 1]
+                out[w][t] += v
+    return out
+
+
+def test_polyphase_arithmetic_equals_direct_correlation():
+    rng = np.random.default_rng(3)
+    for n, kb in ((3000, 1), (8192, 7), (70000, 7)):
+        x = rng.integers(-kb, kb + 1, n)
+        y = rng.integers(-kb, kb + 1, n)
+        full = np.correlate(y, x, mode="full")  # full[k] = sum_i x[i] y[i + k - (n - 1)]
+        prng = random.Random(n)
+        unaligned = [(lo, lo + 256) for lo in prng.sample(range(-(n - 1), n - 257), 8)]
+        for wins in (_windows_adjacent(n, prng.randint(-3, 3), prng), _windows_random(n, prng), unaligned,
+                     [(-(n - 1), -(n - 1) + 100), (n - 1 - 256, n - 1), (5, 4)]):
+            got = _pp_windows(x, y, wins, n)
+            for (lo, hi), o in zip(wins, got):
+                want = full[np.arange(lo, hi + 1) + n - 1]
+                assert np.array_equal(o[:hi - lo + 1], want)
+                assert not o[hi - lo + 1:].any()
