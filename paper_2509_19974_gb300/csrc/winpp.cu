@@ -133,18 +133,62 @@ __device__ __forceinline__ void red_shared_s32(uint32_t addr, int v) {
   asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-// 32 lanes x 32 consecutive columns of FP32 accumulator -> v[0 .. 31] (the
-// caller waits with tcgen05.wait::ld).
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* v) {
+// 16 lanes x 32 consecutive columns of FP32 accumulator -> v[0 .. 15] (the
+// caller waits with tcgen05.wait::ld).  Thread t receives lanes t / 4 and
+// t / 4 + 8 of the 16: v[4 g + e] = (lane t / 4, column 8 g + 2 (t % 4) + e)
+// and v[4 g + 2 + e] = (lane t / 4 + 8, the same column), g < 4, e < 2 (the
+// 16x256b shape's layout, checked on the device with a one-warp probe).
+__device__ __forceinline__ void tmem_ld16x256_x4(uint32_t taddr, uint32_t* v) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
+}
+
+// The diagonal sums of one warp's share of a finished accumulator: TMEM lanes
+// 32 qd .. 32 qd + 31 (rows b) and kCols columns from c0 (columns j = jcol0 +
+// the column's offset within them, in its block).  Thread t holds rows
+// b_k = 32 qd + t / 4 + 8 k (k < 4) and columns 8 g + 2 (t % 4) + e, so its
+// values with the same g - k lie on one diagonal j - b: it sums each such
+// chain of four in FP32 (exact: |D| <= 512 * 49 and 4 * 512 * 49 < 2^24) and
+// adds the 2 (kCols / 8 + 3) chain sums to the block's diagonals with
+// shared-memory atomics, a third of one atomic per value.
+template <int kCols>
+__device__ __forceinline__ void pp_drain(uint32_t tcol, int qd, int lane, uint32_t drow) {
+  constexpr int G = kCols / 8;
+  float acc[2][G + 3];
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int i = 0; i < G + 3; ++i) acc[e][i] = 0.f;
+#pragma unroll
+  for (int cb = 0; cb < kCols; cb += 32) {
+    uint32_t lo[16], hi[16];  // lanes 32 qd + 0..15 (k = 0, 1) and + 16..31 (k = 2, 3)
+    tmem_ld16x256_x4(tcol + (uint32_t)cb, lo);
+    tmem_ld16x256_x4(tcol + (16u << 16) + (uint32_t)cb, hi);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg) {
+      const int g = cb / 8 + gg;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        acc[e][g + 3] += __uint_as_float(lo[4 * gg + e]);      // k = 0: g - k = g
+        acc[e][g + 2] += __uint_as_float(lo[4 * gg + 2 + e]);  // k = 1
+        acc[e][g + 1] += __uint_as_float(hi[4 * gg + e]);      // k = 2
+        acc[e][g] += __uint_as_float(hi[4 * gg + 2 + e]);      // k = 3
+      }
+    }
+  }
+  // chain s = g - k (acc index s + 3) of column parity e lies on diagonal
+  // j - b + 127 = 8 s + e + 2 (t % 4) - t / 4 - 32 qd + 127 (+ the columns' offset)
+  const uint32_t d0 = drow + 4u * (uint32_t)(2 * (lane & 3) - (lane >> 2) - 32 * qd + 127 - 24);
+#pragma unroll
+  for (int i = 0; i < G + 3; ++i)
+#pragma unroll
+    for (int e = 0; e < 2; ++e)  // |sum| < 2^22: adding 1.5 * 2^23 leaves it in the low mantissa bits
+      red_shared_s32(d0 + 4u * (uint32_t)(8 * i + e), __float_as_int(acc[e][i] + 12582912.0f) - 0x4B400000);
 }
 
 // Named barrier of the epilogue's 256 threads.
@@ -382,7 +426,7 @@ __global__ void __launch_bounds__(kPpThreads, 1)
     uint32_t xl = 0, yl = 0;
     auto load_x = [&](int row, int sig) -> bool {
       if ((li++ & 3) == lane) {
-        if (xl > 0 && !mbar_wait(xempty + 8 * xs, (xl - 1) & 1u)) return false;
+        if (xl > 0 && !mbar_wait_sleep(xempty + 8 * xs, (xl - 1) & 1u)) return false;
         const uint32_t fb = xfull + 8 * xs;
         mbar_expect_tx_win(fb, kPpHalfBytes);
         tma_load3(xbuf + (uint32_t)(xs * kPpHalfBytes), &xmap, 0, row, sig, fb);
@@ -392,7 +436,7 @@ __global__ void __launch_bounds__(kPpThreads, 1)
     };
     auto load_y = [&](int row, int sig) -> bool {
       if ((li++ & 3) == lane) {
-        if (yl > 0 && !mbar_wait(yempty + 8 * ys, (yl - 1) & 1u)) return false;
+        if (yl > 0 && !mbar_wait_sleep(yempty + 8 * ys, (yl - 1) & 1u)) return false;
         const uint32_t fb = yfull + 8 * ys;
         mbar_expect_tx_win(fb, ys == 0 ? kPpUnitBytes + kPpMirrorRows * 128 : kPpUnitBytes);
         tma_load3(ybuf + (uint32_t)(ys * kPpUnitBytes), &ymap, 0, row, sig, fb);
@@ -406,7 +450,7 @@ __global__ void __launch_bounds__(kPpThreads, 1)
       PpVisit& V = plans[ps];
       int more = 1;
       if (lane == 0) {
-        if (v >= kPpPlans && !mbar_wait(plan_empty + 8 * ps, (uint32_t)(((v / kPpPlans) - 1) & 1))) {
+        if (v >= kPpPlans && !mbar_wait_sleep(plan_empty + 8 * ps, (uint32_t)(((v / kPpPlans) - 1) & 1))) {
           ok = false;
         } else {
           more = R.next(V) ? 1 : 0;
@@ -446,74 +490,76 @@ __global__ void __launch_bounds__(kPpThreads, 1)
       for (int i = 0; i < kPpYUnits; ++i) yfills[i] = (int)yl + (i < ys ? 1 : 0);
     }
   } else if (warp == 0) {
-    // ---- MMAs (lane 0 issues; the warp waits converged).  Ring slots and
-    // phases advance incrementally: no division in the loops.
-    bool ok = true;
-    int64_t jc = 0;  // jobs issued
-    const uint64_t da0 = sdesc(xbuf, 128u, 1024u, 2u, 0u), db0 = sdesc(ybuf, 128u, 1024u, 2u, 0u);
-    constexpr int kTilesPerHalf = kPpHalfRows / kPpTileRows;
-    for (long long v = 0; ok && !*abort_flag; ++v) {
-      const int ps = (int)(v % kPpPlans);
-      if (!warp_wait(plan_full + 8 * ps, (uint32_t)((v / kPpPlans) & 1))) {
-        ok = false;
-        break;
-      }
-      const PpVisit& V = plans[ps];
-      const int nj = V.nj, tiles = V.tiles, ng = V.ng;
-      if (nj == 0) break;
-      // the visit's x halves: slots and fill phases
-      const int xs0 = (int)(V.xh % kPpXHalves), xs1 = xs0 + 1 == kPpXHalves ? 0 : xs0 + 1;
-      const uint32_t xp0 = (uint32_t)((V.xh / kPpXHalves) & 1), xp1 = xs1 == 0 ? xp0 ^ 1u : xp0;
-      const uint32_t xa0 = (uint32_t)(xs0 * kPpHalfBytes), xa1 = (uint32_t)(xs1 * kPpHalfBytes);
-      for (int g = 0; g < ng && ok; ++g) {
-        const int gb = V.gbeg[g], ge = V.gbeg[g + 1], ufirst = V.u[gb], gun = V.gun[g];
-        const int gys = (int)(V.gyu[g] % kPpYUnits);                  // slot of the group's unit 0
-        const uint32_t gyp = (uint32_t)((V.gyu[g] / kPpYUnits) & 1);  // and its fill phase
-        int ywaited = -1;               // group units known loaded
-        int wys = gys;                  // slot and phase of unit ywaited + 1
-        uint32_t wyp = gyp;
-        int freed = 0, fys = gys;       // group units released; slot of unit freed
-        const int yrow0 = gys * kPpUnitRows;  // ring row of the group's row 0
-        for (int kk = gb; kk < ge && ok; ++kk, ++jc) {
-          const int nb = V.nb[kk], urel = V.u[kk] - ufirst;
-          const bool last_visit = kk == nj - 1, last_group = kk == ge - 1, first_job = kk == 0;
-          const int jb = (int)(jc & 1);
-          if (jc >= 2 && !warp_wait(acce + 8 * jb, (uint32_t)(((jc >> 1) - 1) & 1))) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t d = tmem + 256u * (uint32_t)jb;
-          const uint32_t idesc = pp_idesc(nb);
-          int row = yrow0 + urel;  // ring row of this job's tile 0
-          if (row >= kPpYRows) row -= kPpYRows;
-          uint64_t db = db0 + (uint64_t)(row * 8);
-          // the K tiles in batches of one x half: waits before a batch,
-          // releases after it, the batch's MMAs back to back
-          for (int h = 0, t0 = 0; t0 < tiles; ++h, t0 += kTilesPerHalf) {
-            const int t1 = t0 + kTilesPerHalf < tiles ? t0 + kTilesPerHalf : tiles;
-            bool waited = false;
-            if (first_job) {
-              if (!warp_wait(xfull + 8 * (h ? xs1 : xs0), h ? xp1 : xp0)) {
-                ok = false;
-                break;
-              }
-              waited = true;
+    // ---- MMAs: lane 0 alone (its waits are its own; no warp-wide exchange
+    // sits between the MMAs).  Ring slots and phases advance incrementally:
+    // no division in the loops.
+    if (lane == 0) {
+      bool ok = true;
+      int64_t jc = 0;  // jobs issued
+      const uint64_t da0 = sdesc(xbuf, 128u, 1024u, 2u, 0u), db0 = sdesc(ybuf, 128u, 1024u, 2u, 0u);
+      constexpr int kTilesPerHalf = kPpHalfRows / kPpTileRows;
+      auto wait = [&](uint32_t bar, uint32_t parity) { return mbar_try(bar, parity) || mbar_wait_sleep(bar, parity); };
+      for (long long v = 0; ok && !*abort_flag; ++v) {
+        const int ps = (int)(v % kPpPlans);
+        if (!wait(plan_full + 8 * ps, (uint32_t)((v / kPpPlans) & 1))) {
+          ok = false;
+          break;
+        }
+        const PpVisit& V = plans[ps];
+        const int nj = V.nj, tiles = V.tiles, ng = V.ng;
+        if (nj == 0) break;
+        // the visit's x halves: slots and fill phases
+        const int xs0 = (int)(V.xh % kPpXHalves), xs1 = xs0 + 1 == kPpXHalves ? 0 : xs0 + 1;
+        const uint32_t xp0 = (uint32_t)((V.xh / kPpXHalves) & 1), xp1 = xs1 == 0 ? xp0 ^ 1u : xp0;
+        const uint32_t xa0 = (uint32_t)(xs0 * kPpHalfBytes), xa1 = (uint32_t)(xs1 * kPpHalfBytes);
+        for (int g = 0; g < ng && ok; ++g) {
+          const int gb = V.gbeg[g], ge = V.gbeg[g + 1], ufirst = V.u[gb], gun = V.gun[g];
+          const int gys = (int)(V.gyu[g] % kPpYUnits);                  // slot of the group's unit 0
+          const uint32_t gyp = (uint32_t)((V.gyu[g] / kPpYUnits) & 1);  // and its fill phase
+          int ywaited = -1;               // group units known loaded
+          int wys = gys;                  // slot and phase of unit ywaited + 1
+          uint32_t wyp = gyp;
+          int freed = 0, fys = gys;       // group units released; slot of unit freed
+          const int yrow0 = gys * kPpUnitRows;  // ring row of the group's row 0
+          for (int kk = gb; kk < ge && ok; ++kk, ++jc) {
+            const int nb = V.nb[kk], urel = V.u[kk] - ufirst;
+            const bool last_visit = kk == nj - 1, last_group = kk == ge - 1, first_job = kk == 0;
+            const int jb = (int)(jc & 1);
+            if (jc >= 2 && !wait(acce + 8 * jb, (uint32_t)(((jc >> 1) - 1) & 1))) {
+              ok = false;
+              break;
             }
-            // tile t reads group rows urel + 32 t .. urel + 32 t + 32 + nb - 2
-            const int need = (urel + kPpTileRows * t1 + nb - 2) / kPpUnitRows;
-            while (ywaited < need) {
-              if (!warp_wait(yfull + 8 * wys, wyp)) {
-                ok = false;
-                break;
+            tc_fence_after();
+            const uint32_t d = tmem + 256u * (uint32_t)jb;
+            const uint32_t idesc = pp_idesc(nb);
+            int row = yrow0 + urel;  // ring row of this job's tile 0
+            if (row >= kPpYRows) row -= kPpYRows;
+            uint64_t db = db0 + (uint64_t)(row * 8);
+            // the K tiles in batches of one x half: waits before a batch,
+            // releases after it, the batch's MMAs back to back
+            for (int h = 0, t0 = 0; t0 < tiles; ++h, t0 += kTilesPerHalf) {
+              const int t1 = t0 + kTilesPerHalf < tiles ? t0 + kTilesPerHalf : tiles;
+              bool waited = false;
+              if (first_job) {
+                if (!wait(xfull + 8 * (h ? xs1 : xs0), h ? xp1 : xp0)) {
+                  ok = false;
+                  break;
+                }
+                waited = true;
               }
-              ++ywaited;
-              if (++wys == kPpYUnits) wys = 0, wyp ^= 1u;
-              waited = true;
-            }
-            if (!ok) break;
-            if (waited) tc_fence_after();
-            if (lane == 0) {
+              // tile t reads group rows urel + 32 t .. urel + 32 t + 32 + nb - 2
+              const int need = (urel + kPpTileRows * t1 + nb - 2) / kPpUnitRows;
+              while (ywaited < need) {
+                if (!wait(yfull + 8 * wys, wyp)) {
+                  ok = false;
+                  break;
+                }
+                ++ywaited;
+                if (++wys == kPpYUnits) wys = 0, wyp ^= 1u;
+                waited = true;
+              }
+              if (!ok) break;
+              if (waited) tc_fence_after();
               uint64_t da = da0 + ((h ? xa1 : xa0) >> 4);
               for (int t = t0; t < t1; ++t) {
                 pp_mma(d, da, db, idesc, t > 0 ? 1u : 0u);
@@ -532,28 +578,20 @@ __global__ void __launch_bounds__(kPpThreads, 1)
                 }
               }
             }
-            row = __shfl_sync(0xffffffffu, row, 0);
-            db = __shfl_sync(0xffffffffu, db, 0);
-            freed = __shfl_sync(0xffffffffu, freed, 0);
-            fys = __shfl_sync(0xffffffffu, fys, 0);
-            __syncwarp();
+            if (!ok) break;
+            mma_commit(accf + 8 * jb);
           }
-          if (!ok) break;
-          if (lane == 0) mma_commit(accf + 8 * jb);
-          __syncwarp();
         }
+        mbar_arrive(plan_empty + 8 * ps);  // the issuer is done with the plan
       }
-      if (lane == 0) mbar_arrive(plan_empty + 8 * ps);  // the issuer is done with the plan
-      __syncwarp();
+      if (!ok) *abort_flag = 1;
+      mma_commit(done_bar);
     }
-    if (!ok) *abort_flag = 1;
-    if (lane == 0) mma_commit(done_bar);
     __syncwarp();
   } else {
     // ---- epilogue (warps 2-9): TMEM lanes 32 (warp & 3) .., column half h
     const int qd = warp & 3, h = (warp - 2) >> 2;
     const int e = tid - 64;  // 0 .. 255
-    const int b = 32 * qd + lane;
     int64_t jc = 0;
     bool ok = true;
     for (long long v = 0; ok && !*abort_flag; ++v) {
@@ -589,22 +627,11 @@ __global__ void __launch_bounds__(kPpThreads, 1)
         tc_fence_after();
         // block h (two blocks) or columns 64 h .. (one block) of this warp's
         // lanes: value D[b][j] to diagonal j - b + 127 of its block's slot
-        const int blk = nb == 2 ? h : 0;
-        const int c0 = nb == 2 ? 128 * h : 64 * h, ncol = nb == 2 ? 128 : 64;
-        const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + 256u * (uint32_t)jb;
-        const uint32_t arow = diag_s + 4u * (uint32_t)(256 * (slot + blk) + 127 - b);
-        for (int cc = 0; cc < ncol; cc += 64) {
-          uint32_t r[64];
-          tmem_ld32_nowait(tbase + (uint32_t)(c0 + cc), r);
-          tmem_ld32_nowait(tbase + (uint32_t)(c0 + cc + 32), r + 32);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const int j0 = (nb == 2 ? 0 : c0) + cc;  // column within the block
-          // |D| < 2^22: adding 1.5 * 2^23 leaves D in the low mantissa bits
-#pragma unroll
-          for (int i = 0; i < 64; ++i)
-            red_shared_s32(arow + 4u * (uint32_t)(j0 + i),
-                           __float_as_int(__uint_as_float(r[i]) + 12582912.0f) - 0x4B400000);
-        }
+        const uint32_t tcol = tmem + ((uint32_t)(32 * qd) << 16) + 256u * (uint32_t)jb;
+        if (nb == 2)  // block h: its 128 columns
+          pp_drain<128>(tcol + 128u * (uint32_t)h, qd, lane, diag_s + 4u * (uint32_t)(256 * (slot + h)));
+        else  // columns 64 h .. 64 h + 63 of the one block
+          pp_drain<64>(tcol + 64u * (uint32_t)h, qd, lane, diag_s + 4u * (uint32_t)(256 * slot + 64 * h));
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce + 8 * jb);

@@ -308,3 +308,49 @@ def test_polyphase_arithmetic_equals_direct_correlation():
                 want = full[np.arange(lo, hi + 1) + n - 1]
                 assert np.array_equal(o[:hi - lo + 1], want)
                 assert not o[hi - lo + 1:].any()
+
+
+def _drain_16x256b(D, qd, h, cols):
+    """The epilogue's drain of one warp's share as pp_drain does it: lanes
+    32 qd .. + 31, `cols` columns from 64 h (one block) or the whole block
+    (cols = 128); thread t holds rows 32 qd + t // 4 + 8 k and columns
+    8 g + 2 (t % 4) + e, sums each chain of equal g - k and adds it at
+    diagonal index 8 s + e + 2 (t % 4) - t // 4 - 32 qd + 127 (+ 64 h)."""
+    G = cols // 8
+    c0 = 64 * h if cols == 64 else 0
+    out = np.zeros(256, np.int64)
+    seen = np.zeros((128, 128), np.int64)
+    for t in range(32):
+        r, m = t // 4, t % 4
+        acc = np.zeros((2, G + 3), np.int64)
+        for k in range(4):
+            for g in range(G):
+                for e in range(2):
+                    b, j = 32 * qd + r + 8 * k, c0 + 8 * g + 2 * m + e
+                    acc[e, g - k + 3] += D[b, j]
+                    seen[b, j] += 1
+        for i in range(G + 3):
+            for e in range(2):
+                idx = 8 * (i - 3) + e + 2 * m - r - 32 * qd + 127 + c0
+                assert 0 <= idx <= 254
+                out[idx] += acc[e, i]
+    return out, seen
+
+
+def test_epilogue_chains_sum_every_value_on_its_diagonal():
+    rng = np.random.default_rng(5)
+    D = rng.integers(-1000, 1000, (128, 128))
+    want = np.zeros(256, np.int64)
+    for b in range(128):
+        for j in range(128):
+            want[j - b + 127] += D[b, j]
+    for cols, halves in ((128, (0,)), (64, (0, 1))):
+        got = np.zeros(256, np.int64)
+        seen = np.zeros((128, 128), np.int64)
+        for qd in range(4):
+            for h in halves:
+                o, sn = _drain_16x256b(D, qd, h, cols)
+                got += o
+                seen += sn
+        assert (seen == 1).all()  # every value read once
+        assert np.array_equal(got, want)
