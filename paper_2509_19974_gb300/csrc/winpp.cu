@@ -39,10 +39,10 @@
 // scans all pairs' job counts (written with the windows) to find its run.  Within a run, a visit is the run's
 // jobs of one (pair, segment): its x rows are loaded once, as one or two
 // halves of 256 rows, and its y rows once per group of jobs whose rows fit
-// the y ring, as units of 64 rows.  Roles (10 warps):
+// the y ring, as units of 64 rows.  Roles (11 warps):
 //   warp 1:          lane 0 plans each visit (jobs, groups, block slots) into
 //                    a ring of 4 plans the other roles read; lanes 0-3 issue
-//                    the TMA loads, load i of a visit by lane i % 4 (one
+//                    the TMA loads, slot s of a ring by lane s % 4 (one
 //                    thread issues a tiled load in about 600 cycles).  x
 //                    halves go to a ring of 3, y units to a ring of 11 (the
 //                    first 32 rows of unit slot 0 mirrored past the end, so an
@@ -50,8 +50,9 @@
 //                    once the last MMA that reads it has completed (an
 //                    "empty" barrier committed by the issuer), so the next
 //                    visit's loads overlap this visit's MMAs.
-//   warp 0:          MMAs (lane 0), one per K tile of a job, into one of two
-//                    256-column accumulators (double-buffered across jobs).
+//   warps 0, 10:     MMAs (lane 0 of each), one per K tile of a job, the two
+//                    issuers taking alternate jobs, each into its own
+//                    256-column accumulator; a slot's release takes both.
 //   warps 2-9:       epilogue: a warp reads 32 lanes x 128 (or 64) columns of
 //                    the finished accumulator, converts to int32 and adds each
 //                    value to its block's diagonal with a shared-memory
@@ -68,7 +69,8 @@
 
 namespace {
 
-constexpr int kPpThreads = 320;                   // 10 warps
+constexpr int kPpThreads = 352;                   // 11 warps
+constexpr int kPpIssuerB = 10;                    // the second MMA warp
 constexpr int kPpSegRows = 512;                   // rows summed per accumulator
 constexpr int kPpTileRows = 32;                   // K rows per MMA (E4M3: K = 32)
 constexpr int kPpHalfRows = 256;                  // x rows per load (and per release)
@@ -395,11 +397,12 @@ __global__ void __launch_bounds__(kPpThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int i = 0; i < kPpXHalves; ++i) mbar_init(xfull + 8 * i, 1), mbar_init(xempty + 8 * i, 1);
-    for (int i = 0; i < kPpYUnits; ++i) mbar_init(yfull + 8 * i, 1), mbar_init(yempty + 8 * i, 1);
+    // a slot is released by both issuers (each after its last MMA reading it)
+    for (int i = 0; i < kPpXHalves; ++i) mbar_init(xfull + 8 * i, 1), mbar_init(xempty + 8 * i, 2);
+    for (int i = 0; i < kPpYUnits; ++i) mbar_init(yfull + 8 * i, 1), mbar_init(yempty + 8 * i, 2);
     for (int i = 0; i < 2; ++i) mbar_init(accf + 8 * i, 1), mbar_init(acce + 8 * i, kPpEpi / 32);
-    mbar_init(done_bar, 1);
-    for (int i = 0; i < kPpPlans; ++i) mbar_init(plan_full + 8 * i, 1), mbar_init(plan_empty + 8 * i, 2);
+    mbar_init(done_bar, 2);
+    for (int i = 0; i < kPpPlans; ++i) mbar_init(plan_full + 8 * i, 1), mbar_init(plan_empty + 8 * i, 3);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < kPpMaxBlocks * 256; i += kPpThreads) diag[i] = 0;
@@ -410,8 +413,9 @@ __global__ void __launch_bounds__(kPpThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 1) {
-    // ---- the plans (lane 0) and the TMA loads (lanes 0-3, load i of a visit
-    // by lane i % 4)
+    // ---- the plans (lane 0) and the TMA loads (lanes 0-3: slot s of each
+    // ring by lane s % 4, so a slot's fills are issued in order and a lap's
+    // empty-barrier wait can never see a phase two behind)
     PpRun R;
     if (lane == 0) {
       R.init(jobs, nseg, rows_total, p0, off0, J1 - J0);
@@ -422,10 +426,10 @@ __global__ void __launch_bounds__(kPpThreads, 1)
     bool ok = true;
     // x half i goes to slot xs (lap xl), y unit i to slot ys (lap yl); a
     // slot's lap l >= 1 waits for the release of lap l - 1
-    int xs = 0, ys = 0, li = 0;
+    int xs = 0, ys = 0;
     uint32_t xl = 0, yl = 0;
     auto load_x = [&](int row, int sig) -> bool {
-      if ((li++ & 3) == lane) {
+      if ((xs & 3) == lane) {
         if (xl > 0 && !mbar_wait_sleep(xempty + 8 * xs, (xl - 1) & 1u)) return false;
         const uint32_t fb = xfull + 8 * xs;
         mbar_expect_tx_win(fb, kPpHalfBytes);
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(kPpThreads, 1)
       return true;
     };
     auto load_y = [&](int row, int sig) -> bool {
-      if ((li++ & 3) == lane) {
+      if ((ys & 3) == lane) {
         if (yl > 0 && !mbar_wait_sleep(yempty + 8 * ys, (yl - 1) & 1u)) return false;
         const uint32_t fb = yfull + 8 * ys;
         mbar_expect_tx_win(fb, ys == 0 ? kPpUnitBytes + kPpMirrorRows * 128 : kPpUnitBytes);
@@ -489,16 +493,22 @@ __global__ void __launch_bounds__(kPpThreads, 1)
       for (int i = 0; i < kPpXHalves; ++i) xfills[i] = (int)xl + (i < xs ? 1 : 0);
       for (int i = 0; i < kPpYUnits; ++i) yfills[i] = (int)yl + (i < ys ? 1 : 0);
     }
-  } else if (warp == 0) {
-    // ---- MMAs: lane 0 alone (its waits are its own; no warp-wide exchange
-    // sits between the MMAs).  Ring slots and phases advance incrementally:
-    // no division in the loops.
+  } else if (warp == 0 || warp == kPpIssuerB) {
+    // ---- MMAs: two issuers (lane 0 of warps 0 and kPpIssuerB) take
+    // alternate jobs, each into its own accumulator, so that one thread's
+    // issue cost (about 65 cycles per MMA plus its loop) has twice the
+    // tensor pipe's time per MMA.  A slot's release takes both: the issuer of
+    // the last job that reads it commits after that job's batch, the other
+    // after its own last job of the group (y) or visit (x).  Ring slots and
+    // phases advance incrementally: no division in the loops.
     if (lane == 0) {
+      const int me = warp == 0 ? 0 : 1;
       bool ok = true;
-      int64_t jc = 0;  // jobs issued
+      int64_t jc = 0;  // jobs walked (both issuers'); this issuer's are those with jc % 2 == me
       const uint64_t da0 = sdesc(xbuf, 128u, 1024u, 2u, 0u), db0 = sdesc(ybuf, 128u, 1024u, 2u, 0u);
       constexpr int kTilesPerHalf = kPpHalfRows / kPpTileRows;
       auto wait = [&](uint32_t bar, uint32_t parity) { return mbar_try(bar, parity) || mbar_wait_sleep(bar, parity); };
+      const uint32_t d = tmem + 256u * (uint32_t)me;  // this issuer's accumulator
       for (long long v = 0; ok && !*abort_flag; ++v) {
         const int ps = (int)(v % kPpPlans);
         if (!wait(plan_full + 8 * ps, (uint32_t)((v / kPpPlans) & 1))) {
@@ -509,9 +519,12 @@ __global__ void __launch_bounds__(kPpThreads, 1)
         const int nj = V.nj, tiles = V.tiles, ng = V.ng;
         if (nj == 0) break;
         // the visit's x halves: slots and fill phases
+        const int nh = (tiles + kTilesPerHalf - 1) / kTilesPerHalf;
         const int xs0 = (int)(V.xh % kPpXHalves), xs1 = xs0 + 1 == kPpXHalves ? 0 : xs0 + 1;
         const uint32_t xp0 = (uint32_t)((V.xh / kPpXHalves) & 1), xp1 = xs1 == 0 ? xp0 ^ 1u : xp0;
         const uint32_t xa0 = (uint32_t)(xs0 * kPpHalfBytes), xa1 = (uint32_t)(xs1 * kPpHalfBytes);
+        const int vlast = (int)((jc + nj - 1) & 1);  // the issuer of the visit's last job
+        bool xwaited = false;
         for (int g = 0; g < ng && ok; ++g) {
           const int gb = V.gbeg[g], ge = V.gbeg[g + 1], ufirst = V.u[gb], gun = V.gun[g];
           const int gys = (int)(V.gyu[g] % kPpYUnits);                  // slot of the group's unit 0
@@ -521,30 +534,47 @@ __global__ void __launch_bounds__(kPpThreads, 1)
           uint32_t wyp = gyp;
           int freed = 0, fys = gys;       // group units released; slot of unit freed
           const int yrow0 = gys * kPpUnitRows;  // ring row of the group's row 0
+          const int64_t jg = jc + (ge - gb);    // jc after the group
+          const int glast = (int)((jg - 1) & 1);  // the issuer of the group's last job
           for (int kk = gb; kk < ge && ok; ++kk, ++jc) {
+            if ((int)(jc & 1) != me) continue;
             const int nb = V.nb[kk], urel = V.u[kk] - ufirst;
-            const bool last_visit = kk == nj - 1, last_group = kk == ge - 1, first_job = kk == 0;
-            const int jb = (int)(jc & 1);
-            if (jc >= 2 && !wait(acce + 8 * jb, (uint32_t)(((jc >> 1) - 1) & 1))) {
+            const bool last_visit = kk == nj - 1, last_group = kk == ge - 1;
+            const int64_t mine = jc >> 1;  // this issuer's job count
+            if (mine >= 1 && !wait(acce + 8 * me, (uint32_t)((mine - 1) & 1))) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t d = tmem + 256u * (uint32_t)jb;
             const uint32_t idesc = pp_idesc(nb);
             int row = yrow0 + urel;  // ring row of this job's tile 0
             if (row >= kPpYRows) row -= kPpYRows;
             uint64_t db = db0 + (uint64_t)(row * 8);
+            if (xwaited && !last_visit && !last_group &&
+                (urel + kPpTileRows * tiles + nb - 2) / kPpUnitRows <= ywaited) {
+              // every operand is loaded and no slot is released: one run of MMAs
+              uint64_t da = da0 + (xa0 >> 4);
+              for (int t = 0; t < tiles; ++t) {
+                pp_mma(d, da, db, idesc, t > 0 ? 1u : 0u);
+                da = t == kTilesPerHalf - 1 ? da0 + (xa1 >> 4) : da + (kPpTileRows * 128 >> 4);
+                db += kPpTileRows * 128 >> 4;
+                row += kPpTileRows;
+                if (row >= kPpYRows) row -= kPpYRows, db -= kPpYRows * 128 >> 4;
+              }
+              mma_commit(accf + 8 * me);
+              continue;
+            }
             // the K tiles in batches of one x half: waits before a batch,
             // releases after it, the batch's MMAs back to back
             for (int h = 0, t0 = 0; t0 < tiles; ++h, t0 += kTilesPerHalf) {
               const int t1 = t0 + kTilesPerHalf < tiles ? t0 + kTilesPerHalf : tiles;
               bool waited = false;
-              if (first_job) {
+              if (!xwaited) {
                 if (!wait(xfull + 8 * (h ? xs1 : xs0), h ? xp1 : xp0)) {
                   ok = false;
                   break;
                 }
+                if (t1 == tiles) xwaited = true;
                 waited = true;
               }
               // tile t reads group rows urel + 32 t .. urel + 32 t + 32 + nb - 2
@@ -579,16 +609,35 @@ __global__ void __launch_bounds__(kPpThreads, 1)
               }
             }
             if (!ok) break;
-            mma_commit(accf + 8 * jb);
+            mma_commit(accf + 8 * me);
+          }
+          // the other issuer's share of the group's releases: after its own
+          // last MMAs of the group (all of them precede the commit), and only
+          // once the group's units are loaded, so that no release runs ahead
+          // of the fill it answers
+          if (ok && glast != me) {
+            while (ok && ywaited < gun - 1) {
+              ok = wait(yfull + 8 * wys, wyp);
+              ++ywaited;
+              if (++wys == kPpYUnits) wys = 0, wyp ^= 1u;
+            }
+            for (int i = 0, sl = gys; ok && i < gun; ++i) {
+              mma_commit(yempty + 8 * sl);
+              if (++sl == kPpYUnits) sl = 0;
+            }
           }
         }
-        mbar_arrive(plan_empty + 8 * ps);  // the issuer is done with the plan
+        if (ok && vlast != me) {  // and of the visit's x halves
+          for (int h = 0; ok && !xwaited && h < nh; ++h) ok = wait(xfull + 8 * (h ? xs1 : xs0), h ? xp1 : xp0);
+          for (int h = 0; ok && h < nh; ++h) mma_commit(xempty + 8 * (h ? xs1 : xs0));
+        }
+        mbar_arrive(plan_empty + 8 * ps);  // this issuer is done with the plan
       }
       if (!ok) *abort_flag = 1;
       mma_commit(done_bar);
     }
     __syncwarp();
-  } else {
+  } else if (warp >= 2 && warp < 10) {
     // ---- epilogue (warps 2-9): TMEM lanes 32 (warp & 3) .., column half h
     const int qd = warp & 3, h = (warp - 2) >> 2;
     const int e = tid - 64;  // 0 .. 255

@@ -73,105 +73,183 @@ def visits(plans, nseg, rows_total, J0, J1):
         yield p, s, tiles, groups
 
 
-def simulate(plans, nseg, rows_total, J0, J1, lanes=4):
-    """Runs the TMA role (load i of a visit by lane i % lanes, each lane in
-    order) and the MMA role as the kernel orders them: a load into a slot's
-    lap L waits for the release of lap L - 1; an MMA waits for the loads it
-    reads; releases follow the kernel's rules.  Checks that the run
-    finishes (no circular wait) and that every MMA finds in its x half and
-    y rows (through the mirror past the ring's end) the data it expects."""
+class _Bar:
+    """An mbarrier: `count` arrivals complete a phase; a wait for parity p
+    passes once the phase counter's parity differs from p."""
+
+    def __init__(self, count):
+        self.count, self.pending, self.phase = count, 0, 0
+
+    def arrive(self):
+        self.pending += 1
+        if self.pending == self.count:
+            self.pending, self.phase = 0, self.phase + 1
+
+    def ready(self, parity):
+        return (self.phase & 1) != parity
+
+
+def simulate(plans, nseg, rows_total, J0, J1, lanes=4, seed=0, by_slot=True):
+    """Runs the kernel's TMA role (a slot's loads by lane slot % lanes) and its
+    two MMA issuers (alternate jobs; a slot released by both: the last job's
+    issuer after each batch, the other after its own last job of the group or
+    visit, once the group's units or visit's halves are loaded) in a random
+    interleaving, with the slots' full and empty barriers modelled as
+    mbarriers (waits by parity).  Checks that the run finishes (no circular
+    wait, no barrier lapped) and that every MMA finds in its x half and y rows
+    (through the mirror past the ring's end) the data it expects."""
+    rng = random.Random(seed)
     V = list(visits(plans, nseg, rows_total, J0, J1))
-    loads = []  # ('x', logical half, (p, first row)) / ('y', logical unit, (p, first row))
-    xh = 0
+    tph = HALF_ROWS // TILE_ROWS
+    # ---- the TMA role's loads, as in the kernel
+    loads = []  # ('x', slot, lap, (p, first row)) / ('y', ...)
+    xh = yu = 0
     for p, s, tiles, groups in V:
         nh = -(-tiles * TILE_ROWS // HALF_ROWS)
         rowbase = s * SEG_ROWS
-        for gi, (yu, gun, jl) in enumerate(groups):
+        for gi, (gyu, gun, jl) in enumerate(groups):
             ubase = rowbase + jl[0][0]
             c = 0
             if gi == 0:
                 for h in range(nh):
-                    loads.append(('x', xh + h, (p, rowbase + HALF_ROWS * h)))
+                    loads.append(('x', (xh + h) % X_HALVES, (xh + h) // X_HALVES, (p, rowbase + HALF_ROWS * h)))
                     need = (HALF_ROWS * (h + 1) + TILE_ROWS) // UNIT_ROWS
                     while c < gun and c <= need:
-                        loads.append(('y', yu + c, (p, ubase + UNIT_ROWS * c)))
+                        loads.append(('y', (gyu + c) % Y_UNITS, (gyu + c) // Y_UNITS, (p, ubase + UNIT_ROWS * c)))
                         c += 1
             while c < gun:
-                loads.append(('y', yu + c, (p, ubase + UNIT_ROWS * c)))
+                loads.append(('y', (gyu + c) % Y_UNITS, (gyu + c) // Y_UNITS, (p, ubase + UNIT_ROWS * c)))
                 c += 1
         xh += nh
-    mmas = []
+    # ---- each issuer's program: ('wait', kind, slot, parity) / ('mma', ...) / ('rel', kind, slot)
+    progs = [[], []]
+    jc = 0
     xh = 0
+    nmma = 0
     for p, s, tiles, groups in V:
         nh = -(-tiles * TILE_ROWS // HALF_ROWS)
-        tph = HALF_ROWS // TILE_ROWS
-        for gi, (yu, gun, jl) in enumerate(groups):
-            freed = yu
+        nj = sum(len(jl) for _, _, jl in groups)
+        vlast = (jc + nj - 1) & 1
+        xwaited = [False, False]
+        for gi, (gyu, gun, jl) in enumerate(groups):
+            glast = (jc + len(jl) - 1) & 1
+            ywaited = [-1, -1]
+            freed = 0
             for k, (u, nb) in enumerate(jl):
+                me = jc & 1
+                prog = progs[me]
                 urel = u - jl[0][0]
                 last_visit = gi == len(groups) - 1 and k == len(jl) - 1
                 last_group = k == len(jl) - 1
-                for t in range(tiles):
-                    # K tiles in batches of one x half: the batch's waits before
-                    # its first tile, its releases after its last
-                    hh = xh + t // tph
-                    t1 = min(tiles, (t // tph + 1) * tph)
-                    need_y = yu + (urel + TILE_ROWS * t1 + nb - 2) // UNIT_ROWS
-                    rel = []
-                    if t + 1 == t1:
-                        if last_visit:
-                            rel.append(('x', hh))
-                        if last_group:
-                            upto = yu + gun if t1 == tiles else yu + (urel + TILE_ROWS * t1) // UNIT_ROWS
-                            while freed < upto:
-                                rel.append(('y', freed))
-                                freed += 1
-                    want_x = [(p, s * SEG_ROWS + TILE_ROWS * t + r) for r in range(TILE_ROWS)]
-                    want_y = [(p, s * SEG_ROWS + u + TILE_ROWS * t + r) for r in range(TILE_ROWS + nb - 1)]
-                    pos = UNIT_ROWS * yu + urel + TILE_ROWS * t  # logical y row of the tile's first row
-                    mmas.append((hh, t % tph, need_y, rel, want_x, pos, want_y))
+                for h in range(nh):
+                    t0, t1 = tph * h, min(tiles, tph * (h + 1))
+                    if not xwaited[me]:
+                        prog.append(('wait', 'x', (xh + h) % X_HALVES, ((xh + h) // X_HALVES) & 1))
+                        if t1 == tiles:
+                            xwaited[me] = True
+                    need = (urel + TILE_ROWS * t1 + nb - 2) // UNIT_ROWS
+                    while ywaited[me] < need:
+                        ywaited[me] += 1
+                        U = gyu + ywaited[me]
+                        prog.append(('wait', 'y', U % Y_UNITS, (U // Y_UNITS) & 1))
+                    for t in range(t0, t1):
+                        want_x = [(p, s * SEG_ROWS + TILE_ROWS * t + r) for r in range(TILE_ROWS)]
+                        want_y = [(p, s * SEG_ROWS + u + TILE_ROWS * t + r) for r in range(TILE_ROWS + nb - 1)]
+                        pos = UNIT_ROWS * gyu + urel + TILE_ROWS * t
+                        prog.append(('mma', (xh + h) % X_HALVES, t - t0, want_x, pos, want_y))
+                        nmma += 1
+                    if last_visit:
+                        prog.append(('rel', 'x', (xh + h) % X_HALVES))
+                    if last_group:
+                        upto = gun if t1 == tiles else (urel + TILE_ROWS * t1) // UNIT_ROWS
+                        while freed < upto:
+                            prog.append(('rel', 'y', (gyu + freed) % Y_UNITS))
+                            freed += 1
+                jc += 1
+            other = 1 - glast
+            while ywaited[other] < gun - 1:
+                ywaited[other] += 1
+                U = gyu + ywaited[other]
+                progs[other].append(('wait', 'y', U % Y_UNITS, (U // Y_UNITS) & 1))
+            for i in range(gun):
+                progs[other].append(('rel', 'y', (gyu + i) % Y_UNITS))
+        other = 1 - vlast
+        for h in range(nh):
+            if not xwaited[other]:
+                progs[other].append(('wait', 'x', (xh + h) % X_HALVES, ((xh + h) // X_HALVES) & 1))
+        for h in range(nh):
+            progs[other].append(('rel', 'x', (xh + h) % X_HALVES))
         xh += nh
-    filled = {'x': set(), 'y': set()}
-    released = {'x': set(), 'y': set()}
-    xrows = [[None] * HALF_ROWS for _ in range(X_HALVES)]
+    # ---- run
+    full = {'x': [_Bar(1) for _ in range(X_HALVES)], 'y': [_Bar(1) for _ in range(Y_UNITS)]}
+    empty = {'x': [_Bar(2) for _ in range(X_HALVES)], 'y': [_Bar(2) for _ in range(Y_UNITS)]}
+    xrows = [None] * X_HALVES
     yrows = [None] * (Y_UNITS * UNIT_ROWS + MIRROR_ROWS)
-    lane_loads = [[ld for i, ld in enumerate(loads) if i % lanes == l] for l in range(lanes)]
-    lp = [0] * lanes
-    mi = 0
-    while any(lp[l] < len(lane_loads[l]) for l in range(lanes)) or mi < len(mmas):
-        progressed = False
-        for l in range(lanes):
-            if lp[l] < len(lane_loads[l]):
-                kind, idx, (p, row) = lane_loads[l][lp[l]]
-                ring = X_HALVES if kind == 'x' else Y_UNITS
-                if idx < ring or (idx - ring) in released[kind]:
-                    slot = idx % ring
-                    if kind == 'x':
-                        xrows[slot] = [(p, row + r) for r in range(HALF_ROWS)]
-                    else:
-                        for r in range(UNIT_ROWS):
-                            yrows[slot * UNIT_ROWS + r] = (p, row + r)
-                        if slot == 0:
-                            for r in range(MIRROR_ROWS):
-                                yrows[Y_UNITS * UNIT_ROWS + r] = (p, row + r)
-                    filled[kind].add(idx)
-                    lp[l] += 1
-                    progressed = True
-        if mi < len(mmas):
-            hh, tin, need_y, rel, want_x, pos, want_y = mmas[mi]
-            if hh in filled['x'] and all(c in filled['y'] for c in range(need_y + 1) if c >= 0) \
-                    and all(c in filled['y'] for c in range(pos // UNIT_ROWS, need_y + 1)):
-                got_x = xrows[hh % X_HALVES][TILE_ROWS * tin:TILE_ROWS * (tin + 1)]
-                assert got_x == want_x, (mi, got_x[:2], want_x[:2])
-                phys = pos % (Y_UNITS * UNIT_ROWS)
-                got = yrows[phys:phys + len(want_y)]
-                assert got == want_y, (mi, pos, got[:3], want_y[:3])
-                for kind, idx in rel:
-                    released[kind].add(idx)
-                mi += 1
-                progressed = True
-        assert progressed, f"circular wait at loads {lp}, mma {mi}/{len(mmas)}"
-    return len(mmas)
+    if by_slot:  # slot s by lane s % lanes (the kernel's rule)
+        lane_loads = [[ld for ld in loads if ld[1] % lanes == l] for l in range(lanes)]
+    else:  # load i by lane i % lanes
+        lane_loads = [[ld for i, ld in enumerate(loads) if i % lanes == l] for l in range(lanes)]
+    pcs = {('L', l): 0 for l in range(lanes)}
+    pcs.update({('I', 0): 0, ('I', 1): 0})
+    done_mma = 0
+
+    def step(actor):
+        nonlocal done_mma
+        kind_, idx = actor
+        if kind_ == 'L':
+            q = lane_loads[idx]
+            if pcs[actor] >= len(q):
+                return False
+            kind, slot, lap, (p, row) = q[pcs[actor]]
+            if lap > 0 and not empty[kind][slot].ready((lap - 1) & 1):
+                return False
+            if kind == 'x':
+                xrows[slot] = [(p, row + r) for r in range(HALF_ROWS)]
+            else:
+                for r in range(UNIT_ROWS):
+                    yrows[slot * UNIT_ROWS + r] = (p, row + r)
+                if slot == 0:
+                    for r in range(MIRROR_ROWS):
+                        yrows[Y_UNITS * UNIT_ROWS + r] = (p, row + r)
+            full[kind][slot].arrive()
+            pcs[actor] += 1
+            return True
+        prog = progs[idx]
+        if pcs[actor] >= len(prog):
+            return False
+        op = prog[pcs[actor]]
+        if op[0] == 'wait':
+            if not full[op[1]][op[2]].ready(op[3]):
+                return False
+        elif op[0] == 'mma':
+            _, xs, tin, want_x, pos, want_y = op
+            assert xrows[xs][TILE_ROWS * tin:TILE_ROWS * (tin + 1)] == want_x
+            phys = pos % (Y_UNITS * UNIT_ROWS)
+            assert yrows[phys:phys + len(want_y)] == want_y, (pos, yrows[phys], want_y[0])
+            done_mma += 1
+        else:
+            empty[op[1]][op[2]].arrive()
+        pcs[actor] += 1
+        return True
+
+    actors = list(pcs)
+    while True:
+        live = [a for a in actors if pcs[a] < (len(lane_loads[a[1]]) if a[0] == 'L' else len(progs[a[1]]))]
+        if not live:
+            break
+        rng.shuffle(live)
+        if not any(step(a) for a in live):
+            info = []
+            for a in live:
+                if a[0] == 'L':
+                    info.append((a, lane_loads[a[1]][pcs[a]][:3]))
+                else:
+                    info.append((a, progs[a[1]][pcs[a]][:4]))
+            raise AssertionError(f"circular wait: {info} x-empty {[(b.phase, b.pending) for b in empty['x']]} "
+                                 f"y-empty {[(b.phase, b.pending) for b in empty['y']]} "
+                                 f"x-full {[b.phase for b in full['x']]} y-full {[b.phase for b in full['y']]}")
+    assert done_mma == nmma
+    return nmma
 
 
 def _windows_adjacent(n, centre_bin, rng):
@@ -211,10 +289,9 @@ def test_plan_blocks_cover_every_window_lag():
     assert sum(nb for _, nb in pl) == 17 and len(pl) == 9
 
 
-def test_rings_fill_before_read_and_release_after_last_read():
-    rng = random.Random(2)
-    cases = 0
-    for trial in range(40):
+def _ring_cases(seed, trials):
+    rng = random.Random(seed)
+    for trial in range(trials):
         n = rng.choice([65536, 65536, 4096, 3000, 100000, 140000])
         rows_total = -(-n // 128)
         nseg = -(-rows_total // SEG_ROWS)
@@ -235,8 +312,28 @@ def test_rings_fill_before_read_and_release_after_last_read():
         G = rng.choice([1, 2, 3, 7])
         for J0, J1 in _runs(J, G):
             if J1 > J0:
-                cases += simulate(plans, nseg, rows_total, J0, J1)
-    assert cases > 1000
+                yield trial, plans, nseg, rows_total, J0, J1
+
+
+def test_rings_fill_before_read_and_release_after_last_read():
+    cases = 0
+    for trial, plans, nseg, rows_total, J0, J1 in _ring_cases(2, 40):
+        for seed in range(3):  # interleavings of the loader lanes and the two issuers
+            cases += simulate(plans, nseg, rows_total, J0, J1, seed=100 * trial + seed)
+    assert cases > 3000
+
+
+def test_ring_model_catches_a_lane_lapping_its_slot():
+    # loads dealt to lanes in turn (not by slot) let one lane fill a slot's
+    # next lap before another lane's fill of the previous one: the model must
+    # see it (a wrong operand or a circular wait)
+    failures = 0
+    for trial, plans, nseg, rows_total, J0, J1 in _ring_cases(2, 40):
+        try:
+            simulate(plans, nseg, rows_total, J0, J1, seed=trial, by_slot=False)
+        except AssertionError:
+            failures += 1
+    assert failures > 0
 
 
 def _pp_windows(x, y, wins, n):
