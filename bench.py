@@ -75,7 +75,7 @@ def tensor_peak(pk, bits):
 # DRAM bytes (read + write) per launch of each form's dominant kernel, from one
 # ncu capture of this bench's workload (profiles/); keyed by (kernel, pairs,
 # N, bits).  Cleared whenever the kernel changes.
-TRAFFIC = {("k_xcorr_mma4", 256, 65536, 2): 214.2e6}
+TRAFFIC = {("k_xcorr_mma4", 256, 65536, 2): 214.2e6, ("k_xcorr_win_pp", 256, 65536, 2): 35.78e6}
 CKPT = os.path.join(ROOT, "paper_2509_19974_gb300", "models", "proposal_n65536_b2.npz")
 
 

@@ -8,7 +8,7 @@
 // 8 bins) is below a threshold, over the full lag range.
 //
 // The windows' exact correlation runs on the tensor cores
-// (launch_xcorr_mma_windows in mma.cu); this file holds their argmax.
+// (launch_xcorr_win_pp in winpp.cu); this file holds their argmax.
 //
 // Weights are BF16-rounded everywhere and every sum is FP32.  Inference runs
 // its four conv layers on tcgen05 (mma.cu: k_conv1_tc, k_conv_tc) with BF16

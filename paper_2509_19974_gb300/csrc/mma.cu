@@ -1,7 +1,8 @@
 // mma.cu -- exact integer cross-correlation (Algorithm 1's correlation step; Eq. (1) of
 // arXiv 2509.19974) as a Toeplitz-structured GEMM on the 5th-generation
 // tensor cores (tcgen05.mma, accumulators in tensor memory), and the
-// learned proposal's windows in the same form.
+// learned proposal's convolution layers on the same tensor cores.  (The
+// proposal's windows are in winpp.cu.)
 //
 // tcgen05 has no 8-bit integer kind on sm_103a, so the integer arithmetic
 // rides on kind::f8f6f4 with E4M3 operands and FP32 accumulation: the levels
@@ -389,453 +390,6 @@ __global__ void k_zero_outputs(const MmaPair* __restrict__ pairs, int npairs, co
 }
 
 
-// ---------------------------------------------------------------------------
-// Windowed form (the learned proposal's exact check), FP8 like the engine
-// above: for one pair and its 8 windows, window w's lags are covered by
-// tau = T_w + 128 j + 127 - m (j = 0..7, T_w = its first lag rounded down to
-// a multiple of 128), 1024 lags of which the window's <= 257 are kept.  A is
-// the same E4M3 Hankel slot ring; B needs no per-chunk copies: each window's
-// y segment is one array of 128-byte E4M3 rows
-//   Y_w[r] = y[ks + T_w + 128 r .. + 127],
-// and because ks and T_w are multiples of 128 the 8 B rows of window w for K
-// chunk c are rows c .. c + 7 of Y_w -- the same rows for every window, one
-// core-matrix group per window.  The windows' arrays sit at a fixed stride, so
-// one descriptor (stride byte offset = that stride) gives an N = 64 tile:
-// 8 windows x 8 columns.
-//
-// The inputs are the levels as E4M3 bytes, so a segment's operands arrive by
-// TMA: per window one 3-D tiled load (signal, 128-byte row, byte) of 32 rows
-// with the 128-byte swizzle the B descriptor expects, zero-filled outside the
-// signal, and the x segment as two loads of 112 16-byte rows.  Roles:
-//   warp 3, lane 0: TMA, two segment buffers ahead of the MMAs;
-//   warps 1-2:      Hankel slot rows, one super-chunk (2 chunks) at a time;
-//   warps 0 and 8:  MMAs (lane 0), each into its own accumulator set (K steps
-//                   0, 2 and 1, 3 of every chunk; at N = 64 one thread's issue
-//                   loop, not the tensor pipe, bounds the MMA rate), sets
-//                   double-buffered across pairs;
-//   warps 4-7:      epilogue of each finished pair (stores, or integer
-//                   atomics when the pair is split between CTAs).
-// Slot ring positions run on across segments: super-chunk S (counted over
-// the CTA's run, in segment g of the run) has origin R(S) = 32 (S + g) --
-// each segment starts one 32-slot block further on -- reads ring positions
-// [R, R + 46) and writes [R + 14, R + 46), or all of [R, R + 46) when it
-// starts a segment.  On a ring of 256 a super-chunk S' can alias those writes
-// only if R(S) - R(S') > 210, so the producers wait for the newest such S'
-// (at most 7 back): up to 6 super-chunks of MMAs stay in flight, and no
-// segment start waits for the previous segment's MMAs.  Eight producer lanes
-// write the 8 rows of 4 consecutive slots (128-byte runs per store): a lane
-// loads six 8-byte words, realigns them once by its byte offset and stores
-// aligned word pairs.  The (pair, K segment) units of the batch, pair-major, are dealt to
-// the CTAs as contiguous runs of equal length.  A CTA accumulates a pair's
-// segments in groups of at most grp (grp * seg * K_b^2 < 2^24, set by the
-// host from the bits), reads each group out and adds groups that do not
-// cover the whole pair with integer atomics, so every FP32 value it rounds
-// is an exact integer whatever n is.  Every wait is bounded; a role
-// whose wait gives up raises the CTA's abort flag and leaves its loop, the
-// others leave theirs at their next wait, and the CTA flags TDE_ST_TIMEOUT,
-// waits (bounded) for its copies and MMAs in flight and frees its tensor
-// memory.
-
-constexpr int kWinW = kCnnTopK;                  // windows per pair (8)
-constexpr int kWinJ = 8;                         // columns per window (one core-matrix group)
-constexpr int kWinN = kWinW * kWinJ;             // MMA N = 64
-constexpr int kWinKs = 3072;                     // max samples of the sum per segment
-constexpr int kWinRows = kWinKs / kKc8 + kWinJ;  // rows per window (32)
-constexpr int kWinArr = kWinRows * 128;          // bytes per window array, = the SBO
-constexpr int kWinYBytes = kWinW * kWinArr;      // one segment's window rows
-constexpr int kWinXBox = 112;                    // 16-byte rows per x load (two loads)
-constexpr int kWinXBytes = 2 * kWinXBox * 16;    // x bytes staged per segment
-constexpr int kWinXStride = kWinXBytes;          // x buffer stride
-constexpr int kWinTx = kWinYBytes + kWinXBytes;  // TMA bytes per segment
-constexpr int kWinSC = 2;                        // chunks per super-chunk
-constexpr int kWinRing = 256, kWinMirror = 32;
-constexpr int kWinSlotBytes = (kWinRing + kWinMirror) * 128;
-constexpr int kWinOffSlots = 2 * kWinYBytes;
-constexpr int kWinOffX = kWinOffSlots + kWinSlotBytes;
-constexpr int kWinOffBar = kWinOffX + 2 * kWinXStride;
-constexpr int kWinNBar = 2 + 2 + kNB + kNB + 2 + 2;
-// tensor memory: 2 pair buffers x 2 accumulator sets x 64 columns (the K
-// steps of a chunk alternate between the sets, so consecutive MMAs do not
-// wait on one another's accumulator; the epilogue adds the sets)
-constexpr int kWinCols = 4 * kWinN;
-// warps: 0 and kWinIssuerB issue MMAs, 1-2 write slots, 3 (lane 0) runs the
-// TMA, 4-7 read the accumulators out
-constexpr int kWinIssuerB = 8;
-constexpr int kWinThreads = 32 * (kWinIssuerB + 1);
-constexpr int kWinSmemBytes = kWinOffBar + kWinNBar * 8 + 32 + 1024;
-static_assert(kWinArr % 1024 == 0 && kWinYBytes % 1024 == 0, "window arrays keep the swizzle pattern");
-static_assert((16 * kWinXBox) % 128 == 0 && kWinXStride % 128 == 0, "TMA destinations 128-byte aligned");
-static_assert(kWinKs + 160 <= kWinXBytes, "x segment (slot producers read 32-byte windows)");
-static_assert(2 * (kWinSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
-
-__global__ void __launch_bounds__(kWinThreads, 2)
-    k_xcorr_mma_win(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap xmap,
-                    int64_t n, int npairs, const WinJob* __restrict__ jobs, int nseg, int seg,
-                    int grp, uint32_t* __restrict__ status) {
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t ybuf = base;  // segment buffer b at ybuf + b * kWinYBytes, window w at + w * kWinArr
-  const uint32_t slots = base + kWinOffSlots;
-  const uint32_t xbuf = base + kWinOffX;  // segment buffer b at xbuf + b * kWinXStride
-  const uint32_t seg_full = base + kWinOffBar;
-  const uint32_t seg_empty = seg_full + 16;
-  const uint32_t full_bar = seg_empty + 16;
-  const uint32_t cmt_bar = full_bar + 8 * kNB;
-  const uint32_t acc_full = cmt_bar + 8 * kNB;
-  const uint32_t acc_empty = acc_full + 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (acc_empty + 16 - raw));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int* loaded_sh = reinterpret_cast<int*>(tmem_slot + 2);     // segments whose loads were issued
-  int* committed_sh = reinterpret_cast<int*>(tmem_slot + 3);  // super-chunks whose MMAs were committed
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t kmax = (n + 127 + 127) / 128 * 128;
-  const int64_t units = (int64_t)npairs * nseg;
-  const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
-  const int G = (int)(u1 - u0);  // segments of this CTA's run
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kWinCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (threadIdx.x == 32) {
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(seg_full + 8 * i, 1);
-      mbar_init(seg_empty + 8 * i, 2);  // both issuers commit
-      mbar_init(acc_full + 8 * i, 2);
-      mbar_init(acc_empty + 8 * i, 128);
-    }
-    for (int i = 0; i < kNB; ++i) {
-      mbar_init(full_bar + 8 * i, kProducers);
-      mbar_init(cmt_bar + 8 * i, 2);
-    }
-    *abort_flag = 0;
-    *loaded_sh = 0;
-    *committed_sh = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  // accumulation group of unit u: a pair's segments in runs of grp, so that
-  // no FP32 accumulator sums more than grp * seg samples
-  auto group_of = [&](int64_t u) -> int64_t {
-    const int64_t p = u / nseg;
-    return p * nseg + (u - p * nseg) / grp;
-  };
-  // K chunks of segment g of the run
-  auto seg_of = [&](int g, int* p, int64_t* ks, int* nchunks) {
-    const int64_t u = u0 + g;
-    *p = (int)(u / nseg);
-    *ks = (u - (int64_t)*p * nseg) * seg;
-    const int64_t ke = *ks + seg < kmax ? *ks + seg : kmax;
-    *nchunks = (int)((ke - *ks) / kKc8);
-  };
-
-  if (warp == 3) {
-    // ---- TMA: segment g into buffer g & 1 once segment g - 2's MMAs are done
-    if (lane == 0) {
-      for (int g = 0; g < G && !*abort_flag; ++g) {
-        const int b = g & 1;
-        if (g >= 2 && !mbar_wait_sleep(seg_empty + 8 * b, (uint32_t)(((g - 2) >> 1) & 1))) {
-          *abort_flag = 1;
-          break;
-        }
-        int p, nch;
-        int64_t ks;
-        seg_of(g, &p, &ks, &nch);
-        if (nch <= 0 || nch * kKc8 > kWinKs || (ks & 127) != 0) {  // not the host's segmentation
-          atomicOr(status, TDE_ST_INTERNAL);
-          *abort_flag = 1;
-          break;
-        }
-        const uint32_t fb = seg_full + 8 * b;
-        mbar_expect_tx_win(fb, (uint32_t)kWinTx);
-        for (int w = 0; w < kWinW; ++w) {
-          const int64_t T = fdiv(jobs[(int64_t)p * kWinW + w].lag_lo, 128) * 128;
-          tma_load3(ybuf + (uint32_t)(b * kWinYBytes + w * kWinArr), &ymap, 0, (int)((ks + T) / 128),
-                    2 * p + 1, fb);
-        }
-        const int xr = (int)fdiv(ks - 127, 16);
-        const uint32_t xb = xbuf + (uint32_t)(b * kWinXStride);
-        tma_load3(xb, &xmap, 0, xr, 2 * p, fb);
-        tma_load3(xb + 16u * kWinXBox, &xmap, 0, xr + kWinXBox, 2 * p, fb);
-        *loaded_sh = g + 1;
-      }
-    }
-  } else if (warp == 1 || warp == 2) {
-    // ---- Hankel slots of x, one super-chunk at a time
-    const int t = threadIdx.x - 32;
-    int64_t S = 0;
-    int64_t hist[8];  // unwrapped ring origins of super-chunks S - 1 .. S - 8
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hist[i] = INT64_MIN / 2;
-    bool ok = true;
-    for (int g = 0; g < G && ok && !*abort_flag; ++g) {
-      const int b = g & 1;
-      if (!mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1))) {
-        ok = false;
-        break;
-      }
-      int p, nch;
-      int64_t ks;
-      seg_of(g, &p, &ks, &nch);
-      const uint32_t xs = xbuf + (uint32_t)(b * kWinXStride);
-      const uint32_t xoff = (uint32_t)(ks - 127 - fdiv(ks - 127, 16) * 16);
-      const int nsc = (nch + kWinSC - 1) / kWinSC;
-      const int64_t R0 = 32 * (S + g);  // the segment's ring origin (unwrapped)
-      for (int sc = 0; sc < nsc; ++sc, ++S) {
-        const int64_t R = R0 + 32 * sc;
-        // newest earlier super-chunk whose reads may alias this one's writes
-        int64_t prev = -1;
-#pragma unroll
-        for (int k = 8; k >= 1; --k)
-          if (R - hist[k - 1] > kWinRing - 46) prev = S - k;
-        if (prev >= 0 && !mbar_try(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1)) &&
-            !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
-          ok = false;
-          break;
-        }
-        const int c_last = 2 * sc + 1 < nch ? 2 * sc + 1 : nch - 1;
-        const int e_lo = sc == 0 ? 0 : 32 * sc + 14, e_hi = 16 * c_last + 30;  // relative slots
-        // lane (octet o8, row r) writes row r of 4 consecutive slots: x bytes
-        // [xoff + 8 e + r, + 16) for e = e0 .. e0 + 3, i.e. aligned 8-byte
-        // word pairs of the stream realigned by (xoff + r) mod 8
-        const int r = t & 7;
-        for (int e0 = e_lo + 4 * (t >> 3); e0 < e_hi; e0 += 4 * (kProducers / 8)) {
-          const uint32_t pos = xoff + 8u * (uint32_t)e0 + (uint32_t)r;
-          const uint32_t al = xs + (pos & ~7u);
-          uint32_t u[12], a[10];
-#pragma unroll
-          for (int i = 0; i < 6; ++i) {
-            const uint64_t w = ld_shared_u64(al + 8u * i);
-            u[2 * i] = (uint32_t)w, u[2 * i + 1] = (uint32_t)(w >> 32);
-          }
-          // realign by (pos & 7) bytes: word select, then a byte permute
-          const bool wo = (pos & 4u) != 0;
-          const uint32_t sel = 0x3210u + 0x1111u * (pos & 3u);
-#pragma unroll
-          for (int j = 0; j < 10; ++j)
-            a[j] = __byte_perm(wo ? u[j + 1] : u[j], wo ? u[j + 2] : u[j + 1], sel);
-          const uint32_t rp = (uint32_t)R0 + (uint32_t)e0;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (e0 + k >= e_hi) break;
-            const uint32_t ps = (rp + (uint32_t)k) & (kWinRing - 1);
-            const uint32_t ad = slots + 128u * ps + 16u * (uint32_t)r;
-            st_shared_v4(ad, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
-            if (ps < (uint32_t)kWinMirror)
-              st_shared_v4(ad + 128u * kWinRing, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
-          }
-        }
-        fence_proxy_async();
-        mbar_arrive(full_bar + 8 * (uint32_t)(S % kNB));
-#pragma unroll
-        for (int i = 7; i > 0; --i) hist[i] = hist[i - 1];
-        hist[0] = R;
-      }
-    }
-    if (!ok) *abort_flag = 1;
-  } else if (warp == 0 || warp == kWinIssuerB) {
-    // ---- MMAs: issuer warp 0 takes the K steps 0, 2 of every chunk into
-    // accumulator set 0, the second issuer steps 1, 3 into set 1 (a single
-    // thread's issue loop bounds the MMA rate at this N)
-    const uint32_t set = warp == 0 ? 0u : 1u;
-    const uint32_t idesc = idesc8_for(kWinN);
-    const uint64_t da0 = sdesc(slots, 256, 128, 0, 0) + 32u * set;          // + ring slot * 8
-    const uint64_t db0 = sdesc(ybuf, 16, kWinArr, 2, 0) + 2u * set;         // + (buffer + row * 128) >> 4
-    int64_t S = 0, cur_grp = -1;
-    int pp = -1;
-    bool ok = true, fresh = false;  // fresh: the set is not yet written for this group
-    for (int g = 0; g < G && ok && !*abort_flag; ++g) {
-      int p, nch;
-      int64_t ks;
-      seg_of(g, &p, &ks, &nch);
-      if (group_of(u0 + g) != cur_grp) {  // a new group: its accumulator must have been read out
-        cur_grp = group_of(u0 + g);
-        ++pp;
-        fresh = true;
-        if (pp >= 2)
-          ok = __all_sync(0xffffffffu, mbar_wait_sleep(acc_empty + 8 * (uint32_t)(pp & 1),
-                                                       (uint32_t)(((pp - 2) >> 1) & 1)));
-        if (!ok) break;
-      }
-      const int b = g & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1)));
-      if (!ok) break;
-      const uint32_t d = tmem + (uint32_t)((pp & 1) * 2 * kWinN) + set * kWinN;
-      const int nsc = (nch + kWinSC - 1) / kWinSC;
-      // ring slot of chunk 0 of this segment; chunk c reads from slot + 16 c (the
-      // mirror covers runs that pass the ring's end)
-      const uint32_t pos0 = (uint32_t)((32 * (S + g)) % kWinRing);
-      const uint64_t dbs = db0 + (uint64_t)((uint32_t)(b * kWinYBytes) >> 4);
-      for (int sc = 0; sc < nsc; ++sc, ++S) {
-        {
-          const uint32_t fb = full_bar + 8 * (uint32_t)(S % kNB), ph = (uint32_t)((S / kNB) & 1);
-          ok = __all_sync(0xffffffffu, mbar_try(fb, ph) || mbar_wait_sleep(fb, ph));
-        }
-        if (!ok) break;
-        tc_fence_after();
-        if (lane == 0) {
-          const int c0 = sc * kWinSC;
-          const uint64_t da = da0 + 8u * ((pos0 + 32u * (uint32_t)sc) % kWinRing);
-          const uint64_t db = dbs + 8u * (uint32_t)c0;
-          mma_e4m3(d, da, db, idesc, fresh ? 0u : 1u);
-          mma_e4m3(d, da + 64u, db + 4u, idesc, 1u);
-          if (c0 + 1 < nch) {
-            mma_e4m3(d, da + 128u, db + 8u, idesc, 1u);
-            mma_e4m3(d, da + 192u, db + 12u, idesc, 1u);
-          }
-          mma_commit(cmt_bar + 8 * (uint32_t)(S % kNB));
-          if (set == 0) *committed_sh = (int)(S + 1);
-        }
-        fresh = false;
-        __syncwarp();
-      }
-      if (!ok) break;
-      if (lane == 0) {
-        mma_commit(seg_empty + 8 * b);  // the segment's buffers are free once its MMAs are done
-        if (g + 1 >= G || group_of(u0 + g + 1) != cur_grp)
-          mma_commit(acc_full + 8 * (uint32_t)(pp & 1));  // the group's sum is complete
-      }
-      __syncwarp();
-    }
-    if (!ok) *abort_flag = 1;
-  } else if (warp >= 4) {
-    // ---- epilogue: TMEM lanes 32 (warp & 3) .., all 64 columns
-    const int qd = warp & 3;
-    const int m = 32 * qd + lane;
-    int pp = 0;
-    for (int64_t u = u0; u < u1; ++pp) {
-      // the group's segments [sg_lo, sg_hi) of pair p within this CTA's run
-      const int p = (int)(u / nseg);
-      const int sg_lo = (int)(u - (int64_t)p * nseg);
-      int sg_hi = (sg_lo / grp + 1) * grp;
-      if (sg_hi > nseg) sg_hi = nseg;
-      if (u1 - u < sg_hi - sg_lo) sg_hi = sg_lo + (int)(u1 - u);
-      const bool whole = sg_lo == 0 && sg_hi == nseg;  // no other group adds to this pair
-      u += sg_hi - sg_lo;
-      if (*abort_flag) break;
-      if (!mbar_wait_sleep(acc_full + 8 * (uint32_t)(pp & 1), (uint32_t)((pp >> 1) & 1))) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      uint32_t v[32], v1[32];
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((pp & 1) * 2 * kWinN + 32 * half);
-        tmem_ld32(col, v);
-        tmem_ld32(col + kWinN, v1);
-#pragma unroll
-        for (int wq = 0; wq < 4; ++wq) {
-          const WinJob jw = jobs[(int64_t)p * kWinW + 4 * half + wq];
-          const int64_t T = fdiv(jw.lag_lo, 128) * 128;
-#pragma unroll
-          for (int j = 0; j < kWinJ; ++j) {
-            const int64_t tau = T + 128 * j + 127 - m;
-            if (tau < jw.lag_lo || tau > jw.lag_hi) continue;
-            const int val = __float2int_rn(__uint_as_float(v[8 * wq + j]) + __uint_as_float(v1[8 * wq + j]));
-            if (whole)
-              jw.c[tau - jw.lag_lo] = val;
-            else if (val != 0)
-              atomicAdd(jw.c + (tau - jw.lag_lo), val);
-          }
-        }
-      }
-      tc_fence_before();
-      mbar_arrive(acc_empty + 8 * (uint32_t)(pp & 1));
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (*abort_flag && threadIdx.x == 0) {
-    atomicOr(status, TDE_ST_TIMEOUT);
-    // bounded waits for the copies and MMAs still in flight
-    const int L = *loaded_sh;
-    for (int g = L - 2 < 0 ? 0 : L - 2; g < L; ++g)
-      mbar_wait_sleep(seg_full + 8 * (uint32_t)(g & 1), (uint32_t)((g >> 1) & 1));
-    const int C = *committed_sh;
-    if (C > 0) mbar_wait_sleep(cmt_bar + 8 * (uint32_t)((C - 1) % kNB), (uint32_t)(((C - 1) / kNB) & 1));
-  }
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWinCols)
-                 : "memory");
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The same windows with packed E2M1 operands, for levels in {-1, 0, 1} (bits
-// 1 and 2): tcgen05 kind::mxf4 with every block scale 1.0 (UE8M0 0x7F), so
-// the products are the exact levels and the FP32 sums exact integers.  One
-// MMA takes K = 64 samples (32 bytes per row), half as many MMAs and half the
-// operand bytes per sample as E4M3.
-//   A: Hankel slots as before, now 32 samples (16 bytes) per slot row: slot
-//      e, row r = x[8 e + r - 127 + ks ..], 32 samples; core matrix (g, h) of
-//      an MMA is slot e0 + g + 4 h (leading byte offset 4 slots, stride 1).
-//      A chunk of 128 samples is 2 MMAs (e0 + 0, e0 + 8) reading 28 slots.  A
-//      super-chunk is 8 chunks (16 MMAs per wait and commit: the per-batch
-//      costs of a small batch kept the issuers from the tensor pipe): it reads
-//      [R, R + 140) and writes [R + 12, R + 140) (all of it at a segment
-//      start) on a ring of 512 slots, and the producers wait for the newest
-//      earlier super-chunk with R - R' > 512 - 140.  Odd rows start mid-byte,
-//      so producers realign the packed stream with 32-bit funnel shifts
-//      (sample p at bits 4 p .. 4 p + 3).
-//   B: each window's y segment as 64-byte rows of 128 samples (row r =
-//      y[ks + T_w + 128 r ..]) in the 64-byte swizzle, one TMA load per window;
-//      chunk c uses rows c .. c + 7 of every window (N = 64), an MMA's second
-//      K step is the row's second 32 bytes.
-// Roles (11 warps, two CTAs per SM): warp 3 lane 0 TMA; warps 1, 2, 8, 9 the
-// slot rows (two slots per lane); warps 0 and 10 the MMAs, one K step of
-// every chunk each, into two accumulator sets (a thread issues an MMA in
-// about 90 cycles, twice the tensor pipe's time for one of N = 64); warps 4-7
-// set the block scales once, then read each accumulation group out (both
-// sets, summed) and release the accumulators before storing.  Tensor
-// memory: 2 sets x 64 columns, then 64 columns of scales (UE8M0 1.0).
-
-constexpr int kW4Rows = kWinKs / kKc8 + kWinJ;   // 64-byte rows per window (32)
-constexpr int kW4Arr = kW4Rows * 64;             // bytes per window array (= the SBO)
-constexpr int kW4YBytes = kWinW * kW4Arr;        // one segment's window rows
-constexpr int kW4XBox = 128;                     // 16-byte rows (32 samples) of x per segment
-constexpr int kW4XBytes = kW4XBox * 16;
-constexpr int kW4Tx = kW4YBytes + kW4XBytes;     // TMA bytes per segment
-#ifndef TDE_W4_SC
-#define TDE_W4_SC 8
-#endif
-constexpr int kW4SC = TDE_W4_SC;                 // chunks per super-chunk
-constexpr int kW4Ring = 512;                     // slot ring (+ kWinMirror mirrored slots)
-constexpr int kW4SlotBytes = (kW4Ring + kWinMirror) * 128;
-constexpr int kW4Step = 16 * kW4SC;              // new slots per super-chunk
-constexpr int kW4Read = kW4Step + 12;            // slots a super-chunk reads
-constexpr int kW4OffSlots = 2 * kW4YBytes;
-constexpr int kW4OffX = kW4OffSlots + kW4SlotBytes;
-constexpr int kW4OffBar = kW4OffX + 2 * kW4XBytes;
-constexpr int kW4NBar = 2 + 2 + kNB + kNB + 2 + 2;
-constexpr int kW4Cols = 256;                     // 2 accumulator sets x 64 columns + block scales
-constexpr int kW4ScaleCol = 128;                 // scales fill columns 128 .. 191
-constexpr int kW4Producers = 128;                // warps 1, 2, 8, 9
-constexpr int kW4IssuerB = 10;                   // second MMA warp
-constexpr int kW4Threads = 32 * (kW4IssuerB + 1);
-constexpr int kW4SmemBytes = kW4OffBar + kW4NBar * 8 + 32 + 1024;
-static_assert(kW4Arr % 512 == 0 && kW4YBytes % 1024 == 0, "window arrays keep the 64-byte swizzle pattern");
-static_assert(kW4XBytes % 128 == 0, "TMA destinations 128-byte aligned");
-// the furthest producer read: nibble offset < 32 + 8 (last slot e) + 7 + 40,
-// last slot e < 16 nch + 28 with nch <= kWinKs / 128, plus 8 bytes of word alignment
-static_assert((32 + 8 * (16 * (kWinKs / kKc8) + 28) + 7 + 40) / 2 + 8 <= kW4XBytes, "x segment");
-static_assert(2 * (kW4SmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
-static_assert(2 * kW4Cols <= 512, "two CTAs' tensor memory per SM");
-static_assert(kW4Ring % kW4Step == 0 && kW4Ring - kW4Step + kW4Read <= kW4Ring + kWinMirror,
-              "a super-chunk's reads stay inside the ring and its mirror");
-static_assert((kW4Ring - kW4Read) / kW4Step + 1 <= 8 && kNB >= 8,
-              "the super-chunk a write may alias is among the 8 the producers remember");
-
 // Instruction descriptor, kind::mxf4 (block-scaled): A and B E2M1 (format 1,
 // bits 7-9 and 10-12), both K-major, N >> 3 at bits 17-22, UE8M0 scales (bit
 // 23), M >> 4 at bits 24-28, scale-factor ids 0 (bits 4-5 and 29-30).
@@ -851,314 +405,6 @@ __device__ __forceinline__ void mma_mxf4(uint32_t d_tmem, uint64_t a, uint64_t b
           d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(acc)
       : "memory");
-}
-
-__global__ void __launch_bounds__(kW4Threads, 2)
-    k_xcorr_mma_win4(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap xmap,
-                     int64_t n, int npairs, const WinJob* __restrict__ jobs, int nseg, int seg, int grp,
-                     uint32_t* __restrict__ status) {
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t ybuf = base;  // segment buffer b at ybuf + b * kW4YBytes, window w at + w * kW4Arr
-  const uint32_t slots = base + kW4OffSlots;
-  const uint32_t xbuf = base + kW4OffX;  // segment buffer b at xbuf + b * kW4XBytes
-  const uint32_t seg_full = base + kW4OffBar;
-  const uint32_t seg_empty = seg_full + 16;
-  const uint32_t full_bar = seg_empty + 16;
-  const uint32_t cmt_bar = full_bar + 8 * kNB;
-  const uint32_t acc_full = cmt_bar + 8 * kNB;
-  const uint32_t acc_empty = acc_full + 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + (acc_empty + 16 - raw));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int* loaded_sh = reinterpret_cast<int*>(tmem_slot + 2);
-  int* committed_sh = reinterpret_cast<int*>(tmem_slot + 3);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t kmax = (n + 127 + 127) / 128 * 128;
-  const int64_t units = (int64_t)npairs * nseg;
-  const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
-  const int G = (int)(u1 - u0);
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kW4Cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (threadIdx.x == 32) {
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(seg_full + 8 * i, 1);
-      mbar_init(seg_empty + 8 * i, 2);  // both issuers commit
-      mbar_init(acc_full + 8 * i, 2);
-      mbar_init(acc_empty + 8 * i, 128);
-    }
-    for (int i = 0; i < kNB; ++i) {
-      mbar_init(full_bar + 8 * i, kW4Producers);
-      mbar_init(cmt_bar + 8 * i, 2);
-    }
-    *abort_flag = 0;
-    *loaded_sh = 0;
-    *committed_sh = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  if (warp >= 4 && warp < 8) {
-    // block scales: UE8M0 1.0 in every byte of columns kW4ScaleCol .. + 63 of
-    // this warp's 32 lanes
-    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 32)
-      asm volatile(
-          "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-          "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-          "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(tmem + lanes +
-                                                                                   kW4ScaleCol + c0),
-          "r"(0x7F7F7F7Fu)
-          : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-
-  auto group_of = [&](int64_t u) -> int64_t {
-    const int64_t p = u / nseg;
-    return p * nseg + (u - p * nseg) / grp;
-  };
-  auto seg_of = [&](int g, int* p, int64_t* ks, int* nchunks) {
-    const int64_t u = u0 + g;
-    *p = (int)(u / nseg);
-    *ks = (u - (int64_t)*p * nseg) * seg;
-    const int64_t ke = *ks + seg < kmax ? *ks + seg : kmax;
-    *nchunks = (int)((ke - *ks) / kKc8);
-  };
-
-  if (warp == 3) {
-    // ---- TMA: segment g into buffer g & 1 once segment g - 2's MMAs are done
-    if (lane == 0) {
-      for (int g = 0; g < G && !*abort_flag; ++g) {
-        const int b = g & 1;
-        if (g >= 2 && !mbar_wait_sleep(seg_empty + 8 * b, (uint32_t)(((g - 2) >> 1) & 1))) {
-          *abort_flag = 1;
-          break;
-        }
-        int p, nch;
-        int64_t ks;
-        seg_of(g, &p, &ks, &nch);
-        if (nch <= 0 || nch * kKc8 > kWinKs || (ks & 127) != 0) {  // not the host's segmentation
-          atomicOr(status, TDE_ST_INTERNAL);
-          *abort_flag = 1;
-          break;
-        }
-        const uint32_t fb = seg_full + 8 * b;
-        mbar_expect_tx_win(fb, (uint32_t)kW4Tx);
-        for (int w = 0; w < kWinW; ++w) {
-          const int64_t T = fdiv(jobs[(int64_t)p * kWinW + w].lag_lo, 128) * 128;
-          tma_load3(ybuf + (uint32_t)(b * kW4YBytes + w * kW4Arr), &ymap, 0, (int)((ks + T) / 128),
-                    2 * p + 1, fb);
-        }
-        tma_load3(xbuf + (uint32_t)(b * kW4XBytes), &xmap, 0, (int)fdiv(ks - 127, 32), 2 * p, fb);
-        *loaded_sh = g + 1;
-      }
-    }
-  } else if (warp == 1 || warp == 2 || warp == 8 || warp == 9) {
-    // ---- Hankel slots of x, one super-chunk at a time; lane (pair o, row r)
-    // writes row r of the 2 consecutive slots e0, e0 + 1: packed words
-    // W[0 .. 4] of the nibble stream from sample 8 e0 + r - 127 + ks, slot
-    // e0 + i getting W[i .. i + 3]
-    const int t = warp <= 2 ? threadIdx.x - 32 : threadIdx.x - 256 + 64;
-    const int r = t & 7, o = t >> 3;
-    int64_t S = 0;
-    int64_t hist[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hist[i] = INT64_MIN / 2;
-    bool ok = true;
-    for (int g = 0; g < G && ok && !*abort_flag; ++g) {
-      const int b = g & 1;
-      if (!mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1))) {
-        ok = false;
-        break;
-      }
-      int p, nch;
-      int64_t ks;
-      seg_of(g, &p, &ks, &nch);
-      const uint32_t xs = xbuf + (uint32_t)(b * kW4XBytes);
-      const uint32_t bp = (uint32_t)(ks - 127 - fdiv(ks - 127, 32) * 32);  // nibble of sample ks - 127
-      const int nsc = (nch + kW4SC - 1) / kW4SC;
-      const int64_t R0 = (int64_t)kW4Step * (S + g);
-      for (int sc = 0; sc < nsc; ++sc, ++S) {
-        const int64_t R = R0 + kW4Step * sc;
-        int64_t prev = -1;
-#pragma unroll
-        for (int k = 8; k >= 1; --k)
-          if (R - hist[k - 1] > kW4Ring - kW4Read) prev = S - k;
-        if (prev >= 0 && !mbar_try(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1)) &&
-            !mbar_wait_sleep(cmt_bar + 8 * (uint32_t)(prev % kNB), (uint32_t)((prev / kNB) & 1))) {
-          ok = false;
-          break;
-        }
-        const int c_last = kW4SC * sc + kW4SC - 1 < nch ? kW4SC * sc + kW4SC - 1 : nch - 1;
-        const int e_lo = sc == 0 ? 0 : kW4Step * sc + (kW4Read - kW4Step), e_hi = 16 * c_last + 28;
-        for (int e0 = e_lo + 2 * o; e0 < e_hi; e0 += 2 * (kW4Producers / 8)) {
-          const uint32_t pn = bp + 8u * (uint32_t)e0 + (uint32_t)r;  // nibble offset in the x buffer
-          const uint32_t a8 = (pn >> 1) & ~7u;
-          const uint32_t sbit = 4u * pn - 8u * a8;  // 0 .. 60
-          uint32_t u[8], w[5];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const uint64_t v = ld_shared_u64(xs + a8 + 8u * i);
-            u[2 * i] = (uint32_t)v, u[2 * i + 1] = (uint32_t)(v >> 32);
-          }
-          const bool wo = sbit >= 32u;
-          const uint32_t sh = sbit & 31u;
-#pragma unroll
-          for (int j = 0; j < 5; ++j) w[j] = __funnelshift_r(wo ? u[j + 1] : u[j], wo ? u[j + 2] : u[j + 1], sh);
-          const uint32_t rp = (uint32_t)R0 + (uint32_t)e0;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            if (e0 + k >= e_hi) break;
-            const uint32_t ps = (rp + (uint32_t)k) & (kW4Ring - 1);
-            const uint32_t ad = slots + 128u * ps + 16u * (uint32_t)r;
-            st_shared_v4(ad, w[k], w[k + 1], w[k + 2], w[k + 3]);
-            if (ps < (uint32_t)kWinMirror) st_shared_v4(ad + 128u * kW4Ring, w[k], w[k + 1], w[k + 2], w[k + 3]);
-          }
-        }
-        fence_proxy_async();
-        mbar_arrive(full_bar + 8 * (uint32_t)(S % kNB));
-#pragma unroll
-        for (int i = 7; i > 0; --i) hist[i] = hist[i - 1];
-        hist[0] = R;
-      }
-    }
-    if (!ok) *abort_flag = 1;
-  } else if (warp == 0 || warp == kW4IssuerB) {
-    // ---- MMAs (lane 0 issues, the warp waits): warp 0 takes the first K step
-    // (64 samples) of every chunk into accumulator set 0, the second warp the
-    // second step into set 1; one accumulation group at a time
-    const uint32_t set = warp == 0 ? 0u : 1u;
-    const uint32_t idesc = idesc4_for(kWinN);
-    const uint32_t sfa = tmem + kW4ScaleCol, sfb = tmem + kW4ScaleCol + 32;
-    const uint64_t da0 = sdesc(slots, 512, 128, 0, 0) + 64u * set;  // + ring slot * 8
-    const uint64_t db0 = sdesc(ybuf, 16, kW4Arr, 4, 0) + 2u * set;  // + (buffer + row * 64) >> 4
-    int64_t S = 0, cur_grp = -1;
-    int pp = -1;
-    bool ok = true, fresh = false;
-    for (int g = 0; g < G && ok && !*abort_flag; ++g) {
-      int p, nch;
-      int64_t ks;
-      seg_of(g, &p, &ks, &nch);
-      if (group_of(u0 + g) != cur_grp) {  // a new group: its accumulator must have been read out
-        cur_grp = group_of(u0 + g);
-        ++pp;
-        fresh = true;
-        if (pp >= 1)  // the epilogue has read the previous group out
-          ok = __all_sync(0xffffffffu, mbar_wait_sleep(acc_empty, (uint32_t)((pp - 1) & 1)));
-        if (!ok) break;
-      }
-      const int b = g & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait_sleep(seg_full + 8 * b, (uint32_t)((g >> 1) & 1)));
-      if (!ok) break;
-      const uint32_t d = tmem + set * (uint32_t)kWinN;
-      const int nsc = (nch + kW4SC - 1) / kW4SC;
-      const uint32_t pos0 = (uint32_t)(((int64_t)kW4Step * (S + g)) % kW4Ring);
-      const uint64_t dbs = db0 + (uint64_t)((uint32_t)(b * kW4YBytes) >> 4);
-      for (int sc = 0; sc < nsc; ++sc, ++S) {
-        {
-          const uint32_t fb = full_bar + 8 * (uint32_t)(S % kNB), ph = (uint32_t)((S / kNB) & 1);
-          ok = __all_sync(0xffffffffu, mbar_try(fb, ph) || mbar_wait_sleep(fb, ph));
-        }
-        if (!ok) break;
-        tc_fence_after();
-        if (lane == 0) {
-          const int c0 = sc * kW4SC;
-          const uint64_t da = da0 + 8u * ((pos0 + (uint32_t)kW4Step * (uint32_t)sc) % kW4Ring);
-          const uint64_t db = dbs + 4u * (uint32_t)c0;
-          mma_mxf4(d, da, db, idesc, sfa, sfb, fresh ? 0u : 1u);
-#pragma unroll
-          for (int cc = 1; cc < kW4SC; ++cc)
-            if (c0 + cc < nch) mma_mxf4(d, da + 128u * cc, db + 4u * cc, idesc, sfa, sfb, 1u);
-          mma_commit(cmt_bar + 8 * (uint32_t)(S % kNB));
-          if (set == 0) *committed_sh = (int)(S + 1);
-        }
-        fresh = false;
-        __syncwarp();
-      }
-      if (!ok) break;
-      if (lane == 0) {
-        mma_commit(seg_empty + 8 * b);
-        if (g + 1 >= G || group_of(u0 + g + 1) != cur_grp) mma_commit(acc_full);
-      }
-      __syncwarp();
-    }
-    if (!ok) *abort_flag = 1;
-  } else if (warp >= 4 && warp < 8) {
-    // ---- epilogue: TMEM lanes 32 (warp & 3) .., the pair buffer's 64 columns
-    const int qd = warp & 3;
-    const int m = 32 * qd + lane;
-    int pp = 0;
-    for (int64_t u = u0; u < u1; ++pp) {
-      const int p = (int)(u / nseg);
-      const int sg_lo = (int)(u - (int64_t)p * nseg);
-      int sg_hi = (sg_lo / grp + 1) * grp;
-      if (sg_hi > nseg) sg_hi = nseg;
-      if (u1 - u < sg_hi - sg_lo) sg_hi = sg_lo + (int)(u1 - u);
-      const bool whole = sg_lo == 0 && sg_hi == nseg;
-      u += sg_hi - sg_lo;
-      if (*abort_flag) break;
-      if (!mbar_wait_sleep(acc_full, (uint32_t)(pp & 1))) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      uint32_t v[16], v1[16];
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {  // 16 columns: windows 2 qq, 2 qq + 1
-        const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * qq);
-        tmem_ld16_nowait(col, v);
-        tmem_ld16_nowait(col + kWinN, v1);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (qq == 3) {  // the accumulators are read: the next group's MMAs may start
-          tc_fence_before();
-          mbar_arrive(acc_empty);
-        }
-#pragma unroll
-        for (int wq = 0; wq < 2; ++wq) {
-          const WinJob jw = jobs[(int64_t)p * kWinW + 2 * qq + wq];
-          const int64_t T = fdiv(jw.lag_lo, 128) * 128;
-#pragma unroll
-          for (int j = 0; j < kWinJ; ++j) {
-            const int64_t tau = T + 128 * j + 127 - m;
-            if (tau < jw.lag_lo || tau > jw.lag_hi) continue;
-            const int val = __float2int_rn(__uint_as_float(v[8 * wq + j]) + __uint_as_float(v1[8 * wq + j]));
-            if (whole)
-              jw.c[tau - jw.lag_lo] = val;
-            else if (val != 0)
-              atomicAdd(jw.c + (tau - jw.lag_lo), val);
-          }
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (*abort_flag && threadIdx.x == 0) {
-    atomicOr(status, TDE_ST_TIMEOUT);
-    const int L = *loaded_sh;
-    for (int g = L - 2 < 0 ? 0 : L - 2; g < L; ++g)
-      mbar_wait_sleep(seg_full + 8 * (uint32_t)(g & 1), (uint32_t)((g >> 1) & 1));
-    const int C = *committed_sh;
-    if (C > 0) mbar_wait_sleep(cmt_bar + 8 * (uint32_t)((C - 1) % kNB), (uint32_t)(((C - 1) / kNB) & 1));
-  }
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kW4Cols)
-                 : "memory");
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -2047,100 +1293,6 @@ cudaError_t launch_xcorr_mma4(const MmaPair* d_pairs, const MmaItem* d_items, in
   if (grid > nitems) grid = nitems;
   k_xcorr_mma4<<<grid, kThreads, kSmemBytes4, st>>>(d_pairs, d_items, nitems, d_nitems, d_counter,
                                                      d_status);
-  TDE_COUNT_LAUNCH(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, int bits,
-                                     const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st) {
-  if (npairs <= 0) return cudaSuccess;
-  if (n_pad % 128 != 0 || n_pad < n || (reinterpret_cast<uintptr_t>(d_qe) & 15) != 0)
-    return cudaErrorInvalidValue;
-  if (bits != 1 && bits != 2 && bits != 4) return cudaErrorInvalidValue;
-  // K range [0, n + 127) rounded up to 128; segments are multiples of 128
-  // (so that each segment's windows start on a 128-sample row)
-  const int64_t kmax = ceil_div64(n + 127, 128) * 128;
-  const int nseg = (int)ceil_div64(kmax, kWinKs);
-  const int seg = (int)(ceil_div64(ceil_div64(kmax, nseg), 128) * 128);
-  // segments per accumulator: grp * seg * K_b^2 < 2^24 keeps every FP32 partial
-  // (and the sum of the two sets) an exact integer; K_b = 2^(bits-1) bounds |level|
-  const int64_t kb2 = (int64_t)1 << (2 * (bits - 1));
-  const int grp = (int)(((int64_t)1 << 24) / ((int64_t)seg * kb2 + 1));
-  if (grp < 1) return cudaErrorInvalidValue;
-  CUtensorMap ymap, xmap;
-  if (!tmap_bytes3(&ymap, d_qe, n_pad, 2 * npairs, 128, kWinRows, 128) ||
-      !tmap_bytes3(&xmap, d_qe, n_pad, 2 * npairs, 16, kWinXBox, 0))
-    return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kWinSmemBytes);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // two CTAs per SM, each with an equal run of the (pair, segment) units
-  const int64_t units = (int64_t)npairs * nseg;
-  const int grid = (int)(units < 2 * (int64_t)sms ? units : 2 * (int64_t)sms);
-  k_xcorr_mma_win<<<grid, kWinThreads, kWinSmemBytes, st>>>(ymap, xmap, n, npairs, d_jobs, nseg, seg,
-                                                            grp, d_status);
-  TDE_COUNT_LAUNCH(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_xcorr_mma_windows4(const uint8_t* d_qf, int64_t n, int64_t n_pad, int npairs, int bits,
-                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st) {
-  if (npairs <= 0) return cudaSuccess;
-  if (n_pad % 128 != 0 || n_pad < n || (reinterpret_cast<uintptr_t>(d_qf) & 15) != 0)
-    return cudaErrorInvalidValue;
-  if (bits != 1 && bits != 2) return cudaErrorInvalidValue;
-  const int64_t kmax = ceil_div64(n + 127, 128) * 128;
-  const int nseg = (int)ceil_div64(kmax, kWinKs);
-  const int seg = (int)(ceil_div64(ceil_div64(kmax, nseg), 128) * 128);
-  // |level| <= 1: an accumulator may sum up to 2^24 - 1 samples exactly
-  const int grp = (int)((((int64_t)1 << 24) - 1) / seg);
-  CUtensorMap ymap, xmap;
-  if (!tmap_bytes3(&ymap, d_qf, n_pad / 2, 2 * npairs, 64, kW4Rows, 64) ||
-      !tmap_bytes3(&xmap, d_qf, n_pad / 2, 2 * npairs, 16, kW4XBox, 0))
-    return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_xcorr_mma_win4, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kW4SmemBytes);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t units = (int64_t)npairs * nseg;
-  const int grid = (int)(units < 2 * (int64_t)sms ? units : 2 * (int64_t)sms);
-  k_xcorr_mma_win4<<<grid, kW4Threads, kW4SmemBytes, st>>>(ymap, xmap, n, npairs, d_jobs, nseg, seg, grp,
-                                                           d_status);
-  TDE_COUNT_LAUNCH(1);
-  return cudaGetLastError();
-}
-
-// Levels -> packed E2M1 nibbles with a padded signal stride of n_pad / 2 bytes
-// (zeros in [n, n_pad)); flags TDE_ST_INTERNAL for a level outside {-1, 0, 1}.
-__global__ void k_to_e2m1(const int8_t* __restrict__ q, int64_t n, int64_t n_pad, int nsig,
-                          uint8_t* __restrict__ qf, uint32_t* __restrict__ status) {
-  const int64_t total = (int64_t)nsig * n_pad;
-  bool bad = false;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; i < total;
-       i += (int64_t)gridDim.x * blockDim.x * 8) {
-    const int64_t s = i / n_pad, j = i - s * n_pad;  // n_pad % 8 == 0: one signal per 8 samples
-    uint32_t w[2] = {0u, 0u};
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (j + k < n) w[k >> 2] |= (uint32_t)(uint8_t)q[s * n + j + k] << (8 * (k & 3));
-    bad |= __vcmpgtu4(__vabs4(w[0]), 0x01010101u) != 0u || __vcmpgtu4(__vabs4(w[1]), 0x01010101u) != 0u;
-    *reinterpret_cast<uint32_t*>(qf + i / 2) = e2m1x4(w[0]) | (e2m1x4(w[1]) << 16);
-  }
-  if (bad) atomicOr(status, TDE_ST_INTERNAL);
-}
-
-cudaError_t launch_to_e2m1(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qf,
-                           uint32_t* d_status, cudaStream_t st) {
-  if (nsig <= 0) return cudaSuccess;
-  if (n_pad % 8 != 0 || n_pad < n) return cudaErrorInvalidValue;
-  const int64_t groups = (int64_t)nsig * n_pad / 8;
-  const int64_t grid = groups / 256 + 1 < 4096 ? groups / 256 + 1 : 4096;
-  k_to_e2m1<<<(unsigned)grid, 256, 0, st>>>(d_q, n, n_pad, nsig, d_qf, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

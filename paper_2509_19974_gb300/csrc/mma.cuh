@@ -57,35 +57,20 @@ cudaError_t launch_xcorr_mma4(const MmaPair* d_pairs, const MmaItem* d_items, in
                               int* d_counter, int grid, uint32_t* d_status, cudaStream_t st,
                               const int* d_nitems = nullptr);
 
-// The learned proposal's windows on the tensor cores: the levels as E4M3
-// bytes d_qe, signal stride n_pad (a multiple of 128, zeros in [n, n_pad),
-// 16-byte aligned); pair p is x = signal 2 p, y = signal 2 p + 1 (n levels
-// each, |level| <= 2^(bits-1)); its 8 windows d_jobs[8 p + w] (lag_lo,
-// lag_hi <= lag_lo + 256, c) receive c[i] += sum_n x[n] y[n + lag_lo + i] for
-// lag_lo + i <= lag_hi (other entries are not written): the c buffers must be
-// zeroed first.  bits sets how many samples one FP32 accumulator may sum while
-// staying exact; the caller checks that n * 4^(bits-1) < 2^31 for the int32 c.
-cudaError_t launch_xcorr_mma_windows(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, int bits,
-                                     const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
-// The same windows from packed E2M1 levels (levels in {-1, 0, 1}, bits 1 or
-// 2): d_qf holds signal s at d_qf + s * n_pad / 2, sample i in nibble i & 1 of
-// byte i / 2 (low nibble first), zeros in [n, n_pad); n_pad a multiple of
-// 128, d_qf 16-byte aligned.  Computed with block-scaled FP4 MMAs (unit
-// scales), K = 64 samples per MMA.
-cudaError_t launch_xcorr_mma_windows4(const uint8_t* d_qf, int64_t n, int64_t n_pad, int npairs, int bits,
-                                      const WinJob* d_jobs, uint32_t* d_status, cudaStream_t st);
-// The same windows in polyphase form (winpp.cu): per pair the 128 x 128
-// blocks D_u[b][j] = sum_a x[128 a + b] y[128 (a + u) + j] that the windows
-// need, as MN-major E4M3 GEMMs over the rows a, and each window lag as a sum
-// of block diagonals.  d_qe as for launch_xcorr_mma_windows (any bits: a
-// block sums at most 512 rows, exact in FP32); the c buffers must be zeroed
-// first; d_njobs[p] = win_jobs of pair p's windows (device).  One CTA per SM.
+// The learned proposal's windows on the tensor cores, in polyphase form
+// (winpp.cu): per pair the 128 x 128 blocks
+// D_u[b][j] = sum_a x[128 a + b] y[128 (a + u) + j] that the windows need, as
+// MN-major E4M3 GEMMs over the 128-sample rows a, and each window lag as a
+// sum of block diagonals.  d_qe: the levels as E4M3 bytes, signal stride n_pad
+// (a multiple of 128, zeros in [n, n_pad), 16-byte aligned); pair p is
+// x = signal 2 p, y = signal 2 p + 1 (n levels each, |level| <= 7; a block
+// sums at most 512 rows, exact in FP32); its 8 windows d_jobs[8 p + w]
+// (lag_lo, lag_hi <= lag_lo + 256, c) receive c[i] += sum_n x[n] y[n + lag_lo
+// + i] for lag_lo + i <= lag_hi: the c buffers must be zeroed first, and the
+// caller checks n * 4^(bits-1) < 2^31 for the int32 c.  d_njobs[p] = win_jobs
+// of pair p's windows (device).  One CTA per SM.
 cudaError_t launch_xcorr_win_pp(const uint8_t* d_qe, int64_t n, int64_t n_pad, int npairs, const WinJob* d_jobs,
                                 const int32_t* d_njobs, uint32_t* d_status, cudaStream_t st);
-// Levels [nsig][n] -> packed E2M1 [nsig][n_pad / 2 bytes] (zeros past n);
-// n_pad % 8 == 0.  A level outside {-1, 0, 1} flags TDE_ST_INTERNAL.
-cudaError_t launch_to_e2m1(const int8_t* d_q, int64_t n, int64_t n_pad, int nsig, uint8_t* d_qf,
-                           uint32_t* d_status, cudaStream_t st);
 // One CTA whose bounded waits (the kernels' own) run out on a barrier
 // nothing arrives on: TDE_ST_TIMEOUT in d_status after about 4 s.
 cudaError_t launch_wait_selftest(uint32_t* d_status, cudaStream_t st);

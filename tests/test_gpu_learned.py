@@ -307,3 +307,40 @@ def test_learned_batch_graph_mixed_fallback(ctx):
     assert torch.equal(lags2, l3) and torch.equal(vals2, v3) and torch.equal(fb2, f3)
     lb.close()
     m.close()
+
+
+def test_xcorr_windows_many_pairs_mixed_patterns(ctx):
+    """Enough pairs that every CTA of the windows kernel walks several
+    visits (its plan ring and both slot rings lap), with every window
+    pattern the proposal or a caller gives: 8 adjacent bins, scattered bins,
+    centres on no 128-lag boundary, 8 identical centres, windows partly or
+    wholly outside the lag range.  48 pairs, every pattern among them, are
+    compared with the oracle lag by lag."""
+    import oracle
+    n, P = 8192 + 77, 600
+    rng = np.random.default_rng(21)
+    q = rng.integers(-1, 2, size=(2 * P, n)).astype(np.int8)
+    lf = n // 256
+    cent = np.empty((P, 8), np.int32)
+    for p in range(P):
+        kind = p % 5
+        if kind == 0:
+            b0 = rng.integers(-lf + 5, lf - 5)
+            cent[p] = 256 * (b0 + np.arange(-4, 4))
+        elif kind == 1:
+            cent[p] = 256 * rng.choice(np.arange(-lf + 1, lf), 8, replace=False)
+        elif kind == 2:
+            cent[p] = rng.integers(-(n - 1), n, 8)
+        elif kind == 3:
+            cent[p] = rng.integers(-(n - 1), n)
+        else:
+            cent[p] = [-(n - 1), n - 1, -(n + 200), n + 500, 0, 128, 129, rng.integers(-(n - 1), n)]
+    c = tde.tde_xcorr_windows(ctx, torch.from_numpy(q).cuda(), 2, torch.from_numpy(cent).cuda())
+    ctx.sync()
+    c = c.cpu().numpy().astype(np.int64)
+    for p in list(range(10)) + list(rng.choice(np.arange(10, P), 38, replace=False)):
+        lags = _window_lags(cent[p])
+        inr = np.abs(lags) <= n - 1
+        want = np.zeros((8, 257), np.int64)
+        want[inr] = oracle.xcorr_at(q[2 * p], q[2 * p + 1], lags[inr])
+        assert np.array_equal(c[p], want), (p, p % 5)

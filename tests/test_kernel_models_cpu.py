@@ -6,103 +6,6 @@ import random
 
 import numpy as np
 
-RING = 256          # k_xcorr_mma_win: slot ring of 256 (+ a 32-slot mirror)
-SC_SLOTS = 46       # slots a super-chunk reads: [R, R + 46)
-
-
-def _ring_rule(nchunks_per_segment):
-    """k_xcorr_mma_win's slot ring.  Super-chunk S (two 128-sample chunks,
-    counted over the CTA's run; g = its segment's index in the run) has
-    origin R(S) = 32 (S + g).  Chunk c of a segment reads ring positions
-    [16 c, 16 c + 30) from the segment origin; a super-chunk writes
-    [32 sc + 14, 16 c_last + 30) (all of [0, 16 c_last + 30) at a segment
-    start).  Before writing, the producers wait for the newest earlier
-    super-chunk S' with R(S) - R(S') > RING - 46 (at most 8 back).  Checks:
-    every earlier super-chunk whose reads alias this one's writes is one the
-    producers waited for."""
-    S, origins, reads = 0, [], {}
-    for g, nch in enumerate(nchunks_per_segment):
-        nsc = -(-nch // 2)
-        r0 = 32 * (S + g)
-        for sc in range(nsc):
-            R = r0 + 32 * sc
-            waited = -1
-            for k in range(8, 0, -1):
-                rk = origins[-k] if len(origins) >= k else -10 ** 18
-                if R - rk > RING - SC_SLOTS:
-                    waited = S - k
-            c_last = min(2 * sc + 1, nch - 1)
-            lo = 0 if sc == 0 else 32 * sc + 14
-            writes = {(r0 + e) % RING for e in range(lo, 16 * c_last + 30)}
-            for s_prev, rd in reads.items():
-                if rd & writes:
-                    assert s_prev <= waited, (nchunks_per_segment, S, s_prev, waited)
-            rd = set()
-            for c in range(2 * sc, c_last + 1):
-                rd |= {(r0 + 16 * c + i) % RING for i in range(30)}
-            reads[S] = rd
-            origins.append(R)
-            S += 1
-
-
-def test_windows_slot_ring_never_overwrites_unread_slots():
-    _ring_rule([24] * 20)
-    _ring_rule([1] * 30)
-    _ring_rule([2, 3, 24, 1, 24, 9, 24])
-    rng = random.Random(0)
-    for _ in range(300):
-        _ring_rule([rng.randint(1, 24) for _ in range(rng.randint(1, 30))])
-
-
-def _ring_rule_fp4(nchunks_per_segment, sc_chunks=4, ring=512):
-    """k_xcorr_mma_win4's slot ring: a chunk reads [16 c, 16 c + 28) (two
-    K = 64 steps over slots e0 + g + 4 h, e0 = 16 c + 8 s); a super-chunk of
-    sc_chunks chunks has origin R(S) = 16 sc_chunks (S + g), reads
-    16 sc_chunks + 12 slots, writes [step sc + 12, 16 c_last + 28) (from 0 at
-    a segment start), and the producers wait for the newest earlier
-    super-chunk with R - R' > ring - reads.  Checks that every earlier
-    super-chunk whose reads alias this one's writes is one they waited for,
-    and that a super-chunk's reads stay inside the ring and its 32-slot
-    mirror."""
-    step = 16 * sc_chunks
-    nread = step + 12
-    S, origins, reads = 0, [], {}
-    for g, nch in enumerate(nchunks_per_segment):
-        nsc = -(-nch // sc_chunks)
-        r0 = step * (S + g)
-        for sc in range(nsc):
-            R = r0 + step * sc
-            assert R % ring + nread <= ring + 32
-            waited = -1
-            for k in range(8, 0, -1):
-                rk = origins[-k] if len(origins) >= k else -10 ** 18
-                if R - rk > ring - nread:
-                    waited = S - k
-            c_last = min(sc_chunks * sc + sc_chunks - 1, nch - 1)
-            lo = 0 if sc == 0 else step * sc + 12
-            writes = {(r0 + e) % ring for e in range(lo, 16 * c_last + 28)}
-            for s_prev, rd in reads.items():
-                if rd & writes:
-                    assert s_prev <= waited, (nchunks_per_segment, S, s_prev, waited)
-            rd = set()
-            for c in range(sc_chunks * sc, c_last + 1):
-                for st in range(2):
-                    rd |= {(r0 + 16 * c + 8 * st + gg + 4 * h) % ring for gg in range(16) for h in range(2)}
-            reads[S] = rd
-            origins.append(R)
-            S += 1
-
-
-def test_windows_fp4_slot_ring_never_overwrites_unread_slots():
-    for scc in (4, 8):
-        _ring_rule_fp4([24] * 20, scc)
-        _ring_rule_fp4([1] * 30, scc)
-        _ring_rule_fp4([2, 3, 24, 1, 24, 9, 24], scc)
-        rng = random.Random(scc)
-        for _ in range(150):
-            _ring_rule_fp4([rng.randint(1, 24) for _ in range(rng.randint(1, 30))], scc)
-
-
 def test_engine_fp4_slot_ring_waits_cover_every_alias():
     """k_xcorr_mma4's slot ring per item: super-chunk j (4 chunks) reads
     [64 j, 64 j + 76) and writes [64 j + 12, 64 j + 76) (from 0 when j = 0)
@@ -125,56 +28,6 @@ def test_engine_fp4_slot_ring_waits_cover_every_alias():
                 assert (16 * c) % ring + 28 <= ring + 32
                 rd |= {(16 * c + i) % ring for i in range(28)}
             reads[j] = rd
-
-
-def _funnel_r(lo, hi, sh):
-    return (((hi << 32) | lo) >> (sh & 31)) & 0xFFFFFFFF
-
-
-def test_windows_fp4_slots_hold_the_hankel_operand():
-    """k_xcorr_mma_win4's producers: the x segment as TMA stages it (packed
-    nibbles from sample 32 floor((ks - 127) / 32), 2048 bytes, zeros outside
-    the signal), each lane's two slot rows from five funnel-shifted words of
-    four aligned 8-byte loads; every read stays in the 2048-byte buffer, and
-    the core matrices an MMA's descriptor names (slot e0 + g + 4 h, e0 =
-    16 c + 8 s) hold A[m][k] = x[ks - 127 + 128 c + 64 s + m + k]."""
-    rng = np.random.default_rng(3)
-    n = 9000
-    x = rng.integers(0, 16, size=n)      # nibble values stand for the levels
-    for ks in (0, 128, 3072, 6144, 8832):
-        nch = min(24, (-(-(n + 254) // 128) * 128 - ks) // 128)
-        x0 = 32 * ((ks - 127) // 32)
-        nib = np.zeros(4096, np.int64)
-        for i in range(4096):
-            if 0 <= x0 + i < n:
-                nib[i] = x[x0 + i]
-        buf = [int(nib[2 * j]) | (int(nib[2 * j + 1]) << 4) for j in range(2048)]
-        bp = (ks - 127) - x0
-        slots = {}
-        e_hi = 16 * (nch - 1) + 28
-        for e0 in range(0, e_hi, 2):
-            for r in range(8):
-                pn = bp + 8 * e0 + r
-                a8 = (pn >> 1) & ~7
-                sbit = 4 * pn - 8 * a8
-                assert 0 <= sbit <= 60 and a8 + 32 <= 2048
-                u = [int.from_bytes(bytes(buf[a8 + 4 * i: a8 + 4 * i + 4]), "little") for i in range(8)]
-                wo, sh = sbit >= 32, sbit & 31
-                w = [_funnel_r(u[j + 1] if wo else u[j], u[j + 2] if wo else u[j + 1], sh) for j in range(5)]
-                for k in range(2):
-                    if e0 + k < e_hi:
-                        slots.setdefault(e0 + k, {})[r] = w[k:k + 4]
-        for c in range(nch):
-            for st in range(2):
-                e0 = 16 * c + 8 * st
-                for m in range(0, 128, 7):
-                    for kk in range(64):
-                        g, r, h, cc = m // 8, m % 8, kk // 32, kk % 32
-                        words = slots[e0 + g + 4 * h][r]
-                        v = (words[cc // 8] >> (4 * (cc % 8))) & 0xF
-                        t = ks - 127 + 128 * c + 64 * st + m + kk
-                        want = x[t] if 0 <= t < n else 0
-                        assert v == want, (ks, c, st, m, kk)
 
 
 def _argmax32_visits(addr, n, gx, threads=256):
