@@ -344,7 +344,7 @@ struct QuantStage {
   int64_t max_n = 0;
   bool with_planes = false;
   size_t o_sigs = 0, o_hist = 0, o_chist = 0, o_state = 0, o_candp = 0, o_planes = 0;
-  std::vector<size_t> o_cand;  // per signal: room for all its keys, then their indices
+  std::vector<size_t> o_cand;  // per signal: room for all its keys, then their indices (+ slack)
   // ns: the signals' lengths (host), or nullptr when all are max_n.  With
   // want_planes the rank quantizer also writes bit planes (set_planes);
   // callers check planes_written() and pack themselves otherwise.
@@ -359,7 +359,7 @@ struct QuantStage {
     o_chist = L.w<uint32_t>((size_t)nsig * 7 * 1024);
     o_state = L.w<QState>(nsig);
     o_cand.resize(nsig);
-    for (int i = 0; i < nsig; ++i) o_cand[i] = L.w<uint32_t>(2 * (size_t)(ns ? ns[i] : mx));
+    for (int i = 0; i < nsig; ++i) o_cand[i] = L.w<uint32_t>(2 * ((size_t)(ns ? ns[i] : mx) + kQCandSlack));
   }
   bool planes_written() const { return with_planes; }
   void fill(const Bases& B, const float* const* xs, int8_t* const* qs, const int64_t* ns) const {

@@ -130,10 +130,13 @@ struct QState {
   int32_t owner[7];  // first threshold with the same prefix (shares its histogram)
   uint32_t ncand;    // keys in the candidate list
 };
+// Slack words of a candidate list beyond the signal's length: the one-launch
+// quantizer keeps one column per thread (up to n + 2048 entries).
+constexpr size_t kQCandSlack = 2048;
 struct QWork {
   uint32_t* hist;               // [nsig][4096]
   QState* state;                // [nsig]
-  uint32_t* const* cand;        // [nsig] device pointers to lists of 2 n words (keys, index | sign)
+  uint32_t* const* cand;        // [nsig] device pointers to lists of 2 (n + kQCandSlack) words (keys, index | sign)
   uint32_t* chist;              // [nsig][7][1024] candidate histograms
 };
 // The rank quantizer (bits 2, 4) as five streaming launches; d_planes

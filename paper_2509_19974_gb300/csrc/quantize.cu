@@ -311,6 +311,67 @@ __device__ __noinline__ void warp_find(const uint32_t* h, int nbins, uint32_t r,
   rest = __shfl_sync(0xffffffffu, fr, src);
 }
 
+// warp_find for a bin count fixed at compile time (NB = 4096, 1024 or 512),
+// everything in registers: lane l sums bins [l NB/32, (l + 1) NB/32), reading
+// its 16-byte words in a lane-rotated order so that the warp's loads spread
+// over eight bank groups instead of one; the owning lane's bins are then split
+// over the warp.  Every lane returns the bin holding rank r and the rank left
+// within it (bin 0, rank 0 when r is not below the total).
+template <int NB>
+__device__ __noinline__ void warp_find_t(const uint32_t* h, uint32_t r, uint32_t& bin, uint32_t& rest) {
+  constexpr int kPer = NB / 32;                 // bins per lane: 128, 32, 16
+  constexpr int kV = kPer / 4;                  // 16-byte words per lane
+  constexpr int kSub = kPer >= 32 ? kPer / 32 : 1;  // second-level bins per lane
+  static_assert(kSub == 1 || kSub == 4, "second level");
+  const int lane = threadIdx.x & 31;
+  const uint4* hv = reinterpret_cast<const uint4*>(h + lane * kPer);
+  uint32_t local = 0;
+#pragma unroll
+  for (int k = 0; k < kV; ++k) {
+    const uint4 v = hv[(k + lane) & (kV - 1)];
+    local += (v.x + v.y) + (v.z + v.w);
+  }
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t own = __ballot_sync(0xffffffffu, r >= incl - local && r < incl);
+  const int L1 = own ? __ffs(own) - 1 : 0;
+  const uint32_t r1 = r - __shfl_sync(0xffffffffu, incl - local, L1);
+  const bool act = lane * kSub < kPer;
+  const int base = L1 * kPer + lane * kSub;
+  uint32_t c[kSub];
+  if (kSub == 4) {
+    const uint4 v = act ? *reinterpret_cast<const uint4*>(h + base) : make_uint4(0, 0, 0, 0);
+    c[0] = v.x, c[kSub > 1 ? 1 : 0] = v.y, c[kSub > 2 ? 2 : 0] = v.z, c[kSub > 3 ? 3 : 0] = v.w;
+  } else {
+    c[0] = act ? h[base] : 0u;
+  }
+  uint32_t loc2 = 0;
+#pragma unroll
+  for (int k = 0; k < kSub; ++k) loc2 += c[k];
+  uint32_t inc2 = loc2;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc2, o);
+    if (lane >= o) inc2 += t;
+  }
+  const bool mine = act && r1 >= inc2 - loc2 && r1 < inc2;
+  uint32_t fb = 0, fr = 0, acc = inc2 - loc2;
+  bool found = false;
+#pragma unroll
+  for (int k = 0; k < kSub; ++k) {
+    if (!found && r1 < acc + c[k]) fb = (uint32_t)(base + k), fr = r1 - acc, found = true;
+    acc += c[k];
+  }
+  const uint32_t who = __ballot_sync(0xffffffffu, mine);
+  const int src = who ? __ffs(who) - 1 : 0;
+  bin = __shfl_sync(0xffffffffu, fb, src);
+  rest = __shfl_sync(0xffffffffu, fr, src);
+}
+
 // Per signal: first digit of every threshold (warp m for threshold m).
 __global__ void __launch_bounds__(kQT) k_qsel1(const QSig* __restrict__ sigs, QWork w, int M, int L) {
   __shared__ __align__(16) uint32_t sh[kQB];
@@ -565,194 +626,355 @@ __global__ void __launch_bounds__(kQT) k_qsel2(const QSig* __restrict__ sigs, QW
 // One CTA per signal (persistent over the signals), for signals up to
 // kQOneMax samples when no bit planes are wanted: the streaming form's steps
 // in one launch, with x read from HBM once --
-//   1. the first-digit histogram in shared memory (x from HBM);
-//   2. each threshold's bin and rank within it (one warp per threshold);
-//   3. x again (still in L2: the CTA read it just before): every level its
-//      first digit decides is written, the rest go to the signal's candidate
-//      list (key, index | sign);
-//   4. two radix passes over the candidates (digits 18..9, 8..0, one
+//   1. the first-digit histogram in shared memory (x from HBM); a non-finite
+//      sample lands in the top 16 bins (bit patterns from 0x7F800000 up);
+//   2. each threshold's bin and rank within it (all threads: a scan of the
+//      bins' 16-bin sums);
+//   3. the level table: for every 13-bit key (sign, first digit) the signed
+//      level its first digit decides, or kQMark where the digit is a
+//      threshold's (the sample is a candidate);
+//   4. x again (still in L2, read last chunk first so the lines the CTA read
+//      most recently come first): each sample's level, candidates to the
+//      signal's list (key, then index | sign) -- at b = 2 (about 1 % of the
+//      samples) each thread appends to its own column, so no step of the
+//      pass waits on another thread; at b = 4 (about 10 %) the list is
+//      filled densely, one shared atomic per warp and chunk;
+//   5. two radix passes over the candidates (digits 18..9, 8..0, one
 //      histogram per distinct prefix) give the exact thresholds;
-//   5. the candidates' levels.
-// No grid-wide step: a signal's chain is the CTA's own.
+//   6. the candidates' levels.
+// Steps 5 and 6 read the list as columns: entry i * kQOC + t is thread t's.
+// It has qone_rows(n) rows (no thread sees more samples than that): keys in
+// the first kQOC * rows words, their index | sign in the next.
+// Four CTAs per SM, so that a batch of up to 4 x #SM signals is resident at
+// once; each thread holds two chunks of loads in flight (the next chunk's
+// loads are issued before the current one is processed).  No grid-wide
+// step: a signal's chain is the CTA's own.
 constexpr int kQOneMax = 1 << 18;
-constexpr int kQOT = 512;  // threads per CTA of k_qone
+constexpr int kQOC = 256;                  // threads of k_qone
+constexpr int kQOV = 4;                    // float4 per thread and chunk
+constexpr uint32_t kQOChunk = kQOV * kQOC; // float4 per chunk (16 KB)
+constexpr int kQOLV = 4;                   // float4 per thread and chunk of step 4
+constexpr int kQTE = kQB / kQOC;           // table entries per thread and sign
+constexpr uint32_t kQMark = 0x80u;         // level byte of a candidate (levels are -7..7)
+constexpr int kQOneRound = 4;              // CTAs per SM in one round of signals
+static_assert(kQTE % 4 == 0, "table words per thread");
+
+// Rows of k_qone's column-major candidate list: a consumer thread sees at
+// most 4 ceil(n4 / kQOC) + ceil((n - 4 n4) / kQOC) <= n / kQOC + 5 samples.
+__host__ __device__ constexpr uint32_t qone_rows(uint32_t n) { return n / kQOC + 8; }
+static_assert(kQOC * 8 <= kQCandSlack, "the columns fit a list of n + kQCandSlack entries");
+
+__device__ __forceinline__ void qone_bar() { __syncthreads(); }
+
+// The level table of step 3 for first digits [kQTE * t, kQTE * (t + 1)):
+// bytes 0..4095 for x >= 0, 4096..8191 for x < 0 (index = bits >> 19).
+template <int M>
+__device__ __forceinline__ void qone_table(uint8_t* tab, const uint32_t* pre) {
+  const uint32_t h0 = (uint32_t)(kQTE * threadIdx.x);
+  uint32_t lv0 = 0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) lv0 += pre[m] < h0 ? 1u : 0u;
+  uint32_t w[kQTE / 4], cm = 0;  // levels (bytes) and candidate entries (bits)
+#pragma unroll
+  for (int k = 0; k < kQTE / 4; ++k) w[k] = lv0 * 0x01010101u;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const uint32_t d = pre[m] - h0;
+    if (d < (uint32_t)kQTE) {  // a threshold digit in this thread's range
+      cm |= 1u << d;
+#pragma unroll
+      for (int j = 0; j < kQTE; ++j)
+        if ((uint32_t)j > d) w[j >> 2] += 1u << (8 * (j & 3));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kQTE / 4; ++k) {
+    uint32_t mk = 0;  // 0xFF in each candidate byte
+#pragma unroll
+    for (int e = 0; e < 4; ++e) mk |= ((cm >> (4 * k + e)) & 1u) ? 0xFFu << (8 * e) : 0u;
+    // -l per byte without borrows across bytes: (0x80 - l) ^ 0x80 for l <= 7
+    const uint32_t neg = (0x80808080u - w[k]) ^ 0x80808080u;
+    reinterpret_cast<uint32_t*>(tab)[kQTE / 4 * threadIdx.x + k] = (w[k] & ~mk) | (0x80808080u & mk);
+    reinterpret_cast<uint32_t*>(tab + kQB)[kQTE / 4 * threadIdx.x + k] = (neg & ~mk) | (0x80808080u & mk);
+  }
+}
+
+// 0x80 in each byte of p that is kQMark (bit 7 set, bit 6 clear: negative
+// levels are 0xF9..0xFF, positive ones 0..7).
+__device__ __forceinline__ uint32_t qone_marks(uint32_t p) { return p & ~(p << 1) & 0x80808080u; }
+
+// The level byte of one sample (FP32 bits b): a lookup of its sign and first
+// digit.
+__device__ __forceinline__ uint32_t qone_level(uint32_t b, const uint8_t* tab) { return tab[b >> 19]; }
+
+__device__ __forceinline__ void qone_load(float4 (&v)[kQOV], const float4* x4, uint32_t c0, uint32_t n4) {
+#pragma unroll
+  for (int k = 0; k < kQOV; ++k) {
+    const uint32_t i = c0 + k * kQOC + threadIdx.x;
+    v[k] = i < n4 ? x4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ void qone_hist(const float4 (&v)[kQOV], uint32_t* h, uint32_t c0, uint32_t n4) {
+#pragma unroll
+  for (int k = 0; k < kQOV; ++k) {
+    if (c0 + k * kQOC + threadIdx.x >= n4) continue;
+    atomicAdd(&h[(__float_as_uint(v[k].x) & 0x7FFFFFFFu) >> 19], 1u);
+    atomicAdd(&h[(__float_as_uint(v[k].y) & 0x7FFFFFFFu) >> 19], 1u);
+    atomicAdd(&h[(__float_as_uint(v[k].z) & 0x7FFFFFFFu) >> 19], 1u);
+    atomicAdd(&h[(__float_as_uint(v[k].w) & 0x7FFFFFFFu) >> 19], 1u);
+  }
+}
+
+// Step 4 on one chunk: levels stored four to a word, candidates appended.
+// kCols (b = 2, about 1 % candidates): each thread appends to its own column
+// (cnt: the entries it holds), so no step waits on another thread.  Else
+// (b = 4, about 10 %): the list is filled densely from entry 0, each warp
+// reserving its room with one shared atomic (ncand).
+template <int V, bool kCols>
+__device__ __forceinline__ void qone_levels(const float4 (&v)[V], uint32_t c0, uint32_t n4, const uint8_t* tab,
+                                            uint32_t* q4, uint32_t* cand, uint32_t* cidx, uint32_t& cnt,
+                                            uint32_t* ncand) {
+  uint32_t mk[V], any = 0;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const uint32_t i = c0 + k * kQOC + threadIdx.x;
+    const uint32_t l0 = qone_level(__float_as_uint(v[k].x), tab), l1 = qone_level(__float_as_uint(v[k].y), tab);
+    const uint32_t l2 = qone_level(__float_as_uint(v[k].z), tab), l3 = qone_level(__float_as_uint(v[k].w), tab);
+    const uint32_t p = __byte_perm(__byte_perm(l0, l1, 0x0040), __byte_perm(l2, l3, 0x0040), 0x5410);
+    mk[k] = i < n4 ? qone_marks(p) : 0u;
+    any |= mk[k];
+    if (i < n4) __stcs(q4 + i, p);  // a candidate's byte is rewritten in step 6
+  }
+  uint32_t slot;
+  if (kCols) {
+    if (any == 0) return;
+    slot = cnt;
+  } else {
+    if (__ballot_sync(0xffffffffu, any != 0) == 0) return;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) c += __popc(mk[k]);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(ncand, incl);
+    slot = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+    if (c == 0) return;
+  }
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (mk[k] == 0) continue;
+    const uint32_t b[4] = {__float_as_uint(v[k].x), __float_as_uint(v[k].y), __float_as_uint(v[k].z),
+                           __float_as_uint(v[k].w)};
+    const uint32_t i4 = 4 * (c0 + k * kQOC + threadIdx.x);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((mk[k] >> (8 * e + 7)) & 1u) {
+        const uint32_t a = kCols ? slot * kQOC + threadIdx.x : slot;
+        cand[a] = b[e] & 0x7FFFFFFFu;
+        cidx[a] = (i4 + e) | (b[e] & 0x80000000u);
+        ++slot;
+      }
+  }
+  if (kCols) cnt = slot;
+}
 
 template <int M>
-__global__ void __launch_bounds__(kQOT, 2) k_qone(const QSig* __restrict__ sigs, int nsig, QWork w, int L,
-                                              uint32_t* __restrict__ status) {
+__global__ void __launch_bounds__(kQOC, kQOneRound) k_qone(const QSig* __restrict__ sigs, int nsig, QWork w,
+                                                             int L, uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) uint32_t qs[];  // max(kQB, M * 1024) words
-  __shared__ uint32_t pre_s[7], rank_s[7], ncand_s;
+  __shared__ uint32_t pre_s[7], rank_s[7], r_s[7], wsum_s[kQOC / 32], ncand_s;
   __shared__ int owner_s[7];
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tid = threadIdx.x;
   for (int sig = blockIdx.x; sig < nsig; sig += gridDim.x) {
     const QSig s = sigs[sig];
+    const uint32_t n = (uint32_t)s.n;
     uint32_t* cand = w.cand[sig];
-    uint32_t* cidx = cand + s.n;
+    uint32_t* cidx = cand + kQOC * qone_rows(n);
     // ---- 1. first-digit histogram
-    for (int i = threadIdx.x; i < kQB; i += kQOT) qs[i] = 0;
-    __syncthreads();
-    int bad = 0;
+    for (uint32_t i = tid; i < (uint32_t)kQB / 4; i += kQOC) reinterpret_cast<uint4*>(qs)[i] = make_uint4(0, 0, 0, 0);
+    if (tid < (uint32_t)M) {
+      const int64_t idx = ((2 * (int64_t)tid + 1) * s.n) / L;
+      r_s[tid] = (uint32_t)(idx > s.n - 1 ? s.n - 1 : idx);
+      pre_s[tid] = 0, rank_s[tid] = 0;
+    }
+    if (tid == 0) ncand_s = 0;
+    qone_bar();
     const bool vec = (reinterpret_cast<uintptr_t>(s.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(s.q) & 3) == 0;
-    const int64_t n4 = vec ? s.n >> 2 : 0;
+    const uint32_t n4 = vec ? n >> 2 : 0;
     const float4* x4 = reinterpret_cast<const float4*>(s.x);
-    for (int64_t c0 = 0; c0 < n4; c0 += 8 * kQOT) {
-      float4 v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int64_t i = c0 + k * kQOT + threadIdx.x;
-        if (i < n4) v[k] = x4[i];
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (c0 + k * kQOT + threadIdx.x >= n4) continue;
-        const uint32_t u0 = __float_as_uint(v[k].x) & 0x7FFFFFFFu, u1 = __float_as_uint(v[k].y) & 0x7FFFFFFFu;
-        const uint32_t u2 = __float_as_uint(v[k].z) & 0x7FFFFFFFu, u3 = __float_as_uint(v[k].w) & 0x7FFFFFFFu;
-        q_bad(u0, bad), q_bad(u1, bad), q_bad(u2, bad), q_bad(u3, bad);
-        atomicAdd(&qs[u0 >> 19], 1u);
-        atomicAdd(&qs[u1 >> 19], 1u);
-        atomicAdd(&qs[u2 >> 19], 1u);
-        atomicAdd(&qs[u3 >> 19], 1u);
+    const uint32_t nc4 = (n4 + kQOChunk - 1) / kQOChunk;  // chunks of the float4 passes
+    {
+      float4 va[kQOV], vb[kQOV];
+      if (nc4 > 0) qone_load(va, x4, 0, n4);
+      for (uint32_t c = 0; c < nc4; c += 2) {
+        if (c + 1 < nc4) qone_load(vb, x4, (c + 1) * kQOChunk, n4);
+        qone_hist(va, qs, c * kQOChunk, n4);
+        if (c + 1 < nc4) {
+          if (c + 2 < nc4) qone_load(va, x4, (c + 2) * kQOChunk, n4);
+          qone_hist(vb, qs, (c + 1) * kQOChunk, n4);
+        }
       }
     }
-    for (int64_t j = (n4 << 2) + threadIdx.x; j < s.n; j += kQOT) {
-      const uint32_t u = __float_as_uint(s.x[j]) & 0x7FFFFFFFu;
-      q_bad(u, bad);
-      atomicAdd(&qs[u >> 19], 1u);
+    for (uint32_t j = 4 * n4 + tid; j < n; j += kQOC) atomicAdd(&qs[(__float_as_uint(s.x[j]) & 0x7FFFFFFFu) >> 19], 1u);
+    qone_bar();
+    if (tid < 16 && qs[kQB - 16 + tid] != 0) atomicOr(status, TDE_ST_NONFINITE);
+    // ---- 2. each threshold's bin: thread t sums bins [16 t, 16 t + 16)
+    // (words read in a lane-rotated order: eight bank groups per warp)
+    {
+      const uint4* hv = reinterpret_cast<const uint4*>(qs + 16 * tid);
+      uint32_t loc = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint4 v = hv[(k + lane) & 3];
+        loc += (v.x + v.y) + (v.z + v.w);
+      }
+      uint32_t incl = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) wsum_s[warp] = incl;
+      qone_bar();
+      uint32_t before = 0;
+      for (int k = 0; k < warp; ++k) before += wsum_s[k];
+      const uint32_t P = before + incl - loc;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const uint32_t r = r_s[m];
+        if (r >= P && r - P < loc) {  // this thread's bins hold rank r
+          uint32_t acc = P;
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t c = qs[16 * tid + j];
+            if (r < acc + c) {
+              pre_s[m] = 16 * tid + j, rank_s[m] = r - acc;
+              break;
+            }
+            acc += c;
+          }
+        }
+      }
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, TDE_ST_NONFINITE);
-    // ---- 2. the bin of each threshold's rank
-    if (warp < M) {
-      const int64_t idx = ((2 * (int64_t)warp + 1) * s.n) / L;
-      const uint32_t r = (uint32_t)(idx > s.n - 1 ? s.n - 1 : idx);
-      uint32_t bin, rest;
-      warp_find(qs, kQB, r, bin, rest);
-      if ((threadIdx.x & 31) == 0) pre_s[warp] = bin, rank_s[warp] = rest;
-    }
-    if (threadIdx.x == 0) ncand_s = 0;
-    __syncthreads();
-    // ---- 3. decided levels; candidates to the list
+    qone_bar();
+    // ---- 3. the level table (over the histogram, no longer needed)
+    uint8_t* tab = reinterpret_cast<uint8_t*>(qs);
     {
       uint32_t pre[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) pre[m] = pre_s[m];
-      for (int64_t c0 = 0; c0 < n4; c0 += 8 * kQOT) {
-        float4 v[8];
+      qone_table<M>(tab, pre);
+    }
+    qone_bar();
+    // ---- 4. levels; candidates to the list (last chunk first)
+    constexpr bool kCols = M == 1;
+    uint32_t cnt = 0;
+    {
+      uint32_t* q4 = reinterpret_cast<uint32_t*>(s.q);
+      // one chunk of loads in flight: the candidate appends keep a chunk's
+      // samples live, and two chunks would not fit the CTA's registers
+      constexpr int V2 = kQOLV;
+      const uint32_t ncl = (n4 + V2 * kQOC - 1) / (V2 * kQOC);
+      for (uint32_t c = ncl; c-- > 0;) {
+        float4 v[V2];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t i = c0 + k * kQOT + threadIdx.x;
+        for (int k = 0; k < V2; ++k) {
+          const uint32_t i = c * V2 * kQOC + k * kQOC + tid;
           v[k] = i < n4 ? x4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        uint32_t hits = 0;  // bit 4k + e: element e of load k
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t i = c0 + k * kQOT + threadIdx.x;
-          if (i >= n4) continue;
-          const uint32_t b[4] = {__float_as_uint(v[k].x), __float_as_uint(v[k].y), __float_as_uint(v[k].z),
-                                 __float_as_uint(v[k].w)};
-          uint32_t packed = 0;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const uint32_t hi = (b[e] & 0x7FFFFFFFu) >> 19;
-            bool c = false;
-            int lv = 0;
-#pragma unroll
-            for (int m = 0; m < M; ++m) c |= hi == pre[m], lv += hi > pre[m];
-            hits |= (uint32_t)c << (4 * k + e);
-            packed |= ((uint32_t)((b[e] >> 31) ? -lv : lv) & 0xFFu) << (8 * e);
-          }
-          reinterpret_cast<uint32_t*>(s.q)[i] = packed;  // a candidate's byte is rewritten in step 5
-        }
-        if (hits) {
-          uint32_t slot = atomicAdd(&ncand_s, (uint32_t)__popc(hits));
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float f[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-            const uint32_t i4 = (uint32_t)(4 * (c0 + k * kQOT + threadIdx.x));
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (hits >> (4 * k + e) & 1u) {
-                cand[slot] = __float_as_uint(f[e]) & 0x7FFFFFFFu;
-                cidx[slot] = (i4 + e) | (f[e] < 0.f ? 0x80000000u : 0u);
-                ++slot;
-              }
-          }
-        }
+        qone_levels<V2, kCols>(v, c * V2 * kQOC, n4, tab, q4, cand, cidx, cnt, &ncand_s);
       }
-      for (int64_t j = (n4 << 2) + threadIdx.x; j < s.n; j += kQOT) {
-        const float f = s.x[j];
-        const uint32_t u = __float_as_uint(f) & 0x7FFFFFFFu, hi = u >> 19;
-        bool c = false;
-        int lv = 0;
-#pragma unroll
-        for (int m = 0; m < M; ++m) c |= hi == pre[m], lv += hi > pre[m];
-        if (c) {
-          const uint32_t slot = atomicAdd(&ncand_s, 1u);
-          cand[slot] = u;
-          cidx[slot] = (uint32_t)j | (f < 0.f ? 0x80000000u : 0u);
+      for (uint32_t j = 4 * n4 + tid; j < n; j += kQOC) {
+        const uint32_t b = __float_as_uint(s.x[j]);
+        const uint32_t l = qone_level(b, tab);
+        if (l == kQMark) {
+          const uint32_t a = kCols ? cnt++ * kQOC + tid : atomicAdd(&ncand_s, 1u);
+          cand[a] = b & 0x7FFFFFFFu;
+          cidx[a] = j | (b & 0x80000000u);
         } else {
-          s.q[j] = (int8_t)(sign_of(f) * lv);
+          s.q[j] = (int8_t)l;
         }
       }
     }
-    __syncthreads();  // the candidate list (global, this CTA's writes) and its count
-    const uint32_t nc = ncand_s;
-    // ---- 4. exact thresholds from the candidates
+    qone_bar();  // the table is read no more (step 5 reuses its words)
+    if (!kCols) {  // the dense list read as columns: entry i * kQOC + t is thread t's
+      const uint32_t nc = ncand_s;
+      cnt = nc > tid ? (nc - tid + kQOC - 1) / kQOC : 0u;
+    }
+    // ---- 5. exact thresholds from the candidates
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-      const int nbins = pass == 0 ? 1024 : 512, shift = pass == 0 ? 9 : 0, hs = pass == 0 ? 19 : 9;
+      const int shift = pass == 0 ? 9 : 0, hs = pass == 0 ? 19 : 9;
       const uint32_t mask = pass == 0 ? 1023u : 511u;
-      if (threadIdx.x < 7) {  // thresholds with equal prefixes share the first one's histogram
-        const int m = threadIdx.x;
+      if (tid < 7) {  // thresholds with equal prefixes share the first one's histogram
+        const int m = tid;
         int o = m;
         if (m < M)
           for (int k = m - 1; k >= 0; --k)
             if (pre_s[k] == pre_s[m]) o = k;
         owner_s[m] = o;
       }
-      for (int i = threadIdx.x; i < M * 1024; i += kQOT) qs[i] = 0;
-      __syncthreads();
+      for (uint32_t i = tid; i < (uint32_t)M * 1024 / 4; i += kQOC)
+        reinterpret_cast<uint4*>(qs)[i] = make_uint4(0, 0, 0, 0);
+      qone_bar();
       uint32_t pre[M];
       int own[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) pre[m] = pre_s[m], own[m] = owner_s[m];
-      for (uint32_t i = threadIdx.x; i < nc; i += kQOT) {
-        const uint32_t u = cand[i];
-        const uint32_t hi = u >> hs;
-        int mm = -1;
+      for (uint32_t i0 = 0; i0 < cnt; i0 += 8) {  // the thread's own column
+        uint32_t u[8];
 #pragma unroll
-        for (int m = M - 1; m >= 0; --m)
-          if (hi == pre[m]) mm = own[m];
-        if (mm >= 0) atomicAdd(&qs[mm * 1024 + ((u >> shift) & mask)], 1u);
+        for (int k = 0; k < 8; ++k) u[k] = i0 + k < cnt ? cand[(i0 + k) * kQOC + tid] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (i0 + k >= cnt) break;
+          const uint32_t hi = u[k] >> hs;
+          int mm = -1;
+#pragma unroll
+          for (int m = M - 1; m >= 0; --m)
+            if (hi == pre[m]) mm = own[m];
+          if (mm >= 0) atomicAdd(&qs[mm * 1024 + ((u[k] >> shift) & mask)], 1u);
+        }
       }
-      __syncthreads();
+      qone_bar();
       if (warp < M) {
         uint32_t bin, rest;
-        warp_find(qs + owner_s[warp] * 1024, nbins, rank_s[warp], bin, rest);
-        if ((threadIdx.x & 31) == 0) {
+        if (pass == 0)
+          warp_find_t<1024>(qs + owner_s[warp] * 1024, rank_s[warp], bin, rest);
+        else
+          warp_find_t<512>(qs + owner_s[warp] * 1024, rank_s[warp], bin, rest);
+        if (lane == 0) {
           pre_s[warp] = (pre_s[warp] << (pass == 0 ? 10 : 9)) | bin;
           rank_s[warp] = rest;
         }
       }
-      __syncthreads();
+      qone_bar();
     }
-    // ---- 5. the candidates' levels (loads batched ahead of the byte stores,
+    // ---- 6. the candidates' levels (loads batched ahead of the byte stores,
     // which could alias the list)
     {
       uint32_t t[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) t[m] = pre_s[m];
-      constexpr int kFixB = 16;
-      for (uint32_t i0 = threadIdx.x; i0 < nc; i0 += kFixB * kQOT) {
+      constexpr int kFixB = 8;
+      for (uint32_t i0 = 0; i0 < cnt; i0 += kFixB) {
         uint32_t u[kFixB], c[kFixB];
 #pragma unroll
         for (int k = 0; k < kFixB; ++k) {
-          const uint32_t i = i0 + k * kQOT;
-          u[k] = i < nc ? cand[i] : 0u;
-          c[k] = i < nc ? cidx[i] : 0u;
+          const uint32_t i = i0 + k;
+          u[k] = i < cnt ? cand[i * kQOC + tid] : 0u;
+          c[k] = i < cnt ? cidx[i * kQOC + tid] : 0u;
         }
 #pragma unroll
         for (int k = 0; k < kFixB; ++k) {
-          if (i0 + k * kQOT >= nc) break;
+          if (i0 + k >= cnt) break;
           int lv = 0;
 #pragma unroll
           for (int m = 0; m < M; ++m) lv += u[k] >= t[m];
@@ -760,7 +982,7 @@ __global__ void __launch_bounds__(kQOT, 2) k_qone(const QSig* __restrict__ sigs,
         }
       }
     }
-    __syncthreads();  // shared state is reused by the next signal
+    qone_bar();  // shared state is reused by the next signal
   }
 }
 
@@ -973,18 +1195,18 @@ cudaError_t launch_quantize_stream(const QSig* d_sigs, const QPlanes* d_planes, 
   if (bits != 2 && bits != 4) return cudaErrorInvalidValue;
   const int M = (1 << (bits - 1)) - 1, L = (1 << bits) - 1;
   if (d_planes == nullptr && max_n <= kQOneMax) {
-    // one CTA per signal, x read from HBM once: two CTAs per SM, the signals
-    // dealt in equal rounds, so that the signals in flight (one per CTA)
-    // stay within L2 until their second read
+    // one CTA per signal, x read from HBM once: kQOneRound CTAs per SM, the
+    // signals dealt in equal rounds, so that the signals in flight (one per
+    // CTA) stay within L2 until their second read
     const size_t smem = sizeof(uint32_t) * (M == 1 ? kQB : 7 * 1024);
     auto kern = M == 1 ? k_qone<1> : k_qone<7>;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t cap = 2 * (int64_t)sms;
+    const int64_t cap = kQOneRound * (int64_t)sms;
     const int64_t rounds = ceil_div64(nsig, cap);
     const int grid = (int)ceil_div64(nsig, rounds);
-    kern<<<grid, kQOT, smem, st>>>(d_sigs, nsig, w, L, d_status);
+    kern<<<grid, kQOC, smem, st>>>(d_sigs, nsig, w, L, d_status);
     TDE_COUNT_LAUNCH(1);
     return cudaGetLastError();
   }

@@ -70,6 +70,24 @@ def test_quantize_heavy_ties_and_scales(ctx, bits):
     assert np.array_equal(got.cpu().numpy(), oracle.quantize(x, bits))
 
 
+@pytest.mark.parametrize("bits", [2, 4])
+@pytest.mark.parametrize("xoff,qoff", [(1, 0), (0, 3), (3, 1)])
+def test_quantize_unaligned_buffers(ctx, bits, xoff, qoff):
+    """x not 16-byte aligned or q not 4-byte aligned: the one-launch
+    quantizer takes its per-sample path for the whole signal."""
+    rng = np.random.default_rng(31 * xoff + qoff + bits)
+    n = 9000 + 7
+    x = rng.standard_normal(n).astype(np.float32)
+    x[::13] = 0.0
+    xb = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+    xb[xoff:xoff + n] = _gpu(x)
+    qb = torch.zeros(n + 4, dtype=torch.int8, device="cuda")
+    got = ctx.quantize(xb[xoff:xoff + n], bits, q_out=qb[qoff:qoff + n])
+    ctx.sync()
+    assert np.array_equal(got.cpu().numpy(), oracle.quantize(x, bits))
+    assert int(qb[:qoff].abs().sum()) == 0 and int(qb[qoff + n:].abs().sum()) == 0
+
+
 @pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
 @pytest.mark.parametrize("bits", [1, 2, 4])
 def test_quantize_nonfinite_is_reported(ctx, bits, bad):

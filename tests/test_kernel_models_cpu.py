@@ -190,3 +190,99 @@ def test_scores_pair_walk_stays_in_bounds_and_scores_every_bin():
         got = _scores_pair_model(fx, fy, Lf, 0.5)
         assert not np.isnan(got).any(), Lf
         assert np.abs(got - ref).max() < 1e-9, Lf
+
+
+def _qone_table_model(pre, kqte=16):
+    """k_qone's level table built the kernel's way: thread t owns first
+    digits [16 t, 16 t + 16) as four words of bytes, starts every byte at the
+    count of threshold digits below its range, adds 1 to the bytes above each
+    threshold digit inside its range and marks that digit's byte; negative
+    levels are (0x80 - l) ^ 0x80 per byte; a marked byte is 0x80 in both
+    halves.  Returns the 8192 table bytes (index = float bits >> 19)."""
+    tab = np.zeros(8192, np.uint8)
+    for t in range(4096 // kqte):
+        h0 = kqte * t
+        lv0 = sum(1 for p in pre if p < h0)
+        w = [lv0 * 0x01010101] * (kqte // 4)
+        cm = 0
+        for p in pre:
+            d = (p - h0) & 0xFFFFFFFF
+            if d < kqte:
+                cm |= 1 << d
+                for j in range(kqte):
+                    if j > d:
+                        w[j >> 2] += 1 << (8 * (j & 3))
+        for k in range(kqte // 4):
+            mk = 0
+            for e in range(4):
+                if (cm >> (4 * k + e)) & 1:
+                    mk |= 0xFF << (8 * e)
+            neg = ((0x80808080 - w[k]) & 0xFFFFFFFF) ^ 0x80808080
+            pos_w = (w[k] & ~mk & 0xFFFFFFFF) | (0x80808080 & mk)
+            neg_w = (neg & ~mk & 0xFFFFFFFF) | (0x80808080 & mk)
+            for e in range(4):
+                tab[h0 + 4 * k + e] = (pos_w >> (8 * e)) & 0xFF
+                tab[4096 + h0 + 4 * k + e] = (neg_w >> (8 * e)) & 0xFF
+    return tab
+
+
+def test_qone_level_table_matches_the_first_digit_rule():
+    """Every table byte equals its definition: 0x80 where the first digit is
+    a threshold's (the sample is a candidate), else sign * #{m : digit >
+    digit of t_m} as a two's-complement byte -- for sorted threshold digits
+    drawn at random, with repeats, at range edges and several in one
+    thread's range."""
+    rng = np.random.default_rng(5)
+    cases = [[0], [4095], [15, 16], [16, 16, 16, 17, 31, 32, 47], [0, 0, 0, 0, 0, 0, 0]]
+    for _ in range(40):
+        M = int(rng.choice([1, 7]))
+        cases.append(sorted(int(v) for v in rng.integers(0, 4096, M)))
+    for _ in range(20):  # clustered, like the thresholds of Gaussian data
+        base = int(rng.integers(900, 1100))
+        cases.append(sorted(base + int(v) for v in rng.integers(0, 40, 7)))
+    hi = np.arange(4096)
+    for pre in cases:
+        tab = _qone_table_model(pre)
+        pa = np.array(pre)
+        cand = (hi[:, None] == pa[None, :]).any(1)
+        lv = (hi[:, None] > pa[None, :]).sum(1)
+        want_pos = np.where(cand, 0x80, lv).astype(np.uint8)
+        want_neg = np.where(cand, 0x80, (-lv) & 0xFF).astype(np.uint8)
+        assert np.array_equal(tab[:4096], want_pos), pre
+        assert np.array_equal(tab[4096:], want_neg), pre
+
+
+def test_qone_marks_flag_exactly_the_candidate_bytes():
+    """qone_marks: p & ~(p << 1) & 0x80808080 has bit 7 of a byte set iff
+    the byte is 0x80, over every byte a table holds (levels -7..7 and the
+    mark) in every position of a word, with the neighbouring bytes'
+    carries."""
+    vals = [v & 0xFF for v in range(-7, 8)] + [0x80]
+    rng = np.random.default_rng(9)
+    for _ in range(4000):
+        b = [int(rng.choice(vals)) for _ in range(4)]
+        p = b[0] | b[1] << 8 | b[2] << 16 | b[3] << 24
+        m = p & ~((p << 1) & 0xFFFFFFFF) & 0x80808080
+        for e in range(4):
+            assert bool((m >> (8 * e + 7)) & 1) == (b[e] == 0x80), b
+
+
+def test_qone_candidate_columns_hold_every_sample_a_thread_sees():
+    """k_qone's candidate list is column-major, qone_rows(n) = n // 256 + 8
+    rows of 256 threads: no thread sees more samples than that in either
+    pass (float4 i = 1024 c + 256 k + t below n4, four samples each, then
+    the tail j = 4 n4 + t + 256 m, or every sample when x is unaligned), and
+    the two columns fit the list's 2 (n + 2048) words."""
+    T, V = 256, 4
+    ns = list(range(0, 3000)) + [65536, 65536 + 123, 262144, 262143, 9007]
+    for n in ns:
+        rows = n // T + 8
+        assert 2 * T * rows <= 2 * (n + 2048)
+        for vec in (True, False):
+            n4 = n >> 2 if vec else 0
+            per = np.zeros(T, np.int64)
+            idx = np.arange(n4)
+            np.add.at(per, idx % T, 4)
+            tail = np.arange(4 * n4, n)
+            np.add.at(per, (tail - 4 * n4) % T, 1)
+            assert per.max(initial=0) <= rows, (n, vec, per.max())
