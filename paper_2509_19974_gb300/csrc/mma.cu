@@ -919,16 +919,30 @@ __global__ void __launch_bounds__(kThreads, kCvCtasPerSm)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // weight blocks W_s[j][t][co][e], t = tap + 1 (zero blocks at t = 0, 10),
-  // two elements per store
-  for (int idx = threadIdx.x; idx < (kCvWBytes / 4); idx += kThreads) {
-    const int e2 = idx & 3, co = (idx >> 2) & (kCnnC - 1), jt = idx >> 7;
-    const int t = jt % kCvTaps, j = jt / kCvTaps, k = t - 1;
-    uint32_t v = 0;
-    if (k >= 0 && k < kCnnK) {
-      const int ci = 8 * j + 2 * e2;
-      v = (uint32_t)wbf[(co * kCnnC + ci) * kCnnK + k] | ((uint32_t)wbf[(co * kCnnC + ci + 1) * kCnnK + k] << 16);
+  // two elements per store: every load of the thread's share is issued
+  // before its first store (plain stores, so the loads are not held behind
+  // them)
+  {
+    constexpr int kPer = (kCvWBytes / 4 + kThreads - 1) / kThreads;
+    uint32_t v[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int idx = threadIdx.x + r * kThreads;
+      const int e2 = idx & 3, co = (idx >> 2) & (kCnnC - 1), jt = idx >> 7;
+      const int t = jt % kCvTaps, j = jt / kCvTaps, k = t - 1;
+      v[r] = 0;
+      if (idx < kCvWBytes / 4 && k >= 0 && k < kCnnK) {
+        const int ci = 8 * j + 2 * e2;
+        v[r] = (uint32_t)__ldg(wbf + (co * kCnnC + ci) * kCnnK + k) |
+               ((uint32_t)__ldg(wbf + (co * kCnnC + ci + 1) * kCnnK + k) << 16);
+      }
     }
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(wsm + 4u * (uint32_t)idx), "r"(v) : "memory");
+    uint32_t* wdst = reinterpret_cast<uint32_t*>(smem_raw + (wsm - raw));
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int idx = threadIdx.x + r * kThreads;
+      if (idx < kCvWBytes / 4) wdst[idx] = v[r];
+    }
   }
   // the next layer's zero rows: 0, 1 and [L/4 + 2, R') of each array
   if (!kLast) {
@@ -1114,8 +1128,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restri
   for (int idx = threadIdx.x; idx < 2 * kCnnC * 8; idx += kThreads) {
     const int e = idx & 7, co = (idx >> 3) & (kCnnC - 1), h = idx >> 8;
     const int k = 8 * h + e;
-    const uint16_t v = k < kCnnK ? wbf[co * kCnnK + k] : (uint16_t)0;
-    asm volatile("st.shared.u16 [%0], %1;" ::"r"(w_s + 2u * (uint32_t)idx), "h"(v) : "memory");
+    reinterpret_cast<uint16_t*>(sbase + kC1ABytes)[idx] = k < kCnnK ? __ldg(wbf + co * kCnnK + k) : (uint16_t)0;
   }
   const int qd = warp & 3, ch = warp >> 2;
   float bv[16];
