@@ -1360,7 +1360,7 @@ struct CnnPlan {
                                        B.dw<float>(o_out[kCnnLayers - 1]), qe, status, st);
       if (e == cudaSuccess && scores)
         e = launch_cnn_scores(B.dw<float>(o_out[kCnnLayers - 1]), P, Lf, m->params,
-                              B.dw<float>(o_scores), st, true);
+                              B.dw<float>(o_scores), st, true, status);
       return e;
     }
     cudaError_t e = launch_cnn_decimate(q, n, 2 * P, B.dw<float>(o_d), st);
@@ -1751,7 +1751,8 @@ cudaError_t learned_launch(tde_ctx* ctx, const tde_model* m, const LearnedWork& 
   if (e == cudaSuccess && fused)
     e = launch_cnn_scores_propose(B.dw<float>(w.C.o_out[kCnnLayers - 1]), P, w.C.Lf, m->params,
                                   B.dw<float>(w.C.o_scores), cent, marg, jobs,
-                                  B.dw<int32_t>(w.o_cwin), n, B.dw<int32_t>(w.o_njobs), st);
+                                  B.dw<int32_t>(w.o_cwin), n, B.dw<int32_t>(w.o_njobs), st,
+                                  ctx->d_status);
   if (e == cudaSuccess && !fused) {
     e = launch_cnn_topk(B.dw<float>(w.C.o_scores), P, w.C.Lf, cent, marg, st);
     if (e == cudaSuccess) {

@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "cnn.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -424,19 +425,16 @@ __device__ __forceinline__ void topk_warp(const float (&v)[PER], int nb, int Lf,
   margin = top / sum;
 }
 
-// Short features (Lf <= 256): one CTA per pair with both features whole in
+// Short features (Lf <= 256) in FP32 FMA (the training forward's
+// channel-major features): one CTA per pair with both features whole in
 // shared memory (32 zero rows padding y on both sides), 16 warps, warp w
 // taking the bin groups w and w + ngroups/2: their overlaps add up to about
 // Lf, so every warp does the same work and the grid is one wave.  The inner
-// loop and the lane reduction are those of k_scores.  With kTop the CTA
-// also keeps its scores in shared memory and warp 0 then takes the pair's
-// top 8 (topk_warp, as k_topk) and writes its centres, margin and window
-// jobs (the learned step's proposal in one launch).
+// loop and the lane reduction are those of k_scores.
 constexpr int kSpWarps = 16;
 constexpr int kSpMaxLf = kCnnFusedMaxLf;
 constexpr int kSpPad = 32;
 constexpr int kSpSmem = ((kSpMaxLf + 16) + (kSpMaxLf + 2 * kSpPad)) * kScRow * 4;
-constexpr int kSpTopSmem = kSpSmem + 2 * kSpMaxLf * 4;  // + the scores
 
 struct TopOut {
   int32_t* centres;  // [P][8]
@@ -447,14 +445,13 @@ struct TopOut {
   int32_t* njobs;    // [P]: jobs of the polyphase windows kernel
 };
 
-template <bool kPosMajor, bool kTop>
+template <bool kPosMajor>
 __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* __restrict__ feat, int Lf,
                                                                   const float* __restrict__ params,
-                                                                  float* __restrict__ scores, TopOut top) {
+                                                                  float* __restrict__ scores) {
   extern __shared__ __align__(16) float sm[];
   float* xs = sm;                               // [Lf + 16][kScRow]: fx at row i
   float* ys = sm + (kSpMaxLf + 16) * kScRow;    // [Lf + 64][kScRow]: fy at row i + kSpPad
-  float* ss = sm + kSpSmem / 4;                 // kTop: [2 Lf - 1] scores
   const int p = blockIdx.x;
   const int nb = 2 * Lf - 1;
   const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
@@ -516,14 +513,181 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* _
     }
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
     const int bin = kScG * g + ((lane >> 1) & (kScG - 1));
-    if ((lane & 1) == 0 && bin < nb) {
-      scores[(int64_t)p * nb + bin] = alpha * acc[0];
-      if (kTop) ss[bin] = alpha * acc[0];
-    }
+    if ((lane & 1) == 0 && bin < nb) scores[(int64_t)p * nb + bin] = alpha * acc[0];
   }
+}
+
+
+// Short features (Lf <= 256, position-major) on the tensor cores: per pair the
+// Gram matrix G[i][j] = sum_c fx[i][c] fy[j][c] (rows past Lf zero; two M = 128
+// tiles of N = 256, K = 32, FP32 in tensor memory) and the scores as its
+// diagonal sums, score[l] = alpha sum_i G[i][i + l].  Each FP32 feature is
+// split as f = hi + lo (hi = BF16(f), lo = BF16(f - hi)) and G accumulates
+// hi.hi + hi.lo + lo.hi (kind::f16, BF16 operands): what is left out, lo.lo
+// and the rounding of lo, is below 2^-16 of each product, whose terms are all
+// non-negative (ReLU features), so the scores keep about 16 bits -- the FP32
+// sums they replace keep about as many over 8192 terms.  The diagonal sums are
+// deterministic: warp w reads its 32 x 32 blocks of G (TMEM lanes of quadrant
+// w % 4, columns of half w / 4) in a fixed order, sums each block's 63
+// diagonals through a skewed shared-memory copy (row stride 33: the writes
+// and the diagonal reads are conflict-free) into its own row of partial
+// scores, and the eight rows are added in warp order.  Operands: per part
+// (x hi, x lo, y hi, y lo) four 8-channel chunks of 256 rows of 16 bytes,
+// K-major without swizzle (core matrices of 8 rows at 128 bytes, the next
+// chunk 4096 bytes on).  The skew copies reuse the operands' space once the
+// MMAs are done.  With kTop the epilogue is k_scores_pair's.
+constexpr int kStWarps = 8;
+constexpr int kStRows = 256;                       // rows of an operand (Lf padded with zeros)
+constexpr int kStChunk = kStRows * 16;             // one 8-channel chunk (4096 bytes)
+constexpr int kStOp = 4 * kStChunk;                // one part: 256 rows x 32 channels BF16
+constexpr int kStPart = 512;                       // partial scores per warp (lag + 255)
+constexpr int kStSkew = 32 * 33;                   // floats of a warp's skew copy
+constexpr int kStSmem = 4 * kStOp + kStWarps * kStPart * 4 + 2 * kSpMaxLf * 4 + 16 + 16 + 128;
+static_assert(kStWarps * kStSkew * 4 <= 4 * kStOp, "skew copies fit the operands' space");
+static_assert(kSpMaxLf <= kStRows, "features fit an operand");
+// kind::f16: D F32 (bit 4), A and B BF16 (bits 7, 10), both K-major, N = 256
+// (N >> 3 at bits 17-22), M = 128 (M >> 4 at bits 24-28).
+constexpr uint32_t kStIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void st_mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kStIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t st_pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+template <bool kTop>
+__global__ void __launch_bounds__(kStWarps * 32, 2) k_scores_tc(const float* __restrict__ feat, int Lf,
+                                                                const float* __restrict__ params,
+                                                                float* __restrict__ scores, TopOut top,
+                                                                uint32_t* __restrict__ status) {
+  extern __shared__ uint8_t st_raw[];
+  const uint32_t raw = smem_u32(st_raw);
+  const uint32_t base = (raw + 127u) & ~127u;
+  uint8_t* sb = st_raw + (base - raw);
+  float* part = reinterpret_cast<float*>(sb + 4 * kStOp);           // [8][512]
+  float* ss = part + kStWarps * kStPart;                              // kTop: [2 Lf - 1]
+  const uint32_t bar = base + 4 * kStOp + kStWarps * kStPart * 4 + 2 * kSpMaxLf * 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + 4 * kStOp + kStWarps * kStPart * 4 + 2 * kSpMaxLf * 4 + 16);
+  const int p = blockIdx.x, nb = 2 * Lf - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* gx = feat + (int64_t)(2 * p) * kCnnC * Lf;
+  const float* gy = feat + (int64_t)(2 * p + 1) * kCnnC * Lf;
+  // operands: item (signal, chunk c, row r) -> 8 channels split into hi, lo
+  for (int it = threadIdx.x; it < 2 * 4 * kStRows; it += kStWarps * 32) {
+    const int r = it & (kStRows - 1), c = (it >> 8) & 3, sg = it >> 10;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (r < Lf) {
+      const float4* src = reinterpret_cast<const float4*>((sg ? gy : gx) + (int64_t)r * kCnnC + 8 * c);
+      a = __ldg(src);
+      b = __ldg(src + 1);
+    }
+    const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = st_pack_bf16x2(f[2 * e], f[2 * e + 1]);
+      const float h0 = __uint_as_float(h[e] << 16), h1 = __uint_as_float(h[e] & 0xFFFF0000u);
+      l[e] = st_pack_bf16x2(f[2 * e] - h0, f[2 * e + 1] - h1);
+    }
+    const uint32_t off = (uint32_t)(c * kStChunk + r * 16);
+    st_shared_v4(base + (uint32_t)((2 * sg) * kStOp) + off, h[0], h[1], h[2], h[3]);
+    st_shared_v4(base + (uint32_t)((2 * sg + 1) * kStOp) + off, l[0], l[1], l[2], l[3]);
+  }
+  for (int i = threadIdx.x; i < kStWarps * kStPart; i += kStWarps * 32) part[i] = 0.f;
   if (kTop) {
     int32_t* cz = top.cbuf + (int64_t)p * kCnnTopK * kCnnWin;
-    for (int i = threadIdx.x; i < kCnnTopK * kCnnWin; i += kSpWarps * 32) cz[i] = 0;
+    for (int i = threadIdx.x; i < kCnnTopK * kCnnWin; i += kStWarps * 32) cz[i] = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (threadIdx.x == 0) {
+    const uint32_t xh = base, xl = base + kStOp, yh = base + 2 * kStOp, yl = base + 3 * kStOp;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const uint32_t d = tmem + 256u * (uint32_t)mt;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t ko = (uint32_t)(2 * k * kStChunk), mo = (uint32_t)(mt * 128 * 16);
+        const uint64_t ah = sdesc(xh + ko + mo, kStChunk, 128, 0, 0), al = sdesc(xl + ko + mo, kStChunk, 128, 0, 0);
+        const uint64_t bh = sdesc(yh + ko, kStChunk, 128, 0, 0), bl = sdesc(yl + ko, kStChunk, 128, 0, 0);
+        st_mma_bf16(d, ah, bh, k > 0 ? 1u : 0u);
+        st_mma_bf16(d, ah, bl, 1u);
+        st_mma_bf16(d, al, bh, 1u);
+      }
+    }
+    mma_commit(bar);
+  }
+  const bool ok = __syncthreads_and(warp_wait(bar, 0));
+  if (ok) {
+    tc_fence_after();
+    // each warp: its 8 blocks of 32 x 32 in a fixed order
+    const int q = warp & 3, half = warp >> 2;
+    float* S = reinterpret_cast<float*>(sb) + warp * kStSkew;
+    float* pw = part + warp * kStPart;
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll 1
+      for (int cb = 0; cb < 4; ++cb) {
+        const int j0 = 128 * half + 32 * cb, i0 = 128 * mt + 32 * q;
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(256 * mt + j0), v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) S[lane * 33 + c] = __uint_as_float(v[c]);
+        __syncwarp();
+        // diagonals d1 = lane - 31 (rows 31 - lane .. 31) and d2 = lane + 1
+        // (rows 0 .. 30 - lane), rows in ascending order
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          if (r >= 31 - lane) s1 += S[r * 33 + r + lane - 31];
+          if (r <= 30 - lane) s2 += S[r * 33 + r + lane + 1];
+        }
+        pw[j0 - i0 + lane - 31 + 255] += s1;
+        if (lane < 31) pw[j0 - i0 + lane + 1 + 255] += s2;
+        __syncwarp();
+      }
+    }
+  } else if (threadIdx.x == 0 && status) {
+    atomicOr(status, TDE_ST_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+  const float alpha = params[kCnnAlpha];
+  for (int b = threadIdx.x; b < nb; b += kStWarps * 32) {
+    const int li = b - (Lf - 1) + 255;
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kStWarps; ++w) t += part[w * kStPart + li];
+    scores[(int64_t)p * nb + b] = alpha * t;
+    if (kTop) ss[b] = alpha * t;
+  }
+  if (kTop) {
     __syncthreads();
     if (warp != 0) return;
     float v[kSpMaxLf * 2 / 32];
@@ -555,7 +719,6 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* _
     }
   }
 }
-
 
 // Any length: the bins are re-read from global memory every round.
 __global__ void k_topk_any(const float* __restrict__ scores, int npairs, int Lf,
@@ -939,12 +1102,17 @@ cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_
 }
 
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
-                              float* scores, cudaStream_t st, bool pos_major) {
+                              float* scores, cudaStream_t st, bool pos_major, uint32_t* status) {
   if (Lf < 1 || npairs <= 0) return npairs <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  if (pos_major && Lf <= kSpMaxLf) {  // inference: the tensor cores
+    cudaFuncSetAttribute(k_scores_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem);
+    k_scores_tc<false><<<npairs, kStWarps * 32, kStSmem, st>>>(feat, Lf, params, scores, TopOut{}, status);
+    TDE_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+  }
   if (Lf <= kSpMaxLf) {
-    auto kp = pos_major ? k_scores_pair<true, false> : k_scores_pair<false, false>;
-    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmem);
-    kp<<<npairs, kSpWarps * 32, kSpSmem, st>>>(feat, Lf, params, scores, TopOut{});
+    cudaFuncSetAttribute(k_scores_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmem);
+    k_scores_pair<false><<<npairs, kSpWarps * 32, kSpSmem, st>>>(feat, Lf, params, scores);
     TDE_COUNT_LAUNCH(1);
     return cudaGetLastError();
   }
@@ -958,13 +1126,13 @@ cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float
 
 cudaError_t launch_cnn_scores_propose(const float* feat, int npairs, int Lf, const float* params,
                                       float* scores, int32_t* centres, float* margin, WinJob* jobs,
-                                      int32_t* cbuf, int64_t n, int32_t* njobs, cudaStream_t st) {
+                                      int32_t* cbuf, int64_t n, int32_t* njobs, cudaStream_t st,
+                                      uint32_t* status) {
   if (npairs <= 0) return cudaSuccess;
   if (Lf < 1 || Lf > kSpMaxLf) return cudaErrorNotSupported;
-  cudaFuncSetAttribute(k_scores_pair<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kSpTopSmem);
-  k_scores_pair<true, true><<<npairs, kSpWarps * 32, kSpTopSmem, st>>>(
-      feat, Lf, params, scores, TopOut{centres, margin, jobs, cbuf, n, njobs});
+  cudaFuncSetAttribute(k_scores_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem);
+  k_scores_tc<true><<<npairs, kStWarps * 32, kStSmem, st>>>(
+      feat, Lf, params, scores, TopOut{centres, margin, jobs, cbuf, n, njobs}, status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

@@ -72,8 +72,14 @@ cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint
                                 uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1;
 // channel-major [S][32][Lf], or position-major [S][Lf][32] with pos_major).
+// Channel-major features (the training forward) are scored in FP32 FMA;
+// position-major ones (inference) up to Lf = kCnnFusedMaxLf on the tensor
+// cores (the Gram matrix of the pair's features in split BF16, its diagonal
+// sums in a fixed order), a time-out there setting TDE_ST_TIMEOUT in status
+// (nullable).
 cudaError_t launch_cnn_scores(const float* feat, int npairs, int Lf, const float* params,
-                              float* scores, cudaStream_t st, bool pos_major = false);
+                              float* scores, cudaStream_t st, bool pos_major = false,
+                              uint32_t* status = nullptr);
 // Top-8 bins per pair -> window centres in samples (256 l), softmax mass of
 // the top 8 (margin).
 cudaError_t launch_cnn_topk(const float* scores, int npairs, int Lf, int32_t* centres,
@@ -166,14 +172,15 @@ __device__ __forceinline__ int win_jobs(const int (&a)[kCnnTopK], const int (&b)
 #endif
 // The learned step's proposal in one launch, for Lf <= kCnnFusedMaxLf (else
 // cudaErrorNotSupported): the scores of launch_cnn_scores (position-major
-// features), then per pair the centres and margin of launch_cnn_topk
+// features, tensor cores), then per pair the centres and margin of launch_cnn_topk
 // (identical arithmetic, so identical values) and its 8 window jobs for
 // signals of length n (window w of pair p writes cbuf + (8 p + w) * 257),
 // with those 8 * 257 correlations zeroed, and njobs[p] = the pair's job
 // count in the polyphase windows kernel (win_jobs).
 cudaError_t launch_cnn_scores_propose(const float* feat, int npairs, int Lf, const float* params,
                                       float* scores, int32_t* centres, float* margin, WinJob* jobs,
-                                      int32_t* cbuf, int64_t n, int32_t* njobs, cudaStream_t st);
+                                      int32_t* cbuf, int64_t n, int32_t* njobs, cudaStream_t st,
+                                      uint32_t* status = nullptr);
 // Per pair: tie-ruled argmax over its 8 windows -> lag, value.
 cudaError_t launch_window_argmax(const WinJob* d_jobs, int npairs, int64_t* lag, int64_t* val,
                                  cudaStream_t st);

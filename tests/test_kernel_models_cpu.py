@@ -286,3 +286,57 @@ def test_qone_candidate_columns_hold_every_sample_a_thread_sees():
             tail = np.arange(4 * n4, n)
             np.add.at(per, (tail - 4 * n4) % T, 1)
             assert per.max(initial=0) <= rows, (n, vec, per.max())
+
+
+def _scores_tc_drain_model(G, Lf):
+    """k_scores_tc's diagonal sums restated: warp w (quadrant q = w % 4, half
+    w // 4) takes its 32 x 32 blocks of G (rows 128 mt + 32 q + r, columns
+    128 half + 32 cb + c) in the kernel's order; lane t sums the block's
+    diagonals d1 = t - 31 (rows 31 - t .. 31) and d2 = t + 1 (rows 0 .. 30 - t)
+    of the skewed copy S[r][c] (row stride 33) and adds them to its warp's
+    row at lag + 255; bin b = l + Lf - 1 is then the sum of the 8 rows in
+    warp order.  Asserts every read stays in the copy and every write in the
+    row."""
+    part = np.zeros((8, 512))
+    for w in range(8):
+        q, half = w & 3, w >> 2
+        for mt in range(2):
+            for cb in range(4):
+                j0, i0 = 128 * half + 32 * cb, 128 * mt + 32 * q
+                S = np.zeros(32 * 33)
+                for r in range(32):
+                    S[r * 33:r * 33 + 32] = G[i0 + r, j0:j0 + 32]
+                for t in range(32):
+                    s1 = s2 = 0.0
+                    for r in range(32):
+                        if r >= 31 - t:
+                            a = r * 33 + r + t - 31
+                            assert r * 33 <= a < r * 33 + 32
+                            s1 += S[a]
+                        if r <= 30 - t:
+                            a = r * 33 + r + t + 1
+                            assert r * 33 <= a < r * 33 + 32
+                            s2 += S[a]
+                    i1 = j0 - i0 + t - 31 + 255
+                    assert 0 <= i1 < 512
+                    part[w, i1] += s1
+                    if t < 31:
+                        i2 = j0 - i0 + t + 1 + 255
+                        assert 0 <= i2 < 512
+                        part[w, i2] += s2
+    nb = 2 * Lf - 1
+    return np.array([part[:, b - (Lf - 1) + 255].sum() for b in range(nb)])
+
+
+def test_scores_tc_diagonal_sums_cover_every_entry_once():
+    """The drain's block diagonals add up to score[l] = sum_i G[i][i + l] for
+    every bin, with rows past Lf zero (as the kernel's operands are), for the
+    full length and a shorter one."""
+    rng = np.random.default_rng(12)
+    for Lf in (256, 200, 8):
+        X = np.zeros((256, 32)); Y = np.zeros((256, 32))
+        X[:Lf] = rng.random((Lf, 32)); Y[:Lf] = rng.random((Lf, 32))
+        G = X @ Y.T
+        got = _scores_tc_drain_model(G, Lf)
+        want = np.array([np.trace(G, offset=l) for l in range(-(Lf - 1), Lf)])
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-9), Lf
