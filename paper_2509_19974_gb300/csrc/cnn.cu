@@ -535,7 +535,9 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_scores_pair(const float* _
 // (x hi, x lo, y hi, y lo) four 8-channel chunks of 256 rows of 16 bytes,
 // K-major without swizzle (core matrices of 8 rows at 128 bytes, the next
 // chunk 4096 bytes on).  The skew copies reuse the operands' space once the
-// MMAs are done.  With kTop the epilogue is k_scores_pair's.
+// MMAs are done.  With kTop the CTA then takes the pair's top 8 and writes
+// its centres, margin and window jobs (the learned step's proposal in one
+// launch).
 constexpr int kStWarps = 8;
 constexpr int kStRows = 256;                       // rows of an operand (Lf padded with zeros)
 constexpr int kStChunk = kStRows * 16;             // one 8-channel chunk (4096 bytes)
@@ -562,6 +564,27 @@ __device__ __forceinline__ uint32_t st_pack_bf16x2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
+}
+
+// Ordering key of a bin: the score's bits mapped to an unsigned order (-0
+// taken as +0), then 2 |l| + (l > 0) inverted, so that the larger key is the
+// better bin of `better` (higher score, then smaller |l|, then negative l).
+// Never 0 for a bin, so 0 marks "none".
+__device__ __forceinline__ unsigned long long st_key(float s, int l) {
+  uint32_t u = __float_as_uint(s == 0.f ? 0.f : s);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  const uint32_t a = (uint32_t)(l < 0 ? -l : l);
+  const uint32_t rank = 2u * a + (l > 0 ? 1u : 0u);
+  return ((unsigned long long)u << 32) | (0xFFFFFFFFu - rank);
+}
+__device__ __forceinline__ float st_key_score(unsigned long long k) {
+  const uint32_t u = (uint32_t)(k >> 32);
+  return __uint_as_float((u & 0x80000000u) ? (u ^ 0x80000000u) : ~u);
+}
+__device__ __forceinline__ int st_key_lag(unsigned long long k) {
+  const uint32_t rank = 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
+  const int a = (int)(rank >> 1);
+  return (rank & 1u) ? a : -a;
 }
 
 template <bool kTop>
@@ -688,17 +711,60 @@ __global__ void __launch_bounds__(kStWarps * 32, 2) k_scores_tc(const float* __r
     if (kTop) ss[b] = alpha * t;
   }
   if (kTop) {
+    // softmax max and sum over the bins, then the top 8 as the largest keys
+    // (st_key: score, then the lag order of `better`): each warp keeps the 8
+    // best of its 64 bins, warp 0 takes the 8 best of those 64
+    __shared__ float red_s[kStWarps];
+    __shared__ unsigned long long cand_s[kStWarps * kCnnTopK];
+    __syncthreads();
+    const int b0 = threadIdx.x, b1 = threadIdx.x + kStWarps * 32;
+    const float s0 = b0 < nb ? ss[b0] : -INFINITY, s1 = b1 < nb ? ss[b1] : -INFINITY;
+    float mx = fmaxf(s0, s1);
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red_s[warp] = mx;
+    __syncthreads();
+    mx = red_s[0];
+#pragma unroll
+    for (int w = 1; w < kStWarps; ++w) mx = fmaxf(mx, red_s[w]);
+    float e = (b0 < nb ? __expf(s0 - mx) : 0.f) + (b1 < nb ? __expf(s1 - mx) : 0.f);
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    __syncthreads();  // every thread has read red_s
+    if (lane == 0) red_s[warp] = e;
+    unsigned long long k0 = b0 < nb ? st_key(s0, b0 - (Lf - 1)) : 0ull;
+    unsigned long long k1 = b1 < nb ? st_key(s1, b1 - (Lf - 1)) : 0ull;
+#pragma unroll 1
+    for (int r = 0; r < kCnnTopK; ++r) {
+      unsigned long long bk = k0 > k1 ? k0 : k1;
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, bk, o);
+        bk = t > bk ? t : bk;
+      }
+      if (lane == 0) cand_s[warp * kCnnTopK + r] = bk;
+      if (k0 == bk) k0 = 0ull;  // keys are distinct (one per lag)
+      if (k1 == bk) k1 = 0ull;
+    }
     __syncthreads();
     if (warp != 0) return;
-    float v[kSpMaxLf * 2 / 32];
+    float sum = 0.f;
 #pragma unroll
-    for (int i = 0; i < kSpMaxLf * 2 / 32; ++i) {
-      const int b = lane + 32 * i;
-      v[i] = b < nb ? ss[b] : -INFINITY;
+    for (int w = 0; w < kStWarps; ++w) sum += red_s[w];
+    k0 = cand_s[lane], k1 = cand_s[lane + 32];
+    float topm = 0.f;
+    int32_t centre = 0;
+#pragma unroll 1
+    for (int r = 0; r < kCnnTopK; ++r) {
+      unsigned long long bk = k0 > k1 ? k0 : k1;
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, bk, o);
+        bk = t > bk ? t : bk;
+      }
+      if (k0 == bk) k0 = 0ull;
+      if (k1 == bk) k1 = 0ull;
+      if (bk == 0ull) continue;  // fewer than 8 bins
+      topm += __expf(st_key_score(bk) - mx);
+      if (lane == r) centre = kCnnBin * st_key_lag(bk);
     }
-    int32_t centre;
-    float margin;
-    topk_warp(v, nb, Lf, lane, centre, margin);
+    const float margin = topm / sum;
     const int64_t i = (int64_t)p * kCnnTopK + lane;
     const WinJob J = win_job_of(centre, top.n, top.cbuf + i * kCnnWin);
     if (lane < kCnnTopK) {

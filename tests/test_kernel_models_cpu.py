@@ -340,3 +340,37 @@ def test_scores_tc_diagonal_sums_cover_every_entry_once():
         got = _scores_tc_drain_model(G, Lf)
         want = np.array([np.trace(G, offset=l) for l in range(-(Lf - 1), Lf)])
         assert np.allclose(got, want, rtol=1e-12, atol=1e-9), Lf
+
+
+def _st_key(s, l):
+    """k_scores_tc's bin key (float32 score, lag) as a Python int."""
+    s = np.float32(s)
+    if s == 0:
+        s = np.float32(0.0)
+    u = int(np.array(s, np.float32).view(np.uint32))
+    u = (~u & 0xFFFFFFFF) if u & 0x80000000 else (u | 0x80000000)
+    rank = 2 * abs(l) + (1 if l > 0 else 0)
+    return (u << 32) | (0xFFFFFFFF - rank)
+
+
+def test_scores_key_orders_bins_like_better():
+    """The key's order is `better`'s: higher score, then smaller |l|, then
+    negative l; -0 ties +0; the score and lag decode back."""
+    def better(s, l, bs, bl):
+        if s != bs:
+            return s > bs
+        return abs(l) < abs(bl) if abs(l) != abs(bl) else l < bl
+    rng = np.random.default_rng(4)
+    vals = [0.0, -0.0, 1.5, -1.5, 3.0, -7.25, 1e-30, -1e-30, 2.0 ** 100]
+    for _ in range(3000):
+        s1, s2 = (float(rng.choice(vals)) if rng.random() < 0.5 else float(np.float32(rng.normal())) for _ in range(2))
+        l1, l2 = (int(v) for v in rng.integers(-255, 256, 2))
+        if l1 == l2:
+            continue
+        k1, k2 = _st_key(s1, l1), _st_key(s2, l2)
+        assert (k1 > k2) == better(np.float32(s1), l1, np.float32(s2), l2), (s1, l1, s2, l2)
+        rank = 0xFFFFFFFF - (k1 & 0xFFFFFFFF)
+        assert ((rank >> 1) if rank & 1 else -(rank >> 1)) == l1
+        u = k1 >> 32
+        bits = (u ^ 0x80000000) if u & 0x80000000 else (~u & 0xFFFFFFFF)
+        assert np.array(bits, np.uint32).view(np.float32) == np.float32(s1)
