@@ -11,7 +11,7 @@
 // (launch_xcorr_win_pp in winpp.cu); this file holds their argmax.
 //
 // Weights are BF16-rounded everywhere and every sum is FP32.  Inference runs
-// its four conv layers on tcgen05 (mma.cu: k_conv1_tc, k_conv_tc) with BF16
+// its four conv layers on tcgen05 (mma.cu: k_conv12_tc, k_conv_tc) with BF16
 // activations between layers; the training forward keeps FP32 activations
 // (the first layer in FP32 FMA, the 32-channel layers as mma.sync BF16 tiles
 // with FP32 accumulation), and the backward pass is deterministic (per-signal
@@ -248,17 +248,6 @@ __global__ void __launch_bounds__(kThreads) k_conv_fwd_tc(const float* __restric
 // FP32 chain rounded where the tensor cores read them, at half the traffic.
 // The last layer writes FP32 features [signal][Lf][32] for the scores.
 
-// The zero rows of a layer input of length L (rows 0, 1 and [L/2 + 2, R)).
-__global__ void k_eo_pad(uint16_t* __restrict__ act, int L, int nsig) {
-  const int R = cnn_eo_rows(L), v = L / 2 + 2, npad = 2 + (R - v);
-  const int64_t total = (int64_t)nsig * 8 * npad;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int pr = (int)(i % npad);
-    const int r = pr < 2 ? pr : v + (pr - 2);
-    *reinterpret_cast<uint4*>(act + ((i / npad) * R + r) * 8) = make_uint4(0u, 0u, 0u, 0u);
-  }
-}
 
 // Scores: score[l] = alpha * sum_c sum_i fx[c][i] fy[c][i + l].  A CTA
 // takes 128 consecutive bins of one pair, a warp 16 of them, a lane one
@@ -1153,13 +1142,11 @@ cudaError_t launch_cnn_infer(const int8_t* q, int64_t n, int nsig, const uint16_
                              uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
   const int Ld = (int)(n / kCnnDec);
   if (Ld % 128 != 0) return cudaErrorInvalidValue;  // every layer's length a multiple of 16
-  cudaError_t e = launch_cnn_conv1_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), act[0], qe,
-                                      d_status, st);
-  if (e != cudaSuccess) return e;
-  k_eo_pad<<<(nsig + 63) / 64, 256, 0, st>>>(act[0], Ld / 2, nsig);
-  TDE_COUNT_LAUNCH(1);
-  e = cudaGetLastError();
-  for (int l = 1; l < kCnnLayers && e == cudaSuccess; ++l) {
+  // layers 1 and 2 in one kernel (layer 2's input stays on chip; act[0] is
+  // not used), then layers 3 and 4
+  cudaError_t e = launch_cnn_conv12_tc(q, n, nsig, wbf + cnn_woff(0), params + cnn_boff(0), wbf + cnn_woff(1),
+                                       params + cnn_boff(1), act[1], qe, d_status, st);
+  for (int l = 2; l < kCnnLayers && e == cudaSuccess; ++l) {
     const bool last = l == kCnnLayers - 1;
     e = launch_cnn_conv_tc(act[l - 1], last ? static_cast<void*>(feat) : static_cast<void*>(act[l]),
                            Ld >> l, nsig, wbf + cnn_woff(l), params + cnn_boff(l), last, d_status, st);

@@ -64,12 +64,15 @@ __host__ __device__ constexpr int64_t cnn_eo_elems(int L) { return (int64_t)8 * 
 // TDE_ST_TIMEOUT.
 cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, const uint16_t* wbf,
                                const float* bias, bool last, uint32_t* d_status, cudaStream_t st);
-// The first layer of the inference forward on the tensor cores (mma.cu):
-// decimation of q [nsig][n] int8, conv 1 -> 32 (weights wbf [32][1][9], bias)
-// -> out, the second layer's input (length n/32, parity arrays; the zero rows
-// are the caller's); qe (nullable) receives the levels as E4M3 bytes.
-cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
-                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st);
+// Layers 1 and 2 of the inference forward in one kernel (mma.cu): decimation
+// of q [nsig][n] int8, conv 1 -> 32 (weights w1bf [32][1][9], bias1), whose
+// output (layer 2's input) stays in shared memory, then conv 32 -> 32 (w2bf,
+// bias2); out = the third layer's input (length n/64, parity arrays with
+// their zero rows); qe (nullable, nsig x n bytes) receives the levels as E4M3
+// bytes.  n/16 a multiple of 8.  Time-outs set TDE_ST_TIMEOUT.
+cudaError_t launch_cnn_conv12_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* w1bf, const float* bias1,
+                                 const uint16_t* w2bf, const float* bias2, uint16_t* out, uint8_t* qe,
+                                 uint32_t* d_status, cudaStream_t st);
 // score[p][l + Lf - 1] for npairs pairs (features of pair p: signals 2p, 2p+1;
 // channel-major [S][32][Lf], or position-major [S][Lf][32] with pos_major).
 // Channel-major features (the training forward) are scored in FP32 FMA;

@@ -1072,173 +1072,21 @@ __global__ void __launch_bounds__(kThreads, kCvCtasPerSm)
 
 // ---------------------------------------------------------------------------
 // The learned proposal's first layer (decimation + conv 1 -> 32 channels,
-// kernel 9, pad 4, bias, ReLU, max-pool 2) on the tensor cores.  A CTA takes
-// 128 pooled outputs P0 + m of one signal: it reads the 16 (264) level bytes
-// per decimated sample d[j] = (sum of 16 levels) / 4 (exact in BF16: |4 d| <=
-// 112), writes the E4M3 copy of the levels it owns (the windows' operands),
-// builds the im2col operand
-//   A_par[m][k] = d[2 (P0 + m) + par + k - 4]   (k < 9; k = 9..15 zero)
+// kernel 9, pad 4, bias, ReLU, max-pool 2) on the tensor cores, as
+// k_conv12_tc runs it: for 128 layer-1 outputs u0 + m it builds the im2col
+// operand
+//   A_par[m][k] = d[2 (u0 + m) + par + k - 4]   (k < 9; k = 9..15 zero)
 // for both parities of the pooling pair as K-major no-swizzle tiles (16-byte
 // rows of 8 taps, leading byte offset 2048 between the two 8-tap halves), and
 // issues one MMA of 128 x 32 x 16 per parity (columns 0-31 odd, 32-63 even)
-// against W[co][k].  The epilogue is that of k_conv_tc: y = relu(max(z_even,
-// z_odd) + b), stored as the next layer's parity arrays.
+// against W[co][k]; y = relu(max(z_even, z_odd) + b).  The decimated samples
+// d[j] = (sum of 16 levels) / 4 are exact in BF16 (|4 d| <= 112).
 constexpr int kC1M = 128;                      // pooled outputs per CTA
-constexpr int kC1D = 2 * kC1M + 8;             // decimated samples per CTA (264)
 constexpr int kC1ABytes = 2 * 2 * kC1M * 16;   // A tiles: parity x 8-tap half x rows
 constexpr int kC1WBytes = 2 * kCnnC * 16;      // B: 8-tap half x co rows
-constexpr int kC1Smem = kC1ABytes + kC1WBytes + kC1D * 2 + 16 + 16 + 128;
 constexpr uint32_t kC1Idesc =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCnnC >> 3) << 17) | ((uint32_t)(kC1M >> 4) << 24);
 
-__global__ void __launch_bounds__(kThreads, 4) k_conv1_tc(const int8_t* __restrict__ q, int64_t n, int nsig,
-                                                      const uint16_t* __restrict__ wbf,
-                                                      const float* __restrict__ bias,
-                                                      uint16_t* __restrict__ out,
-                                                      uint8_t* __restrict__ qe,
-                                                      uint32_t* __restrict__ status) {
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base = (raw + 127u) & ~127u;
-  uint8_t* sbase = smem_raw + (base - raw);
-  const uint32_t a_s = base;                       // [par][half][m] 16-byte rows
-  const uint32_t w_s = base + kC1ABytes;           // [half][co] 16-byte rows
-  uint16_t* d_s = reinterpret_cast<uint16_t*>(sbase + kC1ABytes + kC1WBytes);  // BF16 d
-  const uint32_t bar = base + kC1ABytes + kC1WBytes + kC1D * 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + kC1ABytes + kC1WBytes + kC1D * 2 + 16);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int Ld = (int)(n / kCnnDec), Lo = Ld / 2;  // decimated length, pooled outputs
-  const int tps = (Lo + kC1M - 1) / kC1M;
-  const int units = nsig * tps;
-  const int u0 = (int)((int64_t)units * blockIdx.x / gridDim.x);
-  const int u1 = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x);
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(2 * kCnnC)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (threadIdx.x == 32) {
-    mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // weights: W_s[half][co][e] = W[co][0][8 half + e] (taps 9..15 zero)
-  for (int idx = threadIdx.x; idx < 2 * kCnnC * 8; idx += kThreads) {
-    const int e = idx & 7, co = (idx >> 3) & (kCnnC - 1), h = idx >> 8;
-    const int k = 8 * h + e;
-    reinterpret_cast<uint16_t*>(sbase + kC1ABytes)[idx] = k < kCnnK ? __ldg(wbf + co * kCnnK + k) : (uint16_t)0;
-  }
-  const int qd = warp & 3, ch = warp >> 2;
-  float bv[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) bv[j] = bias[16 * ch + j];
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint64_t bd = sdesc(w_s, kCnnC * 16, 128, 0, 0);
-  const uint64_t ad_odd = sdesc(a_s + 2u * kC1M * 16, kC1M * 16, 128, 0, 0), ad_even = sdesc(a_s, kC1M * 16, 128, 0, 0);
-  bool ok = true;
-  uint32_t phase = 0;
-  // level bytes of a tile's decimated samples d[2 P0 - 4 + i], i = threadIdx.x
-  // and threadIdx.x + kThreads, loaded one tile ahead
-  static_assert(kC1D <= 2 * kThreads, "two samples per thread");
-  auto fetch = [&](int u, uint4 (&w)[2]) {
-    const int s = u / tps, P0 = (u - s * tps) * kC1M;
-    const int8_t* src = q + (int64_t)s * n;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int i = threadIdx.x + t * kThreads, j = 2 * P0 - 4 + i;
-      w[t] = (i < kC1D && j >= 0 && j < Ld) ? __ldg(reinterpret_cast<const uint4*>(src + (int64_t)j * kCnnDec))
-                                            : make_uint4(0u, 0u, 0u, 0u);
-    }
-  };
-  uint4 wn[2];
-  if (u0 < u1) fetch(u0, wn);
-  for (int u = u0; u < u1 && ok; ++u) {
-    const int s = u / tps, P0 = (u - s * tps) * kC1M;
-    uint4 wc[2] = {wn[0], wn[1]};
-    if (u + 1 < u1) fetch(u + 1, wn);
-    // decimate: d_s[i] = d[2 P0 - 4 + i]; the E4M3 copy of the samples this tile owns
-    const int d0 = 2 * P0 - 4;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int i = threadIdx.x + t * kThreads;
-      if (i >= kC1D) continue;
-      const int j = d0 + i;
-      float v = 0.f;
-      if (j >= 0 && j < Ld) {
-        const uint4 w = wc[t];
-        int acc = 0;
-        acc = __dp4a((int)w.x, 0x01010101, acc);
-        acc = __dp4a((int)w.y, 0x01010101, acc);
-        acc = __dp4a((int)w.z, 0x01010101, acc);
-        acc = __dp4a((int)w.w, 0x01010101, acc);
-        v = 0.25f * (float)acc;
-        if (qe && i >= 4 && i < 2 * kC1M + 4)
-          *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
-      }
-      d_s[i] = (uint16_t)(__float_as_uint(v) >> 16);  // exact: |4 d| <= 112
-    }
-    __syncthreads();
-    // im2col: thread (par, half, m) writes one 16-byte row of 8 taps
-    for (int row = threadIdx.x; row < 2 * 2 * kC1M; row += kThreads) {
-      const int m = row & (kC1M - 1), h = (row >> 7) & 1, par = row >> 8;
-      uint32_t wv[4];
-#pragma unroll
-      for (int e2 = 0; e2 < 4; ++e2) {
-        const int k0 = 8 * h + 2 * e2;  // taps k0, k0 + 1
-        const int i0 = 2 * m + par + k0;
-        const uint32_t lo = k0 < kCnnK ? d_s[i0] : 0u, hi = k0 + 1 < kCnnK ? d_s[i0 + 1] : 0u;
-        wv[e2] = lo | (hi << 16);
-      }
-      st_shared_v4(a_s + 16u * (uint32_t)row, wv[0], wv[1], wv[2], wv[3]);
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x == 0) {  // odd parity -> columns 0-31, even -> 32-63
-      mma_bf16(tmem, ad_odd, bd, kC1Idesc, 0u);
-      mma_bf16(tmem + kCnnC, ad_even, bd, kC1Idesc, 0u);
-      mma_commit(bar);
-    }
-    ok = __syncthreads_and(mbar_wait_sleep(bar, phase));
-    phase ^= 1u;
-    if (!ok) break;
-    tc_fence_after();
-    const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * ch);
-    uint32_t vo[16], ve[16];
-    tmem_ld16_nowait(col, vo);
-    tmem_ld16_nowait(col + 32u, ve);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int P = P0 + 32 * qd + lane;
-    if (P < Lo) {
-      float y[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        y[j] = fmaxf(fmaxf(__uint_as_float(ve[j]), __uint_as_float(vo[j])) + bv[j], 0.f);
-      const int Rn = cnn_eo_rows(Lo);
-      uint16_t* o = out + ((((int64_t)s * 2 + (P & 1)) * 4 + 2 * ch) * Rn + (P >> 1) + 2) * 8;
-      *reinterpret_cast<uint4*>(o) = make_uint4(pack_bf16x2_rn(y[0], y[1]), pack_bf16x2_rn(y[2], y[3]),
-                                                pack_bf16x2_rn(y[4], y[5]), pack_bf16x2_rn(y[6], y[7]));
-      *reinterpret_cast<uint4*>(o + (int64_t)Rn * 8) =
-          make_uint4(pack_bf16x2_rn(y[8], y[9]), pack_bf16x2_rn(y[10], y[11]),
-                     pack_bf16x2_rn(y[12], y[13]), pack_bf16x2_rn(y[14], y[15]));
-    }
-    tc_fence_before();  // the next tile's MMAs overwrite the accumulator after the loop's barriers
-  }
-  if (!ok && threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCnnC)
-                 : "memory");
-  }
-}
 
 // Self-test of the bounded waits the kernels above use: thread 0 waits on a
 // shared-memory barrier that nothing arrives on, first spinning (mbar_wait),
@@ -1253,6 +1101,283 @@ __global__ void k_wait_selftest(uint32_t* __restrict__ status) {
     bool ok = mbar_wait(b, 0);
     ok = mbar_wait_sleep(b, 0) && ok;
     if (!ok) atomicOr(status, TDE_ST_TIMEOUT);
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// The inference forward's first two layers in one kernel: decimation + conv
+// 1 -> 32 + pool (the first layer above) feeding conv 32 -> 32 + pool
+// (k_conv_tc's) through shared memory, so layer 2's input never goes to
+// global memory.  A unit is one layer-2 tile: 128 pooled outputs P0 + m of
+// one signal.  It needs layer-1 outputs u = 2 P0 - 4 + t, t in [0, 264) (zero
+// outside [0, Ld / 2)): t < 256 come from two 128-row MMA tiles per parity
+// as above (im2col operand from the 536 decimated samples
+// d[4 P0 - 12 + i]), t = 256..263 from CUDA-core FMAs over the same BF16
+// products.  They are written, BF16, as the E/O parity arrays of k_conv_tc's
+// tile (t even -> E row t / 2, t odd -> O row t / 2), and that tile's 20
+// MMAs and epilogue follow.  Layer 1's im2col tiles share the tile's space
+// (they are read before it is written), and layer 2's accumulator reuses
+// layer 1's tensor-memory columns, so a CTA holds 128 columns and about
+// 41 KB: four CTAs per SM.  The CTA also writes the E4M3 copy of the levels
+// its unit owns (q samples [64 P0, 64 P0 + 8192)) and, as layer 2 of
+// k_conv_tc does, the zero rows of layer 3's input.
+constexpr int kF2M = 128;                    // layer-2 pooled outputs per unit
+constexpr int kF1U = 2 * kF2M + 8;           // layer-1 outputs per unit (264)
+constexpr int kF1D = 2 * kF1U + 8;           // decimated samples per unit (536)
+constexpr int kF1Fetch = 3;                  // uint4 per thread holding the unit's level bytes
+constexpr int kF1ABytes = 2 * kC1ABytes;     // two conv-1 im2col tiles (aliasing the layer-2 tile)
+constexpr int kF12Smem = kCvXBytes + kCvWBytes + kC1WBytes + 1152 + 16 + 16 + 128;
+static_assert(kF1ABytes <= kCvXBytes, "conv-1 tiles fit the layer-2 tile");
+static_assert(kF1D <= kF1Fetch * kThreads && kF1D * 2 <= 1152, "per-unit samples");
+static_assert(4 * (kF12Smem + 1024) <= 228 * 1024, "four CTAs per SM");
+
+__global__ void __launch_bounds__(kThreads, 4)
+    k_conv12_tc(const int8_t* __restrict__ q, int64_t n, int nsig, const uint16_t* __restrict__ w1bf,
+                const float* __restrict__ bias1, const uint16_t* __restrict__ w2bf,
+                const float* __restrict__ bias2, uint16_t* __restrict__ out, uint8_t* __restrict__ qe,
+                uint32_t* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 127u) & ~127u;
+  uint8_t* sbase = smem_raw + (base - raw);
+  const uint32_t xb = base;                          // layer-2 tile; conv-1 im2col tiles first
+  const uint32_t wsm = xb + kCvXBytes;               // layer-2 weight blocks
+  const uint32_t w1s = wsm + kCvWBytes;              // layer-1 weights
+  uint16_t* d_s = reinterpret_cast<uint16_t*>(sbase + kCvXBytes + kCvWBytes + kC1WBytes);
+  const uint32_t bar1 = w1s + kC1WBytes + 1152, bar2 = bar1 + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + kCvXBytes + kCvWBytes + kC1WBytes + 1152 + 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Ld = (int)(n / kCnnDec), L2 = Ld / 2, Lo = L2 / 2;  // decimated, layer-2 input, layer-2 pooled
+  const int tps = (Lo + kF2M - 1) / kF2M;
+  const int units = nsig * tps;
+  const int u0 = (int)((int64_t)units * blockIdx.x / gridDim.x);
+  const int u1 = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * kCnnC * 2)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    mbar_init(bar1, 1);
+    mbar_init(bar2, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // layer-1 weights W_s[half][co][e] = W1[co][8 half + e] (taps 9..15 zero)
+  for (int idx = threadIdx.x; idx < 2 * kCnnC * 8; idx += kThreads) {
+    const int e = idx & 7, co = (idx >> 3) & (kCnnC - 1), h = idx >> 8;
+    const int k = 8 * h + e;
+    reinterpret_cast<uint16_t*>(sbase + kCvXBytes + kCvWBytes)[idx] = k < kCnnK ? __ldg(w1bf + co * kCnnK + k) : (uint16_t)0;
+  }
+  // layer-2 weight blocks as in k_conv_tc, in two batches of loads
+  {
+    uint32_t* wdst = reinterpret_cast<uint32_t*>(sbase + kCvXBytes);
+    constexpr int kPer = (kCvWBytes / 4 + kThreads - 1) / kThreads;
+#pragma unroll
+    for (int r0 = 0; r0 < kPer; r0 += (kPer + 1) / 2) {
+      uint32_t v[(kPer + 1) / 2];
+#pragma unroll
+      for (int r = 0; r < (kPer + 1) / 2; ++r) {
+        const int idx = threadIdx.x + (r0 + r) * kThreads;
+        const int e2 = idx & 3, co = (idx >> 2) & (kCnnC - 1), jt = idx >> 7;
+        const int t = jt % kCvTaps, j = jt / kCvTaps, k = t - 1;
+        v[r] = 0;
+        if (r0 + r < kPer && idx < kCvWBytes / 4 && k >= 0 && k < kCnnK) {
+          const int ci = 8 * j + 2 * e2;
+          v[r] = (uint32_t)__ldg(w2bf + (co * kCnnC + ci) * kCnnK + k) |
+                 ((uint32_t)__ldg(w2bf + (co * kCnnC + ci + 1) * kCnnK + k) << 16);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < (kPer + 1) / 2; ++r) {
+        const int idx = threadIdx.x + (r0 + r) * kThreads;
+        if (r0 + r < kPer && idx < kCvWBytes / 4) wdst[idx] = v[r];
+      }
+    }
+  }
+  // the zero rows of layer 3's input: 0, 1 and [Lo / 2 + 2, Rn) of each array
+  {
+    const int Rn = cnn_eo_rows(Lo), vn = Lo / 2 + 2, npad = 2 + (Rn - vn);
+    const int64_t total = (int64_t)nsig * 8 * npad;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += (int64_t)gridDim.x * kThreads) {
+      const int pr = (int)(i % npad);
+      const int64_t arr = i / npad;
+      const int r = pr < 2 ? pr : vn + (pr - 2);
+      *reinterpret_cast<uint4*>(out + (arr * Rn + r) * 8) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  const int qd = warp & 3, ch = warp >> 2;
+  const uint16_t* w1h = reinterpret_cast<const uint16_t*>(sbase + kCvXBytes + kCvWBytes);
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t bd1 = sdesc(w1s, kCnnC * 16, 128, 0, 0);
+  bool ok = true;
+  uint32_t ph1 = 0, ph2 = 0;
+  auto fetch = [&](int u, uint4 (&w)[kF1Fetch]) {
+    const int s = u / tps, P0 = (u - s * tps) * kF2M;
+    const int8_t* src = q + (int64_t)s * n;
+#pragma unroll
+    for (int f = 0; f < kF1Fetch; ++f) {
+      const int i = threadIdx.x + f * kThreads, j = 4 * P0 - 12 + i;
+      w[f] = (i < kF1D && j >= 0 && j < Ld) ? __ldg(reinterpret_cast<const uint4*>(src + (int64_t)j * kCnnDec))
+                                            : make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  uint4 wn[kF1Fetch];
+  if (u0 < u1) fetch(u0, wn);
+  for (int u = u0; u < u1 && ok; ++u) {
+    const int s = u / tps, P0 = (u - s * tps) * kF2M;
+    // decimate (the level bytes were fetched one unit ahead): d_s[i] = d[4 P0 - 12 + i]; the E4M3 copy of the samples the unit owns
+#pragma unroll
+    for (int f = 0; f < kF1Fetch; ++f) {
+      const int i = threadIdx.x + f * kThreads;
+      if (i >= kF1D) continue;
+      const int j = 4 * P0 - 12 + i;
+      float v = 0.f;
+      if (j >= 0 && j < Ld) {
+        const uint4 w = wn[f];
+        int acc = 0;
+        acc = __dp4a((int)w.x, 0x01010101, acc);
+        acc = __dp4a((int)w.y, 0x01010101, acc);
+        acc = __dp4a((int)w.z, 0x01010101, acc);
+        acc = __dp4a((int)w.w, 0x01010101, acc);
+        v = 0.25f * (float)acc;
+        if (qe && i >= 12 && i < 12 + 4 * kF2M)
+          *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
+      }
+      d_s[i] = (uint16_t)(__float_as_uint(v) >> 16);  // exact: |4 d| <= 112
+    }
+    if (u + 1 < u1) fetch(u + 1, wn);
+    __syncthreads();
+    // conv-1 im2col: tile h1 (t = 128 h1 + m), row (par, half, m) of 8 taps
+    for (int row = threadIdx.x; row < 2 * 2 * 2 * kC1M; row += kThreads) {
+      const int m = row & (kC1M - 1), h = (row >> 7) & 1, par = (row >> 8) & 1, h1 = row >> 9;
+      uint32_t wv[4];
+#pragma unroll
+      for (int e2 = 0; e2 < 4; ++e2) {
+        const int k0 = 8 * h + 2 * e2;
+        const int i0 = 2 * (kC1M * h1 + m) + par + k0;
+        const uint32_t lo = k0 < kCnnK ? d_s[i0] : 0u, hi = k0 + 1 < kCnnK ? d_s[i0 + 1] : 0u;
+        wv[e2] = lo | (hi << 16);
+      }
+      st_shared_v4(xb + (uint32_t)(h1 * kC1ABytes) + 16u * (uint32_t)(row & 511), wv[0], wv[1], wv[2], wv[3]);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {  // tile h1: odd parity -> columns 64 h1 .. +31, even -> +32 .. +63
+#pragma unroll
+      for (int h1 = 0; h1 < 2; ++h1) {
+        const uint32_t a = xb + (uint32_t)(h1 * kC1ABytes);
+        mma_bf16(tmem + 64u * (uint32_t)h1, sdesc(a + 2u * kC1M * 16, kC1M * 16, 128, 0, 0), bd1, kC1Idesc, 0u);
+        mma_bf16(tmem + 64u * (uint32_t)h1 + kCnnC, sdesc(a, kC1M * 16, 128, 0, 0), bd1, kC1Idesc, 0u);
+      }
+      mma_commit(bar1);
+    }
+    // the halo t = 256 .. 263 on the CUDA cores while the MMAs run: warp w
+    // takes t = 256 + w, lane = channel
+    float yh;
+    {
+      const int t = 2 * kF2M + warp, uu = 2 * P0 - 4 + t;
+      float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < kCnnK; ++k) {
+        const float wk = __uint_as_float((uint32_t)w1h[((k >> 3) * kCnnC + lane) * 8 + (k & 7)] << 16);
+        z0 = fmaf(__uint_as_float((uint32_t)d_s[2 * t + k] << 16), wk, z0);
+        z1 = fmaf(__uint_as_float((uint32_t)d_s[2 * t + 1 + k] << 16), wk, z1);
+      }
+      yh = (uu >= 0 && uu < L2) ? fmaxf(fmaxf(z0, z1) + __ldg(bias1 + lane), 0.f) : 0.f;
+    }
+    ok = __syncthreads_and(mbar_wait_sleep(bar1, ph1));
+    ph1 ^= 1u;
+    if (!ok) break;
+    tc_fence_after();
+    // conv-1 epilogue -> the layer-2 tile (its space held the im2col tiles)
+    {
+      const float* b1 = bias1 + 16 * ch;
+#pragma unroll 1
+      for (int h1 = 0; h1 < 2; ++h1) {
+        const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + 64u * (uint32_t)h1 + (uint32_t)(16 * ch);
+        uint32_t vo[16], ve[16];
+        tmem_ld16_nowait(col, vo);
+        tmem_ld16_nowait(col + 32u, ve);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int t = kC1M * h1 + 32 * qd + lane, uu = 2 * P0 - 4 + t;
+        const bool valid = uu >= 0 && uu < L2;
+        float y[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          y[j] = valid ? fmaxf(fmaxf(__uint_as_float(ve[j]), __uint_as_float(vo[j])) + __ldg(b1 + j), 0.f) : 0.f;
+        // generic stores after every thread's tensor-memory read of the
+        // tiles' MMAs is done: the im2col tiles they read share this space
+        const uint32_t row = xb + (uint32_t)(((t & 1) * 4 + 2 * ch) * kCvArr + 16 * (t >> 1));
+        st_shared_v4(row, pack_bf16x2_rn(y[0], y[1]), pack_bf16x2_rn(y[2], y[3]), pack_bf16x2_rn(y[4], y[5]),
+                     pack_bf16x2_rn(y[6], y[7]));
+        st_shared_v4(row + kCvArr, pack_bf16x2_rn(y[8], y[9]), pack_bf16x2_rn(y[10], y[11]),
+                     pack_bf16x2_rn(y[12], y[13]), pack_bf16x2_rn(y[14], y[15]));
+      }
+      const int t = 2 * kF2M + warp;  // the halo row: channel = lane
+      const uint32_t hrow = xb + (uint32_t)(((t & 1) * 4 + (lane >> 3)) * kCvArr + 16 * (t >> 1) + 2 * (lane & 7));
+      asm volatile("st.shared.u16 [%0], %1;" ::"r"(hrow), "h"((uint16_t)(pack_bf16x2_rn(yh, 0.f) & 0xFFFFu)) : "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {  // layer 2 into columns 0 .. 63 (layer 1's, drained)
+#pragma unroll
+      for (int w = 0; w < 10; ++w) {
+        const int par = w / 5, dd = w % 5;
+        const int t0 = 2 * dd + par;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          mma_bf16(tmem, sdesc(xb + (uint32_t)((par * 4 + 2 * h) * kCvArr + 16 * dd), kCvArr, 128, 0, 0),
+                   sdesc(wsm + (uint32_t)(((2 * h) * kCvTaps + t0) * kCnnC * 16), kCvTaps * kCnnC * 16, 128, 0, 0),
+                   kCvIdesc, (w | h) != 0);
+      }
+      mma_commit(bar2);
+    }
+    ok = __syncthreads_and(mbar_wait_sleep(bar2, ph2));
+    ph2 ^= 1u;
+    if (!ok) break;
+    tc_fence_after();
+    {
+      const int P = P0 + 32 * qd + lane;
+      const uint32_t col = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * ch);
+      uint32_t vo[16], ve[16];
+      tmem_ld16_nowait(col, vo);
+      tmem_ld16_nowait(col + 32u, ve);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (P < Lo) {
+        const float* b2 = bias2 + 16 * ch;
+        float y[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          y[j] = fmaxf(fmaxf(__uint_as_float(ve[j]), __uint_as_float(vo[j])) + __ldg(b2 + j), 0.f);
+        const int Rn = cnn_eo_rows(Lo);
+        uint16_t* o = out + ((((int64_t)s * 2 + (P & 1)) * 4 + 2 * ch) * Rn + (P >> 1) + 2) * 8;
+        *reinterpret_cast<uint4*>(o) = make_uint4(pack_bf16x2_rn(y[0], y[1]), pack_bf16x2_rn(y[2], y[3]),
+                                                  pack_bf16x2_rn(y[4], y[5]), pack_bf16x2_rn(y[6], y[7]));
+        *reinterpret_cast<uint4*>(o + (int64_t)Rn * 8) =
+            make_uint4(pack_bf16x2_rn(y[8], y[9]), pack_bf16x2_rn(y[10], y[11]),
+                       pack_bf16x2_rn(y[12], y[13]), pack_bf16x2_rn(y[14], y[15]));
+      }
+    }
+    tc_fence_before();  // the next unit's MMAs overwrite the columns after the loop's barriers
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(status, TDE_ST_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCnnC * 2)
+                 : "memory");
   }
 }
 
@@ -1362,21 +1487,23 @@ cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_cnn_conv1_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* wbf, const float* bias,
-                                uint16_t* out, uint8_t* qe, uint32_t* d_status, cudaStream_t st) {
+
+cudaError_t launch_cnn_conv12_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* w1bf, const float* bias1,
+                                 const uint16_t* w2bf, const float* bias2, uint16_t* out, uint8_t* qe,
+                                 uint32_t* d_status, cudaStream_t st) {
   if (nsig <= 0) return cudaSuccess;
   const int64_t Ld = n / kCnnDec;
-  if (n % kCnnDec != 0 || Ld % 4 != 0 || Ld > INT32_MAX) return cudaErrorInvalidValue;
-  const int64_t ctas = (int64_t)nsig * ((Ld / 2 + kC1M - 1) / kC1M);
-  if (ctas > INT32_MAX) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_conv1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kC1Smem);
+  if (n % kCnnDec != 0 || Ld % 8 != 0 || Ld > INT32_MAX) return cudaErrorInvalidValue;
+  const int64_t units = (int64_t)nsig * ((Ld / 4 + kF2M - 1) / kF2M);
+  if (units > INT32_MAX) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_conv12_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kF12Smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t cap = 4 * (int64_t)sms;  // persistent: four CTAs per SM, contiguous tile runs
-  const int grid = (int)(ctas < cap ? ctas : cap);
-  k_conv1_tc<<<grid, kThreads, kC1Smem, st>>>(q, n, nsig, wbf, bias, out, qe, d_status);
+  const int64_t cap = 4 * (int64_t)sms;  // persistent: four CTAs per SM, contiguous unit runs
+  const int grid = (int)(units < cap ? units : cap);
+  k_conv12_tc<<<grid, kThreads, kF12Smem, st>>>(q, n, nsig, w1bf, bias1, w2bf, bias2, out, qe, d_status);
   TDE_COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

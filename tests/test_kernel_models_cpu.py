@@ -374,3 +374,44 @@ def test_scores_key_orders_bins_like_better():
         u = k1 >> 32
         bits = (u ^ 0x80000000) if u & 0x80000000 else (~u & 0xFFFFFFFF)
         assert np.array(bits, np.uint32).view(np.float32) == np.float32(s1)
+
+
+def test_conv12_unit_builds_layer2_tile_and_owns_each_level_once():
+    """k_conv12_tc's unit (layer-2 tile P0, 128 outputs): the decimated
+    window d[4 P0 - 12 + i] (i < 536), layer-1 outputs t < 256 from the
+    im2col rows (tile t // 128, parity, taps 2 t + par + k) and t = 256..263
+    from the halo formula, written to E/O rows t // 2 of parity t % 2, equal
+    the direct conv + bias + ReLU + pool of layer 1 at u = 2 P0 - 4 + t (zero
+    outside [0, Ld / 2)); and the units' owned samples [4 P0, 4 P0 + 512)
+    cover the decimated signal once."""
+    rng = np.random.default_rng(8)
+    for Ld in (1024, 4096, 512):
+        d = rng.integers(-16, 17, Ld) / 4.0
+        w = rng.normal(size=(32, 9))
+        b = rng.normal(size=32)
+        L2 = Ld // 2
+        # direct layer 1: z[v] = sum_k d[v + k - 4] w[k], pooled pairs (2u, 2u + 1)
+        dp = np.concatenate([np.zeros(4), d, np.zeros(4)])
+        z = np.stack([dp[v:v + 9] @ w.T for v in range(Ld)])
+        x2 = np.maximum(np.maximum(z[0::2], z[1::2]) + b, 0)  # [L2][32]
+        Lo = L2 // 2
+        tps = -(-Lo // 128)
+        owned = np.zeros(Ld, int)
+        for unit in range(tps):
+            P0 = unit * 128
+            ds = np.array([d[j] if 0 <= j < Ld else 0.0 for j in range(4 * P0 - 12, 4 * P0 - 12 + 536)])
+            for i in range(12, 12 + 512):
+                j = 4 * P0 - 12 + i
+                if 0 <= j < Ld:
+                    owned[j] += 1
+            E = np.full((132, 32), np.nan); O = np.full((132, 32), np.nan)
+            for t in range(264):
+                zz = [ds[2 * t + par:2 * t + par + 9] @ w.T for par in (0, 1)]
+                uu = 2 * P0 - 4 + t
+                y = np.maximum(np.maximum(zz[0], zz[1]) + b, 0) if 0 <= uu < L2 else np.zeros(32)
+                (E if t % 2 == 0 else O)[t // 2] = y
+            for r in range(132):
+                for arr, pos in ((E, 2 * (P0 + r) - 4), (O, 2 * (P0 + r) - 3)):
+                    want = x2[pos] if 0 <= pos < L2 else np.zeros(32)
+                    assert np.allclose(arr[r], want), (Ld, unit, r)
+        assert (owned == 1).all(), Ld
