@@ -1069,20 +1069,39 @@ __device__ __forceinline__ unsigned long long pack_key(int32_t v, int64_t tau) {
   return ((unsigned long long)((uint32_t)v ^ 0x80000000u) << 32) | (0xFFFFFFFFu - rank);
 }
 
+// The pair's 8 window descriptors are staged in shared memory first, so that
+// every thread's loads of window values are independent (flat index f over
+// the 8 x 257 slots: window f / 257, lag lag_lo + f % 257 when inside it).
 __global__ void __launch_bounds__(kThreads) k_window_argmax(const WinJob* __restrict__ jobs,
                                                             int64_t* __restrict__ lag,
                                                             int64_t* __restrict__ val) {
   __shared__ unsigned long long red[kThreads / 32];
+  __shared__ WinJob js[kCnnTopK];
   const int p = blockIdx.x;
-  unsigned long long best = 0;
-  for (int w = 0; w < kCnnTopK; ++w) {
-    const WinJob J = jobs[(int64_t)p * kCnnTopK + w];
-    const int64_t cnt = J.lag_hi - J.lag_lo + 1;
-    for (int64_t i = threadIdx.x; i < cnt; i += kThreads) {
-      const unsigned long long k = pack_key(J.c[i], J.lag_lo + i);
-      best = k > best ? k : best;
+  if (threadIdx.x < kCnnTopK) js[threadIdx.x] = jobs[(int64_t)p * kCnnTopK + threadIdx.x];
+  __syncthreads();
+  constexpr int kPer = (kCnnTopK * kCnnWin + kThreads - 1) / kThreads;
+  int32_t v[kPer];
+  int64_t tau[kPer];
+  bool in[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int f = threadIdx.x + r * kThreads, w = f / kCnnWin, i = f - w * kCnnWin;
+    in[r] = false;
+    if (w < kCnnTopK) {
+      const WinJob& J = js[w];
+      in[r] = i <= J.lag_hi - J.lag_lo;
+      tau[r] = J.lag_lo + i;
+      if (in[r]) v[r] = J.c[i];
     }
   }
+  unsigned long long best = 0;
+#pragma unroll
+  for (int r = 0; r < kPer; ++r)
+    if (in[r]) {
+      const unsigned long long k = pack_key(v[r], tau[r]);
+      best = k > best ? k : best;
+    }
   for (int o = 16; o; o >>= 1) {
     const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
     best = t > best ? t : best;
