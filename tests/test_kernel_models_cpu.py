@@ -415,4 +415,3 @@ def test_conv12_unit_builds_layer2_tile_and_owns_each_level_once():
                     want = x2[pos] if 0 <= pos < L2 else np.zeros(32)
                     assert np.allclose(arr[r], want), (Ld, unit, r)
         assert (owned == 1).all(), Ld
-
