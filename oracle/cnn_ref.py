@@ -6,8 +6,9 @@ library documents (include/tde.h: 16x block-sum decimation / 4, four
 [conv k9 pad 4, 32 channels, bias, ReLU, max-pool 2] layers shared by x and
 y, score[l] = alpha sum_c sum_i fx[c][i] fy[c][i + l]).  The proposal is not
 part of the paper's method; these are the definitions its kernels must match.
-Parity: this file is the reference; its own pin is a finite-difference check
-of its gradient (tests/test_cnn_ref_cpu.py).
+Parity: this file is the reference; its pins (tests/test_cnn_ref_cpu.py) are a
+finite-difference check of its gradient, the forward restated as explicit
+sums, and a closed form with pass-through weights.
 """
 from __future__ import annotations
 
