@@ -13,7 +13,7 @@ steps.
 Two forms run on the same pairs: the full form (every lag, one planned batch
 replayed from its CUDA graph) and the learned-proposal form (the shipped
 checkpoint; its whole step, fallback included, replayed from a CUDA graph).
-The learned form is timed with --in-flight batches (default 3) in flight on
+The learned form is timed with --in-flight batches (default 6) in flight on
 separate streams, each its own planned graph, and with one stream
 (learned_proposal.single_stream); both count every pair of every step.
 
@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
-    ap.add_argument("--in-flight", type=int, default=3,
+    ap.add_argument("--in-flight", type=int, default=6,
                     help="learned form: batches in flight on separate streams (1 = one stream)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--agree-pairs", type=int, default=16384,
