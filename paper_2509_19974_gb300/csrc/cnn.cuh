@@ -69,7 +69,8 @@ cudaError_t launch_cnn_conv_tc(const uint16_t* in, void* out, int L, int nsig, c
 // output (layer 2's input) stays in shared memory, then conv 32 -> 32 (w2bf,
 // bias2); out = the third layer's input (length n/64, parity arrays with
 // their zero rows); qe (nullable, nsig x n bytes) receives the levels as E4M3
-// bytes.  n/16 a multiple of 8.  Time-outs set TDE_ST_TIMEOUT.
+// bytes, for levels in {-1, 0, 1} (the learned path's b <= 2; other levels
+// give other bytes).  n/16 a multiple of 8.  Time-outs set TDE_ST_TIMEOUT.
 cudaError_t launch_cnn_conv12_tc(const int8_t* q, int64_t n, int nsig, const uint16_t* w1bf, const float* bias1,
                                  const uint16_t* w2bf, const float* bias2, uint16_t* out, uint8_t* qe,
                                  uint32_t* d_status, cudaStream_t st);

@@ -1247,8 +1247,15 @@ __global__ void __launch_bounds__(kThreads, 4)
         acc = __dp4a((int)w.z, 0x01010101, acc);
         acc = __dp4a((int)w.w, 0x01010101, acc);
         v = 0.25f * (float)acc;
-        if (qe && i >= 12 && i < 12 + 4 * kF2M)
-          *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e4m3x16(w);
+        if (qe && i >= 12 && i < 12 + 4 * kF2M) {
+          // levels in {-1, 0, 1} (bit 0 set iff non-zero, bit 7 the sign):
+          // E4M3 bytes 0x00, 0x38 = 1.0, 0xB8 = -1.0
+          const uint4 e = make_uint4(((w.x & 0x01010101u) * 0x38u) | (w.x & 0x80808080u),
+                                     ((w.y & 0x01010101u) * 0x38u) | (w.y & 0x80808080u),
+                                     ((w.z & 0x01010101u) * 0x38u) | (w.z & 0x80808080u),
+                                     ((w.w & 0x01010101u) * 0x38u) | (w.w & 0x80808080u));
+          *reinterpret_cast<uint4*>(qe + (int64_t)s * n + (int64_t)j * kCnnDec) = e;
+        }
       }
       d_s[i] = (uint16_t)(__float_as_uint(v) >> 16);  // exact: |4 d| <= 112
     }

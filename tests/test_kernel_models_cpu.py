@@ -415,3 +415,17 @@ def test_conv12_unit_builds_layer2_tile_and_owns_each_level_once():
                     want = x2[pos] if 0 <= pos < L2 else np.zeros(32)
                     assert np.allclose(arr[r], want), (Ld, unit, r)
         assert (owned == 1).all(), Ld
+
+
+def test_conv12_e4m3_bytes_of_unit_levels():
+    """k_conv12_tc's E4M3 copy of levels in {-1, 0, 1}: per word
+    ((w & 0x01010101) * 0x38) | (w & 0x80808080) gives 0x00 for 0, 0x38 (1.0)
+    for 1 and 0xB8 (-1.0) for -1 in every byte of every combination."""
+    import itertools
+    enc = {0: 0x00, 1: 0x38, -1: 0xB8}
+    for lv in itertools.product((-1, 0, 1), repeat=4):
+        w = 0
+        for k, v in enumerate(lv):
+            w |= (v & 0xFF) << (8 * k)
+        e = (((w & 0x01010101) * 0x38) | (w & 0x80808080)) & 0xFFFFFFFF
+        assert all(((e >> (8 * k)) & 0xFF) == enc[v] for k, v in enumerate(lv)), lv
